@@ -1,0 +1,498 @@
+"""Pins of the FP64 oracle against facts the paper and the mathematics fix.
+
+Each test names the passage that fixes the expected value.  None of them
+re-types the oracle's own formula: they use closed forms, brute-force
+minimisation of the primal, optimality (KKT) conditions, invariants or an
+independent form of the same operation (Algorithm 1 vs Algorithm 2 vs the
+log-domain form; separable vs dense kernel).
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import optimize
+
+import oracle as O
+from paper_1607_05816_gb300 import synth
+
+pytestmark = pytest.mark.filterwarnings("ignore::RuntimeWarning")
+
+
+def small_problem(n, m, seed, d=1, zeros=False):
+    g = synth.rng(seed)
+    x = g.uniform(0, 1, size=(n, d))
+    y = g.uniform(0, 1, size=(m, d))
+    dx = g.uniform(0.5, 1.5, size=n)
+    dx /= dx.sum()
+    dy = g.uniform(0.5, 1.5, size=m)
+    dy /= dy.sum()
+    p = g.uniform(0.3, 2.0, size=n)
+    q = g.uniform(0.3, 2.0, size=m)
+    if zeros:
+        p[0] = 0.0
+    return O.Geometry("points", x=x, y=y), dx, dy, p, q
+
+
+# --------------------------------------------------------------------------
+# log-sum-exp and the Gibbs operator
+# --------------------------------------------------------------------------
+
+def test_lse_conventions():
+    assert O.lse(np.array([-np.inf, -np.inf])) == -np.inf
+    z = np.array([1.0, 2.0, -3.0])
+    assert abs(O.lse(z) - math.log(sum(math.exp(t) for t in z))) < 1e-15
+    big = np.array([1000.0, 1000.0])
+    assert abs(O.lse(big) - (1000.0 + math.log(2.0))) < 1e-12
+
+
+def test_gibbs_operator_matches_definition():
+    """eps log K(b.dy) with K = exp(-C/eps) (Sec. 4.2), by plain sums."""
+    geom, dx, dy, p, q = small_problem(5, 4, 1)
+    eps = 0.3
+    V = np.array([0.1, -0.2, 0.3, 0.05])
+    C = geom.cost_matrix()
+    K = np.exp(-C / eps)
+    expect = eps * np.log(K @ (np.exp(V / eps) * dy))
+    got = O.apply_K_log(geom, V, np.log(dy), eps)
+    assert np.max(np.abs(got - expect)) < 1e-14
+    expectT = eps * np.log(K.T @ (np.exp(np.zeros(5) / eps) * dx))
+    gotT = O.apply_K_log(geom, np.zeros(5), np.log(dx), eps, transpose=True)
+    assert np.max(np.abs(gotT - expectT)) < 1e-14
+
+
+@pytest.mark.parametrize("shape_x,shape_y", [((6, 5), (6, 5)), ((4, 7), (5, 3)), ((9,), (7,)), ((3, 4, 2), (2, 3, 3))])
+def test_separable_equals_dense(shape_x, shape_y):
+    """The separable grid kernel (successive 1-D operations, Sec. 4.4) equals
+    the full kernel on the product grid."""
+    g = synth.rng(7)
+    xs = [np.sort(g.uniform(0, 1, n)) for n in shape_x]
+    ys = [np.sort(g.uniform(0, 1, n)) for n in shape_y]
+    geom = O.Geometry("grid", xs=xs, ys=ys)
+    eps = 0.02
+    V = g.normal(size=shape_y) * 0.05
+    logw = np.log(g.uniform(0.5, 1.0, size=shape_y))
+    a = O.apply_K_log(geom, V, logw, eps, separable=True)
+    b = O.apply_K_log(geom, V, logw, eps, separable=False)
+    assert a.shape == tuple(shape_x)
+    assert np.max(np.abs(a - b)) < 1e-12
+    U = g.normal(size=shape_x) * 0.05
+    logwx = np.log(g.uniform(0.5, 1.0, size=shape_x))
+    a = O.apply_K_log(geom, U, logwx, eps, transpose=True, separable=True)
+    b = O.apply_K_log(geom, U, logwx, eps, transpose=True, separable=False)
+    assert np.max(np.abs(a - b)) < 1e-12
+
+
+# --------------------------------------------------------------------------
+# Table 1: each prox row against scalar brute-force minimisation
+# --------------------------------------------------------------------------
+
+def scalar_prox_brute(F, s, p, eps):
+    """argmin_{t>=0} eps KLbar(t|s) + Dbar_F(t|p), KLbar(t|s)=t log(t/s)-t+s."""
+    def obj(lt):
+        t = math.exp(lt)
+        val = eps * (t * (lt - math.log(s)) - t + s)
+        if F.kind == "kl":
+            val += F.lam * (t * math.log(t / p) - t + p)
+        elif F.kind == "tv":
+            val += F.lam * abs(t - p)
+        elif F.kind == "rg":
+            lo, hi = F.alpha * p, F.beta * p
+            if t < lo * (1 - 1e-15) or t > hi * (1 + 1e-15):
+                return 1e300
+        return val
+    if F.kind == "eq":
+        return p
+    if F.kind == "rg":
+        lo = math.log(F.alpha * p) if F.alpha > 0 else math.log(s) - 50
+        hi = math.log(F.beta * p) if not math.isinf(F.beta) else math.log(s) + 50
+        if lo > math.log(s):
+            return F.alpha * p
+        if hi < math.log(s):
+            return F.beta * p
+        return s
+    lo = min(math.log(s), math.log(p)) - 1.0
+    hi = max(math.log(s), math.log(p)) + 1.0
+    r = optimize.minimize_scalar(obj, bounds=(lo, hi), method="bounded", options=dict(xatol=1e-12))
+    # polish with a dense scan around the minimiser for the kinked TV case
+    grid = r.x + np.linspace(-1e-3, 1e-3, 20001)
+    vals = [obj(t) for t in grid]
+    return math.exp(grid[int(np.argmin(vals))])
+
+
+@pytest.mark.parametrize("F", [O.KL(0.7), O.KL(5.0), O.TV(0.05), O.TV(0.8), O.RG(0.7, 1.2), O.RG(0.0, 2.0), O.RG(0.5, math.inf), O.EQ()])
+def test_prox_rows_brute_force(F):
+    """Middle column of Table 1 equals the scalar minimiser of
+    eps KL(t|s) + D_phi(t|p) (definition of prox^KL, Sec. 3.3)."""
+    g = synth.rng(11)
+    for _ in range(25):
+        s = float(np.exp(g.uniform(-3, 3)))
+        p = float(np.exp(g.uniform(-2, 2)))
+        eps = float(np.exp(g.uniform(-3, 0)))
+        got = math.exp(O.prox_target_log(F, np.array([math.log(p)]), np.array([eps * math.log(s)]), eps)[0])
+        want = scalar_prox_brute(F, s, p, eps)
+        assert abs(got - want) <= 2e-6 * max(want, 1e-12), (F, s, p, eps, got, want)
+
+
+@pytest.mark.parametrize("F", [O.KL(0.4), O.TV(0.3), O.RG(0.6, 1.5), O.RG(0.0, math.inf), O.EQ()])
+def test_stabilized_proxdiv_equals_log_update(F):
+    """Table 1's proxdiv(s, u, eps) with u != 0 (Sec. 4.3) is the total-potential
+    update shifted by u: eps log proxdiv(s~, u) = U(eps log s~ - u) - u."""
+    g = synth.rng(12)
+    eps = 0.05
+    s = np.exp(g.uniform(-4, 4, size=64))
+    u = g.uniform(-0.5, 0.5, size=64)
+    p = np.exp(g.uniform(-2, 2, size=64))
+    lhs = eps * np.log(O.proxdiv(F, p, s, u, eps))
+    rhs = O.prox_update_log(F, np.log(p), eps * np.log(s) - u, eps) - u
+    assert np.max(np.abs(lhs - rhs)) < 1e-12
+
+
+def test_balanced_rows():
+    """Table 1: RG[1,1] is the equality row; lam KL and lam TV tend to it as lam -> inf."""
+    g = synth.rng(13)
+    eps = 0.1
+    S = g.uniform(-1, 1, size=50)
+    lp = g.uniform(-1, 1, size=50)
+    eq = O.prox_update_log(O.EQ(), lp, S, eps)
+    assert np.array_equal(O.prox_update_log(O.RG(1.0, 1.0), lp, S, eps), eq)
+    assert np.max(np.abs(O.prox_update_log(O.KL(1e9), lp, S, eps) - eq)) < 1e-8
+    assert np.array_equal(O.prox_update_log(O.TV(1e9), lp, S, eps), eq)
+
+
+def test_zero_mass_conventions():
+    """Prop. 5.1 with 0/0 = 0: s = 0 gives a = 0; p = 0 gives a = 0 except for
+    TV (phi'_inf = 1: eps log(s*/s) = -lam) and RG with beta = inf."""
+    eps = 0.1
+    S = np.array([0.2, -np.inf, 0.2])
+    lp = np.array([-np.inf, 0.0, 0.0])
+    for F in (O.EQ(), O.KL(1.0), O.RG(0.5, 2.0)):
+        U = O.prox_update_log(F, lp, S, eps)
+        assert np.isneginf(U[0]) and np.isneginf(U[1]) and np.isfinite(U[2])
+    U = O.prox_update_log(O.TV(0.3), lp, S, eps)
+    assert U[0] == -0.3 and np.isneginf(U[1])
+    U = O.prox_update_log(O.RG(0.5, math.inf), lp, S, eps)
+    assert U[0] == 0.0
+
+
+# --------------------------------------------------------------------------
+# one-point problems: closed forms
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("l1,l2,eps,c,p,q", [(1.0, 1.0, 0.5, 0.3, 1.0, 2.0), (0.2, 3.0, 0.1, 1.0, 0.5, 1.7), (5.0, 0.5, 0.05, 0.0, 2.0, 0.3)])
+def test_one_point_kl_closed_form(l1, l2, eps, c, p, q):
+    """n = m = 1, dx = dy = 1: stationarity of l1 KL(r|p) + l2 KL(r|q) + eps KL(r|e^{-c/eps})
+    gives log r* = (l1 log p + l2 log q - c)/(l1 + l2 + eps)."""
+    geom = O.Geometry("dense", C=np.array([[c]]))
+    one = np.ones(1)
+    r = O.solve_log(geom, one, one, np.array([p]), np.array([q]), O.KL(l1), O.KL(l2), eps, max_iter=4000)
+    logr = (r["U"][0] + r["V"][0] - c) / eps
+    want = (l1 * math.log(p) + l2 * math.log(q) - c) / (l1 + l2 + eps)
+    assert abs(logr - want) < 1e-13
+
+
+@pytest.mark.parametrize("F1,F2", [(O.TV(0.3), O.TV(0.2)), (O.TV(0.05), O.KL(1.0)), (O.RG(0.7, 1.2), O.KL(0.5)), (O.EQ(), O.KL(0.5)), (O.RG(0.5, 2.0), O.RG(0.8, 1.5))])
+def test_one_point_piecewise_brute(F1, F2):
+    """One-point primal F1(r) + F2(r) + eps KL(r|e^{-c/eps}) minimised by brute force."""
+    eps, c, p, q = 0.1, 0.2, 1.0, 1.6
+    geom = O.Geometry("dense", C=np.array([[c]]))
+    one = np.ones(1)
+    r = O.solve_log(geom, one, one, np.array([p]), np.array([q]), F1, F2, eps, max_iter=3000)
+    got = math.exp((r["U"][0] + r["V"][0] - c) / eps)
+
+    def obj(lt):
+        t = math.exp(lt)
+        v = eps * (t * (lt + c / eps) - t + math.exp(-c / eps))
+        v1 = O.div_value(F1, np.array([t]), np.array([p]), one)
+        v2 = O.div_value(F2, np.array([t]), np.array([q]), one)
+        return v + (v1 if math.isfinite(v1) else 1e300) + (v2 if math.isfinite(v2) else 1e300)
+    grid = np.linspace(-4, 4, 80001)
+    vals = np.array([obj(t) for t in grid])
+    k = int(np.argmin(vals))
+    fine = grid[k] + np.linspace(-2e-4, 2e-4, 40001)
+    best = fine[int(np.argmin([obj(t) for t in fine]))]
+    assert abs(math.log(got) - best) < 2e-8, (got, math.exp(best))
+
+
+# --------------------------------------------------------------------------
+# Algorithms 1 and 2 and the log-domain form
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("F1,F2", [(O.KL(0.5), O.KL(0.1)), (O.TV(0.2), O.KL(1.0)), (O.RG(0.7, 1.2), O.TV(0.3)), (O.EQ(), O.EQ()), (O.KL(1.0), O.RG(0.0, 1.5))])
+def test_alg1_alg2_logdomain_agree(F1, F2):
+    """Algorithm 1, Algorithm 2 (absorbing when |log a~| > tau) and the log-domain
+    form are reparametrisations of one iteration (Sec. 4.3), so their iterates agree."""
+    geom, dx, dy, p, q = small_problem(7, 5, 3)
+    eps, iters = 0.08, 60
+    C = geom.cost_matrix()
+    a, b = O.scaling_alg1(np.exp(-C / eps), dx, dy, p, q, F1, F2, eps, iters)
+    U1, V1 = eps * np.log(a), eps * np.log(b)
+    U2, V2, nabs = O.scaling_alg2(C, dx, dy, p, q, F1, F2, eps, iters, tau=0.5)
+    assert nabs > 0
+    U3, V3 = O.iterate_log(geom, np.log(dx), np.log(dy), np.log(p), np.log(q), F1, F2, eps, iters)
+    for A, B in ((U1, U3), (V1, V3), (U2, U3), (V2, V3)):
+        assert np.max(np.abs(A - B)) < 1e-11 * max(1.0, np.max(np.abs(B)))
+
+
+def test_alg2_reaches_small_eps_where_alg1_fails():
+    """Sec. 4.3: for small eps, K underflows and Algorithm 1 breaks down while the
+    stabilized iteration stays finite and optimal (KKT for KL: r1 = p e^{-U/lam})."""
+    geom, dx, dy, p, q = small_problem(6, 6, 4)
+    eps = 1e-5
+    C = geom.cost_matrix()
+    with np.errstate(all="ignore"):
+        a, b = O.scaling_alg1(np.exp(-C / eps), dx, dy, p, q, O.KL(1.0), O.KL(1.0), eps, 50)
+    assert np.any(a == 0) or np.any(b == 0) or not np.all(np.isfinite(a * b.sum()))
+    U, V = O.iterate_log(geom, np.log(dx), np.log(dy), np.log(p), np.log(q), O.KL(1.0), O.KL(1.0), eps, 3000)
+    assert np.all(np.isfinite(U)) and np.all(np.isfinite(V))
+    r1, r2 = O.marginals(geom, dx, dy, U, V, eps)
+    # after the b-update the second marginal satisfies -V in dF2(r2) exactly
+    assert np.max(np.abs(r2 - q * np.exp(-V / 1.0)) / r2) < 1e-10
+
+
+# --------------------------------------------------------------------------
+# convergence theory
+# --------------------------------------------------------------------------
+
+def test_thompson_contraction_kl_kl():
+    """Theorem 3.10: for lam1 KL / lam2 KL the map a^l -> a^{l+1} contracts the
+    Thompson metric d(a,a') = max |log a - log a'| by z1 z2, z_i = lam_i/(lam_i+eps)."""
+    geom, dx, dy, p, q = small_problem(8, 6, 5)
+    l1, l2, eps = 0.7, 1.3, 0.05
+    z = (l1 / (l1 + eps)) * (l2 / (l2 + eps))
+    logs = (np.log(dx), np.log(dy), np.log(p), np.log(q))
+    U, V = None, None
+    Us = []
+    for _ in range(40):
+        U, V = O.iterate_log(geom, *logs, O.KL(l1), O.KL(l2), eps, 1, U, V)
+        Us.append(U.copy())
+    d = [np.max(np.abs(Us[k + 1] - Us[k])) / eps for k in range(len(Us) - 1)]
+    for k in range(len(d) - 1):
+        if d[k] > 1e-13:
+            assert d[k + 1] <= z * d[k] * (1 + 1e-9) + 1e-14
+
+
+@pytest.mark.parametrize("F1,F2", [(O.KL(0.5), O.KL(0.5)), (O.TV(0.3), O.TV(0.2)), (O.KL(0.1), O.TV(0.5))])
+def test_duality_gap(F1, F2):
+    """Theorem 3.2 / 4.1: P_eps >= D_eps at every iterate, the gap equals the two
+    Fenchel-Young gaps F(r) + F*(-U) + <U, r>, and it goes to 0."""
+    geom, dx, dy, p, q = small_problem(6, 5, 6)
+    eps = 0.05
+    logs = (np.log(dx), np.log(dy), np.log(p), np.log(q))
+    U, V = None, None
+    gaps = []
+    for it in range(400):
+        U, V = O.iterate_log(geom, *logs, F1, F2, eps, 1, U, V)
+        if it % 20 == 0 or it == 399:
+            P = O.primal(geom, dx, dy, p, q, F1, F2, eps, U, V)
+            D = O.dual(geom, dx, dy, p, q, F1, F2, eps, U, V)
+            r1, r2 = O.marginals(geom, dx, dy, U, V, eps)
+            fy = (O.div_value(F1, r1, p, dx) + O.div_conj(F1, -U, p, dx) + np.sum(dx * U * r1)
+                  + O.div_value(F2, r2, q, dy) + O.div_conj(F2, -V, q, dy) + np.sum(dy * V * r2))
+            assert P - D >= -1e-13
+            assert abs((P - D) - fy) < 1e-11
+            gaps.append(P - D)
+    assert gaps[-1] < 1e-10
+    assert gaps[-1] < gaps[1]
+
+
+def newton_primal_kl(C, dx, dy, p, q, l1, l2, eps):
+    """Brute-force minimiser of the KL/KL primal (eq. primal_discr with dx dy
+    weights): damped Newton in R with the analytic Hessian
+      H_(ij),(kl) = w_ij [l1 d_ik dy_l / r1_i + l2 d_jl dx_k / r2_j + eps d_ik d_jl / R_ij],
+    steps kept inside R > 0 and backtracked on the objective.  Returns log R."""
+    n, m = C.shape
+    W = dx[:, None] * dy[None, :]
+    K = np.exp(-C / eps)
+
+    def f(R):
+        r1, r2 = R @ dy, R.T @ dx
+        kl1 = l1 * np.sum(dx * (r1 * np.log(r1 / p) - r1 + p))
+        kl2 = l2 * np.sum(dy * (r2 * np.log(r2 / q) - r2 + q))
+        return kl1 + kl2 + eps * np.sum(W * (R * np.log(R / K) - R + K))
+
+    R = np.ones((n, m))
+    for _ in range(500):
+        r1, r2 = R @ dy, R.T @ dx
+        g = (W * (l1 * np.log(r1 / p)[:, None] + l2 * np.log(r2 / q)[None, :] + eps * np.log(R) + C)).ravel()
+        if np.max(np.abs(g / W.ravel())) < 1e-15:
+            break
+        H = np.zeros((n * m, n * m))
+        for i in range(n):
+            for j in range(m):
+                for k in range(n):
+                    for l in range(m):
+                        v = 0.0
+                        if i == k:
+                            v += l1 * dy[l] / r1[i]
+                        if j == l:
+                            v += l2 * dx[k] / r2[j]
+                        if i == k and j == l:
+                            v += eps / R[i, j]
+                        H[i * m + j, k * m + l] = W[i, j] * v
+        step = -np.linalg.solve(H, g).reshape(n, m)
+        t = 1.0
+        neg = step < 0
+        if np.any(neg):
+            t = min(1.0, 0.99 * np.min(-R[neg] / step[neg]))
+        f0 = f(R)
+        while f(R + t * step) > f0 + 1e-4 * t * (g @ step.ravel()) and t > 1e-14:
+            t *= 0.5
+        R = R + t * step
+    return np.log(R)
+
+
+@pytest.mark.parametrize("n,m", [(1, 3), (3, 2), (4, 4)])
+def test_brute_force_primal_kl(n, m):
+    """The converged iteration minimises the primal (Prop. 3.8): compare the plan
+    to an independent Newton minimisation of the primal on tiny problems."""
+    geom, dx, dy, p, q = small_problem(n, m, 20 + n)
+    l1, l2, eps = 0.6, 0.9, 0.1
+    C = geom.cost_matrix()
+    Z = newton_primal_kl(C, dx, dy, p, q, l1, l2, eps)
+    r = O.solve_log(geom, dx, dy, p, q, O.KL(l1), O.KL(l2), eps, max_iter=3000)
+    LR = O.log_plan(geom, r["U"], r["V"], eps)
+    assert np.max(np.abs(LR - Z)) < 1e-9
+
+
+@pytest.mark.parametrize("F1,F2", [(O.TV(0.2), O.TV(0.3)), (O.RG(0.7, 1.2), O.RG(0.8, 1.5)), (O.TV(0.1), O.KL(0.5)), (O.EQ(), O.KL(0.4))])
+def test_kkt_optimality(F1, F2):
+    """Theorem 3.2: (U, V) is optimal iff -U in dF1(r1), -V in dF2(r2) with
+    R = e^{(U+V-C)/eps}.  Checked on the converged iterate from the subdifferentials
+    of the divergences (Prop. A.3)."""
+    geom, dx, dy, p, q = small_problem(6, 7, 30)
+    eps = 0.05
+    r = O.solve_log(geom, dx, dy, p, q, F1, F2, eps, max_iter=20000, tol=1e-14)
+    U, V = r["U"], r["V"]
+    r1, r2 = O.marginals(geom, dx, dy, U, V, eps)
+    for F, W, rr, pp in ((F1, U, r1, p), (F2, V, r2, q)):
+        if F.kind == "tv":
+            lam = F.lam
+            assert np.all(np.abs(W) <= lam * (1 + 1e-10))
+            above = rr > pp * (1 + 1e-8)
+            below = rr < pp * (1 - 1e-8)
+            assert np.allclose(W[above], -lam, atol=1e-9)
+            assert np.allclose(W[below], lam, atol=1e-9)
+        elif F.kind == "rg":
+            assert np.all(rr >= F.alpha * pp * (1 - 1e-8)) and np.all(rr <= F.beta * pp * (1 + 1e-8))
+            inside = (rr > F.alpha * pp * (1 + 1e-8)) & (rr < F.beta * pp * (1 - 1e-8))
+            assert np.allclose(W[inside], 0.0, atol=1e-9)
+            assert np.all(W[rr >= F.beta * pp * (1 - 1e-8)] <= 1e-9)
+            assert np.all(W[rr <= F.alpha * pp * (1 + 1e-8)] >= -1e-9)
+        elif F.kind == "kl":
+            # -U = lam log(r/p)
+            assert np.allclose(-W, F.lam * np.log(rr / pp), atol=1e-9)
+        elif F.kind == "eq":
+            assert np.allclose(rr, pp, rtol=1e-9)
+
+
+def test_tv_primal_slsqp():
+    """Brute-force TV/TV primal with split variables (r - p = t+ - t-) by SLSQP;
+    the converged iteration reaches the same objective value and plan."""
+    geom, dx, dy, p, q = small_problem(3, 3, 40)
+    l1, l2, eps = 0.2, 0.3, 0.1
+    C = geom.cost_matrix()
+    n, m = C.shape
+    W = dx[:, None] * dy[None, :]
+    K = np.exp(-C / eps)
+    N = n * m
+
+    def unpack(xv):
+        return xv[:N].reshape(n, m), xv[N:N + n], xv[N + n:N + 2 * n], xv[N + 2 * n:N + 2 * n + m], xv[N + 2 * n + m:]
+
+    def f(xv):
+        R, a1, b1, a2, b2 = unpack(xv)
+        R = np.maximum(R, 1e-300)
+        return eps * np.sum(W * (R * np.log(R / K) - R + K)) + l1 * np.sum(dx * (a1 + b1)) + l2 * np.sum(dy * (a2 + b2))
+
+    cons = [{"type": "eq", "fun": lambda xv: unpack(xv)[0] @ dy - p - unpack(xv)[1] + unpack(xv)[2]},
+            {"type": "eq", "fun": lambda xv: unpack(xv)[0].T @ dx - q - unpack(xv)[3] + unpack(xv)[4]}]
+    x0 = np.concatenate([np.ones(N), np.zeros(2 * n + 2 * m)])
+    bounds = [(1e-12, None)] * N + [(0, None)] * (2 * n + 2 * m)
+    res = optimize.minimize(f, x0, method="SLSQP", constraints=cons, bounds=bounds,
+                            options=dict(ftol=1e-15, maxiter=2000))
+    r = O.solve_log(geom, dx, dy, p, q, O.TV(l1), O.TV(l2), eps, max_iter=20000, tol=1e-15)
+    P = O.primal(geom, dx, dy, p, q, O.TV(l1), O.TV(l2), eps, r["U"], r["V"])
+    assert P <= res.fun + 1e-9
+    assert abs(P - res.fun) < 1e-6
+    R = np.exp(O.log_plan(geom, r["U"], r["V"], eps))
+    assert np.max(np.abs(R - unpack(res.x)[0])) < 1e-3 * np.max(R)
+
+
+def test_eps_scaling_same_fixed_point():
+    """eps-scaling (Sec. 4.4) only changes the starting point; by uniqueness of the
+    solution (Theorem 3.2) it ends at the cold-start fixed point."""
+    geom, dx, dy, p, q = small_problem(8, 8, 50)
+    eps = 0.01
+    a = O.solve_log(geom, dx, dy, p, q, O.KL(0.5), O.KL(0.5), eps, max_iter=20000, tol=1e-13)
+    b = O.solve_log(geom, dx, dy, p, q, O.KL(0.5), O.KL(0.5), eps, max_iter=20000, tol=1e-13,
+                    eps_start=1.0, stages=10, iters_per_stage=50)
+    assert np.max(np.abs(a["U"] - b["U"])) < 1e-9
+    assert np.max(np.abs(a["V"] - b["V"])) < 1e-9
+    assert b["iters"] < a["iters"]
+
+
+def test_marginal_violation_is_sinkhorn_error_when_balanced():
+    """For the equality constraint the stopping criterion is the L1(dx) marginal
+    error of the plan relative to the mass of p (classical Sinkhorn)."""
+    geom, dx, dy, p, q = small_problem(5, 6, 60)
+    q = q * (np.sum(p * dx) / np.sum(q * dy))
+    eps = 0.1
+    U, V = O.iterate_log(geom, np.log(dx), np.log(dy), np.log(p), np.log(q), O.EQ(), O.EQ(), eps, 7)
+    r1, _ = O.marginals(geom, dx, dy, U, V, eps)
+    want = np.sum(dx * np.abs(r1 - p)) / np.sum(dx * p)
+    got = O.marginal_violation(geom, dx, dy, p, q, O.EQ(), O.EQ(), eps, U, V)
+    assert abs(got - want) < 1e-13
+
+
+# --------------------------------------------------------------------------
+# barycenters (Sec. 5.2, Table 2, Appendix A.3)
+# --------------------------------------------------------------------------
+
+def test_barycenter_h_kl_optimality():
+    """Appendix A.3 (KL case): with t_k = s_k^{eps/(eps+lam)} h^{lam/(eps+lam)} the
+    optimal h satisfies sum_k alpha_k (1 - t_k/h) = 0; Table 2 (i) is the geometric mean."""
+    g = synth.rng(70)
+    eps, lam = 0.07, 0.4
+    T = g.uniform(-1, 1, size=(5, 30))
+    alpha = g.uniform(0.2, 1.0, size=5)
+    elogh = O.bary_h_log(T, alpha, lam, eps, "kl")
+    logt = (eps / (eps + lam)) * (T / eps) + (lam / (eps + lam)) * (elogh / eps)
+    res = np.sum(alpha[:, None] * (1 - np.exp(logt - elogh / eps)), axis=0)
+    assert np.max(np.abs(res)) < 1e-12
+    geo = O.bary_h_log(T, alpha, lam, eps, "eq")
+    assert np.allclose(np.exp(geo / eps), np.prod(np.exp(T / eps) ** alpha[:, None], axis=0) ** (1 / alpha.sum()))
+
+
+def test_barycenter_single_measure():
+    """With one measure and F1 the equality constraint, h = s after the first
+    iteration, so b = 1 (V = 0) and the plan is one Sinkhorn half-step."""
+    g = synth.rng(71)
+    xs = [synth.grid_axis(6), synth.grid_axis(5)]
+    geom = O.Geometry("grid", xs=xs, ys=xs)
+    dx = np.full((6, 5), 1 / 30)
+    P = g.uniform(0.5, 2, size=(1, 6, 5))
+    U, V, elogh = O.barycenter_log(geom, dx, dx, P, np.array([1.0]), O.EQ(), 0.5, 0.05, 3)
+    assert np.max(np.abs(V)) < 1e-13
+    r1, r2 = O.marginals(geom, dx.ravel(), dx.ravel(), U[0].ravel(), V[0].ravel(), 0.05)
+    assert np.allclose(r1, P[0].ravel(), rtol=1e-12)
+    assert np.allclose(np.exp(elogh / 0.05).ravel(), r2, rtol=1e-12)
+
+
+def test_barycenter_fixed_point_optimality():
+    """At convergence of the KL barycenter, r2_k = t_k (prox target with p -> h)
+    and sum_k alpha_k (1 - r2_k/h) = 0 pointwise (Prop. 5.3)."""
+    g = synth.rng(72)
+    xs = [synth.grid_axis(5), synth.grid_axis(4)]
+    geom = O.Geometry("grid", xs=xs, ys=xs)
+    dx = np.full((5, 4), 1 / 20)
+    P = g.uniform(0.5, 2, size=(3, 5, 4))
+    alpha = np.array([0.2, 0.3, 0.5])
+    eps, lam = 0.05, 0.3
+    U, V, elogh = O.barycenter_log(geom, dx, dx, P, alpha, O.EQ(), lam, eps, 1500)
+    h = np.exp(elogh / eps).ravel()
+    acc = np.zeros_like(h)
+    for k in range(3):
+        r1, r2 = O.marginals(geom, dx.ravel(), dx.ravel(), U[k].ravel(), V[k].ravel(), eps)
+        acc += alpha[k] * (1 - r2 / h)
+        assert np.allclose(r1, P[k].ravel(), rtol=1e-8)
+    assert np.max(np.abs(acc)) < 1e-8
