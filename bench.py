@@ -1,0 +1,344 @@
+"""Benchmark: 2-D grid unbalanced OT, 256x256 images, KL lambda = 0.5 on both
+marginals, eps-scaling 1e-1 -> 1e-3 (10 stages x 100 iterations, Sec. 4.4),
+then iterations at eps = 1e-3 until the marginal violation is <= 1e-6.
+
+One step = one complete solve through the C ABI (uot_solve) on synthetic
+inputs resident in HBM.  Reported:
+  value        Sinkhorn iterations per second (whole job, all ranks)
+  ms_per_step  time to 1e-6 marginal violation (one solve)
+  e2e          the same metric through uot_solve with host buffers: pinned
+               host -> device copies of the inputs and the device -> host read
+               of the potentials inside the timed region
+  roofline     the dominant kernel (separable grid pass, FP32): exponentials
+               per launch / average launch time (CUDA events on its stream)
+               against the SFU ex2 throughput of the chip
+  cpu_baseline the FP64 oracle timed on the host on a bounded sample
+
+Multi-GPU (torchrun): replicas only.  Every rank solves its own copy of the
+problem (weak scaling, no collective on the data path); value = iterations of
+all ranks / max time over ranks.
+
+--impl reference runs the CPU oracle (the only reference this method has) on
+the same workload, a bounded number of iterations per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+H = W = 256
+LAM = 0.5
+EPS, EPS_START, STAGES, IPS = 1e-3, 1e-1, 10, 100
+TOL, CHECK_EVERY, MAX_ITER = 1e-6, 20, 20000
+SEED = 1235
+# SFU throughput used as the ALU roofline of the grid pass: 16 ex2 per clock
+# per SM (compute capability 10.x arithmetic-throughput table) x 152 SMs x the
+# 2070 MHz maximum SM clock.
+SM_COUNT, MUFU_PER_CLK, SM_MAX_MHZ = 152, 16, 2070.0
+MUFU_PEAK_GEXP = SM_COUNT * MUFU_PER_CLK * SM_MAX_MHZ * 1e6 / 1e9
+
+WORKLOAD = "grid2d-256x256-kl0.5-epsscale1e-1to1e-3-tol1e-6"
+
+
+def config_dict(extra=None):
+    c = {"workload": WORKLOAD, "grid": [H, W], "lambda": LAM, "eps": EPS, "eps_start": EPS_START,
+         "eps_stages": STAGES, "iters_per_stage": IPS, "tol": TOL, "check_every": CHECK_EVERY,
+         "l2": "flushed between steps (256 MB write)", "parallelism": "replicas"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+def inputs(seed):
+    from paper_1607_05816_gb300 import synth
+    return synth.problem_grid2d(H, W, seed=seed, masses=(1.0, 1.3))
+
+
+# ----------------------------------------------------------------------------
+# clocks sampling during the timed region
+# ----------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------
+# our implementation
+# ----------------------------------------------------------------------------
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1607_05816_gb300 import uot
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    uot.load()
+    prec = uot.F32 if args.precision == "f32" else uot.F64
+    dt = torch.float32 if prec == uot.F32 else torch.float64
+    d = inputs(SEED + rank)
+
+    def dev_t(a):
+        return torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev).ravel()
+
+    geo = uot.Geometry.grid([dev_t(a) for a in d["xs"]], [dev_t(a) for a in d["ys"]])
+    p, dx, q, dy = dev_t(d["p"]), dev_t(d["dx"]), dev_t(d["q"]), dev_t(d["dy"])
+    Ub = torch.empty(H * W, dtype=dt, device=dev)
+    Vb = torch.empty(H * W, dtype=dt, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step(Uo=Ub, Vo=Vb, pp=p, dxx=dx, qq=q, dyy=dy, g=geo):
+        return uot.solve(g, pp, dxx, qq, dyy, uot.KL(LAM), uot.KL(LAM), EPS, precision=prec,
+                         max_iter=MAX_ITER, tol=TOL, check_every=CHECK_EVERY,
+                         eps_start=EPS_START, eps_stages=STAGES, iters_per_stage=IPS, U=Uo, V=Vo)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    # ---- device-resident timed region ----
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    launches0 = uot.launch_count()
+    uot.profile_begin()
+    total_ms, iters, errs = 0.0, 0, []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        _, _, info = step()
+        e1.record()
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        iters += info["total_iters"]
+        errs.append(info["marg_err"])
+    torch.cuda.synchronize()
+    barrier()
+    kern_ms, kern_n = uot.profile_end(uot.PROF_GRID_PASS)
+    launches = uot.launch_count() - launches0
+    clocks = sampler.stop()
+
+    # ---- end-to-end through the C ABI with host buffers ----
+    def pinned(a):
+        return torch.as_tensor(np.ascontiguousarray(a), dtype=dt).ravel().pin_memory()
+
+    hp, hdx, hq, hdy = pinned(d["p"]), pinned(d["dx"]), pinned(d["q"]), pinned(d["dy"])
+    hax = [pinned(a) for a in d["xs"]] + [pinned(a) for a in d["ys"]]
+    hU = torch.empty(H * W, dtype=dt).pin_memory()
+    hV = torch.empty(H * W, dtype=dt).pin_memory()
+    h2d = sum(t.numel() * t.element_size() for t in [hp, hdx, hq, hdy] + hax)
+    d2h = hU.numel() * hU.element_size() + hV.numel() * hV.element_size()
+    barrier()
+    torch.cuda.synchronize()
+    e2e_ms, e2e_iters = 0.0, 0
+    for _ in range(max(1, args.steps // 2)):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        gp, gdx, gq, gdy = (t.to(dev, non_blocking=True) for t in (hp, hdx, hq, hdy))
+        axes = [t.to(dev, non_blocking=True) for t in hax]
+        g2 = uot.Geometry.grid(axes[:2], axes[2:])
+        Ud, Vd, info = step(Uo=torch.empty_like(Ub), Vo=torch.empty_like(Vb), pp=gp, dxx=gdx,
+                            qq=gq, dyy=gdy, g=g2)
+        hU.copy_(Ud, non_blocking=True)
+        hV.copy_(Vd, non_blocking=True)
+        e1.record()
+        e1.synchronize()
+        e2e_ms += e0.elapsed_time(e1)
+        e2e_iters += info["total_iters"]
+    barrier()
+
+    # ---- max over ranks ----
+    t_dev = torch.tensor([total_ms, e2e_ms], dtype=torch.float64, device=dev)
+    n_it = torch.tensor([iters, e2e_iters], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t_dev, op=dist.ReduceOp.MAX)
+        dist.all_reduce(n_it, op=dist.ReduceOp.SUM)
+    total_ms_max, e2e_ms_max = t_dev.tolist()
+    all_iters, all_e2e_iters = n_it.tolist()
+    if rank != 0:
+        return
+    value = all_iters / (total_ms_max / 1e3)
+    exps_per_launch = float(H) ** 3  # nlines * nout * nin for a 256x256 grid pass
+    avg_kern_ms = kern_ms / max(1, kern_n)
+    achieved = exps_per_launch / (avg_kern_ms / 1e3) / 1e9
+    line = {
+        "metric": "sinkhorn_iters_per_s",
+        "value": value,
+        "unit": "iters/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": total_ms_max / args.steps,
+        "time_to_tol_ms": total_ms_max / args.steps,
+        "iters_per_step": iters / args.steps,
+        "final_marg_err": max(errs),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32" if prec == uot.F32 else "f64",
+        "data": "synthetic",
+        "config": config_dict({"precision": args.precision}),
+        "e2e": {"value": all_e2e_iters / (e2e_ms_max / 1e3), "unit": "iters/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "roofline": {"bound": "alu", "kernel": "grid_pass_f32" if prec == uot.F32 else "grid_pass_f64",
+                     "achieved": achieved, "peak": MUFU_PEAK_GEXP, "unit": "Gexp2/s",
+                     "frac": achieved / MUFU_PEAK_GEXP, "traffic": None,
+                     "launches": kern_n, "avg_launch_us": avg_kern_ms * 1e3,
+                     "share_of_step": kern_ms / total_ms if total_ms > 0 else None,
+                     "peak_source": "derived: 152 SMs x 16 MUFU.EX2/clk x 2070 MHz"},
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_iters)
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# the oracle on the host (baseline and --impl reference)
+# ----------------------------------------------------------------------------
+
+def oracle_iterations(n_iters, seed=SEED):
+    """Run n_iters oracle iterations of the bench workload at the final eps;
+    returns (seconds, iterations)."""
+    import oracle as O
+    d = inputs(seed)
+    og = O.Geometry("grid", xs=d["xs"], ys=d["ys"])
+    logs = tuple(O.safe_log(d[k]) for k in ("dx", "dy", "p", "q"))
+    t0 = time.perf_counter()
+    O.iterate_log(og, *logs, O.KL(LAM), O.KL(LAM), EPS, n_iters)
+    return time.perf_counter() - t0, n_iters
+
+
+def cpu_baseline(n_iters):
+    sec, n = oracle_iterations(n_iters)
+    return {"value": n / sec, "unit": "iters/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n} FP64 numpy iterations of the 256x256 grid problem at eps=1e-3 "
+                      f"(separable log-domain form), {sec:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    per_step = max(1, args.cpu_iters // 2)
+    for _ in range(args.warmup):
+        oracle_iterations(1)
+    sec, n = 0.0, 0
+    for _ in range(args.steps):
+        s, k = oracle_iterations(per_step)
+        sec += s
+        n += k
+    value = n / sec
+    line = {
+        "metric": "sinkhorn_iters_per_s", "value": value, "unit": "iters/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "impl": "reference", "config": config_dict({"precision": "f64"}),
+        "cpu_baseline": {"value": value, "unit": "iters/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{per_step} iterations per step at eps=1e-3"},
+        "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--cpu-iters", type=int, default=6)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,241 @@
+/*
+ * uot.h -- C ABI of the GB300 (sm_103a) generalized Sinkhorn scaling library.
+ *
+ * Method: Chizat, Peyre, Schmitzer, Vialard, "Scaling algorithms for unbalanced
+ * optimal transport problems" (arXiv:1607.05816).
+ *
+ * Discrete problem (Sec. 4.2, eq. primal_discr, weighted by the reference
+ * measures): points x_1..x_n with reference probability weights dx, points
+ * y_1..y_m with weights dy, densities p (w.r.t. dx) and q (w.r.t. dy), cost C,
+ * Gibbs kernel K = exp(-C/eps) (eq. GibbsKernel), marginal penalties
+ * F1(s) = sum_i dx_i D_phi1(s_i | p_i), F2(s) = sum_j dy_j D_phi2(s_j | q_j)
+ * (eq. UOT, eq. divergencefunctions):
+ *
+ *   min_R  F1(R dy) + F2(R^T dx) + eps sum_ij dx_i dy_j KL(R_ij | K_ij).
+ *
+ * The solver runs the scaling iterations (S) of Sec. 3.3,
+ *   a <- proxdiv_F1(K (b.dy)),  b <- proxdiv_F2(K^T (a.dx)),
+ * in the log domain of Sec. 4.3 (Algorithm 2 with every update absorbed), and
+ * returns the dual potentials U = eps log a, V = eps log b.  The optimal plan
+ * is R_ij = exp((U_i + V_j - C_ij)/eps) (Theorem 3.2).
+ *
+ * Conventions for every entry point:
+ *  - Array arguments are DEVICE pointers owned by the caller unless the
+ *    comment says "host".  The library keeps no pointer after it returns.
+ *  - Floating-point arrays have the element type selected by `precision`:
+ *    UOT_F64 -> double, UOT_F32 -> float.  (UOT_F32 runs the per-entry
+ *    kernel arithmetic in FP32; per-point potentials are still accumulated in
+ *    FP64 internally and returned as float.)
+ *  - Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
+ *    stream).  Entry points that return host values (uot_solve's result,
+ *    uot_objective) synchronise that stream before returning.
+ *  - Temporary device memory is taken from the CUDA stream-ordered allocator
+ *    (cudaMallocAsync) and released before return.
+ *  - Errors are returned as uot_status, never thrown.  Arguments are checked on
+ *    the host before any launch; UOT_EINVAL leaves outputs untouched.
+ *  - There is no CPU fallback: if no sm_103a device is present every entry
+ *    point returns UOT_ECUDA.
+ */
+#ifndef UOT_H
+#define UOT_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  UOT_OK = 0,
+  UOT_NOT_CONVERGED = 1, /* iteration cap reached before `tol`; outputs hold the last iterate */
+  UOT_EINVAL = -1,       /* invalid argument (checked on the host, nothing launched) */
+  UOT_ENOMEM = -2,       /* device allocation failed */
+  UOT_NUMERICAL = -3,    /* NaN appeared in the potentials */
+  UOT_TIMEOUT = -4,      /* a bounded device-side wait expired */
+  UOT_ECUDA = -5,        /* CUDA runtime error (no device, launch failure, ...) */
+  UOT_EUNSUPPORTED = -6  /* valid request outside what this build implements */
+} uot_status;
+
+/* Marginal penalties (Sec. 2.1 examples; Table 1 rows). */
+typedef enum {
+  UOT_DIV_EQ = 0, /* iota_{=}(s|p): s = p exactly (balanced OT) */
+  UOT_DIV_KL = 1, /* lambda KL(s|p),  lambda > 0 */
+  UOT_DIV_TV = 2, /* lambda TV(s|p),  lambda > 0 */
+  UOT_DIV_RG = 3  /* RG[alpha,beta](s|p): alpha p <= s <= beta p, 0 <= alpha <= beta <= +inf */
+} uot_div_kind;
+
+typedef struct {
+  int kind;      /* uot_div_kind */
+  double lambda; /* KL, TV weight */
+  double alpha;  /* RG lower ratio (>= 0) */
+  double beta;   /* RG upper ratio (may be +INFINITY) */
+} uot_div;
+
+/* Where the points live and how the cost is given. */
+typedef enum {
+  UOT_GEOM_DENSE = 0,  /* explicit cost matrix C[n*m], row-major */
+  UOT_GEOM_GRID = 1,   /* Cartesian grids, cost |x - y|^2, applied axis by axis (Sec. 4.4) */
+  UOT_GEOM_POINTS = 2  /* point clouds x[n*d], y[m*d], cost |x - y|^2 computed on the fly */
+} uot_geom_kind;
+
+#define UOT_MAX_DIM 3
+
+typedef struct {
+  int kind; /* uot_geom_kind */
+  int n, m; /* number of points on each side; for grids the product of the shape */
+  /* UOT_GEOM_DENSE */
+  const void* C; /* [n*m] row-major, C_ij >= 0 need not hold but must be finite */
+  /* UOT_GEOM_GRID: potentials and densities are row-major arrays of the grid's shape */
+  int ndim;                        /* 1..UOT_MAX_DIM */
+  int shape_x[UOT_MAX_DIM];        /* grid of X: shape_x[0] x ... x shape_x[ndim-1] */
+  int shape_y[UOT_MAX_DIM];        /* grid of Y */
+  const void* axes_x[UOT_MAX_DIM]; /* 1-D coordinates of each axis of X, length shape_x[k] */
+  const void* axes_y[UOT_MAX_DIM];
+  /* UOT_GEOM_POINTS */
+  const void* x; /* [n*d] row-major */
+  const void* y; /* [m*d] row-major */
+  int d;         /* 1..8 */
+} uot_geom;
+
+typedef enum { UOT_F64 = 0, UOT_F32 = 1 } uot_precision;
+
+typedef struct {
+  int precision;       /* uot_precision */
+  double eps;          /* final entropic regularisation eps > 0 */
+  double eps_start;    /* eps-scaling start (Sec. 4.4); <= eps disables eps-scaling */
+  int eps_stages;      /* number of divisions of eps (the paper uses 10) */
+  int iters_per_stage; /* iterations before each division (the paper uses 100) */
+  int max_iter;        /* iterations at the final eps (cap) */
+  double tol;          /* stop when the marginal violation <= tol; 0 runs max_iter */
+  int check_every;     /* iterations between violation checks (>= 1) */
+  int plain_scaling;   /* 1: Algorithm 1 (non-log scalings a, b on a stored kernel
+                          K = exp(-C/eps)); dense geometry and UOT_F64 only.
+                          0: log domain (Algorithm 2 with every update absorbed) */
+  const void* U0;      /* optional warm start [n] (NULL: U = 0) */
+  const void* V0;      /* optional warm start [m] (NULL: V = 0, i.e. b = 1 as in Algorithm 1) */
+} uot_opts;
+
+typedef struct {
+  int iters;        /* iterations run at the final eps */
+  int total_iters;  /* including the eps-scaling stages */
+  double marg_err;  /* last measured marginal violation (see uot_solve) */
+  double ms;        /* device time of the whole solve (CUDA events) */
+  int status;       /* uot_status of the solve */
+} uot_result;
+
+/* Version string of the library build. */
+const char* uot_version(void);
+
+/* Last CUDA error string seen by the library on this thread ("" if none). */
+const char* uot_last_error(void);
+
+/*
+ * Instrumentation (not part of the method).
+ * uot_launch_count: number of kernels this library has launched in this
+ * process (host-side counter, incremented at every launch).
+ * uot_profile_begin / uot_profile_end: while enabled, each launch of a Gibbs
+ * operator kernel is bracketed by a pair of CUDA events recorded on the stream
+ * it is launched on; uot_profile_end synchronises those events and returns the
+ * summed kernel time (ms) and the number of launches of one family:
+ *   family 0: separable grid passes, family 1: row kernels (dense / points).
+ * Not thread-safe across concurrent solves.
+ */
+long long uot_launch_count(void);
+void uot_profile_begin(void);
+uot_status uot_profile_end(int family, double* total_ms, long long* launches);
+
+/*
+ * uot_solve -- scaling iterations for entropic unbalanced OT (eq. S, Sec. 3.3;
+ * Algorithm 2 of Sec. 4.3 in log form; eps-scaling of Sec. 4.4).
+ *
+ *  g           geometry (dense cost, grid or point clouds)
+ *  p, dx       [n] density of mu w.r.t. dx (p >= 0) and reference weights (dx > 0)
+ *  q, dy       [m] density of nu w.r.t. dy and reference weights
+ *  F1, F2      host structs, marginal penalties on the X and Y marginals
+ *  o           host struct, options
+ *  U, V        [n], [m] outputs: dual potentials eps log a, eps log b;
+ *              -inf where the scaling is 0 (zero density, Prop. 5.1)
+ *  res         host struct, may be NULL
+ *
+ * One iteration: S = eps log K(b.dy); U = prox_F1(S); T = eps log K^T(a.dx);
+ * V = prox_F2(T), with the Table 1 rows in log form (U_bar = eps log p - S):
+ *   EQ: U = U_bar;  KL: U = lambda/(lambda+eps) U_bar;  TV: U = clamp(U_bar, -lambda, lambda);
+ *   RG: U = min(eps log beta + U_bar, max(eps log alpha + U_bar, 0)).
+ * Marginal violation (the stopping criterion, which the paper leaves open):
+ *   sum_i dx_i |r1_i - t_i| / sum_i dx_i t_i, r1 = a.K(b.dy) the first marginal
+ *   of the current plan and t = prox^KL_{F1/eps}(K(b.dy)) its target.  It is
+ *   measured inside the a-update of the iteration after the checked one, so
+ *   the returned iterate is one iteration past the checked state.
+ * Returns UOT_OK (tol reached), UOT_NOT_CONVERGED (cap hit; tol > 0 only),
+ * UOT_NUMERICAL, UOT_EINVAL, UOT_ENOMEM, UOT_ECUDA.
+ */
+uot_status uot_solve(const uot_geom* g, const void* p, const void* dx, const void* q,
+                     const void* dy, const uot_div* F1, const uot_div* F2, const uot_opts* o,
+                     void* U, void* V, uot_result* res, void* stream);
+
+/*
+ * uot_gibbs_log -- the log-domain Gibbs operator alone (Sec. 4.2, 4.3):
+ *   transpose = 0: out_i = eps log sum_j exp((W_j - C_ij)/eps) w_j   (out [n], W,w [m])
+ *   transpose = 1: out_j = eps log sum_i exp((W_i - C_ij)/eps) w_i   (out [m], W,w [n])
+ * i.e. eps log K(e^{W/eps} . w).  W may hold -inf (zero scaling).
+ */
+uot_status uot_gibbs_log(const uot_geom* g, const void* W, const void* w, double eps,
+                         int transpose, int precision, void* out, void* stream);
+
+/*
+ * uot_apply_plan -- apply the plan R_ij = exp((U_i + V_j - C_ij)/eps) to
+ * nonnegative functions (Sec. 4.2 projections; barycentric projection, Sec. 5.1):
+ *   transpose = 0: out[i*ncols + c] = sum_j R_ij dy_j f[j*ncols + c]   (f [m*ncols])
+ *   transpose = 1: out[j*ncols + c] = sum_i R_ij dx_i f[i*ncols + c]   (f [n*ncols])
+ * f = NULL means f = 1, which gives the marginals r1 = R dy, r2 = R^T dx.
+ * f must be >= 0 (UOT_EINVAL is not detected on the device; negative entries
+ * give NaN).  1 <= ncols <= 64.
+ */
+uot_status uot_apply_plan(const uot_geom* g, const void* U, const void* V, double eps,
+                          const void* dx, const void* dy, const void* f, int ncols,
+                          int transpose, int precision, void* out, void* stream);
+
+/*
+ * uot_objective -- primal, dual and gap at potentials (U, V) (Theorem 3.2):
+ *   primal = F1(r1) + F2(r2) + eps sum_ij dx_i dy_j (R_ij log(R_ij/K_ij) - R_ij + K_ij)
+ *   dual   = -F1*(-U) - F2*(-V) - eps sum_ij dx_i dy_j (R_ij - K_ij)
+ *   gap    = primal - dual = sum over both sides of F(r) + F*(-U) + <U, r>_dx,
+ * with r1 = R dy, r2 = R^T dx.  out (host) receives {primal, dual, gap, marg_err}
+ * in FP64 (reductions in FP64).  EQ and RG penalties are +inf off their
+ * constraint sets, so primal/gap are +inf unless the marginal is feasible to
+ * the relative tolerance 1e-9.
+ */
+uot_status uot_objective(const uot_geom* g, const void* p, const void* dx, const void* q,
+                         const void* dy, const uot_div* F1, const uot_div* F2, double eps,
+                         const void* U, const void* V, int precision, double* out, void* stream);
+
+/* Barycenter divergence for uot_barycenter (Table 2 rows). */
+typedef enum { UOT_BARY_KL = 1, UOT_BARY_EQ = 0 } uot_bary_kind;
+
+/*
+ * uot_barycenter -- unbalanced barycenter of K measures (Sec. 5.2) by the
+ * scaling iterations with K couplings sharing the kernel exp(-c/eps)
+ * (c_k = alpha_k c with the weighted entropy of Sec. 5.2).
+ *   F1 acts per measure (eq. proxcomponentbary): proxdiv with p_k;
+ *   F2(s) = min_h lambda sum_k alpha_k D(s_k | h) (eq. Fbary), h from Table 2
+ *   (UOT_BARY_KL: power mean; UOT_BARY_EQ: geometric mean), then
+ *   V_k = prox for lambda KL(.|h) (Table 1 with p -> h).
+ *  Kmeas       number of measures K >= 1
+ *  alpha       host [K] weights alpha_k > 0
+ *  P           [K*n] densities of the measures w.r.t. dx
+ *  F1          host, penalty of each coupling's first marginal (EQ in the
+ *              paper's experiments; KL/TV/RG accepted, see the weighting reading)
+ *  lambda      barycenter weight lambda > 0 (ignored for UOT_BARY_EQ)
+ *  logh        [m] output eps log h of the barycenter density h (w.r.t. dy)
+ *  U, V        [K*n], [K*m] outputs
+ * tol/check_every are honoured with the violation of the first coupling's F1
+ * side summed over k.
+ */
+uot_status uot_barycenter(const uot_geom* g, int Kmeas, const double* alpha, const void* P,
+                          const void* dx, const void* dy, const uot_div* F1, double lambda,
+                          int bary_kind, const uot_opts* o, void* logh, void* U, void* V,
+                          uot_result* res, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* UOT_H */

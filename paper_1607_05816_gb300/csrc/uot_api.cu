@@ -1,0 +1,1064 @@
+// C-ABI entry points and host orchestration of the scaling iterations.
+//
+// The host side validates arguments, converts the caller's arrays to the
+// internal FP64 per-point state (log densities, log reference weights,
+// potentials), and enqueues the iteration on the caller's stream:
+//
+//   iteration (eq. S, Sec. 3.3, log form of Sec. 4.3):
+//     U <- prox_F1(eps log K(e^{V/eps} . dy))     (Gibbs operator + fused Table 1 row)
+//     V <- prox_F2(eps log K^T(e^{U/eps} . dx))
+//
+// eps-scaling (Sec. 4.4) runs `eps_stages` stages of `iters_per_stage`
+// iterations at eps_start / rho^s before iterating at eps; potentials carry
+// over between stages (they are the absorbed duals of Algorithm 2).
+//
+// Every kernel on the path is this library's own; no CPU fallback exists.
+#include <math.h>
+#include <string.h>
+
+#include <atomic>
+#include <mutex>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "uot_internal.cuh"
+
+namespace uot {
+namespace {
+
+thread_local std::string g_last_error;
+
+std::atomic<long long> g_launches{0};
+
+// Optional CUDA-event timing of the Gibbs operator kernels: when enabled, an
+// event pair brackets each launch on the launching stream.
+struct Prof {
+  std::mutex mu;
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> marks[PROF_NFAM];
+  cudaEvent_t pending[PROF_NFAM] = {nullptr, nullptr};
+} g_prof;
+
+cudaEvent_t prof_event() {
+  if (!g_prof.pool.empty()) {
+    cudaEvent_t e = g_prof.pool.back();
+    g_prof.pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+uot_status fail_cuda(cudaError_t e) {
+  g_last_error = cudaGetErrorString(e);
+  return (e == cudaErrorMemoryAllocation) ? UOT_ENOMEM : UOT_ECUDA;
+}
+
+#define UOT_CK(expr)                               \
+  do {                                             \
+    cudaError_t e_ = (expr);                       \
+    if (e_ != cudaSuccess) return fail_cuda(e_);   \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// pointwise kernels
+// ---------------------------------------------------------------------------
+
+constexpr int kNT = 256;
+
+inline int nblocks(int64_t n) {
+  int64_t b = (n + kNT - 1) / kNT;
+  return (int)(b < 1 ? 1 : (b > 65535 * 8 ? 65535 * 8 : b));
+}
+
+template <typename T>
+__global__ void k_to_log(const T* __restrict__ src, int64_t n, double* __restrict__ dst) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = (double)src[i];
+    dst[i] = (v > 0.0) ? log(v) : -kInf;
+  }
+}
+
+template <typename T>
+__global__ void k_to_f64(const T* __restrict__ src, int64_t n, double* __restrict__ dst) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = (double)src[i];
+}
+
+template <typename T>
+__global__ void k_from_f64(const double* __restrict__ src, int64_t n, T* __restrict__ dst) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = (T)src[i];
+}
+
+__global__ void k_fill(double* __restrict__ dst, int64_t n, double v) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = v;
+}
+
+// W = V + eps log f[:, col]  (apply_plan: fold a nonnegative function into the input)
+template <typename T>
+__global__ void k_add_logf(const double* __restrict__ V, const T* __restrict__ f, int ncols,
+                           int col, int64_t n, double eps, double* __restrict__ W) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = V[i];
+    const double fv = f ? (double)f[i * ncols + col] : 1.0;
+    W[i] = (v == -kInf || !(fv > 0.0)) ? -kInf : v + eps * log(fv);
+  }
+}
+
+template <typename T>
+__global__ void k_transpose(const T* __restrict__ A, int n, int m, T* __restrict__ AT) {
+  __shared__ T tile[32][33];
+  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int i = by + r, j = bx + threadIdx.x;
+    if (i < n && j < m) tile[r][threadIdx.x] = A[(int64_t)i * m + j];
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int j = bx + r, i = by + threadIdx.x;
+    if (i < n && j < m) AT[(int64_t)j * n + i] = tile[threadIdx.x][r];
+  }
+}
+
+// K = exp(-C/eps) (eq. GibbsKernel) in FP64, and its transpose.
+template <typename T>
+__global__ void k_gibbs_matrix(const T* __restrict__ C, int n, int m, double eps,
+                               double* __restrict__ K, double* __restrict__ KT) {
+  const int64_t nm = (int64_t)n * m;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nm;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t / m, j = t % m;
+    const double k = exp(-(double)C[t] / eps);
+    K[t] = k;
+    KT[j * n + i] = k;
+  }
+}
+
+// scalings <-> potentials for Algorithm 1: a = exp(U/eps), U = eps log a.
+__global__ void k_exp_scale(const double* __restrict__ U, int64_t n, double eps,
+                            double* __restrict__ a) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    a[i] = exp(U[i] / eps);
+}
+__global__ void k_log_scale(const double* __restrict__ a, int64_t n, double eps,
+                            double* __restrict__ U) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    U[i] = (a[i] > 0.0) ? eps * log(a[i]) : -kInf;
+}
+
+__global__ void k_nan_flag(const double* __restrict__ a, int64_t n, int* flag) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    if (a[i] != a[i]) *flag = 1;
+}
+
+// Barycenter F2 step (Sec. 5.2): from T_k = eps log s_k, the barycenter
+//   KL (Table 2 ii): eps log h = (eps+lam) (log sum_k alpha_k e^{T_k/(eps+lam)} - log sum alpha)
+//   EQ (Table 2 i):  eps log h = sum_k alpha_k T_k / sum alpha
+// and V_k = prox for lam KL(.|h) (resp. the equality row) with p -> h.
+__global__ void k_bary_update(const double* __restrict__ T, int K, int64_t m,
+                              const double* __restrict__ alpha, double sum_alpha, double lam,
+                              double eps, int kind, double* __restrict__ logh,
+                              double* __restrict__ V) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    double elogh;
+    if (kind == UOT_BARY_KL) {
+      const double c = 1.0 / (eps + lam);
+      double mx = -kInf;
+      for (int k = 0; k < K; ++k) mx = fmax(mx, log(alpha[k]) + T[(int64_t)k * m + j] * c);
+      if (mx == -kInf) {
+        elogh = -kInf;
+      } else {
+        double s = 0.0;
+        for (int k = 0; k < K; ++k) s += exp(log(alpha[k]) + T[(int64_t)k * m + j] * c - mx);
+        elogh = (eps + lam) * (mx + log(s) - log(sum_alpha));
+      }
+    } else {
+      double s = 0.0;
+      for (int k = 0; k < K; ++k) s += alpha[k] * T[(int64_t)k * m + j];
+      elogh = s / sum_alpha;
+    }
+    logh[j] = elogh;
+    const double lh = (elogh == -kInf) ? -kInf : elogh / eps;
+    DivParams F;
+    F.kind = (kind == UOT_BARY_KL) ? UOT_DIV_KL : UOT_DIV_EQ;
+    F.lam = lam;
+    F.log_alpha = 0.0;
+    F.log_beta = 0.0;
+    for (int k = 0; k < K; ++k) V[(int64_t)k * m + j] = prox_update(F, lh, T[(int64_t)k * m + j], eps);
+  }
+}
+
+// ---- objective terms (Theorem 3.2, Prop. A.3), FP64 ----
+
+// F(r) = sum w Dbar(r|p) pointwise term
+__device__ double div_term(const DivParams& F, double r, double p, double w) {
+  switch (F.kind) {
+    case UOT_DIV_KL:
+      if (p > 0.0) return F.lam * w * ((r > 0.0 ? r * log(r / p) : 0.0) - r + p);
+      return (r > 0.0) ? kInf : 0.0;
+    case UOT_DIV_TV:
+      return F.lam * w * fabs(r - p);
+    case UOT_DIV_EQ:
+      return (fabs(r - p) <= 1e-9 * fmax(fabs(p), 1e-300)) ? 0.0 : kInf;
+    default: {
+      const double lo = exp(F.log_alpha) * p, hi = (F.log_beta == kInf) ? kInf : exp(F.log_beta) * p;
+      return (r >= lo * (1.0 - 1e-9) - 1e-300 && r <= hi * (1.0 + 1e-9) + 1e-300) ? 0.0 : kInf;
+    }
+  }
+}
+
+// F*(wv) pointwise term for the pairing sum_i w_i wv_i s_i
+__device__ double conj_term(const DivParams& F, double wv, double p, double w) {
+  if (p == 0.0) {
+    // phi'_inf bound only: KL/EQ: no bound; TV: wv <= lam; RG: beta finite no bound
+    if (F.kind == UOT_DIV_TV && wv > F.lam * (1.0 + 1e-12)) return kInf;
+    return 0.0;
+  }
+  switch (F.kind) {
+    case UOT_DIV_KL:
+      return F.lam * w * p * expm1(wv / F.lam);
+    case UOT_DIV_TV:
+      if (wv > F.lam * (1.0 + 1e-12)) return kInf;
+      return w * p * fmax(wv, -F.lam);
+    case UOT_DIV_EQ:
+      return w * p * wv;
+    default: {
+      const double a = exp(F.log_alpha);
+      if (F.log_beta == kInf) return (wv > 0.0) ? kInf : w * p * a * wv;
+      return w * p * fmax(a * wv, exp(F.log_beta) * wv);
+    }
+  }
+}
+
+// acc[0] += F(r) ; acc[1] += F*(-U) ; acc[2] += sum w U r ; acc[3] += sum w r
+// acc[4] += sum w e^{zK} (the sum of K against dx dy) ; acc[5..6] violation
+__global__ void k_objective_side(const double* __restrict__ r, const double* __restrict__ U,
+                                 const double* __restrict__ logp, const double* __restrict__ logw,
+                                 const double* __restrict__ zK, const double* __restrict__ S,
+                                 DivParams F, double eps, int64_t n, double* acc) {
+  double t[7] = {0, 0, 0, 0, 0, 0, 0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double w = exp(logw[i]);
+    const double p = (logp[i] == -kInf) ? 0.0 : exp(logp[i]);
+    const double u = U[i];
+    t[0] += div_term(F, r[i], p, w);
+    t[1] += conj_term(F, (u == -kInf) ? 0.0 : -u, p, w);
+    if (u != -kInf && r[i] > 0.0) t[2] += w * u * r[i];
+    t[3] += w * r[i];
+    if (zK) t[4] += w * exp(zK[i]);
+    if (S) {
+      double a, b;
+      violation_terms(u, prox_update(F, logp[i], S[i], eps), S[i], logw[i], eps, a, b);
+      t[5] += a;
+      t[6] += b;
+    }
+  }
+  __shared__ double sm[7][kNT / 32];
+  for (int k = 0; k < 7; ++k) {
+    double v = t[k];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) sm[k][threadIdx.x >> 5] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 7) {
+    double v = 0.0;
+    for (int w = 0; w < kNT / 32; ++w) v += sm[threadIdx.x][w];
+    atomicAdd(acc + threadIdx.x, v);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// argument checking and problem description
+// ---------------------------------------------------------------------------
+
+bool div_ok(const uot_div* F) {
+  if (!F) return false;
+  switch (F->kind) {
+    case UOT_DIV_EQ:
+      return true;
+    case UOT_DIV_KL:
+    case UOT_DIV_TV:
+      return F->lambda > 0.0 && isfinite(F->lambda);
+    case UOT_DIV_RG:
+      return F->alpha >= 0.0 && isfinite(F->alpha) && F->beta >= F->alpha && !(F->beta != F->beta);
+    default:
+      return false;
+  }
+}
+
+DivParams make_div(const uot_div& F) {
+  DivParams d;
+  d.kind = F.kind;
+  d.lam = F.lambda;
+  d.log_alpha = (F.kind == UOT_DIV_RG) ? (F.alpha > 0.0 ? log(F.alpha) : -kInf) : 0.0;
+  d.log_beta = (F.kind == UOT_DIV_RG) ? (isinf(F.beta) ? kInf : log(F.beta)) : 0.0;
+  return d;
+}
+
+bool prec_ok(int p) { return p == UOT_F64 || p == UOT_F32; }
+
+uot_status check_geom(const uot_geom* g) {
+  if (!g) return UOT_EINVAL;
+  if (g->n < 1 || g->m < 1) return UOT_EINVAL;
+  switch (g->kind) {
+    case UOT_GEOM_DENSE:
+      return g->C ? UOT_OK : UOT_EINVAL;
+    case UOT_GEOM_POINTS:
+      return (g->x && g->y && g->d >= 1 && g->d <= 8) ? UOT_OK : UOT_EINVAL;
+    case UOT_GEOM_GRID: {
+      if (g->ndim < 1 || g->ndim > UOT_MAX_DIM) return UOT_EINVAL;
+      int64_t nx = 1, ny = 1;
+      for (int k = 0; k < g->ndim; ++k) {
+        if (g->shape_x[k] < 1 || g->shape_y[k] < 1) return UOT_EINVAL;
+        if (!g->axes_x[k] || !g->axes_y[k]) return UOT_EINVAL;
+        // a staged line must fit in shared memory (4 warps x nin x 16 bytes)
+        if (g->shape_x[k] > 3000 || g->shape_y[k] > 3000) return UOT_EUNSUPPORTED;
+        nx *= g->shape_x[k];
+        ny *= g->shape_y[k];
+      }
+      return (nx == g->n && ny == g->m) ? UOT_OK : UOT_EINVAL;
+    }
+    default:
+      return UOT_EINVAL;
+  }
+}
+
+// Device memory carved out of one stream-ordered allocation, released on destruction.
+class Scratch {
+ public:
+  explicit Scratch(cudaStream_t s) : s_(s) {}
+  ~Scratch() {
+    if (base_) cudaFreeAsync(base_, s_);
+  }
+  void reserve(size_t bytes) { need_ += (bytes + 255) & ~(size_t)255; }
+  cudaError_t allocate() {
+    if (need_ == 0) return cudaSuccess;
+    return cudaMallocAsync((void**)&base_, need_, s_);
+  }
+  template <typename T>
+  T* take(size_t count) {
+    T* p = (T*)(base_ + off_);
+    off_ += (count * sizeof(T) + 255) & ~(size_t)255;
+    return p;
+  }
+
+ private:
+  cudaStream_t s_;
+  char* base_ = nullptr;
+  size_t need_ = 0, off_ = 0;
+};
+
+struct Gibbs {
+  uot_geom g;
+  int prec;
+  size_t esz;
+  const void* CT = nullptr;     // dense: C^T in the precision's type
+  double* pass[2] = {nullptr, nullptr};  // grid intermediates
+  void* Lscratch = nullptr;     // rows: shifted input line
+  int64_t inter = 0;            // grid intermediate size (elements)
+  int nbatch = 1;
+
+  void plan(Scratch& sc, int batch) {
+    nbatch = batch;
+    esz = (prec == UOT_F64) ? 8 : 4;
+    if (g.kind == UOT_GEOM_DENSE) sc.reserve((size_t)g.n * g.m * esz);
+    if (g.kind == UOT_GEOM_GRID) {
+      inter = 1;
+      for (int k = 0; k < g.ndim; ++k) inter *= (g.shape_x[k] > g.shape_y[k] ? g.shape_x[k] : g.shape_y[k]);
+      if (g.ndim > 1) {
+        sc.reserve((size_t)inter * nbatch * 8);
+        sc.reserve((size_t)inter * nbatch * 8);
+      }
+    } else {
+      const int64_t mx = (g.n > g.m ? g.n : g.m);
+      sc.reserve((size_t)mx * 8 + 512);
+    }
+  }
+  cudaError_t take(Scratch& sc, cudaStream_t s) {
+    if (g.kind == UOT_GEOM_DENSE) {
+      void* ct = sc.take<char>((size_t)g.n * g.m * esz);
+      dim3 grid((g.m + 31) / 32, (g.n + 31) / 32), blk(32, 8);
+      count_launches(1);
+      if (prec == UOT_F64)
+        k_transpose<double><<<grid, blk, 0, s>>>((const double*)g.C, g.n, g.m, (double*)ct);
+      else
+        k_transpose<float><<<grid, blk, 0, s>>>((const float*)g.C, g.n, g.m, (float*)ct);
+      CT = ct;
+    }
+    if (g.kind == UOT_GEOM_GRID) {
+      if (g.ndim > 1) {
+        pass[0] = sc.take<double>((size_t)inter * nbatch);
+        pass[1] = sc.take<double>((size_t)inter * nbatch);
+      }
+    } else {
+      const int64_t mx = (g.n > g.m ? g.n : g.m);
+      Lscratch = sc.take<char>((size_t)mx * 8 + 512);
+    }
+    return cudaGetLastError();
+  }
+
+  // dir 0: W on the Y side (size m) -> result on the X side (size n); dir 1: reverse.
+  cudaError_t apply(int dir, const double* W, const double* logw, double eps, const Epilogue& epi,
+                    cudaStream_t s) const {
+    if (g.kind == UOT_GEOM_GRID) {
+      const int d = g.ndim;
+      const int* in_shape = dir == 0 ? g.shape_y : g.shape_x;
+      const int* out_shape = dir == 0 ? g.shape_x : g.shape_y;
+      const void* const* in_axes = dir == 0 ? g.axes_y : g.axes_x;
+      const void* const* out_axes = dir == 0 ? g.axes_x : g.axes_y;
+      const double* cur = W;
+      int cur_is_pot = 1;
+      for (int k = 0; k < d; ++k) {
+        const int ax = d - 1 - k;
+        int64_t nlines = 1;
+        for (int t = 0; t < ax; ++t) nlines *= in_shape[t];
+        for (int t = ax + 1; t < d; ++t) nlines *= out_shape[t];
+        Epilogue e = epi;
+        if (k < d - 1) {
+          memset(&e, 0, sizeof(e));
+          e.mode = EPI_RAW;
+          e.eps = eps;
+          e.out = pass[k & 1];
+          e.bstride = nlines * out_shape[ax];
+        }
+        cudaError_t err = launch_grid_pass(prec, cur, logw, cur_is_pot, (int)nlines, in_shape[ax],
+                                           in_axes[ax], out_shape[ax], out_axes[ax], eps, nbatch,
+                                           e, s);
+        if (err != cudaSuccess) return err;
+        cur = pass[k & 1];
+        cur_is_pot = 0;
+      }
+      return cudaSuccess;
+    }
+    RowsGeom rg;
+    rg.kind = g.kind;
+    rg.d = g.d;
+    rg.C = (dir == 0) ? g.C : CT;
+    rg.x = (dir == 0) ? g.x : g.y;
+    rg.y = (dir == 0) ? g.y : g.x;
+    const int nrows = (dir == 0) ? g.n : g.m;
+    const int nin = (dir == 0) ? g.m : g.n;
+    for (int b = 0; b < nbatch; ++b) {
+      Epilogue e = epi;
+      // batches for rows geometries are run one by one
+      if (b > 0) {
+        if (e.pot) e.pot += b * e.bstride;
+        if (e.out) e.out += b * e.bstride;
+        if (e.logp) e.logp += b * e.bstride_p;
+        if (e.pot_shift) e.pot_shift += b * e.bstride;
+      }
+      cudaError_t err = launch_rows(prec, rg, nrows, nin, W + (int64_t)b * nin, logw, eps,
+                                    Lscratch, e, s);
+      if (err != cudaSuccess) return err;
+    }
+    return cudaSuccess;
+  }
+};
+
+cudaError_t to_log(int prec, const void* src, int64_t n, double* dst, cudaStream_t s) {
+  count_launches(1);
+  if (prec == UOT_F64)
+    k_to_log<double><<<nblocks(n), kNT, 0, s>>>((const double*)src, n, dst);
+  else
+    k_to_log<float><<<nblocks(n), kNT, 0, s>>>((const float*)src, n, dst);
+  return cudaGetLastError();
+}
+cudaError_t to_f64(int prec, const void* src, int64_t n, double* dst, cudaStream_t s) {
+  if (prec == UOT_F64)
+    return cudaMemcpyAsync(dst, src, n * 8, cudaMemcpyDeviceToDevice, s);
+  count_launches(1);
+  k_to_f64<float><<<nblocks(n), kNT, 0, s>>>((const float*)src, n, dst);
+  return cudaGetLastError();
+}
+cudaError_t from_f64(int prec, const double* src, int64_t n, void* dst, cudaStream_t s) {
+  if (prec == UOT_F64)
+    return cudaMemcpyAsync(dst, src, n * 8, cudaMemcpyDeviceToDevice, s);
+  count_launches(1);
+  k_from_f64<float><<<nblocks(n), kNT, 0, s>>>(src, n, (float*)dst);
+  return cudaGetLastError();
+}
+
+Epilogue prox_epilogue(const DivParams& F, const double* logp, double* pot, const double* logw,
+                       double* err, double eps) {
+  Epilogue e;
+  memset(&e, 0, sizeof(e));
+  e.mode = EPI_PROX;
+  e.eps = eps;
+  e.F = F;
+  e.logp = logp;
+  e.pot = pot;
+  e.logw = logw;
+  e.err = err;
+  return e;
+}
+
+struct Stage {
+  double eps;
+  int iters;
+};
+
+std::vector<Stage> eps_schedule(const uot_opts& o) {
+  std::vector<Stage> st;
+  if (o.eps_start > o.eps && o.eps_stages > 0 && o.iters_per_stage > 0) {
+    const double rho = pow(o.eps_start / o.eps, 1.0 / o.eps_stages);
+    for (int s = 0; s < o.eps_stages; ++s) st.push_back({o.eps_start / pow(rho, s), o.iters_per_stage});
+  }
+  return st;
+}
+
+uot_status check_opts(const uot_opts* o) {
+  if (!o || !prec_ok(o->precision)) return UOT_EINVAL;
+  if (!(o->eps > 0.0) || !isfinite(o->eps)) return UOT_EINVAL;
+  if (o->max_iter < 0 || o->check_every < 0 || !(o->tol >= 0.0)) return UOT_EINVAL;
+  if (o->eps_stages < 0 || o->iters_per_stage < 0) return UOT_EINVAL;
+  if (o->eps_start > o->eps && !isfinite(o->eps_start)) return UOT_EINVAL;
+  return UOT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// solve
+// ---------------------------------------------------------------------------
+
+uot_status solve_impl(const uot_geom* g, const void* p, const void* dx, const void* q,
+                      const void* dy, const uot_div* F1, const uot_div* F2, const uot_opts* o,
+                      void* Uout, void* Vout, uot_result* res, cudaStream_t s) {
+  uot_status st = check_geom(g);
+  if (st != UOT_OK) return st;
+  if ((st = check_opts(o)) != UOT_OK) return st;
+  if (!p || !dx || !q || !dy || !Uout || !Vout || !div_ok(F1) || !div_ok(F2)) return UOT_EINVAL;
+  if (o->plain_scaling && (g->kind != UOT_GEOM_DENSE || o->precision != UOT_F64))
+    return UOT_EUNSUPPORTED;
+  const int prec = o->precision;
+  const int64_t n = g->n, m = g->m;
+  const DivParams D1 = make_div(*F1), D2 = make_div(*F2);
+
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  UOT_CK(cudaEventCreate(&ev0));
+  UOT_CK(cudaEventCreate(&ev1));
+  struct EvGuard {
+    cudaEvent_t a, b;
+    ~EvGuard() {
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+    }
+  } evg{ev0, ev1};
+  UOT_CK(cudaEventRecord(ev0, s));
+
+  Scratch sc(s);
+  Gibbs G;
+  G.g = *g;
+  G.prec = prec;
+  G.plan(sc, 1);
+  sc.reserve(n * 8 * 3);  // logp, logdx, U
+  sc.reserve(m * 8 * 3);  // logq, logdy, V
+  sc.reserve(64);         // err accumulators + flag
+  if (o->plain_scaling) sc.reserve((size_t)n * m * 8 * 2 + n * 8 * 2 + m * 8 * 2);
+  UOT_CK(sc.allocate());
+  UOT_CK(G.take(sc, s));
+  double* logp = sc.take<double>(n);
+  double* logdx = sc.take<double>(n);
+  double* U = sc.take<double>(n);
+  double* logq = sc.take<double>(m);
+  double* logdy = sc.take<double>(m);
+  double* V = sc.take<double>(m);
+  double* acc = sc.take<double>(8);
+  int* flag = (int*)(acc + 4);
+  UOT_CK(to_log(prec, p, n, logp, s));
+  UOT_CK(to_log(prec, dx, n, logdx, s));
+  UOT_CK(to_log(prec, q, m, logq, s));
+  UOT_CK(to_log(prec, dy, m, logdy, s));
+  if (o->U0) {
+    UOT_CK(to_f64(prec, o->U0, n, U, s));
+  } else {
+    count_launches(1);
+    k_fill<<<nblocks(n), kNT, 0, s>>>(U, n, 0.0);
+  }
+  if (o->V0) {
+    UOT_CK(to_f64(prec, o->V0, m, V, s));
+  } else {
+    count_launches(1);
+    k_fill<<<nblocks(m), kNT, 0, s>>>(V, m, 0.0);
+  }
+  UOT_CK(cudaGetLastError());
+
+  const std::vector<Stage> stages = eps_schedule(*o);
+  const int check_every = o->check_every > 0 ? o->check_every : 1;
+  int it = 0, total = 0;
+  double err = INFINITY;
+  bool converged = false;
+
+  if (!o->plain_scaling) {
+    auto iteration = [&](double eps, bool check) -> cudaError_t {
+      cudaError_t e;
+      if (check && (e = cudaMemsetAsync(acc, 0, 16, s)) != cudaSuccess) return e;
+      if ((e = G.apply(0, V, logdy, eps, prox_epilogue(D1, logp, U, logdx, check ? acc : nullptr, eps), s)) != cudaSuccess)
+        return e;
+      return G.apply(1, U, logdx, eps, prox_epilogue(D2, logq, V, logdy, nullptr, eps), s);
+    };
+    for (const Stage& sg : stages)
+      for (int k = 0; k < sg.iters; ++k, ++total) UOT_CK(iteration(sg.eps, false));
+    while (it < o->max_iter) {
+      const bool check = (it % check_every == 0) || (it == o->max_iter - 1);
+      UOT_CK(iteration(o->eps, check));
+      ++it;
+      ++total;
+      if (check) {
+        double h[2];
+        UOT_CK(cudaMemcpyAsync(h, acc, 16, cudaMemcpyDeviceToHost, s));
+        UOT_CK(cudaStreamSynchronize(s));
+        err = (h[1] > 0.0) ? h[0] / h[1] : 0.0;
+        if (it > 1 && o->tol > 0.0 && err <= o->tol) {
+          converged = true;
+          break;
+        }
+      }
+    }
+  } else {
+    // Algorithm 1 on a stored FP64 kernel.
+    double* K = sc.take<double>((size_t)n * m);
+    double* KT = sc.take<double>((size_t)n * m);
+    double* a = sc.take<double>(n);
+    double* b = sc.take<double>(m);
+    double* pd = sc.take<double>(n);
+    double* qd = sc.take<double>(m);
+    double* dxd = sc.take<double>(n);
+    double* dyd = sc.take<double>(m);
+    UOT_CK(to_f64(prec, p, n, pd, s));
+    UOT_CK(to_f64(prec, q, m, qd, s));
+    UOT_CK(to_f64(prec, dx, n, dxd, s));
+    UOT_CK(to_f64(prec, dy, m, dyd, s));
+    auto set_eps = [&](double eps) -> cudaError_t {
+      count_launches(1);
+      k_gibbs_matrix<double><<<nblocks(n * m), kNT, 0, s>>>((const double*)g->C, (int)n, (int)m, eps, K, KT);
+      count_launches(1);
+      k_exp_scale<<<nblocks(n), kNT, 0, s>>>(U, n, eps, a);
+      count_launches(1);
+      k_exp_scale<<<nblocks(m), kNT, 0, s>>>(V, m, eps, b);
+      return cudaGetLastError();
+    };
+    auto to_pot = [&](double eps) -> cudaError_t {
+      count_launches(1);
+      k_log_scale<<<nblocks(n), kNT, 0, s>>>(a, n, eps, U);
+      count_launches(1);
+      k_log_scale<<<nblocks(m), kNT, 0, s>>>(b, m, eps, V);
+      return cudaGetLastError();
+    };
+    for (const Stage& sg : stages) {
+      UOT_CK(set_eps(sg.eps));
+      for (int k = 0; k < sg.iters; ++k, ++total) {
+        UOT_CK(launch_alg1_half(K, (int)n, (int)m, b, dyd, pd, D1, sg.eps, a, dxd, nullptr, s));
+        UOT_CK(launch_alg1_half(KT, (int)m, (int)n, a, dxd, qd, D2, sg.eps, b, dyd, nullptr, s));
+      }
+      UOT_CK(to_pot(sg.eps));
+    }
+    UOT_CK(set_eps(o->eps));
+    while (it < o->max_iter) {
+      const bool check = (it % check_every == 0) || (it == o->max_iter - 1);
+      if (check) UOT_CK(cudaMemsetAsync(acc, 0, 16, s));
+      UOT_CK(launch_alg1_half(K, (int)n, (int)m, b, dyd, pd, D1, o->eps, a, dxd, check ? acc : nullptr, s));
+      UOT_CK(launch_alg1_half(KT, (int)m, (int)n, a, dxd, qd, D2, o->eps, b, dyd, nullptr, s));
+      ++it;
+      ++total;
+      if (check) {
+        double h[2];
+        UOT_CK(cudaMemcpyAsync(h, acc, 16, cudaMemcpyDeviceToHost, s));
+        UOT_CK(cudaStreamSynchronize(s));
+        err = (h[1] > 0.0) ? h[0] / h[1] : 0.0;
+        if (it > 1 && o->tol > 0.0 && err <= o->tol) {
+          converged = true;
+          break;
+        }
+      }
+    }
+    UOT_CK(to_pot(o->eps));
+  }
+
+  // NaN check and output conversion
+  UOT_CK(cudaMemsetAsync(flag, 0, 4, s));
+  count_launches(1);
+  k_nan_flag<<<nblocks(n), kNT, 0, s>>>(U, n, flag);
+  count_launches(1);
+  k_nan_flag<<<nblocks(m), kNT, 0, s>>>(V, m, flag);
+  UOT_CK(cudaGetLastError());
+  UOT_CK(from_f64(prec, U, n, Uout, s));
+  UOT_CK(from_f64(prec, V, m, Vout, s));
+  UOT_CK(cudaEventRecord(ev1, s));
+  int hflag = 0;
+  UOT_CK(cudaMemcpyAsync(&hflag, flag, 4, cudaMemcpyDeviceToHost, s));
+  UOT_CK(cudaStreamSynchronize(s));
+  float ms = 0.f;
+  UOT_CK(cudaEventElapsedTime(&ms, ev0, ev1));
+  uot_status out = hflag ? UOT_NUMERICAL
+                         : ((o->tol > 0.0 && !converged && o->max_iter > 0) ? UOT_NOT_CONVERGED : UOT_OK);
+  if (res) {
+    res->iters = it;
+    res->total_iters = total;
+    res->marg_err = err;
+    res->ms = ms;
+    res->status = out;
+  }
+  return out;
+}
+
+}  // namespace
+
+void count_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+void prof_mark_begin(int family, cudaStream_t s) {
+  if (!g_prof.on) return;
+  std::lock_guard<std::mutex> lk(g_prof.mu);
+  cudaEvent_t e = prof_event();
+  cudaEventRecord(e, s);
+  g_prof.pending[family] = e;
+}
+
+void prof_mark_end(int family, cudaStream_t s) {
+  if (!g_prof.on) return;
+  std::lock_guard<std::mutex> lk(g_prof.mu);
+  cudaEvent_t e = prof_event();
+  cudaEventRecord(e, s);
+  g_prof.marks[family].push_back({g_prof.pending[family], e});
+}
+
+}  // namespace uot
+
+using namespace uot;
+
+extern "C" {
+
+const char* uot_version(void) { return "uot-gb300 0.1 (sm_103a)"; }
+
+const char* uot_last_error(void) { return g_last_error.c_str(); }
+
+long long uot_launch_count(void) { return g_launches.load(); }
+
+void uot_profile_begin(void) {
+  std::lock_guard<std::mutex> lk(g_prof.mu);
+  for (auto& v : g_prof.marks) {
+    for (auto& pr : v) {
+      g_prof.pool.push_back(pr.first);
+      g_prof.pool.push_back(pr.second);
+    }
+    v.clear();
+  }
+  g_prof.on = true;
+}
+
+uot_status uot_profile_end(int family, double* total_ms, long long* launches) {
+  if (family < 0 || family >= PROF_NFAM || !total_ms || !launches) return UOT_EINVAL;
+  std::lock_guard<std::mutex> lk(g_prof.mu);
+  g_prof.on = false;
+  double tot = 0.0;
+  for (auto& pr : g_prof.marks[family]) {
+    cudaError_t e = cudaEventSynchronize(pr.second);
+    if (e != cudaSuccess) return fail_cuda(e);
+    float ms = 0.f;
+    e = cudaEventElapsedTime(&ms, pr.first, pr.second);
+    if (e != cudaSuccess) return fail_cuda(e);
+    tot += ms;
+  }
+  *total_ms = tot;
+  *launches = (long long)g_prof.marks[family].size();
+  return UOT_OK;
+}
+
+uot_status uot_solve(const uot_geom* g, const void* p, const void* dx, const void* q,
+                     const void* dy, const uot_div* F1, const uot_div* F2, const uot_opts* o,
+                     void* U, void* V, uot_result* res, void* stream) {
+  return solve_impl(g, p, dx, q, dy, F1, F2, o, U, V, res, (cudaStream_t)stream);
+}
+
+uot_status uot_gibbs_log(const uot_geom* g, const void* W, const void* w, double eps,
+                         int transpose, int precision, void* out, void* stream) {
+  uot_status st = check_geom(g);
+  if (st != UOT_OK) return st;
+  if (!W || !w || !out || !(eps > 0.0) || !prec_ok(precision)) return UOT_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t nin = transpose ? g->n : g->m, nout = transpose ? g->m : g->n;
+  Scratch sc(s);
+  Gibbs G;
+  G.g = *g;
+  G.prec = precision;
+  G.plan(sc, 1);
+  sc.reserve(nin * 8 * 2 + nout * 8);
+  UOT_CK(sc.allocate());
+  UOT_CK(G.take(sc, s));
+  double* Wd = sc.take<double>(nin);
+  double* logw = sc.take<double>(nin);
+  double* od = sc.take<double>(nout);
+  UOT_CK(to_f64(precision, W, nin, Wd, s));
+  UOT_CK(to_log(precision, w, nin, logw, s));
+  Epilogue e;
+  memset(&e, 0, sizeof(e));
+  e.mode = EPI_SCALE;
+  e.eps = eps;
+  e.out = od;
+  UOT_CK(G.apply(transpose ? 1 : 0, Wd, logw, eps, e, s));
+  UOT_CK(from_f64(precision, od, nout, out, s));
+  return UOT_OK;
+}
+
+uot_status uot_apply_plan(const uot_geom* g, const void* U, const void* V, double eps,
+                          const void* dx, const void* dy, const void* f, int ncols,
+                          int transpose, int precision, void* out, void* stream) {
+  uot_status st = check_geom(g);
+  if (st != UOT_OK) return st;
+  if (!U || !V || !dx || !dy || !out || !(eps > 0.0) || !prec_ok(precision)) return UOT_EINVAL;
+  if (ncols < 1 || ncols > 64) return UOT_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t n = g->n, m = g->m;
+  const int64_t nin = transpose ? n : m, nout = transpose ? m : n;
+  Scratch sc(s);
+  Gibbs G;
+  G.g = *g;
+  G.prec = precision;
+  G.plan(sc, 1);
+  sc.reserve(nin * 8 * 3 + nout * 8 * (ncols + 1));
+  UOT_CK(sc.allocate());
+  UOT_CK(G.take(sc, s));
+  double* Win = sc.take<double>(nin);
+  double* W = sc.take<double>(nin);
+  double* logw = sc.take<double>(nin);
+  double* Sh = sc.take<double>(nout);
+  double* od = sc.take<double>(nout * ncols);
+  UOT_CK(to_f64(precision, transpose ? U : V, nin, Win, s));
+  UOT_CK(to_f64(precision, transpose ? V : U, nout, Sh, s));
+  UOT_CK(to_log(precision, transpose ? dx : dy, nin, logw, s));
+  for (int c = 0; c < ncols; ++c) {
+    count_launches(1);
+    if (precision == UOT_F64)
+      k_add_logf<double><<<nblocks(nin), kNT, 0, s>>>(Win, (const double*)f, ncols, c, nin, eps, W);
+    else
+      k_add_logf<float><<<nblocks(nin), kNT, 0, s>>>(Win, (const float*)f, ncols, c, nin, eps, W);
+    UOT_CK(cudaGetLastError());
+    Epilogue e;
+    memset(&e, 0, sizeof(e));
+    e.mode = EPI_PLAN;
+    e.eps = eps;
+    e.out = od;
+    e.pot_shift = Sh;
+    e.ncols = ncols;
+    e.col = c;
+    UOT_CK(G.apply(transpose ? 1 : 0, W, logw, eps, e, s));
+  }
+  UOT_CK(from_f64(precision, od, nout * ncols, out, s));
+  return UOT_OK;
+}
+
+uot_status uot_objective(const uot_geom* g, const void* p, const void* dx, const void* q,
+                         const void* dy, const uot_div* F1, const uot_div* F2, double eps,
+                         const void* U, const void* V, int precision, double* out, void* stream) {
+  uot_status st = check_geom(g);
+  if (st != UOT_OK) return st;
+  if (!p || !dx || !q || !dy || !U || !V || !out || !(eps > 0.0) || !prec_ok(precision) ||
+      !div_ok(F1) || !div_ok(F2))
+    return UOT_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t n = g->n, m = g->m;
+  Scratch sc(s);
+  Gibbs G;
+  G.g = *g;
+  G.prec = precision;
+  G.plan(sc, 1);
+  sc.reserve(n * 8 * 7 + m * 8 * 7 + 128);
+  UOT_CK(sc.allocate());
+  UOT_CK(G.take(sc, s));
+  double* Ud = sc.take<double>(n);
+  double* Vd = sc.take<double>(m);
+  double* logp = sc.take<double>(n);
+  double* logq = sc.take<double>(m);
+  double* logdx = sc.take<double>(n);
+  double* logdy = sc.take<double>(m);
+  double* r1 = sc.take<double>(n);
+  double* r2 = sc.take<double>(m);
+  double* zK1 = sc.take<double>(n);
+  double* S1 = sc.take<double>(n);
+  double* zero = sc.take<double>(n > m ? n : m);
+  double* acc = sc.take<double>(16);
+  UOT_CK(to_f64(precision, U, n, Ud, s));
+  UOT_CK(to_f64(precision, V, m, Vd, s));
+  UOT_CK(to_log(precision, p, n, logp, s));
+  UOT_CK(to_log(precision, q, m, logq, s));
+  UOT_CK(to_log(precision, dx, n, logdx, s));
+  UOT_CK(to_log(precision, dy, m, logdy, s));
+  count_launches(1);
+  k_fill<<<nblocks(n > m ? n : m), kNT, 0, s>>>(zero, n > m ? n : m, 0.0);
+  UOT_CK(cudaMemsetAsync(acc, 0, 16 * 8, s));
+  Epilogue e;
+  memset(&e, 0, sizeof(e));
+  e.eps = eps;
+  // r1 = R dy, r2 = R^T dx
+  e.mode = EPI_PLAN;
+  e.ncols = 1;
+  e.out = r1;
+  e.pot_shift = Ud;
+  UOT_CK(G.apply(0, Vd, logdy, eps, e, s));
+  e.out = r2;
+  e.pot_shift = Vd;
+  UOT_CK(G.apply(1, Ud, logdx, eps, e, s));
+  // z_i = log sum_j K_ij dy_j  (for sum dx dy K) and S = eps log K(b.dy)
+  e.mode = EPI_RAW;
+  e.out = zK1;
+  UOT_CK(G.apply(0, zero, logdy, eps, e, s));
+  e.mode = EPI_SCALE;
+  e.out = S1;
+  UOT_CK(G.apply(0, Vd, logdy, eps, e, s));
+  const DivParams D1 = make_div(*F1), D2 = make_div(*F2);
+  count_launches(1);
+  k_objective_side<<<nblocks(n) > 1024 ? 1024 : nblocks(n), kNT, 0, s>>>(r1, Ud, logp, logdx, zK1, S1, D1, eps, n, acc);
+  count_launches(1);
+  k_objective_side<<<nblocks(m) > 1024 ? 1024 : nblocks(m), kNT, 0, s>>>(r2, Vd, logq, logdy, nullptr, nullptr, D2, eps, m, acc + 8);
+  UOT_CK(cudaGetLastError());
+  double h[16];
+  UOT_CK(cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, s));
+  UOT_CK(cudaStreamSynchronize(s));
+  // eps sum dx dy (R - K) = eps (sum dx r1 - sum dx dy K)
+  const double mass_term = eps * (h[3] - h[4]);
+  const double primal = h[0] + h[8] + h[2] + h[10] - mass_term;
+  const double dual = -h[1] - h[9] - mass_term;
+  out[0] = primal;
+  out[1] = dual;
+  out[2] = (h[0] + h[1] + h[2]) + (h[8] + h[9] + h[10]);
+  out[3] = (h[6] > 0.0) ? h[5] / h[6] : 0.0;
+  return UOT_OK;
+}
+
+uot_status uot_barycenter(const uot_geom* g, int Kmeas, const double* alpha, const void* P,
+                          const void* dx, const void* dy, const uot_div* F1, double lambda,
+                          int bary_kind, const uot_opts* o, void* logh_out, void* Uout,
+                          void* Vout, uot_result* res, void* stream) {
+  uot_status st = check_geom(g);
+  if (st != UOT_OK) return st;
+  if ((st = check_opts(o)) != UOT_OK) return st;
+  if (Kmeas < 1 || !alpha || !P || !dx || !dy || !div_ok(F1) || !logh_out || !Uout || !Vout)
+    return UOT_EINVAL;
+  if (bary_kind != UOT_BARY_KL && bary_kind != UOT_BARY_EQ) return UOT_EINVAL;
+  if (bary_kind == UOT_BARY_KL && !(lambda > 0.0)) return UOT_EINVAL;
+  if (o->plain_scaling) return UOT_EUNSUPPORTED;
+  double sum_alpha = 0.0;
+  for (int k = 0; k < Kmeas; ++k) {
+    if (!(alpha[k] > 0.0) || !isfinite(alpha[k])) return UOT_EINVAL;
+    sum_alpha += alpha[k];
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const int prec = o->precision;
+  const int64_t n = g->n, m = g->m;
+  const DivParams D1 = make_div(*F1);
+
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  UOT_CK(cudaEventCreate(&ev0));
+  UOT_CK(cudaEventCreate(&ev1));
+  struct EvGuard {
+    cudaEvent_t a, b;
+    ~EvGuard() {
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+    }
+  } evg{ev0, ev1};
+  UOT_CK(cudaEventRecord(ev0, s));
+
+  Scratch sc(s);
+  Gibbs G;
+  G.g = *g;
+  G.prec = prec;
+  G.plan(sc, Kmeas);
+  sc.reserve(n * Kmeas * 8 * 2 + n * 8);
+  sc.reserve(m * Kmeas * 8 * 2 + m * 8 * 2);
+  sc.reserve(Kmeas * 8 + 64);
+  UOT_CK(sc.allocate());
+  UOT_CK(G.take(sc, s));
+  double* logP = sc.take<double>(n * Kmeas);
+  double* U = sc.take<double>(n * Kmeas);
+  double* logdx = sc.take<double>(n);
+  double* V = sc.take<double>(m * Kmeas);
+  double* T = sc.take<double>(m * Kmeas);
+  double* logdy = sc.take<double>(m);
+  double* logh = sc.take<double>(m);
+  double* alpha_d = sc.take<double>(Kmeas);
+  double* acc = sc.take<double>(8);
+  UOT_CK(to_log(prec, P, n * Kmeas, logP, s));
+  UOT_CK(to_log(prec, dx, n, logdx, s));
+  UOT_CK(to_log(prec, dy, m, logdy, s));
+  UOT_CK(cudaMemcpyAsync(alpha_d, alpha, Kmeas * 8, cudaMemcpyHostToDevice, s));
+  count_launches(1);
+  k_fill<<<nblocks(n * Kmeas), kNT, 0, s>>>(U, n * Kmeas, 0.0);
+  count_launches(1);
+  k_fill<<<nblocks(m * Kmeas), kNT, 0, s>>>(V, m * Kmeas, 0.0);
+  UOT_CK(cudaGetLastError());
+
+  auto iteration = [&](double eps, bool check) -> cudaError_t {
+    cudaError_t e;
+    if (check && (e = cudaMemsetAsync(acc, 0, 16, s)) != cudaSuccess) return e;
+    Epilogue e1 = prox_epilogue(D1, logP, U, logdx, check ? acc : nullptr, eps);
+    e1.bstride = n;
+    e1.bstride_p = n;
+    if ((e = G.apply(0, V, logdy, eps, e1, s)) != cudaSuccess) return e;
+    Epilogue e2;
+    memset(&e2, 0, sizeof(e2));
+    e2.mode = EPI_SCALE;
+    e2.eps = eps;
+    e2.out = T;
+    e2.bstride = m;
+    count_launches(1);
+    if ((e = G.apply(1, U, logdx, eps, e2, s)) != cudaSuccess) return e;
+    k_bary_update<<<nblocks(m), kNT, 0, s>>>(T, Kmeas, m, alpha_d, sum_alpha, lambda, eps,
+                                             bary_kind, logh, V);
+    return cudaGetLastError();
+  };
+  const std::vector<Stage> stages = eps_schedule(*o);
+  const int check_every = o->check_every > 0 ? o->check_every : 1;
+  int it = 0, total = 0;
+  double err = INFINITY;
+  bool converged = false;
+  for (const Stage& sg : stages)
+    for (int k = 0; k < sg.iters; ++k, ++total) UOT_CK(iteration(sg.eps, false));
+  while (it < o->max_iter) {
+    const bool check = (it % check_every == 0) || (it == o->max_iter - 1);
+    UOT_CK(iteration(o->eps, check));
+    ++it;
+    ++total;
+    if (check) {
+      double h[2];
+      UOT_CK(cudaMemcpyAsync(h, acc, 16, cudaMemcpyDeviceToHost, s));
+      UOT_CK(cudaStreamSynchronize(s));
+      err = (h[1] > 0.0) ? h[0] / h[1] : 0.0;
+      if (it > 1 && o->tol > 0.0 && err <= o->tol) {
+        converged = true;
+        break;
+      }
+    }
+  }
+  UOT_CK(from_f64(prec, U, n * Kmeas, Uout, s));
+  UOT_CK(from_f64(prec, V, m * Kmeas, Vout, s));
+  UOT_CK(from_f64(prec, logh, m, logh_out, s));
+  UOT_CK(cudaEventRecord(ev1, s));
+  UOT_CK(cudaStreamSynchronize(s));
+  float ms = 0.f;
+  UOT_CK(cudaEventElapsedTime(&ms, ev0, ev1));
+  uot_status out = (o->tol > 0.0 && !converged && o->max_iter > 0) ? UOT_NOT_CONVERGED : UOT_OK;
+  if (res) {
+    res->iters = it;
+    res->total_iters = total;
+    res->marg_err = err;
+    res->ms = ms;
+    res->status = out;
+  }
+  return out;
+}
+
+}  // extern "C"

@@ -1,0 +1,194 @@
+// Internal declarations shared by the library's translation units.
+//
+// Notation (arXiv:1607.05816): potentials U = eps log a, V = eps log b
+// (Sec. 4.3 with every update absorbed), S = eps log K(b.dy),
+// T = eps log K^T(a.dx).  Per-point state is FP64; the per-entry arithmetic of
+// the Gibbs operator is FP32 or FP64 depending on the requested precision.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "../../include/uot.h"
+
+namespace uot {
+
+constexpr double kInf = __builtin_huge_val();
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kLn2 = 0.6931471805599453f;
+
+// A marginal penalty prepared for the device (Table 1 row + parameters).
+struct DivParams {
+  int kind;          // uot_div_kind
+  double lam;        // KL, TV weight
+  double log_alpha;  // RG: log alpha (-inf when alpha == 0)
+  double log_beta;   // RG: log beta (+inf when beta == +inf)
+};
+
+// Table 1 in log form with u = 0: U = eps log proxdiv_F(s, eps) given
+// S = eps log s and log p.  Zero masses follow Prop. 5.1 with 0/0 = 0:
+// s = 0 (S = -inf) gives a = 0; p = 0 gives U_bar = -inf.
+__host__ __device__ inline double prox_update(const DivParams& F, double logp, double S,
+                                              double eps) {
+  if (S == -kInf) return -kInf;
+  const double ubar = (logp == -kInf) ? -kInf : eps * logp - S;
+  switch (F.kind) {
+    case UOT_DIV_EQ:
+      return ubar;
+    case UOT_DIV_KL:
+      return (F.lam / (F.lam + eps)) * ubar;
+    case UOT_DIV_TV:
+      return fmin(F.lam, fmax(-F.lam, ubar));
+    default: {  // UOT_DIV_RG
+      const double inner = fmax(eps * F.log_alpha + ubar, 0.0);
+      if (F.log_beta == kInf) return inner;
+      return fmin(eps * F.log_beta + ubar, inner);
+    }
+  }
+}
+
+// What the last operator pass does with its LSE result z = log sum (natural
+// units) at output point `pt`.
+enum EpiMode {
+  EPI_RAW = 0,    // out[pt] = z                      (intermediate pass)
+  EPI_SCALE = 1,  // out[pt] = eps * z                (Gibbs operator alone)
+  EPI_PROX = 2,   // pot[pt] = prox(eps log p - eps z) (+ violation terms)
+  EPI_PLAN = 3    // out[pt*ncols+col] = exp(pot_shift[pt]/eps + z)
+};
+
+struct Epilogue {
+  int mode;
+  double eps;
+  // EPI_PROX
+  DivParams F;
+  const double* logp;      // log density of the output side
+  double* pot;             // potential written (read first as the old value)
+  const double* logw;      // log reference weight of the output side (violation)
+  double* err;             // [2] = {sum dx |r_old - r_new|, sum dx r_new}; NULL: no check
+  // EPI_PLAN
+  const double* pot_shift; // U (or V) of the output side
+  int ncols, col;
+  // all modes except PROX
+  double* out;
+  // batches of independent arrays (barycenters): element (b, pt) of pot/out
+  // lives at b*bstride + pt, of logp at b*bstride_p + pt; logw is shared.
+  int64_t bstride;
+  int64_t bstride_p;
+};
+
+// Violation terms of one point: r_old = exp((U_old+S)/eps), r_new = exp((U_new+S)/eps).
+__device__ inline void violation_terms(double Uold, double Unew, double S, double logw,
+                                       double eps, double& num, double& den) {
+  const double w = exp(logw);
+  const double ro = (Uold == -kInf || S == -kInf) ? 0.0 : exp((Uold + S) / eps);
+  const double rn = (Unew == -kInf || S == -kInf) ? 0.0 : exp((Unew + S) / eps);
+  num = w * fabs(ro - rn);
+  den = w * rn;
+}
+
+// Applies the epilogue to one result; returns the violation terms through num/den.
+__device__ inline void apply_epilogue(const Epilogue& e, int64_t b, int64_t pt, double z,
+                                      double& num, double& den) {
+  num = 0.0;
+  den = 0.0;
+  const int64_t q = b * e.bstride + pt;
+  switch (e.mode) {
+    case EPI_RAW:
+      e.out[q] = z;
+      break;
+    case EPI_SCALE:
+      e.out[q] = (z == -kInf) ? -kInf : e.eps * z;
+      break;
+    case EPI_PROX: {
+      const double S = (z == -kInf) ? -kInf : e.eps * z;
+      const double Uold = e.pot[q];
+      const double Unew = prox_update(e.F, e.logp[b * e.bstride_p + pt], S, e.eps);
+      e.pot[q] = Unew;
+      if (e.err) violation_terms(Uold, Unew, S, e.logw[pt], e.eps, num, den);
+      break;
+    }
+    default: {  // EPI_PLAN
+      const double u = e.pot_shift[q];
+      const double v = (u == -kInf || z == -kInf) ? 0.0 : exp(u / e.eps + z);
+      e.out[q * e.ncols + e.col] = v;
+      break;
+    }
+  }
+}
+
+// Block-wide sum of two doubles, then one atomicAdd per block into acc[0..1].
+template <int NT>
+__device__ inline void block_add2(double a, double b, double* acc) {
+  __shared__ double sa[NT / 32], sb[NT / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) {
+    sa[w] = a;
+    sb[w] = b;
+  }
+  __syncthreads();
+  if (w == 0) {
+    a = (l < NT / 32) ? sa[l] : 0.0;
+    b = (l < NT / 32) ? sb[l] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if (l == 0 && acc) {
+      atomicAdd(acc, a);
+      atomicAdd(acc + 1, b);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// instrumentation: launch counting and optional event timing of the Gibbs
+// operator kernels (on the stream they are launched on)
+// ---------------------------------------------------------------------------
+
+enum ProfFamily { PROF_GRID_PASS = 0, PROF_ROWS = 1, PROF_NFAM = 2 };
+void count_launches(int k);
+void prof_mark_begin(int family, cudaStream_t s);
+void prof_mark_end(int family, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// launchers implemented in the kernel translation units
+// ---------------------------------------------------------------------------
+
+// One separable pass of the log-domain Gibbs operator on a grid axis:
+//   z[i][l] = log sum_j exp(L[l][j] - (xo[i] - yi[j])^2 / eps)
+// L[l][j] = in[l*nin + j] (in_is_pot = 0) or in[.]/eps + logw[.] (in_is_pot = 1).
+// Output layout is transposed: point index i*nlines + l.
+// `nbatch` independent arrays: input b at in + b*nlines*nin, results at batch b
+// of the epilogue (output batch stride nout*nlines for EPI_RAW).
+cudaError_t launch_grid_pass(int prec, const double* in, const double* logw, int in_is_pot,
+                             int nlines, int nin, const void* yi, int nout, const void* xo,
+                             double eps, int nbatch, const Epilogue& epi, cudaStream_t s);
+
+// Row-wise log-domain Gibbs operator for dense costs and point clouds:
+//   z_i = log sum_j exp(L_j - C_ij / eps),  L_j = W_j/eps + logw_j
+// C given densely (C row-major [nrows][ncols_c]) or as |x_i - y_j|^2.
+struct RowsGeom {
+  int kind;          // UOT_GEOM_DENSE or UOT_GEOM_POINTS
+  const void* C;     // dense, in the precision's type
+  const void* x;     // points [nrows*d]
+  const void* y;     // points [nin*d]
+  int d;
+};
+cudaError_t launch_rows(int prec, const RowsGeom& g, int nrows, int nin, const double* W,
+                        const double* logw, double eps, void* scratch_L, const Epilogue& epi,
+                        cudaStream_t s);
+
+// Algorithm 1 (non-log) half-step on a stored FP64 kernel:
+//   a_i = proxdiv_F(sum_j K_ij b_j w_j, eps), also the violation terms.
+cudaError_t launch_alg1_half(const double* K, int nrows, int nin, const double* b,
+                             const double* w, const double* p, DivParams F, double eps,
+                             double* a, const double* wout, double* err, cudaStream_t s);
+
+}  // namespace uot

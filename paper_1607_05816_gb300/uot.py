@@ -1,0 +1,345 @@
+"""Thin ctypes binding of the C ABI in include/uot.h (argument marshalling only).
+
+Every function takes torch tensors that already live on the GPU, checks their
+dtype/device/contiguity, and passes raw device pointers and the current CUDA
+stream to libuot.so.  All computation happens in the library's kernels; there
+is no CPU path.  If the library is missing or cannot be loaded the functions
+raise instead of falling back.
+
+Names follow the C ABI: solve, gibbs_log, apply_plan, objective, barycenter.
+Divergences (Sec. 2.1, Table 1): EQ(), KL(lam), TV(lam), RG(alpha, beta).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+from dataclasses import dataclass
+
+import torch
+
+from . import build as _build
+
+UOT_OK, UOT_NOT_CONVERGED = 0, 1
+STATUS = {0: "UOT_OK", 1: "UOT_NOT_CONVERGED", -1: "UOT_EINVAL", -2: "UOT_ENOMEM",
+          -3: "UOT_NUMERICAL", -4: "UOT_TIMEOUT", -5: "UOT_ECUDA", -6: "UOT_EUNSUPPORTED"}
+DIV_EQ, DIV_KL, DIV_TV, DIV_RG = 0, 1, 2, 3
+GEOM_DENSE, GEOM_GRID, GEOM_POINTS = 0, 1, 2
+F64, F32 = 0, 1
+BARY_EQ, BARY_KL = 0, 1
+MAX_DIM = 3
+
+
+class UotError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = status
+        super().__init__(f"{what}: {STATUS.get(status, status)} {_last_error()}".strip())
+
+
+class CDiv(C.Structure):
+    _fields_ = [("kind", C.c_int), ("lam", C.c_double), ("alpha", C.c_double), ("beta", C.c_double)]
+
+
+class CGeom(C.Structure):
+    _fields_ = [("kind", C.c_int), ("n", C.c_int), ("m", C.c_int), ("C", C.c_void_p),
+                ("ndim", C.c_int), ("shape_x", C.c_int * MAX_DIM), ("shape_y", C.c_int * MAX_DIM),
+                ("axes_x", C.c_void_p * MAX_DIM), ("axes_y", C.c_void_p * MAX_DIM),
+                ("x", C.c_void_p), ("y", C.c_void_p), ("d", C.c_int)]
+
+
+class COpts(C.Structure):
+    _fields_ = [("precision", C.c_int), ("eps", C.c_double), ("eps_start", C.c_double),
+                ("eps_stages", C.c_int), ("iters_per_stage", C.c_int), ("max_iter", C.c_int),
+                ("tol", C.c_double), ("check_every", C.c_int), ("plain_scaling", C.c_int),
+                ("U0", C.c_void_p), ("V0", C.c_void_p)]
+
+
+class CResult(C.Structure):
+    _fields_ = [("iters", C.c_int), ("total_iters", C.c_int), ("marg_err", C.c_double),
+                ("ms", C.c_double), ("status", C.c_int)]
+
+
+_LIB = None
+
+_SIGS = {
+    "uot_version": (C.c_char_p, []),
+    "uot_last_error": (C.c_char_p, []),
+    "uot_launch_count": (C.c_longlong, []),
+    "uot_profile_begin": (None, []),
+    "uot_profile_end": (C.c_int, [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
+    "uot_solve": (C.c_int, [C.POINTER(CGeom), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                            C.POINTER(CDiv), C.POINTER(CDiv), C.POINTER(COpts), C.c_void_p,
+                            C.c_void_p, C.POINTER(CResult), C.c_void_p]),
+    "uot_gibbs_log": (C.c_int, [C.POINTER(CGeom), C.c_void_p, C.c_void_p, C.c_double, C.c_int,
+                                C.c_int, C.c_void_p, C.c_void_p]),
+    "uot_apply_plan": (C.c_int, [C.POINTER(CGeom), C.c_void_p, C.c_void_p, C.c_double, C.c_void_p,
+                                 C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p,
+                                 C.c_void_p]),
+    "uot_objective": (C.c_int, [C.POINTER(CGeom), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                C.POINTER(CDiv), C.POINTER(CDiv), C.c_double, C.c_void_p,
+                                C.c_void_p, C.c_int, C.POINTER(C.c_double), C.c_void_p]),
+    "uot_barycenter": (C.c_int, [C.POINTER(CGeom), C.c_int, C.POINTER(C.c_double), C.c_void_p,
+                                 C.c_void_p, C.c_void_p, C.POINTER(CDiv), C.c_double, C.c_int,
+                                 C.POINTER(COpts), C.c_void_p, C.c_void_p, C.c_void_p,
+                                 C.POINTER(CResult), C.c_void_p]),
+}
+
+
+def exported_symbols():
+    """Entry points declared in include/uot.h."""
+    return list(_SIGS)
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Load libuot.so (building it if absent) and bind the C signatures."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = path or lib_path()
+    if not os.path.exists(path):
+        _build.build()
+    lib = C.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def _last_error() -> str:
+    if _LIB is None:
+        return ""
+    return _LIB.uot_last_error().decode()
+
+
+def version() -> str:
+    return load().uot_version().decode()
+
+
+def launch_count() -> int:
+    """Kernels launched by the library so far in this process."""
+    return int(load().uot_launch_count())
+
+
+PROF_GRID_PASS, PROF_ROWS = 0, 1
+
+
+def profile_begin():
+    load().uot_profile_begin()
+
+
+def profile_end(family=PROF_GRID_PASS):
+    """(total ms, launches) of one kernel family since profile_begin()."""
+    ms = C.c_double()
+    n = C.c_longlong()
+    _check(load().uot_profile_end(int(family), C.byref(ms), C.byref(n)), "uot_profile_end")
+    return ms.value, n.value
+
+
+# ---------------------------------------------------------------------------
+# argument helpers
+# ---------------------------------------------------------------------------
+
+
+@dataclass
+class Div:
+    kind: int
+    lam: float = 1.0
+    alpha: float = 0.0
+    beta: float = math.inf
+
+    def c(self) -> CDiv:
+        return CDiv(self.kind, float(self.lam), float(self.alpha), float(self.beta))
+
+
+def EQ():
+    return Div(DIV_EQ)
+
+
+def KL(lam):
+    return Div(DIV_KL, lam=lam)
+
+
+def TV(lam):
+    return Div(DIV_TV, lam=lam)
+
+
+def RG(alpha, beta):
+    return Div(DIV_RG, alpha=alpha, beta=beta)
+
+
+def _dtype(prec):
+    return torch.float64 if prec == F64 else torch.float32
+
+
+def _ptr(t: torch.Tensor | None, dtype=None, what="tensor"):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{what} must be a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{what} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    return t.data_ptr()
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+@dataclass
+class Geometry:
+    """Device-side geometry; tensors must outlive the calls that use it."""
+    kind: int
+    n: int
+    m: int
+    C: torch.Tensor | None = None
+    axes_x: tuple = ()
+    axes_y: tuple = ()
+    x: torch.Tensor | None = None
+    y: torch.Tensor | None = None
+
+    @staticmethod
+    def dense(C):
+        return Geometry(GEOM_DENSE, C.shape[0], C.shape[1], C=C.contiguous())
+
+    @staticmethod
+    def grid(axes_x, axes_y=None):
+        axes_y = axes_x if axes_y is None else axes_y
+        n = math.prod(a.numel() for a in axes_x)
+        m = math.prod(a.numel() for a in axes_y)
+        return Geometry(GEOM_GRID, n, m, axes_x=tuple(a.contiguous() for a in axes_x),
+                        axes_y=tuple(a.contiguous() for a in axes_y))
+
+    @staticmethod
+    def points(x, y):
+        return Geometry(GEOM_POINTS, x.shape[0], y.shape[0], x=x.contiguous(), y=y.contiguous())
+
+    @property
+    def shape_x(self):
+        return tuple(a.numel() for a in self.axes_x) if self.kind == GEOM_GRID else (self.n,)
+
+    @property
+    def shape_y(self):
+        return tuple(a.numel() for a in self.axes_y) if self.kind == GEOM_GRID else (self.m,)
+
+    def c(self, prec) -> CGeom:
+        dt = _dtype(prec)
+        g = CGeom()
+        g.kind, g.n, g.m = self.kind, self.n, self.m
+        if self.kind == GEOM_DENSE:
+            g.C = _ptr(self.C, dt, "C")
+        elif self.kind == GEOM_POINTS:
+            g.x = _ptr(self.x, dt, "x")
+            g.y = _ptr(self.y, dt, "y")
+            g.d = self.x.shape[1]
+            if self.y.shape[1] != g.d:
+                raise ValueError("x and y must have the same dimension")
+        else:
+            if len(self.axes_x) != len(self.axes_y) or not 1 <= len(self.axes_x) <= MAX_DIM:
+                raise ValueError("grid axes")
+            g.ndim = len(self.axes_x)
+            for k, (ax, ay) in enumerate(zip(self.axes_x, self.axes_y)):
+                g.shape_x[k], g.shape_y[k] = ax.numel(), ay.numel()
+                g.axes_x[k] = _ptr(ax, dt, "axis")
+                g.axes_y[k] = _ptr(ay, dt, "axis")
+        return g
+
+
+def _check(status, what):
+    if status < 0:
+        raise UotError(status, what)
+    return status
+
+
+def solve(geom: Geometry, p, dx, q, dy, F1: Div, F2: Div, eps: float, *, precision=F64,
+          max_iter=1000, tol=0.0, check_every=10, eps_start=None, eps_stages=10,
+          iters_per_stage=100, plain_scaling=False, U0=None, V0=None, U=None, V=None):
+    """uot_solve: returns (U, V, result dict).  Inputs are CUDA tensors of the
+    precision's dtype; U, V (optional) are preallocated outputs."""
+    lib = load()
+    dt = _dtype(precision)
+    U = torch.empty(geom.n, dtype=dt, device=p.device) if U is None else U
+    V = torch.empty(geom.m, dtype=dt, device=p.device) if V is None else V
+    o = COpts(precision, float(eps), float(eps_start) if eps_start else 0.0, int(eps_stages),
+              int(iters_per_stage), int(max_iter), float(tol), int(check_every),
+              int(bool(plain_scaling)), _ptr(U0, dt, "U0"), _ptr(V0, dt, "V0"))
+    r = CResult()
+    g = geom.c(precision)
+    st = lib.uot_solve(C.byref(g), _ptr(p, dt, "p"), _ptr(dx, dt, "dx"), _ptr(q, dt, "q"),
+                       _ptr(dy, dt, "dy"), C.byref(F1.c()), C.byref(F2.c()), C.byref(o),
+                       _ptr(U, dt, "U"), _ptr(V, dt, "V"), C.byref(r), _stream())
+    _check(st, "uot_solve")
+    return U, V, dict(iters=r.iters, total_iters=r.total_iters, marg_err=r.marg_err, ms=r.ms,
+                      status=STATUS[st])
+
+
+def gibbs_log(geom: Geometry, W, w, eps, transpose=False, precision=F64, out=None):
+    """uot_gibbs_log: eps log K(e^{W/eps} . w) (or with K^T)."""
+    lib = load()
+    dt = _dtype(precision)
+    nout = geom.m if transpose else geom.n
+    out = torch.empty(nout, dtype=dt, device=W.device) if out is None else out
+    g = geom.c(precision)
+    _check(lib.uot_gibbs_log(C.byref(g), _ptr(W, dt, "W"), _ptr(w, dt, "w"), float(eps),
+                             int(bool(transpose)), precision, _ptr(out, dt, "out"), _stream()),
+           "uot_gibbs_log")
+    return out
+
+
+def apply_plan(geom: Geometry, U, V, eps, dx, dy, f=None, transpose=False, precision=F64, out=None):
+    """uot_apply_plan: R f (or R^T f) for nonnegative f of shape [m, ncols] ([n, ncols])."""
+    lib = load()
+    dt = _dtype(precision)
+    nout = geom.m if transpose else geom.n
+    ncols = 1 if f is None else (f.shape[1] if f.dim() == 2 else 1)
+    out = torch.empty(nout, ncols, dtype=dt, device=U.device) if out is None else out
+    g = geom.c(precision)
+    _check(lib.uot_apply_plan(C.byref(g), _ptr(U, dt, "U"), _ptr(V, dt, "V"), float(eps),
+                              _ptr(dx, dt, "dx"), _ptr(dy, dt, "dy"), _ptr(f, dt, "f"), ncols,
+                              int(bool(transpose)), precision, _ptr(out, dt, "out"), _stream()),
+           "uot_apply_plan")
+    return out
+
+
+def objective(geom: Geometry, p, dx, q, dy, F1: Div, F2: Div, eps, U, V, precision=F64):
+    """uot_objective: dict(primal, dual, gap, marg_err) in FP64."""
+    lib = load()
+    dt = _dtype(precision)
+    out = (C.c_double * 4)()
+    g = geom.c(precision)
+    _check(lib.uot_objective(C.byref(g), _ptr(p, dt, "p"), _ptr(dx, dt, "dx"), _ptr(q, dt, "q"),
+                             _ptr(dy, dt, "dy"), C.byref(F1.c()), C.byref(F2.c()), float(eps),
+                             _ptr(U, dt, "U"), _ptr(V, dt, "V"), precision, out, _stream()),
+           "uot_objective")
+    return dict(primal=out[0], dual=out[1], gap=out[2], marg_err=out[3])
+
+
+def barycenter(geom: Geometry, alpha, P, dx, dy, F1: Div, lam, eps, *, kind=BARY_KL,
+               precision=F64, max_iter=1000, tol=0.0, check_every=10, eps_start=None,
+               eps_stages=10, iters_per_stage=100):
+    """uot_barycenter: returns (eps log h, U [K,n], V [K,m], result dict)."""
+    lib = load()
+    dt = _dtype(precision)
+    K = P.shape[0]
+    logh = torch.empty(geom.m, dtype=dt, device=P.device)
+    U = torch.empty(K, geom.n, dtype=dt, device=P.device)
+    V = torch.empty(K, geom.m, dtype=dt, device=P.device)
+    a = (C.c_double * K)(*[float(v) for v in alpha])
+    o = COpts(precision, float(eps), float(eps_start) if eps_start else 0.0, int(eps_stages),
+              int(iters_per_stage), int(max_iter), float(tol), int(check_every), 0, None, None)
+    r = CResult()
+    g = geom.c(precision)
+    st = lib.uot_barycenter(C.byref(g), K, a, _ptr(P, dt, "P"), _ptr(dx, dt, "dx"),
+                            _ptr(dy, dt, "dy"), C.byref(F1.c()), float(lam), int(kind),
+                            C.byref(o), _ptr(logh, dt, "logh"), _ptr(U, dt, "U"),
+                            _ptr(V, dt, "V"), C.byref(r), _stream())
+    _check(st, "uot_barycenter")
+    return logh, U, V, dict(iters=r.iters, total_iters=r.total_iters, marg_err=r.marg_err,
+                            ms=r.ms, status=STATUS[st])

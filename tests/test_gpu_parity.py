@@ -1,0 +1,302 @@
+"""GPU parity: the CUDA library (through the C ABI) against the FP64 oracle on
+the same seeded inputs, element by element.
+
+Tolerances (relative to max(1, |reference|_inf) on log-potentials, as the
+accuracy targets state): FP64 path 1e-10, FP32 path 1e-5.  Sizes span several
+CTA tiles with ragged tails (64 outputs and 4 lines per CTA for grid passes,
+8 rows per CTA for row kernels).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_1607_05816_gb300 import synth
+from paper_1607_05816_gb300 import uot as U
+
+pytestmark = [pytest.mark.gpu, pytest.mark.filterwarnings("ignore::RuntimeWarning")]
+
+TOL = {U.F64: 1e-10, U.F32: 1e-5}
+DEV = "cuda"
+
+
+def T(a, prec):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=U._dtype(prec), device=DEV)
+
+
+def rel_err(got, want):
+    got = np.asarray(got, dtype=np.float64).ravel()
+    want = np.asarray(want, dtype=np.float64).ravel()
+    assert np.array_equal(np.isneginf(got), np.isneginf(want)), "-inf pattern differs"
+    f = np.isfinite(want)
+    if not f.any():
+        return 0.0
+    return float(np.max(np.abs(got[f] - want[f])) / max(1.0, np.max(np.abs(want[f]))))
+
+
+def to_np(t):
+    return t.detach().double().cpu().numpy()
+
+
+# ----------------------------------------------------------------------------
+# problem builders: (oracle geometry, library geometry factory, dx, dy, p, q)
+# ----------------------------------------------------------------------------
+
+def grid_problem(shape_x, shape_y, seed, zeros=True):
+    g = synth.rng(seed)
+    xs = [synth.grid_axis(n) for n in shape_x]
+    ys = [synth.grid_axis(n) for n in shape_y]
+    dx = np.full(shape_x, 1.0 / np.prod(shape_x))
+    dy = np.full(shape_y, 1.0 / np.prod(shape_y))
+    p = g.uniform(0.2, 2.0, size=shape_x)
+    q = g.uniform(0.2, 2.0, size=shape_y)
+    if zeros:
+        p.ravel()[:: 7] = 0.0
+        q.ravel()[3:: 11] = 0.0
+    p *= 1.0 / np.sum(p * dx)
+    q *= 1.3 / np.sum(q * dy)
+    og = O.Geometry("grid", xs=xs, ys=ys)
+
+    def lg(prec):
+        return U.Geometry.grid([T(a, prec) for a in xs], [T(a, prec) for a in ys])
+    return og, lg, dx, dy, p, q
+
+
+def points_problem(n, m, d, seed):
+    g = synth.rng(seed)
+    x = synth.mixture_points(g, n, d, 4)
+    y = synth.mixture_points(g, m, d, 4)
+    og = O.Geometry("points", x=x, y=y)
+
+    def lg(prec):
+        return U.Geometry.points(T(x, prec), T(y, prec))
+    return og, lg, np.full(n, 1.0 / n), np.full(m, 1.0 / m), np.full(n, 1.0), np.full(m, 0.7)
+
+
+def dense_problem(n, m, seed):
+    d = synth.problem_1d(n, m, seed=seed)
+    C = O.sqdist(d["x"], d["y"])
+    og = O.Geometry("dense", C=C)
+
+    def lg(prec):
+        return U.Geometry.dense(T(C, prec))
+    return og, lg, d["dx"], d["dy"], d["p"], d["q"]
+
+
+# ----------------------------------------------------------------------------
+# the Gibbs operator alone
+# ----------------------------------------------------------------------------
+
+GIBBS_CASES = [
+    ("grid2d", lambda: grid_problem((70, 45), (33, 129), 1)),
+    ("grid1d", lambda: grid_problem((300,), (257,), 2)),
+    ("grid3d", lambda: grid_problem((9, 13, 6), (7, 5, 11), 3)),
+    ("points", lambda: points_problem(301, 260, 3, 4)),
+    ("dense", lambda: dense_problem(97, 130, 5)),
+]
+
+
+@pytest.mark.parametrize("prec", [U.F64, U.F32])
+@pytest.mark.parametrize("name,make", GIBBS_CASES)
+@pytest.mark.parametrize("transpose", [False, True])
+def test_gibbs_log_parity(name, make, prec, transpose):
+    og, lg, dx, dy, p, q = make()
+    g = synth.rng(9)
+    eps = 0.01
+    shape_in = np.shape(dx) if transpose else np.shape(dy)
+    W = g.normal(size=shape_in) * 0.05
+    W.ravel()[5:: 13] = -np.inf
+    w = dx if transpose else dy
+    want = O.apply_K_log(og, W, np.log(w), eps, transpose=transpose)
+    got = U.gibbs_log(lg(prec), T(W, prec).ravel(), T(w, prec).ravel(), eps, transpose, prec)
+    assert rel_err(to_np(got), want) <= TOL[prec]
+
+
+def test_gibbs_all_zero_line():
+    """A whole grid line with b = 0 yields empty sums (-inf), not NaN."""
+    og, lg, dx, dy, p, q = grid_problem((20, 24), (20, 24), 6)
+    W = np.zeros((20, 24))
+    W[3, :] = -np.inf
+    W[:, 5] = -np.inf
+    want = O.apply_K_log(og, W, np.log(dy), 0.02)
+    for prec in (U.F64, U.F32):
+        got = U.gibbs_log(lg(prec), T(W, prec).ravel(), T(dy, prec).ravel(), 0.02, False, prec)
+        assert rel_err(to_np(got), want) <= TOL[prec]
+    W[:] = -np.inf
+    got = U.gibbs_log(lg(U.F64), T(W, U.F64).ravel(), T(dy, U.F64).ravel(), 0.02, False, U.F64)
+    assert np.all(np.isneginf(to_np(got)))
+
+
+# ----------------------------------------------------------------------------
+# iterations: U, V at equal iteration counts
+# ----------------------------------------------------------------------------
+
+DIVS = [
+    (O.KL(0.5), O.KL(0.5), U.KL(0.5), U.KL(0.5)),
+    (O.TV(0.1), O.KL(0.1), U.TV(0.1), U.KL(0.1)),
+    (O.RG(0.7, 1.2), O.TV(0.3), U.RG(0.7, 1.2), U.TV(0.3)),
+    (O.EQ(), O.KL(1.0), U.EQ(), U.KL(1.0)),
+    (O.RG(0.0, math.inf), O.RG(0.5, 2.0), U.RG(0.0, math.inf), U.RG(0.5, 2.0)),
+]
+
+
+def run_both(og, lg, dx, dy, p, q, divs, eps, iters, prec, eps_start=None, stages=0, ips=0):
+    OF1, OF2, UF1, UF2 = divs
+    r = O.solve_log(og, dx, dy, p, q, OF1, OF2, eps, max_iter=iters, eps_start=eps_start,
+                    stages=stages, iters_per_stage=ips)
+    Ug, Vg, info = U.solve(lg(prec), T(p, prec).ravel(), T(dx, prec).ravel(), T(q, prec).ravel(),
+                           T(dy, prec).ravel(), UF1, UF2, eps, precision=prec, max_iter=iters,
+                           eps_start=eps_start, eps_stages=stages, iters_per_stage=ips)
+    return r, to_np(Ug), to_np(Vg), info
+
+
+@pytest.mark.parametrize("prec", [U.F64, U.F32])
+@pytest.mark.parametrize("divs", DIVS, ids=["kl-kl", "tv-kl", "rg-tv", "eq-kl", "rg-rg"])
+def test_solve_grid_parity(divs, prec):
+    og, lg, dx, dy, p, q = grid_problem((40, 67), (52, 38), 10)
+    r, Ug, Vg, info = run_both(og, lg, dx, dy, p, q, divs, 0.01, 30, prec)
+    assert info["iters"] == 30
+    assert rel_err(Ug, r["U"]) <= TOL[prec]
+    assert rel_err(Vg, r["V"]) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [U.F64, U.F32])
+def test_solve_grid_eps_scaling_parity(prec):
+    """eps-scaling stages (Sec. 4.4) then iterations at the final eps."""
+    og, lg, dx, dy, p, q = grid_problem((48, 48), (48, 48), 11, zeros=False)
+    r, Ug, Vg, info = run_both(og, lg, dx, dy, p, q, DIVS[0], 1e-3, 20, prec,
+                               eps_start=0.1, stages=10, ips=5)
+    assert info["total_iters"] == 70
+    assert rel_err(Ug, r["U"]) <= TOL[prec]
+    assert rel_err(Vg, r["V"]) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [U.F64, U.F32])
+@pytest.mark.parametrize("divs", DIVS[:3], ids=["kl-kl", "tv-kl", "rg-tv"])
+def test_solve_points_parity(divs, prec):
+    og, lg, dx, dy, p, q = points_problem(333, 250, 3, 12)
+    r, Ug, Vg, info = run_both(og, lg, dx, dy, p, q, divs, 0.01, 25, prec)
+    assert rel_err(Ug, r["U"]) <= TOL[prec]
+    assert rel_err(Vg, r["V"]) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [U.F64, U.F32])
+def test_solve_dense_parity(prec):
+    og, lg, dx, dy, p, q = dense_problem(256, 256, 1234)
+    r, Ug, Vg, info = run_both(og, lg, dx, dy, p, q, DIVS[0], 1e-2, 50, prec)
+    assert rel_err(Ug, r["U"]) <= TOL[prec]
+    assert rel_err(Vg, r["V"]) <= TOL[prec]
+
+
+def test_plain_scaling_alg1_parity():
+    """Algorithm 1 (no stabilisation) on the dense 1-D problem: 256 points,
+    KL lambda = 1 both sides, eps = 1e-2, FP64, against the oracle's
+    Algorithm 1 run verbatim."""
+    d = synth.problem_1d(256, 256, seed=1234)
+    C = O.sqdist(d["x"], d["y"])
+    eps, iters = 1e-2, 2000
+    a, b = O.scaling_alg1(np.exp(-C / eps), d["dx"], d["dy"], d["p"], d["q"], O.KL(1.0), O.KL(1.0), eps, iters)
+    Ug, Vg, info = U.solve(U.Geometry.dense(T(C, U.F64)), T(d["p"], U.F64), T(d["dx"], U.F64),
+                           T(d["q"], U.F64), T(d["dy"], U.F64), U.KL(1.0), U.KL(1.0), eps,
+                           precision=U.F64, max_iter=iters, plain_scaling=True)
+    assert rel_err(to_np(Ug), eps * np.log(a)) <= 1e-10
+    assert rel_err(to_np(Vg), eps * np.log(b)) <= 1e-10
+
+
+def test_tolerance_stop_matches_oracle():
+    """The stopping rule (violation measured in the next a-update) stops at the
+    same iteration as the oracle's solve_log and reports the same violation."""
+    og, lg, dx, dy, p, q = dense_problem(120, 90, 77)
+    r = O.solve_log(og, dx, dy, p, q, O.KL(0.3), O.KL(0.3), 0.02, max_iter=5000, tol=1e-8, check_every=7)
+    Ug, Vg, info = U.solve(lg(U.F64), T(p, U.F64), T(dx, U.F64), T(q, U.F64), T(dy, U.F64),
+                           U.KL(0.3), U.KL(0.3), 0.02, precision=U.F64, max_iter=5000, tol=1e-8,
+                           check_every=7)
+    assert info["status"] == "UOT_OK"
+    assert info["iters"] == r["iters"]
+    assert abs(info["marg_err"] - r["err"]) <= 1e-6 * r["err"]
+    assert rel_err(to_np(Ug), r["U"]) <= 1e-10
+
+
+# ----------------------------------------------------------------------------
+# plan application and objective
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec", [U.F64, U.F32])
+def test_apply_plan_marginals_and_projection(prec):
+    og, lg, dx, dy, p, q = grid_problem((21, 34), (30, 17), 13, zeros=False)
+    r = O.solve_log(og, dx, dy, p, q, O.KL(0.5), O.KL(0.5), 0.02, max_iter=40)
+    r1, r2 = O.marginals(og, dx.ravel(), dy.ravel(), r["U"].ravel(), r["V"].ravel(), 0.02)
+    geo = lg(prec)
+    Ut, Vt = T(r["U"], prec).ravel(), T(r["V"], prec).ravel()
+    g1 = U.apply_plan(geo, Ut, Vt, 0.02, T(dx, prec).ravel(), T(dy, prec).ravel(), precision=prec)
+    g2 = U.apply_plan(geo, Ut, Vt, 0.02, T(dx, prec).ravel(), T(dy, prec).ravel(), transpose=True, precision=prec)
+    tol = 1e-10 if prec == U.F64 else 2e-4
+    assert np.max(np.abs(to_np(g1)[:, 0] - r1) / r1) <= tol
+    assert np.max(np.abs(to_np(g2)[:, 0] - r2) / r2) <= tol
+    # barycentric projection numerator R (y . dy): coordinates as nonnegative f
+    Y = O.grid_points(og.ys)
+    R = np.exp(O.log_plan(og, r["U"], r["V"], 0.02))
+    want = R @ (Y * dy.ravel()[:, None])
+    got = U.apply_plan(geo, Ut, Vt, 0.02, T(dx, prec).ravel(), T(dy, prec).ravel(), f=T(Y, prec), precision=prec)
+    assert np.max(np.abs(to_np(got) - want) / want) <= tol
+
+
+@pytest.mark.parametrize("divs", [DIVS[0], DIVS[1], (O.TV(0.2), O.TV(0.3), U.TV(0.2), U.TV(0.3))], ids=["kl", "tv-kl", "tv"])
+def test_objective_parity(divs):
+    OF1, OF2, UF1, UF2 = divs
+    og, lg, dx, dy, p, q = points_problem(90, 70, 2, 14)
+    eps = 0.05
+    r = O.solve_log(og, dx, dy, p, q, OF1, OF2, eps, max_iter=60)
+    P = O.primal(og, dx, dy, p, q, OF1, OF2, eps, r["U"], r["V"])
+    D = O.dual(og, dx, dy, p, q, OF1, OF2, eps, r["U"], r["V"])
+    err = O.marginal_violation(og, dx, dy, p, q, OF1, OF2, eps, r["U"], r["V"])
+    got = U.objective(lg(U.F64), T(p, U.F64), T(dx, U.F64), T(q, U.F64), T(dy, U.F64), UF1, UF2,
+                      eps, T(r["U"], U.F64), T(r["V"], U.F64))
+    assert abs(got["primal"] - P) <= 1e-10 * max(1, abs(P))
+    assert abs(got["dual"] - D) <= 1e-10 * max(1, abs(D))
+    assert abs(got["gap"] - (P - D)) <= 1e-10 * max(1, abs(P))
+    assert abs(got["marg_err"] - err) <= 1e-8 * max(err, 1e-12)
+
+
+# ----------------------------------------------------------------------------
+# barycenters
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec", [U.F64, U.F32])
+@pytest.mark.parametrize("kind", [U.BARY_KL, U.BARY_EQ])
+def test_barycenter_parity(kind, prec):
+    d = synth.barycenter_images(K=5, H=24, W=36, seed=15)
+    og = O.Geometry("grid", xs=d["xs"], ys=d["ys"])
+    alpha = np.array([0.1, 0.3, 0.2, 0.25, 0.15])
+    eps, lam, iters = 0.01, 1.0, 25
+    Uo, Vo, lho = O.barycenter_log(og, d["dx"], d["dy"], d["P"], alpha, O.EQ(), lam, eps, iters,
+                                   bary_kind="kl" if kind == U.BARY_KL else "eq")
+    geo = U.Geometry.grid([T(a, prec) for a in d["xs"]])
+    lh, Ug, Vg, info = U.barycenter(geo, alpha, T(d["P"].reshape(5, -1), prec), T(d["dx"], prec).ravel(),
+                                    T(d["dy"], prec).ravel(), U.EQ(), lam, eps, kind=kind,
+                                    precision=prec, max_iter=iters)
+    assert rel_err(to_np(lh), lho) <= TOL[prec]
+    assert rel_err(to_np(Ug), Uo.reshape(5, -1)) <= TOL[prec]
+    assert rel_err(to_np(Vg), Vo.reshape(5, -1)) <= TOL[prec]
+
+
+# ----------------------------------------------------------------------------
+# argument checking (host side, nothing launched)
+# ----------------------------------------------------------------------------
+
+def test_invalid_arguments_rejected():
+    og, lg, dx, dy, p, q = dense_problem(16, 16, 3)
+    geo = lg(U.F64)
+    args = (T(p, U.F64), T(dx, U.F64), T(q, U.F64), T(dy, U.F64))
+    with pytest.raises(U.UotError, match="EINVAL"):
+        U.solve(geo, *args, U.KL(-1.0), U.KL(1.0), 0.1)
+    with pytest.raises(U.UotError, match="EINVAL"):
+        U.solve(geo, *args, U.KL(1.0), U.KL(1.0), 0.0)
+    with pytest.raises(U.UotError, match="EINVAL"):
+        U.solve(geo, *args, U.RG(2.0, 1.0), U.KL(1.0), 0.1)
+    with pytest.raises(U.UotError, match="EUNSUPPORTED"):
+        gp = grid_problem((8,), (8,), 1)
+        U.solve(gp[1](U.F64), T(gp[4], U.F64), T(gp[2], U.F64), T(gp[5], U.F64), T(gp[3], U.F64),
+                U.KL(1.0), U.KL(1.0), 0.1, plain_scaling=True)
