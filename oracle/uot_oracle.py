@@ -371,9 +371,11 @@ def solve_log(geom: Geometry, dx, dy, p, q, F1: Div, F2: Div, eps: float,
               iters_per_stage: int = 100, check_every: int = 1, U0=None, V0=None):
     """eps-scaling then iterations at eps until marginal_violation <= tol.
 
-    The check of iterate l happens inside iteration l+1 (its a-update), so the
-    returned state is one iteration past the first one under tol; `iters`
-    counts iterations at the final eps only.
+    The violation is measured every `check_every` iterations, in iterations
+    number check_every, 2 check_every, ... (and the last one).  The check of
+    iterate l happens inside iteration l+1 (its a-update), so the returned
+    state is one iteration past the first one under tol; `iters` counts
+    iterations at the final eps only.
     """
     logdx, logdy, logp, logq = map(safe_log, (dx, dy, p, q))
     U, V = U0, V0
@@ -388,7 +390,7 @@ def solve_log(geom: Geometry, dx, dy, p, q, F1: Div, F2: Div, eps: float,
     while it < max_iter:
         S = apply_K_log(geom, V, logdy, eps)
         Un = prox_update_log(F1, logp, S, eps)
-        if (it % check_every) == 0 or it == max_iter - 1:
+        if (it + 1) % check_every == 0 or it == max_iter - 1:
             err = _violation_from(U, Un, S, logdx, eps)
             if it > 0 and err <= tol:
                 stop = True

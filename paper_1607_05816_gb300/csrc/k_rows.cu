@@ -133,6 +133,78 @@ __global__ void __launch_bounds__(WARPS * 32)
   if (epi.err) block_add2<WARPS * 32>(num, den, epi.err);
 }
 
+// FP32 path: L_j = W_j/eps + log w_j in float-float; Lt_j = (L_j - max) log2(e)
+// in FP32; *Lmax (a float) receives the maximum of the high parts.
+template <int NT>
+__global__ void __launch_bounds__(NT) prepare_L_ff(const float2* __restrict__ W,
+                                                   const float2* __restrict__ logw, int nin,
+                                                   float2 inv_eps, float* __restrict__ Lt,
+                                                   float* __restrict__ Lmax) {
+  __shared__ float red[NT / 32];
+  float mx = -INFINITY;
+  for (int j = threadIdx.x; j < nin; j += NT) {
+    const ff w = ffl(W[j]);
+    const ff L = (w.hi == -INFINITY) ? ff_ninf() : ff_add(ff_mul(w, ffl(inv_eps)), ffl(logw[j]));
+    mx = fmaxf(mx, L.hi);
+  }
+  mx = wmax(mx);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    float v = (threadIdx.x < NT / 32) ? red[threadIdx.x] : -INFINITY;
+    v = wmax(v);
+    if (threadIdx.x == 0) red[0] = v;
+  }
+  __syncthreads();
+  mx = red[0];
+  for (int j = threadIdx.x; j < nin; j += NT) {
+    const ff w = ffl(W[j]);
+    const ff L = (w.hi == -INFINITY) ? ff_ninf() : ff_add(ff_mul(w, ffl(inv_eps)), ffl(logw[j]));
+    Lt[j] = (mx == -INFINITY || L.hi == -INFINITY) ? -INFINITY : ((L.hi - mx) + L.lo) * kLog2e;
+  }
+  if (threadIdx.x == 0) *Lmax = mx;
+}
+
+template <int DMAX, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32)
+    rows_lse_f32(int kind, const float* __restrict__ C, const float* __restrict__ x,
+                 const float* __restrict__ y, int d, int nrows, int nin,
+                 const float* __restrict__ Lt, const float* __restrict__ Lmax_p, float k2,
+                 Epilogue epi) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.x * WARPS + warp;
+  float num = 0.0f, den = 0.0f;
+  const float Lmax = *Lmax_p;
+  if (i < nrows) {
+    if (Lmax == -INFINITY) {
+      if (lane == 0) apply_epilogue_ff(epi, 0, i, ff_ninf(), num, den);
+    } else {
+      RowCtx<float, DMAX> c;
+      if (kind == UOT_GEOM_POINTS) {
+#pragma unroll
+        for (int k = 0; k < DMAX; ++k) c.xi[k] = (k < d) ? x[(int64_t)i * d + k] : 0.0f;
+      }
+      const int64_t rowbase = (int64_t)i * nin;
+      float m = -INFINITY;
+      for (int j = lane; j < nin; j += 32)
+        m = fmaxf(m, fmaf(-k2, cost_ij<float, DMAX>(kind, C, y, d, rowbase, j, c), Lt[j]));
+      m = wmax(m);
+      float s = 0.0f;
+      for (int j = lane; j < nin; j += 32)
+        s += ex2_approx(fmaf(-k2, cost_ij<float, DMAX>(kind, C, y, d, rowbase, j, c), Lt[j] - m));
+      s = wsum(s);
+      if (lane == 0) {
+        const ff ln2 = ff{0.693147182464599609375f, -1.904654323148236017e-09f};
+        float lg;
+        asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(lg) : "f"(s));
+        const ff z = ff_add_f(ff_add_f(ff_mul_f(ln2, m), Lmax), kLn2 * lg);
+        apply_epilogue_ff(epi, 0, i, z, num, den);
+      }
+    }
+  }
+  if (epi.err) block_add2f<WARPS * 32>(num, den, epi.err);
+}
+
 // Table 1 proxdiv column with u = 0 (non-log form), 0/0 = 0.
 __device__ inline double proxdiv_plain(const DivParams& F, double p, double s, double eps) {
   if (!(s > 0.0)) return 0.0;
@@ -190,18 +262,19 @@ cudaError_t launch_rows(int prec, const RowsGeom& g, int nrows, int nin, const d
   count_launches(2);
   if (prec == UOT_F32) {
     float* Lt = (float*)scratch_L;
-    double* Lmax = (double*)((char*)scratch_L + (((size_t)nin * 4 + 255) & ~(size_t)255));
-    prepare_L<float, 1024><<<1, 1024, 0, s>>>(W, logw, nin, eps, Lt, Lmax);
+    float* Lmax = (float*)((char*)scratch_L + (((size_t)nin * 4 + 255) & ~(size_t)255));
+    prepare_L_ff<1024><<<1, 1024, 0, s>>>(reinterpret_cast<const float2*>(W),
+                                           reinterpret_cast<const float2*>(logw), nin,
+                                           ff2(ff_make(1.0 / eps)), Lt, Lmax);
     prof_mark_begin(PROF_ROWS, s);
     const float* C = (const float*)g.C;
     const float* x = (const float*)g.x;
     const float* y = (const float*)g.y;
+    const float k2 = (float)((double)kLog2e / eps);
     if (g.kind == UOT_GEOM_DENSE || g.d <= 4)
-      rows_lse<float, 4, WARPS><<<grid, WARPS * 32, 0, s>>>(g.kind, C, x, y, g.d, nrows, nin, Lt,
-                                                           Lmax, eps, epi);
+      rows_lse_f32<4, WARPS><<<grid, WARPS * 32, 0, s>>>(g.kind, C, x, y, g.d, nrows, nin, Lt, Lmax, k2, epi);
     else
-      rows_lse<float, 8, WARPS><<<grid, WARPS * 32, 0, s>>>(g.kind, C, x, y, g.d, nrows, nin, Lt,
-                                                           Lmax, eps, epi);
+      rows_lse_f32<8, WARPS><<<grid, WARPS * 32, 0, s>>>(g.kind, C, x, y, g.d, nrows, nin, Lt, Lmax, k2, epi);
   } else {
     double* Lt = (double*)scratch_L;
     double* Lmax = (double*)((char*)scratch_L + (((size_t)nin * 8 + 255) & ~(size_t)255));

@@ -52,16 +52,21 @@ cudaEvent_t prof_event() {
   return e;
 }
 
-uot_status fail_cuda(cudaError_t e) {
+uot_status fail_cuda(cudaError_t e, const char* what = nullptr, int line = 0) {
   g_last_error = cudaGetErrorString(e);
+  if (what) g_last_error += std::string(" [") + what + " @uot_api.cu:" + std::to_string(line) + "]";
   return (e == cudaErrorMemoryAllocation) ? UOT_ENOMEM : UOT_ECUDA;
 }
 
-#define UOT_CK(expr)                               \
-  do {                                             \
-    cudaError_t e_ = (expr);                       \
-    if (e_ != cudaSuccess) return fail_cuda(e_);   \
+#define UOT_CK(expr)                                                \
+  do {                                                              \
+    cudaError_t e_ = (expr);                                        \
+    if (e_ != cudaSuccess) return fail_cuda(e_, #expr, __LINE__);   \
   } while (0)
+
+// Errors raised by other code sharing this CUDA runtime (non-sticky ones) must
+// not be attributed to this call: clear them on entry.
+inline void clear_stale_error() { (void)cudaGetLastError(); }
 
 // ---------------------------------------------------------------------------
 // pointwise kernels
@@ -83,6 +88,35 @@ __global__ void k_to_log(const T* __restrict__ src, int64_t n, double* __restric
   }
 }
 
+// FP32 path: per-point arrays hold float-float pairs in 8-byte slots.
+__global__ void k_to_log_ff(const float* __restrict__ src, int64_t n, float2* __restrict__ dst) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = (double)src[i];
+    dst[i] = ff2(ff_make(v > 0.0 ? log(v) : -kInf));
+  }
+}
+__global__ void k_to_ff(const float* __restrict__ src, int64_t n, float2* __restrict__ dst) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = make_float2(src[i], 0.0f);
+}
+__global__ void k_from_ff(const float2* __restrict__ src, int64_t n, float* __restrict__ dst) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float2 v = src[i];
+    dst[i] = (v.x == -INFINITY) ? v.x : v.x + v.y;
+  }
+}
+// in place: float-float slot -> double slot (for FP64 reductions of FP32-path results)
+__global__ void k_ff_to_double(double* __restrict__ a, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float2 v = reinterpret_cast<const float2*>(a)[i];
+    a[i] = (v.x == -INFINITY) ? -kInf : (double)v.x + (double)v.y;
+  }
+}
+
 template <typename T>
 __global__ void k_to_f64(const T* __restrict__ src, int64_t n, double* __restrict__ dst) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -101,6 +135,19 @@ __global__ void k_fill(double* __restrict__ dst, int64_t n, double v) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
     dst[i] = v;
+}
+
+// FP32 path of k_add_logf: float-float V, float f.
+__global__ void k_add_logf_ff(const double* __restrict__ Vd, const float* __restrict__ f, int ncols,
+                              int col, int64_t n, double eps, double* __restrict__ Wd) {
+  const float2* V = reinterpret_cast<const float2*>(Vd);
+  float2* W = reinterpret_cast<float2*>(Wd);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const ff v = ffl(V[i]);
+    const double fv = f ? (double)f[i * ncols + col] : 1.0;
+    W[i] = (v.hi == -INFINITY || !(fv > 0.0)) ? ff2(ff_ninf()) : ff2(ff_add(v, ff_make(eps * log(fv))));
+  }
 }
 
 // W = V + eps log f[:, col]  (apply_plan: fold a nonnegative function into the input)
@@ -158,10 +205,16 @@ __global__ void k_log_scale(const double* __restrict__ a, int64_t n, double eps,
     U[i] = (a[i] > 0.0) ? eps * log(a[i]) : -kInf;
 }
 
-__global__ void k_nan_flag(const double* __restrict__ a, int64_t n, int* flag) {
+__global__ void k_nan_flag(const double* __restrict__ a, int64_t n, int ffmode, int* flag) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    if (a[i] != a[i]) *flag = 1;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (ffmode) {
+      const float2 v = reinterpret_cast<const float2*>(a)[i];
+      if (v.x != v.x || v.y != v.y) *flag = 1;
+    } else if (a[i] != a[i]) {
+      *flag = 1;
+    }
+  }
 }
 
 // Barycenter F2 step (Sec. 5.2): from T_k = eps log s_k, the barycenter
@@ -199,6 +252,57 @@ __global__ void k_bary_update(const double* __restrict__ T, int K, int64_t m,
     F.log_alpha = 0.0;
     F.log_beta = 0.0;
     for (int k = 0; k < K; ++k) V[(int64_t)k * m + j] = prox_update(F, lh, T[(int64_t)k * m + j], eps);
+  }
+}
+
+// FP32 path of k_bary_update: float-float T, V, logh; FP32 arithmetic.
+__global__ void k_bary_update_ff(const double* __restrict__ Td, int K, int64_t m,
+                                 const float* __restrict__ log_alpha, float log_sum_alpha,
+                                 float2 epslam, float2 inv_epslam, float2 inv_eps, float2 eps_ff,
+                                 int kind, DivFF Fh, double* __restrict__ loghd,
+                                 double* __restrict__ Vd) {
+  const float2* T = reinterpret_cast<const float2*>(Td);
+  float2* logh = reinterpret_cast<float2*>(loghd);
+  float2* V = reinterpret_cast<float2*>(Vd);
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    ff elogh;
+    if (kind == UOT_BARY_KL) {
+      // eps log h = (eps+lam) (LSE_k(log alpha_k + T_k/(eps+lam)) - log sum alpha)
+      float mx = -INFINITY;
+      for (int k = 0; k < K; ++k) {
+        const ff t = ffl(T[(int64_t)k * m + j]);
+        if (t.hi != -INFINITY) mx = fmaxf(mx, ff_add_f(ff_mul(t, ffl(inv_epslam)), log_alpha[k]).hi);
+      }
+      if (mx == -INFINITY) {
+        elogh = ff_ninf();
+      } else {
+        float acc = 0.0f;
+        ff lead = ff{0.0f, 0.0f};
+        for (int k = 0; k < K; ++k) {
+          const ff t = ffl(T[(int64_t)k * m + j]);
+          if (t.hi == -INFINITY) continue;
+          const ff a = ff_add_f(ff_mul(t, ffl(inv_epslam)), log_alpha[k]);
+          acc += expf((a.hi - mx) + a.lo);
+        }
+        lead = ff_add_f(ff{mx, 0.0f}, logf(acc) - log_sum_alpha);
+        elogh = ff_mul(lead, ffl(epslam));
+      }
+    } else {
+      // eps log h = sum_k alpha_k T_k / sum alpha (geometric mean)
+      ff acc = ff{0.0f, 0.0f};
+      bool neg_inf = false;
+      for (int k = 0; k < K; ++k) {
+        const ff t = ffl(T[(int64_t)k * m + j]);
+        if (t.hi == -INFINITY) neg_inf = true;
+        else acc = ff_add(acc, ff_mul_f(t, expf(log_alpha[k] - log_sum_alpha)));
+      }
+      elogh = neg_inf ? ff_ninf() : acc;
+    }
+    logh[j] = ff2(elogh);
+    const ff lh = (elogh.hi == -INFINITY) ? ff_ninf() : ff_mul(elogh, ffl(inv_eps));
+    for (int k = 0; k < K; ++k)
+      V[(int64_t)k * m + j] = ff2(prox_update_ff(Fh, lh, ffl(T[(int64_t)k * m + j]), ffl(eps_ff)));
   }
 }
 
@@ -338,30 +442,50 @@ uot_status check_geom(const uot_geom* g) {
   }
 }
 
-// Device memory carved out of one stream-ordered allocation, released on destruction.
+// Device memory carved out of one stream-ordered allocation, released on
+// destruction.  Every buffer is reserved with the same element count that is
+// later taken, each rounded to 256 bytes; take() refuses to run past the end.
 class Scratch {
  public:
   explicit Scratch(cudaStream_t s) : s_(s) {}
   ~Scratch() {
     if (base_) cudaFreeAsync(base_, s_);
   }
-  void reserve(size_t bytes) { need_ += (bytes + 255) & ~(size_t)255; }
+  template <typename T>
+  void reserve(size_t count) { need_ += round(count * sizeof(T)); }
   cudaError_t allocate() {
     if (need_ == 0) return cudaSuccess;
     return cudaMallocAsync((void**)&base_, need_, s_);
   }
   template <typename T>
   T* take(size_t count) {
+    const size_t b = round(count * sizeof(T));
+    if (!base_ || off_ + b > need_) {
+      overflow_ = true;
+      return nullptr;
+    }
     T* p = (T*)(base_ + off_);
-    off_ += (count * sizeof(T) + 255) & ~(size_t)255;
+    off_ += b;
     return p;
   }
+  // false if any take() did not fit what was reserved (a bug: nothing may be launched)
+  bool ok() const { return !overflow_; }
 
  private:
+  static size_t round(size_t b) { return (b + 255) & ~(size_t)255; }
   cudaStream_t s_;
   char* base_ = nullptr;
   size_t need_ = 0, off_ = 0;
+  bool overflow_ = false;
 };
+
+#define UOT_SCRATCH_OK(sc)                                         \
+  do {                                                             \
+    if (!(sc).ok()) {                                              \
+      g_last_error = "internal scratch accounting error";          \
+      return UOT_ECUDA;                                            \
+    }                                                              \
+  } while (0)
 
 struct Gibbs {
   uot_geom g;
@@ -369,6 +493,11 @@ struct Gibbs {
   size_t esz;
   const void* CT = nullptr;     // dense: C^T in the precision's type
   double* pass[2] = {nullptr, nullptr};  // grid intermediates
+  // FP32 grid passes: result of each (direction, pass) from the previous call,
+  // reused as the log-sum-exp shift while eps is unchanged (see k_grid.cu)
+  float* zbuf[2][UOT_MAX_DIM] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+  double zeps[2] = {-1.0, -1.0};
+  bool speculate = false;
   void* Lscratch = nullptr;     // rows: shifted input line
   int64_t inter = 0;            // grid intermediate size (elements)
   int nbatch = 1;
@@ -376,22 +505,25 @@ struct Gibbs {
   void plan(Scratch& sc, int batch) {
     nbatch = batch;
     esz = (prec == UOT_F64) ? 8 : 4;
-    if (g.kind == UOT_GEOM_DENSE) sc.reserve((size_t)g.n * g.m * esz);
+    if (g.kind == UOT_GEOM_DENSE) sc.reserve<char>((size_t)g.n * g.m * esz);
     if (g.kind == UOT_GEOM_GRID) {
       inter = 1;
       for (int k = 0; k < g.ndim; ++k) inter *= (g.shape_x[k] > g.shape_y[k] ? g.shape_x[k] : g.shape_y[k]);
       if (g.ndim > 1) {
-        sc.reserve((size_t)inter * nbatch * 8);
-        sc.reserve((size_t)inter * nbatch * 8);
+        sc.reserve<double>((size_t)inter * nbatch);
+        sc.reserve<double>((size_t)inter * nbatch);
       }
+      if (speculate && prec == UOT_F32)
+        for (int k = 0; k < 2 * g.ndim; ++k) sc.reserve<float>((size_t)inter * nbatch);
     } else {
       const int64_t mx = (g.n > g.m ? g.n : g.m);
-      sc.reserve((size_t)mx * 8 + 512);
+      sc.reserve<char>((size_t)mx * 8 + 512);
     }
   }
   cudaError_t take(Scratch& sc, cudaStream_t s) {
     if (g.kind == UOT_GEOM_DENSE) {
       void* ct = sc.take<char>((size_t)g.n * g.m * esz);
+      if (!ct) return cudaErrorInvalidValue;
       dim3 grid((g.m + 31) / 32, (g.n + 31) / 32), blk(32, 8);
       count_launches(1);
       if (prec == UOT_F64)
@@ -405,6 +537,9 @@ struct Gibbs {
         pass[0] = sc.take<double>((size_t)inter * nbatch);
         pass[1] = sc.take<double>((size_t)inter * nbatch);
       }
+      if (speculate && prec == UOT_F32)
+        for (int d = 0; d < 2; ++d)
+          for (int k = 0; k < g.ndim; ++k) zbuf[d][k] = sc.take<float>((size_t)inter * nbatch);
     } else {
       const int64_t mx = (g.n > g.m ? g.n : g.m);
       Lscratch = sc.take<char>((size_t)mx * 8 + 512);
@@ -413,9 +548,12 @@ struct Gibbs {
   }
 
   // dir 0: W on the Y side (size m) -> result on the X side (size n); dir 1: reverse.
+  // zero_acc: two doubles cleared before the result is produced (violation
+  // accumulators of a checked iteration), inside the first kernel when possible.
   cudaError_t apply(int dir, const double* W, const double* logw, double eps, const Epilogue& epi,
-                    cudaStream_t s) const {
+                    cudaStream_t s, double* zero_acc = nullptr) {
     if (g.kind == UOT_GEOM_GRID) {
+      const int use_prev = (zbuf[dir][0] != nullptr && zeps[dir] == eps) ? 1 : 0;
       const int d = g.ndim;
       const int* in_shape = dir == 0 ? g.shape_y : g.shape_x;
       const int* out_shape = dir == 0 ? g.shape_x : g.shape_y;
@@ -436,14 +574,28 @@ struct Gibbs {
           e.out = pass[k & 1];
           e.bstride = nlines * out_shape[ax];
         }
+        double* za = nullptr;
+        if (k == 0 && zero_acc) {
+          if (prec == UOT_F32) {
+            za = zero_acc;
+          } else {
+            cudaError_t e0 = cudaMemsetAsync(zero_acc, 0, 16, s);
+            if (e0 != cudaSuccess) return e0;
+          }
+        }
         cudaError_t err = launch_grid_pass(prec, cur, logw, cur_is_pot, (int)nlines, in_shape[ax],
                                            in_axes[ax], out_shape[ax], out_axes[ax], eps, nbatch,
-                                           e, s);
+                                           e, s, zbuf[dir][k], use_prev, za);
         if (err != cudaSuccess) return err;
         cur = pass[k & 1];
         cur_is_pot = 0;
       }
+      if (zbuf[dir][0]) zeps[dir] = eps;
       return cudaSuccess;
+    }
+    if (zero_acc) {
+      cudaError_t e0 = cudaMemsetAsync(zero_acc, 0, 16, s);
+      if (e0 != cudaSuccess) return e0;
     }
     RowsGeom rg;
     rg.kind = g.kind;
@@ -470,27 +622,45 @@ struct Gibbs {
   }
 };
 
+// Per-point state conversions: FP64 path -> double slots; FP32 path ->
+// float-float pairs in the same 8-byte slots.
 cudaError_t to_log(int prec, const void* src, int64_t n, double* dst, cudaStream_t s) {
   count_launches(1);
   if (prec == UOT_F64)
     k_to_log<double><<<nblocks(n), kNT, 0, s>>>((const double*)src, n, dst);
   else
-    k_to_log<float><<<nblocks(n), kNT, 0, s>>>((const float*)src, n, dst);
+    k_to_log_ff<<<nblocks(n), kNT, 0, s>>>((const float*)src, n, reinterpret_cast<float2*>(dst));
   return cudaGetLastError();
 }
 cudaError_t to_f64(int prec, const void* src, int64_t n, double* dst, cudaStream_t s) {
   if (prec == UOT_F64)
     return cudaMemcpyAsync(dst, src, n * 8, cudaMemcpyDeviceToDevice, s);
   count_launches(1);
-  k_to_f64<float><<<nblocks(n), kNT, 0, s>>>((const float*)src, n, dst);
+  k_to_ff<<<nblocks(n), kNT, 0, s>>>((const float*)src, n, reinterpret_cast<float2*>(dst));
   return cudaGetLastError();
 }
 cudaError_t from_f64(int prec, const double* src, int64_t n, void* dst, cudaStream_t s) {
   if (prec == UOT_F64)
     return cudaMemcpyAsync(dst, src, n * 8, cudaMemcpyDeviceToDevice, s);
   count_launches(1);
-  k_from_f64<float><<<nblocks(n), kNT, 0, s>>>(src, n, (float*)dst);
+  k_from_ff<<<nblocks(n), kNT, 0, s>>>(reinterpret_cast<const float2*>(src), n, (float*)dst);
   return cudaGetLastError();
+}
+
+DivFF make_div_ff(const DivParams& F, double eps) {
+  DivFF d;
+  d.kind = F.kind;
+  d.zf = ff2(ff_make(F.lam / (F.lam + eps)));
+  d.lam = ff2(ff_make(F.lam));
+  d.elog_a = (F.log_alpha == -kInf) ? make_float2(-INFINITY, 0.0f) : ff2(ff_make(eps * F.log_alpha));
+  d.elog_b = (F.log_beta == kInf) ? make_float2(INFINITY, 0.0f) : ff2(ff_make(eps * F.log_beta));
+  return d;
+}
+
+void set_eps(Epilogue& e, double eps) {
+  e.eps = eps;
+  e.eps_ff = ff2(ff_make(eps));
+  e.inv_eps_ff = ff2(ff_make(1.0 / eps));
 }
 
 Epilogue prox_epilogue(const DivParams& F, const double* logp, double* pot, const double* logw,
@@ -498,7 +668,8 @@ Epilogue prox_epilogue(const DivParams& F, const double* logp, double* pot, cons
   Epilogue e;
   memset(&e, 0, sizeof(e));
   e.mode = EPI_PROX;
-  e.eps = eps;
+  set_eps(e, eps);
+  e.Fff = make_div_ff(F, eps);
   e.F = F;
   e.logp = logp;
   e.pot = pot;
@@ -563,11 +734,17 @@ uot_status solve_impl(const uot_geom* g, const void* p, const void* dx, const vo
   Gibbs G;
   G.g = *g;
   G.prec = prec;
+  G.speculate = true;
   G.plan(sc, 1);
-  sc.reserve(n * 8 * 3);  // logp, logdx, U
-  sc.reserve(m * 8 * 3);  // logq, logdy, V
-  sc.reserve(64);         // err accumulators + flag
-  if (o->plain_scaling) sc.reserve((size_t)n * m * 8 * 2 + n * 8 * 2 + m * 8 * 2);
+  for (int k = 0; k < 3; ++k) sc.reserve<double>(n);  // logp, logdx, U
+  for (int k = 0; k < 3; ++k) sc.reserve<double>(m);  // logq, logdy, V
+  sc.reserve<double>(8);                              // err accumulators + flag
+  if (o->plain_scaling) {
+    sc.reserve<double>((size_t)n * m);  // K
+    sc.reserve<double>((size_t)n * m);  // K^T
+    for (int k = 0; k < 3; ++k) sc.reserve<double>(n);  // a, p, dx
+    for (int k = 0; k < 3; ++k) sc.reserve<double>(m);  // b, q, dy
+  }
   UOT_CK(sc.allocate());
   UOT_CK(G.take(sc, s));
   double* logp = sc.take<double>(n);
@@ -578,6 +755,7 @@ uot_status solve_impl(const uot_geom* g, const void* p, const void* dx, const vo
   double* V = sc.take<double>(m);
   double* acc = sc.take<double>(8);
   int* flag = (int*)(acc + 4);
+  UOT_SCRATCH_OK(sc);
   UOT_CK(to_log(prec, p, n, logp, s));
   UOT_CK(to_log(prec, dx, n, logdx, s));
   UOT_CK(to_log(prec, q, m, logq, s));
@@ -605,15 +783,15 @@ uot_status solve_impl(const uot_geom* g, const void* p, const void* dx, const vo
   if (!o->plain_scaling) {
     auto iteration = [&](double eps, bool check) -> cudaError_t {
       cudaError_t e;
-      if (check && (e = cudaMemsetAsync(acc, 0, 16, s)) != cudaSuccess) return e;
-      if ((e = G.apply(0, V, logdy, eps, prox_epilogue(D1, logp, U, logdx, check ? acc : nullptr, eps), s)) != cudaSuccess)
+      if ((e = G.apply(0, V, logdy, eps, prox_epilogue(D1, logp, U, logdx, check ? acc : nullptr, eps), s,
+                       check ? acc : nullptr)) != cudaSuccess)
         return e;
       return G.apply(1, U, logdx, eps, prox_epilogue(D2, logq, V, logdy, nullptr, eps), s);
     };
     for (const Stage& sg : stages)
       for (int k = 0; k < sg.iters; ++k, ++total) UOT_CK(iteration(sg.eps, false));
     while (it < o->max_iter) {
-      const bool check = (it % check_every == 0) || (it == o->max_iter - 1);
+      const bool check = ((it + 1) % check_every == 0) || (it == o->max_iter - 1);
       UOT_CK(iteration(o->eps, check));
       ++it;
       ++total;
@@ -638,6 +816,7 @@ uot_status solve_impl(const uot_geom* g, const void* p, const void* dx, const vo
     double* qd = sc.take<double>(m);
     double* dxd = sc.take<double>(n);
     double* dyd = sc.take<double>(m);
+    UOT_SCRATCH_OK(sc);
     UOT_CK(to_f64(prec, p, n, pd, s));
     UOT_CK(to_f64(prec, q, m, qd, s));
     UOT_CK(to_f64(prec, dx, n, dxd, s));
@@ -668,7 +847,7 @@ uot_status solve_impl(const uot_geom* g, const void* p, const void* dx, const vo
     }
     UOT_CK(set_eps(o->eps));
     while (it < o->max_iter) {
-      const bool check = (it % check_every == 0) || (it == o->max_iter - 1);
+      const bool check = ((it + 1) % check_every == 0) || (it == o->max_iter - 1);
       if (check) UOT_CK(cudaMemsetAsync(acc, 0, 16, s));
       UOT_CK(launch_alg1_half(K, (int)n, (int)m, b, dyd, pd, D1, o->eps, a, dxd, check ? acc : nullptr, s));
       UOT_CK(launch_alg1_half(KT, (int)m, (int)n, a, dxd, qd, D2, o->eps, b, dyd, nullptr, s));
@@ -691,9 +870,9 @@ uot_status solve_impl(const uot_geom* g, const void* p, const void* dx, const vo
   // NaN check and output conversion
   UOT_CK(cudaMemsetAsync(flag, 0, 4, s));
   count_launches(1);
-  k_nan_flag<<<nblocks(n), kNT, 0, s>>>(U, n, flag);
+  k_nan_flag<<<nblocks(n), kNT, 0, s>>>(U, n, prec == UOT_F32, flag);
   count_launches(1);
-  k_nan_flag<<<nblocks(m), kNT, 0, s>>>(V, m, flag);
+  k_nan_flag<<<nblocks(m), kNT, 0, s>>>(V, m, prec == UOT_F32, flag);
   UOT_CK(cudaGetLastError());
   UOT_CK(from_f64(prec, U, n, Uout, s));
   UOT_CK(from_f64(prec, V, m, Vout, s));
@@ -780,11 +959,13 @@ uot_status uot_profile_end(int family, double* total_ms, long long* launches) {
 uot_status uot_solve(const uot_geom* g, const void* p, const void* dx, const void* q,
                      const void* dy, const uot_div* F1, const uot_div* F2, const uot_opts* o,
                      void* U, void* V, uot_result* res, void* stream) {
+  clear_stale_error();
   return solve_impl(g, p, dx, q, dy, F1, F2, o, U, V, res, (cudaStream_t)stream);
 }
 
 uot_status uot_gibbs_log(const uot_geom* g, const void* W, const void* w, double eps,
                          int transpose, int precision, void* out, void* stream) {
+  clear_stale_error();
   uot_status st = check_geom(g);
   if (st != UOT_OK) return st;
   if (!W || !w || !out || !(eps > 0.0) || !prec_ok(precision)) return UOT_EINVAL;
@@ -795,18 +976,21 @@ uot_status uot_gibbs_log(const uot_geom* g, const void* W, const void* w, double
   G.g = *g;
   G.prec = precision;
   G.plan(sc, 1);
-  sc.reserve(nin * 8 * 2 + nout * 8);
+  sc.reserve<double>(nin);
+  sc.reserve<double>(nin);
+  sc.reserve<double>(nout);
   UOT_CK(sc.allocate());
   UOT_CK(G.take(sc, s));
   double* Wd = sc.take<double>(nin);
   double* logw = sc.take<double>(nin);
   double* od = sc.take<double>(nout);
+  UOT_SCRATCH_OK(sc);
   UOT_CK(to_f64(precision, W, nin, Wd, s));
   UOT_CK(to_log(precision, w, nin, logw, s));
   Epilogue e;
   memset(&e, 0, sizeof(e));
   e.mode = EPI_SCALE;
-  e.eps = eps;
+  set_eps(e, eps);
   e.out = od;
   UOT_CK(G.apply(transpose ? 1 : 0, Wd, logw, eps, e, s));
   UOT_CK(from_f64(precision, od, nout, out, s));
@@ -816,6 +1000,7 @@ uot_status uot_gibbs_log(const uot_geom* g, const void* W, const void* w, double
 uot_status uot_apply_plan(const uot_geom* g, const void* U, const void* V, double eps,
                           const void* dx, const void* dy, const void* f, int ncols,
                           int transpose, int precision, void* out, void* stream) {
+  clear_stale_error();
   uot_status st = check_geom(g);
   if (st != UOT_OK) return st;
   if (!U || !V || !dx || !dy || !out || !(eps > 0.0) || !prec_ok(precision)) return UOT_EINVAL;
@@ -828,7 +1013,9 @@ uot_status uot_apply_plan(const uot_geom* g, const void* U, const void* V, doubl
   G.g = *g;
   G.prec = precision;
   G.plan(sc, 1);
-  sc.reserve(nin * 8 * 3 + nout * 8 * (ncols + 1));
+  for (int k = 0; k < 3; ++k) sc.reserve<double>(nin);
+  sc.reserve<double>(nout);
+  sc.reserve<double>(nout * ncols);
   UOT_CK(sc.allocate());
   UOT_CK(G.take(sc, s));
   double* Win = sc.take<double>(nin);
@@ -836,6 +1023,7 @@ uot_status uot_apply_plan(const uot_geom* g, const void* U, const void* V, doubl
   double* logw = sc.take<double>(nin);
   double* Sh = sc.take<double>(nout);
   double* od = sc.take<double>(nout * ncols);
+  UOT_SCRATCH_OK(sc);
   UOT_CK(to_f64(precision, transpose ? U : V, nin, Win, s));
   UOT_CK(to_f64(precision, transpose ? V : U, nout, Sh, s));
   UOT_CK(to_log(precision, transpose ? dx : dy, nin, logw, s));
@@ -844,12 +1032,12 @@ uot_status uot_apply_plan(const uot_geom* g, const void* U, const void* V, doubl
     if (precision == UOT_F64)
       k_add_logf<double><<<nblocks(nin), kNT, 0, s>>>(Win, (const double*)f, ncols, c, nin, eps, W);
     else
-      k_add_logf<float><<<nblocks(nin), kNT, 0, s>>>(Win, (const float*)f, ncols, c, nin, eps, W);
+      k_add_logf_ff<<<nblocks(nin), kNT, 0, s>>>(Win, (const float*)f, ncols, c, nin, eps, W);
     UOT_CK(cudaGetLastError());
     Epilogue e;
     memset(&e, 0, sizeof(e));
     e.mode = EPI_PLAN;
-    e.eps = eps;
+    set_eps(e, eps);
     e.out = od;
     e.pot_shift = Sh;
     e.ncols = ncols;
@@ -863,6 +1051,7 @@ uot_status uot_apply_plan(const uot_geom* g, const void* U, const void* V, doubl
 uot_status uot_objective(const uot_geom* g, const void* p, const void* dx, const void* q,
                          const void* dy, const uot_div* F1, const uot_div* F2, double eps,
                          const void* U, const void* V, int precision, double* out, void* stream) {
+  clear_stale_error();
   uot_status st = check_geom(g);
   if (st != UOT_OK) return st;
   if (!p || !dx || !q || !dy || !U || !V || !out || !(eps > 0.0) || !prec_ok(precision) ||
@@ -875,7 +1064,10 @@ uot_status uot_objective(const uot_geom* g, const void* p, const void* dx, const
   G.g = *g;
   G.prec = precision;
   G.plan(sc, 1);
-  sc.reserve(n * 8 * 7 + m * 8 * 7 + 128);
+  for (int k = 0; k < 6; ++k) sc.reserve<double>(n);  // Ud logp logdx r1 zK1 S1
+  for (int k = 0; k < 4; ++k) sc.reserve<double>(m);  // Vd logq logdy r2
+  sc.reserve<double>(n > m ? n : m);                  // zero
+  sc.reserve<double>(16);                             // acc
   UOT_CK(sc.allocate());
   UOT_CK(G.take(sc, s));
   double* Ud = sc.take<double>(n);
@@ -890,6 +1082,7 @@ uot_status uot_objective(const uot_geom* g, const void* p, const void* dx, const
   double* S1 = sc.take<double>(n);
   double* zero = sc.take<double>(n > m ? n : m);
   double* acc = sc.take<double>(16);
+  UOT_SCRATCH_OK(sc);
   UOT_CK(to_f64(precision, U, n, Ud, s));
   UOT_CK(to_f64(precision, V, m, Vd, s));
   UOT_CK(to_log(precision, p, n, logp, s));
@@ -901,7 +1094,7 @@ uot_status uot_objective(const uot_geom* g, const void* p, const void* dx, const
   UOT_CK(cudaMemsetAsync(acc, 0, 16 * 8, s));
   Epilogue e;
   memset(&e, 0, sizeof(e));
-  e.eps = eps;
+  set_eps(e, eps);
   // r1 = R dy, r2 = R^T dx
   e.mode = EPI_PLAN;
   e.ncols = 1;
@@ -919,6 +1112,19 @@ uot_status uot_objective(const uot_geom* g, const void* p, const void* dx, const
   e.out = S1;
   UOT_CK(G.apply(0, Vd, logdy, eps, e, s));
   const DivParams D1 = make_div(*F1), D2 = make_div(*F2);
+  if (precision == UOT_F32) {
+    double* arrs_n[] = {Ud, logp, logdx, r1, zK1, S1};
+    double* arrs_m[] = {Vd, logq, logdy, r2};
+    for (double* a : arrs_n) {
+      count_launches(1);
+      k_ff_to_double<<<nblocks(n), kNT, 0, s>>>(a, n);
+    }
+    for (double* a : arrs_m) {
+      count_launches(1);
+      k_ff_to_double<<<nblocks(m), kNT, 0, s>>>(a, m);
+    }
+    UOT_CK(cudaGetLastError());
+  }
   count_launches(1);
   k_objective_side<<<nblocks(n) > 1024 ? 1024 : nblocks(n), kNT, 0, s>>>(r1, Ud, logp, logdx, zK1, S1, D1, eps, n, acc);
   count_launches(1);
@@ -942,6 +1148,7 @@ uot_status uot_barycenter(const uot_geom* g, int Kmeas, const double* alpha, con
                           const void* dx, const void* dy, const uot_div* F1, double lambda,
                           int bary_kind, const uot_opts* o, void* logh_out, void* Uout,
                           void* Vout, uot_result* res, void* stream) {
+  clear_stale_error();
   uot_status st = check_geom(g);
   if (st != UOT_OK) return st;
   if ((st = check_opts(o)) != UOT_OK) return st;
@@ -976,10 +1183,18 @@ uot_status uot_barycenter(const uot_geom* g, int Kmeas, const double* alpha, con
   Gibbs G;
   G.g = *g;
   G.prec = prec;
+  G.speculate = true;
   G.plan(sc, Kmeas);
-  sc.reserve(n * Kmeas * 8 * 2 + n * 8);
-  sc.reserve(m * Kmeas * 8 * 2 + m * 8 * 2);
-  sc.reserve(Kmeas * 8 + 64);
+  sc.reserve<double>(n * Kmeas);  // logP
+  sc.reserve<double>(n * Kmeas);  // U
+  sc.reserve<double>(n);          // logdx
+  sc.reserve<double>(m * Kmeas);  // V
+  sc.reserve<double>(m * Kmeas);  // T
+  sc.reserve<double>(m);          // logdy
+  sc.reserve<double>(m);          // logh
+  sc.reserve<double>(Kmeas);      // alpha
+  sc.reserve<float>(Kmeas);       // log alpha (FP32 path)
+  sc.reserve<double>(8);          // acc
   UOT_CK(sc.allocate());
   UOT_CK(G.take(sc, s));
   double* logP = sc.take<double>(n * Kmeas);
@@ -990,11 +1205,18 @@ uot_status uot_barycenter(const uot_geom* g, int Kmeas, const double* alpha, con
   double* logdy = sc.take<double>(m);
   double* logh = sc.take<double>(m);
   double* alpha_d = sc.take<double>(Kmeas);
+  float* log_alpha_d = sc.take<float>(Kmeas);
   double* acc = sc.take<double>(8);
+  UOT_SCRATCH_OK(sc);
   UOT_CK(to_log(prec, P, n * Kmeas, logP, s));
   UOT_CK(to_log(prec, dx, n, logdx, s));
   UOT_CK(to_log(prec, dy, m, logdy, s));
   UOT_CK(cudaMemcpyAsync(alpha_d, alpha, Kmeas * 8, cudaMemcpyHostToDevice, s));
+  std::vector<float> log_alpha_h(Kmeas);
+  for (int k = 0; k < Kmeas; ++k) log_alpha_h[k] = (float)log(alpha[k]);
+  UOT_CK(cudaMemcpyAsync(log_alpha_d, log_alpha_h.data(), Kmeas * 4, cudaMemcpyHostToDevice, s));
+  // pageable source: make sure the copy has consumed it before the vector dies
+  UOT_CK(cudaStreamSynchronize(s));
   count_launches(1);
   k_fill<<<nblocks(n * Kmeas), kNT, 0, s>>>(U, n * Kmeas, 0.0);
   count_launches(1);
@@ -1003,21 +1225,31 @@ uot_status uot_barycenter(const uot_geom* g, int Kmeas, const double* alpha, con
 
   auto iteration = [&](double eps, bool check) -> cudaError_t {
     cudaError_t e;
-    if (check && (e = cudaMemsetAsync(acc, 0, 16, s)) != cudaSuccess) return e;
     Epilogue e1 = prox_epilogue(D1, logP, U, logdx, check ? acc : nullptr, eps);
     e1.bstride = n;
     e1.bstride_p = n;
-    if ((e = G.apply(0, V, logdy, eps, e1, s)) != cudaSuccess) return e;
+    if ((e = G.apply(0, V, logdy, eps, e1, s, check ? acc : nullptr)) != cudaSuccess) return e;
     Epilogue e2;
     memset(&e2, 0, sizeof(e2));
     e2.mode = EPI_SCALE;
-    e2.eps = eps;
+    set_eps(e2, eps);
     e2.out = T;
     e2.bstride = m;
     count_launches(1);
     if ((e = G.apply(1, U, logdx, eps, e2, s)) != cudaSuccess) return e;
-    k_bary_update<<<nblocks(m), kNT, 0, s>>>(T, Kmeas, m, alpha_d, sum_alpha, lambda, eps,
-                                             bary_kind, logh, V);
+    if (prec == UOT_F64) {
+      k_bary_update<<<nblocks(m), kNT, 0, s>>>(T, Kmeas, m, alpha_d, sum_alpha, lambda, eps,
+                                               bary_kind, logh, V);
+    } else {
+      DivParams Dh;
+      Dh.kind = (bary_kind == UOT_BARY_KL) ? UOT_DIV_KL : UOT_DIV_EQ;
+      Dh.lam = lambda;
+      Dh.log_alpha = Dh.log_beta = 0.0;
+      k_bary_update_ff<<<nblocks(m), kNT, 0, s>>>(
+          T, Kmeas, m, log_alpha_d, (float)log(sum_alpha), ff2(ff_make(eps + lambda)),
+          ff2(ff_make(1.0 / (eps + lambda))), ff2(ff_make(1.0 / eps)), ff2(ff_make(eps)),
+          bary_kind, make_div_ff(Dh, eps), logh, V);
+    }
     return cudaGetLastError();
   };
   const std::vector<Stage> stages = eps_schedule(*o);
@@ -1028,7 +1260,7 @@ uot_status uot_barycenter(const uot_geom* g, int Kmeas, const double* alpha, con
   for (const Stage& sg : stages)
     for (int k = 0; k < sg.iters; ++k, ++total) UOT_CK(iteration(sg.eps, false));
   while (it < o->max_iter) {
-    const bool check = (it % check_every == 0) || (it == o->max_iter - 1);
+    const bool check = ((it + 1) % check_every == 0) || (it == o->max_iter - 1);
     UOT_CK(iteration(o->eps, check));
     ++it;
     ++total;

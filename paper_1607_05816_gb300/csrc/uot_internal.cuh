@@ -18,12 +18,83 @@ constexpr double kInf = __builtin_huge_val();
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kLn2 = 0.6931471805599453f;
 
+// ---------------------------------------------------------------------------
+// Float-float numbers (hi + lo, two FP32 values, ~48-bit significand).
+// The FP32 path keeps every per-point quantity (potentials, log densities and
+// weights, intermediate log-sums) in this form so that the iteration never
+// uses the FP64 pipe, which on GB300 runs at a small fraction of the FP32 rate.
+// Built from the error-free transformations TwoSum and TwoProd (Knuth, Dekker);
+// infinities are carried in `hi` with lo = 0.
+// ---------------------------------------------------------------------------
+struct ff {
+  float hi, lo;
+};
+
+__host__ __device__ inline ff ff_make(double x) {
+  ff r;
+  r.hi = (float)x;
+  r.lo = (x == x && x != kInf && x != -kInf) ? (float)(x - (double)r.hi) : 0.0f;
+  return r;
+}
+__host__ __device__ inline float2 ff2(const ff& a) { return make_float2(a.hi, a.lo); }
+__device__ __forceinline__ ff ffl(float2 v) { return ff{v.x, v.y}; }
+__device__ __forceinline__ ff ff_two_sum(float a, float b) {
+  const float s = a + b;
+  if (!isfinite(s)) return ff{s, 0.0f};
+  const float bb = s - a;
+  const float e = (a - (s - bb)) + (b - bb);
+  return ff{s, e};
+}
+__device__ __forceinline__ ff ff_fast_two_sum(float a, float b) {
+  const float s = a + b;
+  if (!isfinite(s)) return ff{s, 0.0f};
+  return ff{s, b - (s - a)};
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+  const ff s = ff_two_sum(a.hi, b.hi);
+  if (!isfinite(s.hi)) return s;
+  return ff_fast_two_sum(s.hi, s.lo + (a.lo + b.lo));
+}
+__device__ __forceinline__ ff ff_neg(ff a) { return ff{-a.hi, -a.lo}; }
+__device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, ff_neg(b)); }
+__device__ __forceinline__ ff ff_add_f(ff a, float b) {
+  const ff s = ff_two_sum(a.hi, b);
+  if (!isfinite(s.hi)) return s;
+  return ff_fast_two_sum(s.hi, s.lo + a.lo);
+}
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+  const float p = a.hi * b.hi;
+  if (!isfinite(p) || p == 0.0f) return ff{p, 0.0f};
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
+  return ff_fast_two_sum(p, e);
+}
+__device__ __forceinline__ ff ff_mul_f(ff a, float b) {
+  const float p = a.hi * b;
+  if (!isfinite(p) || p == 0.0f) return ff{p, 0.0f};
+  const float e = fmaf(a.lo, b, fmaf(a.hi, b, -p));
+  return ff_fast_two_sum(p, e);
+}
+__device__ __forceinline__ bool ff_lt(ff a, ff b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+__device__ __forceinline__ ff ff_min(ff a, ff b) { return ff_lt(b, a) ? b : a; }
+__device__ __forceinline__ ff ff_max(ff a, ff b) { return ff_lt(a, b) ? b : a; }
+__host__ __device__ constexpr ff ff_ninf() { return ff{-__builtin_huge_valf(), 0.0f}; }
+
 // A marginal penalty prepared for the device (Table 1 row + parameters).
 struct DivParams {
   int kind;          // uot_div_kind
   double lam;        // KL, TV weight
   double log_alpha;  // RG: log alpha (-inf when alpha == 0)
   double log_beta;   // RG: log beta (+inf when beta == +inf)
+};
+
+// eps-dependent constants of one Table 1 row in float-float form (FP32 path).
+struct DivFF {
+  int kind;
+  float2 zf;         // KL: lam/(lam+eps)
+  float2 lam;        // TV: lam
+  float2 elog_a;     // RG: eps log alpha (hi = -inf when alpha == 0)
+  float2 elog_b;     // RG: eps log beta (hi = +inf when beta == +inf)
 };
 
 // Table 1 in log form with u = 0: U = eps log proxdiv_F(s, eps) given
@@ -60,6 +131,10 @@ enum EpiMode {
 struct Epilogue {
   int mode;
   double eps;
+  // FP32 path: arrays hold float-float pairs in their 8-byte slots
+  int ff;
+  float2 eps_ff, inv_eps_ff;
+  DivFF Fff;
   // EPI_PROX
   DivParams F;
   const double* logp;      // log density of the output side
@@ -117,6 +192,127 @@ __device__ inline void apply_epilogue(const Epilogue& e, int64_t b, int64_t pt, 
   }
 }
 
+// Table 1 in log form, float-float version of prox_update.
+__device__ inline ff prox_update_ff(const DivFF& F, ff logp, ff S, ff eps) {
+  if (S.hi == -INFINITY) return ff_ninf();
+  const ff ubar = (logp.hi == -INFINITY) ? ff_ninf() : ff_sub(ff_mul(eps, logp), S);
+  switch (F.kind) {
+    case UOT_DIV_EQ:
+      return ubar;
+    case UOT_DIV_KL:
+      return (ubar.hi == -INFINITY) ? ubar : ff_mul(ffl(F.zf), ubar);
+    case UOT_DIV_TV: {
+      const ff lam = ffl(F.lam);
+      return ff_min(lam, ff_max(ff_neg(lam), ubar));
+    }
+    default: {
+      const ff lo = (F.elog_a.x == -INFINITY || ubar.hi == -INFINITY) ? ff_ninf() : ff_add(ffl(F.elog_a), ubar);
+      const ff inner = ff_max(lo, ff{0.0f, 0.0f});
+      if (F.elog_b.x == INFINITY) return inner;
+      const ff hi = (ubar.hi == -INFINITY) ? ff_ninf() : ff_add(ffl(F.elog_b), ubar);
+      return ff_min(hi, inner);
+    }
+  }
+}
+
+// FP32 violation terms from float-float potentials: r_new = e^{(U_new+S)/eps},
+// |r_old - r_new| = r_new |expm1((U_old - U_new)/eps)|.
+__device__ inline void violation_terms_ff(ff Uold, ff Unew, ff S, ff logw, ff inv_eps, float& num,
+                                          float& den) {
+  const float w = expf(logw.hi + logw.lo);
+  if (S.hi == -INFINITY) {
+    num = den = 0.0f;
+    return;
+  }
+  float rn = 0.0f, ro = 0.0f;
+  if (Unew.hi != -INFINITY) {
+    const ff a = ff_mul(ff_add(Unew, S), inv_eps);
+    rn = expf(a.hi + a.lo);
+  }
+  if (Uold.hi != -INFINITY) {
+    const ff a = ff_mul(ff_add(Uold, S), inv_eps);
+    ro = expf(a.hi + a.lo);
+  }
+  float diff;
+  if (Uold.hi != -INFINITY && Unew.hi != -INFINITY) {
+    const ff d = ff_mul(ff_sub(Uold, Unew), inv_eps);
+    diff = rn * fabsf(expm1f(d.hi + d.lo));
+  } else {
+    diff = fabsf(ro - rn);
+  }
+  num = w * diff;
+  den = w * rn;
+}
+
+// Float-float epilogue (FP32 path): z is the log-sum in natural units.
+__device__ inline void apply_epilogue_ff(const Epilogue& e, int64_t b, int64_t pt, ff z, float& num,
+                                         float& den) {
+  num = 0.0f;
+  den = 0.0f;
+  const int64_t q = b * e.bstride + pt;
+  switch (e.mode) {
+    case EPI_RAW:
+      reinterpret_cast<float2*>(e.out)[q] = ff2(z);
+      break;
+    case EPI_SCALE:
+      reinterpret_cast<float2*>(e.out)[q] = ff2(z.hi == -INFINITY ? z : ff_mul(z, ffl(e.eps_ff)));
+      break;
+    case EPI_PROX: {
+      const ff eps = ffl(e.eps_ff);
+      const ff S = (z.hi == -INFINITY) ? ff_ninf() : ff_mul(z, eps);
+      float2* pot = reinterpret_cast<float2*>(e.pot);
+      const ff Uold = ffl(pot[q]);
+      const ff lp = ffl(reinterpret_cast<const float2*>(e.logp)[b * e.bstride_p + pt]);
+      const ff Unew = prox_update_ff(e.Fff, lp, S, eps);
+      pot[q] = ff2(Unew);
+      if (e.err)
+        violation_terms_ff(Uold, Unew, S, ffl(reinterpret_cast<const float2*>(e.logw)[pt]),
+                           ffl(e.inv_eps_ff), num, den);
+      break;
+    }
+    default: {  // EPI_PLAN
+      const ff u = ffl(reinterpret_cast<const float2*>(e.pot_shift)[q]);
+      float v = 0.0f;
+      if (u.hi != -INFINITY && z.hi != -INFINITY) {
+        const ff a = ff_add(ff_mul(u, ffl(e.inv_eps_ff)), z);
+        v = expf(a.hi + a.lo);
+      }
+      reinterpret_cast<float2*>(e.out)[q * e.ncols + e.col] = make_float2(v, 0.0f);
+      break;
+    }
+  }
+}
+
+// Block-wide sum of two floats, then one double atomicAdd per block.
+template <int NT>
+__device__ inline void block_add2f(float a, float b, double* acc) {
+  __shared__ float sa[NT / 32], sb[NT / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) {
+    sa[w] = a;
+    sb[w] = b;
+  }
+  __syncthreads();
+  if (w == 0) {
+    a = (l < NT / 32) ? sa[l] : 0.0f;
+    b = (l < NT / 32) ? sb[l] : 0.0f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if (l == 0 && acc) {
+      atomicAdd(acc, (double)a);
+      atomicAdd(acc + 1, (double)b);
+    }
+  }
+}
+
 // Block-wide sum of two doubles, then one atomicAdd per block into acc[0..1].
 template <int NT>
 __device__ inline void block_add2(double a, double b, double* acc) {
@@ -167,9 +363,13 @@ void prof_mark_end(int family, cudaStream_t s);
 // Output layout is transposed: point index i*nlines + l.
 // `nbatch` independent arrays: input b at in + b*nlines*nin, results at batch b
 // of the epilogue (output batch stride nout*nlines for EPI_RAW).
+// FP32 only: zprev (optional, [nbatch][nout*nlines]) receives this pass's
+// result; with use_prev = 1 its previous content is used as the shift of the
+// log-sum-exp (see k_grid.cu).
 cudaError_t launch_grid_pass(int prec, const double* in, const double* logw, int in_is_pot,
                              int nlines, int nin, const void* yi, int nout, const void* xo,
-                             double eps, int nbatch, const Epilogue& epi, cudaStream_t s);
+                             double eps, int nbatch, const Epilogue& epi, cudaStream_t s,
+                             float* zprev, int use_prev, double* zero_acc = nullptr);
 
 // Row-wise log-domain Gibbs operator for dense costs and point clouds:
 //   z_i = log sum_j exp(L_j - C_ij / eps),  L_j = W_j/eps + logw_j
