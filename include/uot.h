@@ -181,6 +181,35 @@ uot_status uot_gibbs_log(const uot_geom* g, const void* W, const void* w, double
                          int transpose, int precision, void* out, void* stream);
 
 /*
+ * uot_gibbs_log_noalloc -- uot_gibbs_log without any device allocation.
+ *
+ * The paper has no counterpart: this is a deployment variant for callers that
+ * cannot allocate device memory (inside a CUDA stream capture that must stay
+ * free of allocation nodes, under a foreign allocator that owns all device
+ * memory, or in latency-critical loops where an allocation may block).
+ * Arguments, layout and result are those of uot_gibbs_log; the caller still
+ * provides W, w and out.  Temporary buffers come from one fixed device array
+ * of UOT_NOALLOC_SCRATCH_BYTES bytes inside the library, which every GPU that
+ * loads the library holds until the process exits.
+ *  - Grid and point-cloud geometries only (UOT_EUNSUPPORTED for dense costs).
+ *  - A problem whose scratch would exceed UOT_NOALLOC_SCRATCH_BYTES is
+ *    rejected with UOT_EINVAL and a message in uot_last_error().  A 2-D grid
+ *    needs about 40 bytes per point of its larger side, so grids of up to
+ *    about 100,000 points per side (e.g. 256 x 256) fit.
+ *  - The first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture on the device.
+ *  - All calls share the array and it keeps the last call's contents: calls
+ *    whose work overlaps on the GPU (different streams, or several host
+ *    threads) race and corrupt each other's results.  Serialise them.
+ *  - No cudaMalloc, cudaMallocAsync, cudaFree or allocating library routine
+ *    is called.
+ */
+#define UOT_NOALLOC_SCRATCH_BYTES (4u << 20)
+uot_status uot_gibbs_log_noalloc(const uot_geom* g, const void* W, const void* w, double eps,
+                                 int transpose, int precision, void* out, void* stream);
+
+/*
  * uot_apply_plan -- apply the plan R_ij = exp((U_i + V_j - C_ij)/eps) to
  * nonnegative functions (Sec. 4.2 projections; barycentric projection, Sec. 5.1):
  *   transpose = 0: out[i*ncols + c] = sum_j R_ij dy_j f[j*ncols + c]   (f [m*ncols])

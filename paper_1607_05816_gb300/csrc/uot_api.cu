@@ -448,13 +448,23 @@ uot_status check_geom(const uot_geom* g) {
 class Scratch {
  public:
   explicit Scratch(cudaStream_t s) : s_(s) {}
+  // Carve from caller-provided device memory of `capacity` bytes instead of
+  // allocating (used by the no-allocation entry point).
+  Scratch(cudaStream_t s, char* fixed_base, size_t capacity)
+      : s_(s), fixed_(fixed_base), capacity_(capacity) {}
   ~Scratch() {
-    if (base_) cudaFreeAsync(base_, s_);
+    if (base_ && !fixed_) cudaFreeAsync(base_, s_);
   }
   template <typename T>
   void reserve(size_t count) { need_ += round(count * sizeof(T)); }
+  size_t needed() const { return need_; }
   cudaError_t allocate() {
     if (need_ == 0) return cudaSuccess;
+    if (fixed_) {
+      if (need_ > capacity_) return cudaErrorMemoryAllocation;
+      base_ = fixed_;
+      return cudaSuccess;
+    }
     return cudaMallocAsync((void**)&base_, need_, s_);
   }
   template <typename T>
@@ -474,6 +484,8 @@ class Scratch {
  private:
   static size_t round(size_t b) { return (b + 255) & ~(size_t)255; }
   cudaStream_t s_;
+  char* fixed_ = nullptr;
+  size_t capacity_ = 0;
   char* base_ = nullptr;
   size_t need_ = 0, off_ = 0;
   bool overflow_ = false;
@@ -985,6 +997,101 @@ uot_status uot_gibbs_log(const uot_geom* g, const void* W, const void* w, double
   double* logw = sc.take<double>(nin);
   double* od = sc.take<double>(nout);
   UOT_SCRATCH_OK(sc);
+  UOT_CK(to_f64(precision, W, nin, Wd, s));
+  UOT_CK(to_log(precision, w, nin, logw, s));
+  Epilogue e;
+  memset(&e, 0, sizeof(e));
+  e.mode = EPI_SCALE;
+  set_eps(e, eps);
+  e.out = od;
+  UOT_CK(G.apply(transpose ? 1 : 0, Wd, logw, eps, e, s));
+  UOT_CK(from_f64(precision, od, nout, out, s));
+  return UOT_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// No-allocation variant of uot_gibbs_log.
+//
+// Some callers cannot allocate device memory at all: code running inside a
+// CUDA stream capture that must not add allocation nodes, processes whose
+// device memory is fully owned by another allocator, or real-time loops where
+// an allocation can block.  For them the operator's scratch lives in one
+// file-scope device array of fixed size that every GPU loading this library
+// holds until the process exits.  In host code the array's name is only a
+// host-side stand-in, so its device address is looked up once per device with
+// cudaGetSymbolAddress (with that device current) and passed to the kernels.
+// ---------------------------------------------------------------------------
+namespace uot {
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = (size_t)UOT_NOALLOC_SCRATCH_BYTES;
+static __device__ __align__(256) char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+char* g_noalloc_addr[kMaxDevices] = {nullptr};
+
+// Device address of g_noalloc_scratch on the current device (set up on the
+// first call per device).
+cudaError_t noalloc_scratch(char** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_addr[dev] = (char*)p;
+  }
+  *out = g_noalloc_addr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace uot
+
+extern "C" {
+
+uot_status uot_gibbs_log_noalloc(const uot_geom* g, const void* W, const void* w, double eps,
+                                 int transpose, int precision, void* out, void* stream) {
+  clear_stale_error();
+  uot_status st = check_geom(g);
+  if (st != UOT_OK) return st;
+  if (!W || !w || !out || !(eps > 0.0) || !prec_ok(precision)) return UOT_EINVAL;
+  if (g->kind == UOT_GEOM_DENSE) {
+    g_last_error = "uot_gibbs_log_noalloc: dense cost matrices are not supported (grid and points only)";
+    return UOT_EUNSUPPORTED;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  char* base = nullptr;
+  UOT_CK(noalloc_scratch(&base));
+  const int64_t nin = transpose ? g->n : g->m, nout = transpose ? g->m : g->n;
+  Scratch sc(s, base, kNoAllocScratchBytes);
+  Gibbs G;
+  G.g = *g;
+  G.prec = precision;
+  G.plan(sc, 1);
+  sc.reserve<double>(nin);
+  sc.reserve<double>(nin);
+  sc.reserve<double>(nout);
+  if (sc.needed() > kNoAllocScratchBytes) {
+    g_last_error = "uot_gibbs_log_noalloc: problem needs " + std::to_string(sc.needed()) +
+                   " bytes of scratch, more than the fixed " +
+                   std::to_string(kNoAllocScratchBytes) + " bytes (UOT_NOALLOC_SCRATCH_BYTES)";
+    return UOT_EINVAL;
+  }
+  UOT_CK(sc.allocate());
+  UOT_CK(G.take(sc, s));
+  double* Wd = sc.take<double>(nin);
+  double* logw = sc.take<double>(nin);
+  double* od = sc.take<double>(nout);
+  UOT_SCRATCH_OK(sc);
+  // Every buffer carved here is fully written before it is read, so nothing
+  // left by an earlier call needs clearing.
   UOT_CK(to_f64(precision, W, nin, Wd, s));
   UOT_CK(to_log(precision, w, nin, logw, s));
   Epilogue e;

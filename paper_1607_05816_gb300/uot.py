@@ -72,6 +72,8 @@ _SIGS = {
                             C.c_void_p, C.POINTER(CResult), C.c_void_p]),
     "uot_gibbs_log": (C.c_int, [C.POINTER(CGeom), C.c_void_p, C.c_void_p, C.c_double, C.c_int,
                                 C.c_int, C.c_void_p, C.c_void_p]),
+    "uot_gibbs_log_noalloc": (C.c_int, [C.POINTER(CGeom), C.c_void_p, C.c_void_p, C.c_double,
+                                        C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
     "uot_apply_plan": (C.c_int, [C.POINTER(CGeom), C.c_void_p, C.c_void_p, C.c_double, C.c_void_p,
                                  C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p,
                                  C.c_void_p]),
@@ -290,6 +292,21 @@ def gibbs_log(geom: Geometry, W, w, eps, transpose=False, precision=F64, out=Non
     _check(lib.uot_gibbs_log(C.byref(g), _ptr(W, dt, "W"), _ptr(w, dt, "w"), float(eps),
                              int(bool(transpose)), precision, _ptr(out, dt, "out"), _stream()),
            "uot_gibbs_log")
+    return out
+
+
+def gibbs_log_noalloc(geom: Geometry, W, w, eps, transpose=False, precision=F64, out=None):
+    """uot_gibbs_log_noalloc: same result as gibbs_log, computed with the
+    library's fixed scratch array instead of device allocations (for callers
+    that cannot allocate; see include/uot.h).  `out` may be preallocated."""
+    lib = load()
+    dt = _dtype(precision)
+    nout = geom.m if transpose else geom.n
+    out = torch.empty(nout, dtype=dt, device=W.device) if out is None else out
+    g = geom.c(precision)
+    _check(lib.uot_gibbs_log_noalloc(C.byref(g), _ptr(W, dt, "W"), _ptr(w, dt, "w"), float(eps),
+                                     int(bool(transpose)), precision, _ptr(out, dt, "out"),
+                                     _stream()), "uot_gibbs_log_noalloc")
     return out
 
 
