@@ -49,6 +49,10 @@ SM_COUNT, MUFU_PER_CLK, SM_MAX_MHZ = 152, 32, 2070.0
 MUFU_PEAK_GEXP = SM_COUNT * MUFU_PER_CLK * SM_MAX_MHZ * 1e6 / 1e9
 
 WORKLOAD = "grid2d-256x256-kl0.5-epsscale1e-1to1e-3-tol1e-6"
+# dram__bytes_read.sum + dram__bytes_write.sum of one grid_pass_f32 launch on
+# this workload (profiles/grid_pass_f32_grid256.md); None once the kernel
+# changes after that capture.
+GRID_PASS_F32_TRAFFIC_BYTES = 903936
 
 
 def config_dict(extra=None):
@@ -277,7 +281,8 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clocks,
         "roofline": {"bound": "alu", "kernel": "grid_pass_f32" if prec == uot.F32 else "grid_pass_f64",
                      "achieved": achieved, "peak": MUFU_PEAK_GEXP, "unit": "Gexp2/s",
-                     "frac": achieved / MUFU_PEAK_GEXP, "traffic": None,
+                     "frac": achieved / MUFU_PEAK_GEXP,
+                     "traffic": GRID_PASS_F32_TRAFFIC_BYTES if prec == uot.F32 else None,
                      "launches_per_step": launches_per_step,
                      "pipelined_launch_us": eff_launch_ms * 1e3,
                      "isolated_launch_us": avg_kern_ms * 1e3,
