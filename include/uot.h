@@ -236,6 +236,39 @@ uot_status uot_objective(const uot_geom* g, const void* p, const void* dx, const
                          const void* dy, const uot_div* F1, const uot_div* F2, double eps,
                          const void* U, const void* V, int precision, double* out, void* stream);
 
+/* One problem of a batch for uot_solve_batch. */
+typedef struct {
+  int n, m;      /* points on each side, 1..3072 */
+  uot_div F1;    /* penalty on the first marginal */
+  uot_div F2;    /* penalty on the second marginal */
+} uot_batch_problem;
+
+/*
+ * uot_solve_batch -- many independent unbalanced OT problems between point
+ * clouds (cost |x - y|^2, computed on the fly) solved in one persistent launch.
+ * Each problem runs the iteration of uot_solve (eq. S, Sec. 3.3; log form of
+ * Sec. 4.3; eps-scaling of Sec. 4.4) to its own tolerance; problems of uneven
+ * sizes are taken from a device work queue, largest first.
+ *  nprob       number of problems >= 1
+ *  probs       host [nprob] sizes and penalties
+ *  d           dimension of the points, 1..3
+ *  x, dx, p    packed X sides: problem k occupies points [Xk, Xk + n_k) with
+ *              Xk = n_0 + ... + n_{k-1}; x is [sum n][d] row-major, dx and p [sum n]
+ *  y, dy, q    packed Y sides likewise
+ *  o           options: precision must be UOT_F32; eps, eps_start, eps_stages,
+ *              iters_per_stage, max_iter, tol, check_every as in uot_solve;
+ *              plain_scaling, U0 and V0 must be 0/NULL
+ *  U, V        [sum n], [sum m] outputs (float), packed like the inputs
+ *  iters       host [nprob] iterations at the final eps per problem, or NULL
+ *  errs        host [nprob] last measured marginal violation per problem, or NULL
+ * Returns UOT_OK if every problem reached tol (or tol == 0), UOT_NOT_CONVERGED
+ * if some hit the cap.  Synchronises `stream`.
+ */
+uot_status uot_solve_batch(int nprob, const uot_batch_problem* probs, int d, const void* x,
+                           const void* p, const void* dx, const void* y, const void* q,
+                           const void* dy, const uot_opts* o, void* U, void* V, int* iters,
+                           double* errs, uot_result* res, void* stream);
+
 /* Barycenter divergence for uot_barycenter (Table 2 rows). */
 typedef enum { UOT_BARY_KL = 1, UOT_BARY_EQ = 0 } uot_bary_kind;
 

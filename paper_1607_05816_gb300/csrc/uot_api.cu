@@ -16,6 +16,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <atomic>
 #include <mutex>
 #include <string>
@@ -1249,6 +1250,187 @@ uot_status uot_objective(const uot_geom* g, const void* p, const void* dx, const
   out[2] = (h[0] + h[1] + h[2]) + (h[8] + h[9] + h[10]);
   out[3] = (h[6] > 0.0) ? h[5] / h[6] : 0.0;
   return UOT_OK;
+}
+
+uot_status uot_solve_batch(int nprob, const uot_batch_problem* probs, int d, const void* x,
+                           const void* p, const void* dx, const void* y, const void* q,
+                           const void* dy, const uot_opts* o, void* Uout, void* Vout, int* iters,
+                           double* errs, uot_result* res, void* stream) {
+  clear_stale_error();
+  uot_status st = check_opts(o);
+  if (st != UOT_OK) return st;
+  if (nprob < 1 || !probs || d < 1 || d > 3 || !x || !p || !dx || !y || !q || !dy || !Uout || !Vout)
+    return UOT_EINVAL;
+  if (o->precision != UOT_F32 || o->plain_scaling || o->U0 || o->V0) return UOT_EUNSUPPORTED;
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<int> hn(nprob), hm(nprob), order(nprob);
+  std::vector<int64_t> hxo(nprob), hyo(nprob);
+  int64_t N = 0, M = 0;
+  int nmax = 0, mmax = 0;
+  for (int k = 0; k < nprob; ++k) {
+    const uot_batch_problem& pr = probs[k];
+    if (pr.n < 1 || pr.m < 1 || pr.n > 3072 || pr.m > 3072) return UOT_EINVAL;
+    if (!div_ok(&pr.F1) || !div_ok(&pr.F2)) return UOT_EINVAL;
+    hn[k] = pr.n;
+    hm[k] = pr.m;
+    hxo[k] = N;
+    hyo[k] = M;
+    N += pr.n;
+    M += pr.m;
+    nmax = pr.n > nmax ? pr.n : nmax;
+    mmax = pr.m > mmax ? pr.m : mmax;
+    order[k] = k;
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return (int64_t)hn[a] * hm[a] > (int64_t)hn[b] * hm[b];
+  });
+  const std::vector<Stage> stages = eps_schedule(*o);
+  const int nstage = (int)stages.size();
+  std::vector<double> eps_list;
+  for (const Stage& sg : stages) eps_list.push_back(sg.eps);
+  eps_list.push_back(o->eps);
+  std::vector<DivFF> divs((size_t)(nstage + 1) * nprob * 2);
+  std::vector<float2> heps(nstage + 1), hieps(nstage + 1);
+  std::vector<float> hk2(nstage + 1);
+  for (int sidx = 0; sidx <= nstage; ++sidx) {
+    const double e = eps_list[sidx];
+    heps[sidx] = ff2(ff_make(e));
+    hieps[sidx] = ff2(ff_make(1.0 / e));
+    hk2[sidx] = (float)((double)kLog2e / e);
+    for (int k = 0; k < nprob; ++k) {
+      divs[((size_t)sidx * nprob + k) * 2] = make_div_ff(make_div(probs[k].F1), e);
+      divs[((size_t)sidx * nprob + k) * 2 + 1] = make_div_ff(make_div(probs[k].F2), e);
+    }
+  }
+  int dev = 0, sms = 0;
+  UOT_CK(cudaGetDevice(&dev));
+  UOT_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int per_sm = batch_ctas_per_sm(nmax, mmax);
+  if (per_sm < 1) {
+    g_last_error = "uot_solve_batch: problem sizes do not fit in shared memory";
+    return UOT_EUNSUPPORTED;
+  }
+
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  UOT_CK(cudaEventCreate(&ev0));
+  UOT_CK(cudaEventCreate(&ev1));
+  struct EvGuard {
+    cudaEvent_t a, b;
+    ~EvGuard() {
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+    }
+  } evg{ev0, ev1};
+  UOT_CK(cudaEventRecord(ev0, s));
+
+  Scratch sc(s);
+  sc.reserve<int>(nprob);      // order
+  sc.reserve<int>(nprob);      // n
+  sc.reserve<int>(nprob);      // m
+  sc.reserve<int64_t>(nprob);  // xoff
+  sc.reserve<int64_t>(nprob);  // yoff
+  sc.reserve<DivFF>(divs.size());
+  sc.reserve<float2>(nstage + 1);
+  sc.reserve<float2>(nstage + 1);
+  sc.reserve<float>(nstage + 1);
+  sc.reserve<double>(N);  // logp
+  sc.reserve<double>(N);  // logdx
+  sc.reserve<double>(M);  // logq
+  sc.reserve<double>(M);  // logdy
+  sc.reserve<int>(nprob);    // iters
+  sc.reserve<float>(nprob);  // errs
+  sc.reserve<int>(1);        // work counter
+  UOT_CK(sc.allocate());
+  int* d_order = sc.take<int>(nprob);
+  int* d_n = sc.take<int>(nprob);
+  int* d_m = sc.take<int>(nprob);
+  int64_t* d_xo = sc.take<int64_t>(nprob);
+  int64_t* d_yo = sc.take<int64_t>(nprob);
+  DivFF* d_divs = sc.take<DivFF>(divs.size());
+  float2* d_eps = sc.take<float2>(nstage + 1);
+  float2* d_ieps = sc.take<float2>(nstage + 1);
+  float* d_k2 = sc.take<float>(nstage + 1);
+  double* d_logp = sc.take<double>(N);
+  double* d_logdx = sc.take<double>(N);
+  double* d_logq = sc.take<double>(M);
+  double* d_logdy = sc.take<double>(M);
+  int* d_iters = sc.take<int>(nprob);
+  float* d_errs = sc.take<float>(nprob);
+  int* d_next = sc.take<int>(1);
+  UOT_SCRATCH_OK(sc);
+  UOT_CK(cudaMemcpyAsync(d_order, order.data(), nprob * sizeof(int), cudaMemcpyHostToDevice, s));
+  UOT_CK(cudaMemcpyAsync(d_n, hn.data(), nprob * sizeof(int), cudaMemcpyHostToDevice, s));
+  UOT_CK(cudaMemcpyAsync(d_m, hm.data(), nprob * sizeof(int), cudaMemcpyHostToDevice, s));
+  UOT_CK(cudaMemcpyAsync(d_xo, hxo.data(), nprob * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  UOT_CK(cudaMemcpyAsync(d_yo, hyo.data(), nprob * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  UOT_CK(cudaMemcpyAsync(d_divs, divs.data(), divs.size() * sizeof(DivFF), cudaMemcpyHostToDevice, s));
+  UOT_CK(cudaMemcpyAsync(d_eps, heps.data(), heps.size() * sizeof(float2), cudaMemcpyHostToDevice, s));
+  UOT_CK(cudaMemcpyAsync(d_ieps, hieps.data(), hieps.size() * sizeof(float2), cudaMemcpyHostToDevice, s));
+  UOT_CK(cudaMemcpyAsync(d_k2, hk2.data(), hk2.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+  UOT_CK(cudaMemsetAsync(d_next, 0, sizeof(int), s));
+  UOT_CK(to_log(UOT_F32, p, N, d_logp, s));
+  UOT_CK(to_log(UOT_F32, dx, N, d_logdx, s));
+  UOT_CK(to_log(UOT_F32, q, M, d_logq, s));
+  UOT_CK(to_log(UOT_F32, dy, M, d_logdy, s));
+  BatchArgs a;
+  a.nprob = nprob;
+  a.d = d;
+  a.nstage = nstage;
+  a.iters_per_stage = o->iters_per_stage;
+  a.max_iter = o->max_iter;
+  a.check_every = o->check_every > 0 ? o->check_every : 1;
+  a.nmax = nmax;
+  a.mmax = mmax;
+  a.tol = (float)o->tol;
+  a.order = d_order;
+  a.n = d_n;
+  a.m = d_m;
+  a.xoff = d_xo;
+  a.yoff = d_yo;
+  a.x = (const float*)x;
+  a.y = (const float*)y;
+  a.logp = reinterpret_cast<const float2*>(d_logp);
+  a.logdx = reinterpret_cast<const float2*>(d_logdx);
+  a.logq = reinterpret_cast<const float2*>(d_logq);
+  a.logdy = reinterpret_cast<const float2*>(d_logdy);
+  a.divs = d_divs;
+  a.eps_ff = d_eps;
+  a.inv_eps_ff = d_ieps;
+  a.k2 = d_k2;
+  a.Uout = (float*)Uout;
+  a.Vout = (float*)Vout;
+  a.iters_out = d_iters;
+  a.err_out = d_errs;
+  a.next = d_next;
+  const int grid = (int)std::min<int64_t>(nprob, (int64_t)sms * per_sm);
+  UOT_CK(launch_batch(a, grid, s));
+  UOT_CK(cudaEventRecord(ev1, s));
+  std::vector<int> it_h(nprob);
+  std::vector<float> er_h(nprob);
+  UOT_CK(cudaMemcpyAsync(it_h.data(), d_iters, nprob * sizeof(int), cudaMemcpyDeviceToHost, s));
+  UOT_CK(cudaMemcpyAsync(er_h.data(), d_errs, nprob * sizeof(float), cudaMemcpyDeviceToHost, s));
+  UOT_CK(cudaStreamSynchronize(s));
+  float ms = 0.f;
+  UOT_CK(cudaEventElapsedTime(&ms, ev0, ev1));
+  bool all_conv = true;
+  int total = 0;
+  double worst = 0.0;
+  for (int k = 0; k < nprob; ++k) {
+    if (iters) iters[k] = it_h[k];
+    if (errs) errs[k] = er_h[k];
+    total += it_h[k];
+    worst = std::max(worst, (double)er_h[k]);
+    if (o->tol > 0.0 && !(er_h[k] <= o->tol)) all_conv = false;
+  }
+  const uot_status out = all_conv ? UOT_OK : UOT_NOT_CONVERGED;
+  if (res) {
+    res->iters = total;
+    res->total_iters = total + nprob * nstage * o->iters_per_stage;
+    res->marg_err = worst;
+    res->ms = ms;
+    res->status = out;
+  }
+  return out;
 }
 
 uot_status uot_barycenter(const uot_geom* g, int Kmeas, const double* alpha, const void* P,

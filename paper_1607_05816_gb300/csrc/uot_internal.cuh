@@ -385,6 +385,35 @@ cudaError_t launch_rows(int prec, const RowsGeom& g, int nrows, int nin, const d
                         const double* logw, double eps, void* scratch_L, const Epilogue& epi,
                         cudaStream_t s);
 
+// Persistent batched solver for many point-cloud problems (k_batch.cu).
+struct BatchArgs {
+  int nprob, d, nstage, iters_per_stage, max_iter, check_every, nmax, mmax;
+  float tol;
+  const int* order;
+  const int* n;
+  const int* m;
+  const int64_t* xoff;
+  const int64_t* yoff;
+  const float* x;
+  const float* y;
+  const float2* logp;
+  const float2* logdx;
+  const float2* logq;
+  const float2* logdy;
+  const DivFF* divs;
+  const float2* eps_ff;
+  const float2* inv_eps_ff;
+  const float* k2;
+  float* Uout;
+  float* Vout;
+  int* iters_out;
+  float* err_out;
+  int* next;
+};
+size_t batch_smem_bytes(int nmax, int mmax);
+int batch_ctas_per_sm(int nmax, int mmax);
+cudaError_t launch_batch(const BatchArgs& a, int grid, cudaStream_t s);
+
 // Algorithm 1 (non-log) half-step on a stored FP64 kernel:
 //   a_i = proxdiv_F(sum_j K_ij b_j w_j, eps), also the violation terms.
 cudaError_t launch_alg1_half(const double* K, int nrows, int nin, const double* b,

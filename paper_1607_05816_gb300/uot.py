@@ -54,6 +54,10 @@ class COpts(C.Structure):
                 ("U0", C.c_void_p), ("V0", C.c_void_p)]
 
 
+class CBatchProblem(C.Structure):
+    _fields_ = [("n", C.c_int), ("m", C.c_int), ("F1", CDiv), ("F2", CDiv)]
+
+
 class CResult(C.Structure):
     _fields_ = [("iters", C.c_int), ("total_iters", C.c_int), ("marg_err", C.c_double),
                 ("ms", C.c_double), ("status", C.c_int)]
@@ -80,6 +84,10 @@ _SIGS = {
     "uot_objective": (C.c_int, [C.POINTER(CGeom), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                 C.POINTER(CDiv), C.POINTER(CDiv), C.c_double, C.c_void_p,
                                 C.c_void_p, C.c_int, C.POINTER(C.c_double), C.c_void_p]),
+    "uot_solve_batch": (C.c_int, [C.c_int, C.POINTER(CBatchProblem), C.c_int, C.c_void_p,
+                                  C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                  C.POINTER(COpts), C.c_void_p, C.c_void_p, C.POINTER(C.c_int),
+                                  C.POINTER(C.c_double), C.POINTER(CResult), C.c_void_p]),
     "uot_barycenter": (C.c_int, [C.POINTER(CGeom), C.c_int, C.POINTER(C.c_double), C.c_void_p,
                                  C.c_void_p, C.c_void_p, C.POINTER(CDiv), C.c_double, C.c_int,
                                  C.POINTER(COpts), C.c_void_p, C.c_void_p, C.c_void_p,
@@ -360,3 +368,32 @@ def barycenter(geom: Geometry, alpha, P, dx, dy, F1: Div, lam, eps, *, kind=BARY
     _check(st, "uot_barycenter")
     return logh, U, V, dict(iters=r.iters, total_iters=r.total_iters, marg_err=r.marg_err,
                             ms=r.ms, status=STATUS[st])
+
+
+def solve_batch(sizes, divs, d, x, p, dx, y, q, dy, eps, *, max_iter=1000, tol=0.0,
+                check_every=10, eps_start=None, eps_stages=10, iters_per_stage=100, U=None, V=None):
+    """uot_solve_batch (FP32): sizes = [(n_k, m_k)], divs = [(F1_k, F2_k)]; x, p, dx
+    packed over the X sides ([sum n, d], [sum n], [sum n]) and y, q, dy over the
+    Y sides.  Returns (U, V, iters [nprob], errs [nprob], result dict)."""
+    lib = load()
+    nprob = len(sizes)
+    arr = (CBatchProblem * nprob)()
+    for k, ((n, m), (F1, F2)) in enumerate(zip(sizes, divs)):
+        arr[k] = CBatchProblem(int(n), int(m), F1.c(), F2.c())
+    N = sum(n for n, _ in sizes)
+    M = sum(m for _, m in sizes)
+    dt = torch.float32
+    U = torch.empty(N, dtype=dt, device=x.device) if U is None else U
+    V = torch.empty(M, dtype=dt, device=x.device) if V is None else V
+    iters = (C.c_int * nprob)()
+    errs = (C.c_double * nprob)()
+    o = COpts(F32, float(eps), float(eps_start) if eps_start else 0.0, int(eps_stages),
+              int(iters_per_stage), int(max_iter), float(tol), int(check_every), 0, None, None)
+    r = CResult()
+    st = lib.uot_solve_batch(nprob, arr, int(d), _ptr(x, dt, "x"), _ptr(p, dt, "p"),
+                             _ptr(dx, dt, "dx"), _ptr(y, dt, "y"), _ptr(q, dt, "q"),
+                             _ptr(dy, dt, "dy"), C.byref(o), _ptr(U, dt, "U"), _ptr(V, dt, "V"),
+                             iters, errs, C.byref(r), _stream())
+    _check(st, "uot_solve_batch")
+    return U, V, list(iters), list(errs), dict(iters=r.iters, total_iters=r.total_iters,
+                                               marg_err=r.marg_err, ms=r.ms, status=STATUS[st])

@@ -1,0 +1,93 @@
+"""Batched persistent solver (uot_solve_batch) against the FP64 oracle,
+problem by problem, on uneven point-cloud problems."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_1607_05816_gb300 import synth
+from paper_1607_05816_gb300 import uot as U
+
+pytestmark = [pytest.mark.gpu, pytest.mark.filterwarnings("ignore::RuntimeWarning")]
+
+
+def packed(probs):
+    f32 = lambda a: np.asarray(a, dtype=np.float32)
+    cat = lambda key: np.concatenate([f32(pr[key]) for pr in probs])
+    dev = lambda a: torch.as_tensor(a, device="cuda")
+    return (dev(cat("x")), dev(cat("p")), dev(cat("dx")), dev(cat("y")), dev(cat("q")), dev(cat("dy")))
+
+
+def rounded(a):
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+def rel_err(got, want):
+    f = np.isfinite(want)
+    assert np.array_equal(np.isneginf(got), np.isneginf(want))
+    return np.max(np.abs(got[f] - want[f])) / max(1.0, np.max(np.abs(want[f])))
+
+
+def make_divs(probs, kinds):
+    out_u, out_o = [], []
+    for k, pr in enumerate(probs):
+        lam = pr["lam"]
+        if kinds[k % len(kinds)] == "kl":
+            out_u.append((U.KL(lam), U.KL(lam)))
+            out_o.append((O.KL(lam), O.KL(lam)))
+        else:
+            out_u.append((U.TV(lam), U.KL(lam)))
+            out_o.append((O.TV(lam), O.KL(lam)))
+    return out_u, out_o
+
+
+@pytest.mark.parametrize("d,stages", [(2, 0), (3, 4), (1, 0)])
+def test_batch_parity_fixed_iterations(d, stages):
+    probs = synth.batch_points(nprob=14, size=(5, 300), d=d, seed=40 + d)
+    sizes = [(len(pr["x"]), len(pr["y"])) for pr in probs]
+    udivs, odivs = make_divs(probs, ["kl", "tv"])
+    x, p, dx, y, q, dy = packed(probs)
+    eps, iters = 0.02, 25
+    Ug, Vg, it, errs, info = U.solve_batch(sizes, udivs, d, x, p, dx, y, q, dy, eps, max_iter=iters,
+                                           eps_start=0.2 if stages else None, eps_stages=stages,
+                                           iters_per_stage=5)
+    Ug = Ug.double().cpu().numpy()
+    Vg = Vg.double().cpu().numpy()
+    xo = yo = 0
+    for k, pr in enumerate(probs):
+        n, m = sizes[k]
+        og = O.Geometry("points", x=rounded(pr["x"]), y=rounded(pr["y"]))
+        r = O.solve_log(og, rounded(pr["dx"]), rounded(pr["dy"]), rounded(pr["p"]), rounded(pr["q"]),
+                        *odivs[k], eps, max_iter=iters, eps_start=0.2 if stages else None,
+                        stages=stages, iters_per_stage=5)
+        assert it[k] == iters
+        assert rel_err(Ug[xo:xo + n], r["U"]) <= 1e-5, k
+        assert rel_err(Vg[yo:yo + m], r["V"]) <= 1e-5, k
+        xo += n
+        yo += m
+
+
+def test_batch_converges_to_tolerance():
+    """Every problem stops with its violation <= tol, and the oracle, evaluating
+    the returned potentials in FP64, agrees that they are that close to a
+    fixed point."""
+    probs = synth.batch_points(nprob=40, size=(64, 700), d=2, seed=77)
+    sizes = [(len(pr["x"]), len(pr["y"])) for pr in probs]
+    udivs, odivs = make_divs(probs, ["kl"])
+    x, p, dx, y, q, dy = packed(probs)
+    eps, tol = 0.02, 1e-6
+    Ug, Vg, it, errs, info = U.solve_batch(sizes, udivs, 2, x, p, dx, y, q, dy, eps, max_iter=20000,
+                                           tol=tol, check_every=10)
+    assert info["status"] == "UOT_OK"
+    assert max(errs) <= tol
+    Ug = Ug.double().cpu().numpy()
+    Vg = Vg.double().cpu().numpy()
+    xo = yo = 0
+    for k, pr in enumerate(probs[:6]):
+        n, m = sizes[k]
+        og = O.Geometry("points", x=rounded(pr["x"]), y=rounded(pr["y"]))
+        v = O.marginal_violation(og, rounded(pr["dx"]), rounded(pr["dy"]), rounded(pr["p"]),
+                                 rounded(pr["q"]), *odivs[k], eps, Ug[xo:xo + n], Vg[yo:yo + m])
+        assert v <= 20 * tol, (k, v)
+        xo += n
+        yo += m
