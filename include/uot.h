@@ -172,6 +172,18 @@ uot_status uot_solve(const uot_geom* g, const void* p, const void* dx, const voi
                      void* U, void* V, uot_result* res, void* stream);
 
 /*
+ * uot_solve_many -- `batch` independent problems that share the geometry, the
+ * reference weights dx, dy, eps and the penalties F1, F2 but not the
+ * densities: p and U are [batch][n], q and V are [batch][m] (row-major).  For
+ * grids every Gibbs-operator pass treats all problems in one launch.  Options
+ * as in uot_solve (plain_scaling unsupported); the iteration runs until every
+ * problem's marginal violation is <= tol, and res->marg_err is the largest.
+ */
+uot_status uot_solve_many(const uot_geom* g, int batch, const void* p, const void* dx,
+                          const void* q, const void* dy, const uot_div* F1, const uot_div* F2,
+                          const uot_opts* o, void* U, void* V, uot_result* res, void* stream);
+
+/*
  * uot_gibbs_log -- the log-domain Gibbs operator alone (Sec. 4.2, 4.3):
  *   transpose = 0: out_i = eps log sum_j exp((W_j - C_ij)/eps) w_j   (out [n], W,w [m])
  *   transpose = 1: out_j = eps log sum_i exp((W_i - C_ij)/eps) w_i   (out [m], W,w [n])
@@ -295,6 +307,43 @@ uot_status uot_barycenter(const uot_geom* g, int Kmeas, const double* alpha, con
                           const void* dx, const void* dy, const uot_div* F1, double lambda,
                           int bary_kind, const uot_opts* o, void* logh, void* U, void* V,
                           uot_result* res, void* stream);
+
+/*
+ * Learned warm start (not in the paper).  A small dilated convolutional
+ * network maps (log p, log q, log eps, log lambda) on a grid to initial
+ * potentials (U0, V0) that replace b = 1 of Algorithm 1; the plain iteration
+ * remains the judge of the result.  These are its training and inference
+ * kernels; all arrays are FP32 device arrays, activations [N][C][H][W],
+ * weights [Cout][Cin][3][3], biases [Cout].
+ *
+ * uot_conv2d_forward: y = act(b + conv3x3_dilated(x, w)), zero padding;
+ *   leaky = 1: act(v) = v (v >= 0), 0.1 v (v < 0); leaky = 0: identity.
+ * uot_conv2d_backward: given dy = dLoss/dy of the layer's output y (the
+ *   post-activation values stored by the forward pass), writes dx (if not
+ *   NULL), dw and db (both overwritten).
+ * uot_adam_step: one Adam update of n parameters (step counts from 1).
+ * uot_mse_grad: grad = 2 (pred - target)/n and *loss_dev = mean (pred - target)^2
+ *   (loss_dev is a device double).
+ * uot_scale_instances: x[n][...] *= scale[n] for n < N, per_instance values
+ *   each (the network works with potentials divided by lambda).
+ * uot_warmstart_features: out [N][4][H][W] = (max(log p, -30), max(log q, -30),
+ *   log eps, log lambda) / 4, from p, q [N][H][W] and per-instance log_eps,
+ *   log_lam [N].
+ */
+uot_status uot_conv2d_forward(const float* x, const float* w, const float* b, float* y, int N,
+                              int Cin, int Cout, int H, int W, int dilation, int leaky, void* stream);
+uot_status uot_conv2d_backward(const float* x, const float* w, const float* y, const float* dy,
+                               float* dx, float* dw, float* db, int N, int Cin, int Cout, int H,
+                               int W, int dilation, int leaky, void* stream);
+uot_status uot_adam_step(float* param, const float* grad, float* m, float* v, long long n,
+                         float lr, float beta1, float beta2, float eps, int step, void* stream);
+uot_status uot_mse_grad(const float* pred, const float* target, float* grad, long long n,
+                        double* loss_dev, void* stream);
+uot_status uot_scale_instances(float* x, const float* scale, int N, long long per_instance,
+                               void* stream);
+uot_status uot_warmstart_features(const float* p, const float* q, const float* log_eps,
+                                  const float* log_lam, float* out, int N, int H, int W,
+                                  void* stream);
 
 #ifdef __cplusplus
 }

@@ -109,7 +109,7 @@ struct PassArgs {
   float k2;            // log2(e)/eps
   float* zprev;        // [nbatch][nout*nlines] approximate result of the previous call, or NULL
   int use_prev;
-  double* zero_acc;    // if set, block (0,0,0) clears these two doubles (violation accumulators)
+  double* zero_acc;    // if set, the first block of each batch entry b clears zero_acc[2b..2b+1]
 };
 
 __device__ __forceinline__ ff load_L_ff(const PassArgs& a, const float2* in, int64_t idx) {
@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(kNW * 32, 4)
   }
 
   pdl_wait();
-  if (a.zero_acc && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && tid < 2) a.zero_acc[tid] = 0.0;
+  if (a.zero_acc && blockIdx.x == 0 && blockIdx.y == 0 && tid < 2) a.zero_acc[2 * bz + tid] = 0.0;
   pdl_launch_dependents();
 
   // ---- line values: one read, kept in registers when the line is short ----
@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(kNW * 32, 4)
       if (zprev) zprev[my_pt] = -INFINITY;
       epilogue_apply(epi, bz, my_pt, ff_ninf(), pre, num, den);
     }
-    if (epi.err) block_add2f<kNW * 32>(num, den, epi.err);
+    if (epi.err) block_add2f<kNW * 32>(num, den, epi.err + 2 * bz);
     return;
   }
   if (in_regs) {
@@ -343,7 +343,7 @@ __global__ void __launch_bounds__(kNW * 32, 4)
     }
     break;
   }
-  if (epi.err) block_add2f<kNW * 32>(num, den, epi.err);
+  if (epi.err) block_add2f<kNW * 32>(num, den, epi.err + 2 * bz);
 }
 
 // FP64 arithmetic throughout.
@@ -420,7 +420,7 @@ __global__ void __launch_bounds__(WARPS * 32)
       }
     }
   }
-  if (epi.err) block_add2<WARPS * 32>(num, den, epi.err);
+  if (epi.err) block_add2<WARPS * 32>(num, den, epi.err + 2 * bz);
 }
 
 }  // namespace

@@ -592,7 +592,7 @@ struct Gibbs {
           if (prec == UOT_F32) {
             za = zero_acc;
           } else {
-            cudaError_t e0 = cudaMemsetAsync(zero_acc, 0, 16, s);
+            cudaError_t e0 = cudaMemsetAsync(zero_acc, 0, 16 * (size_t)nbatch, s);
             if (e0 != cudaSuccess) return e0;
           }
         }
@@ -607,7 +607,7 @@ struct Gibbs {
       return cudaSuccess;
     }
     if (zero_acc) {
-      cudaError_t e0 = cudaMemsetAsync(zero_acc, 0, 16, s);
+      cudaError_t e0 = cudaMemsetAsync(zero_acc, 0, 16 * (size_t)nbatch, s);
       if (e0 != cudaSuccess) return e0;
     }
     RowsGeom rg;
@@ -626,6 +626,7 @@ struct Gibbs {
         if (e.out) e.out += b * e.bstride;
         if (e.logp) e.logp += b * e.bstride_p;
         if (e.pot_shift) e.pot_shift += b * e.bstride;
+        if (e.err) e.err += 2 * b;
       }
       cudaError_t err = launch_rows(prec, rg, nrows, nin, W + (int64_t)b * nin, logw, eps,
                                     Lscratch, e, s);
@@ -718,17 +719,23 @@ uot_status check_opts(const uot_opts* o) {
 // solve
 // ---------------------------------------------------------------------------
 
-uot_status solve_impl(const uot_geom* g, const void* p, const void* dx, const void* q,
+// `batch` independent problems sharing the geometry, eps and penalties: p, U
+// are [batch][n], q, V are [batch][m]; dx, dy are shared.  The iteration stops
+// when every problem's violation is <= tol (the reported error is the largest).
+uot_status solve_impl(const uot_geom* g, int batch, const void* p, const void* dx, const void* q,
                       const void* dy, const uot_div* F1, const uot_div* F2, const uot_opts* o,
                       void* Uout, void* Vout, uot_result* res, cudaStream_t s) {
   uot_status st = check_geom(g);
   if (st != UOT_OK) return st;
   if ((st = check_opts(o)) != UOT_OK) return st;
-  if (!p || !dx || !q || !dy || !Uout || !Vout || !div_ok(F1) || !div_ok(F2)) return UOT_EINVAL;
-  if (o->plain_scaling && (g->kind != UOT_GEOM_DENSE || o->precision != UOT_F64))
+  if (batch < 1 || !p || !dx || !q || !dy || !Uout || !Vout || !div_ok(F1) || !div_ok(F2))
+    return UOT_EINVAL;
+  if (o->plain_scaling && (g->kind != UOT_GEOM_DENSE || o->precision != UOT_F64 || batch != 1))
     return UOT_EUNSUPPORTED;
+  if (g->kind == UOT_GEOM_GRID && batch > 65535) return UOT_EUNSUPPORTED;
   const int prec = o->precision;
   const int64_t n = g->n, m = g->m;
+  const int64_t bn = n * batch, bm = m * batch;
   const DivParams D1 = make_div(*F1), D2 = make_div(*F2);
 
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -748,10 +755,14 @@ uot_status solve_impl(const uot_geom* g, const void* p, const void* dx, const vo
   G.g = *g;
   G.prec = prec;
   G.speculate = true;
-  G.plan(sc, 1);
-  for (int k = 0; k < 3; ++k) sc.reserve<double>(n);  // logp, logdx, U
-  for (int k = 0; k < 3; ++k) sc.reserve<double>(m);  // logq, logdy, V
-  sc.reserve<double>(8);                              // err accumulators + flag
+  G.plan(sc, batch);
+  sc.reserve<double>(bn);  // logp
+  sc.reserve<double>(n);   // logdx
+  sc.reserve<double>(bn);  // U
+  sc.reserve<double>(bm);  // logq
+  sc.reserve<double>(m);   // logdy
+  sc.reserve<double>(bm);  // V
+  sc.reserve<double>(2 * (size_t)batch + 4);  // err accumulators + flag
   if (o->plain_scaling) {
     sc.reserve<double>((size_t)n * m);  // K
     sc.reserve<double>((size_t)n * m);  // K^T
@@ -760,30 +771,31 @@ uot_status solve_impl(const uot_geom* g, const void* p, const void* dx, const vo
   }
   UOT_CK(sc.allocate());
   UOT_CK(G.take(sc, s));
-  double* logp = sc.take<double>(n);
+  double* logp = sc.take<double>(bn);
   double* logdx = sc.take<double>(n);
-  double* U = sc.take<double>(n);
-  double* logq = sc.take<double>(m);
+  double* U = sc.take<double>(bn);
+  double* logq = sc.take<double>(bm);
   double* logdy = sc.take<double>(m);
-  double* V = sc.take<double>(m);
-  double* acc = sc.take<double>(8);
-  int* flag = (int*)(acc + 4);
+  double* V = sc.take<double>(bm);
+  double* acc = sc.take<double>(2 * (size_t)batch + 4);
+  int* flag = (int*)(acc + 2 * (size_t)batch);
+  std::vector<double> acc_h(2 * (size_t)batch);
   UOT_SCRATCH_OK(sc);
-  UOT_CK(to_log(prec, p, n, logp, s));
+  UOT_CK(to_log(prec, p, bn, logp, s));
   UOT_CK(to_log(prec, dx, n, logdx, s));
-  UOT_CK(to_log(prec, q, m, logq, s));
+  UOT_CK(to_log(prec, q, bm, logq, s));
   UOT_CK(to_log(prec, dy, m, logdy, s));
   if (o->U0) {
-    UOT_CK(to_f64(prec, o->U0, n, U, s));
+    UOT_CK(to_f64(prec, o->U0, bn, U, s));
   } else {
     count_launches(1);
-    k_fill<<<nblocks(n), kNT, 0, s>>>(U, n, 0.0);
+    k_fill<<<nblocks(bn), kNT, 0, s>>>(U, bn, 0.0);
   }
   if (o->V0) {
-    UOT_CK(to_f64(prec, o->V0, m, V, s));
+    UOT_CK(to_f64(prec, o->V0, bm, V, s));
   } else {
     count_launches(1);
-    k_fill<<<nblocks(m), kNT, 0, s>>>(V, m, 0.0);
+    k_fill<<<nblocks(bm), kNT, 0, s>>>(V, bm, 0.0);
   }
   UOT_CK(cudaGetLastError());
 
@@ -793,13 +805,26 @@ uot_status solve_impl(const uot_geom* g, const void* p, const void* dx, const vo
   double err = INFINITY;
   bool converged = false;
 
+  auto read_err = [&](double& out) -> cudaError_t {
+    cudaError_t e = cudaMemcpyAsync(acc_h.data(), acc, 16 * (size_t)batch, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    out = 0.0;
+    for (int b = 0; b < batch; ++b) {
+      const double v = (acc_h[2 * b + 1] > 0.0) ? acc_h[2 * b] / acc_h[2 * b + 1] : 0.0;
+      out = (v > out || v != v) ? v : out;
+    }
+    return cudaSuccess;
+  };
   if (!o->plain_scaling) {
     auto iteration = [&](double eps, bool check) -> cudaError_t {
       cudaError_t e;
-      if ((e = G.apply(0, V, logdy, eps, prox_epilogue(D1, logp, U, logdx, check ? acc : nullptr, eps), s,
-                       check ? acc : nullptr)) != cudaSuccess)
-        return e;
-      return G.apply(1, U, logdx, eps, prox_epilogue(D2, logq, V, logdy, nullptr, eps), s);
+      Epilogue e1 = prox_epilogue(D1, logp, U, logdx, check ? acc : nullptr, eps);
+      e1.bstride = e1.bstride_p = n;
+      if ((e = G.apply(0, V, logdy, eps, e1, s, check ? acc : nullptr)) != cudaSuccess) return e;
+      Epilogue e2 = prox_epilogue(D2, logq, V, logdy, nullptr, eps);
+      e2.bstride = e2.bstride_p = m;
+      return G.apply(1, U, logdx, eps, e2, s);
     };
     for (const Stage& sg : stages)
       for (int k = 0; k < sg.iters; ++k, ++total) UOT_CK(iteration(sg.eps, false));
@@ -809,10 +834,7 @@ uot_status solve_impl(const uot_geom* g, const void* p, const void* dx, const vo
       ++it;
       ++total;
       if (check) {
-        double h[2];
-        UOT_CK(cudaMemcpyAsync(h, acc, 16, cudaMemcpyDeviceToHost, s));
-        UOT_CK(cudaStreamSynchronize(s));
-        err = (h[1] > 0.0) ? h[0] / h[1] : 0.0;
+        UOT_CK(read_err(err));
         if (it > 1 && o->tol > 0.0 && err <= o->tol) {
           converged = true;
           break;
@@ -883,12 +905,12 @@ uot_status solve_impl(const uot_geom* g, const void* p, const void* dx, const vo
   // NaN check and output conversion
   UOT_CK(cudaMemsetAsync(flag, 0, 4, s));
   count_launches(1);
-  k_nan_flag<<<nblocks(n), kNT, 0, s>>>(U, n, prec == UOT_F32, flag);
+  k_nan_flag<<<nblocks(bn), kNT, 0, s>>>(U, bn, prec == UOT_F32, flag);
   count_launches(1);
-  k_nan_flag<<<nblocks(m), kNT, 0, s>>>(V, m, prec == UOT_F32, flag);
+  k_nan_flag<<<nblocks(bm), kNT, 0, s>>>(V, bm, prec == UOT_F32, flag);
   UOT_CK(cudaGetLastError());
-  UOT_CK(from_f64(prec, U, n, Uout, s));
-  UOT_CK(from_f64(prec, V, m, Vout, s));
+  UOT_CK(from_f64(prec, U, bn, Uout, s));
+  UOT_CK(from_f64(prec, V, bm, Vout, s));
   UOT_CK(cudaEventRecord(ev1, s));
   int hflag = 0;
   UOT_CK(cudaMemcpyAsync(&hflag, flag, 4, cudaMemcpyDeviceToHost, s));
@@ -973,7 +995,14 @@ uot_status uot_solve(const uot_geom* g, const void* p, const void* dx, const voi
                      const void* dy, const uot_div* F1, const uot_div* F2, const uot_opts* o,
                      void* U, void* V, uot_result* res, void* stream) {
   clear_stale_error();
-  return solve_impl(g, p, dx, q, dy, F1, F2, o, U, V, res, (cudaStream_t)stream);
+  return solve_impl(g, 1, p, dx, q, dy, F1, F2, o, U, V, res, (cudaStream_t)stream);
+}
+
+uot_status uot_solve_many(const uot_geom* g, int batch, const void* p, const void* dx,
+                          const void* q, const void* dy, const uot_div* F1, const uot_div* F2,
+                          const uot_opts* o, void* U, void* V, uot_result* res, void* stream) {
+  clear_stale_error();
+  return solve_impl(g, batch, p, dx, q, dy, F1, F2, o, U, V, res, (cudaStream_t)stream);
 }
 
 uot_status uot_gibbs_log(const uot_geom* g, const void* W, const void* w, double eps,
@@ -1483,7 +1512,7 @@ uot_status uot_barycenter(const uot_geom* g, int Kmeas, const double* alpha, con
   sc.reserve<double>(m);          // logh
   sc.reserve<double>(Kmeas);      // alpha
   sc.reserve<float>(Kmeas);       // log alpha (FP32 path)
-  sc.reserve<double>(8);          // acc
+  sc.reserve<double>(2 * (size_t)Kmeas);  // violation accumulators per measure
   UOT_CK(sc.allocate());
   UOT_CK(G.take(sc, s));
   double* logP = sc.take<double>(n * Kmeas);
@@ -1495,7 +1524,8 @@ uot_status uot_barycenter(const uot_geom* g, int Kmeas, const double* alpha, con
   double* logh = sc.take<double>(m);
   double* alpha_d = sc.take<double>(Kmeas);
   float* log_alpha_d = sc.take<float>(Kmeas);
-  double* acc = sc.take<double>(8);
+  double* acc = sc.take<double>(2 * (size_t)Kmeas);
+  std::vector<double> acc_h(2 * (size_t)Kmeas);
   UOT_SCRATCH_OK(sc);
   UOT_CK(to_log(prec, P, n * Kmeas, logP, s));
   UOT_CK(to_log(prec, dx, n, logdx, s));
@@ -1554,9 +1584,13 @@ uot_status uot_barycenter(const uot_geom* g, int Kmeas, const double* alpha, con
     ++it;
     ++total;
     if (check) {
-      double h[2];
-      UOT_CK(cudaMemcpyAsync(h, acc, 16, cudaMemcpyDeviceToHost, s));
+      UOT_CK(cudaMemcpyAsync(acc_h.data(), acc, 16 * (size_t)Kmeas, cudaMemcpyDeviceToHost, s));
       UOT_CK(cudaStreamSynchronize(s));
+      double h[2] = {0.0, 0.0};
+      for (int k = 0; k < Kmeas; ++k) {
+        h[0] += acc_h[2 * k];
+        h[1] += acc_h[2 * k + 1];
+      }
       err = (h[1] > 0.0) ? h[0] / h[1] : 0.0;
       if (it > 1 && o->tol > 0.0 && err <= o->tol) {
         converged = true;

@@ -140,7 +140,7 @@ struct Epilogue {
   const double* logp;      // log density of the output side
   double* pot;             // potential written (read first as the old value)
   const double* logw;      // log reference weight of the output side (violation)
-  double* err;             // [2] = {sum dx |r_old - r_new|, sum dx r_new}; NULL: no check
+  double* err;             // [2 per batch entry] = {sum dx |r_old - r_new|, sum dx r_new}; NULL: no check
   // EPI_PLAN
   const double* pot_shift; // U (or V) of the output side
   int ncols, col;

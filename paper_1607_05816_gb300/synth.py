@@ -149,3 +149,29 @@ def batch_points(nprob: int = 4096, size=(64, 2048), d: int = 2, seed: int = 123
         probs.append(dict(x=x, y=y, dx=np.full(n, 1.0 / n), dy=np.full(m, 1.0 / m),
                           p=np.full(n, mp), q=np.full(m, mq), lam=lm))
     return probs
+
+
+def warmstart_instances(n: int, H: int = 64, W: int = 64, seed: int = 1239, group: int = 64,
+                        mass=(0.5, 2.0), eps=(1e-3, 1e-1), lam=(0.1, 10.0), floor: float = 1e-6):
+    """Instances for the learned warm start: pairs of 1-6 Gaussian-blob images
+    with masses uniform in `mass` (plus a relative floor so every density is
+    positive), eps and lambda log-uniform.  Consecutive blocks of `group`
+    instances share (eps, lambda) so that they can be solved as one batch.
+    Returns dict(P [n,H,W], Q [n,H,W], eps [n], lam [n], dx [H,W])."""
+    g = rng(seed)
+    dx = np.full((H, W), 1.0 / (H * W))
+    P = np.empty((n, H, W))
+    Q = np.empty((n, H, W))
+    E = np.empty(n)
+    L = np.empty(n)
+    for k in range(n):
+        if k % group == 0:
+            e = float(np.exp(g.uniform(np.log(eps[0]), np.log(eps[1]))))
+            lm = float(np.exp(g.uniform(np.log(lam[0]), np.log(lam[1]))))
+        for arr in (P, Q):
+            img = blob_image(g, H, W)
+            img = img + floor * img.max()
+            arr[k] = normalise_mass(img, dx, float(g.uniform(*mass)))
+        E[k] = e
+        L[k] = lm
+    return dict(P=P, Q=Q, eps=E, lam=L, dx=dx, xs=[grid_axis(H), grid_axis(W)])

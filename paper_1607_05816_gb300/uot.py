@@ -74,6 +74,9 @@ _SIGS = {
     "uot_solve": (C.c_int, [C.POINTER(CGeom), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                             C.POINTER(CDiv), C.POINTER(CDiv), C.POINTER(COpts), C.c_void_p,
                             C.c_void_p, C.POINTER(CResult), C.c_void_p]),
+    "uot_solve_many": (C.c_int, [C.POINTER(CGeom), C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                 C.c_void_p, C.POINTER(CDiv), C.POINTER(CDiv), C.POINTER(COpts),
+                                 C.c_void_p, C.c_void_p, C.POINTER(CResult), C.c_void_p]),
     "uot_gibbs_log": (C.c_int, [C.POINTER(CGeom), C.c_void_p, C.c_void_p, C.c_double, C.c_int,
                                 C.c_int, C.c_void_p, C.c_void_p]),
     "uot_gibbs_log_noalloc": (C.c_int, [C.POINTER(CGeom), C.c_void_p, C.c_void_p, C.c_double,
@@ -88,6 +91,19 @@ _SIGS = {
                                   C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                   C.POINTER(COpts), C.c_void_p, C.c_void_p, C.POINTER(C.c_int),
                                   C.POINTER(C.c_double), C.POINTER(CResult), C.c_void_p]),
+    "uot_conv2d_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                                     C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                     C.c_void_p]),
+    "uot_conv2d_backward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                      C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int,
+                                      C.c_int, C.c_int, C.c_int, C.c_void_p]),
+    "uot_adam_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_longlong,
+                                C.c_float, C.c_float, C.c_float, C.c_float, C.c_int, C.c_void_p]),
+    "uot_mse_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_longlong, C.c_void_p,
+                               C.c_void_p]),
+    "uot_scale_instances": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_longlong, C.c_void_p]),
+    "uot_warmstart_features": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                         C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p]),
     "uot_barycenter": (C.c_int, [C.POINTER(CGeom), C.c_int, C.POINTER(C.c_double), C.c_void_p,
                                  C.c_void_p, C.c_void_p, C.POINTER(CDiv), C.c_double, C.c_int,
                                  C.POINTER(COpts), C.c_void_p, C.c_void_p, C.c_void_p,
@@ -290,6 +306,29 @@ def solve(geom: Geometry, p, dx, q, dy, F1: Div, F2: Div, eps: float, *, precisi
                       status=STATUS[st])
 
 
+def solve_many(geom: Geometry, P, dx, Q, dy, F1: Div, F2: Div, eps, *, precision=F64,
+               max_iter=1000, tol=0.0, check_every=10, eps_start=None, eps_stages=10,
+               iters_per_stage=100, U0=None, V0=None, U=None, V=None):
+    """uot_solve_many: P [B, n], Q [B, m] densities of B independent problems
+    sharing geometry, weights, eps and penalties.  Returns (U [B,n], V [B,m], info)."""
+    lib = load()
+    dt = _dtype(precision)
+    B = P.shape[0]
+    U = torch.empty(B, geom.n, dtype=dt, device=P.device) if U is None else U
+    V = torch.empty(B, geom.m, dtype=dt, device=P.device) if V is None else V
+    o = COpts(precision, float(eps), float(eps_start) if eps_start else 0.0, int(eps_stages),
+              int(iters_per_stage), int(max_iter), float(tol), int(check_every), 0,
+              _ptr(U0, dt, "U0"), _ptr(V0, dt, "V0"))
+    r = CResult()
+    g = geom.c(precision)
+    st = lib.uot_solve_many(C.byref(g), int(B), _ptr(P, dt, "P"), _ptr(dx, dt, "dx"),
+                            _ptr(Q, dt, "Q"), _ptr(dy, dt, "dy"), C.byref(F1.c()), C.byref(F2.c()),
+                            C.byref(o), _ptr(U, dt, "U"), _ptr(V, dt, "V"), C.byref(r), _stream())
+    _check(st, "uot_solve_many")
+    return U, V, dict(iters=r.iters, total_iters=r.total_iters, marg_err=r.marg_err, ms=r.ms,
+                      status=STATUS[st])
+
+
 def gibbs_log(geom: Geometry, W, w, eps, transpose=False, precision=F64, out=None):
     """uot_gibbs_log: eps log K(e^{W/eps} . w) (or with K^T)."""
     lib = load()
@@ -397,3 +436,67 @@ def solve_batch(sizes, divs, d, x, p, dx, y, q, dy, eps, *, max_iter=1000, tol=0
     _check(st, "uot_solve_batch")
     return U, V, list(iters), list(errs), dict(iters=r.iters, total_iters=r.total_iters,
                                                marg_err=r.marg_err, ms=r.ms, status=STATUS[st])
+
+
+# ---------------------------------------------------------------------------
+# learned warm start kernels
+# ---------------------------------------------------------------------------
+
+def conv2d_forward(x, w, b, dilation, leaky, out=None):
+    """uot_conv2d_forward on [N, Cin, H, W] FP32 tensors."""
+    N, Cin, H, W = x.shape
+    Cout = w.shape[0]
+    f = torch.float32
+    out = torch.empty(N, Cout, H, W, dtype=f, device=x.device) if out is None else out
+    _check(load().uot_conv2d_forward(_ptr(x, f, "x"), _ptr(w, f, "w"), _ptr(b, f, "b"),
+                                     _ptr(out, f, "y"), N, Cin, Cout, H, W, int(dilation),
+                                     int(bool(leaky)), _stream()), "uot_conv2d_forward")
+    return out
+
+
+def conv2d_backward(x, w, y, dy, dilation, leaky, need_dx=True):
+    """uot_conv2d_backward: returns (dx or None, dw, db)."""
+    N, Cin, H, W = x.shape
+    Cout = w.shape[0]
+    f = torch.float32
+    dx = torch.empty_like(x) if need_dx else None
+    dw = torch.empty_like(w)
+    db = torch.empty(Cout, dtype=f, device=x.device)
+    _check(load().uot_conv2d_backward(_ptr(x, f, "x"), _ptr(w, f, "w"), _ptr(y, f, "y"),
+                                      _ptr(dy, f, "dy"), _ptr(dx, f, "dx") if need_dx else None,
+                                      _ptr(dw, f, "dw"), _ptr(db, f, "db"), N, Cin, Cout, H, W,
+                                      int(dilation), int(bool(leaky)), _stream()),
+           "uot_conv2d_backward")
+    return dx, dw, db
+
+
+def adam_step(param, grad, m, v, lr, step, beta1=0.9, beta2=0.999, eps=1e-8):
+    f = torch.float32
+    _check(load().uot_adam_step(_ptr(param, f, "param"), _ptr(grad, f, "grad"), _ptr(m, f, "m"),
+                                _ptr(v, f, "v"), param.numel(), float(lr), float(beta1),
+                                float(beta2), float(eps), int(step), _stream()), "uot_adam_step")
+
+
+def mse_grad(pred, target, grad, loss_dev):
+    f = torch.float32
+    _check(load().uot_mse_grad(_ptr(pred, f, "pred"), _ptr(target, f, "target"), _ptr(grad, f, "grad"),
+                               pred.numel(), _ptr(loss_dev, torch.float64, "loss"), _stream()),
+           "uot_mse_grad")
+
+
+def scale_instances(x, scale):
+    """In place: x[n] *= scale[n] (x [N, ...] FP32, scale [N] FP32)."""
+    f = torch.float32
+    _check(load().uot_scale_instances(_ptr(x, f, "x"), _ptr(scale, f, "scale"), x.shape[0],
+                                      x.numel() // x.shape[0], _stream()), "uot_scale_instances")
+    return x
+
+
+def warmstart_features(P, Q, log_eps, log_lam, out=None):
+    N, H, W = P.shape
+    f = torch.float32
+    out = torch.empty(N, 4, H, W, dtype=f, device=P.device) if out is None else out
+    _check(load().uot_warmstart_features(_ptr(P, f, "p"), _ptr(Q, f, "q"), _ptr(log_eps, f, "log_eps"),
+                                         _ptr(log_lam, f, "log_lam"), _ptr(out, f, "out"), N, H, W,
+                                         _stream()), "uot_warmstart_features")
+    return out
