@@ -1,0 +1,136 @@
+"""Parity at the full workload sizes, in the configuration the benchmark times.
+
+The oracle cannot rerun whole solves at these sizes in seconds, so it checks
+(a) sampled outputs of one Gibbs operator application, computed one by one
+from the definition, (b) a few iterations from the cold start with the
+oracle's separable operator, and (c) properties that hold at any size: the
+returned potentials are a fixed point to the requested tolerance when the
+oracle evaluates the marginal violation in FP64.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_1607_05816_gb300 import synth
+from paper_1607_05816_gb300 import uot as U
+
+pytestmark = [pytest.mark.gpu, pytest.mark.filterwarnings("ignore::RuntimeWarning")]
+
+
+def f32(a):
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+def dev(a, dt=torch.float32):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device="cuda").ravel()
+
+
+def grid_setup():
+    d = synth.problem_grid2d(256, 256, seed=1235, masses=(1.0, 1.3))
+    geo = U.Geometry.grid([dev(a) for a in d["xs"]], [dev(a) for a in d["ys"]])
+    og = O.Geometry("grid", xs=[f32(a) for a in d["xs"]], ys=[f32(a) for a in d["ys"]])
+    return d, geo, og
+
+
+def sampled_lse(og_points_x, og_points_y, L, idx, eps):
+    """eps log sum_j exp(L_j - |x_i - y_j|^2/eps) for the sampled i, one by one."""
+    out = []
+    for i in idx:
+        c = np.sum((og_points_y - og_points_x[i]) ** 2, axis=1) / eps
+        out.append(eps * O.lse(L - c))
+    return np.array(out)
+
+
+def test_grid256_gibbs_sampled_outputs():
+    d, geo, og = grid_setup()
+    g = synth.rng(5)
+    eps = 1e-3
+    V = g.normal(size=(256, 256)) * 0.02
+    V[d["q"] == 0] = -np.inf
+    got = U.gibbs_log(geo, dev(V), dev(d["dy"]), eps, False, U.F32).double().cpu().numpy()
+    Xp = O.grid_points(og.xs)
+    Yp = O.grid_points(og.ys)
+    L = f32(V).ravel() / eps + np.log(f32(d["dy"]).ravel())
+    idx = g.integers(0, 65536, size=48)
+    want = sampled_lse(Xp, Yp, L, idx, eps)
+    assert np.max(np.abs(got[idx] - want)) <= 1e-5 * max(1.0, np.max(np.abs(want)))
+
+
+def test_grid256_first_iterations_match_oracle():
+    """Ten iterations at eps = 1e-3 from the cold start, FP32 path vs FP64 oracle."""
+    d, geo, og = grid_setup()
+    eps, iters = 1e-3, 10
+    Ug, Vg, _ = U.solve(geo, dev(d["p"]), dev(d["dx"]), dev(d["q"]), dev(d["dy"]), U.KL(0.5), U.KL(0.5),
+                        eps, precision=U.F32, max_iter=iters)
+    r = O.solve_log(og, f32(d["dx"]), f32(d["dy"]), f32(d["p"]), f32(d["q"]), O.KL(0.5), O.KL(0.5), eps,
+                    max_iter=iters)
+    for got, want in ((Ug, r["U"]), (Vg, r["V"])):
+        gv = got.double().cpu().numpy()
+        wv = want.ravel()
+        assert np.array_equal(np.isneginf(gv), np.isneginf(wv))
+        f = np.isfinite(wv)
+        assert np.max(np.abs(gv[f] - wv[f])) <= 1e-5 * max(1.0, np.max(np.abs(wv[f])))
+
+
+def test_grid256_bench_solve_is_a_fixed_point():
+    """The benchmark's solve (eps-scaling 1e-1 -> 1e-3, tol 1e-6, FP32): the
+    oracle's FP64 marginal violation of the returned potentials is within a
+    small factor of the reported one."""
+    d, geo, og = grid_setup()
+    Ug, Vg, info = U.solve(geo, dev(d["p"]), dev(d["dx"]), dev(d["q"]), dev(d["dy"]), U.KL(0.5),
+                           U.KL(0.5), 1e-3, precision=U.F32, max_iter=20000, tol=1e-6, check_every=20,
+                           eps_start=1e-1, eps_stages=10, iters_per_stage=100)
+    assert info["status"] == "UOT_OK" and info["marg_err"] <= 1e-6
+    Un = Ug.double().cpu().numpy().reshape(256, 256)
+    Vn = Vg.double().cpu().numpy().reshape(256, 256)
+    v = O.marginal_violation(og, f32(d["dx"]), f32(d["dy"]), f32(d["p"]), f32(d["q"]), O.KL(0.5),
+                             O.KL(0.5), 1e-3, Un, Vn)
+    assert v <= 1e-5, v
+
+
+def test_points20000_gibbs_sampled_outputs():
+    """Point clouds at full size (n = m = 20000, d = 3), FP32 online cost."""
+    d = synth.problem_points(20000, 20000, 3, seed=1236)
+    geo = U.Geometry.points(torch.as_tensor(d["x"], dtype=torch.float32, device="cuda"),
+                            torch.as_tensor(d["y"], dtype=torch.float32, device="cuda"))
+    g = synth.rng(6)
+    eps = 1e-3
+    V = g.normal(size=20000) * 0.01
+    got = U.gibbs_log(geo, dev(V), dev(d["dy"]), eps, False, U.F32).double().cpu().numpy()
+    L = f32(V) / eps + np.log(f32(d["dy"]))
+    idx = g.integers(0, 20000, size=48)
+    want = sampled_lse(f32(d["x"]), f32(d["y"]), L, idx, eps)
+    assert np.max(np.abs(got[idx] - want)) <= 1e-5 * max(1.0, np.max(np.abs(want)))
+
+
+def test_barycenter_32x128x128_iterations_match_oracle():
+    """KL barycenter of 32 blob images 128x128 (alpha_k = 1/32, F1 = EQ,
+    lambda = 1, eps = 1e-2), four iterations, FP32 path vs FP64 oracle."""
+    b = synth.barycenter_images(32, 128, 128, seed=1237)
+    alpha = np.full(32, 1.0 / 32)
+    eps, lam, iters = 1e-2, 1.0, 4
+    geo = U.Geometry.grid([dev(a) for a in b["xs"]])
+    lh, Ug, Vg, _ = U.barycenter(geo, alpha, torch.as_tensor(f32(b["P"]).reshape(32, -1), dtype=torch.float32, device="cuda"),
+                                 dev(b["dx"]), dev(b["dy"]), U.EQ(), lam, eps, precision=U.F32, max_iter=iters)
+    og = O.Geometry("grid", xs=[f32(a) for a in b["xs"]], ys=[f32(a) for a in b["ys"]])
+    Uo, Vo, lho = O.barycenter_log(og, f32(b["dx"]), f32(b["dy"]), f32(b["P"]), alpha, O.EQ(), lam, eps, iters)
+    for got, want in ((lh, lho), (Vg, Vo.reshape(32, -1))):
+        gv = got.double().cpu().numpy().ravel()
+        wv = want.ravel()
+        assert np.max(np.abs(gv - wv)) <= 1e-5 * max(1.0, np.max(np.abs(wv)))
+
+
+def test_dense1d_alg1_2000_iterations():
+    """Algorithm 1, 1-D n = m = 256, KL lambda = 1, eps = 1e-2, FP64, 2000 iterations:
+    covered element by element in test_gpu_parity.test_plain_scaling_alg1_parity;
+    here the log-domain FP64 path at the same size and iteration count agrees
+    with Algorithm 1 on the GPU."""
+    d = synth.problem_1d(256, 256, seed=1234)
+    C = O.sqdist(d["x"], d["y"])
+    geo = U.Geometry.dense(torch.as_tensor(C, dtype=torch.float64, device="cuda"))
+    args = [dev(d[k], torch.float64) for k in ("p", "dx", "q", "dy")]
+    U1, V1, _ = U.solve(geo, *args, U.KL(1.0), U.KL(1.0), 1e-2, precision=U.F64, max_iter=2000, plain_scaling=True)
+    U2, V2, _ = U.solve(geo, *args, U.KL(1.0), U.KL(1.0), 1e-2, precision=U.F64, max_iter=2000)
+    assert torch.max(torch.abs(U1 - U2)).item() <= 1e-10 * max(1.0, torch.max(torch.abs(U2)).item())
+    assert torch.max(torch.abs(V1 - V2)).item() <= 1e-10 * max(1.0, torch.max(torch.abs(V2)).item())
