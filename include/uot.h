@@ -95,7 +95,15 @@ typedef struct {
   int d;         /* 1..8 */
 } uot_geom;
 
-typedef enum { UOT_F64 = 0, UOT_F32 = 1 } uot_precision;
+/*
+ * UOT_MIXED: as UOT_F32 (float arrays, float-float per-point state), but on
+ * grids each separable pass runs on the tensor cores (tcgen05, BF16 operands,
+ * FP32 accumulation) in a block-stabilised form that needs about a tenth of
+ * the exponentials; results carry the BF16 operand rounding (relative error of
+ * the kernel sums ~2^-8).  Grid axes whose 32-point blocks are too wide for
+ * that form at the given eps, and non-grid geometries, use the FP32 kernels.
+ */
+typedef enum { UOT_F64 = 0, UOT_F32 = 1, UOT_MIXED = 2 } uot_precision;
 
 typedef struct {
   int precision;       /* uot_precision */

@@ -1,0 +1,328 @@
+// FP32 log-domain Gibbs operator for point clouds (cost |x - y|^2 recomputed on
+// the fly, never stored), split into two kernels:
+//
+//  points_partial: CTA = (1024 outputs, one chunk of the inputs).  The chunk's
+//    shifted log-values t_j and coordinates are staged in shared memory as
+//    packed pairs; each warp owns 128 outputs (4 per lane, two f32x2 pairs) and
+//    sweeps the chunk.  The log-sum-exp shift of an output is its result from
+//    the previous call at the same eps; a warp whose partial sum overflows
+//    redoes the chunk with the exact chunk maximum.  Writes (shift, sum) per
+//    (chunk, output).
+//  points_combine: one warp per output merges the chunks' pairs; if the
+//    merged sum underflowed (shift far above the result) the warp recomputes
+//    that output exactly over all inputs; then the epilogue (Table 1 row,
+//    violation terms) runs on the float-float result.
+//
+// Work: n m exponentials per call, bound by the SFU rate.
+#include <string.h>
+
+#include "uot_internal.cuh"
+
+namespace uot {
+namespace {
+
+typedef unsigned long long f2p;
+__device__ __forceinline__ f2p pk(float a, float b) {
+  f2p r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ float2 upk(f2p r) {
+  float2 v;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
+  return v;
+}
+__device__ __forceinline__ f2p fma2(f2p a, f2p b, f2p c) {
+  f2p d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ f2p add2(f2p a, f2p b) {
+  f2p d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2p sub2(f2p a, f2p b) {
+  f2p d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2p mul2(f2p a, f2p b) {
+  f2p d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ float ex2f(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float lg2f(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+constexpr int kNW = 8;                 // warps per CTA
+constexpr int kOutBlk = kNW * 128;     // outputs per CTA
+
+struct PtArgs {
+  const float* x;     // [nout][d]  output points
+  const float* y;     // [nin][d]   input points
+  int d, nout, nin, chunk;
+  const float* Lt;    // [nin] (L_j - Lmax) log2(e), from prepare_L_ff
+  const float* Lmax;  // [1]
+  float k2;           // log2(e)/eps
+  const float* zprev; // [nout] previous result (natural log), or NULL
+  int use_prev;
+  float2* part;       // [nchunks][nout] (shift, sum) in log2 units relative to Lmax
+};
+
+__global__ void __launch_bounds__(kNW * 32)
+    points_partial(PtArgs a) {
+  extern __shared__ float4 st[];  // 2 x chunk float4: {t,t,y0,y0}, {y1,y1,y2,y2}
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int c = blockIdx.y;
+  const int j0 = c * a.chunk, j1 = min(a.nin, j0 + a.chunk);
+  const int d = a.d;
+  const float Lmax = *a.Lmax;
+  for (int j = j0 + tid; j < j1; j += kNW * 32) {
+    const float t = a.Lt[j];
+    const float c0 = a.y[(int64_t)j * d];
+    const float c1 = d > 1 ? a.y[(int64_t)j * d + 1] : 0.0f;
+    const float c2 = d > 2 ? a.y[(int64_t)j * d + 2] : 0.0f;
+    st[2 * (j - j0)] = make_float4(t, t, c0, c0);
+    st[2 * (j - j0) + 1] = make_float4(c1, c1, c2, c2);
+  }
+  __syncthreads();
+  const int base = blockIdx.x * kOutBlk + warp * 128;
+  if (base >= a.nout) return;
+  float xc[3][4];
+  bool valid[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int i = base + lane + 32 * q;
+    valid[q] = i < a.nout;
+    const int ii = valid[q] ? i : a.nout - 1;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) xc[k][q] = (k < d) ? a.x[(int64_t)ii * d + k] : 0.0f;
+  }
+  const f2p XA0 = pk(xc[0][0], xc[0][1]), XA1 = pk(xc[1][0], xc[1][1]), XA2 = pk(xc[2][0], xc[2][1]);
+  const f2p XB0 = pk(xc[0][2], xc[0][3]), XB1 = pk(xc[1][2], xc[1][3]), XB2 = pk(xc[2][2], xc[2][3]);
+  const f2p nk2 = pk(-a.k2, -a.k2);
+  const int nj = j1 - j0;
+  float mq[4], sq[4];
+  bool exact = !(a.use_prev && a.zprev);
+  if (!exact) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float zp = valid[q] ? a.zprev[base + lane + 32 * q] : Lmax;
+      mq[q] = (zp == -INFINITY) ? 0.0f : (zp - Lmax) * kLog2e;
+    }
+  }
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    if (exact) {
+      float m4[4] = {-INFINITY, -INFINITY, -INFINITY, -INFINITY};
+#pragma unroll 2
+      for (int j = 0; j < nj; ++j) {
+        const float4 s0 = st[2 * j], s1 = st[2 * j + 1];
+        const f2p T = pk(s0.x, s0.y), Y0 = pk(s0.z, s0.w), Y1 = pk(s1.x, s1.y), Y2 = pk(s1.z, s1.w);
+        f2p DA = sub2(XA0, Y0), DB = sub2(XB0, Y0);
+        f2p QA = mul2(DA, DA), QB = mul2(DB, DB);
+        if (d > 1) {
+          DA = sub2(XA1, Y1);
+          DB = sub2(XB1, Y1);
+          QA = fma2(DA, DA, QA);
+          QB = fma2(DB, DB, QB);
+        }
+        if (d > 2) {
+          DA = sub2(XA2, Y2);
+          DB = sub2(XB2, Y2);
+          QA = fma2(DA, DA, QA);
+          QB = fma2(DB, DB, QB);
+        }
+        const float2 A = upk(fma2(nk2, QA, T)), B = upk(fma2(nk2, QB, T));
+        m4[0] = fmaxf(m4[0], A.x);
+        m4[1] = fmaxf(m4[1], A.y);
+        m4[2] = fmaxf(m4[2], B.x);
+        m4[3] = fmaxf(m4[3], B.y);
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) mq[q] = m4[q];
+    }
+    const f2p MA = pk(mq[0] == -INFINITY ? 0.0f : mq[0], mq[1] == -INFINITY ? 0.0f : mq[1]);
+    const f2p MB = pk(mq[2] == -INFINITY ? 0.0f : mq[2], mq[3] == -INFINITY ? 0.0f : mq[3]);
+    f2p SA = pk(0.0f, 0.0f), SB = SA;
+#pragma unroll 2
+    for (int j = 0; j < nj; ++j) {
+      const float4 s0 = st[2 * j], s1 = st[2 * j + 1];
+      const f2p T = pk(s0.x, s0.y), Y0 = pk(s0.z, s0.w), Y1 = pk(s1.x, s1.y), Y2 = pk(s1.z, s1.w);
+      f2p DA = sub2(XA0, Y0), DB = sub2(XB0, Y0);
+      f2p QA = mul2(DA, DA), QB = mul2(DB, DB);
+      if (d > 1) {
+        DA = sub2(XA1, Y1);
+        DB = sub2(XB1, Y1);
+        QA = fma2(DA, DA, QA);
+        QB = fma2(DB, DB, QB);
+      }
+      if (d > 2) {
+        DA = sub2(XA2, Y2);
+        DB = sub2(XB2, Y2);
+        QA = fma2(DA, DA, QA);
+        QB = fma2(DB, DB, QB);
+      }
+      const float2 A = upk(fma2(nk2, QA, sub2(T, MA)));
+      const float2 B = upk(fma2(nk2, QB, sub2(T, MB)));
+      SA = add2(SA, pk(ex2f(A.x), ex2f(A.y)));
+      SB = add2(SB, pk(ex2f(B.x), ex2f(B.y)));
+    }
+    const float2 s01 = upk(SA), s23 = upk(SB);
+    sq[0] = s01.x;
+    sq[1] = s01.y;
+    sq[2] = s23.x;
+    sq[3] = s23.y;
+    bool bad = false;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (valid[q] && !exact && !(sq[q] <= 0x1p100f)) bad = true;  // overflow or NaN
+    if (__any_sync(0xffffffffu, bad)) {
+      exact = true;
+      continue;
+    }
+    break;
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    if (!valid[q]) continue;
+    const int i = base + lane + 32 * q;
+    a.part[(int64_t)c * a.nout + i] = (mq[q] == -INFINITY) ? make_float2(0.0f, 0.0f) : make_float2(mq[q], sq[q]);
+  }
+}
+
+struct CombArgs {
+  const float* x;
+  const float* y;
+  int d, nout, nin, nchunks;
+  const float* Lt;
+  const float* Lmax;
+  float k2;
+  const float2* part;
+  float* zprev;  // written (NULL: not kept)
+};
+
+// One warp per output: merge chunk partials, exact recomputation if the
+// merged sum underflowed, then the epilogue.
+__global__ void __launch_bounds__(256)
+    points_combine(CombArgs a, Epilogue epi) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.x * 8 + warp;
+  float num = 0.0f, den = 0.0f;
+  const float Lmax = *a.Lmax;
+  if (i < a.nout) {
+    float M = -INFINITY;
+    for (int c = lane; c < a.nchunks; c += 32) {
+      const float2 pr = a.part[(int64_t)c * a.nout + i];
+      if (pr.y > 0.0f) M = fmaxf(M, pr.x);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) M = fmaxf(M, __shfl_xor_sync(0xffffffffu, M, o));
+    float S = 0.0f;
+    if (M != -INFINITY)
+      for (int c = lane; c < a.nchunks; c += 32) {
+        const float2 pr = a.part[(int64_t)c * a.nout + i];
+        if (pr.y > 0.0f) S += pr.y * ex2f(pr.x - M);
+      }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) S += __shfl_xor_sync(0xffffffffu, S, o);
+    if (!(S >= 0x1p-90f) && Lmax != -INFINITY) {
+      // the shift was far above the result: exact log-sum-exp over all inputs
+      float xi[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) xi[k] = (k < a.d) ? a.x[(int64_t)i * a.d + k] : 0.0f;
+      float m = -INFINITY;
+      for (int j = lane; j < a.nin; j += 32) {
+        float q = 0.0f;
+        for (int k = 0; k < a.d; ++k) {
+          const float t = xi[k] - a.y[(int64_t)j * a.d + k];
+          q = fmaf(t, t, q);
+        }
+        m = fmaxf(m, fmaf(-a.k2, q, a.Lt[j]));
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+      float s = 0.0f;
+      if (m != -INFINITY)
+        for (int j = lane; j < a.nin; j += 32) {
+          float q = 0.0f;
+          for (int k = 0; k < a.d; ++k) {
+            const float t = xi[k] - a.y[(int64_t)j * a.d + k];
+            q = fmaf(t, t, q);
+          }
+          s += ex2f(fmaf(-a.k2, q, a.Lt[j]) - m);
+        }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      M = m;
+      S = s;
+    }
+    if (lane == 0) {
+      ff z = ff_ninf();
+      if (Lmax != -INFINITY && M != -INFINITY && S > 0.0f) {
+        const ff ln2 = ff{0.693147182464599609375f, -1.904654323148236017e-09f};
+        z = ff_add_f(ff_add_f(ff_mul_f(ln2, M), Lmax), kLn2 * lg2f(S));
+      }
+      if (a.zprev) a.zprev[i] = z.hi;
+      apply_epilogue_ff(epi, 0, i, z, num, den);
+    }
+  }
+  if (epi.err) block_add2f<256>(num, den, epi.err);
+}
+
+}  // namespace
+
+// Chunking of the inputs: about 1024 inputs per chunk.
+int points_nchunks(int nin) { return (nin + 1023) / 1024; }
+
+cudaError_t launch_points(const float* x, const float* y, int d, int nout, int nin,
+                          const float* Lt, const float* Lmax, double eps, float* zprev,
+                          int use_prev, float2* part, const Epilogue& epi, cudaStream_t s) {
+  const int nchunks = points_nchunks(nin);
+  const int chunk = (nin + nchunks - 1) / nchunks;
+  PtArgs a;
+  a.x = x;
+  a.y = y;
+  a.d = d;
+  a.nout = nout;
+  a.nin = nin;
+  a.chunk = chunk;
+  a.Lt = Lt;
+  a.Lmax = Lmax;
+  a.k2 = (float)((double)kLog2e / eps);
+  a.zprev = zprev;
+  a.use_prev = use_prev;
+  a.part = part;
+  const size_t smem = (size_t)2 * chunk * sizeof(float4);
+  cudaError_t e = cudaFuncSetAttribute(points_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((nout + kOutBlk - 1) / kOutBlk, nchunks);
+  prof_mark_begin(PROF_ROWS, s);
+  count_launches(2);
+  points_partial<<<grid, kNW * 32, smem, s>>>(a);
+  CombArgs b;
+  b.x = x;
+  b.y = y;
+  b.d = d;
+  b.nout = nout;
+  b.nin = nin;
+  b.nchunks = nchunks;
+  b.Lt = Lt;
+  b.Lmax = Lmax;
+  b.k2 = a.k2;
+  b.part = part;
+  b.zprev = zprev;
+  points_combine<<<(nout + 7) / 8, 256, 0, s>>>(b, epi);
+  prof_mark_end(PROF_ROWS, s);
+  return cudaGetLastError();
+}
+
+}  // namespace uot

@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(WARPS * 32)
 
 cudaError_t launch_rows(int prec, const RowsGeom& g, int nrows, int nin, const double* W,
                         const double* logw, double eps, void* scratch_L, const Epilogue& epi,
-                        cudaStream_t s) {
+                        cudaStream_t s, float* zprev, int use_prev, void* part) {
   // scratch_L: nin elements of the precision's type followed by one double (Lmax).
   constexpr int WARPS = 8;
   const int grid = (nrows + WARPS - 1) / WARPS;
@@ -266,6 +266,12 @@ cudaError_t launch_rows(int prec, const RowsGeom& g, int nrows, int nin, const d
     prepare_L_ff<1024><<<1, 1024, 0, s>>>(reinterpret_cast<const float2*>(W),
                                            reinterpret_cast<const float2*>(logw), nin,
                                            ff2(ff_make(1.0 / eps)), Lt, Lmax);
+    if (g.kind == UOT_GEOM_POINTS && g.d <= 3 && part) {
+      count_launches(-1);  // launch_points counts its own two kernels
+      cudaError_t e = launch_points((const float*)g.x, (const float*)g.y, g.d, nrows, nin, Lt, Lmax,
+                                    eps, zprev, use_prev, reinterpret_cast<float2*>(part), epi, s);
+      return e != cudaSuccess ? e : cudaGetLastError();
+    }
     prof_mark_begin(PROF_ROWS, s);
     const float* C = (const float*)g.C;
     const float* x = (const float*)g.x;

@@ -17,6 +17,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <atomic>
 #include <mutex>
 #include <string>
@@ -415,7 +416,7 @@ DivParams make_div(const uot_div& F) {
   return d;
 }
 
-bool prec_ok(int p) { return p == UOT_F64 || p == UOT_F32; }
+bool prec_ok(int p) { return p == UOT_F64 || p == UOT_F32 || p == UOT_MIXED; }
 
 uot_status check_geom(const uot_geom* g) {
   if (!g) return UOT_EINVAL;
@@ -511,7 +512,13 @@ struct Gibbs {
   float* zbuf[2][UOT_MAX_DIM] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
   double zeps[2] = {-1.0, -1.0};
   bool speculate = false;
+  // UOT_MIXED: largest coordinate span of 32 consecutive points per axis (X, Y),
+  // and a flag set by the tensor-core kernel if a bounded wait gave up
+  double span_x[UOT_MAX_DIM] = {0, 0, 0}, span_y[UOT_MAX_DIM] = {0, 0, 0};
+  int* tc_err = nullptr;
   void* Lscratch = nullptr;     // rows: shifted input line
+  void* part = nullptr;         // FP32 point clouds: per-chunk partial sums
+  float* zrow[2] = {nullptr, nullptr};  // FP32 point clouds: previous results per direction
   int64_t inter = 0;            // grid intermediate size (elements)
   int nbatch = 1;
 
@@ -528,10 +535,22 @@ struct Gibbs {
       }
       if (speculate && prec == UOT_F32)
         for (int k = 0; k < 2 * g.ndim; ++k) sc.reserve<float>((size_t)inter * nbatch);
+      if (prec == UOT_MIXED) sc.reserve<int>(1);
     } else {
       const int64_t mx = (g.n > g.m ? g.n : g.m);
       sc.reserve<char>((size_t)mx * 8 + 512);
+      if (points_fast()) {
+        sc.reserve<float2>(part_elems());
+        if (speculate) {
+          sc.reserve<float>((size_t)g.n);
+          sc.reserve<float>((size_t)g.m);
+        }
+      }
     }
+  }
+  bool points_fast() const { return g.kind == UOT_GEOM_POINTS && prec != UOT_F64 && g.d <= 3; }
+  size_t part_elems() const {
+    return std::max((size_t)points_nchunks(g.m) * g.n, (size_t)points_nchunks(g.n) * g.m);
   }
   cudaError_t take(Scratch& sc, cudaStream_t s) {
     if (g.kind == UOT_GEOM_DENSE) {
@@ -553,14 +572,51 @@ struct Gibbs {
       if (speculate && prec == UOT_F32)
         for (int d = 0; d < 2; ++d)
           for (int k = 0; k < g.ndim; ++k) zbuf[d][k] = sc.take<float>((size_t)inter * nbatch);
+      if (prec == UOT_MIXED) {
+        tc_err = sc.take<int>(1);
+        if (!tc_err) return cudaErrorInvalidValue;
+        cudaError_t e = cudaMemsetAsync(tc_err, 0, sizeof(int), s);
+        if (e != cudaSuccess) return e;
+        for (int side = 0; side < 2; ++side) {
+          for (int k = 0; k < g.ndim; ++k) {
+            const int len = side == 0 ? g.shape_x[k] : g.shape_y[k];
+            std::vector<float> h(len);
+            e = cudaMemcpyAsync(h.data(), side == 0 ? g.axes_x[k] : g.axes_y[k], len * sizeof(float),
+                                cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) return e;
+            double span = 0.0;
+            for (int i0 = 0; i0 < len; i0 += 32)
+              for (int i = i0; i < std::min(len, i0 + 32); ++i)
+                span = std::max(span, std::fabs((double)h[i] - (double)h[i0]));
+            (side == 0 ? span_x : span_y)[k] = span;
+          }
+        }
+      }
     } else {
       const int64_t mx = (g.n > g.m ? g.n : g.m);
       Lscratch = sc.take<char>((size_t)mx * 8 + 512);
+      if (points_fast()) {
+        part = sc.take<float2>(part_elems());
+        if (speculate) {
+          zrow[0] = sc.take<float>((size_t)g.n);
+          zrow[1] = sc.take<float>((size_t)g.m);
+        }
+      }
     }
     return cudaGetLastError();
   }
 
   // dir 0: W on the Y side (size m) -> result on the X side (size n); dir 1: reverse.
+  // The tensor-core pass needs the local kernel exp(-(delta - eta)^2/eps) of
+  // two 32-point blocks to stay far above the FP32 underflow threshold
+  // (2^-100 in log2 units) and the staged lines to fit in shared memory.
+  bool tc_ok(int dir, int ax, double eps, int nin) const {
+    const double so = (dir == 0 ? span_x : span_y)[ax], si = (dir == 0 ? span_y : span_x)[ax];
+    const double reach = (double)kLog2e / eps * (so + si) * (so + si);
+    return reach <= 100.0 && grid_pass_tc_smem(nin) <= 200 * 1024;
+  }
+
   // zero_acc: two doubles cleared before the result is produced (violation
   // accumulators of a checked iteration), inside the first kernel when possible.
   cudaError_t apply(int dir, const double* W, const double* logw, double eps, const Epilogue& epi,
@@ -589,16 +645,22 @@ struct Gibbs {
         }
         double* za = nullptr;
         if (k == 0 && zero_acc) {
-          if (prec == UOT_F32) {
+          if (prec != UOT_F64) {
             za = zero_acc;
           } else {
             cudaError_t e0 = cudaMemsetAsync(zero_acc, 0, 16 * (size_t)nbatch, s);
             if (e0 != cudaSuccess) return e0;
           }
         }
-        cudaError_t err = launch_grid_pass(prec, cur, logw, cur_is_pot, (int)nlines, in_shape[ax],
-                                           in_axes[ax], out_shape[ax], out_axes[ax], eps, nbatch,
-                                           e, s, zbuf[dir][k], use_prev, za);
+        cudaError_t err;
+        if (prec == UOT_MIXED && tc_ok(dir, ax, eps, in_shape[ax])) {
+          err = launch_grid_pass_tc(cur, logw, cur_is_pot, (int)nlines, in_shape[ax], in_axes[ax],
+                                    out_shape[ax], out_axes[ax], eps, nbatch, e, s, tc_err, za);
+        } else {
+          err = launch_grid_pass(prec == UOT_F64 ? UOT_F64 : UOT_F32, cur, logw, cur_is_pot,
+                                 (int)nlines, in_shape[ax], in_axes[ax], out_shape[ax],
+                                 out_axes[ax], eps, nbatch, e, s, zbuf[dir][k], use_prev, za);
+        }
         if (err != cudaSuccess) return err;
         cur = pass[k & 1];
         cur_is_pot = 0;
@@ -628,10 +690,13 @@ struct Gibbs {
         if (e.pot_shift) e.pot_shift += b * e.bstride;
         if (e.err) e.err += 2 * b;
       }
-      cudaError_t err = launch_rows(prec, rg, nrows, nin, W + (int64_t)b * nin, logw, eps,
-                                    Lscratch, e, s);
+      const int use_prev = (nbatch == 1 && zrow[dir] != nullptr && zeps[dir] == eps) ? 1 : 0;
+      cudaError_t err = launch_rows(prec == UOT_F64 ? UOT_F64 : UOT_F32, rg, nrows, nin,
+                                    W + (int64_t)b * nin, logw, eps, Lscratch, e, s,
+                                    nbatch == 1 ? zrow[dir] : nullptr, use_prev, part);
       if (err != cudaSuccess) return err;
     }
+    if (zrow[dir] && nbatch == 1) zeps[dir] = eps;
     return cudaSuccess;
   }
 };
@@ -905,20 +970,22 @@ uot_status solve_impl(const uot_geom* g, int batch, const void* p, const void* d
   // NaN check and output conversion
   UOT_CK(cudaMemsetAsync(flag, 0, 4, s));
   count_launches(1);
-  k_nan_flag<<<nblocks(bn), kNT, 0, s>>>(U, bn, prec == UOT_F32, flag);
+  k_nan_flag<<<nblocks(bn), kNT, 0, s>>>(U, bn, prec != UOT_F64, flag);
   count_launches(1);
-  k_nan_flag<<<nblocks(bm), kNT, 0, s>>>(V, bm, prec == UOT_F32, flag);
+  k_nan_flag<<<nblocks(bm), kNT, 0, s>>>(V, bm, prec != UOT_F64, flag);
   UOT_CK(cudaGetLastError());
   UOT_CK(from_f64(prec, U, bn, Uout, s));
   UOT_CK(from_f64(prec, V, bm, Vout, s));
   UOT_CK(cudaEventRecord(ev1, s));
-  int hflag = 0;
+  int hflag = 0, htc = 0;
   UOT_CK(cudaMemcpyAsync(&hflag, flag, 4, cudaMemcpyDeviceToHost, s));
+  if (G.tc_err) UOT_CK(cudaMemcpyAsync(&htc, G.tc_err, 4, cudaMemcpyDeviceToHost, s));
   UOT_CK(cudaStreamSynchronize(s));
   float ms = 0.f;
   UOT_CK(cudaEventElapsedTime(&ms, ev0, ev1));
-  uot_status out = hflag ? UOT_NUMERICAL
-                         : ((o->tol > 0.0 && !converged && o->max_iter > 0) ? UOT_NOT_CONVERGED : UOT_OK);
+  uot_status out = htc ? UOT_TIMEOUT
+                       : hflag ? UOT_NUMERICAL
+                               : ((o->tol > 0.0 && !converged && o->max_iter > 0) ? UOT_NOT_CONVERGED : UOT_OK);
   if (res) {
     res->iters = it;
     res->total_iters = total;
@@ -1249,7 +1316,7 @@ uot_status uot_objective(const uot_geom* g, const void* p, const void* dx, const
   e.out = S1;
   UOT_CK(G.apply(0, Vd, logdy, eps, e, s));
   const DivParams D1 = make_div(*F1), D2 = make_div(*F2);
-  if (precision == UOT_F32) {
+  if (precision != UOT_F64) {
     double* arrs_n[] = {Ud, logp, logdx, r1, zK1, S1};
     double* arrs_m[] = {Vd, logq, logdy, r2};
     for (double* a : arrs_n) {

@@ -371,6 +371,15 @@ cudaError_t launch_grid_pass(int prec, const double* in, const double* logw, int
                              double eps, int nbatch, const Epilogue& epi, cudaStream_t s,
                              float* zprev, int use_prev, double* zero_acc = nullptr);
 
+// Tensor-core (tcgen05) variant of the FP32 grid pass (k_grid_tc.cu); float-
+// float lines in, same epilogues; valid while k (2 r)^2 stays in range (see
+// grid_tc_valid).  err_flag is set if a bounded wait gave up.
+size_t grid_pass_tc_smem(int nin);
+cudaError_t launch_grid_pass_tc(const double* in, const double* logw, int in_is_pot, int nlines,
+                                int nin, const void* yi, int nout, const void* xo, double eps,
+                                int nbatch, const Epilogue& epi, cudaStream_t s, int* err_flag,
+                                double* zero_acc);
+
 // Row-wise log-domain Gibbs operator for dense costs and point clouds:
 //   z_i = log sum_j exp(L_j - C_ij / eps),  L_j = W_j/eps + logw_j
 // C given densely (C row-major [nrows][ncols_c]) or as |x_i - y_j|^2.
@@ -381,9 +390,16 @@ struct RowsGeom {
   const void* y;     // points [nin*d]
   int d;
 };
+// FP32 point clouds with d <= 3 and a `part` buffer use the chunked kernels of
+// k_points.cu (zprev: previous results used as log-sum-exp shifts).
 cudaError_t launch_rows(int prec, const RowsGeom& g, int nrows, int nin, const double* W,
                         const double* logw, double eps, void* scratch_L, const Epilogue& epi,
-                        cudaStream_t s);
+                        cudaStream_t s, float* zprev = nullptr, int use_prev = 0,
+                        void* part = nullptr);
+int points_nchunks(int nin);
+cudaError_t launch_points(const float* x, const float* y, int d, int nout, int nin,
+                          const float* Lt, const float* Lmax, double eps, float* zprev,
+                          int use_prev, float2* part, const Epilogue& epi, cudaStream_t s);
 
 // Persistent batched solver for many point-cloud problems (k_batch.cu).
 struct BatchArgs {

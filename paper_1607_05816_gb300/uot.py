@@ -25,7 +25,7 @@ STATUS = {0: "UOT_OK", 1: "UOT_NOT_CONVERGED", -1: "UOT_EINVAL", -2: "UOT_ENOMEM
           -3: "UOT_NUMERICAL", -4: "UOT_TIMEOUT", -5: "UOT_ECUDA", -6: "UOT_EUNSUPPORTED"}
 DIV_EQ, DIV_KL, DIV_TV, DIV_RG = 0, 1, 2, 3
 GEOM_DENSE, GEOM_GRID, GEOM_POINTS = 0, 1, 2
-F64, F32 = 0, 1
+F64, F32, MIXED = 0, 1, 2
 BARY_EQ, BARY_KL = 0, 1
 MAX_DIM = 3
 
