@@ -1,6 +1,8 @@
 // FP32 log-domain Gibbs operator for point clouds (cost |x - y|^2 recomputed on
 // the fly, never stored), split into two kernels:
 //
+//  points_blockmax: per-block maxima of L_j = W_j/eps + log w_j (the shift of
+//    the staged values).
 //  points_partial: CTA = (1024 outputs, one chunk of the inputs).  The chunk's
 //    shifted log-values t_j and coordinates are staged in shared memory as
 //    packed pairs; each warp owns 128 outputs (4 per lane, two f32x2 pairs) and
@@ -65,13 +67,53 @@ __device__ __forceinline__ float lg2f(float x) {
 
 constexpr int kNW = 8;                 // warps per CTA
 constexpr int kOutBlk = kNW * 128;     // outputs per CTA
+constexpr int kMaxBlk = 1024;          // inputs per block of the max reduction
+
+// The cost is evaluated from coordinate differences, -k |x - y|^2 with
+// x - y formed first: the expanded form -k|x|^2 + 2k x.y - k|y|^2 needs fewer
+// operations but cancels exponent parts of size ~k |x|^2 in FP32, and at
+// eps = 1e-3 in three dimensions that noise kept the marginal violation above
+// 1e-6 (measured), so it is not used.
+
+__device__ __forceinline__ ff load_L_pt(const float2* W, const float2* lw, int64_t j, float2 inv_eps) {
+  const ff w = ffl(W[j]);
+  if (w.hi == -INFINITY) return ff_ninf();
+  return ff_add(ff_mul(w, ffl(inv_eps)), ffl(lw[j]));
+}
+
+// Per-block maxima of the high parts of L_j = W_j/eps + log w_j.
+__global__ void __launch_bounds__(256)
+    points_blockmax(const float2* __restrict__ W, const float2* __restrict__ lw, int nin,
+                    float2 inv_eps, float* __restrict__ bmax) {
+  __shared__ float red[8];
+  float m = -INFINITY;
+  const int j0 = blockIdx.x * kMaxBlk;
+  for (int j = j0 + threadIdx.x; j < min(nin, j0 + kMaxBlk); j += 256) m = fmaxf(m, load_L_pt(W, lw, j, inv_eps).hi);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float r = red[0];
+    for (int w = 1; w < 8; ++w) r = fmaxf(r, red[w]);
+    bmax[blockIdx.x] = r;
+  }
+}
+
+__device__ __forceinline__ float all_max(const float* bmax, int nb) {
+  float m = -INFINITY;
+  for (int b = 0; b < nb; ++b) m = fmaxf(m, bmax[b]);
+  return m;
+}
 
 struct PtArgs {
   const float* x;     // [nout][d]  output points
   const float* y;     // [nin][d]   input points
-  int d, nout, nin, chunk;
-  const float* Lt;    // [nin] (L_j - Lmax) log2(e), from prepare_L_ff
-  const float* Lmax;  // [1]
+  int d, nout, nin, chunk, nbmax;
+  const float2* W;    // [nin] float-float input potentials
+  const float2* lw;   // [nin] float-float log weights
+  float2 inv_eps;
+  const float* bmax;  // [nbmax] block maxima of L
   float k2;           // log2(e)/eps
   const float* zprev; // [nout] previous result (natural log), or NULL
   int use_prev;
@@ -85,12 +127,14 @@ __global__ void __launch_bounds__(kNW * 32)
   const int c = blockIdx.y;
   const int j0 = c * a.chunk, j1 = min(a.nin, j0 + a.chunk);
   const int d = a.d;
-  const float Lmax = *a.Lmax;
+  const float k2 = a.k2;
+  const float Lmax = all_max(a.bmax, a.nbmax);
   for (int j = j0 + tid; j < j1; j += kNW * 32) {
-    const float t = a.Lt[j];
+    const ff L = load_L_pt(a.W, a.lw, j, a.inv_eps);
     const float c0 = a.y[(int64_t)j * d];
     const float c1 = d > 1 ? a.y[(int64_t)j * d + 1] : 0.0f;
     const float c2 = d > 2 ? a.y[(int64_t)j * d + 2] : 0.0f;
+    const float t = (L.hi == -INFINITY || Lmax == -INFINITY) ? -INFINITY : ((L.hi - Lmax) + L.lo) * kLog2e;
     st[2 * (j - j0)] = make_float4(t, t, c0, c0);
     st[2 * (j - j0) + 1] = make_float4(c1, c1, c2, c2);
   }
@@ -109,7 +153,7 @@ __global__ void __launch_bounds__(kNW * 32)
   }
   const f2p XA0 = pk(xc[0][0], xc[0][1]), XA1 = pk(xc[1][0], xc[1][1]), XA2 = pk(xc[2][0], xc[2][1]);
   const f2p XB0 = pk(xc[0][2], xc[0][3]), XB1 = pk(xc[1][2], xc[1][3]), XB2 = pk(xc[2][2], xc[2][3]);
-  const f2p nk2 = pk(-a.k2, -a.k2);
+  const f2p nk2 = pk(-k2, -k2);
   const int nj = j1 - j0;
   float mq[4], sq[4];
   bool exact = !(a.use_prev && a.zprev);
@@ -202,9 +246,11 @@ __global__ void __launch_bounds__(kNW * 32)
 struct CombArgs {
   const float* x;
   const float* y;
-  int d, nout, nin, nchunks;
-  const float* Lt;
-  const float* Lmax;
+  int d, nout, nin, nchunks, nbmax;
+  const float2* W;
+  const float2* lw;
+  float2 inv_eps;
+  const float* bmax;
   float k2;
   const float2* part;
   float* zprev;  // written (NULL: not kept)
@@ -217,7 +263,7 @@ __global__ void __launch_bounds__(256)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int i = blockIdx.x * 8 + warp;
   float num = 0.0f, den = 0.0f;
-  const float Lmax = *a.Lmax;
+  const float Lmax = all_max(a.bmax, a.nbmax);
   if (i < a.nout) {
     float M = -INFINITY;
     for (int c = lane; c < a.nchunks; c += 32) {
@@ -239,27 +285,23 @@ __global__ void __launch_bounds__(256)
       float xi[3];
 #pragma unroll
       for (int k = 0; k < 3; ++k) xi[k] = (k < a.d) ? a.x[(int64_t)i * a.d + k] : 0.0f;
-      float m = -INFINITY;
-      for (int j = lane; j < a.nin; j += 32) {
+      auto arg = [&](int j) -> float {
+        const ff L = load_L_pt(a.W, a.lw, j, a.inv_eps);
+        if (L.hi == -INFINITY) return -INFINITY;
         float q = 0.0f;
         for (int k = 0; k < a.d; ++k) {
           const float t = xi[k] - a.y[(int64_t)j * a.d + k];
           q = fmaf(t, t, q);
         }
-        m = fmaxf(m, fmaf(-a.k2, q, a.Lt[j]));
-      }
+        return fmaf(-a.k2, q, ((L.hi - Lmax) + L.lo) * kLog2e);
+      };
+      float m = -INFINITY;
+      for (int j = lane; j < a.nin; j += 32) m = fmaxf(m, arg(j));
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
       float s = 0.0f;
       if (m != -INFINITY)
-        for (int j = lane; j < a.nin; j += 32) {
-          float q = 0.0f;
-          for (int k = 0; k < a.d; ++k) {
-            const float t = xi[k] - a.y[(int64_t)j * a.d + k];
-            q = fmaf(t, t, q);
-          }
-          s += ex2f(fmaf(-a.k2, q, a.Lt[j]) - m);
-        }
+        for (int j = lane; j < a.nin; j += 32) s += ex2f(arg(j) - m);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
       M = m;
@@ -284,10 +326,18 @@ __global__ void __launch_bounds__(256)
 int points_nchunks(int nin) { return (nin + 1023) / 1024; }
 
 cudaError_t launch_points(const float* x, const float* y, int d, int nout, int nin,
-                          const float* Lt, const float* Lmax, double eps, float* zprev,
-                          int use_prev, float2* part, const Epilogue& epi, cudaStream_t s) {
+                          const double* W, const double* logw, double eps, float* bmax,
+                          float* zprev, int use_prev, float2* part, const Epilogue& epi,
+                          cudaStream_t s) {
   const int nchunks = points_nchunks(nin);
   const int chunk = (nin + nchunks - 1) / nchunks;
+  const int nbmax = (nin + kMaxBlk - 1) / kMaxBlk;
+  const float2 inv_eps = ff2(ff_make(1.0 / eps));
+  const float2* Wf = reinterpret_cast<const float2*>(W);
+  const float2* lwf = reinterpret_cast<const float2*>(logw);
+  prof_mark_begin(PROF_ROWS, s);
+  count_launches(3);
+  points_blockmax<<<nbmax, 256, 0, s>>>(Wf, lwf, nin, inv_eps, bmax);
   PtArgs a;
   a.x = x;
   a.y = y;
@@ -295,8 +345,11 @@ cudaError_t launch_points(const float* x, const float* y, int d, int nout, int n
   a.nout = nout;
   a.nin = nin;
   a.chunk = chunk;
-  a.Lt = Lt;
-  a.Lmax = Lmax;
+  a.nbmax = nbmax;
+  a.W = Wf;
+  a.lw = lwf;
+  a.inv_eps = inv_eps;
+  a.bmax = bmax;
   a.k2 = (float)((double)kLog2e / eps);
   a.zprev = zprev;
   a.use_prev = use_prev;
@@ -305,8 +358,6 @@ cudaError_t launch_points(const float* x, const float* y, int d, int nout, int n
   cudaError_t e = cudaFuncSetAttribute(points_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid((nout + kOutBlk - 1) / kOutBlk, nchunks);
-  prof_mark_begin(PROF_ROWS, s);
-  count_launches(2);
   points_partial<<<grid, kNW * 32, smem, s>>>(a);
   CombArgs b;
   b.x = x;
@@ -315,8 +366,11 @@ cudaError_t launch_points(const float* x, const float* y, int d, int nout, int n
   b.nout = nout;
   b.nin = nin;
   b.nchunks = nchunks;
-  b.Lt = Lt;
-  b.Lmax = Lmax;
+  b.nbmax = nbmax;
+  b.W = Wf;
+  b.lw = lwf;
+  b.inv_eps = inv_eps;
+  b.bmax = bmax;
   b.k2 = a.k2;
   b.part = part;
   b.zprev = zprev;

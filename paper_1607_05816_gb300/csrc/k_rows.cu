@@ -260,18 +260,18 @@ cudaError_t launch_rows(int prec, const RowsGeom& g, int nrows, int nin, const d
   const int grid = (nrows + WARPS - 1) / WARPS;
   if (g.kind == UOT_GEOM_POINTS && (g.d < 1 || g.d > 8)) return cudaErrorInvalidValue;
   count_launches(2);
+  if (prec == UOT_F32 && g.kind == UOT_GEOM_POINTS && g.d <= 3 && part) {
+    // chunked point-cloud kernels; scratch_L holds the block maxima
+    count_launches(-2);
+    return launch_points((const float*)g.x, (const float*)g.y, g.d, nrows, nin, W, logw, eps,
+                         (float*)scratch_L, zprev, use_prev, reinterpret_cast<float2*>(part), epi, s);
+  }
   if (prec == UOT_F32) {
     float* Lt = (float*)scratch_L;
     float* Lmax = (float*)((char*)scratch_L + (((size_t)nin * 4 + 255) & ~(size_t)255));
     prepare_L_ff<1024><<<1, 1024, 0, s>>>(reinterpret_cast<const float2*>(W),
                                            reinterpret_cast<const float2*>(logw), nin,
                                            ff2(ff_make(1.0 / eps)), Lt, Lmax);
-    if (g.kind == UOT_GEOM_POINTS && g.d <= 3 && part) {
-      count_launches(-1);  // launch_points counts its own two kernels
-      cudaError_t e = launch_points((const float*)g.x, (const float*)g.y, g.d, nrows, nin, Lt, Lmax,
-                                    eps, zprev, use_prev, reinterpret_cast<float2*>(part), epi, s);
-      return e != cudaSuccess ? e : cudaGetLastError();
-    }
     prof_mark_begin(PROF_ROWS, s);
     const float* C = (const float*)g.C;
     const float* x = (const float*)g.x;

@@ -398,8 +398,9 @@ cudaError_t launch_rows(int prec, const RowsGeom& g, int nrows, int nin, const d
                         void* part = nullptr);
 int points_nchunks(int nin);
 cudaError_t launch_points(const float* x, const float* y, int d, int nout, int nin,
-                          const float* Lt, const float* Lmax, double eps, float* zprev,
-                          int use_prev, float2* part, const Epilogue& epi, cudaStream_t s);
+                          const double* W, const double* logw, double eps, float* bmax,
+                          float* zprev, int use_prev, float2* part, const Epilogue& epi,
+                          cudaStream_t s);
 
 // Persistent batched solver for many point-cloud problems (k_batch.cu).
 struct BatchArgs {

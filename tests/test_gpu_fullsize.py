@@ -134,3 +134,16 @@ def test_dense1d_alg1_2000_iterations():
     U2, V2, _ = U.solve(geo, *args, U.KL(1.0), U.KL(1.0), 1e-2, precision=U.F64, max_iter=2000)
     assert torch.max(torch.abs(U1 - U2)).item() <= 1e-10 * max(1.0, torch.max(torch.abs(U2)).item())
     assert torch.max(torch.abs(V1 - V2)).item() <= 1e-10 * max(1.0, torch.max(torch.abs(V2)).item())
+
+
+def test_points20000_solve_reaches_tolerance():
+    """The point-cloud benchmark's solve (KL 0.1, eps-scaling 1e-1 -> 1e-3,
+    tol 1e-6, FP32) converges: the FP32 arithmetic of the kernel must not put
+    a noise floor above the tolerance on the marginal violation."""
+    d = synth.problem_points(20000, 20000, 3, seed=1236)
+    geo = U.Geometry.points(torch.as_tensor(d["x"], dtype=torch.float32, device="cuda"),
+                            torch.as_tensor(d["y"], dtype=torch.float32, device="cuda"))
+    ins = [dev(d[k]) for k in ("p", "dx", "q", "dy")]
+    _, _, info = U.solve(geo, *ins, U.KL(0.1), U.KL(0.1), 1e-3, precision=U.F32, max_iter=5000, tol=1e-6,
+                         check_every=20, eps_start=1e-1, eps_stages=10, iters_per_stage=100)
+    assert info["status"] == "UOT_OK" and info["marg_err"] <= 1e-6, info
