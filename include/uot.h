@@ -117,6 +117,13 @@ typedef struct {
   int plain_scaling;   /* 1: Algorithm 1 (non-log scalings a, b on a stored kernel
                           K = exp(-C/eps)); dense geometry and UOT_F64 only.
                           0: log domain (Algorithm 2 with every update absorbed) */
+  int launch_mode;     /* 0: one launch per Gibbs pass (consecutive passes overlap through
+                          programmatic dependent launch), convergence tested by the host every
+                          check_every iterations;
+                          1: FP32 grid problems (batch 1) run as one persistent cooperative
+                          launch, eps stages and convergence test on the device, grid barriers
+                          between passes (measured slower at 256 x 256: 23.7k vs 39.5k it/s);
+                          other problems ignore it */
   const void* U0;      /* optional warm start [n] (NULL: U = 0) */
   const void* V0;      /* optional warm start [m] (NULL: V = 0, i.e. b = 1 as in Algorithm 1) */
 } uot_opts;

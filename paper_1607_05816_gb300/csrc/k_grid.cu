@@ -19,6 +19,8 @@
 // sum-of-exponentials sweep over the line for its R outputs.
 #include <string.h>
 
+#include <algorithm>
+
 #include "uot_internal.cuh"
 
 namespace uot {
@@ -163,16 +165,26 @@ __device__ __forceinline__ void epilogue_apply(const Epilogue& e, int64_t b, int
 
 constexpr int kLineRegs = 4;  // line elements held per thread (nin <= 1024 fast path)
 
-__global__ void __launch_bounds__(kNW * 32, 4)
-    grid_pass_f32(PassArgs a, Epilogue epi) {
-  extern __shared__ float4 sline[];  // nin x {t, t, y, y}
-  __shared__ float2 part[kNW][kOutCTA];
-  __shared__ float sshift[kOutCTA];
-  __shared__ float sred[kNW];
+// Shared-memory workspace of one work item.
+struct ItemSmem {
+  float4* sline;               // nin x {t, t, y, y}
+  float2 (*part)[kOutCTA];     // [kNW][kOutCTA]
+  float* sshift;               // [kOutCTA]
+  float* sred;                 // [kNW]
+};
+
+// One work item of a grid pass: line l of batch entry bz, outputs i0 .. i0+127.
+// With kPDL the item waits for the preceding kernel after its independent
+// prologue (programmatic dependent launch) and clears the violation
+// accumulators when asked.  Returns the item's violation terms in num, den.
+template <bool kPDL>
+__device__ __forceinline__ void grid_item_f32(const PassArgs& a, const Epilogue& epi, int l, int64_t bz,
+                                              int i0, const ItemSmem& sm, float& num, float& den) {
+  float4* sline = sm.sline;
+  float2 (*part)[kOutCTA] = sm.part;
+  float* sshift = sm.sshift;
+  float* sred = sm.sred;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int l = blockIdx.y;
-  const int64_t bz = blockIdx.z;
-  const int i0 = blockIdx.x * kOutCTA;
   const int nin = a.nin, nout = a.nout, nlines = a.nlines;
   const float2* in = a.in + bz * (int64_t)nlines * nin;
   const int64_t base = (int64_t)l * nin;
@@ -202,9 +214,11 @@ __global__ void __launch_bounds__(kNW * 32, 4)
     xq[q] = a.xo[i < nout ? i : nout - 1];
   }
 
-  pdl_wait();
-  if (a.zero_acc && blockIdx.x == 0 && blockIdx.y == 0 && tid < 2) a.zero_acc[2 * bz + tid] = 0.0;
-  pdl_launch_dependents();
+  if (kPDL) {
+    pdl_wait();
+    if (a.zero_acc && blockIdx.x == 0 && blockIdx.y == 0 && tid < 2) a.zero_acc[2 * bz + tid] = 0.0;
+    pdl_launch_dependents();
+  }
 
   // ---- line values: one read, kept in registers when the line is short ----
   ff lv[kLineRegs];
@@ -227,14 +241,14 @@ __global__ void __launch_bounds__(kNW * 32, 4)
 #pragma unroll
   for (int w = 1; w < kNW; ++w) mx = fmaxf(mx, sred[w]);
 
-  float num = 0.0f, den = 0.0f;
+  num = 0.0f;
+  den = 0.0f;
   if (mx == -INFINITY) {
     // b = 0 on the whole line: every sum is empty.
     if (owns) {
       if (zprev) zprev[my_pt] = -INFINITY;
       epilogue_apply(epi, bz, my_pt, ff_ninf(), pre, num, den);
     }
-    if (epi.err) block_add2f<kNW * 32>(num, den, epi.err + 2 * bz);
     return;
   }
   if (in_regs) {
@@ -343,8 +357,236 @@ __global__ void __launch_bounds__(kNW * 32, 4)
     }
     break;
   }
-  if (epi.err) block_add2f<kNW * 32>(num, den, epi.err + 2 * bz);
 }
+
+__global__ void __launch_bounds__(kNW * 32, 4)
+    grid_pass_f32(PassArgs a, Epilogue epi) {
+  extern __shared__ float4 sline[];
+  __shared__ float2 part[kNW][kOutCTA];
+  __shared__ float sshift[kOutCTA];
+  __shared__ float sred[kNW];
+  const ItemSmem sm{sline, part, sshift, sred};
+  float num, den;
+  grid_item_f32<true>(a, epi, blockIdx.y, blockIdx.z, blockIdx.x * kOutCTA, sm, num, den);
+  if (epi.err) block_add2f<kNW * 32>(num, den, epi.err + 2 * (int64_t)blockIdx.z);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent solve: the whole iteration of a single FP32 grid problem in one
+// cooperative launch (all CTAs co-resident).  Each pass is a set of work items
+// (line, 128 outputs) spread over the CTAs, followed by a grid barrier; the
+// eps-scaling stages and the convergence test run on the device, so the host
+// waits only for the end of the solve.  Barrier waits are bounded in time
+// (status[0] = 1 and every CTA returns if one expires).
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Generation-counting barrier: bar[0] arrivals, bar[1] generation.
+__device__ bool grid_barrier(unsigned* bar, int* status) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = bar + 1;
+    const unsigned g = *gen;
+    __threadfence();
+    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+      bar[0] = 0;
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      const unsigned long long t0 = global_ns();
+      while (*gen == g) {
+        __nanosleep(64);
+        if (global_ns() - t0 > 2000000000ull) {
+          atomicExch(status, 1);
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return *(volatile int*)status == 0;
+}
+
+struct PersistArgs {
+  int ndim;
+  int shape_x[UOT_MAX_DIM], shape_y[UOT_MAX_DIM];
+  const float* axes_x[UOT_MAX_DIM];
+  const float* axes_y[UOT_MAX_DIM];
+  float2* U;
+  float2* V;
+  const float2* logp;
+  const float2* logq;
+  const float2* logdx;
+  const float2* logdy;
+  float2* pass[2];
+  float* zbuf[2][UOT_MAX_DIM];
+  int nstage, iters_per_stage, max_iter, check_every;
+  double tol;
+  const float2* eps_ff;      // [nstage+1]
+  const float2* inv_eps_ff;  // [nstage+1]
+  const float* k2;           // [nstage+1]
+  const DivFF* F;            // [nstage+1][2]
+  double* acc;               // [2] violation accumulators
+  unsigned* bar;             // [2] barrier state (zero before the launch)
+  int* status;               // [4] timeout, converged, final iterations, total iterations
+  double* err_out;           // last measured violation
+};
+
+__global__ void __launch_bounds__(kNW * 32, 4)
+    grid_solve_persistent(PersistArgs P) {
+  extern __shared__ float4 sline[];
+  __shared__ float2 part[kNW][kOutCTA];
+  __shared__ float sshift[kOutCTA];
+  __shared__ float sred[kNW];
+  const ItemSmem sm{sline, part, sshift, sred};
+  const int d = P.ndim;
+  if (blockIdx.x == 0 && threadIdx.x < 2) P.acc[threadIdx.x] = 0.0;
+  if (!grid_barrier(P.bar, P.status)) return;
+  int total = 0, it_final = 0;
+  bool stop = false;
+  for (int s = 0; s <= P.nstage && !stop; ++s) {
+    const int iters = (s < P.nstage) ? P.iters_per_stage : P.max_iter;
+    const bool final_stage = (s == P.nstage);
+    for (int it = 0; it < iters; ++it) {
+      const bool check = final_stage && (((it + 1) % P.check_every == 0) || it == iters - 1);
+      for (int pidx = 0; pidx < 2 * d; ++pidx) {
+        const int dir = pidx / d, k = pidx % d, ax = d - 1 - k;
+        const int* in_shape = dir == 0 ? P.shape_y : P.shape_x;
+        const int* out_shape = dir == 0 ? P.shape_x : P.shape_y;
+        int nlines = 1;
+        for (int t = 0; t < ax; ++t) nlines *= in_shape[t];
+        for (int t = ax + 1; t < d; ++t) nlines *= out_shape[t];
+        PassArgs a;
+        a.in = (k == 0) ? (dir == 0 ? P.V : P.U) : P.pass[(k - 1) & 1];
+        a.logw = dir == 0 ? P.logdy : P.logdx;
+        a.in_is_pot = (k == 0);
+        a.nlines = nlines;
+        a.nin = in_shape[ax];
+        a.nout = out_shape[ax];
+        a.yi = dir == 0 ? P.axes_y[ax] : P.axes_x[ax];
+        a.xo = dir == 0 ? P.axes_x[ax] : P.axes_y[ax];
+        a.inv_eps = P.inv_eps_ff[s];
+        a.k2 = P.k2[s];
+        a.zprev = P.zbuf[dir][k];
+        a.use_prev = it > 0;
+        a.zero_acc = nullptr;
+        Epilogue e;
+        memset(&e, 0, sizeof(e));
+        e.ff = 1;
+        e.eps_ff = P.eps_ff[s];
+        e.inv_eps_ff = P.inv_eps_ff[s];
+        if (k < d - 1) {
+          e.mode = EPI_RAW;
+          e.out = reinterpret_cast<double*>(P.pass[k & 1]);
+        } else {
+          e.mode = EPI_PROX;
+          e.Fff = P.F[2 * s + dir];
+          e.logp = reinterpret_cast<const double*>(dir == 0 ? P.logp : P.logq);
+          e.pot = reinterpret_cast<double*>(dir == 0 ? P.U : P.V);
+          e.logw = reinterpret_cast<const double*>(dir == 0 ? P.logdx : P.logdy);
+          e.err = (dir == 0 && check) ? P.acc : nullptr;
+        }
+        const int nob = (a.nout + kOutCTA - 1) / kOutCTA;
+        const int items = nlines * nob;
+        for (int item = blockIdx.x; item < items; item += gridDim.x) {
+          float num, den;
+          grid_item_f32<false>(a, e, item / nob, 0, (item % nob) * kOutCTA, sm, num, den);
+          if (e.err) block_add2f<kNW * 32>(num, den, e.err);
+        }
+        if (!grid_barrier(P.bar, P.status)) return;
+      }
+      ++total;
+      if (final_stage) it_final = it + 1;
+      if (check) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+          volatile double* acc = P.acc;
+          const double num = acc[0], den = acc[1];
+          const double err = (den > 0.0) ? num / den : 0.0;
+          *P.err_out = err;
+          P.status[1] = (it > 0 && P.tol > 0.0 && err <= P.tol) ? 1 : 0;
+          acc[0] = 0.0;
+          acc[1] = 0.0;
+        }
+        if (!grid_barrier(P.bar, P.status)) return;
+        if (*(volatile int*)(P.status + 1)) {
+          stop = true;
+          break;
+        }
+      }
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    P.status[2] = it_final;
+    P.status[3] = total;
+  }
+}
+
+}  // namespace
+
+int grid_solve_persistent_ctas(int nin_max) {
+  int nb = 0, dev = 0, sms = 0;
+  const size_t smem = (size_t)nin_max * sizeof(float4);
+  if (smem > 48 * 1024 &&
+      cudaFuncSetAttribute(grid_solve_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, grid_solve_persistent, kNW * 32, smem) != cudaSuccess) return 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  return nb * sms;
+}
+
+cudaError_t launch_grid_solve_persistent(const PersistLaunch& L, int grid, cudaStream_t s) {
+  PersistArgs P;
+  memset(&P, 0, sizeof(P));
+  P.ndim = L.ndim;
+  for (int k = 0; k < UOT_MAX_DIM; ++k) {
+    P.shape_x[k] = L.shape_x[k];
+    P.shape_y[k] = L.shape_y[k];
+    P.axes_x[k] = (const float*)L.axes_x[k];
+    P.axes_y[k] = (const float*)L.axes_y[k];
+    P.zbuf[0][k] = L.zbuf[0][k];
+    P.zbuf[1][k] = L.zbuf[1][k];
+  }
+  P.U = reinterpret_cast<float2*>(L.U);
+  P.V = reinterpret_cast<float2*>(L.V);
+  P.logp = reinterpret_cast<const float2*>(L.logp);
+  P.logq = reinterpret_cast<const float2*>(L.logq);
+  P.logdx = reinterpret_cast<const float2*>(L.logdx);
+  P.logdy = reinterpret_cast<const float2*>(L.logdy);
+  P.pass[0] = reinterpret_cast<float2*>(L.pass[0]);
+  P.pass[1] = reinterpret_cast<float2*>(L.pass[1]);
+  P.nstage = L.nstage;
+  P.iters_per_stage = L.iters_per_stage;
+  P.max_iter = L.max_iter;
+  P.check_every = L.check_every;
+  P.tol = L.tol;
+  P.eps_ff = L.eps_ff;
+  P.inv_eps_ff = L.inv_eps_ff;
+  P.k2 = L.k2;
+  P.F = L.F;
+  P.acc = L.acc;
+  P.bar = L.bar;
+  P.status = L.status;
+  P.err_out = L.err_out;
+  int nin_max = 1;
+  for (int k = 0; k < L.ndim; ++k) nin_max = std::max(nin_max, std::max(L.shape_x[k], L.shape_y[k]));
+  const size_t smem = (size_t)nin_max * sizeof(float4);
+  cudaError_t e = cudaFuncSetAttribute(grid_solve_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  void* args[] = {&P};
+  count_launches(1);
+  e = cudaLaunchCooperativeKernel((const void*)grid_solve_persistent, dim3(grid), dim3(kNW * 32), args, smem, s);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+namespace {
 
 // FP64 arithmetic throughout.
 template <int R, int WARPS>

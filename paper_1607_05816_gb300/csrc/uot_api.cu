@@ -828,6 +828,20 @@ uot_status solve_impl(const uot_geom* g, int batch, const void* p, const void* d
   sc.reserve<double>(m);   // logdy
   sc.reserve<double>(bm);  // V
   sc.reserve<double>(2 * (size_t)batch + 4);  // err accumulators + flag
+  // one persistent cooperative launch for FP32 grid problems
+  const std::vector<Stage> stages_p = eps_schedule(*o);
+  const int nst = (int)stages_p.size();
+  const bool persist = o->launch_mode == 1 && prec == UOT_F32 && g->kind == UOT_GEOM_GRID &&
+                       batch == 1 && !o->plain_scaling;
+  if (persist) {
+    sc.reserve<float2>(nst + 1);   // eps
+    sc.reserve<float2>(nst + 1);   // 1/eps
+    sc.reserve<float>(nst + 1);    // log2(e)/eps
+    sc.reserve<DivFF>(2 * (nst + 1));
+    sc.reserve<unsigned>(2);       // barrier
+    sc.reserve<int>(4);            // status
+    sc.reserve<double>(1);         // last violation
+  }
   if (o->plain_scaling) {
     sc.reserve<double>((size_t)n * m);  // K
     sc.reserve<double>((size_t)n * m);  // K^T
@@ -881,7 +895,96 @@ uot_status solve_impl(const uot_geom* g, int batch, const void* p, const void* d
     }
     return cudaSuccess;
   };
-  if (!o->plain_scaling) {
+  if (persist) {
+    std::vector<float2> heps(nst + 1), hieps(nst + 1);
+    std::vector<float> hk2(nst + 1);
+    std::vector<DivFF> hF(2 * (nst + 1));
+    for (int sidx = 0; sidx <= nst; ++sidx) {
+      const double e = (sidx < nst) ? stages_p[sidx].eps : o->eps;
+      heps[sidx] = ff2(ff_make(e));
+      hieps[sidx] = ff2(ff_make(1.0 / e));
+      hk2[sidx] = (float)((double)kLog2e / e);
+      hF[2 * sidx] = make_div_ff(D1, e);
+      hF[2 * sidx + 1] = make_div_ff(D2, e);
+    }
+    float2* d_eps = sc.take<float2>(nst + 1);
+    float2* d_ieps = sc.take<float2>(nst + 1);
+    float* d_k2 = sc.take<float>(nst + 1);
+    DivFF* d_F = sc.take<DivFF>(2 * (nst + 1));
+    unsigned* d_bar = sc.take<unsigned>(2);
+    int* d_status = sc.take<int>(4);
+    double* d_err = sc.take<double>(1);
+    UOT_SCRATCH_OK(sc);
+    UOT_CK(cudaMemcpyAsync(d_eps, heps.data(), heps.size() * sizeof(float2), cudaMemcpyHostToDevice, s));
+    UOT_CK(cudaMemcpyAsync(d_ieps, hieps.data(), hieps.size() * sizeof(float2), cudaMemcpyHostToDevice, s));
+    UOT_CK(cudaMemcpyAsync(d_k2, hk2.data(), hk2.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+    UOT_CK(cudaMemcpyAsync(d_F, hF.data(), hF.size() * sizeof(DivFF), cudaMemcpyHostToDevice, s));
+    UOT_CK(cudaMemsetAsync(d_bar, 0, 2 * sizeof(unsigned), s));
+    UOT_CK(cudaMemsetAsync(d_status, 0, 4 * sizeof(int), s));
+    UOT_CK(cudaMemsetAsync(d_err, 0, sizeof(double), s));
+    PersistLaunch L;
+    memset(&L, 0, sizeof(L));
+    L.ndim = g->ndim;
+    int nin_max = 1;
+    int64_t max_items = 1;
+    for (int k = 0; k < g->ndim; ++k) {
+      L.shape_x[k] = g->shape_x[k];
+      L.shape_y[k] = g->shape_y[k];
+      L.axes_x[k] = g->axes_x[k];
+      L.axes_y[k] = g->axes_y[k];
+      L.zbuf[0][k] = G.zbuf[0][k];
+      L.zbuf[1][k] = G.zbuf[1][k];
+      nin_max = std::max(nin_max, std::max(g->shape_x[k], g->shape_y[k]));
+    }
+    for (int dir = 0; dir < 2; ++dir) {
+      const int* in_shape = dir == 0 ? g->shape_y : g->shape_x;
+      const int* out_shape = dir == 0 ? g->shape_x : g->shape_y;
+      for (int ax = 0; ax < g->ndim; ++ax) {
+        int64_t nl = 1;
+        for (int t = 0; t < ax; ++t) nl *= in_shape[t];
+        for (int t = ax + 1; t < g->ndim; ++t) nl *= out_shape[t];
+        max_items = std::max<int64_t>(max_items, nl * ((out_shape[ax] + 127) / 128));
+      }
+    }
+    L.U = U;
+    L.V = V;
+    L.logp = logp;
+    L.logq = logq;
+    L.logdx = logdx;
+    L.logdy = logdy;
+    L.pass[0] = G.pass[0];
+    L.pass[1] = G.pass[1];
+    L.nstage = nst;
+    L.iters_per_stage = o->iters_per_stage;
+    L.max_iter = o->max_iter;
+    L.check_every = check_every;
+    L.tol = o->tol;
+    L.eps_ff = d_eps;
+    L.inv_eps_ff = d_ieps;
+    L.k2 = d_k2;
+    L.F = d_F;
+    L.acc = acc;
+    L.bar = d_bar;
+    L.status = d_status;
+    L.err_out = d_err;
+    const int cap = grid_solve_persistent_ctas(nin_max);
+    if (cap < 1) return UOT_EUNSUPPORTED;
+    const int grid = (int)std::min<int64_t>(cap, max_items);
+    UOT_CK(launch_grid_solve_persistent(L, grid, s));
+    int hs[4];
+    double herr = 0.0;
+    UOT_CK(cudaMemcpyAsync(hs, d_status, sizeof(hs), cudaMemcpyDeviceToHost, s));
+    UOT_CK(cudaMemcpyAsync(&herr, d_err, sizeof(double), cudaMemcpyDeviceToHost, s));
+    UOT_CK(cudaStreamSynchronize(s));
+    if (hs[0]) {
+      g_last_error = "persistent solve: a grid barrier wait expired";
+      return UOT_TIMEOUT;
+    }
+    converged = hs[1] != 0;
+    it = hs[2];
+    total = hs[3];
+    err = (o->max_iter > 0) ? herr : INFINITY;
+  } else if (!o->plain_scaling) {
     auto iteration = [&](double eps, bool check) -> cudaError_t {
       cudaError_t e;
       Epilogue e1 = prox_epilogue(D1, logp, U, logdx, check ? acc : nullptr, eps);

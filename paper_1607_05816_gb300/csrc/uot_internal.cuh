@@ -371,6 +371,35 @@ cudaError_t launch_grid_pass(int prec, const double* in, const double* logw, int
                              double eps, int nbatch, const Epilogue& epi, cudaStream_t s,
                              float* zprev, int use_prev, double* zero_acc = nullptr);
 
+// Persistent FP32 grid solve (k_grid.cu): the whole iteration, eps stages and
+// convergence test of one grid problem in one cooperative launch.
+struct PersistLaunch {
+  int ndim;
+  int shape_x[UOT_MAX_DIM], shape_y[UOT_MAX_DIM];
+  const void* axes_x[UOT_MAX_DIM];
+  const void* axes_y[UOT_MAX_DIM];
+  double* U;            // float-float state in 8-byte slots
+  double* V;
+  const double* logp;
+  const double* logq;
+  const double* logdx;
+  const double* logdy;
+  double* pass[2];
+  float* zbuf[2][UOT_MAX_DIM];
+  int nstage, iters_per_stage, max_iter, check_every;
+  double tol;
+  const float2* eps_ff;
+  const float2* inv_eps_ff;
+  const float* k2;
+  const DivFF* F;       // [nstage+1][2]
+  double* acc;
+  unsigned* bar;
+  int* status;
+  double* err_out;
+};
+int grid_solve_persistent_ctas(int nin_max);
+cudaError_t launch_grid_solve_persistent(const PersistLaunch& L, int grid, cudaStream_t s);
+
 // Tensor-core (tcgen05) variant of the FP32 grid pass (k_grid_tc.cu); float-
 // float lines in, same epilogues; valid while k (2 r)^2 stays in range (see
 // grid_tc_valid).  err_flag is set if a bounded wait gave up.

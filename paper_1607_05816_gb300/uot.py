@@ -51,7 +51,7 @@ class COpts(C.Structure):
     _fields_ = [("precision", C.c_int), ("eps", C.c_double), ("eps_start", C.c_double),
                 ("eps_stages", C.c_int), ("iters_per_stage", C.c_int), ("max_iter", C.c_int),
                 ("tol", C.c_double), ("check_every", C.c_int), ("plain_scaling", C.c_int),
-                ("U0", C.c_void_p), ("V0", C.c_void_p)]
+                ("launch_mode", C.c_int), ("U0", C.c_void_p), ("V0", C.c_void_p)]
 
 
 class CBatchProblem(C.Structure):
@@ -286,7 +286,8 @@ def _check(status, what):
 
 def solve(geom: Geometry, p, dx, q, dy, F1: Div, F2: Div, eps: float, *, precision=F64,
           max_iter=1000, tol=0.0, check_every=10, eps_start=None, eps_stages=10,
-          iters_per_stage=100, plain_scaling=False, U0=None, V0=None, U=None, V=None):
+          iters_per_stage=100, plain_scaling=False, U0=None, V0=None, U=None, V=None,
+          launch_mode=0):
     """uot_solve: returns (U, V, result dict).  Inputs are CUDA tensors of the
     precision's dtype; U, V (optional) are preallocated outputs."""
     lib = load()
@@ -295,7 +296,7 @@ def solve(geom: Geometry, p, dx, q, dy, F1: Div, F2: Div, eps: float, *, precisi
     V = torch.empty(geom.m, dtype=dt, device=p.device) if V is None else V
     o = COpts(precision, float(eps), float(eps_start) if eps_start else 0.0, int(eps_stages),
               int(iters_per_stage), int(max_iter), float(tol), int(check_every),
-              int(bool(plain_scaling)), _ptr(U0, dt, "U0"), _ptr(V0, dt, "V0"))
+              int(bool(plain_scaling)), int(launch_mode), _ptr(U0, dt, "U0"), _ptr(V0, dt, "V0"))
     r = CResult()
     g = geom.c(precision)
     st = lib.uot_solve(C.byref(g), _ptr(p, dt, "p"), _ptr(dx, dt, "dx"), _ptr(q, dt, "q"),
@@ -317,7 +318,7 @@ def solve_many(geom: Geometry, P, dx, Q, dy, F1: Div, F2: Div, eps, *, precision
     U = torch.empty(B, geom.n, dtype=dt, device=P.device) if U is None else U
     V = torch.empty(B, geom.m, dtype=dt, device=P.device) if V is None else V
     o = COpts(precision, float(eps), float(eps_start) if eps_start else 0.0, int(eps_stages),
-              int(iters_per_stage), int(max_iter), float(tol), int(check_every), 0,
+              int(iters_per_stage), int(max_iter), float(tol), int(check_every), 0, 0,
               _ptr(U0, dt, "U0"), _ptr(V0, dt, "V0"))
     r = CResult()
     g = geom.c(precision)
@@ -397,7 +398,7 @@ def barycenter(geom: Geometry, alpha, P, dx, dy, F1: Div, lam, eps, *, kind=BARY
     V = torch.empty(K, geom.m, dtype=dt, device=P.device)
     a = (C.c_double * K)(*[float(v) for v in alpha])
     o = COpts(precision, float(eps), float(eps_start) if eps_start else 0.0, int(eps_stages),
-              int(iters_per_stage), int(max_iter), float(tol), int(check_every), 0, None, None)
+              int(iters_per_stage), int(max_iter), float(tol), int(check_every), 0, 0, None, None)
     r = CResult()
     g = geom.c(precision)
     st = lib.uot_barycenter(C.byref(g), K, a, _ptr(P, dt, "P"), _ptr(dx, dt, "dx"),
@@ -427,7 +428,7 @@ def solve_batch(sizes, divs, d, x, p, dx, y, q, dy, eps, *, max_iter=1000, tol=0
     iters = (C.c_int * nprob)()
     errs = (C.c_double * nprob)()
     o = COpts(F32, float(eps), float(eps_start) if eps_start else 0.0, int(eps_stages),
-              int(iters_per_stage), int(max_iter), float(tol), int(check_every), 0, None, None)
+              int(iters_per_stage), int(max_iter), float(tol), int(check_every), 0, 0, None, None)
     r = CResult()
     st = lib.uot_solve_batch(nprob, arr, int(d), _ptr(x, dt, "x"), _ptr(p, dt, "p"),
                              _ptr(dx, dt, "dx"), _ptr(y, dt, "y"), _ptr(q, dt, "q"),

@@ -319,3 +319,22 @@ def test_invalid_arguments_rejected():
         gp = grid_problem((8,), (8,), 1)
         U.solve(gp[1](U.F64), T(gp[4], U.F64), T(gp[2], U.F64), T(gp[5], U.F64), T(gp[3], U.F64),
                 U.KL(1.0), U.KL(1.0), 0.1, plain_scaling=True)
+
+
+@pytest.mark.parametrize("shape", [(48, 64), (9, 13, 6), (300,)])
+def test_persistent_launch_matches_per_pass_launches(shape):
+    """The persistent cooperative solve and the one-launch-per-pass solve run
+    the same arithmetic: identical iterates, the same stopping iteration and
+    violation (eps-scaling, tolerance stop)."""
+    og, lg, dx, dy, p, q = grid_problem(shape, shape, 31, zeros=False)
+    args = [T(a, U.F32).ravel() for a in (p, dx, q, dy)]
+    outs = []
+    for mode in (1, 0):
+        outs.append(U.solve(lg(U.F32), *args, U.KL(0.5), U.KL(0.5), 2e-3, precision=U.F32, max_iter=3000,
+                            tol=1e-5, check_every=10, eps_start=0.1, eps_stages=5, iters_per_stage=20,
+                            launch_mode=mode))
+    (U0, V0, i0), (U1, V1, i1) = outs
+    assert i0["iters"] == i1["iters"] and i0["total_iters"] == i1["total_iters"]
+    assert i0["status"] == i1["status"] == "UOT_OK"
+    assert abs(i0["marg_err"] - i1["marg_err"]) <= 1e-9
+    assert torch.equal(U0, U1) and torch.equal(V0, V1)
