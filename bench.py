@@ -49,6 +49,34 @@ SM_COUNT, MUFU_PER_CLK, SM_MAX_MHZ = 152, 32, 2070.0
 MUFU_PEAK_GEXP = SM_COUNT * MUFU_PER_CLK * SM_MAX_MHZ * 1e6 / 1e9
 # FP64 pipe (Algorithm 1 matvec): GB300 runs FP64 at 1.25 TFLOP/s nominal.
 FP64_PEAK_GFLOPS = 1250.0
+# FP32 pipe: 128 lanes per clock per SM (FADD/FMUL/FFMA; a packed f32x2
+# instruction occupies it for two lane-slots per pair).
+FP32_PER_CLK = 128
+FP32_PEAK_GOPS = SM_COUNT * FP32_PER_CLK * SM_MAX_MHZ * 1e6 / 1e9
+# FP32-pipe operations per kernel term exp(t_j - k|x_i - y_j|^2 - m_i) summed
+# into a running sum, as the kernels evaluate it: grid pass (1-D) sub, mul,
+# sub, fma, add = 5; point clouds d = 3: 3 sub, mul, 2 fma, sub, fma, add = 9;
+# d = 2: 7.
+FP32_OPS_PER_TERM = {"grid": 5, "points3": 9, "points2": 7}
+
+
+def alu_roofline(kernel, achieved_gexp, fp32_ops, timing, **extra):
+    """Roofline of an exponential-sum kernel: each term needs one MUFU.EX2 and
+    fp32_ops FP32-pipe operations, so its ceiling is the slower of the two
+    units; `achieved` and `peak` are terms (= exponentials) per second."""
+    mufu = MUFU_PEAK_GEXP
+    fp32 = FP32_PEAK_GOPS / fp32_ops
+    peak = min(mufu, fp32)
+    d = {"bound": "alu", "kernel": kernel, "achieved": achieved_gexp, "peak": peak, "unit": "Gexp2/s",
+         "frac": achieved_gexp / peak, "traffic": None,
+         "binding_pipe": "fp32" if fp32 < mufu else "mufu",
+         "pipes": {"mufu_ex2": {"peak_gexp": mufu, "frac": achieved_gexp / mufu},
+                   "fp32": {"ops_per_term": fp32_ops, "peak_gops": FP32_PEAK_GOPS,
+                            "frac": achieved_gexp * fp32_ops / FP32_PEAK_GOPS}},
+         "peak_source": "derived: 152 SMs x 2070 MHz x (32 MUFU.EX2/clk | 128 FP32 lanes/clk / ops per term)",
+         "timing": timing}
+    d.update(extra)
+    return d
 
 WORKLOAD = "grid2d-256x256-kl0.5-epsscale1e-1to1e-3-tol1e-6"
 # dram__bytes_read.sum + dram__bytes_write.sum of one grid_pass_f32 launch on
@@ -144,6 +172,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     uot.load()
+    uot.force_grid_tile(args.grid_tile)
     prec = {"f32": uot.F32, "f64": uot.F64, "mixed": uot.MIXED}[args.precision]
     dt = torch.float64 if prec == uot.F64 else torch.float32
     d = inputs(SEED + rank)
@@ -163,7 +192,8 @@ def run_ours(args, rank, world, local_rank):
     def step(Uo=Ub, Vo=Vb, pp=p, dxx=dx, qq=q, dyy=dy, g=geo):
         return uot.solve(g, pp, dxx, qq, dyy, uot.KL(LAM), uot.KL(LAM), EPS, precision=prec,
                          max_iter=max_iter, tol=TOL, check_every=CHECK_EVERY,
-                         eps_start=EPS_START, eps_stages=stages, iters_per_stage=IPS, U=Uo, V=Vo)
+                         eps_start=EPS_START, eps_stages=stages, iters_per_stage=IPS, U=Uo, V=Vo,
+                         launch_mode=args.launch_mode)
 
     for _ in range(args.warmup):
         step()
@@ -276,22 +306,19 @@ def run_ours(args, rank, world, local_rank):
         "vs_baseline": None,
         "dtype": {uot.F32: "f32", uot.F64: "f64", uot.MIXED: "bf16-mma/f32"}[prec],
         "data": "synthetic",
-        "config": config_dict({"precision": args.precision}),
+        "config": config_dict({"precision": args.precision, "launch_mode": args.launch_mode}),
         "e2e": {"value": all_e2e_iters / (e2e_ms_max / 1e3) if e2e_ms_max > 0 else None, "unit": "iters/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "clocks": clocks,
-        "roofline": {"bound": "alu", "kernel": {uot.F32: "grid_pass_f32", uot.F64: "grid_pass_f64", uot.MIXED: "grid_pass_tc"}[prec],
-                     "achieved": achieved, "peak": MUFU_PEAK_GEXP, "unit": "Gexp2/s",
-                     "frac": achieved / MUFU_PEAK_GEXP,
-                     "traffic": None,
-                     "launches_per_step": launches_per_step,
-                     "pipelined_launch_us": eff_launch_ms * 1e3,
-                     "isolated_launch_us": avg_kern_ms * 1e3,
-                     "timing": "achieved from CUDA events over the timed steps / grid-pass launches; "
-                               "isolated_launch_us brackets each launch with events in one extra step "
-                               "(this serialises the overlapped launches)",
-                     "peak_source": "derived: 152 SMs x 32 MUFU.EX2/clk x 2070 MHz"},
+        "roofline": alu_roofline(
+            {uot.F32: "grid_pass_f32", uot.F64: "grid_pass_f64", uot.MIXED: "grid_pass_tc"}[prec], achieved,
+            FP32_OPS_PER_TERM["grid"],
+            "achieved from CUDA events over the timed steps / grid-pass launches; isolated_launch_us "
+            "brackets each launch with events in one extra step (this serialises the overlapped launches)",
+            launches_per_step=launches_per_step, pipelined_launch_us=eff_launch_ms * 1e3,
+            isolated_launch_us=avg_kern_ms * 1e3),
+        "grid_tiles": uot.autotune_table().strip().splitlines(),
     }
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_iters)
@@ -314,6 +341,7 @@ def run_single(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     uot.load()
+    uot.force_grid_tile(args.grid_tile)
     f = lambda a, dt=torch.float32: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
     wl = args.workload
     if wl == "points":
@@ -324,7 +352,8 @@ def run_single(args, rank, world, local_rank):
 
         def step():
             return uot.solve(geo, *ins, F, F, 1e-3, precision=uot.F32, max_iter=MAX_ITER, tol=TOL,
-                             check_every=CHECK_EVERY, eps_start=1e-1, eps_stages=10, iters_per_stage=100)
+                             check_every=CHECK_EVERY, eps_start=1e-1, eps_stages=10, iters_per_stage=100,
+                             launch_mode=args.launch_mode)
         work_per_iter, unit_work, kernel = 2.0 * 20000 * 20000, "Gexp2/s", "points_partial"
         cfg = {"workload": f"points3d-20000x20000-{args.penalty}0.1-epsscale1e-1to1e-3-tol1e-6",
                "n": 20000, "m": 20000, "d": 3}
@@ -383,7 +412,6 @@ def run_single(args, rank, world, local_rank):
     if rank != 0:
         return
     achieved = work_per_iter * iters / (total_ms / 1e3) / 1e9
-    peak = MUFU_PEAK_GEXP if unit_work == "Gexp2/s" else FP64_PEAK_GFLOPS
     cfg.update({"l2": "flushed between steps (256 MB write)", "parallelism": "replicas"})
     line = {
         "metric": "sinkhorn_iters_per_s", "value": iters / (total_ms / 1e3), "unit": "iters/s",
@@ -391,10 +419,17 @@ def run_single(args, rank, world, local_rank):
         "iters_per_step": iters / args.steps, "final_marg_err": max(errs), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic", "config": cfg,
         "gpu_launches": launches, "clocks": clocks,
-        "roofline": {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peak,
-                     "unit": unit_work, "frac": achieved / peak, "traffic": None,
-                     "timing": "algorithmic work of all iterations / CUDA-event time of the timed steps"},
     }
+    timing = "algorithmic work of all iterations / CUDA-event time of the timed steps"
+    if unit_work == "Gexp2/s":
+        line["roofline"] = alu_roofline(kernel, achieved, FP32_OPS_PER_TERM["points3" if wl == "points" else "grid"],
+                                        timing)
+        if wl == "bary":
+            line["grid_tiles"] = uot.autotune_table().strip().splitlines()
+    else:
+        line["roofline"] = {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": FP64_PEAK_GFLOPS,
+                            "unit": unit_work, "frac": achieved / FP64_PEAK_GFLOPS, "traffic": None,
+                            "timing": timing}
     print(json.dumps(line), flush=True)
 
 
@@ -413,6 +448,7 @@ def run_batch(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     uot.load()
+    uot.force_grid_tile(args.grid_tile)
     nprob = args.batch_nprob or BATCH_NPROB
     probs = synth.batch_points(nprob=nprob, size=BATCH_SIZE, d=2, seed=1238 + rank)
     sizes = [(len(pr["x"]), len(pr["y"])) for pr in probs]
@@ -467,10 +503,8 @@ def run_batch(args, rank, world, local_rank):
                    "nprob": nprob, "sum_nm": int(sum(n * m for n, m in sizes)),
                    "l2": "flushed between steps (256 MB write)", "parallelism": "replicas"},
         "gpu_launches": launches, "clocks": clocks,
-        "roofline": {"bound": "alu", "kernel": "batch_solve", "achieved": achieved,
-                     "peak": MUFU_PEAK_GEXP, "unit": "Gexp2/s", "frac": achieved / MUFU_PEAK_GEXP,
-                     "traffic": None,
-                     "timing": "exponentials of all problems' iterations / CUDA-event time of the launch"},
+        "roofline": alu_roofline("batch_solve", achieved, FP32_OPS_PER_TERM["points2"],
+                                 "exponentials of all problems' iterations / CUDA-event time of the launch"),
     }
     print(json.dumps(line), flush=True)
 
@@ -538,6 +572,10 @@ def main():
     ap.add_argument("--workload", default="grid2d", choices=["grid2d", "batch", "points", "dense1d", "bary"])
     ap.add_argument("--penalty", default="kl", choices=["kl", "tv"])
     ap.add_argument("--batch-nprob", type=int, default=0)
+    ap.add_argument("--launch-mode", type=int, default=2, choices=[0, 1, 2],
+                    help="0 one launch per pass, 1 persistent solve, 2 CUDA-graph blocks")
+    ap.add_argument("--grid-tile", type=int, default=-1,
+                    help="force one FP32 grid-pass tile shape (default: the tuner's choice)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

@@ -123,7 +123,11 @@ typedef struct {
                           1: FP32 grid problems (batch 1) run as one persistent cooperative
                           launch, eps stages and convergence test on the device, grid barriers
                           between passes (measured slower at 256 x 256: 23.7k vs 39.5k it/s);
-                          other problems ignore it */
+                          other problems ignore it;
+                          2: as 0, but once a block of check_every iterations at the final eps
+                          repeats the same launches (shifts from the previous iteration), it
+                          is captured once as a CUDA graph and replayed block by block (log
+                          domain, all geometries; per-pass launches where capture fails) */
   const void* U0;      /* optional warm start [n] (NULL: U = 0) */
   const void* V0;      /* optional warm start [m] (NULL: V = 0, i.e. b = 1 as in Algorithm 1) */
 } uot_opts;
@@ -156,6 +160,33 @@ const char* uot_last_error(void);
 long long uot_launch_count(void);
 void uot_profile_begin(void);
 uot_status uot_profile_end(int family, double* total_ms, long long* launches);
+
+/*
+ * Tile-shape tuner of the FP32 separable grid pass (a schedule choice, not
+ * part of the method: every shape computes the same sums of Sec. 4.4 up to
+ * FP32 rounding order).  A tile is (warps splitting the contraction index,
+ * outputs per lane); the first time a pass shape (lines, inputs, outputs,
+ * batch) is met on a device, every tile is timed on scratch inputs of that
+ * shape with CUDA events (this synchronises the stream once and allocates
+ * stream-ordered scratch); the fastest is kept for the process lifetime,
+ * except that the first tile stays unless another is more than 5% faster.
+ * No tuning happens inside a stream capture or in uot_gibbs_log_noalloc: the
+ * first tile is used there until the shape has been tuned elsewhere.
+ *
+ * uot_set_autotune(mode): 1 (default) = tune on first use; 0 = always the
+ *   first tile (results then do not depend on timing).  Returns the previous mode.
+ * uot_force_grid_tile(idx): use tile idx (0 .. uot_grid_tile_count()-1) for
+ *   every FP32 grid pass; idx = -1 returns to the tuned choice.  UOT_EINVAL if
+ *   idx is out of range.
+ * uot_autotune_table(buf, len): writes the tuned shapes, the chosen tile and
+ *   every tile's measured time per launch as text (one line per pass shape,
+ *   NUL-terminated, truncated to len-1 bytes); returns the full text length.
+ * Process-wide settings, guarded by a mutex.
+ */
+int uot_set_autotune(int mode);
+uot_status uot_force_grid_tile(int idx);
+int uot_grid_tile_count(void);
+int uot_autotune_table(char* buf, int len);
 
 /*
  * uot_solve -- scaling iterations for entropic unbalanced OT (eq. S, Sec. 3.3;

@@ -20,6 +20,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <string>
 
 #include "uot_internal.cuh"
 
@@ -85,10 +88,12 @@ __device__ __forceinline__ float lg2_approx(float x) {
   return y;
 }
 
-// FP32 grid pass.  One CTA = one line x 128 consecutive outputs; its 8 warps
-// split the contraction index j into 8 contiguous ranges (so a 256-point axis
-// gives 8 x 32 terms per output) and combine their partial (max, sum) pairs
-// through shared memory.  Each lane owns 4 outputs handled as two f32x2 pairs.
+// FP32 grid pass.  One CTA = one line x (32 * OPL) consecutive outputs; its NW
+// warps split the contraction index j into NW contiguous ranges and combine
+// their partial (max, sum) pairs through shared memory.  Each lane owns OPL
+// outputs handled as OPL/2 f32x2 pairs.  (NW, OPL) is the tile shape; the
+// shapes below are all compiled and one is picked per pass shape (nlines, nin,
+// nout, batch) by timing them on the device (see the tuner further down).
 //
 // The log-sum-exp needs a shift m per output; any m with every term's
 // exponent <= ~100 and the largest >= ~-90 gives the full FP32 accuracy, and
@@ -97,8 +102,8 @@ __device__ __forceinline__ float lg2_approx(float x) {
 // iterations), that value is used as the shift and each term costs one sweep.
 // If any combined sum of the CTA falls outside [2^-90, 2^100], the CTA redoes
 // its outputs with the exact per-range maximum (a max sweep and a sum sweep).
-constexpr int kNW = 8;                    // warps per CTA = contraction splits
-constexpr int kOutCTA = 128;              // outputs per CTA (4 per lane)
+constexpr int kNW = 8;                    // tile of the persistent solve: warps per CTA
+constexpr int kOutCTA = 128;              // ... and outputs per CTA (4 per lane)
 
 struct PassArgs {
   const float2* in;    // float-float line values (or potentials when in_is_pot)
@@ -163,25 +168,35 @@ __device__ __forceinline__ void epilogue_apply(const Epilogue& e, int64_t b, int
   if (e.err) violation_terms_ff(ffl(o.uold), Unew, S, ffl(o.lw), ffl(e.inv_eps_ff), num, den);
 }
 
-constexpr int kLineRegs = 4;  // line elements held per thread (nin <= 1024 fast path)
+// Compile-time quantities of a tile shape.
+template <int NW, int OPL>
+struct Tile {
+  static_assert(OPL == 2 || OPL == 4, "outputs per lane");
+  static constexpr int kOut = 32 * OPL;                          // outputs per CTA
+  static constexpr int kThreads = 32 * NW;
+  static constexpr int kOwn = (kOut + kThreads - 1) / kThreads;  // outputs per thread in the epilogue
+  static constexpr int kLineRegs = NW >= 2 ? 4 : 8;              // line elements held per thread
+};
 
 // Shared-memory workspace of one work item.
 struct ItemSmem {
-  float4* sline;               // nin x {t, t, y, y}
-  float2 (*part)[kOutCTA];     // [kNW][kOutCTA]
-  float* sshift;               // [kOutCTA]
-  float* sred;                 // [kNW]
+  float4* sline;  // nin x {t, t, y, y}
+  float2* part;   // [NW][kOut] partial (max, sum) pairs
+  float* sshift;  // [kOut]
+  float* sred;    // [NW]
 };
 
-// One work item of a grid pass: line l of batch entry bz, outputs i0 .. i0+127.
+// One work item of a grid pass: line l of batch entry bz, outputs i0 .. i0+kOut-1.
 // With kPDL the item waits for the preceding kernel after its independent
 // prologue (programmatic dependent launch) and clears the violation
 // accumulators when asked.  Returns the item's violation terms in num, den.
-template <bool kPDL>
+template <int NW, int OPL, bool kPDL>
 __device__ __forceinline__ void grid_item_f32(const PassArgs& a, const Epilogue& epi, int l, int64_t bz,
                                               int i0, const ItemSmem& sm, float& num, float& den) {
+  typedef Tile<NW, OPL> T;
+  constexpr int OUT = T::kOut, NT = T::kThreads, OWN = T::kOwn, LR = T::kLineRegs, P = OPL / 2;
   float4* sline = sm.sline;
-  float2 (*part)[kOutCTA] = sm.part;
+  float2* part = sm.part;
   float* sshift = sm.sshift;
   float* sred = sm.sred;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -192,24 +207,31 @@ __device__ __forceinline__ void grid_item_f32(const PassArgs& a, const Epilogue&
   const bool spec = a.use_prev && zprev;
 
   // ---- prologue independent of the preceding kernel ----
-  const int my_i = i0 + tid;
-  const bool owns = (tid < kOutCTA) && (my_i < nout);
-  const int64_t my_pt = (int64_t)my_i * nlines + l;
-  float zp = 0.0f;
-  EpiPre pre;
-  if (owns) {
-    if (spec) zp = zprev[my_pt];
-    epilogue_prefetch(epi, bz, my_pt, pre);
-  }
-  float yv[kLineRegs];
+  bool owns[OWN];
+  int64_t my_pt[OWN];
+  float zp[OWN];
+  EpiPre pre[OWN];
 #pragma unroll
-  for (int r = 0; r < kLineRegs; ++r) {
-    const int j = tid + r * kNW * 32;
+  for (int r = 0; r < OWN; ++r) {
+    const int o = tid + r * NT;
+    const int i = i0 + o;
+    owns[r] = (o < OUT) && (i < nout);
+    my_pt[r] = (int64_t)i * nlines + l;
+    zp[r] = 0.0f;
+    if (owns[r]) {
+      if (spec) zp[r] = zprev[my_pt[r]];
+      epilogue_prefetch(epi, bz, my_pt[r], pre[r]);
+    }
+  }
+  float yv[LR];
+#pragma unroll
+  for (int r = 0; r < LR; ++r) {
+    const int j = tid + r * NT;
     yv[r] = (j < nin) ? a.yi[j] : 0.0f;
   }
-  float xq[4];
+  float xq[OPL];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
+  for (int q = 0; q < OPL; ++q) {
     const int i = i0 + lane + 32 * q;
     xq[q] = a.xo[i < nout ? i : nout - 1];
   }
@@ -221,47 +243,53 @@ __device__ __forceinline__ void grid_item_f32(const PassArgs& a, const Epilogue&
   }
 
   // ---- line values: one read, kept in registers when the line is short ----
-  ff lv[kLineRegs];
-  const bool in_regs = nin <= kLineRegs * kNW * 32;
+  ff lv[LR];
+  const bool in_regs = nin <= LR * NT;
   float mx = -INFINITY;
   if (in_regs) {
 #pragma unroll
-    for (int r = 0; r < kLineRegs; ++r) {
-      const int j = tid + r * kNW * 32;
+    for (int r = 0; r < LR; ++r) {
+      const int j = tid + r * NT;
       lv[r] = (j < nin) ? load_L_ff(a, in, base + j) : ff_ninf();
       mx = fmaxf(mx, lv[r].hi);
     }
   } else {
-    for (int j = tid; j < nin; j += kNW * 32) mx = fmaxf(mx, load_L_ff(a, in, base + j).hi);
+    for (int j = tid; j < nin; j += NT) mx = fmaxf(mx, load_L_ff(a, in, base + j).hi);
   }
   mx = warp_maxf(mx);
   if (lane == 0) sred[warp] = mx;
   __syncthreads();
   mx = sred[0];
 #pragma unroll
-  for (int w = 1; w < kNW; ++w) mx = fmaxf(mx, sred[w]);
+  for (int w = 1; w < NW; ++w) mx = fmaxf(mx, sred[w]);
 
   num = 0.0f;
   den = 0.0f;
   if (mx == -INFINITY) {
     // b = 0 on the whole line: every sum is empty.
-    if (owns) {
-      if (zprev) zprev[my_pt] = -INFINITY;
-      epilogue_apply(epi, bz, my_pt, ff_ninf(), pre, num, den);
+#pragma unroll
+    for (int r = 0; r < OWN; ++r) {
+      if (owns[r]) {
+        if (zprev) zprev[my_pt[r]] = -INFINITY;
+        float n1, d1;
+        epilogue_apply(epi, bz, my_pt[r], ff_ninf(), pre[r], n1, d1);
+        num += n1;
+        den += d1;
+      }
     }
     return;
   }
   if (in_regs) {
 #pragma unroll
-    for (int r = 0; r < kLineRegs; ++r) {
-      const int j = tid + r * kNW * 32;
+    for (int r = 0; r < LR; ++r) {
+      const int j = tid + r * NT;
       if (j < nin) {
         const float t = (lv[r].hi == -INFINITY) ? -INFINITY : ((lv[r].hi - mx) + lv[r].lo) * kLog2e;
         sline[j] = make_float4(t, t, yv[r], yv[r]);
       }
     }
   } else {
-    for (int j = tid; j < nin; j += kNW * 32) {
+    for (int j = tid; j < nin; j += NT) {
       const ff v = load_L_ff(a, in, base + j);
       const float t = (v.hi == -INFINITY) ? -INFINITY : ((v.hi - mx) + v.lo) * kLog2e;
       const float y = a.yi[j];
@@ -269,106 +297,129 @@ __device__ __forceinline__ void grid_item_f32(const PassArgs& a, const Epilogue&
     }
   }
   // speculative shifts in log2 units relative to the staged line
-  if (tid < kOutCTA) sshift[tid] = (!owns || zp == -INFINITY) ? 0.0f : (zp - mx) * kLog2e;
+#pragma unroll
+  for (int r = 0; r < OWN; ++r) {
+    const int o = tid + r * NT;
+    if (o < OUT) sshift[o] = (!owns[r] || zp[r] == -INFINITY) ? 0.0f : (zp[r] - mx) * kLog2e;
+  }
   __syncthreads();
 
   const f2p nk2 = pk(-a.k2, -a.k2);
-  const int J = (nin + kNW - 1) / kNW;
+  const int J = (nin + NW - 1) / NW;
   const int j0 = warp * J, j1 = min(nin, j0 + J);
-  const f2p X0 = pk(xq[0], xq[1]), X1 = pk(xq[2], xq[3]);
+  f2p X[P];
+#pragma unroll
+  for (int p = 0; p < P; ++p) X[p] = pk(xq[2 * p], xq[2 * p + 1]);
 
   bool exact = !spec;
   for (int attempt = 0; attempt < 2; ++attempt) {
-    float mq[4];
+    float mq[OPL];
     if (!exact) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) mq[q] = sshift[lane + 32 * q];
+      for (int q = 0; q < OPL; ++q) mq[q] = sshift[lane + 32 * q];
     } else {
       // exact per-range maximum
-      float m4[4] = {-INFINITY, -INFINITY, -INFINITY, -INFINITY};
+#pragma unroll
+      for (int q = 0; q < OPL; ++q) mq[q] = -INFINITY;
 #pragma unroll 4
       for (int j = j0; j < j1; ++j) {
         const float4 v = sline[j];
-        const f2p T = pk(v.x, v.y), Y = pk(v.z, v.w);
-        const f2p D0 = sub2(X0, Y), D1 = sub2(X1, Y);
-        const float2 A0 = upk(fma2(nk2, mul2(D0, D0), T));
-        const float2 A1 = upk(fma2(nk2, mul2(D1, D1), T));
-        m4[0] = fmaxf(m4[0], A0.x);
-        m4[1] = fmaxf(m4[1], A0.y);
-        m4[2] = fmaxf(m4[2], A1.x);
-        m4[3] = fmaxf(m4[3], A1.y);
-      }
+        const f2p Tv = pk(v.x, v.y), Y = pk(v.z, v.w);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) mq[q] = m4[q];
+        for (int p = 0; p < P; ++p) {
+          const f2p D = sub2(X[p], Y);
+          const float2 A = upk(fma2(nk2, mul2(D, D), Tv));
+          mq[2 * p] = fmaxf(mq[2 * p], A.x);
+          mq[2 * p + 1] = fmaxf(mq[2 * p + 1], A.y);
+        }
+      }
     }
     // sum sweep relative to the shifts (a -inf shift means an empty range)
-    const f2p MS0 = pk(mq[0] == -INFINITY ? 0.0f : mq[0], mq[1] == -INFINITY ? 0.0f : mq[1]);
-    const f2p MS1 = pk(mq[2] == -INFINITY ? 0.0f : mq[2], mq[3] == -INFINITY ? 0.0f : mq[3]);
-    f2p S0 = pk(0.0f, 0.0f), S1 = S0;
+    f2p MS[P], S[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      MS[p] = pk(mq[2 * p] == -INFINITY ? 0.0f : mq[2 * p], mq[2 * p + 1] == -INFINITY ? 0.0f : mq[2 * p + 1]);
+      S[p] = pk(0.0f, 0.0f);
+    }
 #pragma unroll 4
     for (int j = j0; j < j1; ++j) {
       const float4 v = sline[j];
-      const f2p T = pk(v.x, v.y), Y = pk(v.z, v.w);
-      const f2p D0 = sub2(X0, Y), D1 = sub2(X1, Y);
-      const float2 A0 = upk(fma2(nk2, mul2(D0, D0), sub2(T, MS0)));
-      const float2 A1 = upk(fma2(nk2, mul2(D1, D1), sub2(T, MS1)));
-      S0 = add2(S0, pk(ex2_approx(A0.x), ex2_approx(A0.y)));
-      S1 = add2(S1, pk(ex2_approx(A1.x), ex2_approx(A1.y)));
-    }
-    const float2 s01 = upk(S0), s23 = upk(S1);
-    const float sq[4] = {s01.x, s01.y, s23.x, s23.y};
+      const f2p Tv = pk(v.x, v.y), Y = pk(v.z, v.w);
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
-      part[warp][lane + 32 * q] = make_float2(mq[q] == -INFINITY ? 0.0f : mq[q], mq[q] == -INFINITY ? 0.0f : sq[q]);
+      for (int p = 0; p < P; ++p) {
+        const f2p D = sub2(X[p], Y);
+        const float2 A = upk(fma2(nk2, mul2(D, D), sub2(Tv, MS[p])));
+        S[p] = add2(S[p], pk(ex2_approx(A.x), ex2_approx(A.y)));
+      }
+    }
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      const float2 s = upk(S[p]);
+      const float m0 = mq[2 * p], m1 = mq[2 * p + 1];
+      part[warp * OUT + lane + 64 * p] = make_float2(m0 == -INFINITY ? 0.0f : m0, m0 == -INFINITY ? 0.0f : s.x);
+      part[warp * OUT + lane + 64 * p + 32] = make_float2(m1 == -INFINITY ? 0.0f : m1, m1 == -INFINITY ? 0.0f : s.y);
+    }
     __syncthreads();
 
-    // combine the 8 ranges of each output
+    // combine the NW ranges of each output
     bool bad = false;
-    float Mo = -INFINITY, So = 0.0f;
-    if (tid < kOutCTA) {
+    float Mo[OWN], So[OWN];
 #pragma unroll
-      for (int w = 0; w < kNW; ++w) {
-        const float2 pr = part[w][tid];
-        if (pr.y > 0.0f) Mo = fmaxf(Mo, pr.x);
-      }
-      if (Mo != -INFINITY) {
+    for (int r = 0; r < OWN; ++r) {
+      const int o = tid + r * NT;
+      Mo[r] = -INFINITY;
+      So[r] = 0.0f;
+      if (o < OUT) {
 #pragma unroll
-        for (int w = 0; w < kNW; ++w) {
-          const float2 pr = part[w][tid];
-          if (pr.y > 0.0f) So += pr.y * ex2_approx(pr.x - Mo);
+        for (int w = 0; w < NW; ++w) {
+          const float2 pr = part[w * OUT + o];
+          if (pr.y > 0.0f) Mo[r] = fmaxf(Mo[r], pr.x);
         }
+        if (Mo[r] != -INFINITY) {
+#pragma unroll
+          for (int w = 0; w < NW; ++w) {
+            const float2 pr = part[w * OUT + o];
+            if (pr.y > 0.0f) So[r] += pr.y * ex2_approx(pr.x - Mo[r]);
+          }
+        }
+        if (owns[r] && !exact) bad = bad || !(So[r] >= 0x1p-90f && So[r] <= 0x1p100f);
       }
-      if (owns && !exact) bad = !(So >= 0x1p-90f && So <= 0x1p100f);
     }
     const int any_bad = __syncthreads_or(bad ? 1 : 0);
     if (any_bad && !exact) {
       exact = true;
       continue;  // block-uniform: redo with exact maxima
     }
-    if (owns) {
+#pragma unroll
+    for (int r = 0; r < OWN; ++r) {
+      if (!owns[r]) continue;
       ff z = ff_ninf();
-      if (So > 0.0f) {
+      if (So[r] > 0.0f) {
         // z = mx + ln2 Mo + ln2 log2(So), the first product kept exact in float-float
         const ff ln2 = ff{0.693147182464599609375f, -1.904654323148236017e-09f};
-        z = ff_add_f(ff_add_f(ff_mul_f(ln2, Mo), mx), kLn2 * lg2_approx(So));
+        z = ff_add_f(ff_add_f(ff_mul_f(ln2, Mo[r]), mx), kLn2 * lg2_approx(So[r]));
       }
-      if (zprev) zprev[my_pt] = z.hi;
-      epilogue_apply(epi, bz, my_pt, z, pre, num, den);
+      if (zprev) zprev[my_pt[r]] = z.hi;
+      float n1, d1;
+      epilogue_apply(epi, bz, my_pt[r], z, pre[r], n1, d1);
+      num += n1;
+      den += d1;
     }
     break;
   }
 }
 
-__global__ void __launch_bounds__(kNW * 32, 4)
+template <int NW, int OPL>
+__global__ void __launch_bounds__(NW * 32, NW == 1 ? 16 : 32 / NW)
     grid_pass_f32(PassArgs a, Epilogue epi) {
   extern __shared__ float4 sline[];
-  __shared__ float2 part[kNW][kOutCTA];
-  __shared__ float sshift[kOutCTA];
-  __shared__ float sred[kNW];
+  __shared__ float2 part[NW * 32 * OPL];
+  __shared__ float sshift[32 * OPL];
+  __shared__ float sred[NW];
   const ItemSmem sm{sline, part, sshift, sred};
   float num, den;
-  grid_item_f32<true>(a, epi, blockIdx.y, blockIdx.z, blockIdx.x * kOutCTA, sm, num, den);
-  if (epi.err) block_add2f<kNW * 32>(num, den, epi.err + 2 * (int64_t)blockIdx.z);
+  grid_item_f32<NW, OPL, true>(a, epi, blockIdx.y, blockIdx.z, blockIdx.x * (32 * OPL), sm, num, den);
+  if (epi.err) block_add2f<NW * 32>(num, den, epi.err + 2 * (int64_t)blockIdx.z);
 }
 
 // ---------------------------------------------------------------------------
@@ -441,7 +492,7 @@ struct PersistArgs {
 __global__ void __launch_bounds__(kNW * 32, 4)
     grid_solve_persistent(PersistArgs P) {
   extern __shared__ float4 sline[];
-  __shared__ float2 part[kNW][kOutCTA];
+  __shared__ float2 part[kNW * kOutCTA];
   __shared__ float sshift[kOutCTA];
   __shared__ float sred[kNW];
   const ItemSmem sm{sline, part, sshift, sred};
@@ -496,7 +547,7 @@ __global__ void __launch_bounds__(kNW * 32, 4)
         const int items = nlines * nob;
         for (int item = blockIdx.x; item < items; item += gridDim.x) {
           float num, den;
-          grid_item_f32<false>(a, e, item / nob, 0, (item % nob) * kOutCTA, sm, num, den);
+          grid_item_f32<kNW, 4, false>(a, e, item / nob, 0, (item % nob) * kOutCTA, sm, num, den);
           if (e.err) block_add2f<kNW * 32>(num, den, e.err);
         }
         if (!grid_barrier(P.bar, P.status)) return;
@@ -667,21 +718,239 @@ __global__ void __launch_bounds__(WARPS * 32)
 
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// Tile shapes of the FP32 pass and the tuner that picks one per pass shape.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct TileShape {
+  int nw, opl;
+};
+constexpr TileShape kTiles[] = {{8, 4}, {4, 4}, {2, 4}, {1, 4}, {8, 2}, {4, 2}, {2, 2}};
+constexpr int kNumTiles = (int)(sizeof(kTiles) / sizeof(kTiles[0]));
+
+template <int NW, int OPL>
+cudaError_t launch_f32_tile(const PassArgs& a, const Epilogue& epi, int nbatch, cudaStream_t s) {
+  dim3 grid((a.nout + 32 * OPL - 1) / (32 * OPL), a.nlines, nbatch);
+  if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidConfiguration;
+  const size_t smem = (size_t)a.nin * sizeof(float4);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(grid_pass_f32<NW, OPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  cudaLaunchConfig_t cfg;
+  memset(&cfg, 0, sizeof(cfg));
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(NW * 32);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, grid_pass_f32<NW, OPL>, a, epi);
+}
+
+cudaError_t launch_f32(int t, const PassArgs& a, const Epilogue& epi, int nbatch, cudaStream_t s) {
+  switch (t) {
+    case 0: return launch_f32_tile<8, 4>(a, epi, nbatch, s);
+    case 1: return launch_f32_tile<4, 4>(a, epi, nbatch, s);
+    case 2: return launch_f32_tile<2, 4>(a, epi, nbatch, s);
+    case 3: return launch_f32_tile<1, 4>(a, epi, nbatch, s);
+    case 4: return launch_f32_tile<8, 2>(a, epi, nbatch, s);
+    case 5: return launch_f32_tile<4, 2>(a, epi, nbatch, s);
+    default: return launch_f32_tile<2, 2>(a, epi, nbatch, s);
+  }
+}
+
+struct TuneKey {
+  int dev, nlines, nin, nout, nbatch;
+  bool operator<(const TuneKey& o) const {
+    if (dev != o.dev) return dev < o.dev;
+    if (nlines != o.nlines) return nlines < o.nlines;
+    if (nin != o.nin) return nin < o.nin;
+    if (nout != o.nout) return nout < o.nout;
+    return nbatch < o.nbatch;
+  }
+};
+
+struct TuneEntry {
+  int tile;
+  float us[kNumTiles];  // measured time per launch of every tile (negative: not measured)
+};
+
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneEntry> g_tuned;
+int g_autotune = 1;
+int g_forced_tile = -1;
+thread_local int g_tune_hold = 0;
+
+// Times every tile on this pass shape.  The timed chain mimics a solve: each
+// launch reads the previous launch's output (two buffers in turn, each with
+// its own speculative-shift buffer), with the caller's coordinates and eps;
+// the first values are finite.  The common case is timed: speculative shifts
+// taken from the same buffer's previous result.
+TuneEntry tune_tiles(const PassArgs& base, int nbatch, cudaStream_t s) {
+  TuneEntry ent;
+  ent.tile = 0;
+  for (int t = 0; t < kNumTiles; ++t) ent.us[t] = -1.0f;
+  // one buffer holds a pass input or output: the larger of the two shapes
+  const size_t nel = (size_t)nbatch * base.nlines * (size_t)std::max(base.nin, base.nout);
+  float2* buf[2] = {nullptr, nullptr};
+  float* z[2] = {nullptr, nullptr};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  // (a buffer is read as nlines x nin and written as nout x nlines values;
+  // both fit, and every value read is finite: zeros first, results later)
+  bool ok = true;
+  for (int k = 0; k < 2 && ok; ++k)
+    ok = cudaMallocAsync(&buf[k], nel * sizeof(float2), s) == cudaSuccess &&
+         cudaMallocAsync(&z[k], nel * sizeof(float), s) == cudaSuccess &&
+         cudaMemsetAsync(buf[k], 0, nel * sizeof(float2), s) == cudaSuccess;
+  ok = ok && cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
+  if (ok) {
+    PassArgs a = base;
+    a.logw = nullptr;
+    a.in_is_pot = 0;
+    a.zero_acc = nullptr;
+    Epilogue e;
+    memset(&e, 0, sizeof(e));
+    e.mode = EPI_RAW;
+    e.ff = 1;
+    e.bstride = (int64_t)base.nlines * base.nout;
+    int cur = 0;
+    auto step = [&](int t, int use_prev) -> bool {
+      a.in = buf[cur];
+      e.out = reinterpret_cast<double*>(buf[cur ^ 1]);
+      a.zprev = z[cur ^ 1];
+      a.use_prev = use_prev;
+      cur ^= 1;
+      return launch_f32(t, a, e, nbatch, s) == cudaSuccess;
+    };
+    // Warm-up (brings the SM clock up before anything is timed; both shift
+    // buffers get exact values), then rounds that visit every tile in turn; a
+    // tile's time is its best round, so a clock or neighbour transient cannot
+    // favour the tiles timed last.
+    constexpr int kReps = 16, kRounds = 3, kWarm = 64;
+    bool okt[kNumTiles];
+    float tmin[kNumTiles];
+    bool wok = step(0, 0) && step(0, 0);
+    for (int r = 0; r < kWarm && wok; ++r) wok = step(0, 1);
+    for (int t = 0; t < kNumTiles; ++t) {
+      okt[t] = wok;
+      tmin[t] = 1e30f;
+    }
+    for (int round = 0; round < kRounds && wok; ++round) {
+      for (int t = 0; t < kNumTiles; ++t) {
+        if (!okt[t]) continue;
+        bool tok = cudaEventRecord(e0, s) == cudaSuccess;
+        for (int r = 0; r < kReps && tok; ++r) tok = step(t, 1);
+        tok = tok && cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
+        float ms = 0.0f;
+        tok = tok && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+        if (!tok) {
+          (void)cudaGetLastError();
+          okt[t] = false;
+          continue;
+        }
+        tmin[t] = std::min(tmin[t], ms * 1000.0f / kReps);
+      }
+    }
+    float best = 1e30f;
+    for (int t = 0; t < kNumTiles; ++t) {
+      if (!okt[t]) continue;
+      ent.us[t] = tmin[t];
+      if (tmin[t] < best) {
+        best = tmin[t];
+        ent.tile = t;
+      }
+    }
+    // The chain above differs from a solve's (no prox epilogue, no potential
+    // inputs), and tiles within a few percent of each other here can rank
+    // differently there: the first tile is kept unless another one beats it by
+    // more than 5%.
+    if (okt[0] && tmin[0] <= 1.05f * best) ent.tile = 0;
+  }
+  (void)cudaGetLastError();
+  for (int k = 0; k < 2; ++k) {
+    if (buf[k]) cudaFreeAsync(buf[k], s);
+    if (z[k]) cudaFreeAsync(z[k], s);
+  }
+  cudaStreamSynchronize(s);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  (void)cudaGetLastError();
+  return ent;
+}
+
+int pick_tile(const PassArgs& a, int nbatch, cudaStream_t s) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  if (g_forced_tile >= 0) return g_forced_tile;
+  if (!g_autotune) return 0;
+  TuneKey key;
+  if (cudaGetDevice(&key.dev) != cudaSuccess) return 0;
+  key.nlines = a.nlines;
+  key.nin = a.nin;
+  key.nout = a.nout;
+  key.nbatch = nbatch;
+  auto it = g_tuned.find(key);
+  if (it != g_tuned.end()) return it->second.tile;
+  if (g_tune_hold) return 0;
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &st) != cudaSuccess || st != cudaStreamCaptureStatusNone) {
+    (void)cudaGetLastError();
+    return 0;
+  }
+  const TuneEntry ent = tune_tiles(a, nbatch, s);
+  g_tuned[key] = ent;
+  return ent.tile;
+}
+
+}  // namespace
+
+int grid_set_autotune(int mode) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  const int prev = g_autotune;
+  g_autotune = mode ? 1 : 0;
+  return prev;
+}
+
+int grid_force_tile(int idx) {
+  if (idx < -1 || idx >= kNumTiles) return -1;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_forced_tile = idx;
+  return 0;
+}
+
+int grid_tile_count() { return kNumTiles; }
+
+void grid_tune_hold(int on) { g_tune_hold += on ? 1 : -1; }
+
+std::string grid_tile_table() {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  std::string s;
+  char buf[256];
+  for (const auto& kv : g_tuned) {
+    const TuneKey& k = kv.first;
+    const TuneEntry& e = kv.second;
+    snprintf(buf, sizeof(buf), "dev%d lines=%d nin=%d nout=%d batch=%d -> warps=%d outputs/lane=%d;", k.dev,
+             k.nlines, k.nin, k.nout, k.nbatch, kTiles[e.tile].nw, kTiles[e.tile].opl);
+    s += buf;
+    for (int t = 0; t < kNumTiles; ++t) {
+      snprintf(buf, sizeof(buf), " %dx%d:%.2fus", kTiles[t].nw, kTiles[t].opl, e.us[t]);
+      s += buf;
+    }
+    s += "\n";
+  }
+  return s;
+}
+
 cudaError_t launch_grid_pass(int prec, const double* in, const double* logw, int in_is_pot,
                              int nlines, int nin, const void* yi, int nout, const void* xo,
                              double eps, int nbatch, const Epilogue& epi, cudaStream_t s,
                              float* zprev, int use_prev, double* zero_acc) {
-  prof_mark_begin(PROF_GRID_PASS, s);
-  count_launches(1);
   if (prec == UOT_F32) {
-    dim3 grid((nout + kOutCTA - 1) / kOutCTA, nlines, nbatch);
-    if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidConfiguration;
-    const size_t smem = (size_t)nin * sizeof(float4);
-    if (smem > 48 * 1024) {
-      cudaError_t e = cudaFuncSetAttribute(grid_pass_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)smem);
-      if (e != cudaSuccess) return e;
-    }
     PassArgs a;
     a.in = reinterpret_cast<const float2*>(in);
     a.logw = reinterpret_cast<const float2*>(logw);
@@ -696,20 +965,17 @@ cudaError_t launch_grid_pass(int prec, const double* in, const double* logw, int
     a.zprev = zprev;
     a.use_prev = use_prev;
     a.zero_acc = zero_acc;
-    cudaLaunchConfig_t cfg;
-    memset(&cfg, 0, sizeof(cfg));
-    cfg.gridDim = grid;
-    cfg.blockDim = dim3(kNW * 32);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    cudaError_t e = cudaLaunchKernelEx(&cfg, grid_pass_f32, a, epi);
+    const int tile = pick_tile(a, nbatch, s);
+    prof_mark_begin(PROF_GRID_PASS, s);
+    count_launches(1);
+    cudaError_t e = launch_f32(tile, a, epi, nbatch, s);
     if (e != cudaSuccess) return e;
-  } else {
+    prof_mark_end(PROF_GRID_PASS, s);
+    return cudaGetLastError();
+  }
+  prof_mark_begin(PROF_GRID_PASS, s);
+  count_launches(1);
+  {
     constexpr int R = 2, WARPS = 4;
     dim3 grid((nout + 32 * R - 1) / (32 * R), (nlines + WARPS - 1) / WARPS, nbatch);
     if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidConfiguration;

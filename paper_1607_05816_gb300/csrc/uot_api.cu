@@ -43,6 +43,11 @@ struct Prof {
   cudaEvent_t pending[PROF_NFAM] = {nullptr, nullptr};
 } g_prof;
 
+bool profiling_on() {
+  std::lock_guard<std::mutex> lk(g_prof.mu);
+  return g_prof.on;
+}
+
 cudaEvent_t prof_event() {
   if (!g_prof.pool.empty()) {
     cudaEvent_t e = g_prof.pool.back();
@@ -701,6 +706,43 @@ struct Gibbs {
   }
 };
 
+// A block of launches captured once as a CUDA graph and replayed.  Capture
+// runs on a private stream (the caller's may be the legacy default stream,
+// which cannot be captured); every replay runs on the caller's stream.  The
+// launch counter counts each replayed kernel, not the capture.
+struct BlockGraph {
+  cudaGraphExec_t exec = nullptr;
+  long long kernels = 0;
+  template <class F>
+  cudaError_t capture(F&& body) {
+    cudaStream_t cs = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+    const long long before = g_launches.load();
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      const cudaError_t eb = body(cs);
+      const cudaError_t ee = cudaStreamEndCapture(cs, &graph);
+      e = (eb != cudaSuccess) ? eb : ee;
+    }
+    kernels = g_launches.load() - before;
+    g_launches.fetch_sub(kernels);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) exec = nullptr;
+    return e;
+  }
+  cudaError_t launch(cudaStream_t s) {
+    count_launches((int)kernels);
+    return cudaGraphLaunch(exec, s);
+  }
+  ~BlockGraph() {
+    if (exec) cudaGraphExecDestroy(exec);
+  }
+};
+
 // Per-point state conversions: FP64 path -> double slots; FP32 path ->
 // float-float pairs in the same 8-byte slots.
 cudaError_t to_log(int prec, const void* src, int64_t n, double* dst, cudaStream_t s) {
@@ -985,20 +1027,51 @@ uot_status solve_impl(const uot_geom* g, int batch, const void* p, const void* d
     total = hs[3];
     err = (o->max_iter > 0) ? herr : INFINITY;
   } else if (!o->plain_scaling) {
-    auto iteration = [&](double eps, bool check) -> cudaError_t {
+    auto iteration = [&](double eps, bool check, cudaStream_t st) -> cudaError_t {
       cudaError_t e;
       Epilogue e1 = prox_epilogue(D1, logp, U, logdx, check ? acc : nullptr, eps);
       e1.bstride = e1.bstride_p = n;
-      if ((e = G.apply(0, V, logdy, eps, e1, s, check ? acc : nullptr)) != cudaSuccess) return e;
+      if ((e = G.apply(0, V, logdy, eps, e1, st, check ? acc : nullptr)) != cudaSuccess) return e;
       Epilogue e2 = prox_epilogue(D2, logq, V, logdy, nullptr, eps);
       e2.bstride = e2.bstride_p = m;
-      return G.apply(1, U, logdx, eps, e2, s);
+      return G.apply(1, U, logdx, eps, e2, st);
     };
     for (const Stage& sg : stages)
-      for (int k = 0; k < sg.iters; ++k, ++total) UOT_CK(iteration(sg.eps, false));
+      for (int k = 0; k < sg.iters; ++k, ++total) UOT_CK(iteration(sg.eps, false, s));
+    // launch_mode 2: once a block of check_every iterations (the last one
+    // checked) repeats the same launches -- same eps, shifts from the previous
+    // iteration -- it is captured once as a CUDA graph and replayed per block.
+    BlockGraph bg;
+    bool graph_ok = o->launch_mode == 2 && !profiling_on();
     while (it < o->max_iter) {
+      if (graph_ok && it > 0 && it % check_every == 0 && it + check_every <= o->max_iter) {
+        if (!bg.exec) {
+          cudaError_t e = bg.capture([&](cudaStream_t cs) -> cudaError_t {
+            for (int k = 0; k < check_every; ++k) {
+              cudaError_t e2 = iteration(o->eps, k == check_every - 1, cs);
+              if (e2 != cudaSuccess) return e2;
+            }
+            return cudaSuccess;
+          });
+          if (e != cudaSuccess) {
+            // not capturable here (e.g. a legacy-stream dependency): per-pass launches
+            graph_ok = false;
+            (void)cudaGetLastError();
+            continue;
+          }
+        }
+        UOT_CK(bg.launch(s));
+        it += check_every;
+        total += check_every;
+        UOT_CK(read_err(err));
+        if (o->tol > 0.0 && err <= o->tol) {
+          converged = true;
+          break;
+        }
+        continue;
+      }
       const bool check = ((it + 1) % check_every == 0) || (it == o->max_iter - 1);
-      UOT_CK(iteration(o->eps, check));
+      UOT_CK(iteration(o->eps, check, s));
       ++it;
       ++total;
       if (check) {
@@ -1131,6 +1204,22 @@ const char* uot_last_error(void) { return g_last_error.c_str(); }
 
 long long uot_launch_count(void) { return g_launches.load(); }
 
+int uot_set_autotune(int mode) { return grid_set_autotune(mode); }
+
+uot_status uot_force_grid_tile(int idx) { return grid_force_tile(idx) == 0 ? UOT_OK : UOT_EINVAL; }
+
+int uot_grid_tile_count(void) { return grid_tile_count(); }
+
+int uot_autotune_table(char* buf, int len) {
+  const std::string t = grid_tile_table();
+  if (buf && len > 0) {
+    const size_t n = std::min((size_t)(len - 1), t.size());
+    memcpy(buf, t.data(), n);
+    buf[n] = 0;
+  }
+  return (int)t.size();
+}
+
 void uot_profile_begin(void) {
   std::lock_guard<std::mutex> lk(g_prof.mu);
   for (auto& v : g_prof.marks) {
@@ -1259,6 +1348,11 @@ extern "C" {
 uot_status uot_gibbs_log_noalloc(const uot_geom* g, const void* W, const void* w, double eps,
                                  int transpose, int precision, void* out, void* stream) {
   clear_stale_error();
+  // no tuning here: the tuner allocates its scratch inputs
+  struct TuneHold {
+    TuneHold() { grid_tune_hold(1); }
+    ~TuneHold() { grid_tune_hold(0); }
+  } hold;
   uot_status st = check_geom(g);
   if (st != UOT_OK) return st;
   if (!W || !w || !out || !(eps > 0.0) || !prec_ok(precision)) return UOT_EINVAL;

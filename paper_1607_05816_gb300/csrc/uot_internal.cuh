@@ -10,6 +10,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "../../include/uot.h"
 
 namespace uot {
@@ -370,6 +372,19 @@ cudaError_t launch_grid_pass(int prec, const double* in, const double* logw, int
                              int nlines, int nin, const void* yi, int nout, const void* xo,
                              double eps, int nbatch, const Epilogue& epi, cudaStream_t s,
                              float* zprev, int use_prev, double* zero_acc = nullptr);
+
+// Tile shapes of the FP32 grid pass (warps splitting the contraction x
+// outputs per lane) and the tuner that times them once per pass shape
+// (nlines, nin, nout, batch) and device, on first use (k_grid.cu).
+//  grid_set_autotune(0|1): off = always the first shape; returns the previous mode.
+//  grid_force_tile(idx): use shape idx for every pass (-1: back to tuning); -1 if idx is out of range.
+//  grid_tune_hold(1|0): nested hold on the calling thread (no tuning, which allocates).
+//  grid_tile_table(): the tuned shapes and their measured times, one line per pass shape.
+int grid_set_autotune(int mode);
+int grid_force_tile(int idx);
+int grid_tile_count();
+void grid_tune_hold(int on);
+std::string grid_tile_table();
 
 // Persistent FP32 grid solve (k_grid.cu): the whole iteration, eps stages and
 // convergence test of one grid problem in one cooperative launch.

@@ -104,6 +104,10 @@ _SIGS = {
     "uot_scale_instances": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_longlong, C.c_void_p]),
     "uot_warmstart_features": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                          C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p]),
+    "uot_set_autotune": (C.c_int, [C.c_int]),
+    "uot_force_grid_tile": (C.c_int, [C.c_int]),
+    "uot_grid_tile_count": (C.c_int, []),
+    "uot_autotune_table": (C.c_int, [C.c_char_p, C.c_int]),
     "uot_barycenter": (C.c_int, [C.POINTER(CGeom), C.c_int, C.POINTER(C.c_double), C.c_void_p,
                                  C.c_void_p, C.c_void_p, C.POINTER(CDiv), C.c_double, C.c_int,
                                  C.POINTER(COpts), C.c_void_p, C.c_void_p, C.c_void_p,
@@ -150,6 +154,29 @@ def version() -> str:
 def launch_count() -> int:
     """Kernels launched by the library so far in this process."""
     return int(load().uot_launch_count())
+
+
+def set_autotune(mode: int) -> int:
+    """Grid-pass tile tuner on (1) or off (0); returns the previous mode."""
+    return int(load().uot_set_autotune(int(mode)))
+
+
+def force_grid_tile(idx: int):
+    """Use FP32 grid-pass tile idx for every pass (-1: back to the tuned choice)."""
+    _check(load().uot_force_grid_tile(int(idx)), "uot_force_grid_tile")
+
+
+def grid_tile_count() -> int:
+    return int(load().uot_grid_tile_count())
+
+
+def autotune_table() -> str:
+    """Tuned pass shapes, chosen tiles and measured times (text)."""
+    lib = load()
+    n = lib.uot_autotune_table(None, 0)
+    buf = C.create_string_buffer(n + 1)
+    lib.uot_autotune_table(buf, n + 1)
+    return buf.value.decode()
 
 
 PROF_GRID_PASS, PROF_ROWS = 0, 1
