@@ -505,6 +505,7 @@ def run_batch(args, rank, world, local_rank):
         "gpu_launches": launches, "clocks": clocks,
         "roofline": alu_roofline("batch_solve", achieved, FP32_OPS_PER_TERM["points2"],
                                  "exponentials of all problems' iterations / CUDA-event time of the launch"),
+        "tuned": uot.autotune_table().strip().splitlines(),
     }
     print(json.dumps(line), flush=True)
 

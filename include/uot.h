@@ -189,6 +189,18 @@ int uot_grid_tile_count(void);
 int uot_autotune_table(char* buf, int len);
 
 /*
+ * CTA size of uot_solve_batch (a schedule choice; results differ only in FP32
+ * summation order).  8 or 16 warps per CTA are compiled; with the tuner on,
+ * the first call for a batch shape (d, largest n, largest m) times both on a
+ * sample of the batch (every (nprob/S)-th problem of the size-ordered queue,
+ * S = 2 x SM count, six iterations) and keeps the 8-warp CTA unless the other
+ * is more than 3% faster; uot_autotune_table lists the choice.
+ * uot_force_batch_warps(w): w = 8 or 16 forces that size, 0 returns to the
+ * tuned one; UOT_EINVAL otherwise.
+ */
+uot_status uot_force_batch_warps(int warps);
+
+/*
  * uot_solve -- scaling iterations for entropic unbalanced OT (eq. S, Sec. 3.3;
  * Algorithm 2 of Sec. 4.3 in log form; eps-scaling of Sec. 4.4).
  *

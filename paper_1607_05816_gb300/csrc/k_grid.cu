@@ -916,6 +916,11 @@ int grid_set_autotune(int mode) {
   return prev;
 }
 
+int grid_autotune_enabled() {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  return g_autotune;
+}
+
 int grid_force_tile(int idx) {
   if (idx < -1 || idx >= kNumTiles) return -1;
   std::lock_guard<std::mutex> lk(g_tune_mu);

@@ -1210,8 +1210,10 @@ uot_status uot_force_grid_tile(int idx) { return grid_force_tile(idx) == 0 ? UOT
 
 int uot_grid_tile_count(void) { return grid_tile_count(); }
 
+uot_status uot_force_batch_warps(int warps) { return batch_force_warps(warps) == 0 ? UOT_OK : UOT_EINVAL; }
+
 int uot_autotune_table(char* buf, int len) {
-  const std::string t = grid_tile_table();
+  const std::string t = grid_tile_table() + batch_tune_table();
   if (buf && len > 0) {
     const size_t n = std::min((size_t)(len - 1), t.size());
     memcpy(buf, t.data(), n);
@@ -1598,11 +1600,6 @@ uot_status uot_solve_batch(int nprob, const uot_batch_problem* probs, int d, con
   int dev = 0, sms = 0;
   UOT_CK(cudaGetDevice(&dev));
   UOT_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const int per_sm = batch_ctas_per_sm(nmax, mmax);
-  if (per_sm < 1) {
-    g_last_error = "uot_solve_batch: problem sizes do not fit in shared memory";
-    return UOT_EUNSUPPORTED;
-  }
 
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   UOT_CK(cudaEventCreate(&ev0));
@@ -1633,6 +1630,10 @@ uot_status uot_solve_batch(int nprob, const uot_batch_problem* probs, int d, con
   sc.reserve<int>(nprob);    // iters
   sc.reserve<float>(nprob);  // errs
   sc.reserve<int>(1);        // work counter
+  sc.reserve<float2>(N);     // U state (float-float)
+  sc.reserve<float2>(M);     // V state
+  sc.reserve<float>(N);      // U-side shifts
+  sc.reserve<float>(M);      // V-side shifts
   UOT_CK(sc.allocate());
   int* d_order = sc.take<int>(nprob);
   int* d_n = sc.take<int>(nprob);
@@ -1650,6 +1651,10 @@ uot_status uot_solve_batch(int nprob, const uot_batch_problem* probs, int d, con
   int* d_iters = sc.take<int>(nprob);
   float* d_errs = sc.take<float>(nprob);
   int* d_next = sc.take<int>(1);
+  float2* d_Uff = sc.take<float2>(N);
+  float2* d_Vff = sc.take<float2>(M);
+  float* d_zU = sc.take<float>(N);
+  float* d_zV = sc.take<float>(M);
   UOT_SCRATCH_OK(sc);
   UOT_CK(cudaMemcpyAsync(d_order, order.data(), nprob * sizeof(int), cudaMemcpyHostToDevice, s));
   UOT_CK(cudaMemcpyAsync(d_n, hn.data(), nprob * sizeof(int), cudaMemcpyHostToDevice, s));
@@ -1674,6 +1679,7 @@ uot_status uot_solve_batch(int nprob, const uot_batch_problem* probs, int d, con
   a.check_every = o->check_every > 0 ? o->check_every : 1;
   a.nmax = nmax;
   a.mmax = mmax;
+  a.ndiv = nprob;
   a.tol = (float)o->tol;
   a.order = d_order;
   a.n = d_n;
@@ -1695,8 +1701,19 @@ uot_status uot_solve_batch(int nprob, const uot_batch_problem* probs, int d, con
   a.iters_out = d_iters;
   a.err_out = d_errs;
   a.next = d_next;
+  a.Uff = d_Uff;
+  a.Vff = d_Vff;
+  a.zU = d_zU;
+  a.zV = d_zV;
+  const int variant = batch_pick_variant(a, order.data(), s);
+  const int per_sm = batch_ctas_per_sm(d, variant, nmax, mmax);
+  if (per_sm < 1) {
+    g_last_error = "uot_solve_batch: problem sizes do not fit in shared memory";
+    return UOT_EUNSUPPORTED;
+  }
+  UOT_CK(cudaMemsetAsync(d_next, 0, sizeof(int), s));
   const int grid = (int)std::min<int64_t>(nprob, (int64_t)sms * per_sm);
-  UOT_CK(launch_batch(a, grid, s));
+  UOT_CK(launch_batch(a, variant, grid, s));
   UOT_CK(cudaEventRecord(ev1, s));
   std::vector<int> it_h(nprob);
   std::vector<float> er_h(nprob);

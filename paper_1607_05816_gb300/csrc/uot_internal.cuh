@@ -381,6 +381,7 @@ cudaError_t launch_grid_pass(int prec, const double* in, const double* logw, int
 //  grid_tune_hold(1|0): nested hold on the calling thread (no tuning, which allocates).
 //  grid_tile_table(): the tuned shapes and their measured times, one line per pass shape.
 int grid_set_autotune(int mode);
+int grid_autotune_enabled();
 int grid_force_tile(int idx);
 int grid_tile_count();
 void grid_tune_hold(int on);
@@ -449,6 +450,7 @@ cudaError_t launch_points(const float* x, const float* y, int d, int nout, int n
 // Persistent batched solver for many point-cloud problems (k_batch.cu).
 struct BatchArgs {
   int nprob, d, nstage, iters_per_stage, max_iter, check_every, nmax, mmax;
+  int ndiv;  // problems indexed by divs: divs[(stage * ndiv + k) * 2 + side]
   float tol;
   const int* order;
   const int* n;
@@ -470,10 +472,19 @@ struct BatchArgs {
   int* iters_out;
   float* err_out;
   int* next;
+  float2* Uff;  // [sum n] float-float potentials (solver state)
+  float2* Vff;  // [sum m]
+  float* zU;    // [sum n] last log-sums (shifts)
+  float* zV;    // [sum m]
 };
-size_t batch_smem_bytes(int nmax, int mmax);
-int batch_ctas_per_sm(int nmax, int mmax);
-cudaError_t launch_batch(const BatchArgs& a, int grid, cudaStream_t s);
+// CTA-size variant 0 (8 warps) or 1 (16 warps); the variant for a batch shape
+// (d, nmax, mmax) is timed on a sample of the batch on first use when the
+// tuner is on (batch_pick_variant: synchronises `s`; a.next is left dirty).
+int batch_ctas_per_sm(int d, int variant, int nmax, int mmax);
+int batch_pick_variant(const BatchArgs& a, const int* h_order, cudaStream_t s);
+int batch_force_warps(int warps);  // 8 or 16 forces a CTA size, 0 returns to the tuned one; -1 if invalid
+std::string batch_tune_table();
+cudaError_t launch_batch(const BatchArgs& a, int variant, int grid, cudaStream_t s);
 
 // Algorithm 1 (non-log) half-step on a stored FP64 kernel:
 //   a_i = proxdiv_F(sum_j K_ij b_j w_j, eps), also the violation terms.

@@ -107,6 +107,7 @@ _SIGS = {
     "uot_set_autotune": (C.c_int, [C.c_int]),
     "uot_force_grid_tile": (C.c_int, [C.c_int]),
     "uot_grid_tile_count": (C.c_int, []),
+    "uot_force_batch_warps": (C.c_int, [C.c_int]),
     "uot_autotune_table": (C.c_int, [C.c_char_p, C.c_int]),
     "uot_barycenter": (C.c_int, [C.POINTER(CGeom), C.c_int, C.POINTER(C.c_double), C.c_void_p,
                                  C.c_void_p, C.c_void_p, C.POINTER(CDiv), C.c_double, C.c_int,
@@ -164,6 +165,11 @@ def set_autotune(mode: int) -> int:
 def force_grid_tile(idx: int):
     """Use FP32 grid-pass tile idx for every pass (-1: back to the tuned choice)."""
     _check(load().uot_force_grid_tile(int(idx)), "uot_force_grid_tile")
+
+
+def force_batch_warps(warps: int):
+    """CTA size of solve_batch: 8 or 16 warps, 0 = the tuner's choice."""
+    _check(load().uot_force_batch_warps(int(warps)), "uot_force_batch_warps")
 
 
 def grid_tile_count() -> int:

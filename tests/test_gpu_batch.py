@@ -41,13 +41,24 @@ def make_divs(probs, kinds):
     return out_u, out_o
 
 
-@pytest.mark.parametrize("d,stages", [(2, 0), (3, 4), (1, 0)])
-def test_batch_parity_fixed_iterations(d, stages):
-    probs = synth.batch_points(nprob=14, size=(5, 300), d=d, seed=40 + d)
+@pytest.fixture(params=[8, 16], ids=["8warps", "16warps"])
+def warps(request):
+    U.force_batch_warps(request.param)
+    yield request.param
+    U.force_batch_warps(0)
+
+
+@pytest.mark.parametrize("d,stages,size,nprob,iters", [(2, 0, (5, 300), 14, 25), (3, 4, (5, 300), 14, 25),
+                                                      (1, 0, (5, 300), 14, 25), (2, 0, (700, 2100), 3, 6),
+                                                      (3, 2, (1000, 1300), 2, 5)])
+def test_batch_parity_fixed_iterations(d, stages, size, nprob, iters, warps):
+    """Small problems exercise the contraction split across warps, large ones
+    (more output blocks than warps) one warp per block of 128 outputs."""
+    probs = synth.batch_points(nprob=nprob, size=size, d=d, seed=40 + d + size[0])
     sizes = [(len(pr["x"]), len(pr["y"])) for pr in probs]
     udivs, odivs = make_divs(probs, ["kl", "tv"])
     x, p, dx, y, q, dy = packed(probs)
-    eps, iters = 0.02, 25
+    eps = 0.02
     Ug, Vg, it, errs, info = U.solve_batch(sizes, udivs, d, x, p, dx, y, q, dy, eps, max_iter=iters,
                                            eps_start=0.2 if stages else None, eps_stages=stages,
                                            iters_per_stage=5)
@@ -67,7 +78,7 @@ def test_batch_parity_fixed_iterations(d, stages):
         yo += m
 
 
-def test_batch_converges_to_tolerance():
+def test_batch_converges_to_tolerance(warps):
     """Every problem stops with its violation <= tol, and the oracle, evaluating
     the returned potentials in FP64, agrees that they are that close to a
     fixed point."""
