@@ -201,6 +201,18 @@ int uot_autotune_table(char* buf, int len);
 uot_status uot_force_batch_warps(int warps);
 
 /*
+ * uot_selftest_bounded_wait -- failure-detection self-test (instrumentation).
+ * Runs the bounded device-side wait that guards every wait of a kernel on
+ * other CTAs (the persistent solve's grid barrier) on a flag that nothing
+ * sets: after `seconds` (0 < seconds <= 10) of the GPU's global timer the
+ * wait gives up, sets its status flag and the kernel returns, so the call
+ * returns UOT_TIMEOUT with the CUDA context intact.  Returns UOT_OK only if
+ * the flag were set, UOT_EINVAL for seconds out of range.  Synchronises
+ * `stream`.
+ */
+uot_status uot_selftest_bounded_wait(double seconds, void* stream);
+
+/*
  * uot_solve -- scaling iterations for entropic unbalanced OT (eq. S, Sec. 3.3;
  * Algorithm 2 of Sec. 4.3 in log form; eps-scaling of Sec. 4.4).
  *

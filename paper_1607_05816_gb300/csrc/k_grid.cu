@@ -437,6 +437,24 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
+// Waits until *p != v, for at most limit_ns nanoseconds of the global timer;
+// on expiry sets *status = 1 and returns false.  Every device-side wait on
+// another CTA's progress goes through here.
+__device__ bool bounded_wait_change(const volatile unsigned* p, unsigned v, unsigned long long limit_ns,
+                                    int* status) {
+  const unsigned long long t0 = global_ns();
+  while (*p == v) {
+    __nanosleep(64);
+    if (global_ns() - t0 > limit_ns) {
+      atomicExch(status, 1);
+      return false;
+    }
+  }
+  return true;
+}
+
+constexpr unsigned long long kBarrierLimitNs = 2000000000ull;  // 2 s
+
 // Generation-counting barrier: bar[0] arrivals, bar[1] generation.
 __device__ bool grid_barrier(unsigned* bar, int* status) {
   __syncthreads();
@@ -449,19 +467,18 @@ __device__ bool grid_barrier(unsigned* bar, int* status) {
       __threadfence();
       atomicAdd(bar + 1, 1u);
     } else {
-      const unsigned long long t0 = global_ns();
-      while (*gen == g) {
-        __nanosleep(64);
-        if (global_ns() - t0 > 2000000000ull) {
-          atomicExch(status, 1);
-          break;
-        }
-      }
+      bounded_wait_change(gen, g, kBarrierLimitNs, status);
     }
     __threadfence();
   }
   __syncthreads();
   return *(volatile int*)status == 0;
+}
+
+// The bounded wait on a flag that nothing sets: exercises the expiry path of
+// bounded_wait_change (status set, kernel returns, context stays usable).
+__global__ void wait_selftest(const unsigned* flag, unsigned long long limit_ns, int* status) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) bounded_wait_change(flag, 0u, limit_ns, status);
 }
 
 struct PersistArgs {
@@ -579,6 +596,12 @@ __global__ void __launch_bounds__(kNW * 32, 4)
 }
 
 }  // namespace
+
+cudaError_t launch_wait_selftest(const unsigned* flag, unsigned long long limit_ns, int* status, cudaStream_t s) {
+  count_launches(1);
+  wait_selftest<<<1, 32, 0, s>>>(flag, limit_ns, status);
+  return cudaGetLastError();
+}
 
 int grid_solve_persistent_ctas(int nin_max) {
   int nb = 0, dev = 0, sms = 0;

@@ -1210,6 +1210,30 @@ uot_status uot_force_grid_tile(int idx) { return grid_force_tile(idx) == 0 ? UOT
 
 int uot_grid_tile_count(void) { return grid_tile_count(); }
 
+uot_status uot_selftest_bounded_wait(double seconds, void* stream) {
+  clear_stale_error();
+  if (!(seconds > 0.0) || seconds > 10.0) return UOT_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  Scratch sc(s);
+  sc.reserve<unsigned>(1);
+  sc.reserve<int>(1);
+  UOT_CK(sc.allocate());
+  unsigned* flag = sc.take<unsigned>(1);
+  int* status = sc.take<int>(1);
+  UOT_SCRATCH_OK(sc);
+  UOT_CK(cudaMemsetAsync(flag, 0, sizeof(unsigned), s));
+  UOT_CK(cudaMemsetAsync(status, 0, sizeof(int), s));
+  UOT_CK(launch_wait_selftest(flag, (unsigned long long)(seconds * 1e9), status, s));
+  int h = 0;
+  UOT_CK(cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  UOT_CK(cudaStreamSynchronize(s));
+  if (h) {
+    g_last_error = "bounded device wait expired (self-test: the flag is never set)";
+    return UOT_TIMEOUT;
+  }
+  return UOT_OK;
+}
+
 uot_status uot_force_batch_warps(int warps) { return batch_force_warps(warps) == 0 ? UOT_OK : UOT_EINVAL; }
 
 int uot_autotune_table(char* buf, int len) {

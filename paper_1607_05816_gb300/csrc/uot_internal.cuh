@@ -415,6 +415,8 @@ struct PersistLaunch {
 };
 int grid_solve_persistent_ctas(int nin_max);
 cudaError_t launch_grid_solve_persistent(const PersistLaunch& L, int grid, cudaStream_t s);
+// One thread waits (bounded by limit_ns) for *flag to leave 0; *status = 1 on expiry.
+cudaError_t launch_wait_selftest(const unsigned* flag, unsigned long long limit_ns, int* status, cudaStream_t s);
 
 // Tensor-core (tcgen05) variant of the FP32 grid pass (k_grid_tc.cu); float-
 // float lines in, same epilogues; valid while k (2 r)^2 stays in range (see

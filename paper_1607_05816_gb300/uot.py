@@ -108,6 +108,7 @@ _SIGS = {
     "uot_force_grid_tile": (C.c_int, [C.c_int]),
     "uot_grid_tile_count": (C.c_int, []),
     "uot_force_batch_warps": (C.c_int, [C.c_int]),
+    "uot_selftest_bounded_wait": (C.c_int, [C.c_double, C.c_void_p]),
     "uot_autotune_table": (C.c_int, [C.c_char_p, C.c_int]),
     "uot_barycenter": (C.c_int, [C.POINTER(CGeom), C.c_int, C.POINTER(C.c_double), C.c_void_p,
                                  C.c_void_p, C.c_void_p, C.POINTER(CDiv), C.c_double, C.c_int,
@@ -170,6 +171,15 @@ def force_grid_tile(idx: int):
 def force_batch_warps(warps: int):
     """CTA size of solve_batch: 8 or 16 warps, 0 = the tuner's choice."""
     _check(load().uot_force_batch_warps(int(warps)), "uot_force_batch_warps")
+
+
+def selftest_bounded_wait(seconds: float) -> str:
+    """Status name of the bounded-wait self-test ("UOT_TIMEOUT" when the
+    device wait on a never-set flag expired as designed)."""
+    st = load().uot_selftest_bounded_wait(float(seconds), _stream())
+    if st < 0 and STATUS.get(st) != "UOT_TIMEOUT":
+        _check(st, "uot_selftest_bounded_wait")
+    return STATUS[st]
 
 
 def grid_tile_count() -> int:
