@@ -281,14 +281,16 @@ def run_ours(args, rank, world, local_rank):
     if rank != 0:
         return
     value = all_iters / (total_ms_max / 1e3)
-    exps_per_launch = float(H) ** 3  # nlines * nout * nin for a 256x256 grid pass
-    # Consecutive grid passes overlap (programmatic dependent launch), so the
-    # kernel's time is taken in the pipelined steady state: CUDA-event time of
-    # the timed steps divided by the grid-pass launches they contain (counted
-    # in the profiled step; every other launch is < 0.1% of the launches).
+    # Every Sinkhorn iteration applies 4 separable passes of nlines * nout * nin
+    # = 256^3 terms (launch modes 0-2: one kernel per pass; mode 3: two passes per
+    # kernel).  Consecutive kernels overlap (programmatic dependent launch), so
+    # the kernels' time is taken in the pipelined steady state: the terms of
+    # all iterations over the CUDA-event time of the timed steps (grid-pass
+    # kernels are > 99.9% of the launches, counted in the profiled step).
+    terms_per_iter = 4.0 * float(H) ** 3
     launches_per_step = kern_n
     eff_launch_ms = (total_ms / args.steps) / max(1, launches_per_step)
-    achieved = exps_per_launch / (eff_launch_ms / 1e3) / 1e9
+    achieved = terms_per_iter * (iters / args.steps) / (total_ms / args.steps / 1e3) / 1e9
     avg_kern_ms = kern_ms / max(1, kern_n)
     line = {
         "metric": "sinkhorn_iters_per_s",
@@ -312,10 +314,12 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": launches,
         "clocks": clocks,
         "roofline": alu_roofline(
+            "grid_fused2" if (args.launch_mode == 3 and prec == uot.F32) else
             {uot.F32: "grid_pass_f32", uot.F64: "grid_pass_f64", uot.MIXED: "grid_pass_tc"}[prec], achieved,
             FP32_OPS_PER_TERM["grid"],
-            "achieved from CUDA events over the timed steps / grid-pass launches; isolated_launch_us "
-            "brackets each launch with events in one extra step (this serialises the overlapped launches)",
+            "achieved = 4 passes x 256^3 terms per iteration x iterations / CUDA-event time of the timed "
+            "steps; pipelined_launch_us = step time / grid-pass kernels; isolated_launch_us brackets each "
+            "kernel with events in one extra step (this serialises the overlapped launches)",
             launches_per_step=launches_per_step, pipelined_launch_us=eff_launch_ms * 1e3,
             isolated_launch_us=avg_kern_ms * 1e3),
         "grid_tiles": uot.autotune_table().strip().splitlines(),
@@ -579,8 +583,8 @@ def main():
     ap.add_argument("--workload", default="grid2d", choices=["grid2d", "batch", "points", "dense1d", "bary"])
     ap.add_argument("--penalty", default="kl", choices=["kl", "tv"])
     ap.add_argument("--batch-nprob", type=int, default=0)
-    ap.add_argument("--launch-mode", type=int, default=2, choices=[0, 1, 2],
-                    help="0 one launch per pass, 1 persistent solve, 2 CUDA-graph blocks")
+    ap.add_argument("--launch-mode", type=int, default=2, choices=[0, 1, 2, 3],
+                    help="0 one launch per pass, 1 persistent solve, 2 CUDA-graph blocks, 3 fused pass pairs + graph blocks")
     ap.add_argument("--grid-tile", type=int, default=-1,
                     help="force one FP32 grid-pass tile shape (default: the tuner's choice)")
     args = ap.parse_args()

@@ -127,7 +127,12 @@ typedef struct {
                           2: as 0, but once a block of check_every iterations at the final eps
                           repeats the same launches (shifts from the previous iteration), it
                           is captured once as a CUDA graph and replayed block by block (log
-                          domain, all geometries; per-pass launches where capture fails) */
+                          domain, all geometries; per-pass launches where capture fails);
+                          3: FP32 2-D grids (batch 1): two kernels per iteration, each fusing two
+                          passes on one grid line (the U-update's last pass with the V-update's
+                          first, contracting axis 0 first, and the V-update's last pass with the
+                          next U-update's first), replayed as CUDA-graph blocks like 2; other
+                          problems run as 2 */
   const void* U0;      /* optional warm start [n] (NULL: U = 0) */
   const void* V0;      /* optional warm start [m] (NULL: V = 0, i.e. b = 1 as in Algorithm 1) */
 } uot_opts;

@@ -875,6 +875,11 @@ uot_status solve_impl(const uot_geom* g, int batch, const void* p, const void* d
   const int nst = (int)stages_p.size();
   const bool persist = o->launch_mode == 1 && prec == UOT_F32 && g->kind == UOT_GEOM_GRID &&
                        batch == 1 && !o->plain_scaling;
+  // two kernels per iteration, each fusing two passes on one line (2-D FP32 grids)
+  const bool fused2d = o->launch_mode == 3 && prec == UOT_F32 && g->kind == UOT_GEOM_GRID && g->ndim == 2 &&
+                       batch == 1 && !o->plain_scaling &&
+                       grid_fused2_smem(std::max(g->shape_y[0], g->shape_x[1]), std::max(g->shape_x[0], g->shape_y[1])) <=
+                           160 * 1024;
   if (persist) {
     sc.reserve<float2>(nst + 1);   // eps
     sc.reserve<float2>(nst + 1);   // 1/eps
@@ -1026,6 +1031,152 @@ uot_status solve_impl(const uot_geom* g, int batch, const void* p, const void* d
     it = hs[2];
     total = hs[3];
     err = (o->max_iter > 0) ? herr : INFINITY;
+  } else if (fused2d) {
+    // Pass order per iteration: P1 (contract j2 of V rows) | K_A: P2 (contract j1
+    // -> U columns), P3 (contract i1 of the same columns) | K_B: P4 (contract i2
+    // -> V rows), P1 of the next iteration (contract j2 of the same rows).
+    const int H1 = g->shape_x[0], W1 = g->shape_x[1], H2 = g->shape_y[0], W2 = g->shape_y[1];
+    const float* xa0 = (const float*)g->axes_x[0];
+    const float* xa1 = (const float*)g->axes_x[1];
+    const float* ya0 = (const float*)g->axes_y[0];
+    const float* ya1 = (const float*)g->axes_y[1];
+    float2* T1 = reinterpret_cast<float2*>(G.pass[0]);
+    float2* T2 = reinterpret_cast<float2*>(G.pass[1]);
+    float* z[4] = {G.zbuf[0][0], G.zbuf[0][1], G.zbuf[1][0], G.zbuf[1][1]};
+    double zeps[4] = {-1.0, -1.0, -1.0, -1.0};
+    auto use = [&](int k, double e) {
+      const int u = (zeps[k] == e) ? 1 : 0;
+      zeps[k] = e;
+      return u;
+    };
+    auto p1 = [&](double e, cudaStream_t st) -> cudaError_t {
+      Epilogue r;
+      memset(&r, 0, sizeof(r));
+      r.mode = EPI_RAW;
+      r.eps = e;
+      r.ff = 1;
+      r.out = G.pass[0];
+      r.bstride = (int64_t)H2 * W1;
+      const int u = use(0, e);
+      return launch_grid_pass(UOT_F32, V, logdy, 1, H2, W2, ya1, W1, xa1, e, 1, r, st, z[0], u);
+    };
+    auto fused_args = [&](double e) {
+      FusedArgs f;
+      memset(&f, 0, sizeof(f));
+      f.eps1_ff = ff2(ff_make(e));
+      f.inv_eps1_ff = ff2(ff_make(1.0 / e));
+      f.k2_1 = (float)((double)kLog2e / e);
+      f.do2 = 1;
+      return f;
+    };
+    auto ka = [&](double e, bool check, cudaStream_t st) -> cudaError_t {
+      if (check) {
+        cudaError_t e0 = cudaMemsetAsync(acc, 0, 2 * sizeof(double), st);
+        if (e0 != cudaSuccess) return e0;
+      }
+      FusedArgs f = fused_args(e);
+      f.nlines = W1;
+      f.in1 = T1;
+      f.nin1 = H2;
+      f.nout1 = H1;
+      f.y1 = ya0;
+      f.x1 = xa0;
+      f.out1_row = 0;
+      f.F1 = make_div_ff(D1, e);
+      f.logp1 = reinterpret_cast<const float2*>(logp);
+      f.pot1 = reinterpret_cast<float2*>(U);
+      f.logw1 = reinterpret_cast<const float2*>(logdx);
+      f.err = check ? acc : nullptr;
+      f.z1 = z[1];
+      f.use_prev1 = use(1, e);
+      f.nout2 = H2;
+      f.x2 = ya0;
+      f.inv_eps2_ff = ff2(ff_make(1.0 / e));
+      f.k2_2 = (float)((double)kLog2e / e);
+      f.out2 = T2;
+      f.z2 = z[2];
+      f.use_prev2 = use(2, e);
+      return launch_grid_fused2(f, st);
+    };
+    auto kb = [&](double e, double e_next, cudaStream_t st) -> cudaError_t {
+      FusedArgs f = fused_args(e);
+      f.nlines = H2;
+      f.in1 = T2;
+      f.nin1 = W1;
+      f.nout1 = W2;
+      f.y1 = xa1;
+      f.x1 = ya1;
+      f.out1_row = 1;
+      f.F1 = make_div_ff(D2, e);
+      f.logp1 = reinterpret_cast<const float2*>(logq);
+      f.pot1 = reinterpret_cast<float2*>(V);
+      f.logw1 = reinterpret_cast<const float2*>(logdy);
+      f.z1 = z[3];
+      f.use_prev1 = use(3, e);
+      f.nout2 = W1;
+      f.x2 = xa1;
+      f.inv_eps2_ff = ff2(ff_make(1.0 / e_next));
+      f.k2_2 = (float)((double)kLog2e / e_next);
+      f.out2 = T1;
+      f.z2 = z[0];
+      f.use_prev2 = use(0, e_next);
+      return launch_grid_fused2(f, st);
+    };
+    // eps of the iteration after `total` stage iterations (the final eps after the stages)
+    std::vector<double> stage_eps;
+    for (const Stage& sg : stages)
+      for (int k = 0; k < sg.iters; ++k) stage_eps.push_back(sg.eps);
+    auto eps_at = [&](size_t k) { return k < stage_eps.size() ? stage_eps[k] : o->eps; };
+    UOT_CK(p1(eps_at(0), s));
+    for (size_t k = 0; k < stage_eps.size(); ++k, ++total) {
+      UOT_CK(ka(stage_eps[k], false, s));
+      UOT_CK(kb(stage_eps[k], eps_at(k + 1), s));
+    }
+    auto iteration = [&](bool check, cudaStream_t st) -> cudaError_t {
+      cudaError_t e = ka(o->eps, check, st);
+      if (e != cudaSuccess) return e;
+      return kb(o->eps, o->eps, st);
+    };
+    BlockGraph bg;
+    bool graph_ok = !profiling_on();
+    while (it < o->max_iter) {
+      if (graph_ok && it > 0 && it % check_every == 0 && it + check_every <= o->max_iter) {
+        if (!bg.exec) {
+          cudaError_t e = bg.capture([&](cudaStream_t cs) -> cudaError_t {
+            for (int k = 0; k < check_every; ++k) {
+              cudaError_t e2 = iteration(k == check_every - 1, cs);
+              if (e2 != cudaSuccess) return e2;
+            }
+            return cudaSuccess;
+          });
+          if (e != cudaSuccess) {
+            graph_ok = false;
+            (void)cudaGetLastError();
+            continue;
+          }
+        }
+        UOT_CK(bg.launch(s));
+        it += check_every;
+        total += check_every;
+        UOT_CK(read_err(err));
+        if (o->tol > 0.0 && err <= o->tol) {
+          converged = true;
+          break;
+        }
+        continue;
+      }
+      const bool check = ((it + 1) % check_every == 0) || (it == o->max_iter - 1);
+      UOT_CK(iteration(check, s));
+      ++it;
+      ++total;
+      if (check) {
+        UOT_CK(read_err(err));
+        if (it > 1 && o->tol > 0.0 && err <= o->tol) {
+          converged = true;
+          break;
+        }
+      }
+    }
   } else if (!o->plain_scaling) {
     auto iteration = [&](double eps, bool check, cudaStream_t st) -> cudaError_t {
       cudaError_t e;
@@ -1042,7 +1193,7 @@ uot_status solve_impl(const uot_geom* g, int batch, const void* p, const void* d
     // checked) repeats the same launches -- same eps, shifts from the previous
     // iteration -- it is captured once as a CUDA graph and replayed per block.
     BlockGraph bg;
-    bool graph_ok = o->launch_mode == 2 && !profiling_on();
+    bool graph_ok = (o->launch_mode == 2 || o->launch_mode == 3) && !profiling_on();
     while (it < o->max_iter) {
       if (graph_ok && it > 0 && it % check_every == 0 && it + check_every <= o->max_iter) {
         if (!bg.exec) {

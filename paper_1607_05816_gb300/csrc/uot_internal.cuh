@@ -418,6 +418,42 @@ cudaError_t launch_grid_solve_persistent(const PersistLaunch& L, int grid, cudaS
 // One thread waits (bounded by limit_ns) for *flag to leave 0; *status = 1 on expiry.
 cudaError_t launch_wait_selftest(const unsigned* flag, unsigned long long limit_ns, int* status, cudaStream_t s);
 
+// Two fused separable passes per grid line of a 2-D FP32 problem
+// (k_grid_fused.cu): pass 1 contracts the line's values (from in1) and
+// applies the prox update to the potential pot1 (+ violation); pass 2
+// contracts the line of new potentials (pot1/eps2 + log w, from shared memory)
+// and writes raw log-sums to out2.  One CTA per line.
+struct FusedArgs {
+  int nlines;
+  // pass 1
+  const float2* in1;        // [nlines][nin1] float-float log values
+  int nin1, nout1;
+  const float* y1;          // [nin1] input coordinates
+  const float* x1;          // [nout1] output coordinates (= pass-2 input coordinates)
+  float2 eps1_ff, inv_eps1_ff;
+  float k2_1;               // log2(e)/eps1
+  int out1_row;             // output i of line l at l*nout1 + i (1) or i*nlines + l (0)
+  DivFF F1;
+  const float2* logp1;      // log density at pass-1 outputs (same indexing)
+  float2* pot1;             // potential at pass-1 outputs (old value read, new written)
+  const float2* logw1;      // log weights at pass-1 outputs
+  double* err;              // violation accumulators [2] or NULL
+  float* z1;
+  int use_prev1;
+  // pass 2
+  int do2;
+  int nout2;
+  const float* x2;          // [nout2] output coordinates
+  float2 inv_eps2_ff;
+  float k2_2;
+  float2* out2;             // output i of line l at i*nlines + l
+  float* z2;
+  int use_prev2;
+  double* zero_acc;         // two doubles cleared by block 0 after the dependency wait, or NULL
+};
+size_t grid_fused2_smem(int nin1, int nout1);
+cudaError_t launch_grid_fused2(const FusedArgs& a, cudaStream_t s);
+
 // Tensor-core (tcgen05) variant of the FP32 grid pass (k_grid_tc.cu); float-
 // float lines in, same epilogues; valid while k (2 r)^2 stays in range (see
 // grid_tc_valid).  err_flag is set if a bounded wait gave up.

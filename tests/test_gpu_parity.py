@@ -429,3 +429,39 @@ def test_graph_blocks_match_per_pass_launches(name, make, prec):
     assert abs(i0["marg_err"] - i1["marg_err"]) <= 1e-12
     assert torch.equal(U0, U1) and torch.equal(V0, V1)
     assert n0 == n1
+
+
+@pytest.mark.parametrize("shape_x,shape_y", [((48, 64), (48, 64)), ((37, 70), (45, 29)), ((130, 300), (140, 260))])
+@pytest.mark.parametrize("divs", [DIVS[0], DIVS[1], DIVS[2]], ids=["kl-kl", "tv-kl", "rg-tv"])
+def test_fused_pairs_match_oracle(shape_x, shape_y, divs):
+    """launch_mode 3 (two fused passes per kernel, V-update contracting axis 0
+    first) against the oracle: eps-scaling stages then a fixed number of
+    iterations, uneven shapes and zero densities included."""
+    og, lg, dx, dy, p, q = grid_problem(shape_x, shape_y, 41)
+    oF1, oF2, uF1, uF2 = divs
+    dxr, dyr, pr, qr = rounded(U.F32, dx, dy, p, q)
+    args = [T(a, U.F32).ravel() for a in (pr, dxr, qr, dyr)]
+    eps, iters = 0.01, 15
+    Ug, Vg, info = U.solve(lg(U.F32), *args, uF1, uF2, eps, precision=U.F32, max_iter=iters, eps_start=0.1,
+                           eps_stages=3, iters_per_stage=4, check_every=5, launch_mode=3)
+    r = O.solve_log(round_geom(og, U.F32), dxr, dyr, pr, qr, oF1, oF2, eps, max_iter=iters, eps_start=0.1,
+                    stages=3, iters_per_stage=4)
+    assert info["iters"] == iters and info["total_iters"] == iters + 12
+    assert rel_err(to_np(Ug), r["U"]) <= TOL[U.F32]
+    assert rel_err(to_np(Vg), r["V"]) <= TOL[U.F32]
+
+
+def test_fused_pairs_converge_like_per_pass():
+    """The fused solve stops at the same tolerance as the per-pass solve, in
+    (almost) the same number of iterations, at the same potentials to FP32
+    accuracy."""
+    og, lg, dx, dy, p, q = grid_problem((64, 80), (64, 80), 43, zeros=False)
+    args = [T(a, U.F32).ravel() for a in (p, dx, q, dy)]
+    outs = [U.solve(lg(U.F32), *args, U.KL(0.5), U.KL(0.5), 2e-3, precision=U.F32, max_iter=5000, tol=1e-6,
+                    check_every=10, eps_start=0.1, eps_stages=5, iters_per_stage=20, launch_mode=m)
+            for m in (3, 0)]
+    (U3, V3, i3), (U0, V0, i0) = outs
+    assert i3["status"] == i0["status"] == "UOT_OK"
+    assert i3["marg_err"] <= 1e-6 and abs(i3["iters"] - i0["iters"]) <= 20
+    assert torch.max(torch.abs(U3 - U0)).item() <= 1e-5 * max(1.0, torch.max(torch.abs(U0)).item())
+    assert torch.max(torch.abs(V3 - V0)).item() <= 1e-5 * max(1.0, torch.max(torch.abs(V0)).item())
