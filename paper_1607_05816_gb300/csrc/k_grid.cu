@@ -117,6 +117,9 @@ struct PassArgs {
   float* zprev;        // [nbatch][nout*nlines] approximate result of the previous call, or NULL
   int use_prev;
   double* zero_acc;    // if set, the first block of each batch entry b clears zero_acc[2b..2b+1]
+  int tc3_ok;          // the tensor-core pass (k_grid_tc3.cu) is valid for this pass
+  int* tc_err;         // its bounded-wait flag (may be NULL)
+  int nbatch;
 };
 
 __device__ __forceinline__ ff load_L_ff(const PassArgs& a, const float2* in, int64_t idx) {
@@ -544,6 +547,9 @@ __global__ void __launch_bounds__(kNW * 32, 4)
         a.zprev = P.zbuf[dir][k];
         a.use_prev = it > 0;
         a.zero_acc = nullptr;
+        a.tc3_ok = 0;
+        a.tc_err = nullptr;
+        a.nbatch = 1;
         Epilogue e;
         memset(&e, 0, sizeof(e));
         e.ff = 1;
@@ -749,7 +755,10 @@ namespace {
 struct TileShape {
   int nw, opl;
 };
-constexpr TileShape kTiles[] = {{8, 4}, {4, 4}, {2, 4}, {1, 4}, {8, 2}, {4, 2}, {2, 2}};
+// the last entry stands for the tensor-core pass (k_grid_tc3.cu), used where
+// its block-stabilisation condition holds (else the first tile runs)
+constexpr TileShape kTiles[] = {{8, 4}, {4, 4}, {2, 4}, {1, 4}, {8, 2}, {4, 2}, {2, 2}, {0, 0}};
+constexpr int kTc3Tile = 7;
 constexpr int kNumTiles = (int)(sizeof(kTiles) / sizeof(kTiles[0]));
 
 template <int NW, int OPL>
@@ -777,6 +786,9 @@ cudaError_t launch_f32_tile(const PassArgs& a, const Epilogue& epi, int nbatch, 
 }
 
 cudaError_t launch_f32(int t, const PassArgs& a, const Epilogue& epi, int nbatch, cudaStream_t s) {
+  if (t == kTc3Tile && a.tc3_ok)
+    return launch_grid_pass_tc3(a.in, a.logw, a.in_is_pot, a.nlines, a.nin, a.yi, a.nout, a.xo, a.inv_eps, a.k2,
+                                nbatch, epi, s, a.tc_err, a.zero_acc);
   switch (t) {
     case 0: return launch_f32_tile<8, 4>(a, epi, nbatch, s);
     case 1: return launch_f32_tile<4, 4>(a, epi, nbatch, s);
@@ -784,13 +796,15 @@ cudaError_t launch_f32(int t, const PassArgs& a, const Epilogue& epi, int nbatch
     case 3: return launch_f32_tile<1, 4>(a, epi, nbatch, s);
     case 4: return launch_f32_tile<8, 2>(a, epi, nbatch, s);
     case 5: return launch_f32_tile<4, 2>(a, epi, nbatch, s);
-    default: return launch_f32_tile<2, 2>(a, epi, nbatch, s);
+    case 6: return launch_f32_tile<2, 2>(a, epi, nbatch, s);
+    default: return launch_f32_tile<8, 4>(a, epi, nbatch, s);
   }
 }
 
 struct TuneKey {
-  int dev, nlines, nin, nout, nbatch;
+  int dev, nlines, nin, nout, nbatch, tc3;
   bool operator<(const TuneKey& o) const {
+    if (tc3 != o.tc3) return tc3 < o.tc3;
     if (dev != o.dev) return dev < o.dev;
     if (nlines != o.nlines) return nlines < o.nlines;
     if (nin != o.nin) return nin < o.nin;
@@ -861,7 +875,7 @@ TuneEntry tune_tiles(const PassArgs& base, int nbatch, cudaStream_t s) {
     bool wok = step(0, 0) && step(0, 0);
     for (int r = 0; r < kWarm && wok; ++r) wok = step(0, 1);
     for (int t = 0; t < kNumTiles; ++t) {
-      okt[t] = wok;
+      okt[t] = wok && (t != kTc3Tile || base.tc3_ok);
       tmin[t] = 1e30f;
     }
     for (int round = 0; round < kRounds && wok; ++round) {
@@ -917,6 +931,7 @@ int pick_tile(const PassArgs& a, int nbatch, cudaStream_t s) {
   key.nin = a.nin;
   key.nout = a.nout;
   key.nbatch = nbatch;
+  key.tc3 = a.tc3_ok;
   auto it = g_tuned.find(key);
   if (it != g_tuned.end()) return it->second.tile;
   if (g_tune_hold) return 0;
@@ -937,6 +952,12 @@ int grid_set_autotune(int mode) {
   const int prev = g_autotune;
   g_autotune = mode ? 1 : 0;
   return prev;
+}
+
+int grid_tc3_wanted() {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  if (g_tune_hold) return 0;
+  return (g_forced_tile == kTc3Tile || (g_forced_tile < 0 && g_autotune)) ? 1 : 0;
 }
 
 int grid_autotune_enabled() {
@@ -962,11 +983,18 @@ std::string grid_tile_table() {
   for (const auto& kv : g_tuned) {
     const TuneKey& k = kv.first;
     const TuneEntry& e = kv.second;
-    snprintf(buf, sizeof(buf), "dev%d lines=%d nin=%d nout=%d batch=%d -> warps=%d outputs/lane=%d;", k.dev,
-             k.nlines, k.nin, k.nout, k.nbatch, kTiles[e.tile].nw, kTiles[e.tile].opl);
+    if (e.tile == kTc3Tile)
+      snprintf(buf, sizeof(buf), "dev%d lines=%d nin=%d nout=%d batch=%d -> tensor-core tc3;", k.dev, k.nlines, k.nin,
+               k.nout, k.nbatch);
+    else
+      snprintf(buf, sizeof(buf), "dev%d lines=%d nin=%d nout=%d batch=%d -> warps=%d outputs/lane=%d;", k.dev,
+               k.nlines, k.nin, k.nout, k.nbatch, kTiles[e.tile].nw, kTiles[e.tile].opl);
     s += buf;
     for (int t = 0; t < kNumTiles; ++t) {
-      snprintf(buf, sizeof(buf), " %dx%d:%.2fus", kTiles[t].nw, kTiles[t].opl, e.us[t]);
+      if (t == kTc3Tile)
+        snprintf(buf, sizeof(buf), " tc3:%.2fus", e.us[t]);
+      else
+        snprintf(buf, sizeof(buf), " %dx%d:%.2fus", kTiles[t].nw, kTiles[t].opl, e.us[t]);
       s += buf;
     }
     s += "\n";
@@ -977,7 +1005,7 @@ std::string grid_tile_table() {
 cudaError_t launch_grid_pass(int prec, const double* in, const double* logw, int in_is_pot,
                              int nlines, int nin, const void* yi, int nout, const void* xo,
                              double eps, int nbatch, const Epilogue& epi, cudaStream_t s,
-                             float* zprev, int use_prev, double* zero_acc) {
+                             float* zprev, int use_prev, double* zero_acc, int tc3_ok, int* tc_err) {
   if (prec == UOT_F32) {
     PassArgs a;
     a.in = reinterpret_cast<const float2*>(in);
@@ -993,6 +1021,9 @@ cudaError_t launch_grid_pass(int prec, const double* in, const double* logw, int
     a.zprev = zprev;
     a.use_prev = use_prev;
     a.zero_acc = zero_acc;
+    a.tc3_ok = (tc3_ok && nin <= grid_pass_tc3_max_nin()) ? 1 : 0;
+    a.tc_err = tc_err;
+    a.nbatch = nbatch;
     const int tile = pick_tile(a, nbatch, s);
     prof_mark_begin(PROF_GRID_PASS, s);
     count_launches(1);

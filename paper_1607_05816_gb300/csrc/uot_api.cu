@@ -521,6 +521,7 @@ struct Gibbs {
   // and a flag set by the tensor-core kernel if a bounded wait gave up
   double span_x[UOT_MAX_DIM] = {0, 0, 0}, span_y[UOT_MAX_DIM] = {0, 0, 0};
   int* tc_err = nullptr;
+  bool spans_known = false;
   void* Lscratch = nullptr;     // rows: shifted input line
   void* part = nullptr;         // FP32 point clouds: per-chunk partial sums
   float* zrow[2] = {nullptr, nullptr};  // FP32 point clouds: previous results per direction
@@ -540,7 +541,7 @@ struct Gibbs {
       }
       if (speculate && prec == UOT_F32)
         for (int k = 0; k < 2 * g.ndim; ++k) sc.reserve<float>((size_t)inter * nbatch);
-      if (prec == UOT_MIXED) sc.reserve<int>(1);
+      if (prec == UOT_MIXED || prec == UOT_F32) sc.reserve<int>(1);
     } else {
       const int64_t mx = (g.n > g.m ? g.n : g.m);
       sc.reserve<char>((size_t)mx * 8 + 512);
@@ -577,25 +578,34 @@ struct Gibbs {
       if (speculate && prec == UOT_F32)
         for (int d = 0; d < 2; ++d)
           for (int k = 0; k < g.ndim; ++k) zbuf[d][k] = sc.take<float>((size_t)inter * nbatch);
-      if (prec == UOT_MIXED) {
+      if (prec == UOT_MIXED || prec == UOT_F32) {
         tc_err = sc.take<int>(1);
         if (!tc_err) return cudaErrorInvalidValue;
         cudaError_t e = cudaMemsetAsync(tc_err, 0, sizeof(int), s);
         if (e != cudaSuccess) return e;
-        for (int side = 0; side < 2; ++side) {
-          for (int k = 0; k < g.ndim; ++k) {
-            const int len = side == 0 ? g.shape_x[k] : g.shape_y[k];
-            std::vector<float> h(len);
-            e = cudaMemcpyAsync(h.data(), side == 0 ? g.axes_x[k] : g.axes_y[k], len * sizeof(float),
-                                cudaMemcpyDeviceToHost, s);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-            if (e != cudaSuccess) return e;
-            double span = 0.0;
-            for (int i0 = 0; i0 < len; i0 += 32)
-              for (int i = i0; i < std::min(len, i0 + 32); ++i)
-                span = std::max(span, std::fabs((double)h[i] - (double)h[i0]));
-            (side == 0 ? span_x : span_y)[k] = span;
-          }
+        // largest coordinate span of the 32-point blocks of every axis (tensor-core passes)
+        if (prec == UOT_MIXED || grid_tc3_wanted()) {
+          std::vector<float> h[2][UOT_MAX_DIM];
+          for (int side = 0; side < 2; ++side)
+            for (int k = 0; k < g.ndim; ++k) {
+              const int len = side == 0 ? g.shape_x[k] : g.shape_y[k];
+              h[side][k].resize(len);
+              e = cudaMemcpyAsync(h[side][k].data(), side == 0 ? g.axes_x[k] : g.axes_y[k], len * sizeof(float),
+                                  cudaMemcpyDeviceToHost, s);
+              if (e != cudaSuccess) return e;
+            }
+          if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+          for (int side = 0; side < 2; ++side)
+            for (int k = 0; k < g.ndim; ++k) {
+              const std::vector<float>& v = h[side][k];
+              const int len = (int)v.size();
+              double span = 0.0;
+              for (int i0 = 0; i0 < len; i0 += 32)
+                for (int i = i0; i < std::min(len, i0 + 32); ++i)
+                  span = std::max(span, std::fabs((double)v[i] - (double)v[i0]));
+              (side == 0 ? span_x : span_y)[k] = span;
+            }
+          spans_known = true;
         }
       }
     } else {
@@ -620,6 +630,14 @@ struct Gibbs {
     const double so = (dir == 0 ? span_x : span_y)[ax], si = (dir == 0 ? span_y : span_x)[ax];
     const double reach = (double)kLog2e / eps * (so + si) * (so + si);
     return reach <= 100.0 && grid_pass_tc_smem(nin) <= 200 * 1024;
+  }
+  // The three-part tensor-core pass keeps its smallest operand parts normal
+  // while k (span_out + span_in)^2 <= 90 (log2 units) and takes nin <= 256.
+  int tc3_ok(int dir, int ax, double eps, int nin) const {
+    if (!spans_known || prec != UOT_F32) return 0;
+    const double so = (dir == 0 ? span_x : span_y)[ax], si = (dir == 0 ? span_y : span_x)[ax];
+    const double reach = (double)kLog2e / eps * (so + si) * (so + si);
+    return (reach <= 90.0 && nin <= grid_pass_tc3_max_nin()) ? 1 : 0;
   }
 
   // zero_acc: two doubles cleared before the result is produced (violation
@@ -664,7 +682,8 @@ struct Gibbs {
         } else {
           err = launch_grid_pass(prec == UOT_F64 ? UOT_F64 : UOT_F32, cur, logw, cur_is_pot,
                                  (int)nlines, in_shape[ax], in_axes[ax], out_shape[ax],
-                                 out_axes[ax], eps, nbatch, e, s, zbuf[dir][k], use_prev, za);
+                                 out_axes[ax], eps, nbatch, e, s, zbuf[dir][k], use_prev, za,
+                                 tc3_ok(dir, ax, eps, in_shape[ax]), tc_err);
         }
         if (err != cudaSuccess) return err;
         cur = pass[k & 1];

@@ -368,10 +368,21 @@ void prof_mark_end(int family, cudaStream_t s);
 // FP32 only: zprev (optional, [nbatch][nout*nlines]) receives this pass's
 // result; with use_prev = 1 its previous content is used as the shift of the
 // log-sum-exp (see k_grid.cu).
+// tc3_ok: the tensor-core pass (k_grid_tc3.cu) may be used (the tuner's last
+// tile) -- its block-stabilisation condition k (span_out + span_in)^2 <= 90
+// holds for 32-point blocks of both axes; tc_err receives its wait flag.
 cudaError_t launch_grid_pass(int prec, const double* in, const double* logw, int in_is_pot,
                              int nlines, int nin, const void* yi, int nout, const void* xo,
                              double eps, int nbatch, const Epilogue& epi, cudaStream_t s,
-                             float* zprev, int use_prev, double* zero_acc = nullptr);
+                             float* zprev, int use_prev, double* zero_acc = nullptr, int tc3_ok = 0,
+                             int* tc_err = nullptr);
+
+// The tensor-core pass with three-part BF16 operands (k_grid_tc3.cu): same
+// result as the FP32 pass to FP32 accuracy; nin <= grid_pass_tc3_max_nin().
+int grid_pass_tc3_max_nin();
+cudaError_t launch_grid_pass_tc3(const float2* in, const float2* logw, int in_is_pot, int nlines, int nin,
+                                 const float* yi, int nout, const float* xo, float2 inv_eps, float k2, int nbatch,
+                                 const Epilogue& epi, cudaStream_t s, int* err_flag, double* zero_acc);
 
 // Tile shapes of the FP32 grid pass (warps splitting the contraction x
 // outputs per lane) and the tuner that times them once per pass shape
@@ -382,6 +393,7 @@ cudaError_t launch_grid_pass(int prec, const double* in, const double* logw, int
 //  grid_tile_table(): the tuned shapes and their measured times, one line per pass shape.
 int grid_set_autotune(int mode);
 int grid_autotune_enabled();
+int grid_tc3_wanted();  // the tensor-core tile may be chosen (tuner on or tile forced), not held
 int grid_force_tile(int idx);
 int grid_tile_count();
 void grid_tune_hold(int on);

@@ -348,12 +348,14 @@ def test_persistent_launch_matches_per_pass_launches(shape):
 # FP32 grid-pass tile shapes and the tuner
 # ----------------------------------------------------------------------------
 
-@pytest.mark.parametrize("tile", range(7))
+@pytest.mark.parametrize("tile", range(8))
 @pytest.mark.parametrize("name,make", GIBBS_CASES[:3])
 def test_every_grid_tile_matches_oracle(tile, name, make):
     """Every tile shape the tuner may pick computes the operator and a short
-    KL/TV solve to the FP32 tolerance (ragged lines and outputs included)."""
-    assert U.grid_tile_count() == 7
+    KL/TV solve to the FP32 tolerance (ragged lines and outputs included).
+    Tile 7 is the tensor-core pass, which these coarse grids at eps = 0.01
+    do not admit (the SIMT tile runs instead)."""
+    assert U.grid_tile_count() == 8
     og, lg, dx, dy, p, q = make()
     g = synth.rng(19)
     eps = 0.01
@@ -394,13 +396,15 @@ def test_autotuner_records_choice_and_keeps_parity():
         lines = [ln for ln in table.splitlines() if "nin=79 nout=83" in ln and "lines=61" in ln]
         assert len(lines) == 1, table
         times = [float(t.split(":")[1][:-2]) for t in lines[0].split(";")[1].split()]
-        assert len(times) == 7 and all(t > 0 for t in times)
+        assert len(times) == 8 and all(t > 0 for t in times[:7])
+        times = [t if t > 0 else math.inf for t in times]  # tc3 not admitted on this grid
         chosen = lines[0].split("-> ")[1].split(";")[0]
         best = int(np.argmin(times))
         if times[0] <= 1.05 * times[best]:
             best = 0  # the first tile is kept unless another one is more than 5% faster
-        shapes = [(8, 4), (4, 4), (2, 4), (1, 4), (8, 2), (4, 2), (2, 2)]
-        assert chosen == "warps=%d outputs/lane=%d" % shapes[best]
+        names = ["warps=%d outputs/lane=%d" % sh for sh in [(8, 4), (4, 4), (2, 4), (1, 4), (8, 2), (4, 2), (2, 2)]]
+        names.append("tensor-core tc3")
+        assert chosen == names[best]
     finally:
         U.set_autotune(prev)
 
@@ -465,3 +469,68 @@ def test_fused_pairs_converge_like_per_pass():
     assert i3["marg_err"] <= 1e-6 and abs(i3["iters"] - i0["iters"]) <= 20
     assert torch.max(torch.abs(U3 - U0)).item() <= 1e-5 * max(1.0, torch.max(torch.abs(U0)).item())
     assert torch.max(torch.abs(V3 - V0)).item() <= 1e-5 * max(1.0, torch.max(torch.abs(V0)).item())
+
+
+# ----------------------------------------------------------------------------
+# tensor-core pass with three-part BF16 operands (tile 7)
+# ----------------------------------------------------------------------------
+
+TC3_CASES = [
+    ("fine2d", lambda: grid_problem((200, 256), (256, 180), 51), 2e-3),
+    ("batchlike", lambda: grid_problem((128, 128), (128, 128), 52), 1e-2),
+    ("ragged", lambda: grid_problem((150, 97), (130, 70), 53), 1e-2),
+]
+
+
+@pytest.mark.parametrize("name,make,eps", TC3_CASES)
+def test_tc3_pass_matches_oracle(name, make, eps):
+    """Forced tensor-core tile on grids fine enough for its block condition:
+    the Gibbs operator in both directions and a short KL/TV solve at the FP32
+    tolerance, and bitwise different from the SIMT tile (another kernel ran)."""
+    og, lg, dx, dy, p, q = make()
+    g = synth.rng(61)
+    try:
+        for transpose in (False, True):
+            shape_in = np.shape(dx) if transpose else np.shape(dy)
+            W = g.normal(size=shape_in) * 0.05
+            W.ravel()[5:: 13] = -np.inf
+            w = dx if transpose else dy
+            W, w = rounded(U.F32, W, w)
+            want = O.apply_K_log(round_geom(og, U.F32), W, np.log(w), eps, transpose=transpose)
+            outs = []
+            for tile in (7, 0):
+                U.force_grid_tile(tile)
+                outs.append(to_np(U.gibbs_log(lg(U.F32), T(W, U.F32).ravel(), T(w, U.F32).ravel(), eps,
+                                              transpose, U.F32)))
+            assert rel_err(outs[0], want) <= TOL[U.F32]
+            assert not np.array_equal(outs[0], outs[1])
+        U.force_grid_tile(7)
+        dxr, dyr, pr, qr = rounded(U.F32, dx, dy, p, q)
+        Ug, Vg, _ = U.solve(lg(U.F32), *[T(a, U.F32).ravel() for a in (pr, dxr, qr, dyr)], U.KL(0.7),
+                            U.TV(0.4), eps, precision=U.F32, max_iter=10)
+        r = O.solve_log(round_geom(og, U.F32), dxr, dyr, pr, qr, O.KL(0.7), O.TV(0.4), eps, max_iter=10)
+        assert rel_err(to_np(Ug), r["U"]) <= TOL[U.F32]
+        assert rel_err(to_np(Vg), r["V"]) <= TOL[U.F32]
+    finally:
+        U.force_grid_tile(-1)
+
+
+def test_tc3_barycenter_matches_oracle():
+    """Batched lines (8 measures of 128 x 128) through the tensor-core tile."""
+    b = synth.barycenter_images(8, 128, 128, seed=62)
+    alpha = np.full(8, 1.0 / 8)
+    eps, lam, iters = 1e-2, 1.0, 4
+    xs = [np.asarray(a, np.float32).astype(np.float64) for a in b["xs"]]
+    geo = U.Geometry.grid([T(a, U.F32) for a in xs])
+    P = np.asarray(b["P"], np.float32).astype(np.float64)
+    U.force_grid_tile(7)
+    try:
+        lh, Ug, Vg, _ = U.barycenter(geo, alpha, T(P.reshape(8, -1), U.F32), T(b["dx"], U.F32).ravel(),
+                                     T(b["dy"], U.F32).ravel(), U.EQ(), lam, eps, precision=U.F32, max_iter=iters)
+    finally:
+        U.force_grid_tile(-1)
+    og = O.Geometry("grid", xs=xs, ys=xs)
+    dxr, dyr = rounded(U.F32, b["dx"], b["dy"])
+    Uo, Vo, lho = O.barycenter_log(og, dxr, dyr, P, alpha, O.EQ(), lam, eps, iters)
+    assert rel_err(to_np(lh), lho) <= TOL[U.F32]
+    assert rel_err(to_np(Vg).reshape(8, -1), Vo.reshape(8, -1)) <= TOL[U.F32]
