@@ -392,7 +392,8 @@ def run_single(args, rank, world, local_rank):
         def step():
             dt = torch.float64 if prec == uot.F64 else torch.float32
             lh, U_, V_, info = uot.barycenter(geo, alpha, P, f(b["dx"], dt).ravel(), f(b["dy"], dt).ravel(),
-                                              uot.EQ(), 1.0, 1e-2, precision=prec, max_iter=500)
+                                              uot.EQ(), 1.0, 1e-2, precision=prec, max_iter=500,
+                                              launch_mode=args.launch_mode)
             return U_, V_, info
         work_per_iter, unit_work, kernel = 32 * 2 * 2 * 128.0 ** 3, "Gexp2/s", "grid_pass"
         cfg = {"workload": "bary32-128x128-kl1-eps1e-2-500it", "K": 32, "grid": [128, 128]}

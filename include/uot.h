@@ -127,7 +127,8 @@ typedef struct {
                           2: as 0, but once a block of check_every iterations at the final eps
                           repeats the same launches (shifts from the previous iteration), it
                           is captured once as a CUDA graph and replayed block by block (log
-                          domain, all geometries; per-pass launches where capture fails);
+                          domain, all geometries, uot_solve_many and uot_barycenter too;
+                          per-pass launches where capture fails);
                           3: FP32 2-D grids (batch 1): two kernels per iteration, each fusing two
                           passes on one grid line (the U-update's last pass with the V-update's
                           first, contracting axis 0 first, and the V-update's last pass with the

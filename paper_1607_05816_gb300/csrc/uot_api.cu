@@ -263,53 +263,88 @@ __global__ void k_bary_update(const double* __restrict__ T, int K, int64_t m,
 }
 
 // FP32 path of k_bary_update: float-float T, V, logh; FP32 arithmetic.
-__global__ void k_bary_update_ff(const double* __restrict__ Td, int K, int64_t m,
-                                 const float* __restrict__ log_alpha, float log_sum_alpha,
-                                 float2 epslam, float2 inv_epslam, float2 inv_eps, float2 eps_ff,
-                                 int kind, DivFF Fh, double* __restrict__ loghd,
-                                 double* __restrict__ Vd) {
+// Barycenter update (Table 2 with Table 1 for the couplings' second marginals),
+// float-float.  A CTA of kBJ x kBK threads takes 32 consecutive points j
+// (lanes, coalesced over j) and splits the K measures over kBK warps; the
+// per-point reductions over k (max and sum of the power mean, or the weighted
+// geometric mean) are merged through shared memory.
+constexpr int kBJ = 32, kBK = 8;
+
+__global__ void __launch_bounds__(kBJ * kBK)
+    k_bary_update_ff(const double* __restrict__ Td, int K, int64_t m, const float* __restrict__ log_alpha,
+                     float log_sum_alpha, float2 epslam, float2 inv_epslam, float2 inv_eps, float2 eps_ff,
+                     int kind, DivFF Fh, double* __restrict__ loghd, double* __restrict__ Vd) {
   const float2* T = reinterpret_cast<const float2*>(Td);
   float2* logh = reinterpret_cast<float2*>(loghd);
   float2* V = reinterpret_cast<float2*>(Vd);
-  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m;
-       j += (int64_t)gridDim.x * blockDim.x) {
+  __shared__ float r0[kBK][kBJ], r1[kBK][kBJ];
+  __shared__ int rneg[kBK][kBJ];
+  const int lane = threadIdx.x, ky = threadIdx.y;
+  for (int64_t jb = (int64_t)blockIdx.x * kBJ; jb < m; jb += (int64_t)gridDim.x * kBJ) {
+    const int64_t j = jb + lane;
+    const bool valid = j < m;
     ff elogh;
     if (kind == UOT_BARY_KL) {
       // eps log h = (eps+lam) (LSE_k(log alpha_k + T_k/(eps+lam)) - log sum alpha)
       float mx = -INFINITY;
-      for (int k = 0; k < K; ++k) {
+      for (int k = ky; k < K && valid; k += kBK) {
         const ff t = ffl(T[(int64_t)k * m + j]);
         if (t.hi != -INFINITY) mx = fmaxf(mx, ff_add_f(ff_mul(t, ffl(inv_epslam)), log_alpha[k]).hi);
       }
-      if (mx == -INFINITY) {
-        elogh = ff_ninf();
-      } else {
-        float acc = 0.0f;
-        ff lead = ff{0.0f, 0.0f};
-        for (int k = 0; k < K; ++k) {
+      r0[ky][lane] = mx;
+      __syncthreads();
+      mx = r0[0][lane];
+#pragma unroll
+      for (int w = 1; w < kBK; ++w) mx = fmaxf(mx, r0[w][lane]);
+      float acc = 0.0f;
+      if (mx != -INFINITY) {
+        for (int k = ky; k < K && valid; k += kBK) {
           const ff t = ffl(T[(int64_t)k * m + j]);
           if (t.hi == -INFINITY) continue;
           const ff a = ff_add_f(ff_mul(t, ffl(inv_epslam)), log_alpha[k]);
           acc += expf((a.hi - mx) + a.lo);
         }
-        lead = ff_add_f(ff{mx, 0.0f}, logf(acc) - log_sum_alpha);
+      }
+      r1[ky][lane] = acc;
+      __syncthreads();
+      acc = 0.0f;
+#pragma unroll
+      for (int w = 0; w < kBK; ++w) acc += r1[w][lane];
+      if (mx == -INFINITY) {
+        elogh = ff_ninf();
+      } else {
+        const ff lead = ff_add_f(ff{mx, 0.0f}, logf(acc) - log_sum_alpha);
         elogh = ff_mul(lead, ffl(epslam));
       }
     } else {
       // eps log h = sum_k alpha_k T_k / sum alpha (geometric mean)
       ff acc = ff{0.0f, 0.0f};
-      bool neg_inf = false;
-      for (int k = 0; k < K; ++k) {
+      int neg_inf = 0;
+      for (int k = ky; k < K && valid; k += kBK) {
         const ff t = ffl(T[(int64_t)k * m + j]);
-        if (t.hi == -INFINITY) neg_inf = true;
+        if (t.hi == -INFINITY) neg_inf = 1;
         else acc = ff_add(acc, ff_mul_f(t, expf(log_alpha[k] - log_sum_alpha)));
+      }
+      r0[ky][lane] = acc.hi;
+      r1[ky][lane] = acc.lo;
+      rneg[ky][lane] = neg_inf;
+      __syncthreads();
+      acc = ff{0.0f, 0.0f};
+      neg_inf = 0;
+#pragma unroll
+      for (int w = 0; w < kBK; ++w) {
+        acc = ff_add(acc, ff{r0[w][lane], r1[w][lane]});
+        neg_inf |= rneg[w][lane];
       }
       elogh = neg_inf ? ff_ninf() : acc;
     }
-    logh[j] = ff2(elogh);
-    const ff lh = (elogh.hi == -INFINITY) ? ff_ninf() : ff_mul(elogh, ffl(inv_eps));
-    for (int k = 0; k < K; ++k)
-      V[(int64_t)k * m + j] = ff2(prox_update_ff(Fh, lh, ffl(T[(int64_t)k * m + j]), ffl(eps_ff)));
+    if (valid) {
+      if (ky == 0) logh[j] = ff2(elogh);
+      const ff lh = (elogh.hi == -INFINITY) ? ff_ninf() : ff_mul(elogh, ffl(inv_eps));
+      for (int k = ky; k < K; k += kBK)
+        V[(int64_t)k * m + j] = ff2(prox_update_ff(Fh, lh, ffl(T[(int64_t)k * m + j]), ffl(eps_ff)));
+    }
+    __syncthreads();  // the reduction buffers are reused by the next points
   }
 }
 
@@ -2017,12 +2052,12 @@ uot_status uot_barycenter(const uot_geom* g, int Kmeas, const double* alpha, con
   k_fill<<<nblocks(m * Kmeas), kNT, 0, s>>>(V, m * Kmeas, 0.0);
   UOT_CK(cudaGetLastError());
 
-  auto iteration = [&](double eps, bool check) -> cudaError_t {
+  auto iteration = [&](double eps, bool check, cudaStream_t st) -> cudaError_t {
     cudaError_t e;
     Epilogue e1 = prox_epilogue(D1, logP, U, logdx, check ? acc : nullptr, eps);
     e1.bstride = n;
     e1.bstride_p = n;
-    if ((e = G.apply(0, V, logdy, eps, e1, s, check ? acc : nullptr)) != cudaSuccess) return e;
+    if ((e = G.apply(0, V, logdy, eps, e1, st, check ? acc : nullptr)) != cudaSuccess) return e;
     Epilogue e2;
     memset(&e2, 0, sizeof(e2));
     e2.mode = EPI_SCALE;
@@ -2030,19 +2065,29 @@ uot_status uot_barycenter(const uot_geom* g, int Kmeas, const double* alpha, con
     e2.out = T;
     e2.bstride = m;
     count_launches(1);
-    if ((e = G.apply(1, U, logdx, eps, e2, s)) != cudaSuccess) return e;
+    if ((e = G.apply(1, U, logdx, eps, e2, st)) != cudaSuccess) return e;
     if (prec == UOT_F64) {
-      k_bary_update<<<nblocks(m), kNT, 0, s>>>(T, Kmeas, m, alpha_d, sum_alpha, lambda, eps,
-                                               bary_kind, logh, V);
+      k_bary_update<<<nblocks(m), kNT, 0, st>>>(T, Kmeas, m, alpha_d, sum_alpha, lambda, eps,
+                                                bary_kind, logh, V);
     } else {
       DivParams Dh;
       Dh.kind = (bary_kind == UOT_BARY_KL) ? UOT_DIV_KL : UOT_DIV_EQ;
       Dh.lam = lambda;
       Dh.log_alpha = Dh.log_beta = 0.0;
-      k_bary_update_ff<<<nblocks(m), kNT, 0, s>>>(
-          T, Kmeas, m, log_alpha_d, (float)log(sum_alpha), ff2(ff_make(eps + lambda)),
-          ff2(ff_make(1.0 / (eps + lambda))), ff2(ff_make(1.0 / eps)), ff2(ff_make(eps)),
-          bary_kind, make_div_ff(Dh, eps), logh, V);
+      cudaLaunchConfig_t cfg;
+      memset(&cfg, 0, sizeof(cfg));
+      cfg.gridDim = dim3((unsigned)std::min<int64_t>((m + kBJ - 1) / kBJ, 1 << 20));
+      cfg.blockDim = dim3(kBJ, kBK);
+      cfg.stream = st;
+      // a plain (fully serialised) launch: measured faster here than a
+      // programmatic dependent launch, whose early-launched successor CTAs
+      // compete with this small grid
+      cfg.attrs = nullptr;
+      cfg.numAttrs = 0;
+      e = cudaLaunchKernelEx(&cfg, k_bary_update_ff, (const double*)T, Kmeas, (int64_t)m, (const float*)log_alpha_d,
+                             (float)log(sum_alpha), ff2(ff_make(eps + lambda)), ff2(ff_make(1.0 / (eps + lambda))),
+                             ff2(ff_make(1.0 / eps)), ff2(ff_make(eps)), bary_kind, make_div_ff(Dh, eps), logh, V);
+      if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
   };
@@ -2052,12 +2097,37 @@ uot_status uot_barycenter(const uot_geom* g, int Kmeas, const double* alpha, con
   double err = INFINITY;
   bool converged = false;
   for (const Stage& sg : stages)
-    for (int k = 0; k < sg.iters; ++k, ++total) UOT_CK(iteration(sg.eps, false));
+    for (int k = 0; k < sg.iters; ++k, ++total) UOT_CK(iteration(sg.eps, false, s));
+  // launch_mode 2: checked blocks of check_every iterations replayed from a CUDA graph
+  BlockGraph bg;
+  bool graph_ok = o->launch_mode == 2 && !profiling_on();
   while (it < o->max_iter) {
-    const bool check = ((it + 1) % check_every == 0) || (it == o->max_iter - 1);
-    UOT_CK(iteration(o->eps, check));
-    ++it;
-    ++total;
+    bool check;
+    if (graph_ok && it > 0 && it % check_every == 0 && it + check_every <= o->max_iter) {
+      if (!bg.exec) {
+        cudaError_t e = bg.capture([&](cudaStream_t cs) -> cudaError_t {
+          for (int k = 0; k < check_every; ++k) {
+            cudaError_t e2 = iteration(o->eps, k == check_every - 1, cs);
+            if (e2 != cudaSuccess) return e2;
+          }
+          return cudaSuccess;
+        });
+        if (e != cudaSuccess) {
+          graph_ok = false;
+          (void)cudaGetLastError();
+          continue;
+        }
+      }
+      UOT_CK(bg.launch(s));
+      it += check_every;
+      total += check_every;
+      check = true;
+    } else {
+      check = ((it + 1) % check_every == 0) || (it == o->max_iter - 1);
+      UOT_CK(iteration(o->eps, check, s));
+      ++it;
+      ++total;
+    }
     if (check) {
       UOT_CK(cudaMemcpyAsync(acc_h.data(), acc, 16 * (size_t)Kmeas, cudaMemcpyDeviceToHost, s));
       UOT_CK(cudaStreamSynchronize(s));

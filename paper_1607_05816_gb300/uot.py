@@ -431,7 +431,7 @@ def objective(geom: Geometry, p, dx, q, dy, F1: Div, F2: Div, eps, U, V, precisi
 
 def barycenter(geom: Geometry, alpha, P, dx, dy, F1: Div, lam, eps, *, kind=BARY_KL,
                precision=F64, max_iter=1000, tol=0.0, check_every=10, eps_start=None,
-               eps_stages=10, iters_per_stage=100):
+               eps_stages=10, iters_per_stage=100, launch_mode=0):
     """uot_barycenter: returns (eps log h, U [K,n], V [K,m], result dict)."""
     lib = load()
     dt = _dtype(precision)
@@ -441,7 +441,8 @@ def barycenter(geom: Geometry, alpha, P, dx, dy, F1: Div, lam, eps, *, kind=BARY
     V = torch.empty(K, geom.m, dtype=dt, device=P.device)
     a = (C.c_double * K)(*[float(v) for v in alpha])
     o = COpts(precision, float(eps), float(eps_start) if eps_start else 0.0, int(eps_stages),
-              int(iters_per_stage), int(max_iter), float(tol), int(check_every), 0, 0, None, None)
+              int(iters_per_stage), int(max_iter), float(tol), int(check_every), 0, int(launch_mode), None,
+              None)
     r = CResult()
     g = geom.c(precision)
     st = lib.uot_barycenter(C.byref(g), K, a, _ptr(P, dt, "P"), _ptr(dx, dt, "dx"),

@@ -534,3 +534,17 @@ def test_tc3_barycenter_matches_oracle():
     Uo, Vo, lho = O.barycenter_log(og, dxr, dyr, P, alpha, O.EQ(), lam, eps, iters)
     assert rel_err(to_np(lh), lho) <= TOL[U.F32]
     assert rel_err(to_np(Vg).reshape(8, -1), Vo.reshape(8, -1)) <= TOL[U.F32]
+
+
+def test_barycenter_graph_blocks_match_per_pass():
+    """The barycenter loop replayed as CUDA-graph blocks (launch_mode 2) runs
+    the same kernels: identical result to per-pass launches."""
+    b = synth.barycenter_images(6, 48, 40, seed=71)
+    alpha = np.full(6, 1.0 / 6)
+    geo = U.Geometry.grid([T(a, U.F32) for a in b["xs"]])
+    P = T(np.asarray(b["P"]).reshape(6, -1), U.F32)
+    outs = [U.barycenter(geo, alpha, P, T(b["dx"], U.F32).ravel(), T(b["dy"], U.F32).ravel(), U.KL(1.0), 1.0,
+                         1e-2, precision=U.F32, max_iter=45, check_every=10, launch_mode=m) for m in (2, 0)]
+    (h2, U2, V2, i2), (h0, U0, V0, i0) = outs
+    assert i2["iters"] == i0["iters"] == 45
+    assert torch.equal(h2, h0) and torch.equal(U2, U0) and torch.equal(V2, V0)
