@@ -120,13 +120,14 @@ struct PtArgs {
   float2* part;       // [nchunks][nout] (shift, sum) in log2 units relative to Lmax
 };
 
+template <int D>
 __global__ void __launch_bounds__(kNW * 32)
     points_partial(PtArgs a) {
   extern __shared__ float4 st[];  // 2 x chunk float4: {t,t,y0,y0}, {y1,y1,y2,y2}
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int c = blockIdx.y;
   const int j0 = c * a.chunk, j1 = min(a.nin, j0 + a.chunk);
-  const int d = a.d;
+  constexpr int d = D;  // compile-time: no dimension tests in the sweeps
   const float k2 = a.k2;
   const float Lmax = all_max(a.bmax, a.nbmax);
   for (int j = j0 + tid; j < j1; j += kNW * 32) {
@@ -173,13 +174,13 @@ __global__ void __launch_bounds__(kNW * 32)
         const f2p T = pk(s0.x, s0.y), Y0 = pk(s0.z, s0.w), Y1 = pk(s1.x, s1.y), Y2 = pk(s1.z, s1.w);
         f2p DA = sub2(XA0, Y0), DB = sub2(XB0, Y0);
         f2p QA = mul2(DA, DA), QB = mul2(DB, DB);
-        if (d > 1) {
+        if constexpr (d > 1) {
           DA = sub2(XA1, Y1);
           DB = sub2(XB1, Y1);
           QA = fma2(DA, DA, QA);
           QB = fma2(DB, DB, QB);
         }
-        if (d > 2) {
+        if constexpr (d > 2) {
           DA = sub2(XA2, Y2);
           DB = sub2(XB2, Y2);
           QA = fma2(DA, DA, QA);
@@ -203,13 +204,13 @@ __global__ void __launch_bounds__(kNW * 32)
       const f2p T = pk(s0.x, s0.y), Y0 = pk(s0.z, s0.w), Y1 = pk(s1.x, s1.y), Y2 = pk(s1.z, s1.w);
       f2p DA = sub2(XA0, Y0), DB = sub2(XB0, Y0);
       f2p QA = mul2(DA, DA), QB = mul2(DB, DB);
-      if (d > 1) {
+      if constexpr (d > 1) {
         DA = sub2(XA1, Y1);
         DB = sub2(XB1, Y1);
         QA = fma2(DA, DA, QA);
         QB = fma2(DB, DB, QB);
       }
-      if (d > 2) {
+      if constexpr (d > 2) {
         DA = sub2(XA2, Y2);
         DB = sub2(XB2, Y2);
         QA = fma2(DA, DA, QA);
@@ -355,10 +356,15 @@ cudaError_t launch_points(const float* x, const float* y, int d, int nout, int n
   a.use_prev = use_prev;
   a.part = part;
   const size_t smem = (size_t)2 * chunk * sizeof(float4);
-  cudaError_t e = cudaFuncSetAttribute(points_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
   dim3 grid((nout + kOutBlk - 1) / kOutBlk, nchunks);
-  points_partial<<<grid, kNW * 32, smem, s>>>(a);
+  auto run = [&](auto kern) -> cudaError_t {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, kNW * 32, smem, s>>>(a);
+    return cudaGetLastError();
+  };
+  cudaError_t e = (d == 1) ? run(points_partial<1>) : (d == 2) ? run(points_partial<2>) : run(points_partial<3>);
+  if (e != cudaSuccess) return e;
   CombArgs b;
   b.x = x;
   b.y = y;
