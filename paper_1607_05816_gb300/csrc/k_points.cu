@@ -324,13 +324,33 @@ __global__ void __launch_bounds__(256)
 }  // namespace
 
 // Chunking of the inputs: about 1024 inputs per chunk.
-int points_nchunks(int nin) { return (nin + 1023) / 1024; }
+// Chunking of the inputs: at most 1024 inputs per chunk; among the counts up
+// to 1.5x the least, the one that best balances the grid (output blocks x
+// chunks) over the 152 SMs -- the slowest SM sets the pass time -- with a
+// small charge for each extra chunk (more partial sums to combine).
+int points_nchunks(int nin, int nout) {
+  const int least = (nin + 1023) / 1024;
+  const int oblocks = (nout + kOutBlk - 1) / kOutBlk;
+  int best = least;
+  double best_waste = 2.0;
+  for (int c = least; c <= least + least / 2; ++c) {
+    if (c > 1 && (nin + c - 1) / c < 256) break;  // chunks of at least 256 inputs
+    const long g = (long)oblocks * c;
+    const long rounds = (g + 151) / 152;
+    const double waste = (double)(rounds * 152 - g) / (double)(rounds * 152) + 0.1 * (c - least) / least;
+    if (waste < best_waste - 1e-9) {
+      best_waste = waste;
+      best = c;
+    }
+  }
+  return best;
+}
 
 cudaError_t launch_points(const float* x, const float* y, int d, int nout, int nin,
                           const double* W, const double* logw, double eps, float* bmax,
                           float* zprev, int use_prev, float2* part, const Epilogue& epi,
                           cudaStream_t s) {
-  const int nchunks = points_nchunks(nin);
+  const int nchunks = points_nchunks(nin, nout);
   const int chunk = (nin + nchunks - 1) / nchunks;
   const int nbmax = (nin + kMaxBlk - 1) / kMaxBlk;
   const float2 inv_eps = ff2(ff_make(1.0 / eps));

@@ -591,7 +591,7 @@ struct Gibbs {
   }
   bool points_fast() const { return g.kind == UOT_GEOM_POINTS && prec != UOT_F64 && g.d <= 3; }
   size_t part_elems() const {
-    return std::max((size_t)points_nchunks(g.m) * g.n, (size_t)points_nchunks(g.n) * g.m);
+    return std::max((size_t)points_nchunks(g.m, g.n) * g.n, (size_t)points_nchunks(g.n, g.m) * g.m);
   }
   cudaError_t take(Scratch& sc, cudaStream_t s) {
     if (g.kind == UOT_GEOM_DENSE) {

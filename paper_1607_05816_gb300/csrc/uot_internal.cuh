@@ -491,7 +491,7 @@ cudaError_t launch_rows(int prec, const RowsGeom& g, int nrows, int nin, const d
                         const double* logw, double eps, void* scratch_L, const Epilogue& epi,
                         cudaStream_t s, float* zprev = nullptr, int use_prev = 0,
                         void* part = nullptr);
-int points_nchunks(int nin);
+int points_nchunks(int nin, int nout);
 cudaError_t launch_points(const float* x, const float* y, int d, int nout, int nin,
                           const double* W, const double* logw, double eps, float* bmax,
                           float* zprev, int use_prev, float2* part, const Epilogue& epi,
