@@ -534,12 +534,53 @@ def dual(geom, dx, dy, p, q, F1, F2, eps, U, V):
 # ----------------------------------------------------------------------------
 
 
-def bary_h_log(Tstack: np.ndarray, alpha: np.ndarray, lam: float, eps: float, kind: str = "kl"):
+def _pl_root_midpoint(bp: np.ndarray, fvals: np.ndarray, tau: np.ndarray) -> np.ndarray:
+    """Midpoint of the zero set of a continuous non-decreasing piecewise-linear
+    function, given its breakpoints bp [B, npts] (sorted along axis 0), its
+    values there fvals, f(bp[0]) <= 0 <= f(bp[-1]), and f linear between
+    consecutive breakpoints.  The zero set is taken as [r1, r2] with
+    r1 = min{W : f(W) >= -tau}, r2 = max{W : f(W) <= tau}: rounding leaves a
+    flat piece of f at +-1e-16 instead of 0, and tau (~1e-12 of the function's
+    range) keeps such a piece in the zero set."""
+    B, npts = bp.shape
+    cols = np.arange(npts)
+    # r1: first breakpoint with f >= -tau, interpolate from the one before it
+    i1 = np.argmax(fvals >= -tau[None, :], axis=0)
+    lo1 = np.maximum(i1 - 1, 0)
+    f_lo, f_hi = fvals[lo1, cols], fvals[i1, cols]
+    b_lo, b_hi = bp[lo1, cols], bp[i1, cols]
+    with np.errstate(invalid="ignore", divide="ignore"):
+        r1 = np.where(i1 == 0, bp[0, cols], b_lo + (0.0 - f_lo) * (b_hi - b_lo) / (f_hi - f_lo))
+    # r2: last breakpoint with f <= tau, interpolate to the one after it
+    i2 = B - 1 - np.argmax((fvals <= tau[None, :])[::-1], axis=0)
+    hi2 = np.minimum(i2 + 1, B - 1)
+    g_lo, g_hi = fvals[i2, cols], fvals[hi2, cols]
+    c_lo, c_hi = bp[i2, cols], bp[hi2, cols]
+    with np.errstate(invalid="ignore", divide="ignore"):
+        r2 = np.where(i2 == B - 1, bp[B - 1, cols], c_lo + (0.0 - g_lo) * (c_hi - c_lo) / (g_hi - g_lo))
+    return 0.5 * (r1 + r2)
+
+
+def bary_h_log(Tstack: np.ndarray, alpha: np.ndarray, lam: float, eps: float, kind: str = "kl",
+               beta=(1.0, 1.0)):
     """eps log h from the n marginals s_k = e^{T_k/eps} (Table 2).
 
     kl: h = (sum_k alpha_k s_k^{eps/(eps+lam)} / sum_k alpha_k)^{(eps+lam)/eps}
         so eps log h = (eps+lam) (LSE_k(log alpha_k + T_k/(eps+lam)) - log sum alpha)
     eq: h = (prod_k s_k^{alpha_k})^{1/sum alpha}  (geometric mean).
+    tv (Table 2 (iii)): with I+ = {k : s_k > 0} and A0 = sum of alpha_k off I+,
+        h = 0 if A0 >= sum_{I+} alpha_k, else W = eps log h solves
+        A0 + sum_{I+} alpha_k clamp((W - T_k)/lam, -1, 1) = 0
+        (the condition of Table 2 (iii) multiplied through by eps/lam inside the clamp).
+    rg (Table 2 (iv), RG[beta1, beta2], 0 < beta1 <= beta2 < inf): h = 0 if some
+        s_k = 0, else W solves (eps times the condition of the table)
+        sum_k alpha_k [beta2 min(W + eps log beta2 - T_k, 0) + beta1 max(W + eps log beta1 - T_k, 0)] = 0.
+    Both left-hand sides are continuous, non-decreasing and piecewise linear in
+    W; where they vanish on an interval (possible when saturated terms balance)
+    the midpoint of that interval is taken (any point of it minimises
+    eq. prox_barycenter, and the V updates do not depend on the choice).  Roots
+    are located exactly from the values at the sorted breakpoints and linear
+    interpolation.
     """
     alpha = np.asarray(alpha, dtype=np.float64)
     shp = (-1,) + (1,) * (Tstack.ndim - 1)
@@ -548,18 +589,58 @@ def bary_h_log(Tstack: np.ndarray, alpha: np.ndarray, lam: float, eps: float, ki
         return (eps + lam) * (lse(Z, axis=0) - math.log(np.sum(alpha)))
     if kind == "eq":
         return np.sum(alpha.reshape(shp) * Tstack, axis=0) / np.sum(alpha)
-    raise ValueError(kind)
+    if kind not in ("tv", "rg"):
+        raise ValueError(kind)
+    T = np.asarray(Tstack, dtype=np.float64)
+    out_shape = T.shape[1:]
+    T = T.reshape(T.shape[0], -1)
+    n, npts = T.shape
+    a = alpha.reshape(n, 1)
+    pos = np.isfinite(T)
+    Tf = np.where(pos, T, 0.0)
+    if kind == "tv":
+        A0 = np.sum(np.where(pos, 0.0, a), axis=0)
+        Ap = np.sum(np.where(pos, a, 0.0), axis=0)
+        zero = A0 >= Ap
+        # breakpoints T_k -/+ lam of the positive terms; others parked at the first one
+        ref = np.max(np.where(pos, Tf, -np.inf), axis=0)
+        ref = np.where(np.isfinite(ref), ref, 0.0)
+        bp = np.concatenate([np.where(pos, Tf - lam, ref - lam), np.where(pos, Tf + lam, ref - lam)])
+        bp = np.sort(bp, axis=0)
+
+        def f(W):
+            return A0 + np.sum(np.where(pos, a * np.clip((W[None, :] - Tf) / lam, -1.0, 1.0), 0.0), axis=0)
+    else:
+        b1, b2 = float(beta[0]), float(beta[1])
+        if not (0.0 < b1 <= b2 < math.inf):
+            raise ValueError("RG barycenter needs 0 < beta1 <= beta2 < inf")
+        zero = np.any(~pos, axis=0)
+        lo = Tf - eps * math.log(b2)
+        up = Tf - eps * math.log(b1)
+        bp = np.sort(np.concatenate([lo, up]), axis=0)
+
+        def f(W):
+            return np.sum(a * (b2 * np.minimum(W[None, :] - lo, 0.0) + b1 * np.maximum(W[None, :] - up, 0.0)),
+                          axis=0)
+    fvals = np.stack([f(bp[i]) for i in range(bp.shape[0])])
+    scale = np.sum(alpha) * (1.0 if kind == "tv" else float(beta[1]) * max(1.0, float(np.max(np.abs(bp)))))
+    W = _pl_root_midpoint(bp, fvals, np.full(npts, 1e-12 * scale))
+    W = np.where(zero, -np.inf, W)
+    return W.reshape(out_shape)
 
 
 def barycenter_log(geom: Geometry, dx, dy, P, alpha, F1: Div, lam: float, eps: float,
-                   iters: int, bary_kind: str = "kl", history: bool = False):
+                   iters: int, bary_kind: str = "kl", history: bool = False, beta=(1.0, 1.0)):
     """Unbalanced barycenter by the scaling iterations with n couplings sharing
     K = e^{-c/eps} (c_k = alpha_k c with the weighted KL of Sec. 5.2 gives
     K_k = e^{-c/eps} for all k).
 
     F1 acts componentwise (eq. proxcomponentbary): U_k = prox_update_F1(p_k).
     F2 (eq. Fbary): h from Table 2, then V_k = prox_update for lam KL(.|h)
-    (Table 1 with p -> h); bary_kind 'eq' uses Table 2 (i) and the equality row.
+    (Table 1 with p -> h); bary_kind 'eq' uses Table 2 (i) and the equality
+    row, 'tv' Table 2 (iii) and the lam TV row, 'rg' Table 2 (iv) and the
+    RG[beta1, beta2] row (the weights alpha_k multiply both terms of
+    eq. prox_barycenter, so each V_k follows Table 1 unweighted).
     Returns U (n, ...), V (n, ...), eps log h.
     """
     logdx, logdy = safe_log(dx), safe_log(dy)
@@ -568,14 +649,14 @@ def barycenter_log(geom: Geometry, dx, dy, P, alpha, F1: Div, lam: float, eps: f
     logP = safe_log(P)
     V = np.zeros_like(P)
     U = np.zeros_like(P)
-    Fh = KL(lam) if bary_kind == "kl" else EQ()
+    Fh = {"kl": KL(lam), "eq": EQ(), "tv": TV(lam), "rg": RG(beta[0], beta[1])}[bary_kind]
     logh = None
     for _ in range(iters):
         for k in range(n):
             S = apply_K_log(geom, V[k], logdy, eps)
             U[k] = prox_update_log(F1, logP[k], S, eps)
         T = np.stack([apply_K_log(geom, U[k], logdx, eps, transpose=True) for k in range(n)])
-        elogh = bary_h_log(T, alpha, lam, eps, bary_kind)
+        elogh = bary_h_log(T, alpha, lam, eps, bary_kind, beta)
         logh = elogh / eps
         for k in range(n):
             V[k] = prox_update_log(Fh, logh, T[k], eps)

@@ -496,3 +496,117 @@ def test_barycenter_fixed_point_optimality():
         acc += alpha[k] * (1 - r2 / h)
         assert np.allclose(r1, P[k].ravel(), rtol=1e-8)
     assert np.max(np.abs(acc)) < 1e-8
+
+
+# ----------------------------------------------------------------------------
+# Table 2 (iii), (iv): TV and RG barycenters
+# ----------------------------------------------------------------------------
+
+def _kl_bar(t, s):
+    """Pointwise KL-bar(t|s) = t log(t/s) - t + s with 0 log 0 = 0."""
+    return (t * math.log(t / s) if t > 0 else 0.0) - t + s
+
+
+def _prox_bary_value(h, s, alpha, eps, lam, kind, beta):
+    """Objective of eq. prox_barycenter at h, minimised over s~ (each s~_k by
+    bounded scalar search for TV; for RG the constraint set is the interval
+    [beta1 h, beta2 h] and KL-bar(.|s) is convex with its minimum at s, so its
+    minimiser there is the projection of s)."""
+    total = 0.0
+    for sk, ak in zip(s, alpha):
+        if sk == 0.0:
+            # s~_k = 0 is forced (Prop. on barycenter optimality)
+            total += ak * (lam * h if kind == "tv" else (0.0 if h == 0.0 else math.inf))
+            continue
+        if kind == "tv":
+            hi = max(4.0 * sk, 4.0 * h, 1e-300)
+            r = optimize.minimize_scalar(lambda t: eps * _kl_bar(t, sk) + lam * abs(t - h), bounds=(0.0, hi),
+                                         method="bounded", options={"xatol": 1e-14 * hi})
+            cand = [r.fun, eps * _kl_bar(h, sk), eps * _kl_bar(0.0, sk) + lam * h, eps * _kl_bar(sk, sk) + lam * abs(sk - h)]
+            total += ak * min(cand)
+        else:
+            t = min(max(sk, beta[0] * h), beta[1] * h)
+            total += ak * eps * _kl_bar(t, sk)
+    return total
+
+
+@pytest.mark.parametrize("kind", ["tv", "rg"])
+def test_barycenter_h_tv_rg_minimises_prox_problem(kind):
+    """Table 2 (iii)/(iv) against brute force: the oracle's h attains the
+    minimum over h of eq. prox_barycenter (scalar search over log h), including
+    points with zero masses and points where the minimiser is an interval."""
+    g = synth.rng(73 if kind == "tv" else 74)
+    eps, lam, beta = 0.05, 0.08, (0.6, 1.7)
+    npts, n = 12, 4
+    T = eps * np.log(g.uniform(0.05, 3.0, size=(n, npts)))
+    if kind == "tv":
+        T[0, 3] = -np.inf          # some zero masses
+        T[:3, 5] = -np.inf         # mostly zero: h = 0
+        T[:, 7] = [0.0, 0.0, 1.0, 1.0]  # equal weights saturated both ways: interval of minimisers
+    alpha = g.uniform(0.5, 2.0, size=n)
+    alpha[:] = 1.0 if kind == "tv" else alpha
+    W = O.bary_h_log(T, alpha, lam, eps, kind, beta)
+    for j in range(npts):
+        s = [math.exp(t / eps) if np.isfinite(t) else 0.0 for t in T[:, j]]
+        h_or = math.exp(W[j] / eps) if np.isfinite(W[j]) else 0.0
+        v_or = _prox_bary_value(h_or, s, alpha, eps, lam, kind, beta)
+        # brute force over log h on a wide bracket, plus h = 0
+        pos = [x for x in s if x > 0]
+        lo, hi = math.log(min(pos)) - 40 * lam / eps - 5, math.log(max(pos)) + 40 * lam / eps + 5
+        grid = np.linspace(lo, hi, 801)
+        vals = [_prox_bary_value(math.exp(u), s, alpha, eps, lam, kind, beta) for u in grid]
+        i = int(np.argmin(vals))
+        r = optimize.minimize_scalar(lambda u: _prox_bary_value(math.exp(u), s, alpha, eps, lam, kind, beta),
+                                     bounds=(grid[max(i - 1, 0)], grid[min(i + 1, 800)]), method="bounded",
+                                     options={"xatol": 1e-12})
+        v_bf = min(r.fun, vals[i], _prox_bary_value(0.0, s, alpha, eps, lam, kind, beta))
+        assert v_or <= v_bf + 1e-9 * max(1.0, abs(v_bf)), (j, v_or, v_bf)
+    if kind == "tv":
+        assert np.isneginf(W[5]) and np.isfinite(W[3])
+        # the flat interval between the saturated halves: its midpoint
+        assert abs(W[7] - 0.5) <= 1e-12
+
+
+def test_barycenter_h_rg_unit_range_is_geometric_mean():
+    """RG[1, 1] is the equality constraint, so Table 2 (iv) reduces to (i)."""
+    g = synth.rng(75)
+    T = g.normal(size=(5, 30)) * 0.3
+    alpha = g.uniform(0.2, 2.0, size=5)
+    W = O.bary_h_log(T, alpha, 0.0, 0.02, "rg", (1.0, 1.0))
+    assert np.max(np.abs(W - O.bary_h_log(T, alpha, 0.0, 0.02, "eq"))) <= 1e-12
+    T[2, 4] = -np.inf
+    assert np.isneginf(O.bary_h_log(T, alpha, 0.0, 0.02, "rg", (0.5, 2.0))[4])
+
+
+def test_barycenter_h_tv_limits():
+    """TV barycenter: for lam -> 0 the clamps saturate and eps log h is the
+    alpha-weighted median of the T_k; for lam large against the spread of the
+    T_k they never do and it is the alpha-weighted mean (the geometric mean of
+    Table 2 (i))."""
+    g = synth.rng(76)
+    n, npts = 5, 40
+    T = g.normal(size=(n, npts))
+    alpha = g.uniform(0.2, 2.0, size=n)
+    W0 = O.bary_h_log(T, alpha, 1e-9, 0.01, "tv")
+    for j in range(npts):
+        order = np.argsort(T[:, j])
+        cw = np.cumsum(alpha[order])
+        k = int(np.searchsorted(cw, 0.5 * alpha.sum()))
+        assert abs(W0[j] - T[order[k], j]) <= 1e-6
+    # lam = 1e4 >> |T_k - W|: no clamp saturates, the condition is linear in W
+    Winf = O.bary_h_log(T, alpha, 1e4, 0.01, "tv")
+    assert np.max(np.abs(Winf - O.bary_h_log(T, alpha, 0.0, 0.01, "eq"))) <= 1e-7
+
+
+@pytest.mark.parametrize("kind", ["tv", "rg"])
+def test_barycenter_tv_rg_single_measure(kind):
+    """With one measure the barycenter is that measure's marginal (h = s), so
+    b = 1 (V = 0) for both the TV and the RG divergence."""
+    g = synth.rng(77)
+    x = synth.grid_axis(20)
+    geo = O.Geometry("grid", xs=[x], ys=[x])
+    P = g.uniform(0.5, 1.5, size=(1, 20))
+    dx = np.full(20, 1 / 20)
+    U, V, elogh = O.barycenter_log(geo, dx, dx, P, np.array([1.0]), O.EQ(), 0.3, 0.05, 3, "rg" if kind == "rg" else "tv",
+                                   beta=(0.7, 1.4))
+    assert np.max(np.abs(V)) <= 1e-12
