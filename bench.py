@@ -382,21 +382,24 @@ def run_single(args, rank, world, local_rank):
         dtype = "f64"
     else:  # bary
         b = synth.barycenter_images(32, 128, 128, seed=1237 + rank)
-        geo = uot.Geometry.grid([f(a).ravel() for a in b["xs"]])
-        P = f(b["P"].reshape(32, -1))
-        alpha = np.full(32, 1.0 / 32)
         prec = {"f32": uot.F32, "mixed": uot.MIXED, "f64": uot.F64}[args.precision]
-        if prec == uot.F64:
-            P = P.double()
+        adt = torch.float64 if prec == uot.F64 else torch.float32
+        geo = uot.Geometry.grid([f(a, adt).ravel() for a in b["xs"]])
+        P = f(b["P"].reshape(32, -1), adt)
+        alpha = np.full(32, 1.0 / 32)
+
+        Fh = {"kl": uot.KL(1.0), "tv": uot.TV(1.0), "rg": uot.RG(0.5, 2.0)}[args.bary_div]
 
         def step():
             dt = torch.float64 if prec == uot.F64 else torch.float32
-            lh, U_, V_, info = uot.barycenter(geo, alpha, P, f(b["dx"], dt).ravel(), f(b["dy"], dt).ravel(),
-                                              uot.EQ(), 1.0, 1e-2, precision=prec, max_iter=500,
-                                              launch_mode=args.launch_mode)
+            lh, U_, V_, info = uot.barycenter_div(geo, alpha, P, f(b["dx"], dt).ravel(), f(b["dy"], dt).ravel(),
+                                                  uot.EQ(), Fh, 1e-2, precision=prec, max_iter=500,
+                                                  launch_mode=args.launch_mode)
             return U_, V_, info
         work_per_iter, unit_work, kernel = 32 * 2 * 2 * 128.0 ** 3, "Gexp2/s", "grid_pass"
-        cfg = {"workload": "bary32-128x128-kl1-eps1e-2-500it", "K": 32, "grid": [128, 128]}
+        cfg = {"workload": {"kl": "bary32-128x128-kl1-eps1e-2-500it", "tv": "bary32-128x128-tv1-eps1e-2-500it",
+                            "rg": "bary32-128x128-rg[0.5,2]-eps1e-2-500it"}[args.bary_div],
+               "K": 32, "grid": [128, 128], "barycenter_divergence": args.bary_div}
         dtype = args.precision
     for _ in range(args.warmup):
         step()
@@ -586,6 +589,8 @@ def main():
     ap.add_argument("--batch-nprob", type=int, default=0)
     ap.add_argument("--launch-mode", type=int, default=2, choices=[0, 1, 2, 3],
                     help="0 one launch per pass, 1 persistent solve, 2 CUDA-graph blocks, 3 fused pass pairs + graph blocks")
+    ap.add_argument("--bary-div", default="kl", choices=["kl", "tv", "rg"],
+                    help="barycenter divergence of the bary workload (Table 2 (ii), (iii), (iv))")
     ap.add_argument("--grid-tile", type=int, default=-1,
                     help="force one FP32 grid-pass tile shape (default: the tuner's choice)")
     args = ap.parse_args()

@@ -358,7 +358,7 @@ uot_status uot_solve_batch(int nprob, const uot_batch_problem* probs, int d, con
                            double* errs, uot_result* res, void* stream);
 
 /* Barycenter divergence for uot_barycenter (Table 2 rows). */
-typedef enum { UOT_BARY_KL = 1, UOT_BARY_EQ = 0 } uot_bary_kind;
+typedef enum { UOT_BARY_KL = 1, UOT_BARY_EQ = 0, UOT_BARY_TV = 2, UOT_BARY_RG = 3 } uot_bary_kind;
 
 /*
  * uot_barycenter -- unbalanced barycenter of K measures (Sec. 5.2) by the
@@ -366,8 +366,9 @@ typedef enum { UOT_BARY_KL = 1, UOT_BARY_EQ = 0 } uot_bary_kind;
  * (c_k = alpha_k c with the weighted entropy of Sec. 5.2).
  *   F1 acts per measure (eq. proxcomponentbary): proxdiv with p_k;
  *   F2(s) = min_h lambda sum_k alpha_k D(s_k | h) (eq. Fbary), h from Table 2
- *   (UOT_BARY_KL: power mean; UOT_BARY_EQ: geometric mean), then
- *   V_k = prox for lambda KL(.|h) (Table 1 with p -> h).
+ *   (UOT_BARY_KL: power mean; UOT_BARY_EQ: geometric mean; UOT_BARY_TV: the
+ *   root of (iii)), then V_k = prox for lambda D(.|h) (Table 1 with p -> h).
+ *   UOT_BARY_RG needs its range: use uot_barycenter_div (UOT_EINVAL here).
  *  Kmeas       number of measures K >= 1
  *  alpha       host [K] weights alpha_k > 0
  *  P           [K*n] densities of the measures w.r.t. dx
@@ -383,6 +384,28 @@ uot_status uot_barycenter(const uot_geom* g, int Kmeas, const double* alpha, con
                           const void* dx, const void* dy, const uot_div* F1, double lambda,
                           int bary_kind, const uot_opts* o, void* logh, void* U, void* V,
                           uot_result* res, void* stream);
+
+/*
+ * uot_barycenter_div -- uot_barycenter with the barycenter divergence given as
+ * a uot_div Fh (Table 2, with Table 1 for the V_k updates, p -> h):
+ *   UOT_DIV_EQ        (i)   geometric mean;
+ *   UOT_DIV_KL lambda (ii)  power mean;
+ *   UOT_DIV_TV lambda (iii) h = 0 if the weight of the measures with s_k = 0 is at
+ *                           least half of the total, else eps log h = W solves
+ *                           A0 + sum_{s_k > 0} alpha_k clamp((W - eps log s_k)/lambda, -1, 1) = 0;
+ *   UOT_DIV_RG [alpha, beta] (iv), 0 < alpha <= beta < inf: h = 0 if some s_k = 0,
+ *                           else W solves sum_k alpha_k [beta min(W - eps log s_k + eps log beta, 0)
+ *                           + alpha max(W - eps log s_k + eps log alpha, 0)] = 0.
+ * (iii) and (iv) are continuous, non-decreasing and piecewise linear in W; the
+ * root is located exactly from the values at the 2K breakpoints, and where the
+ * function vanishes on an interval its midpoint is taken (every point of it
+ * minimises the per-point prox problem; the V_k do not depend on the choice).
+ * TV and RG take K <= 1024.  Other arguments as for uot_barycenter.
+ */
+uot_status uot_barycenter_div(const uot_geom* g, int Kmeas, const double* alpha, const void* P,
+                              const void* dx, const void* dy, const uot_div* F1, const uot_div* Fh,
+                              const uot_opts* o, void* logh, void* U, void* V, uot_result* res,
+                              void* stream);
 
 /*
  * Learned warm start (not in the paper).  A small dilated convolutional

@@ -228,14 +228,96 @@ __global__ void k_nan_flag(const double* __restrict__ a, int64_t n, int ffmode, 
 //   KL (Table 2 ii): eps log h = (eps+lam) (log sum_k alpha_k e^{T_k/(eps+lam)} - log sum alpha)
 //   EQ (Table 2 i):  eps log h = sum_k alpha_k T_k / sum alpha
 // and V_k = prox for lam KL(.|h) (resp. the equality row) with p -> h.
+// Table 2 (iii), (iv): the barycenter h solves f(w) = 0 for a continuous,
+// non-decreasing, piecewise-linear f of w = eps log h (relative to a
+// reference), with breakpoints known in closed form.  PLRoot collects, from
+// f's values at the breakpoints, the brackets of r1 = min{f >= -tau} and
+// r2 = max{f <= tau} (consecutive breakpoints, f being monotone) and returns
+// the midpoint of [r1, r2], each end found by linear interpolation to f = 0.
+// On a flat zero piece any point minimises the prox problem and the V updates
+// do not depend on the choice; the midpoint is this library's reading.
+template <typename R>
+struct PLRoot {
+  R l1b, l1f, r1b, r1f, l2b, l2f, r2b, r2f;
+  bool hl1 = false, hr1 = false, hl2 = false, hr2 = false;
+  __device__ void add(R b, R fb, R tau) {
+    if (fb < -tau) {
+      if (!hl1 || b > l1b) { l1b = b; l1f = fb; hl1 = true; }
+    } else if (!hr1 || b < r1b) {
+      r1b = b; r1f = fb; hr1 = true;
+    }
+    if (fb <= tau) {
+      if (!hl2 || b > l2b) { l2b = b; l2f = fb; hl2 = true; }
+    } else if (!hr2 || b < r2b) {
+      r2b = b; r2f = fb; hr2 = true;
+    }
+  }
+  __device__ void merge(const PLRoot& o) {
+    if (o.hl1 && (!hl1 || o.l1b > l1b)) { l1b = o.l1b; l1f = o.l1f; hl1 = true; }
+    if (o.hr1 && (!hr1 || o.r1b < r1b)) { r1b = o.r1b; r1f = o.r1f; hr1 = true; }
+    if (o.hl2 && (!hl2 || o.l2b > l2b)) { l2b = o.l2b; l2f = o.l2f; hl2 = true; }
+    if (o.hr2 && (!hr2 || o.r2b < r2b)) { r2b = o.r2b; r2f = o.r2f; hr2 = true; }
+  }
+  __device__ R root() const {
+    const R r1 = hl1 ? (hr1 ? l1b + (R(0) - l1f) * (r1b - l1b) / (r1f - l1f) : l1b) : r1b;
+    const R r2 = hr2 ? (hl2 ? l2b + (R(0) - l2f) * (r2b - l2b) / (r2f - l2f) : r2b) : l2b;
+    return R(0.5) * (r1 + r2);
+  }
+};
+
+// f of Table 2 (iii) (TV, kind 2) or (iv) (RG, kind 3) at w, from the inputs
+// t_k (relative to the same reference; -inf for s_k = 0):
+//   TV: A0 + sum_{t_k finite} alpha_k clamp((w - t_k)/lam, -1, 1), A0 = sum of alpha over s_k = 0
+//   RG: sum_k alpha_k [b2 min(w - t_k + eps log b2, 0) + b1 max(w - t_k + eps log b1, 0)]
+template <typename R>
+__device__ R bary_pl_f(int kind, R w, const R* t, int64_t tstride, const R* alpha, int K, R lam, R elb1, R elb2,
+                       R b1, R b2) {
+  R f = R(0);
+  for (int k = 0; k < K; ++k) {
+    const R tk = t[k * tstride];
+    if (kind == UOT_BARY_TV) {
+      if (tk == -R(INFINITY)) f += alpha[k];
+      else f += alpha[k] * fmin(R(1), fmax(R(-1), (w - tk) / lam));
+    } else {
+      f += alpha[k] * (b2 * fmin(w - tk + elb2, R(0)) + b1 * fmax(w - tk + elb1, R(0)));
+    }
+  }
+  return f;
+}
+
 __global__ void k_bary_update(const double* __restrict__ T, int K, int64_t m,
                               const double* __restrict__ alpha, double sum_alpha, double lam,
-                              double eps, int kind, double* __restrict__ logh,
+                              double eps, int kind, double b1, double b2, double* __restrict__ logh,
                               double* __restrict__ V) {
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m;
        j += (int64_t)gridDim.x * blockDim.x) {
     double elogh;
-    if (kind == UOT_BARY_KL) {
+    if (kind == UOT_BARY_TV || kind == UOT_BARY_RG) {
+      // roots of Table 2 (iii)/(iv) in w = eps log h, from the 2K breakpoints
+      double A0 = 0.0, Ap = 0.0;
+      bool any_zero = false;
+      for (int k = 0; k < K; ++k) {
+        if (T[(int64_t)k * m + j] == -kInf) { A0 += alpha[k]; any_zero = true; }
+        else Ap += alpha[k];
+      }
+      if ((kind == UOT_BARY_TV && A0 >= Ap) || (kind == UOT_BARY_RG && any_zero)) {
+        elogh = -kInf;
+      } else {
+        const double elb1 = (kind == UOT_BARY_RG) ? eps * log(b1) : 0.0;
+        const double elb2 = (kind == UOT_BARY_RG) ? eps * log(b2) : 0.0;
+        const double tau = 1e-12 * sum_alpha * ((kind == UOT_BARY_TV) ? 1.0 : b2);
+        PLRoot<double> pr;
+        for (int k = 0; k < K; ++k) {
+          const double tk = T[(int64_t)k * m + j];
+          if (tk == -kInf) continue;
+          for (int side = 0; side < 2; ++side) {
+            const double b = (kind == UOT_BARY_TV) ? tk + (side ? lam : -lam) : tk - (side ? elb1 : elb2);
+            pr.add(b, bary_pl_f<double>(kind, b, T + j, m, alpha, K, lam, elb1, elb2, b1, b2), tau);
+          }
+        }
+        elogh = pr.root();
+      }
+    } else if (kind == UOT_BARY_KL) {
       const double c = 1.0 / (eps + lam);
       double mx = -kInf;
       for (int k = 0; k < K; ++k) mx = fmax(mx, log(alpha[k]) + T[(int64_t)k * m + j] * c);
@@ -254,15 +336,15 @@ __global__ void k_bary_update(const double* __restrict__ T, int K, int64_t m,
     logh[j] = elogh;
     const double lh = (elogh == -kInf) ? -kInf : elogh / eps;
     DivParams F;
-    F.kind = (kind == UOT_BARY_KL) ? UOT_DIV_KL : UOT_DIV_EQ;
+    F.kind = (kind == UOT_BARY_KL) ? UOT_DIV_KL : (kind == UOT_BARY_TV) ? UOT_DIV_TV
+             : (kind == UOT_BARY_RG) ? UOT_DIV_RG : UOT_DIV_EQ;
     F.lam = lam;
-    F.log_alpha = 0.0;
-    F.log_beta = 0.0;
+    F.log_alpha = (kind == UOT_BARY_RG) ? log(b1) : 0.0;
+    F.log_beta = (kind == UOT_BARY_RG) ? log(b2) : 0.0;
     for (int k = 0; k < K; ++k) V[(int64_t)k * m + j] = prox_update(F, lh, T[(int64_t)k * m + j], eps);
   }
 }
 
-// FP32 path of k_bary_update: float-float T, V, logh; FP32 arithmetic.
 // Barycenter update (Table 2 with Table 1 for the couplings' second marginals),
 // float-float.  A CTA of kBJ x kBK threads takes 32 consecutive points j
 // (lanes, coalesced over j) and splits the K measures over kBK warps; the
@@ -270,21 +352,105 @@ __global__ void k_bary_update(const double* __restrict__ T, int K, int64_t m,
 // geometric mean) are merged through shared memory.
 constexpr int kBJ = 32, kBK = 8;
 
+// TV and RG (Table 2 (iii), (iv)): the inputs of a point are staged relative
+// to their largest finite value in dynamic shared memory ([K][kBJ] floats,
+// then the K weights), each warp scans the breakpoints of its measures and
+// the brackets of the root are merged over the kBK warps.
+struct BaryPL {
+  float lam, b1, b2, elb1, elb2;  // TV weight; RG range and eps log of its ends
+};
+
 __global__ void __launch_bounds__(kBJ * kBK)
     k_bary_update_ff(const double* __restrict__ Td, int K, int64_t m, const float* __restrict__ log_alpha,
                      float log_sum_alpha, float2 epslam, float2 inv_epslam, float2 inv_eps, float2 eps_ff,
-                     int kind, DivFF Fh, double* __restrict__ loghd, double* __restrict__ Vd) {
+                     int kind, DivFF Fh, BaryPL pl, double* __restrict__ loghd, double* __restrict__ Vd) {
   const float2* T = reinterpret_cast<const float2*>(Td);
   float2* logh = reinterpret_cast<float2*>(loghd);
   float2* V = reinterpret_cast<float2*>(Vd);
-  __shared__ float r0[kBK][kBJ], r1[kBK][kBJ];
+  __shared__ float r0[kBK][kBJ], r1[kBK][kBJ], r2[kBK][kBJ];
   __shared__ int rneg[kBK][kBJ];
+  extern __shared__ float bsm[];  // TV/RG: [K][kBJ] staged inputs, then [K] weights
   const int lane = threadIdx.x, ky = threadIdx.y;
+  const bool pwl = (kind == UOT_BARY_TV || kind == UOT_BARY_RG);
+  float* sT = bsm;
+  float* sAl = bsm + (size_t)K * kBJ;
+  __shared__ float pb[kBK][8][kBJ];
+  __shared__ unsigned char ph[kBK][4][kBJ];
+  float sum_alpha = 0.0f;
+  if (pwl) {
+    for (int k = ky * kBJ + lane; k < K; k += kBJ * kBK) sAl[k] = expf(log_alpha[k]);
+    __syncthreads();
+    for (int k = 0; k < K; ++k) sum_alpha += sAl[k];
+  }
   for (int64_t jb = (int64_t)blockIdx.x * kBJ; jb < m; jb += (int64_t)gridDim.x * kBJ) {
     const int64_t j = jb + lane;
     const bool valid = j < m;
     ff elogh;
-    if (kind == UOT_BARY_KL) {
+    if (pwl) {
+      float ref = -INFINITY, a0 = 0.0f, ap = 0.0f;
+      int zero = 0;
+      for (int k = ky; k < K && valid; k += kBK) {
+        const ff t = ffl(T[(int64_t)k * m + j]);
+        if (t.hi == -INFINITY) {
+          a0 += sAl[k];
+          zero = 1;
+        } else {
+          ap += sAl[k];
+          ref = fmaxf(ref, t.hi);
+        }
+      }
+      r0[ky][lane] = ref;
+      r1[ky][lane] = a0;
+      r2[ky][lane] = ap;
+      rneg[ky][lane] = zero;
+      __syncthreads();
+      ref = -INFINITY;
+      a0 = ap = 0.0f;
+      zero = 0;
+#pragma unroll
+      for (int w = 0; w < kBK; ++w) {
+        ref = fmaxf(ref, r0[w][lane]);
+        a0 += r1[w][lane];
+        ap += r2[w][lane];
+        zero |= rneg[w][lane];
+      }
+      const bool hzero = !valid || ((kind == UOT_BARY_TV) ? (a0 >= ap) : (zero != 0));
+      for (int k = ky; k < K && valid; k += kBK) {
+        const ff t = ffl(T[(int64_t)k * m + j]);
+        sT[(size_t)k * kBJ + lane] = (t.hi == -INFINITY) ? -INFINITY : ((t.hi - ref) + t.lo);
+      }
+      __syncthreads();
+      PLRoot<float> pr;
+      if (!hzero) {
+        const float tau = 1e-6f * sum_alpha * ((kind == UOT_BARY_TV) ? 1.0f : pl.b2 * fabsf(pl.elb2 - pl.elb1) + 1e-30f);
+        for (int k = ky; k < K; k += kBK) {
+          const float tk = sT[(size_t)k * kBJ + lane];
+          if (tk == -INFINITY) continue;
+          for (int side = 0; side < 2; ++side) {
+            const float b = (kind == UOT_BARY_TV) ? tk + (side ? pl.lam : -pl.lam) : tk - (side ? pl.elb1 : pl.elb2);
+            pr.add(b, bary_pl_f<float>(kind, b, sT + lane, kBJ, sAl, K, pl.lam, pl.elb1, pl.elb2, pl.b1, pl.b2),
+                   tau);
+          }
+        }
+      }
+      pb[ky][0][lane] = pr.l1b; pb[ky][1][lane] = pr.l1f; pb[ky][2][lane] = pr.r1b; pb[ky][3][lane] = pr.r1f;
+      pb[ky][4][lane] = pr.l2b; pb[ky][5][lane] = pr.l2f; pb[ky][6][lane] = pr.r2b; pb[ky][7][lane] = pr.r2f;
+      ph[ky][0][lane] = pr.hl1; ph[ky][1][lane] = pr.hr1; ph[ky][2][lane] = pr.hl2; ph[ky][3][lane] = pr.hr2;
+      __syncthreads();
+      if (hzero) {
+        elogh = ff_ninf();
+      } else {
+        PLRoot<float> tot;
+        for (int w = 0; w < kBK; ++w) {
+          PLRoot<float> o;
+          o.l1b = pb[w][0][lane]; o.l1f = pb[w][1][lane]; o.r1b = pb[w][2][lane]; o.r1f = pb[w][3][lane];
+          o.l2b = pb[w][4][lane]; o.l2f = pb[w][5][lane]; o.r2b = pb[w][6][lane]; o.r2f = pb[w][7][lane];
+          o.hl1 = ph[w][0][lane]; o.hr1 = ph[w][1][lane]; o.hl2 = ph[w][2][lane]; o.hr2 = ph[w][3][lane];
+          tot.merge(o);
+        }
+        elogh = ff_add_f(ff{ref, 0.0f}, tot.root());
+      }
+    } else if (kind == UOT_BARY_KL) {
       // eps log h = (eps+lam) (LSE_k(log alpha_k + T_k/(eps+lam)) - log sum alpha)
       float mx = -INFINITY;
       for (int k = ky; k < K && valid; k += kBK) {
@@ -1972,18 +2138,61 @@ uot_status uot_solve_batch(int nprob, const uot_batch_problem* probs, int d, con
   return out;
 }
 
+static uot_status barycenter_impl(const uot_geom* g, int Kmeas, const double* alpha, const void* P,
+                                  const void* dx, const void* dy, const uot_div* F1, double lambda,
+                                  int bary_kind, double beta1, double beta2, const uot_opts* o, void* logh_out,
+                                  void* Uout, void* Vout, uot_result* res, void* stream);
+
 uot_status uot_barycenter(const uot_geom* g, int Kmeas, const double* alpha, const void* P,
                           const void* dx, const void* dy, const uot_div* F1, double lambda,
                           int bary_kind, const uot_opts* o, void* logh_out, void* Uout,
                           void* Vout, uot_result* res, void* stream) {
   clear_stale_error();
+  if (bary_kind == UOT_BARY_RG) return UOT_EINVAL;  // its range needs uot_barycenter_div
+  return barycenter_impl(g, Kmeas, alpha, P, dx, dy, F1, lambda, bary_kind, 1.0, 1.0, o, logh_out, Uout, Vout,
+                         res, stream);
+}
+
+uot_status uot_barycenter_div(const uot_geom* g, int Kmeas, const double* alpha, const void* P,
+                              const void* dx, const void* dy, const uot_div* F1, const uot_div* Fh,
+                              const uot_opts* o, void* logh_out, void* Uout, void* Vout, uot_result* res,
+                              void* stream) {
+  clear_stale_error();
+  if (!Fh) return UOT_EINVAL;
+  switch (Fh->kind) {
+    case UOT_DIV_EQ:
+      return barycenter_impl(g, Kmeas, alpha, P, dx, dy, F1, 1.0, UOT_BARY_EQ, 1.0, 1.0, o, logh_out, Uout, Vout,
+                             res, stream);
+    case UOT_DIV_KL:
+      return barycenter_impl(g, Kmeas, alpha, P, dx, dy, F1, Fh->lambda, UOT_BARY_KL, 1.0, 1.0, o, logh_out, Uout,
+                             Vout, res, stream);
+    case UOT_DIV_TV:
+      return barycenter_impl(g, Kmeas, alpha, P, dx, dy, F1, Fh->lambda, UOT_BARY_TV, 1.0, 1.0, o, logh_out, Uout,
+                             Vout, res, stream);
+    case UOT_DIV_RG:
+      return barycenter_impl(g, Kmeas, alpha, P, dx, dy, F1, 1.0, UOT_BARY_RG, Fh->alpha, Fh->beta, o, logh_out,
+                             Uout, Vout, res, stream);
+    default:
+      return UOT_EINVAL;
+  }
+}
+
+}  // extern "C"
+
+static uot_status barycenter_impl(const uot_geom* g, int Kmeas, const double* alpha, const void* P,
+                                  const void* dx, const void* dy, const uot_div* F1, double lambda,
+                                  int bary_kind, double beta1, double beta2, const uot_opts* o, void* logh_out,
+                                  void* Uout, void* Vout, uot_result* res, void* stream) {
   uot_status st = check_geom(g);
   if (st != UOT_OK) return st;
   if ((st = check_opts(o)) != UOT_OK) return st;
   if (Kmeas < 1 || !alpha || !P || !dx || !dy || !div_ok(F1) || !logh_out || !Uout || !Vout)
     return UOT_EINVAL;
-  if (bary_kind != UOT_BARY_KL && bary_kind != UOT_BARY_EQ) return UOT_EINVAL;
-  if (bary_kind == UOT_BARY_KL && !(lambda > 0.0)) return UOT_EINVAL;
+  if (bary_kind != UOT_BARY_KL && bary_kind != UOT_BARY_EQ && bary_kind != UOT_BARY_TV && bary_kind != UOT_BARY_RG)
+    return UOT_EINVAL;
+  if ((bary_kind == UOT_BARY_KL || bary_kind == UOT_BARY_TV) && !(lambda > 0.0)) return UOT_EINVAL;
+  if (bary_kind == UOT_BARY_RG && !(beta1 > 0.0 && beta1 <= beta2 && beta2 < kInf)) return UOT_EINVAL;
+  if ((bary_kind == UOT_BARY_TV || bary_kind == UOT_BARY_RG) && Kmeas > 1024) return UOT_EINVAL;
   if (o->plain_scaling) return UOT_EUNSUPPORTED;
   double sum_alpha = 0.0;
   for (int k = 0; k < Kmeas; ++k) {
@@ -2068,12 +2277,20 @@ uot_status uot_barycenter(const uot_geom* g, int Kmeas, const double* alpha, con
     if ((e = G.apply(1, U, logdx, eps, e2, st)) != cudaSuccess) return e;
     if (prec == UOT_F64) {
       k_bary_update<<<nblocks(m), kNT, 0, st>>>(T, Kmeas, m, alpha_d, sum_alpha, lambda, eps,
-                                                bary_kind, logh, V);
+                                                bary_kind, beta1, beta2, logh, V);
     } else {
       DivParams Dh;
-      Dh.kind = (bary_kind == UOT_BARY_KL) ? UOT_DIV_KL : UOT_DIV_EQ;
+      Dh.kind = (bary_kind == UOT_BARY_KL) ? UOT_DIV_KL : (bary_kind == UOT_BARY_TV) ? UOT_DIV_TV
+                : (bary_kind == UOT_BARY_RG) ? UOT_DIV_RG : UOT_DIV_EQ;
       Dh.lam = lambda;
-      Dh.log_alpha = Dh.log_beta = 0.0;
+      Dh.log_alpha = (bary_kind == UOT_BARY_RG) ? log(beta1) : 0.0;
+      Dh.log_beta = (bary_kind == UOT_BARY_RG) ? log(beta2) : 0.0;
+      BaryPL pl;
+      pl.lam = (float)lambda;
+      pl.b1 = (float)beta1;
+      pl.b2 = (float)beta2;
+      pl.elb1 = (float)(eps * log(beta1));
+      pl.elb2 = (float)(eps * log(beta2));
       cudaLaunchConfig_t cfg;
       memset(&cfg, 0, sizeof(cfg));
       cfg.gridDim = dim3((unsigned)std::min<int64_t>((m + kBJ - 1) / kBJ, 1 << 20));
@@ -2084,9 +2301,17 @@ uot_status uot_barycenter(const uot_geom* g, int Kmeas, const double* alpha, con
       // compete with this small grid
       cfg.attrs = nullptr;
       cfg.numAttrs = 0;
+      const bool pwl = bary_kind == UOT_BARY_TV || bary_kind == UOT_BARY_RG;
+      cfg.dynamicSmemBytes = pwl ? (size_t)Kmeas * (kBJ + 1) * sizeof(float) : 0;
+      if (cfg.dynamicSmemBytes > 48 * 1024) {
+        e = cudaFuncSetAttribute(k_bary_update_ff, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)cfg.dynamicSmemBytes);
+        if (e != cudaSuccess) return e;
+      }
+      const double lam_kl = (bary_kind == UOT_BARY_KL) ? lambda : 1.0;
       e = cudaLaunchKernelEx(&cfg, k_bary_update_ff, (const double*)T, Kmeas, (int64_t)m, (const float*)log_alpha_d,
-                             (float)log(sum_alpha), ff2(ff_make(eps + lambda)), ff2(ff_make(1.0 / (eps + lambda))),
-                             ff2(ff_make(1.0 / eps)), ff2(ff_make(eps)), bary_kind, make_div_ff(Dh, eps), logh, V);
+                             (float)log(sum_alpha), ff2(ff_make(eps + lam_kl)), ff2(ff_make(1.0 / (eps + lam_kl))),
+                             ff2(ff_make(1.0 / eps)), ff2(ff_make(eps)), bary_kind, make_div_ff(Dh, eps), pl, logh, V);
       if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
@@ -2160,5 +2385,3 @@ uot_status uot_barycenter(const uot_geom* g, int Kmeas, const double* alpha, con
   }
   return out;
 }
-
-}  // extern "C"

@@ -26,7 +26,7 @@ STATUS = {0: "UOT_OK", 1: "UOT_NOT_CONVERGED", -1: "UOT_EINVAL", -2: "UOT_ENOMEM
 DIV_EQ, DIV_KL, DIV_TV, DIV_RG = 0, 1, 2, 3
 GEOM_DENSE, GEOM_GRID, GEOM_POINTS = 0, 1, 2
 F64, F32, MIXED = 0, 1, 2
-BARY_EQ, BARY_KL = 0, 1
+BARY_EQ, BARY_KL, BARY_TV, BARY_RG = 0, 1, 2, 3
 MAX_DIM = 3
 
 
@@ -110,6 +110,10 @@ _SIGS = {
     "uot_force_batch_warps": (C.c_int, [C.c_int]),
     "uot_selftest_bounded_wait": (C.c_int, [C.c_double, C.c_void_p]),
     "uot_autotune_table": (C.c_int, [C.c_char_p, C.c_int]),
+    "uot_barycenter_div": (C.c_int, [C.POINTER(CGeom), C.c_int, C.POINTER(C.c_double), C.c_void_p,
+                                     C.c_void_p, C.c_void_p, C.POINTER(CDiv), C.POINTER(CDiv),
+                                     C.POINTER(COpts), C.c_void_p, C.c_void_p, C.c_void_p,
+                                     C.POINTER(CResult), C.c_void_p]),
     "uot_barycenter": (C.c_int, [C.POINTER(CGeom), C.c_int, C.POINTER(C.c_double), C.c_void_p,
                                  C.c_void_p, C.c_void_p, C.POINTER(CDiv), C.c_double, C.c_int,
                                  C.POINTER(COpts), C.c_void_p, C.c_void_p, C.c_void_p,
@@ -450,6 +454,30 @@ def barycenter(geom: Geometry, alpha, P, dx, dy, F1: Div, lam, eps, *, kind=BARY
                             C.byref(o), _ptr(logh, dt, "logh"), _ptr(U, dt, "U"),
                             _ptr(V, dt, "V"), C.byref(r), _stream())
     _check(st, "uot_barycenter")
+    return logh, U, V, dict(iters=r.iters, total_iters=r.total_iters, marg_err=r.marg_err,
+                            ms=r.ms, status=STATUS[st])
+
+
+def barycenter_div(geom: Geometry, alpha, P, dx, dy, F1: Div, Fh: Div, eps, *, precision=F64, max_iter=1000,
+                   tol=0.0, check_every=10, eps_start=None, eps_stages=10, iters_per_stage=100, launch_mode=0):
+    """uot_barycenter_div: the barycenter divergence as a Div (EQ, KL, TV or
+    RG with 0 < alpha <= beta < inf); returns (eps log h, U [K,n], V [K,m], result dict)."""
+    lib = load()
+    dt = _dtype(precision)
+    K = P.shape[0]
+    logh = torch.empty(geom.m, dtype=dt, device=P.device)
+    U = torch.empty(K, geom.n, dtype=dt, device=P.device)
+    V = torch.empty(K, geom.m, dtype=dt, device=P.device)
+    a = (C.c_double * K)(*[float(v) for v in alpha])
+    o = COpts(precision, float(eps), float(eps_start) if eps_start else 0.0, int(eps_stages),
+              int(iters_per_stage), int(max_iter), float(tol), int(check_every), 0, int(launch_mode), None,
+              None)
+    r = CResult()
+    g = geom.c(precision)
+    st = lib.uot_barycenter_div(C.byref(g), K, a, _ptr(P, dt, "P"), _ptr(dx, dt, "dx"), _ptr(dy, dt, "dy"),
+                                C.byref(F1.c()), C.byref(Fh.c()), C.byref(o), _ptr(logh, dt, "logh"),
+                                _ptr(U, dt, "U"), _ptr(V, dt, "V"), C.byref(r), _stream())
+    _check(st, "uot_barycenter_div")
     return logh, U, V, dict(iters=r.iters, total_iters=r.total_iters, marg_err=r.marg_err,
                             ms=r.ms, status=STATUS[st])
 

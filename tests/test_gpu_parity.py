@@ -548,3 +548,59 @@ def test_barycenter_graph_blocks_match_per_pass():
     (h2, U2, V2, i2), (h0, U0, V0, i0) = outs
     assert i2["iters"] == i0["iters"] == 45
     assert torch.equal(h2, h0) and torch.equal(U2, U0) and torch.equal(V2, V0)
+
+
+# ----------------------------------------------------------------------------
+# TV and RG barycenters (Table 2 (iii), (iv))
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec", [U.F64, U.F32])
+@pytest.mark.parametrize("kind", ["tv", "rg", "tv-zeros"])
+def test_barycenter_tv_rg_parity(kind, prec):
+    """uot_barycenter_div with a TV or RG barycenter divergence against the
+    oracle, iterate by iterate (uneven weights; one case with empty measures
+    that outweigh the others, where h = 0)."""
+    d = synth.barycenter_images(K=5, H=24, W=36, seed=16)
+    P = np.array(d["P"], dtype=np.float64)
+    if kind == "tv-zeros":
+        # measures 1 and 3 empty: their weight 0.55 outweighs the rest, so h = 0 (Table 2 (iii))
+        P[1] = 0.0
+        P[3] = 0.0
+    og = O.Geometry("grid", xs=d["xs"], ys=d["ys"])
+    alpha = np.array([0.1, 0.3, 0.2, 0.25, 0.15])
+    eps, lam, iters, beta = 0.01, 0.05, 20, (0.7, 1.6)
+    okind = "rg" if kind == "rg" else "tv"
+    Uo, Vo, lho = O.barycenter_log(og, d["dx"], d["dy"], P, alpha, O.EQ(), lam, eps, iters, bary_kind=okind,
+                                   beta=beta)
+    geo = U.Geometry.grid([T(a, prec) for a in d["xs"]])
+    Fh = U.RG(*beta) if okind == "rg" else U.TV(lam)
+    Pr = rounded(prec, P)
+    lh, Ug, Vg, info = U.barycenter_div(geo, alpha, T(Pr.reshape(5, -1), prec), T(d["dx"], prec).ravel(),
+                                        T(d["dy"], prec).ravel(), U.EQ(), Fh, eps, precision=prec, max_iter=iters)
+    if prec == U.F32:  # the oracle on the inputs the FP32 call receives
+        dxr, dyr = rounded(prec, d["dx"], d["dy"])
+        ogr = round_geom(og, prec)
+        Uo, Vo, lho = O.barycenter_log(ogr, dxr, dyr, Pr, alpha, O.EQ(), lam, eps, iters, bary_kind=okind,
+                                       beta=beta)
+    assert rel_err(to_np(lh), lho) <= TOL[prec]
+    assert rel_err(to_np(Ug), Uo.reshape(5, -1)) <= TOL[prec]
+    assert rel_err(to_np(Vg), Vo.reshape(5, -1)) <= TOL[prec]
+    if kind == "tv-zeros":
+        assert np.isneginf(to_np(lh)).all()
+
+
+def test_barycenter_div_matches_barycenter_for_kl_eq():
+    """uot_barycenter_div with KL / EQ divergences is uot_barycenter."""
+    d = synth.barycenter_images(K=3, H=16, W=20, seed=17)
+    alpha = np.array([0.5, 0.3, 0.2])
+    geo = U.Geometry.grid([T(a, U.F64) for a in d["xs"]])
+    args = (T(d["P"].reshape(3, -1), U.F64), T(d["dx"], U.F64).ravel(), T(d["dy"], U.F64).ravel(), U.EQ())
+    for Fh, kind in ((U.KL(0.7), U.BARY_KL), (U.EQ(), U.BARY_EQ)):
+        a = U.barycenter_div(geo, alpha, *args, Fh, 0.02, precision=U.F64, max_iter=15)
+        b = U.barycenter(geo, alpha, *args, 0.7, 0.02, kind=kind, precision=U.F64, max_iter=15)
+        for x, y in zip(a[:3], b[:3]):
+            assert torch.equal(x, y)
+    with pytest.raises(U.UotError, match="EINVAL"):
+        U.barycenter_div(geo, alpha, *args, U.RG(0.0, 2.0), 0.02, precision=U.F64, max_iter=2)
+    with pytest.raises(U.UotError, match="EINVAL"):
+        U.barycenter(geo, alpha, *args, 0.7, 0.02, kind=U.BARY_RG, precision=U.F64, max_iter=2)
