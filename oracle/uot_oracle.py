@@ -392,7 +392,7 @@ def solve_log(geom: Geometry, dx, dy, p, q, F1: Div, F2: Div, eps: float,
         Un = prox_update_log(F1, logp, S, eps)
         if (it + 1) % check_every == 0 or it == max_iter - 1:
             err = _violation_from(U, Un, S, logdx, eps)
-            if it > 0 and err <= tol:
+            if it > 0 and tol > 0 and err <= tol:  # tol = 0 runs max_iter
                 stop = True
             else:
                 stop = False
@@ -405,6 +405,81 @@ def solve_log(geom: Geometry, dx, dy, p, q, F1: Div, F2: Div, eps: float,
         if stop:
             break
     return dict(U=U, V=V, iters=it, err=err)
+
+
+def scaling_alg4(K, dx, dy, p, q, F1: Div, F2: Div, F3: Div, m0: float, eps: float, iters: int):
+    """Algorithm 4 (Sec. 4.5, a function F3 of the plan's total mass) verbatim:
+    b <- 1, z <- 1; repeat a <- proxdiv_F1(z K(b.dy)), b <- proxdiv_F2(z K^T(a.dx)),
+    z <- proxdiv_F3((a.dx)^T K (b.dy)).  F3 is a divergence of the total mass
+    from m0, i.e. the Table 1 row on a single point of unit weight with
+    density m0.  The plan is z a_i K_ij b_j.  Returns (a, b, z)."""
+    K = np.asarray(K, dtype=np.float64)
+    b = np.ones(K.shape[1])
+    a = np.ones(K.shape[0])
+    z = 1.0
+    for _ in range(iters):
+        a = proxdiv(F1, p, z * (K @ (b * dy)), 0.0, eps)
+        b = proxdiv(F2, q, z * (K.T @ (a * dx)), 0.0, eps)
+        M = float((a * dx) @ K @ (b * dy))
+        z = float(proxdiv(F3, np.array([m0]), np.array([M]), 0.0, eps)[0])
+    return a, b, z
+
+
+def mass_update_log(F3: Div, m0: float, U, S, logdx, eps: float) -> float:
+    """Z = eps log z of Algorithm 4's z-update in log form: the total mass of
+    the plan without z, M = sum_i dx_i e^{(U_i + S_i)/eps} (current a, and S
+    from the current b), then the Table 1 row of F3 at s = M, p = m0."""
+    with np.errstate(invalid="ignore"):
+        lr = np.where(np.isneginf(U) | np.isneginf(S), NEG_INF, np.asarray(logdx) + (U + S) / eps)
+    logM = lse(lr.ravel())
+    SM = eps * logM if np.isfinite(logM) else NEG_INF
+    return float(prox_update_log(F3, np.array([math.log(m0)]), np.array([SM]), eps)[0])
+
+
+def solve_mass_log(geom: Geometry, dx, dy, p, q, F1: Div, F2: Div, F3: Div, m0: float, eps: float,
+                   max_iter: int, tol: float = 0.0, eps_start=None, stages: int = 10,
+                   iters_per_stage: int = 100, check_every: int = 1):
+    """Algorithm 4 in log form, with eps-scaling (Sec. 4.4) as in solve_log.
+    Potentials U = eps log a, V = eps log b, Z = eps log z.  Iteration:
+    S = eps log K(e^{V/eps} dy); except in the very first iteration (z = 1),
+    Z = mass_update_log(U, S) (the z-update of the previous iteration: it needs
+    the new b, i.e. this S, and the current a); U = prox_F1(log p, S + Z);
+    T = eps log K^T(e^{U/eps} dx); V = prox_F2(log q, T + Z).  The measured
+    violation is the larger of that of solve_log with S + Z in place of S and
+    the z-update's own: the total mass of the current plan against its prox
+    target, |e^{(Z_old - Z_new)/eps} - 1| (with a saturated F1 row, U can be
+    stationary while z still moves).  The plan is e^{(U_i + V_j + Z - c_ij)/eps}."""
+    logdx, logdy, logp, logq = map(safe_log, (dx, dy, p, q))
+    U = np.zeros(np.shape(p))
+    V = np.zeros(np.shape(q))
+    Z = 0.0
+    first = True
+    sched = [(e, n, False) for e, n in eps_schedule(eps, eps_start, stages, iters_per_stage)]
+    sched.append((eps, max_iter, True))
+    err, it = math.inf, 0
+    for e, n, final in sched:
+        for k in range(n):
+            S = apply_K_log(geom, V, logdy, e)
+            Zold = Z
+            if not first:
+                Z = mass_update_log(F3, m0, U, S, logdx, e)
+            first = False
+            Sz = np.where(np.isneginf(S), NEG_INF, S + Z)
+            Un = prox_update_log(F1, logp, Sz, e)
+            stop = False
+            if final and ((k + 1) % check_every == 0 or k == n - 1):
+                mass_err = abs(math.expm1((Zold - Z) / e)) if np.isfinite(Z) and np.isfinite(Zold) else 0.0
+                err = max(_violation_from(U, Un, Sz, logdx, e), mass_err)
+                stop = k > 0 and tol > 0 and err <= tol
+            U = Un
+            T = apply_K_log(geom, U, logdx, e, transpose=True)
+            Tz = np.where(np.isneginf(T), NEG_INF, T + Z)
+            V = prox_update_log(F2, logq, Tz, e)
+            if final:
+                it = k + 1
+            if stop:
+                break
+    return dict(U=U, V=V, Z=Z, iters=it, err=err)
 
 
 def _violation_from(U_old, U_new, S, logdx, eps):

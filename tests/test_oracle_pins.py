@@ -610,3 +610,93 @@ def test_barycenter_tv_rg_single_measure(kind):
     U, V, elogh = O.barycenter_log(geo, dx, dx, P, np.array([1.0]), O.EQ(), 0.3, 0.05, 3, "rg" if kind == "rg" else "tv",
                                    beta=(0.7, 1.4))
     assert np.max(np.abs(V)) <= 1e-12
+
+
+# ----------------------------------------------------------------------------
+# Algorithm 4: a function F3 of the plan's total mass (Sec. 4.5)
+# ----------------------------------------------------------------------------
+
+def _mass_problem(n, m, seed):
+    g = synth.rng(seed)
+    x = np.sort(g.uniform(0, 1, n))
+    y = np.sort(g.uniform(0, 1, m))
+    dx, dy = np.full(n, 1.0 / n), np.full(m, 1.0 / m)
+    p, q = g.uniform(0.3, 2.0, n), g.uniform(0.3, 2.0, m)
+    return x, y, dx, dy, p, q
+
+
+@pytest.mark.parametrize("F3", [O.EQ(), O.KL(0.3), O.TV(0.2), O.RG(0.7, 1.1)], ids=["eq", "kl", "tv", "rg"])
+def test_alg4_literal_equals_log_form(F3):
+    """Algorithm 4 verbatim (non-log scalings, z updated after b) and the log
+    form (z-update at the start of the next iteration) give the same a, b and z."""
+    x, y, dx, dy, p, q = _mass_problem(12, 10, 80)
+    C = O.sqdist(x, y)
+    eps, it, m0 = 0.05, 30, 0.6
+    F1, F2 = O.KL(0.5), O.TV(0.4)
+    a, b, _ = O.scaling_alg4(np.exp(-C / eps), dx, dy, p, q, F1, F2, F3, m0, eps, it)
+    _, _, z_prev = O.scaling_alg4(np.exp(-C / eps), dx, dy, p, q, F1, F2, F3, m0, eps, it - 1)
+    r = O.solve_mass_log(O.Geometry("dense", C=C), dx, dy, p, q, F1, F2, F3, m0, eps, max_iter=it)
+    assert np.max(np.abs(eps * np.log(a) - r["U"])) <= 1e-10
+    assert np.max(np.abs(eps * np.log(b) - r["V"])) <= 1e-10
+    assert abs(eps * math.log(z_prev) - r["Z"]) <= 1e-10
+
+
+def test_alg4_without_mass_term_is_the_scaling_iteration():
+    """F3 = RG[0, inf] (no condition on the total mass) gives z = 1 and the
+    iterates of eq. S."""
+    x, y, dx, dy, p, q = _mass_problem(15, 11, 81)
+    geo = O.Geometry("dense", C=O.sqdist(x, y))
+    r4 = O.solve_mass_log(geo, dx, dy, p, q, O.KL(0.5), O.KL(0.8), O.RG(0.0, math.inf), 0.5, 0.02, max_iter=40)
+    r = O.solve_log(geo, dx, dy, p, q, O.KL(0.5), O.KL(0.8), 0.02, max_iter=40)
+    assert r4["Z"] == 0.0
+    assert np.array_equal(r4["U"], r["U"]) and np.array_equal(r4["V"], r["V"])
+
+
+def _mass_plan(C, r, eps):
+    return np.exp((r["U"][:, None] + r["V"][None, :] + r["Z"] - C) / eps)
+
+
+@pytest.mark.parametrize("case", ["kl-eq", "kl-kl", "tv-eq"])
+def test_alg4_matches_brute_force_minimisation(case):
+    """Tiny problems (n = m = 3): the converged plan of Algorithm 4 minimises
+    F1(R dy) + F2(R^T dx) + F3(total mass) + eps sum dx dy (R log(R/K) - R + K),
+    found independently by SLSQP (mass equality) or L-BFGS (soft mass term)
+    over log R."""
+    x, y, dx, dy, p, q = _mass_problem(3, 3, 82)
+    C = O.sqdist(x, y)
+    eps, m0, lam1, lam2, lam3 = 0.1, 0.55, 0.4, 0.6, 0.5
+    F1 = O.KL(lam1) if case != "tv-eq" else O.TV(lam1)
+    F2 = O.KL(lam2)
+    F3 = O.EQ() if case.endswith("eq") else O.KL(lam3)
+    r = O.solve_mass_log(O.Geometry("dense", C=C), dx, dy, p, q, F1, F2, F3, m0, eps, max_iter=20000, tol=1e-13)
+    R = _mass_plan(C, r, eps)
+    K = np.exp(-C / eps)
+    w = dx[:, None] * dy[None, :]
+
+    def div(F, s, pp, ww):
+        if F.kind == "kl":
+            return F.lam * np.sum(ww * (s * np.log(s / pp) - s + pp))
+        return F.lam * np.sum(ww * np.abs(s - pp))
+
+    def obj(lR):
+        Rm = np.exp(lR.reshape(3, 3))
+        r1, r2 = Rm @ dy, Rm.T @ dx
+        mass = np.sum(w * Rm)
+        v = div(F1, r1, p, dx) + div(F2, r2, q, dy) + eps * np.sum(w * (Rm * (lR.reshape(3, 3) + C / eps) - Rm + K))
+        if F3.kind == "kl":
+            v += lam3 * (mass * math.log(mass / m0) - mass + m0)
+        return v
+
+    x0 = np.log(R).ravel() + 0.05
+    if F3.kind == "eq":
+        res = optimize.minimize(obj, x0, method="SLSQP", constraints=[{"type": "eq",
+                                "fun": lambda lR: np.sum(w * np.exp(lR.reshape(3, 3))) - m0}],
+                                options={"ftol": 1e-15, "maxiter": 2000})
+    else:
+        res = optimize.minimize(obj, x0, method="L-BFGS-B", options={"ftol": 1e-16, "gtol": 1e-12, "maxiter": 20000})
+    Rb = np.exp(res.x.reshape(3, 3))
+    assert obj(np.log(R).ravel()) <= res.fun + 1e-9
+    if F1.kind == "kl":  # smooth objective: the minimiser itself is matched (SLSQP stalls on TV's kink)
+        assert np.max(np.abs(R - Rb) / Rb) <= 2e-3
+    if F3.kind == "eq":
+        assert abs(np.sum(w * R) - m0) <= 1e-8  # the last b-update moves the mass slightly
