@@ -83,12 +83,23 @@ WORKLOAD = "grid2d-256x256-kl0.5-epsscale1e-1to1e-3-tol1e-6"
 # launch on this workload (profiles/grid_pass_f32_grid256.md); None once the
 # kernel changes after that capture.
 GRID_PASS_F32_TRAFFIC_BYTES = 965888
+# --mass-div: Algorithm 4 (Sec. 4.5) on the same workload, a divergence on the
+# plan's total mass with target MASS_M0 (the plain solve's plan has mass ~1.14)
+MASS_M0 = 1.5
+MASS_DIVS = {"eq": "eq", "kl": "kl0.5", "tv": "tv0.5", "rg": "rg[0.8,1.2]"}
 
 
-def config_dict(extra=None):
-    c = {"workload": WORKLOAD, "grid": [H, W], "lambda": LAM, "eps": EPS, "eps_start": EPS_START,
+def mass_div(uot_or_oracle, name):
+    m = uot_or_oracle
+    return {"eq": m.EQ(), "kl": m.KL(LAM), "tv": m.TV(LAM), "rg": m.RG(0.8, 1.2)}[name]
+
+
+def config_dict(extra=None, mass=None):
+    c = {"workload": WORKLOAD + (f"-mass-{MASS_DIVS[mass]}-m0{MASS_M0}" if mass else ""), "grid": [H, W], "lambda": LAM, "eps": EPS, "eps_start": EPS_START,
          "eps_stages": STAGES, "iters_per_stage": IPS, "tol": TOL, "check_every": CHECK_EVERY,
          "l2": "flushed between steps (256 MB write)", "parallelism": "replicas"}
+    if mass:
+        c.update({"mass_divergence": MASS_DIVS[mass], "mass_m0": MASS_M0, "algorithm": "Algorithm 4 (Sec. 4.5)"})
     if extra:
         c.update(extra)
     return c
@@ -188,8 +199,15 @@ def run_ours(args, rank, world, local_rank):
 
     max_iter = args.max_iter if args.max_iter else MAX_ITER
     stages = 0 if args.no_eps_scaling else STAGES
+    F3 = mass_div(uot, args.mass_div) if args.mass_div else None
 
     def step(Uo=Ub, Vo=Vb, pp=p, dxx=dx, qq=q, dyy=dy, g=geo):
+        if F3 is not None:
+            U_, V_, _, info = uot.solve_mass(g, pp, dxx, qq, dyy, uot.KL(LAM), uot.KL(LAM), F3, MASS_M0, EPS,
+                                             precision=prec, max_iter=max_iter, tol=TOL,
+                                             check_every=CHECK_EVERY, eps_start=EPS_START, eps_stages=stages,
+                                             iters_per_stage=IPS, U=Uo, V=Vo, launch_mode=args.launch_mode)
+            return U_, V_, info
         return uot.solve(g, pp, dxx, qq, dyy, uot.KL(LAM), uot.KL(LAM), EPS, precision=prec,
                          max_iter=max_iter, tol=TOL, check_every=CHECK_EVERY,
                          eps_start=EPS_START, eps_stages=stages, iters_per_stage=IPS, U=Uo, V=Vo,
@@ -308,7 +326,7 @@ def run_ours(args, rank, world, local_rank):
         "vs_baseline": None,
         "dtype": {uot.F32: "f32", uot.F64: "f64", uot.MIXED: "bf16-mma/f32"}[prec],
         "data": "synthetic",
-        "config": config_dict({"precision": args.precision, "launch_mode": args.launch_mode}),
+        "config": config_dict({"precision": args.precision, "launch_mode": args.launch_mode}, args.mass_div),
         "e2e": {"value": all_e2e_iters / (e2e_ms_max / 1e3) if e2e_ms_max > 0 else None, "unit": "iters/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
@@ -331,7 +349,7 @@ def run_ours(args, rank, world, local_rank):
         line["roofline"]["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
                                               "grid_pass_f32<8, 4> launch (profiles/grid_pass_f32_grid256.md)")
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.cpu_iters)
+        line["cpu_baseline"] = cpu_baseline(args.cpu_iters, args.mass_div)
     print(json.dumps(line), flush=True)
 
 
@@ -528,22 +546,28 @@ def run_batch(args, rank, world, local_rank):
 # the oracle on the host (baseline and --impl reference)
 # ----------------------------------------------------------------------------
 
-def oracle_iterations(n_iters, seed=SEED):
-    """Run n_iters oracle iterations of the bench workload at the final eps;
-    returns (seconds, iterations)."""
+def oracle_iterations(n_iters, seed=SEED, mass=None):
+    """Run n_iters oracle iterations of the bench workload at the final eps
+    (Algorithm 4's with a mass divergence); returns (seconds, iterations)."""
     import oracle as O
     d = inputs(seed)
     og = O.Geometry("grid", xs=d["xs"], ys=d["ys"])
+    if mass:
+        t0 = time.perf_counter()
+        O.solve_mass_log(og, d["dx"], d["dy"], d["p"], d["q"], O.KL(LAM), O.KL(LAM), mass_div(O, mass),
+                         MASS_M0, EPS, max_iter=n_iters)
+        return time.perf_counter() - t0, n_iters
     logs = tuple(O.safe_log(d[k]) for k in ("dx", "dy", "p", "q"))
     t0 = time.perf_counter()
     O.iterate_log(og, *logs, O.KL(LAM), O.KL(LAM), EPS, n_iters)
     return time.perf_counter() - t0, n_iters
 
 
-def cpu_baseline(n_iters):
-    sec, n = oracle_iterations(n_iters)
+def cpu_baseline(n_iters, mass=None):
+    sec, n = oracle_iterations(n_iters, mass=mass)
+    what = "Algorithm 4 (mass divergence) " if mass else ""
     return {"value": n / sec, "unit": "iters/s", "cores": 1, "kind": "oracle",
-            "sample": f"{n} FP64 numpy iterations of the 256x256 grid problem at eps=1e-3 "
+            "sample": f"{n} FP64 numpy {what}iterations of the 256x256 grid problem at eps=1e-3 "
                       f"(separable log-domain form), {sec:.1f} s"}
 
 
@@ -552,10 +576,10 @@ def run_reference(args, rank, world):
         return
     per_step = max(1, args.cpu_iters // 2)
     for _ in range(args.warmup):
-        oracle_iterations(1)
+        oracle_iterations(1, mass=args.mass_div)
     sec, n = 0.0, 0
     for _ in range(args.steps):
-        s, k = oracle_iterations(per_step)
+        s, k = oracle_iterations(per_step, mass=args.mass_div)
         sec += s
         n += k
     value = n / sec
@@ -563,7 +587,7 @@ def run_reference(args, rank, world):
         "metric": "sinkhorn_iters_per_s", "value": value, "unit": "iters/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3 / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "impl": "reference", "config": config_dict({"precision": "f64"}),
+        "data": "synthetic", "impl": "reference", "config": config_dict({"precision": "f64"}, args.mass_div),
         "cpu_baseline": {"value": value, "unit": "iters/s", "cores": 1, "kind": "oracle",
                          "sample": f"{per_step} iterations per step at eps=1e-3"},
         "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -591,6 +615,8 @@ def main():
                     help="0 one launch per pass, 1 persistent solve, 2 CUDA-graph blocks, 3 fused pass pairs + graph blocks")
     ap.add_argument("--bary-div", default="kl", choices=["kl", "tv", "rg"],
                     help="barycenter divergence of the bary workload (Table 2 (ii), (iii), (iv))")
+    ap.add_argument("--mass-div", default=None, choices=sorted(MASS_DIVS),
+                    help="grid2d workload through Algorithm 4 with this divergence on the plan's total mass")
     ap.add_argument("--grid-tile", type=int, default=-1,
                     help="force one FP32 grid-pass tile shape (default: the tuner's choice)")
     args = ap.parse_args()

@@ -260,6 +260,37 @@ uot_status uot_solve_many(const uot_geom* g, int batch, const void* p, const voi
                           const uot_opts* o, void* U, void* V, uot_result* res, void* stream);
 
 /*
+ * uot_solve_mass -- scaling iterations with a third divergence on the total
+ * mass of the plan (Algorithm 4, Sec. 4.5), in the log domain of Sec. 4.3
+ * with eps-scaling (Sec. 4.4):
+ *
+ *   min_R  F1(R dy) + F2(R^T dx) + F3(sum_ij dx_i dy_j R_ij) + eps KL(R | K),
+ *
+ * F3(s) = D_phi3(s | m0) for a scalar s, any Table 1 row (EQ fixes the total
+ * mass to m0).  The plan is R_ij = exp((U_i + V_j + Z - C_ij)/eps): a scalar
+ * z = e^{Z/eps} multiplies the two scalings.
+ *
+ * One iteration: S = eps log K(b.dy); then, except in the very first
+ * iteration (z = 1), the z-update of Algorithm 4 with the current a and the
+ * new b: M = sum_i dx_i exp((U_i + S_i)/eps), Z = the Table 1 row of F3 at
+ * log-mass eps log M with p = m0; U = prox_F1(S + Z); T = eps log K^T(a.dx);
+ * V = prox_F2(T + Z).  The marginal violation is that of uot_solve with
+ * S + Z in place of S, or the mass violation |exp((Z_old - Z)/eps) - 1| of
+ * the z-update if larger (with a saturated F1 the a-side can be stationary
+ * while z still moves).
+ *
+ *  m0          target mass of F3, 0 < m0 < inf
+ *  Z           host double, output: eps log z of the last iteration
+ *  other arguments as for uot_solve (plain_scaling unsupported: UOT_EUNSUPPORTED;
+ *  launch modes 1 and 3 run as 2).  The iteration starts from z = 1.
+ * Returns as uot_solve; UOT_NUMERICAL also when Z is NaN.
+ */
+uot_status uot_solve_mass(const uot_geom* g, const void* p, const void* dx, const void* q,
+                          const void* dy, const uot_div* F1, const uot_div* F2, const uot_div* F3,
+                          double m0, const uot_opts* o, void* U, void* V, double* Z, uot_result* res,
+                          void* stream);
+
+/*
  * uot_gibbs_log -- the log-domain Gibbs operator alone (Sec. 4.2, 4.3):
  *   transpose = 0: out_i = eps log sum_j exp((W_j - C_ij)/eps) w_j   (out [n], W,w [m])
  *   transpose = 1: out_j = eps log sum_i exp((W_i - C_ij)/eps) w_i   (out [m], W,w [n])

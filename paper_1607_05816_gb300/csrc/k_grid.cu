@@ -165,7 +165,8 @@ __device__ __forceinline__ void epilogue_apply(const Epilogue& e, int64_t b, int
   }
   num = den = 0.0f;
   const ff eps = ffl(e.eps_ff);
-  const ff S = (z.hi == -INFINITY) ? ff_ninf() : ff_mul(z, eps);
+  ff S = (z.hi == -INFINITY) ? ff_ninf() : ff_mul(z, eps);
+  if (e.zshift) S = ff_zshift(S, e.zshift);
   const ff Unew = prox_update_ff(e.Fff, ffl(o.lp), S, eps);
   reinterpret_cast<float2*>(e.pot)[b * e.bstride + pt] = ff2(Unew);
   if (e.err) violation_terms_ff(ffl(o.uold), Unew, S, ffl(o.lw), ffl(e.inv_eps_ff), num, den);

@@ -1543,6 +1543,514 @@ uot_status solve_impl(const uot_geom* g, int batch, const void* p, const void* d
   return out;
 }
 
+// ---------------------------------------------------------------------------
+// Algorithm 4 (Sec. 4.5): a divergence F3 on the total mass of the plan
+// ---------------------------------------------------------------------------
+// A scalar z = e^{Z/eps} multiplies the plan; both scaling updates see S + Z
+// and T + Z.  z's own update needs the mass of the current plan without z,
+// M = sum_i dx_i e^{(U_i + S_i)/eps}, over all points before any U_i changes,
+// so the a-side of an iteration is three launches:
+//   Gibbs pass with raw output z_i = S_i/eps  ->  k_mass_reduce (per-block
+//   log-sum-exp of log dx_i + U_i/eps + z_i; the last block to finish merges
+//   the partials and applies the Table 1 row of F3 with p = m0, s = M)  ->
+//   k_mass_prox (U_i = prox_F1(log p_i, S_i + Z) and the violation terms).
+// The b-side is the plain prox pass with Z added to T in its epilogue.  Both
+// kernels take part in programmatic dependent launch like the grid passes:
+// they wait for the preceding kernel before reading anything.
+
+constexpr int kMassBlocks = 304;  // 2 x 152 SMs
+
+// (max, sum) merge of two partial log-sum-exps.
+__device__ inline void lse_merge(double& mx, double& s, double m2, double s2) {
+  if (m2 == -kInf) return;
+  if (mx == -kInf) {
+    mx = m2;
+    s = s2;
+  } else if (m2 > mx) {
+    s = s * exp(mx - m2) + s2;
+    mx = m2;
+  } else {
+    s += s2 * exp(m2 - mx);
+  }
+}
+__device__ inline void lse_merge_ff(ff& mx, float& s, ff m2, float s2) {
+  if (m2.hi == -INFINITY) return;
+  if (mx.hi == -INFINITY) {
+    mx = m2;
+    s = s2;
+  } else if (ff_lt(mx, m2)) {
+    const ff d = ff_sub(mx, m2);
+    s = s * expf(d.hi + d.lo) + s2;
+    mx = m2;
+  } else {
+    const ff d = ff_sub(m2, mx);
+    s += s2 * expf(d.hi + d.lo);
+  }
+}
+
+struct MassArgs {
+  int64_t n;
+  double eps;
+  float2 eps_ff, inv_eps_ff;
+  DivParams F3;
+  DivFF F3ff;
+  double logm0;
+  float2 logm0_ff;
+  int update;        // 0 in the very first iteration: z = 1 stays
+  int check;         // clear acc[0..1] and write the mass violation to acc[2]
+  double* Z;         // [1] Z (FP64) or its float-float pair
+  double* acc;       // [3] violation accumulators
+  double2* part;     // [kMassBlocks] per-block (max, sum); float-float: (max.hi, max.lo) + sum
+  unsigned* count;   // blocks finished (the last one sets it back to 0)
+};
+
+__device__ __forceinline__ void pdl_begin() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <bool FF>
+__global__ void __launch_bounds__(kNT) k_mass_reduce(const double* __restrict__ U, const double* __restrict__ z,
+                                                     const double* __restrict__ logdx, MassArgs a) {
+  __shared__ double smx[kNT / 32], ssum[kNT / 32];
+  __shared__ float2 sfx[kNT / 32];
+  __shared__ bool last;
+  pdl_begin();
+  if (!a.update) {
+    if (blockIdx.x == 0 && threadIdx.x == 0 && a.check) {
+      a.acc[0] = a.acc[1] = a.acc[2] = 0.0;
+    }
+    return;
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if constexpr (!FF) {
+    double mx = -kInf, s = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)kNT + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * kNT) {
+      const double u = U[i], zi = z[i];
+      if (u == -kInf || zi == -kInf) continue;
+      lse_merge(mx, s, logdx[i] + u / a.eps + zi, 1.0);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double m2 = __shfl_xor_sync(0xffffffffu, mx, o), s2 = __shfl_xor_sync(0xffffffffu, s, o);
+      lse_merge(mx, s, m2, s2);
+    }
+    if (lane == 0) {
+      smx[w] = mx;
+      ssum[w] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int k = 1; k < kNT / 32; ++k) lse_merge(mx, s, smx[k], ssum[k]);
+      a.part[blockIdx.x] = make_double2(mx, s);
+      __threadfence();
+      last = atomicAdd(a.count, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    mx = -kInf;
+    s = 0.0;
+    for (int k = threadIdx.x; k < (int)gridDim.x; k += kNT) {
+      const double2 v = __ldcg(&a.part[k]);
+      lse_merge(mx, s, v.x, v.y);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double m2 = __shfl_xor_sync(0xffffffffu, mx, o), s2 = __shfl_xor_sync(0xffffffffu, s, o);
+      lse_merge(mx, s, m2, s2);
+    }
+    __syncthreads();
+    if (lane == 0) {
+      smx[w] = mx;
+      ssum[w] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int k = 1; k < kNT / 32; ++k) lse_merge(mx, s, smx[k], ssum[k]);
+      // eps log M, then Z = prox of F3 at the total mass
+      const double SM = (mx == -kInf || s == 0.0) ? -kInf : a.eps * (mx + log(s));
+      const double Zold = a.Z[0];
+      const double Znew = prox_update(a.F3, a.logm0, SM, a.eps);
+      a.Z[0] = Znew;
+      if (a.check) {
+        a.acc[0] = a.acc[1] = 0.0;
+        a.acc[2] = (isfinite(Zold) && isfinite(Znew)) ? fabs(expm1((Zold - Znew) / a.eps)) : 0.0;
+      }
+      *a.count = 0u;
+    }
+  } else {
+    const float2* U2 = reinterpret_cast<const float2*>(U);
+    const float2* z2 = reinterpret_cast<const float2*>(z);
+    const float2* w2 = reinterpret_cast<const float2*>(logdx);
+    const ff inv_eps = ffl(a.inv_eps_ff);
+    ff mx = ff_ninf();
+    float s = 0.0f;
+    for (int64_t i = blockIdx.x * (int64_t)kNT + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * kNT) {
+      const ff u = ffl(U2[i]), zi = ffl(z2[i]);
+      if (u.hi == -INFINITY || zi.hi == -INFINITY) continue;
+      lse_merge_ff(mx, s, ff_add(ff_add(ffl(w2[i]), ff_mul(u, inv_eps)), zi), 1.0f);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const ff m2{__shfl_xor_sync(0xffffffffu, mx.hi, o), __shfl_xor_sync(0xffffffffu, mx.lo, o)};
+      lse_merge_ff(mx, s, m2, __shfl_xor_sync(0xffffffffu, s, o));
+    }
+    if (lane == 0) {
+      sfx[w] = ff2(mx);
+      ssum[w] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int k = 1; k < kNT / 32; ++k) lse_merge_ff(mx, s, ffl(sfx[k]), (float)ssum[k]);
+      float4* p4 = reinterpret_cast<float4*>(a.part);
+      p4[blockIdx.x] = make_float4(mx.hi, mx.lo, s, 0.0f);
+      __threadfence();
+      last = atomicAdd(a.count, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    mx = ff_ninf();
+    s = 0.0f;
+    for (int k = threadIdx.x; k < (int)gridDim.x; k += kNT) {
+      const float4 v = __ldcg(&reinterpret_cast<const float4*>(a.part)[k]);
+      lse_merge_ff(mx, s, ff{v.x, v.y}, v.z);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const ff m2{__shfl_xor_sync(0xffffffffu, mx.hi, o), __shfl_xor_sync(0xffffffffu, mx.lo, o)};
+      lse_merge_ff(mx, s, m2, __shfl_xor_sync(0xffffffffu, s, o));
+    }
+    __syncthreads();
+    if (lane == 0) {
+      sfx[w] = ff2(mx);
+      ssum[w] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int k = 1; k < kNT / 32; ++k) lse_merge_ff(mx, s, ffl(sfx[k]), (float)ssum[k]);
+      const ff eps = ffl(a.eps_ff);
+      const ff SM = (mx.hi == -INFINITY || s == 0.0f) ? ff_ninf() : ff_mul(eps, ff_add_f(mx, logf(s)));
+      float2* Z2 = reinterpret_cast<float2*>(a.Z);
+      const ff Zold = ffl(Z2[0]);
+      const ff Znew = prox_update_ff(a.F3ff, ffl(a.logm0_ff), SM, eps);
+      Z2[0] = ff2(Znew);
+      if (a.check) {
+        float merr = 0.0f;
+        if (isfinite(Zold.hi) && isfinite(Znew.hi)) {
+          const ff d = ff_mul(ff_sub(Zold, Znew), ffl(a.inv_eps_ff));
+          merr = fabsf(expm1f(d.hi + d.lo));
+        }
+        a.acc[0] = a.acc[1] = 0.0;
+        a.acc[2] = (double)merr;
+      }
+      *a.count = 0u;
+    }
+  }
+}
+
+struct MassProx {
+  int64_t n;
+  double eps;
+  float2 eps_ff, inv_eps_ff;
+  DivParams F;
+  DivFF Fff;
+  const double* Z;  // [1] Z (FP64) or its float-float pair
+  double* err;      // [2] violation accumulators, NULL: no check
+};
+
+// pot_i = prox_F(log p_i, eps z_i + Z), z_i the raw log-sum of the Gibbs pass.
+template <bool FF>
+__global__ void __launch_bounds__(kNT) k_mass_prox(const double* __restrict__ z, const double* __restrict__ logp,
+                                                   double* __restrict__ pot, const double* __restrict__ logw,
+                                                   MassProx a) {
+  pdl_begin();
+  if constexpr (!FF) {
+    const double Zv = a.Z[0];
+    double num = 0.0, den = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)kNT + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * kNT) {
+      const double zi = z[i];
+      const double Sz = (zi == -kInf || Zv == -kInf) ? -kInf : a.eps * zi + Zv;
+      const double Uold = pot[i];
+      const double Unew = prox_update(a.F, logp[i], Sz, a.eps);
+      pot[i] = Unew;
+      if (a.err) {
+        double nu, de;
+        violation_terms(Uold, Unew, Sz, logw[i], a.eps, nu, de);
+        num += nu;
+        den += de;
+      }
+    }
+    if (a.err) block_add2<kNT>(num, den, a.err);
+  } else {
+    const ff Zv = ffl(reinterpret_cast<const float2*>(a.Z)[0]);
+    const ff eps = ffl(a.eps_ff), inv_eps = ffl(a.inv_eps_ff);
+    float2* pot2 = reinterpret_cast<float2*>(pot);
+    float num = 0.0f, den = 0.0f;
+    for (int64_t i = blockIdx.x * (int64_t)kNT + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * kNT) {
+      const ff zi = ffl(reinterpret_cast<const float2*>(z)[i]);
+      const ff Sz = (zi.hi == -INFINITY || Zv.hi == -INFINITY) ? ff_ninf() : ff_add(ff_mul(zi, eps), Zv);
+      const ff Uold = ffl(pot2[i]);
+      const ff Unew = prox_update_ff(a.Fff, ffl(reinterpret_cast<const float2*>(logp)[i]), Sz, eps);
+      pot2[i] = ff2(Unew);
+      if (a.err) {
+        float nu, de;
+        violation_terms_ff(Uold, Unew, Sz, ffl(reinterpret_cast<const float2*>(logw)[i]), inv_eps, nu, de);
+        num += nu;
+        den += de;
+      }
+    }
+    if (a.err) block_add2f<kNT>(num, den, a.err);
+  }
+}
+
+uot_status solve_mass_impl(const uot_geom* g, const void* p, const void* dx, const void* q, const void* dy,
+                           const uot_div* F1, const uot_div* F2, const uot_div* F3, double m0,
+                           const uot_opts* o, void* Uout, void* Vout, double* Zout, uot_result* res,
+                           cudaStream_t s) {
+  uot_status st = check_geom(g);
+  if (st != UOT_OK) return st;
+  if ((st = check_opts(o)) != UOT_OK) return st;
+  if (!p || !dx || !q || !dy || !Uout || !Vout || !Zout || !div_ok(F1) || !div_ok(F2) || !div_ok(F3))
+    return UOT_EINVAL;
+  if (!(m0 > 0.0) || !isfinite(m0)) return UOT_EINVAL;
+  if (o->plain_scaling) return UOT_EUNSUPPORTED;
+  const int prec = o->precision;
+  const bool ffm = prec != UOT_F64;
+  const int64_t n = g->n, m = g->m;
+  const DivParams D1 = make_div(*F1), D2 = make_div(*F2), D3 = make_div(*F3);
+
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  UOT_CK(cudaEventCreate(&ev0));
+  UOT_CK(cudaEventCreate(&ev1));
+  struct EvGuard {
+    cudaEvent_t a, b;
+    ~EvGuard() {
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+    }
+  } evg{ev0, ev1};
+  UOT_CK(cudaEventRecord(ev0, s));
+
+  Scratch sc(s);
+  Gibbs G;
+  G.g = *g;
+  G.prec = prec;
+  G.speculate = true;
+  G.plan(sc, 1);
+  sc.reserve<double>(n);            // logp
+  sc.reserve<double>(n);            // logdx
+  sc.reserve<double>(n);            // U
+  sc.reserve<double>(m);            // logq
+  sc.reserve<double>(m);            // logdy
+  sc.reserve<double>(m);            // V
+  sc.reserve<double>(n);            // raw log-sums z = S/eps of the a-side pass
+  sc.reserve<double>(4);            // acc[3] + NaN flag
+  sc.reserve<double>(1);            // Z
+  sc.reserve<double2>(kMassBlocks); // mass partials
+  sc.reserve<unsigned>(1);          // finished-block counter
+  UOT_CK(sc.allocate());
+  UOT_CK(G.take(sc, s));
+  double* logp = sc.take<double>(n);
+  double* logdx = sc.take<double>(n);
+  double* U = sc.take<double>(n);
+  double* logq = sc.take<double>(m);
+  double* logdy = sc.take<double>(m);
+  double* V = sc.take<double>(m);
+  double* zb = sc.take<double>(n);
+  double* acc = sc.take<double>(4);
+  int* flag = (int*)(acc + 3);
+  double* Zd = sc.take<double>(1);
+  double2* part = sc.take<double2>(kMassBlocks);
+  unsigned* count = sc.take<unsigned>(1);
+  UOT_SCRATCH_OK(sc);
+  UOT_CK(to_log(prec, p, n, logp, s));
+  UOT_CK(to_log(prec, dx, n, logdx, s));
+  UOT_CK(to_log(prec, q, m, logq, s));
+  UOT_CK(to_log(prec, dy, m, logdy, s));
+  if (o->U0) {
+    UOT_CK(to_f64(prec, o->U0, n, U, s));
+  } else {
+    count_launches(1);
+    k_fill<<<nblocks(n), kNT, 0, s>>>(U, n, 0.0);
+  }
+  if (o->V0) {
+    UOT_CK(to_f64(prec, o->V0, m, V, s));
+  } else {
+    count_launches(1);
+    k_fill<<<nblocks(m), kNT, 0, s>>>(V, m, 0.0);
+  }
+  UOT_CK(cudaMemsetAsync(Zd, 0, sizeof(double), s));  // z = 1 (both layouts)
+  UOT_CK(cudaMemsetAsync(acc, 0, 4 * sizeof(double), s));
+  UOT_CK(cudaMemsetAsync(count, 0, sizeof(unsigned), s));
+  UOT_CK(cudaGetLastError());
+
+  const int red_blocks = (int)std::min<int64_t>(kMassBlocks, std::max<int64_t>(1, (n + kNT - 1) / kNT));
+  bool first = true;
+  // programmatic dependent launch (the kernels wait for their predecessor first)
+  auto pdl_launch = [&](auto kern, int grid, cudaStream_t st, auto... args) -> cudaError_t {
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kNT);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    count_launches(1);
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+  };
+  auto prox_a = [&](double eps, double* err, cudaStream_t st) -> cudaError_t {
+    MassProx a;
+    memset(&a, 0, sizeof(a));
+    a.n = n;
+    a.eps = eps;
+    a.eps_ff = ff2(ff_make(eps));
+    a.inv_eps_ff = ff2(ff_make(1.0 / eps));
+    a.F = D1;
+    a.Fff = make_div_ff(D1, eps);
+    a.Z = Zd;
+    a.err = err;
+    const double* zc = zb;
+    const double* lp = logp;
+    const double* lw = logdx;
+    if (ffm) return pdl_launch(k_mass_prox<true>, nblocks(n), st, zc, lp, U, lw, a);
+    return pdl_launch(k_mass_prox<false>, nblocks(n), st, zc, lp, U, lw, a);
+  };
+  auto iteration = [&](double eps, bool check, cudaStream_t st) -> cudaError_t {
+    cudaError_t e;
+    Epilogue r;
+    memset(&r, 0, sizeof(r));
+    r.mode = EPI_RAW;
+    set_eps(r, eps);
+    r.out = zb;
+    r.bstride = n;
+    if ((e = G.apply(0, V, logdy, eps, r, st)) != cudaSuccess) return e;
+    MassArgs a;
+    memset(&a, 0, sizeof(a));
+    a.n = n;
+    a.eps = eps;
+    a.eps_ff = ff2(ff_make(eps));
+    a.inv_eps_ff = ff2(ff_make(1.0 / eps));
+    a.F3 = D3;
+    a.F3ff = make_div_ff(D3, eps);
+    a.logm0 = log(m0);
+    a.logm0_ff = ff2(ff_make(log(m0)));
+    a.update = first ? 0 : 1;
+    a.check = check ? 1 : 0;
+    a.Z = Zd;
+    a.acc = acc;
+    a.part = part;
+    a.count = count;
+    const double* Uc = U;
+    const double* zc = zb;
+    const double* lw = logdx;
+    const int rb = first ? 1 : red_blocks;
+    e = ffm ? pdl_launch(k_mass_reduce<true>, rb, st, Uc, zc, lw, a)
+            : pdl_launch(k_mass_reduce<false>, rb, st, Uc, zc, lw, a);
+    first = false;
+    if (e != cudaSuccess) return e;
+    if ((e = prox_a(eps, check ? acc : nullptr, st)) != cudaSuccess) return e;
+    Epilogue e2 = prox_epilogue(D2, logq, V, logdy, nullptr, eps);
+    e2.bstride = e2.bstride_p = m;
+    e2.zshift = Zd;
+    return G.apply(1, U, logdx, eps, e2, st);
+  };
+  double hacc[3];
+  auto read_err = [&](double& out) -> cudaError_t {
+    cudaError_t e = cudaMemcpyAsync(hacc, acc, sizeof(hacc), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    const double v = (hacc[1] > 0.0) ? hacc[0] / hacc[1] : 0.0;
+    out = (v != v || hacc[2] != hacc[2]) ? NAN : std::max(v, hacc[2]);
+    return cudaSuccess;
+  };
+
+  const std::vector<Stage> stages = eps_schedule(*o);
+  const int check_every = o->check_every > 0 ? o->check_every : 1;
+  int it = 0, total = 0;
+  double err = INFINITY;
+  bool converged = false;
+  for (const Stage& sg : stages)
+    for (int k = 0; k < sg.iters; ++k, ++total) UOT_CK(iteration(sg.eps, false, s));
+  // launch_mode 2 (and 1, 3, which have no mass variant): blocks of
+  // check_every iterations at the final eps replayed as one CUDA graph.
+  BlockGraph bg;
+  bool graph_ok = o->launch_mode != 0 && !profiling_on();
+  while (it < o->max_iter) {
+    if (graph_ok && !first && it > 0 && it % check_every == 0 && it + check_every <= o->max_iter) {
+      if (!bg.exec) {
+        cudaError_t e = bg.capture([&](cudaStream_t cs) -> cudaError_t {
+          for (int k = 0; k < check_every; ++k) {
+            cudaError_t e2 = iteration(o->eps, k == check_every - 1, cs);
+            if (e2 != cudaSuccess) return e2;
+          }
+          return cudaSuccess;
+        });
+        if (e != cudaSuccess) {
+          graph_ok = false;
+          (void)cudaGetLastError();
+          continue;
+        }
+      }
+      UOT_CK(bg.launch(s));
+      it += check_every;
+      total += check_every;
+      UOT_CK(read_err(err));
+      if (o->tol > 0.0 && err <= o->tol) {
+        converged = true;
+        break;
+      }
+      continue;
+    }
+    const bool check = ((it + 1) % check_every == 0) || (it == o->max_iter - 1);
+    UOT_CK(iteration(o->eps, check, s));
+    ++it;
+    ++total;
+    if (check) {
+      UOT_CK(read_err(err));
+      if (it > 1 && o->tol > 0.0 && err <= o->tol) {
+        converged = true;
+        break;
+      }
+    }
+  }
+
+  UOT_CK(cudaMemsetAsync(flag, 0, 4, s));
+  count_launches(1);
+  k_nan_flag<<<nblocks(n), kNT, 0, s>>>(U, n, ffm, flag);
+  count_launches(1);
+  k_nan_flag<<<nblocks(m), kNT, 0, s>>>(V, m, ffm, flag);
+  UOT_CK(cudaGetLastError());
+  UOT_CK(from_f64(prec, U, n, Uout, s));
+  UOT_CK(from_f64(prec, V, m, Vout, s));
+  UOT_CK(cudaEventRecord(ev1, s));
+  int hflag = 0, htc = 0;
+  double hZ = 0.0;
+  UOT_CK(cudaMemcpyAsync(&hflag, flag, 4, cudaMemcpyDeviceToHost, s));
+  UOT_CK(cudaMemcpyAsync(&hZ, Zd, 8, cudaMemcpyDeviceToHost, s));
+  if (G.tc_err) UOT_CK(cudaMemcpyAsync(&htc, G.tc_err, 4, cudaMemcpyDeviceToHost, s));
+  UOT_CK(cudaStreamSynchronize(s));
+  if (ffm) {
+    float2 zz;
+    memcpy(&zz, &hZ, sizeof(zz));
+    hZ = (double)zz.x + (double)zz.y;
+  }
+  *Zout = hZ;
+  float ms = 0.f;
+  UOT_CK(cudaEventElapsedTime(&ms, ev0, ev1));
+  uot_status out = htc ? UOT_TIMEOUT
+                       : (hflag || hZ != hZ) ? UOT_NUMERICAL
+                                             : ((o->tol > 0.0 && !converged && o->max_iter > 0) ? UOT_NOT_CONVERGED : UOT_OK);
+  if (res) {
+    res->iters = it;
+    res->total_iters = total;
+    res->marg_err = err;
+    res->ms = ms;
+    res->status = out;
+  }
+  return out;
+}
+
 }  // namespace
 
 void count_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
@@ -1652,6 +2160,14 @@ uot_status uot_solve(const uot_geom* g, const void* p, const void* dx, const voi
                      void* U, void* V, uot_result* res, void* stream) {
   clear_stale_error();
   return solve_impl(g, 1, p, dx, q, dy, F1, F2, o, U, V, res, (cudaStream_t)stream);
+}
+
+uot_status uot_solve_mass(const uot_geom* g, const void* p, const void* dx, const void* q,
+                          const void* dy, const uot_div* F1, const uot_div* F2, const uot_div* F3,
+                          double m0, const uot_opts* o, void* U, void* V, double* Z, uot_result* res,
+                          void* stream) {
+  clear_stale_error();
+  return solve_mass_impl(g, p, dx, q, dy, F1, F2, F3, m0, o, U, V, Z, res, (cudaStream_t)stream);
 }
 
 uot_status uot_solve_many(const uot_geom* g, int batch, const void* p, const void* dx,

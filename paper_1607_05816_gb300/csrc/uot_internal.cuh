@@ -143,6 +143,9 @@ struct Epilogue {
   double* pot;             // potential written (read first as the old value)
   const double* logw;      // log reference weight of the output side (violation)
   double* err;             // [2 per batch entry] = {sum dx |r_old - r_new|, sum dx r_new}; NULL: no check
+  const double* zshift;    // device scalar added to S before the prox (Algorithm 4's Z; a
+                           // float-float pair on the FP32 path); NULL: none.  Read after the
+                           // pass's inputs are complete.
   // EPI_PLAN
   const double* pot_shift; // U (or V) of the output side
   int ncols, col;
@@ -178,7 +181,8 @@ __device__ inline void apply_epilogue(const Epilogue& e, int64_t b, int64_t pt, 
       e.out[q] = (z == -kInf) ? -kInf : e.eps * z;
       break;
     case EPI_PROX: {
-      const double S = (z == -kInf) ? -kInf : e.eps * z;
+      double S = (z == -kInf) ? -kInf : e.eps * z;
+      if (e.zshift) S = (S == -kInf || *e.zshift == -kInf) ? -kInf : S + *e.zshift;
       const double Uold = e.pot[q];
       const double Unew = prox_update(e.F, e.logp[b * e.bstride_p + pt], S, e.eps);
       e.pot[q] = Unew;
@@ -246,6 +250,12 @@ __device__ inline void violation_terms_ff(ff Uold, ff Unew, ff S, ff logw, ff in
   den = w * rn;
 }
 
+// S + Z with Z a float-float device scalar (-inf absorbs).
+__device__ inline ff ff_zshift(ff S, const double* zshift) {
+  const ff Zv = ffl(*reinterpret_cast<const float2*>(zshift));
+  return (S.hi == -INFINITY || Zv.hi == -INFINITY) ? ff_ninf() : ff_add(S, Zv);
+}
+
 // Float-float epilogue (FP32 path): z is the log-sum in natural units.
 __device__ inline void apply_epilogue_ff(const Epilogue& e, int64_t b, int64_t pt, ff z, float& num,
                                          float& den) {
@@ -261,7 +271,8 @@ __device__ inline void apply_epilogue_ff(const Epilogue& e, int64_t b, int64_t p
       break;
     case EPI_PROX: {
       const ff eps = ffl(e.eps_ff);
-      const ff S = (z.hi == -INFINITY) ? ff_ninf() : ff_mul(z, eps);
+      ff S = (z.hi == -INFINITY) ? ff_ninf() : ff_mul(z, eps);
+      if (e.zshift) S = ff_zshift(S, e.zshift);
       float2* pot = reinterpret_cast<float2*>(e.pot);
       const ff Uold = ffl(pot[q]);
       const ff lp = ffl(reinterpret_cast<const float2*>(e.logp)[b * e.bstride_p + pt]);

@@ -77,6 +77,10 @@ _SIGS = {
     "uot_solve_many": (C.c_int, [C.POINTER(CGeom), C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                                  C.c_void_p, C.POINTER(CDiv), C.POINTER(CDiv), C.POINTER(COpts),
                                  C.c_void_p, C.c_void_p, C.POINTER(CResult), C.c_void_p]),
+    "uot_solve_mass": (C.c_int, [C.POINTER(CGeom), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                 C.POINTER(CDiv), C.POINTER(CDiv), C.POINTER(CDiv), C.c_double,
+                                 C.POINTER(COpts), C.c_void_p, C.c_void_p, C.POINTER(C.c_double),
+                                 C.POINTER(CResult), C.c_void_p]),
     "uot_gibbs_log": (C.c_int, [C.POINTER(CGeom), C.c_void_p, C.c_void_p, C.c_double, C.c_int,
                                 C.c_int, C.c_void_p, C.c_void_p]),
     "uot_gibbs_log_noalloc": (C.c_int, [C.POINTER(CGeom), C.c_void_p, C.c_void_p, C.c_double,
@@ -352,6 +356,30 @@ def solve(geom: Geometry, p, dx, q, dy, F1: Div, F2: Div, eps: float, *, precisi
     _check(st, "uot_solve")
     return U, V, dict(iters=r.iters, total_iters=r.total_iters, marg_err=r.marg_err, ms=r.ms,
                       status=STATUS[st])
+
+
+def solve_mass(geom: Geometry, p, dx, q, dy, F1: Div, F2: Div, F3: Div, m0: float, eps: float, *,
+               precision=F64, max_iter=1000, tol=0.0, check_every=10, eps_start=None, eps_stages=10,
+               iters_per_stage=100, U0=None, V0=None, U=None, V=None, launch_mode=0):
+    """uot_solve_mass (Algorithm 4, a divergence F3(. | m0) on the plan's total
+    mass): returns (U, V, Z, result dict); the plan is e^{(U_i + V_j + Z - C_ij)/eps}."""
+    lib = load()
+    dt = _dtype(precision)
+    U = torch.empty(geom.n, dtype=dt, device=p.device) if U is None else U
+    V = torch.empty(geom.m, dtype=dt, device=p.device) if V is None else V
+    o = COpts(precision, float(eps), float(eps_start) if eps_start else 0.0, int(eps_stages),
+              int(iters_per_stage), int(max_iter), float(tol), int(check_every), 0,
+              int(launch_mode), _ptr(U0, dt, "U0"), _ptr(V0, dt, "V0"))
+    r = CResult()
+    Z = C.c_double(0.0)
+    g = geom.c(precision)
+    st = lib.uot_solve_mass(C.byref(g), _ptr(p, dt, "p"), _ptr(dx, dt, "dx"), _ptr(q, dt, "q"),
+                            _ptr(dy, dt, "dy"), C.byref(F1.c()), C.byref(F2.c()), C.byref(F3.c()),
+                            float(m0), C.byref(o), _ptr(U, dt, "U"), _ptr(V, dt, "V"), C.byref(Z),
+                            C.byref(r), _stream())
+    _check(st, "uot_solve_mass")
+    return U, V, Z.value, dict(iters=r.iters, total_iters=r.total_iters, marg_err=r.marg_err,
+                               ms=r.ms, status=STATUS[st])
 
 
 def solve_many(geom: Geometry, P, dx, Q, dy, F1: Div, F2: Div, eps, *, precision=F64,
