@@ -21,7 +21,11 @@ unbalanced optimal transport problems" (arXiv:1607.05816):
 * separable Gaussian kernel on Cartesian grids applied by successive 1-D
   operations (Sec. 4.4, "Computing the matrix multiplications");
 * primal (P_eps) and dual (D_eps) functionals (Theorem 3.2) and their gap;
-* unbalanced barycenters (Sec. 5.2) with the KL row of Table 2.
+* unbalanced barycenters (Sec. 5.2) with the KL row of Table 2;
+* Algorithm 4 (a divergence on the plan's total mass, Sec. 4.5);
+* WF gradient flows with growth (Sec. 2 "Gradient flows", Sec. 5.3): the WF
+  cost of eq. logcost, the joint proxdiv of the growth functional for one or
+  several species, and the minimizing-movement steps.
 
 Notation used in code: U = eps log a, V = eps log b (total potentials),
 S_i = eps log (K b)_i, T_j = eps log (K^T a)_j.  Readings of points the paper
@@ -736,3 +740,101 @@ def barycenter_log(geom: Geometry, dx, dy, P, alpha, F1: Div, lam: float, eps: f
         for k in range(n):
             V[k] = prox_update_log(Fh, logh, T[k], eps)
     return U, V, (eps * logh if logh is not None else None)
+
+
+# ----------------------------------------------------------------------------
+# WF gradient flows with growth (Sec. 2 "Gradient flows", eq. grad-flow;
+# Sec. 5.3: WF gradient flows, the tumor growth example and its extension to
+# several species)
+# ----------------------------------------------------------------------------
+
+
+def wf_cost(x, y, cut: float = math.pi / 2) -> np.ndarray:
+    """Cost of the Wasserstein-Fisher-Rao distance (eq. logcost, Definition
+    WF of Sec. 2): c(x, y) = -log cos_+^2(d(x, y)) with cos_+(z) = cos(min(z, pi/2)).
+    The distance is rescaled so that c = +inf exactly when |x - y| >= cut,
+    d = (pi/2)|x - y|/cut, as in the paper's figures ("cut locus at 0.2");
+    cut = pi/2 is the plain Euclidean distance.  K = e^{-c/eps} = 0 beyond
+    the cut locus."""
+    d = (math.pi / 2) * np.sqrt(sqdist(x, y)) / cut
+    with np.errstate(divide="ignore"):
+        c = 0.0 - np.log(np.cos(np.minimum(d, math.pi / 2)) ** 2)
+    return np.where(d >= math.pi / 2, np.inf, c)
+
+
+def growth_c(tau: float, alpha: float, lam: float) -> float:
+    """c = 1 - 2 tau alpha / lam, the slope factor of the growth functional
+    G(mu) = -alpha mu(X) + iota_{<=1}(d mu/dx) inside F2 (Sec. 5.3); the step
+    needs 0 < c <= 1 (lam = 1 in the paper)."""
+    c = 1.0 - 2.0 * tau * alpha / lam
+    if not (0.0 < c <= 1.0):
+        raise ValueError("the growth step needs 0 <= 2 tau alpha < lam")
+    return c
+
+
+def prox_growth_log(T: np.ndarray, c: float, lam: float, eps: float) -> np.ndarray:
+    """Log-form proxdiv (u = 0) of the joint F2 of a WF gradient-flow step
+    with S species (Sec. 5.3; S = 1 is the tumor example):
+        F2(s^1..s^S) = inf_{r^k >= 0, sum_k r^k <= 1}
+                       sum_k lam KL(s^k | r^k) - 2 tau alpha sum_k r^k,
+    pointwise in x.  Its optimality conditions give r^k = s~^k / kappa with
+    kappa = max(c, sum_k s~^k), and F2 depends on the s~^k only through their
+    sum, with derivative lam log kappa in every species; the prox condition
+    eps log(s~^k / s^k) + lam log kappa = 0 then gives the same update for all
+    species:
+        V^k = min(-lam log c, -lam Ttot/(lam + eps)),  Ttot = eps log sum_k e^{T^k/eps},
+    T^k = eps log s^k (Ttot = -inf gives -lam log c).  With lam = 1 this is the
+    paper's proxdiv printed for one species and, via beta, for two."""
+    T = np.atleast_2d(np.asarray(T, dtype=np.float64))
+    Ttot = eps * lse(T / eps, axis=0)
+    with np.errstate(invalid="ignore"):
+        lin = np.where(np.isneginf(Ttot), np.inf, -lam * Ttot / (lam + eps))
+    V = np.minimum(-lam * math.log(c), lin)
+    return np.broadcast_to(V, T.shape).copy()
+
+
+def growth_next_density(R2: np.ndarray, c: float) -> np.ndarray:
+    """Densities of the next step from the second marginals r2^k of the
+    step's optimal couplings: the minimisers r^k of the inner infimum of F2,
+    r^k = r2^k / max(c, sum_k r2^k) (for one species min(r2/c, 1), Sec. 5.3)."""
+    R2 = np.atleast_2d(np.asarray(R2, dtype=np.float64))
+    return R2 / np.maximum(c, np.sum(R2, axis=0))
+
+
+def wf_flow_log(geom: Geometry, dx, P0, tau: float, alpha: float, lam: float, eps: float,
+                nsteps: int, iters: int, eps_start=None, stages: int = 10, iters_per_stage: int = 100):
+    """Minimizing movements (eq. grad-flow) of the growth functional
+    G(mu^1..mu^S) = -alpha sum_k mu^k(X) + iota_{<=1}(sum_k d mu^k/dx) for the
+    WF metric (Sec. 5.3), on points X = Y with weights dx (= dy) and the
+    geometry's cost (wf_cost for WF).  Each step solves eq. grad-flow, which
+    for each species k has F1 = lam KL(. | p^k) and all species share the
+    joint F2 of prox_growth_log, by the scaling iterations in log form started
+    from U = V = 0 (b = 1): `iters` iterations at eps after the eps-scaling
+    stages.  The next densities are growth_next_density of the plan's second
+    marginals r2^k = e^{(V^k + T^k)/eps} (T^k from the last iteration).
+    Returns dict(P = [nsteps, S, n] densities after each step, U, V, T of the
+    last step)."""
+    logdx = safe_log(dx)
+    P = np.atleast_2d(np.asarray(P0, dtype=np.float64)).copy()
+    S = P.shape[0]
+    c = growth_c(tau, alpha, lam)
+    F1 = KL(lam)
+    sched = eps_schedule(eps, eps_start, stages, iters_per_stage) + [(eps, iters)]
+    traj = []
+    U = V = T = None
+    for _ in range(nsteps):
+        logP = safe_log(P)
+        U = np.zeros_like(P)
+        V = np.zeros_like(P)
+        T = np.full_like(P, NEG_INF)
+        for e, n_it in sched:
+            for _ in range(n_it):
+                for k in range(S):
+                    U[k] = prox_update_log(F1, logP[k], apply_K_log(geom, V[k], logdx, e), e)
+                T = np.stack([apply_K_log(geom, U[k], logdx, e, transpose=True) for k in range(S)])
+                V = prox_growth_log(T, c, lam, e)
+        with np.errstate(invalid="ignore"):
+            logr2 = np.where(np.isneginf(T), NEG_INF, (V + T) / eps)
+        P = growth_next_density(np.exp(logr2), c)
+        traj.append(P.copy())
+    return dict(P=np.stack(traj), U=U, V=V, T=T)

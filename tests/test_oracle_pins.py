@@ -700,3 +700,180 @@ def test_alg4_matches_brute_force_minimisation(case):
         assert np.max(np.abs(R - Rb) / Rb) <= 2e-3
     if F3.kind == "eq":
         assert abs(np.sum(w * R) - m0) <= 1e-8  # the last b-update moves the mass slightly
+
+
+# --------------------------------------------------------------------------
+# WF gradient flows with growth (Sec. 5.3)
+# --------------------------------------------------------------------------
+
+def test_wf_cost_closed_forms():
+    """eq. logcost: c = -log cos^2(d), d = (pi/2)|x - y|/cut: zero on the
+    diagonal, log 2 at half the cut distance (cos^2(pi/4) = 1/2), log(4/3) at a
+    third (cos^2(pi/6) = 3/4), +inf from the cut locus on, ~d^2 for small d,
+    and isotropic in 2-D."""
+    cut = 0.4
+    x = np.array([0.3])
+    y = np.array([0.3, 0.3 + cut / 2, 0.3 - cut / 3, 0.3 + cut, 0.3 - 1.5 * cut, 0.3 + 1e-4])
+    c = O.wf_cost(x, y, cut)[0]
+    assert c[0] == 0.0
+    assert abs(c[1] - math.log(2.0)) < 1e-14
+    assert abs(c[2] - math.log(4.0 / 3.0)) < 1e-14
+    assert np.isposinf(c[3]) and np.isposinf(c[4])
+    d = (math.pi / 2) * 1e-4 / cut
+    assert abs(c[5] / d**2 - 1.0) < 1e-6
+    th = 0.7
+    P = np.array([[0.0, 0.0]])
+    Q = np.array([[0.25 * cut * math.cos(th), 0.25 * cut * math.sin(th)]])
+    assert abs(O.wf_cost(P, Q, cut)[0, 0] - O.wf_cost(np.array([0.0]), np.array([0.25 * cut]), cut)[0, 0]) < 1e-14
+    # unscaled: cut = pi/2 is the plain distance
+    assert abs(O.wf_cost(np.array([0.0]), np.array([0.5]))[0, 0] + math.log(math.cos(0.5) ** 2)) < 1e-14
+
+
+def _kl(a, b):
+    return a * np.log(a / b) - a + b
+
+
+def _growth_prox_brute(s, c, lam, eps):
+    """argmin over (s~^k, r^k) of eps sum_k KL(s~^k|s^k) + sum_k lam KL(s~^k|r^k)
+    - lam (1 - c) sum_k r^k subject to sum_k r^k <= 1 (the prox problem of F2 with
+    its inner infimum taken jointly; 2 tau alpha = lam (1 - c)); returns
+    eps log(s~^k/s^k) and r^k."""
+    s = np.asarray(s, dtype=float)
+    S = s.size
+
+    def obj(z):
+        st, r = np.exp(z[:S]), np.exp(z[S:])
+        return eps * np.sum(_kl(st, s)) + lam * np.sum(_kl(st, r)) - lam * (1.0 - c) * np.sum(r)
+
+    best = None
+    for z0 in (np.concatenate([np.log(s), np.full(S, math.log(0.5 / S))]),
+               np.concatenate([np.log(s) - 1.0, np.full(S, math.log(0.9 / S))])):
+        res = optimize.minimize(obj, z0, method="SLSQP",
+                                constraints=[{"type": "ineq", "fun": lambda z: 1.0 - np.sum(np.exp(z[S:]))}],
+                                options={"ftol": 1e-16, "maxiter": 5000})
+        if best is None or res.fun < best.fun:
+            best = res
+    return eps * (best.x[:S] - np.log(s)), np.exp(best.x[S:])
+
+
+@pytest.mark.parametrize("lam", [1.0, 0.6])
+@pytest.mark.parametrize("s", [0.05, 0.5, 2.0, 7.0])
+def test_growth_prox_single_species_brute_force(s, lam):
+    """Sec. 5.3, tumor example: the log-form proxdiv of F2 (one species)
+    against brute-force minimisation of its prox problem, on both sides of the
+    switch s = c^{(lam+eps)/eps}; with lam = 1 also against the paper's printed
+    case formula c^{-1/eps} / s^{-1/(1+eps)}."""
+    c, eps = 0.8, 0.3
+    V = O.prox_growth_log(np.array([[eps * math.log(s)]]), c, lam, eps)[0, 0]
+    Vb, _ = _growth_prox_brute([s], c, lam, eps)
+    assert abs(V - Vb[0]) < 2e-6
+    if lam == 1.0:
+        pdiv = c ** (-1.0 / eps) if s <= c ** ((1.0 + eps) / eps) else s ** (-1.0 / (1.0 + eps))
+        assert abs(V - eps * math.log(pdiv)) < 1e-13
+
+
+@pytest.mark.parametrize("lam", [1.0, 0.6])
+@pytest.mark.parametrize("sa,sb", [(0.05, 0.02), (0.4, 1.1), (3.0, 0.2), (0.3, 0.3)])
+def test_growth_prox_two_species_brute_force(sa, sb, lam):
+    """Sec. 5.3, two species: both species get the same update, which
+    minimises the joint prox problem; with lam = 1 it equals the paper's
+    printed 1/beta(s^a, s^b), beta = max((s^a + s^b)^{1/(1+eps)}, c^{1/eps})."""
+    c, eps = 0.7, 0.25
+    T = eps * np.log(np.array([[sa], [sb]]))
+    V = O.prox_growth_log(T, c, lam, eps)[:, 0]
+    Vb, _ = _growth_prox_brute([sa, sb], c, lam, eps)
+    assert np.max(np.abs(V - Vb)) < 2e-6
+    if lam == 1.0:
+        beta = max((sa + sb) ** (1.0 / (1.0 + eps)), c ** (1.0 / eps))
+        assert np.max(np.abs(V - eps * math.log(1.0 / beta))) < 1e-13
+
+
+def test_growth_prox_zero_input():
+    """s = 0 (T = -inf): the prox problem's minimiser is s~ = 0 for any
+    finite proxdiv; the case formula gives the constant branch c^{-1/eps}."""
+    c, lam, eps = 0.6, 1.0, 0.1
+    V = O.prox_growth_log(np.array([[-np.inf], [-np.inf]]), c, lam, eps)
+    assert np.all(V == -lam * math.log(c))
+
+
+@pytest.mark.parametrize("r2", [[0.3], [1.7], [0.1, 0.4], [0.9, 0.8], [0.0, 0.5]])
+def test_growth_next_density_brute_force(r2):
+    """Next densities = minimisers of F2's inner infimum at the plan's second
+    marginals: argmin_{r >= 0, sum r <= 1} sum_k lam KL(r2^k|r^k) - lam (1 - c) sum_k r^k;
+    one species: the paper's min(r2/c, 1)."""
+    c, lam = 0.75, 1.0
+    r2 = np.array(r2)
+    got = O.growth_next_density(r2[:, None], c)[:, 0]
+    pos = r2 > 0
+
+    def obj(z):
+        r = np.exp(z)
+        return lam * np.sum(_kl(r2[pos], r)) - lam * (1.0 - c) * np.sum(r)
+
+    res = optimize.minimize(obj, np.log(r2[pos] * 0.5 + 0.01), method="SLSQP",
+                            constraints=[{"type": "ineq", "fun": lambda z: 1.0 - np.sum(np.exp(z))}],
+                            options={"ftol": 1e-16, "maxiter": 5000})
+    assert np.max(np.abs(got[pos] - np.exp(res.x))) < 1e-6
+    assert np.all(got[~pos] == 0.0)
+    if r2.size == 1:
+        assert abs(got[0] - min(r2[0] / c, 1.0)) < 1e-15
+
+
+def _wf_step_problem(S):
+    n = 5
+    x = (np.arange(n) + 0.5) / n
+    dx = np.full(n, 1.0 / n)
+    g = np.random.default_rng(91 + S)
+    P0 = g.uniform(0.2, 0.45, size=(S, n))
+    return x, dx, P0
+
+
+@pytest.mark.parametrize("S,lam", [(1, 1.0), (2, 1.0), (2, 0.7)])
+def test_wf_step_matches_brute_force_minimisation(S, lam):
+    """One step of the WF gradient flow (eq. grad-flow with the growth
+    functional of Sec. 5.3) on 5 points with the cut locus at 0.5 (K = 0 for
+    pairs 0.6 and 0.8 apart): the oracle's plans e^{(U_i + V_j - c_ij)/eps} and
+    next densities minimise
+      sum_k [lam KL(R^k dy | p^k)_dx + lam KL(R^k^T dx | mu^k)_dx + eps KL(R^k | K)_{dx dy}]
+      - 2 tau alpha sum_j dx_j sum_k mu^k_j,   sum_k mu^k <= 1,
+    jointly over the plans on the kernel's support and the densities mu^k,
+    found by SLSQP."""
+    x, dx, P0 = _wf_step_problem(S)
+    n = x.size
+    tau, alpha, eps = 0.05, 1.0, 0.05
+    C = O.wf_cost(x, x, 0.5)
+    r = O.wf_flow_log(O.Geometry("dense", C=C), dx, P0, tau, alpha, lam, eps, nsteps=1, iters=3000)
+    sup = np.isfinite(C)
+    K = np.exp(-C[sup] / eps)
+    w = (dx[:, None] * dx[None, :])[sup]
+    nz = int(sup.sum())
+
+    def unpack(z):
+        R = np.zeros((S, n, n))
+        for k in range(S):
+            R[k][sup] = np.exp(z[k * nz:(k + 1) * nz])
+        return R, np.exp(z[S * nz:].reshape(S, n))
+
+    def obj(z):
+        R, mu = unpack(z)
+        v = 0.0
+        for k in range(S):
+            r1, r2 = R[k] @ dx, R[k].T @ dx
+            v += lam * np.sum(dx * _kl(r1, P0[k])) + lam * np.sum(dx * _kl(r2, mu[k]))
+            Rk = R[k][sup]
+            v += eps * np.sum(w * (Rk * np.log(Rk / K) - Rk + K))
+        return v - 2.0 * tau * alpha * np.sum(dx * np.sum(mu, axis=0))  # 2 tau G, G = -alpha mass
+
+    Ro = np.stack([np.where(sup, np.exp((r["U"][k][:, None] + r["V"][k][None, :] - C) / eps), 0.0)
+                   for k in range(S)])
+    muo = r["P"][0]
+    z0 = np.concatenate([np.log(Ro[k][sup]) + 0.1 for k in range(S)] + [np.log(muo).ravel() - 0.1])
+    res = optimize.minimize(obj, z0, method="SLSQP",
+                            constraints=[{"type": "ineq", "fun": lambda z: 1.0 - np.sum(unpack(z)[1], axis=0)}],
+                            options={"ftol": 1e-16, "maxiter": 20000})
+    zo = np.concatenate([np.log(Ro[k][sup]) for k in range(S)] + [np.log(muo).ravel()])
+    assert obj(zo) <= res.fun + 1e-10
+    Rb, mub = unpack(res.x)
+    assert np.max(np.abs(mub - muo)) < 2e-4
+    assert np.max(np.abs(Rb - Ro)) < 2e-3 * np.max(Ro)
+    assert np.all(np.sum(muo, axis=0) <= 1.0 + 1e-12)
