@@ -24,6 +24,7 @@ the same workload, a bounded number of iterations per step.
 from __future__ import annotations
 
 import argparse
+import math
 import json
 import os
 import statistics
@@ -47,8 +48,11 @@ SEED = 1235
 # clock per SM) x 152 SMs x the 2070 MHz maximum SM clock.
 SM_COUNT, MUFU_PER_CLK, SM_MAX_MHZ = 152, 32, 2070.0
 MUFU_PEAK_GEXP = SM_COUNT * MUFU_PER_CLK * SM_MAX_MHZ * 1e6 / 1e9
-# FP64 pipe (Algorithm 1 matvec): GB300 runs FP64 at 1.25 TFLOP/s nominal.
+# FP64 pipe (Algorithm 1 matvec): GB300 runs FP64 at 1.25 TFLOP/s nominal,
+# i.e. 2 DFMA per clock per SM.
 FP64_PEAK_GFLOPS = 1250.0
+FP64_PER_CLK = 2
+FP64_OPS_PER_ROW_TERM = 5
 # FP32 pipe: 128 lanes per clock per SM (FADD/FMUL/FFMA; a packed f32x2
 # instruction occupies it for two lane-slots per pair).
 FP32_PER_CLK = 128
@@ -361,7 +365,10 @@ def run_single(args, rank, world, local_rank):
     """points: n = m = 20000 colour-like clouds in [0,1]^3, KL (or TV) lambda = 0.1,
     eps-scaling 1e-1 -> 1e-3, tol 1e-6, FP32 online cost.
     dense1d: 1-D 256 points, KL lambda = 1, eps = 1e-2, Algorithm 1 FP64, 2000 iterations.
-    bary: KL barycenter of 32 blob images 128x128, lambda = 1, eps = 1e-2, 500 iterations."""
+    bary: KL barycenter of 32 blob images 128x128, lambda = 1, eps = 1e-2, 500 iterations.
+    wf: WF gradient flow with growth (Sec. 5.3) on 3000 samples of [0, 1], FP64, 500
+    iterations per flow step, 4 flow steps per bench step: one species tau = 0.006,
+    eps = 1e-8, or two species tau = 0.004, eps = 1e-7 (the paper's runs), alpha = 1."""
     import torch
 
     from paper_1607_05816_gb300 import synth, uot
@@ -397,6 +404,25 @@ def run_single(args, rank, world, local_rank):
                              plain_scaling=True)
         work_per_iter, unit_work, kernel = 2.0 * 256 * 256 * 2, "GFLOP/s", "alg1_half"
         cfg = {"workload": "dense1d-256-kl1-eps1e-2-alg1-2000it", "n": 256, "m": 256}
+        dtype = "f64"
+    elif wl == "wf":
+        S = args.wf_species
+        n, nflow, tau, eps = 3000, 4, (0.006 if S == 1 else 0.004), (1e-8 if S == 1 else 1e-7)
+        x, dxw, P0 = synth.tumor_densities(n, S, seed=1240 + rank)
+        xt = f(x, torch.float64)
+        geo = uot.Geometry.dense(uot.wf_cost(xt, xt, math.pi / 2, precision=uot.F64))
+        P0t, dxt = f(P0, torch.float64), f(dxw, torch.float64)
+
+        def step():
+            P_, U_, V_, info = uot.wf_flow(geo, P0t, dxt, tau, 1.0, 1.0, eps, nflow, precision=uot.F64,
+                                           iters=500, launch_mode=args.launch_mode)
+            info["marg_err"] = float("nan")
+            return U_, V_, info
+        work_per_iter, unit_work, kernel = 2.0 * S * n * n, "Gterm/s", "rows_lse<double>"
+        cfg = {"workload": f"wf-flow-{S}species-3000-eps{eps:g}-tau{tau:g}-alpha1-500it-x4steps",
+               "n": n, "species": S, "eps": eps, "tau": tau, "alpha": 1.0, "lambda": 1.0,
+               "iters_per_flow_step": 500, "flow_steps_per_bench_step": nflow,
+               "cost": "WF, unscaled distance (cut locus at pi/2)"}
         dtype = "f64"
     else:  # bary
         b = synth.barycenter_images(32, 128, 128, seed=1237 + rank)
@@ -458,6 +484,16 @@ def run_single(args, rank, world, local_rank):
                                         timing)
         if wl == "bary":
             line["grid_tiles"] = uot.autotune_table().strip().splitlines()
+    elif unit_work == "Gterm/s":
+        # rows_lse<double>: per term DFMA + DMNMX (max sweep), DADD + DFMA + DSETP
+        # (sum sweep; the FP64 exponential runs only where it does not underflow)
+        peak = SM_COUNT * FP64_PER_CLK * SM_MAX_MHZ * 1e6 / 1e9 / FP64_OPS_PER_ROW_TERM
+        line["roofline"] = {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peak,
+                            "unit": unit_work, "frac": achieved / peak, "traffic": None,
+                            "binding_pipe": "fp64",
+                            "peak_source": "derived: 152 SMs x 2070 MHz x 2 DFMA/clk (1.25 TFLOP/s nominal FP64) "
+                                           f"/ {FP64_OPS_PER_ROW_TERM} FP64-pipe ops per term",
+                            "timing": timing}
     else:
         line["roofline"] = {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": FP64_PEAK_GFLOPS,
                             "unit": unit_work, "frac": achieved / FP64_PEAK_GFLOPS, "traffic": None,
@@ -608,7 +644,9 @@ def main():
     ap.add_argument("--max-iter", type=int, default=0)
     ap.add_argument("--no-eps-scaling", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="grid2d", choices=["grid2d", "batch", "points", "dense1d", "bary"])
+    ap.add_argument("--workload", default="grid2d", choices=["grid2d", "batch", "points", "dense1d", "bary", "wf"])
+    ap.add_argument("--wf-species", type=int, default=1, choices=[1, 2],
+                    help="species of the wf workload (Sec. 5.3: the tumor example or its two-species extension)")
     ap.add_argument("--penalty", default="kl", choices=["kl", "tv"])
     ap.add_argument("--batch-nprob", type=int, default=0)
     ap.add_argument("--launch-mode", type=int, default=2, choices=[0, 1, 2, 3],
@@ -632,7 +670,7 @@ def main():
     try:
         if args.workload == "batch":
             run_batch(args, rank, world, local_rank)
-        elif args.workload in ("points", "dense1d", "bary"):
+        elif args.workload in ("points", "dense1d", "bary", "wf"):
             run_single(args, rank, world, local_rank)
         else:
             run_ours(args, rank, world, local_rank)

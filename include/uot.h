@@ -82,7 +82,8 @@ typedef struct {
   int kind; /* uot_geom_kind */
   int n, m; /* number of points on each side; for grids the product of the shape */
   /* UOT_GEOM_DENSE */
-  const void* C; /* [n*m] row-major, C_ij >= 0 need not hold but must be finite */
+  const void* C; /* [n*m] row-major; C_ij >= 0 need not hold; +INFINITY means K_ij = 0 (not for
+                    uot_objective or plain_scaling, which need finite costs); no NaN or -inf */
   /* UOT_GEOM_GRID: potentials and densities are row-major arrays of the grid's shape */
   int ndim;                        /* 1..UOT_MAX_DIM */
   int shape_x[UOT_MAX_DIM];        /* grid of X: shape_x[0] x ... x shape_x[ndim-1] */
@@ -437,6 +438,56 @@ uot_status uot_barycenter_div(const uot_geom* g, int Kmeas, const double* alpha,
                               const void* dx, const void* dy, const uot_div* F1, const uot_div* Fh,
                               const uot_opts* o, void* logh, void* U, void* V, uot_result* res,
                               void* stream);
+
+/*
+ * uot_wf_cost -- dense cost matrix of the Wasserstein-Fisher-Rao distance
+ * (eq. logcost, Definition WF of Sec. 2):
+ *   C[i*m + j] = -log cos^2((pi/2) |x_i - y_j| / cut)   for |x_i - y_j| < cut,
+ *              = +INFINITY                               otherwise (K_ij = 0),
+ * i.e. the distance rescaled so that the cut locus lies at distance `cut`
+ * (cut = pi/2: the plain Euclidean distance).  x [n*d], y [m*d] row-major,
+ * 1 <= d <= 8, C [n*m] in the precision's type (UOT_F64 or UOT_F32; computed
+ * in FP64 either way).  Use it as a UOT_GEOM_DENSE geometry.
+ */
+uot_status uot_wf_cost(const void* x, int n, const void* y, int m, int d, double cut, int precision,
+                       void* C, void* stream);
+
+/*
+ * uot_wf_flow -- WF gradient flow with growth (Sec. 2 "Gradient flows",
+ * eq. grad-flow; Sec. 5.3, the tumor example and its extension to several
+ * species): `nsteps` minimizing-movement steps of
+ *   G(mu^1..mu^S) = -alpha sum_k mu^k(X) + iota_{<=1}(sum_k d mu^k/dx)
+ * for S = nspecies measures on the same points (X = Y, dy = dx, g->n == g->m),
+ * with the geometry's cost (uot_wf_cost for WF).  Each step solves
+ *   min over couplings R^k:  sum_k [lam KL(R^k dy | p^k) + lam KL(R^k^T dx | mu^k)
+ *                            + eps KL(R^k | K)] + 2 tau G(mu^1..mu^S)
+ * by the scaling iteration in log form started from U = V = 0 (b = 1):
+ *   U^k = lam/(lam+eps) (eps log p^k - S^k)                     (F1 = lam KL(.|p^k))
+ *   V^k = min(-lam log c, -lam Ttot/(lam+eps)),  Ttot = eps log sum_k e^{T^k/eps}
+ * with c = 1 - 2 tau alpha/lam (lam = 1 is the paper's WF; with lam = 1, S = 1
+ * this is the paper's printed proxdiv for the tumor example, and for S = 2
+ * its 1/beta form).  The step ends with the next densities
+ *   p^k <- r2^k / max(c, sum_k r2^k),  r2^k = e^{(V^k + T^k)/eps},
+ * the minimisers of F2's inner infimum at the couplings' second marginals
+ * (for one species min(r2/c, 1)).
+ *  nspecies    S >= 1
+ *  P0          [S*n] initial densities w.r.t. dx (>= 0)
+ *  dx          [n] reference weights (> 0)
+ *  tau, alpha  time step > 0 and growth rate >= 0 with 2 tau alpha < lambda
+ *  lambda      KL weight lam > 0
+ *  o           precision UOT_F64 or UOT_F32 (UOT_MIXED: UOT_EUNSUPPORTED); eps, and the
+ *              eps-scaling fields, apply within every step; max_iter = iterations per step
+ *              at eps (the paper stops each step after a fixed count); tol must be 0;
+ *              U0, V0 must be NULL; launch_mode 2 replays the whole step as one CUDA graph
+ *  P           [nsteps*S*n] output: the densities after each step
+ *  U, V        [S*n] outputs: the last step's potentials
+ *  res         iters = max_iter, total_iters = all iterations, marg_err = NaN (not measured)
+ * The paper's runs use eps = 1e-7 and 1e-8 on 3000 points: only UOT_F64 resolves the
+ * marginals there (FP32 carries exponent errors of |U|/eps x 6e-8).
+ */
+uot_status uot_wf_flow(const uot_geom* g, int nspecies, const void* P0, const void* dx, double tau,
+                       double alpha, double lambda, const uot_opts* o, int nsteps, void* P, void* U,
+                       void* V, uot_result* res, void* stream);
 
 /*
  * Learned warm start (not in the paper).  A small dilated convolutional

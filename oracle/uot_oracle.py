@@ -756,10 +756,11 @@ def wf_cost(x, y, cut: float = math.pi / 2) -> np.ndarray:
     d = (pi/2)|x - y|/cut, as in the paper's figures ("cut locus at 0.2");
     cut = pi/2 is the plain Euclidean distance.  K = e^{-c/eps} = 0 beyond
     the cut locus."""
-    d = (math.pi / 2) * np.sqrt(sqdist(x, y)) / cut
+    dist = np.sqrt(sqdist(x, y))
+    d = (math.pi / 2) * dist / cut
     with np.errstate(divide="ignore"):
         c = 0.0 - np.log(np.cos(np.minimum(d, math.pi / 2)) ** 2)
-    return np.where(d >= math.pi / 2, np.inf, c)
+    return np.where(dist >= cut, np.inf, c)
 
 
 def growth_c(tau: float, alpha: float, lam: float) -> float:
@@ -801,6 +802,15 @@ def growth_next_density(R2: np.ndarray, c: float) -> np.ndarray:
     return R2 / np.maximum(c, np.sum(R2, axis=0))
 
 
+def growth_next_log_density(logR2: np.ndarray, c: float) -> np.ndarray:
+    """growth_next_density in log form: log r2^k - log max(c, sum_k r2^k).  A
+    density below the FP64 range keeps its (finite) logarithm instead of
+    becoming 0, as it would in exact arithmetic."""
+    logR2 = np.atleast_2d(np.asarray(logR2, dtype=np.float64))
+    tot = np.sum(np.exp(logR2), axis=0)
+    return logR2 - np.log(np.maximum(c, tot))
+
+
 def wf_flow_log(geom: Geometry, dx, P0, tau: float, alpha: float, lam: float, eps: float,
                 nsteps: int, iters: int, eps_start=None, stages: int = 10, iters_per_stage: int = 100):
     """Minimizing movements (eq. grad-flow) of the growth functional
@@ -811,22 +821,24 @@ def wf_flow_log(geom: Geometry, dx, P0, tau: float, alpha: float, lam: float, ep
     joint F2 of prox_growth_log, by the scaling iterations in log form started
     from U = V = 0 (b = 1): `iters` iterations at eps after the eps-scaling
     stages.  The next densities are growth_next_density of the plan's second
-    marginals r2^k = e^{(V^k + T^k)/eps} (T^k from the last iteration).
+    marginals r2^k = e^{(V^k + T^k)/eps} (T^k from the last iteration); they
+    pass to the next step as log densities (growth_next_log_density), the
+    log-domain stabilisation of Sec. 4.3 carried over the step boundary, so
+    that a positive density below the FP64 range stays positive.
     Returns dict(P = [nsteps, S, n] densities after each step, U, V, T of the
     last step)."""
     logdx = safe_log(dx)
-    P = np.atleast_2d(np.asarray(P0, dtype=np.float64)).copy()
-    S = P.shape[0]
+    logP = safe_log(np.atleast_2d(np.asarray(P0, dtype=np.float64)))
+    S = logP.shape[0]
     c = growth_c(tau, alpha, lam)
     F1 = KL(lam)
     sched = eps_schedule(eps, eps_start, stages, iters_per_stage) + [(eps, iters)]
     traj = []
     U = V = T = None
     for _ in range(nsteps):
-        logP = safe_log(P)
-        U = np.zeros_like(P)
-        V = np.zeros_like(P)
-        T = np.full_like(P, NEG_INF)
+        U = np.zeros_like(logP)
+        V = np.zeros_like(logP)
+        T = np.full_like(logP, NEG_INF)
         for e, n_it in sched:
             for _ in range(n_it):
                 for k in range(S):
@@ -835,6 +847,6 @@ def wf_flow_log(geom: Geometry, dx, P0, tau: float, alpha: float, lam: float, ep
                 V = prox_growth_log(T, c, lam, e)
         with np.errstate(invalid="ignore"):
             logr2 = np.where(np.isneginf(T), NEG_INF, (V + T) / eps)
-        P = growth_next_density(np.exp(logr2), c)
-        traj.append(P.copy())
+        logP = growth_next_log_density(logr2, c)
+        traj.append(np.exp(logP))
     return dict(P=np.stack(traj), U=U, V=V, T=T)

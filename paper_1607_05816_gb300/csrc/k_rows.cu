@@ -115,15 +115,19 @@ __global__ void __launch_bounds__(WARPS * 32)
         m = fmax(m, fma(-k2, cost_ij<T, DMAX>(kind, C, y, d, rowbase, j, c), Lt[j]));
       m = wmax(m);
       T s = 0;
-      for (int j = lane; j < nin; j += 32) {
-        const T a = fma(-k2, cost_ij<T, DMAX>(kind, C, y, d, rowbase, j, c), Lt[j] - m);
-        if (sizeof(T) == 4)
-          s += ex2_approx((float)a);
-        else
-          s += exp((double)a);
-      }
+      // m = -inf: every term vanishes (C = +inf where the input is finite)
+      if (m != -INFINITY)
+        for (int j = lane; j < nin; j += 32) {
+          const T a = fma(-k2, cost_ij<T, DMAX>(kind, C, y, d, rowbase, j, c), Lt[j] - m);
+          if (sizeof(T) == 4)
+            s += ex2_approx((float)a);
+          else if (a > -746.0)  // below, e^a is 0 in FP64: skip the FP64 exponential
+            s += exp((double)a);
+        }
       s = wsum(s);
-      if (lane == 0) {
+      if (lane == 0 && m == -INFINITY) {
+        apply_epilogue(epi, 0, i, -kInf, num, den);
+      } else if (lane == 0) {
         const double z = Lmax + ((sizeof(T) == 4) ? (double)kLn2 * (double)m : (double)m) +
                          log((double)s);
         apply_epilogue(epi, 0, i, z, num, den);
@@ -190,10 +194,14 @@ __global__ void __launch_bounds__(WARPS * 32)
         m = fmaxf(m, fmaf(-k2, cost_ij<float, DMAX>(kind, C, y, d, rowbase, j, c), Lt[j]));
       m = wmax(m);
       float s = 0.0f;
-      for (int j = lane; j < nin; j += 32)
-        s += ex2_approx(fmaf(-k2, cost_ij<float, DMAX>(kind, C, y, d, rowbase, j, c), Lt[j] - m));
+      // m = -inf: every term vanishes (C = +inf where the input is finite)
+      if (m != -INFINITY)
+        for (int j = lane; j < nin; j += 32)
+          s += ex2_approx(fmaf(-k2, cost_ij<float, DMAX>(kind, C, y, d, rowbase, j, c), Lt[j] - m));
       s = wsum(s);
-      if (lane == 0) {
+      if (lane == 0 && m == -INFINITY) {
+        apply_epilogue_ff(epi, 0, i, ff_ninf(), num, den);
+      } else if (lane == 0) {
         const ff ln2 = ff{0.693147182464599609375f, -1.904654323148236017e-09f};
         float lg;
         asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(lg) : "f"(s));

@@ -12,7 +12,8 @@ Shapes follow the paper's experiments:
   * 2-D images of shapes on [0, 1]^2 (Sec. 5.1, 2-D examples);
   * 3-D colour-like point clouds in [0, 1]^3 (Sec. 5.1, colour transfer);
   * batches of 2-D point clouds and stacks of blob images for barycenters
-    (Sec. 5.2).
+    (Sec. 5.2);
+  * initial tumor densities on [0, 1] for the WF gradient flows (Sec. 5.3).
 The reference measures are the discretised Lebesgue measure (grid) or the
 uniform empirical measure (points), both probability vectors (Sec. 4.2).
 """
@@ -175,3 +176,20 @@ def warmstart_instances(n: int, H: int = 64, W: int = 64, seed: int = 1239, grou
         E[k] = e
         L[k] = lm
     return dict(P=P, Q=Q, eps=E, lam=L, dx=dx, xs=[grid_axis(H), grid_axis(W)])
+
+
+def tumor_densities(n: int = 3000, species: int = 1, seed: int = 1240):
+    """Initial densities of the growth flows (Sec. 5.3): S species on the
+    uniform grid of [0, 1] (the paper uses 3000 samples), each a bump of
+    height 0.3-0.7 below the cap 1, with a seeded ripple, on a subinterval of
+    width 0.1-0.3, exactly 0 elsewhere.  Returns (x, dx, P [S, n])."""
+    g = rng(seed)
+    x = grid_axis(n)
+    P = np.zeros((species, n))
+    for k in range(species):
+        c0 = g.uniform(0.25, 0.75)
+        w = g.uniform(0.05, 0.15)
+        amp = g.uniform(0.3, 0.7)
+        f = g.uniform(10.0, 40.0)
+        P[k] = np.where(np.abs(x - c0) < w, amp * (1.0 + 0.2 * np.sin(f * x)), 0.0)
+    return x, np.full(n, 1.0 / n), P

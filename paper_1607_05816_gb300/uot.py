@@ -81,6 +81,11 @@ _SIGS = {
                                  C.POINTER(CDiv), C.POINTER(CDiv), C.POINTER(CDiv), C.c_double,
                                  C.POINTER(COpts), C.c_void_p, C.c_void_p, C.POINTER(C.c_double),
                                  C.POINTER(CResult), C.c_void_p]),
+    "uot_wf_cost": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_int,
+                              C.c_void_p, C.c_void_p]),
+    "uot_wf_flow": (C.c_int, [C.POINTER(CGeom), C.c_int, C.c_void_p, C.c_void_p, C.c_double, C.c_double,
+                              C.c_double, C.POINTER(COpts), C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                              C.POINTER(CResult), C.c_void_p]),
     "uot_gibbs_log": (C.c_int, [C.POINTER(CGeom), C.c_void_p, C.c_void_p, C.c_double, C.c_int,
                                 C.c_int, C.c_void_p, C.c_void_p]),
     "uot_gibbs_log_noalloc": (C.c_int, [C.POINTER(CGeom), C.c_void_p, C.c_void_p, C.c_double,
@@ -380,6 +385,43 @@ def solve_mass(geom: Geometry, p, dx, q, dy, F1: Div, F2: Div, F3: Div, m0: floa
     _check(st, "uot_solve_mass")
     return U, V, Z.value, dict(iters=r.iters, total_iters=r.total_iters, marg_err=r.marg_err,
                                ms=r.ms, status=STATUS[st])
+
+
+def wf_cost(x, y, cut, precision=F64, out=None):
+    """uot_wf_cost: the WF cost matrix -log cos^2((pi/2)|x - y|/cut), +inf beyond
+    the cut locus; x [n] or [n, d], y [m] or [m, d] on the GPU.  Returns C [n, m]."""
+    lib = load()
+    dt = _dtype(precision)
+    x2 = x.reshape(x.shape[0], -1)
+    y2 = y.reshape(y.shape[0], -1)
+    n, d = x2.shape
+    m = y2.shape[0]
+    out = torch.empty(n, m, dtype=dt, device=x.device) if out is None else out
+    _check(lib.uot_wf_cost(_ptr(x2, dt, "x"), n, _ptr(y2, dt, "y"), m, d, float(cut), precision,
+                           _ptr(out, dt, "C"), _stream()), "uot_wf_cost")
+    return out
+
+
+def wf_flow(geom: Geometry, P0, dx, tau, alpha, lam, eps, nsteps, *, precision=F64, iters=500,
+            eps_start=None, eps_stages=10, iters_per_stage=100, launch_mode=2):
+    """uot_wf_flow: WF gradient flow with growth, P0 [S, n] initial densities.
+    Returns (P [nsteps, S, n], U [S, n], V [S, n], info)."""
+    lib = load()
+    dt = _dtype(precision)
+    P0 = P0.reshape(-1, geom.n)
+    S = P0.shape[0]
+    P = torch.empty(nsteps, S, geom.n, dtype=dt, device=P0.device)
+    U = torch.empty(S, geom.n, dtype=dt, device=P0.device)
+    V = torch.empty(S, geom.n, dtype=dt, device=P0.device)
+    o = COpts(precision, float(eps), float(eps_start) if eps_start else 0.0, int(eps_stages),
+              int(iters_per_stage), int(iters), 0.0, 1, 0, int(launch_mode), None, None)
+    r = CResult()
+    g = geom.c(precision)
+    st = lib.uot_wf_flow(C.byref(g), S, _ptr(P0, dt, "P0"), _ptr(dx, dt, "dx"), float(tau), float(alpha),
+                         float(lam), C.byref(o), int(nsteps), _ptr(P, dt, "P"), _ptr(U, dt, "U"),
+                         _ptr(V, dt, "V"), C.byref(r), _stream())
+    _check(st, "uot_wf_flow")
+    return P, U, V, dict(iters=r.iters, total_iters=r.total_iters, ms=r.ms, status=STATUS[st])
 
 
 def solve_many(geom: Geometry, P, dx, Q, dy, F1: Div, F2: Div, eps, *, precision=F64,

@@ -712,8 +712,8 @@ def test_wf_cost_closed_forms():
     third (cos^2(pi/6) = 3/4), +inf from the cut locus on, ~d^2 for small d,
     and isotropic in 2-D."""
     cut = 0.4
-    x = np.array([0.3])
-    y = np.array([0.3, 0.3 + cut / 2, 0.3 - cut / 3, 0.3 + cut, 0.3 - 1.5 * cut, 0.3 + 1e-4])
+    x = np.array([0.0])  # distances exactly as written (the cut locus included)
+    y = np.array([0.0, cut / 2, -cut / 3, cut, -1.5 * cut, 1e-4])
     c = O.wf_cost(x, y, cut)[0]
     assert c[0] == 0.0
     assert abs(c[1] - math.log(2.0)) < 1e-14
@@ -817,6 +817,20 @@ def test_growth_next_density_brute_force(r2):
     assert np.all(got[~pos] == 0.0)
     if r2.size == 1:
         assert abs(got[0] - min(r2[0] / c, 1.0)) < 1e-15
+
+
+def test_growth_next_log_density_is_the_log_of_the_density():
+    """The log form that carries densities between steps equals the log of
+    growth_next_density where that is representable, and stays finite (and
+    ordered) where the density underflows FP64."""
+    c = 0.8
+    logR2 = np.array([[-3.0, 0.5, -2000.0, -np.inf], [-1.0, -4.0, -2001.0, -np.inf]])
+    lp = O.growth_next_log_density(logR2, c)
+    p = O.growth_next_density(np.exp(logR2), c)
+    ok = p > 0
+    assert np.max(np.abs(lp[ok] - np.log(p[ok]))) < 1e-14
+    assert np.all(np.isfinite(lp[:, 2])) and lp[0, 2] - lp[1, 2] == 1.0
+    assert np.all(np.isneginf(lp[:, 3]))
 
 
 def _wf_step_problem(S):
