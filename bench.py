@@ -52,7 +52,11 @@ MUFU_PEAK_GEXP = SM_COUNT * MUFU_PER_CLK * SM_MAX_MHZ * 1e6 / 1e9
 # i.e. 2 DFMA per clock per SM.
 FP64_PEAK_GFLOPS = 1250.0
 FP64_PER_CLK = 2
-FP64_OPS_PER_ROW_TERM = 5
+# HBM copy bandwidth measured on this GPU type (MEASURED_PEAKS.json hbm_gbs)
+HBM_PEAK_GBS = 6760.6
+# dram bytes of one rows_lse_f64_pf<4, 2, 1> launch of the wf workload (ncu,
+# profiles/rows_lse_f64_pf_wf3000.md); None once the kernel changes
+WF_ROWS_TRAFFIC_BYTES = 36816384
 # FP32 pipe: 128 lanes per clock per SM (FADD/FMUL/FFMA; a packed f32x2
 # instruction occupies it for two lane-slots per pair).
 FP32_PER_CLK = 128
@@ -418,7 +422,7 @@ def run_single(args, rank, world, local_rank):
                                            iters=500, launch_mode=args.launch_mode)
             info["marg_err"] = float("nan")
             return U_, V_, info
-        work_per_iter, unit_work, kernel = 2.0 * S * n * n, "Gterm/s", "rows_lse<double>"
+        work_per_iter, unit_work, kernel = 2.0 * S * n * n, "Gterm/s", "rows_lse_f64_pf<4, 2, 1>"
         cfg = {"workload": f"wf-flow-{S}species-3000-eps{eps:g}-tau{tau:g}-alpha1-500it-x4steps",
                "n": n, "species": S, "eps": eps, "tau": tau, "alpha": 1.0, "lambda": 1.0,
                "iters_per_flow_step": 500, "flow_steps_per_bench_step": nflow,
@@ -485,14 +489,18 @@ def run_single(args, rank, world, local_rank):
         if wl == "bary":
             line["grid_tiles"] = uot.autotune_table().strip().splitlines()
     elif unit_work == "Gterm/s":
-        # rows_lse<double>: per term DFMA + DMNMX (max sweep), DADD + DFMA + DSETP
-        # (sum sweep; the FP64 exponential runs only where it does not underflow)
-        peak = SM_COUNT * FP64_PER_CLK * SM_MAX_MHZ * 1e6 / 1e9 / FP64_OPS_PER_ROW_TERM
-        line["roofline"] = {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peak,
-                            "unit": unit_work, "frac": achieved / peak, "traffic": None,
-                            "binding_pipe": "fp64",
-                            "peak_source": "derived: 152 SMs x 2070 MHz x 2 DFMA/clk (1.25 TFLOP/s nominal FP64) "
-                                           f"/ {FP64_OPS_PER_ROW_TERM} FP64-pipe ops per term",
+        # rows_lse_f64_pf: the FP32 prefilter reads the FP32 copy of the cost once
+        # per term (4 B; both sweeps run from shared memory) and evaluates FP64
+        # exponentials only where they do not underflow, so its floor is HBM.
+        gbs = achieved * 4.0
+        line["roofline"] = {"bound": "hbm", "kernel": kernel, "achieved": gbs, "peak": HBM_PEAK_GBS,
+                            "unit": "GB/s", "frac": gbs / HBM_PEAK_GBS,
+                            "traffic": WF_ROWS_TRAFFIC_BYTES,
+                            "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch "
+                                              "(cold cache; profiles/rows_lse_f64_pf_wf3000.md)",
+                            "algorithmic_bytes_per_launch": 4.0 * n * n,
+                            "terms_per_s": achieved * 1e9,
+                            "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy), of measured",
                             "timing": timing}
     else:
         line["roofline"] = {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": FP64_PEAK_GFLOPS,

@@ -10,6 +10,8 @@
 //
 // Algorithm 1 (Sec. 4.2): a_i = proxdiv_F(sum_j K_ij b_j w_j, eps) on a stored
 // FP64 kernel K = exp(-C/eps), with the proxdiv column of Table 1 (u = 0).
+#include <algorithm>
+
 #include "uot_internal.cuh"
 
 namespace uot {
@@ -35,18 +37,22 @@ __device__ __forceinline__ T wsum(T v) {
 }
 
 // L_j = W_j/eps + log w_j in FP64; then Lt_j = (L_j - max L) in T, scaled by
-// log2(e) for the FP32 variant.  Single block; *Lmax receives max L.
+// log2(e) for the FP32 variant.  Single block; *Lmax receives max L.  Lt32,
+// if given, receives an FP32 copy of the FP64 Lt (the prefilter's input).
 template <typename T, int NT>
 __global__ void __launch_bounds__(NT) prepare_L(const double* __restrict__ W,
                                                 const double* __restrict__ logw, int nin,
                                                 double eps, T* __restrict__ Lt,
-                                                double* __restrict__ Lmax) {
+                                                double* __restrict__ Lmax, float* __restrict__ Lt32 = nullptr) {
   __shared__ double red[NT / 32];
+  const double inv_eps = 1.0 / eps;
   double mx = -kInf;
+  // L_j is stored unshifted first, then shifted in place (one FP64 evaluation each)
   for (int j = threadIdx.x; j < nin; j += NT) {
     const double w = W[j];
-    const double L = (w == -kInf) ? -kInf : w / eps + logw[j];
+    const double L = (w == -kInf) ? -kInf : fma(w, inv_eps, logw[j]);
     mx = fmax(mx, L);
+    if (sizeof(T) == 8) reinterpret_cast<double*>(Lt)[j] = L;
   }
   mx = wmax(mx);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
@@ -59,11 +65,17 @@ __global__ void __launch_bounds__(NT) prepare_L(const double* __restrict__ W,
   __syncthreads();
   mx = red[0];
   for (int j = threadIdx.x; j < nin; j += NT) {
-    const double w = W[j];
-    const double L = (w == -kInf) ? -kInf : w / eps + logw[j];
+    double L;
+    if (sizeof(T) == 8) {
+      L = reinterpret_cast<const double*>(Lt)[j];
+    } else {
+      const double w = W[j];
+      L = (w == -kInf) ? -kInf : fma(w, inv_eps, logw[j]);
+    }
     double v = (mx == -kInf) ? -kInf : L - mx;
     if (sizeof(T) == 4) v *= (double)kLog2e;
     Lt[j] = (T)v;
+    if (Lt32) Lt32[j] = (float)v;
   }
   if (threadIdx.x == 0) *Lmax = mx;
 }
@@ -135,6 +147,199 @@ __global__ void __launch_bounds__(WARPS * 32)
     }
   }
   if (epi.err) block_add2<WARPS * 32>(num, den, epi.err);
+}
+
+// FP64 rows of a dense cost with an FP32 prefilter.  GB300's FP64 pipe
+// issues 2 operations per clock per SM against 128 for FP32, and at small eps
+// most terms of a row underflow (e^a = 0 in FP64 for a < -745.2).  The max
+// sweep and a conservative skip test therefore run on FP32 copies of C and of
+// the shifted input line; only the terms that can reach the FP64 range are
+// evaluated in FP64, shifted by the FP32 maximum (converted exactly), so the
+// result is the plain FP64 row sum up to FP64 rounding.
+constexpr int kPfStageMax = 12288;  // inputs staged in shared memory (48 KB)
+constexpr int kPfPrepBlocks = 32;   // blocks of the prefilter's line preparation
+
+// Line preparation of the FP64 prefilter, spread over up to kPfPrepBlocks
+// blocks: L_j = W_j/eps + log w_j in FP64 (L64, for the surviving terms) and
+// as a float-float pair (Lff), and per-block maxima.  The last block to
+// finish (an atomic counter, no waiting) merges the maxima into *Lmax and
+// writes the shifted FP32 line Lt32_j = L_j - max L from the pairs with FP32
+// operations only (the FP64 pipe of one SM would take longer).
+__global__ void __launch_bounds__(256) prepare_L_pf(const double* __restrict__ W, const double* __restrict__ logw,
+                                                   int nin, double inv_eps, double* __restrict__ L64,
+                                                   float2* __restrict__ Lff, double* __restrict__ Lmax,
+                                                   float* __restrict__ Lt32, float* __restrict__ lerr,
+                                                   double* __restrict__ part, unsigned* __restrict__ count) {
+  __shared__ double red[8];
+  __shared__ bool last;
+  double mx = -kInf;
+  for (int j = blockIdx.x * 256 + threadIdx.x; j < nin; j += gridDim.x * 256) {
+    const double w = W[j];
+    const double L = (w == -kInf) ? -kInf : fma(w, inv_eps, logw[j]);
+    L64[j] = L;
+    const float hi = (float)L;
+    Lff[j] = make_float2(hi, (L == -kInf) ? 0.0f : (float)(L - (double)hi));
+    mx = fmax(mx, L);
+  }
+  mx = wmax(mx);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 1; k < 8; ++k) mx = fmax(mx, red[k]);
+    part[blockIdx.x] = mx;
+    __threadfence();
+    last = atomicAdd(count, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (threadIdx.x < 32) {  // gridDim.x <= 32 partials, one per lane
+    mx = (threadIdx.x < gridDim.x) ? __ldcg(&part[threadIdx.x]) : -kInf;
+    mx = wmax(mx);
+    if (threadIdx.x == 0) red[0] = mx;
+  }
+  __syncthreads();
+  mx = red[0];
+  const float mhi = (float)mx;
+  const float mlo = (mx == -kInf) ? 0.0f : (float)(mx - (double)mhi);
+#pragma unroll 4
+  for (int j = threadIdx.x; j < nin; j += 256) {
+    const float2 l = __ldcg(&Lff[j]);
+    Lt32[j] = (mx == -kInf || l.x == -INFINITY) ? -INFINITY : (l.x - mhi) + (l.y - mlo);
+  }
+  if (threadIdx.x == 0) {
+    *Lmax = mx;
+    // the pairs carry |L| 2^-47 of representation error besides the FP32 rounding
+    *lerr = (mx == -kInf) ? 4.0f : fmaf(fabsf(mhi), 0x1p-44f, 4.0f);
+    *count = 0u;
+  }
+}
+
+// FP64 rows of a dense cost with an FP32 prefilter.  GB300's FP64 pipe
+// issues 2 operations per clock per SM against 128 for FP32, and at small eps
+// most terms of a row underflow (e^a = 0 in FP64 for a < -745.2).  The max
+// sweep and a conservative skip test therefore run on FP32 copies of C and of
+// the shifted input line; the columns that can reach the FP64 range are
+// collected per warp (ballot, shared-memory list) and evaluated in FP64 32 at
+// a time with every lane active, shifted by the FP32 maximum (converted
+// exactly), so the result is the plain FP64 row sum up to FP64 rounding.  WPR
+// warps share a row (RPC rows per CTA) so that enough loads are in flight.
+template <int WPR, int RPC, bool kRows>
+__global__ void __launch_bounds__(WPR * RPC * 32)
+    rows_lse_f64_pf(const double* __restrict__ C, const float* __restrict__ C32, int nrows, int nin,
+                    const double* __restrict__ L64, const float* __restrict__ Lt32,
+                    const double* __restrict__ Lmax_p, const float* __restrict__ lerr_p, double k2,
+                    Epilogue epi) {
+  constexpr int NT = WPR * RPC * 32, NW = WPR * RPC;
+  // shared memory: the shifted FP32 input line (when it fits) and, with kRows,
+  // the CTA's RPC rows of C32, copied in with cp.async so that every byte is
+  // in flight at once and both sweeps read shared memory
+  extern __shared__ float sL[];
+  __shared__ float sm_m[RPC][WPR];
+  __shared__ double sm_s[RPC][WPR];
+  __shared__ int slist[NW][64];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rloc = warp / WPR, part = warp % WPR;
+  const int i = blockIdx.x * RPC + rloc;
+  double num = 0.0, den = 0.0;
+  const double Lmax = *Lmax_p;
+  const float lerr = *lerr_p;
+  const bool staged = kRows || nin <= kPfStageMax;
+  if (kRows) {
+    // nin % 4 == 0 and 16-byte aligned C32: 16-byte copies of the line and the rows
+    const int q = nin >> 2;
+    const int nr = min(RPC, nrows - (int)blockIdx.x * RPC);
+    for (int t = threadIdx.x; t < q * (1 + nr); t += NT) {
+      const int r = t / q, c4 = t - r * q;
+      const float* src = (r == 0) ? Lt32 + 4 * c4 : C32 + ((int64_t)(blockIdx.x * RPC + r - 1) * nin + 4 * c4);
+      const unsigned dst = (unsigned)__cvta_generic_to_shared(sL + (size_t)r * nin + 4 * c4);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+  } else if (staged) {
+    for (int j = threadIdx.x; j < nin; j += NT) sL[j] = Lt32[j];
+  }
+  __syncthreads();
+  const float* L = staged ? sL : Lt32;
+  const bool live = i < nrows && Lmax != -kInf;  // warp-uniform
+  const int64_t rowbase = (int64_t)(live ? i : 0) * nin;
+  const float* crow = kRows ? sL + (size_t)(1 + rloc) * nin : C32 + rowbase;
+  const float k2f = (float)k2;
+  float m = -INFINITY;
+  if (live) {
+#pragma unroll 4
+    for (int j = part * 32 + lane; j < nin; j += WPR * 32) m = fmaxf(m, fmaf(-k2f, crow[j], L[j]));
+  }
+  m = wmax(m);
+  if (lane == 0) sm_m[rloc][part] = m;
+  __syncthreads();
+  m = sm_m[rloc][0];
+#pragma unroll
+  for (int w = 1; w < WPR; ++w) m = fmaxf(m, sm_m[rloc][w]);
+  double s = 0.0;
+  if (live && m != -INFINITY) {
+    const double ms = (double)m;
+    int* lst = slist[warp];
+    int cnt = 0;  // warp-uniform
+    auto term = [&](int j) {
+      const double a64 = fma(-k2, C[rowbase + j], L64[j] - Lmax) - ms;
+      return a64 > -746.0 ? exp(a64) : 0.0;
+    };
+    // warp-uniform sweep (the ballots need every lane)
+    for (int j0 = part * 32; j0 < nin; j0 += WPR * 32) {
+      const int j = j0 + lane;
+      bool keep = false;
+      if (j < nin) {
+        const float c = crow[j], l = L[j];
+        const float t = fmaf(-k2f, c, l);
+        const float a = t - m;
+        // |t - t_FP64| and the error of m are below (k2 c + |l| + |t| + |a|) 2^-22
+        // (the roundings of k2, c, l, the fma and the subtraction) plus lerr
+        const float tol = fmaf(fabsf(t) + fabsf(a) + fmaf(k2f, c, fabsf(l)), 0x1p-22f, lerr);
+        keep = a > -746.0f - tol;
+      }
+      const unsigned mask = __ballot_sync(0xffffffffu, keep);
+      if (mask) {
+        if (keep) lst[cnt + __popc(mask & ((1u << lane) - 1u))] = j;
+        cnt += __popc(mask);
+        if (cnt >= 32) {
+          __syncwarp();
+          s += term(lst[lane]);
+          const int rest = cnt - 32;
+          const int carry = (lane < rest) ? lst[32 + lane] : 0;
+          __syncwarp();
+          if (lane < rest) lst[lane] = carry;
+          __syncwarp();
+          cnt = rest;
+        }
+      }
+    }
+    __syncwarp();
+    if (lane < cnt) s += term(lst[lane]);
+  }
+  if (__any_sync(0xffffffffu, s != 0.0)) s = wsum(s);  // most warps of a row hold no term
+  if (lane == 0) sm_s[rloc][part] = s;
+  __syncthreads();
+  // the CTA's row epilogues (FP64 log and Table 1 row) side by side in the
+  // lanes of warp 0: one warp instruction stream for RPC rows instead of one
+  // per row on the narrow FP64 pipe
+  if (warp == 0 && lane < RPC) {
+    const int r = blockIdx.x * RPC + lane;
+    if (r < nrows) {
+      double z = -kInf;
+      float mr = sm_m[lane][0];
+      double sr = sm_s[lane][0];
+#pragma unroll
+      for (int w = 1; w < WPR; ++w) {
+        mr = fmaxf(mr, sm_m[lane][w]);
+        sr += sm_s[lane][w];
+      }
+      if (Lmax != -kInf && mr != -INFINITY) z = Lmax + (double)mr + log(sr);
+      apply_epilogue(epi, 0, r, z, num, den);
+    }
+  }
+  if (epi.err) block_add2<NT>(num, den, epi.err);
 }
 
 // FP32 path: L_j = W_j/eps + log w_j in float-float; Lt_j = (L_j - max) log2(e)
@@ -260,10 +465,16 @@ __global__ void __launch_bounds__(WARPS * 32)
 
 }  // namespace
 
+size_t rows_pf_scratch_bytes(int64_t nin) {
+  return 768 + 2 * (((size_t)nin * 8 + 255) & ~(size_t)255) + (((size_t)nin * 4 + 255) & ~(size_t)255);
+}
+
 cudaError_t launch_rows(int prec, const RowsGeom& g, int nrows, int nin, const double* W,
                         const double* logw, double eps, void* scratch_L, const Epilogue& epi,
                         cudaStream_t s, float* zprev, int use_prev, void* part) {
-  // scratch_L: nin elements of the precision's type followed by one double (Lmax).
+  // scratch_L: nin elements of the precision's type followed by one double
+  // (Lmax); the FP64 dense prefilter adds nin floats, block maxima and a
+  // counter (rows_pf_scratch_bytes).
   constexpr int WARPS = 8;
   const int grid = (nrows + WARPS - 1) / WARPS;
   if (g.kind == UOT_GEOM_POINTS && (g.d < 1 || g.d > 8)) return cudaErrorInvalidValue;
@@ -292,9 +503,41 @@ cudaError_t launch_rows(int prec, const RowsGeom& g, int nrows, int nin, const d
   } else {
     double* Lt = (double*)scratch_L;
     double* Lmax = (double*)((char*)scratch_L + (((size_t)nin * 8 + 255) & ~(size_t)255));
+    const double* C = (const double*)g.C;
+    // dense rows with an FP32 copy of C: FP32 prefilter (k2 = 1/eps must stay an FP32 number)
+    if (g.kind == UOT_GEOM_DENSE && g.C32 && 1.0 / eps < 1e30) {
+      // scratch: counter (zeroed by the caller) | block maxima [kPfPrepBlocks] | Lmax, lerr |
+      // L64 [nin] | Lff [nin] | Lt32 [nin]; the counter's place does not depend on nin
+      char* base = (char*)scratch_L;
+      const size_t r8 = ((size_t)nin * 8 + 255) & ~(size_t)255;
+      double* Lmx = (double*)(base + 512);
+      float* lerr = (float*)(base + 512 + 16);
+      double* L64 = (double*)(base + 768);
+      float2* Lff = (float2*)(base + 768 + r8);
+      float* Lt32 = (float*)(base + 768 + 2 * r8);
+      const int pblk = std::max(1, std::min(kPfPrepBlocks, (nin + 255) / 256));
+      prepare_L_pf<<<pblk, 256, 0, s>>>(W, logw, nin, 1.0 / eps, L64, Lff, Lmx, Lt32, lerr, (double*)(base + 256),
+                                        (unsigned*)base);
+      prof_mark_begin(PROF_ROWS, s);
+      constexpr int WPR = 4, RPC = 2;
+      const int grid2 = (nrows + RPC - 1) / RPC;
+      // rows and line in shared memory: 16-byte rows (nin % 4 == 0) within 48 KB
+      const bool rows_smem = (nin % 4 == 0) && (size_t)(1 + RPC) * nin * 4 <= 48 * 1024 &&
+                             ((uintptr_t)g.C32 % 16 == 0) && ((uintptr_t)Lt32 % 16 == 0);
+      if (rows_smem) {
+        rows_lse_f64_pf<WPR, RPC, true><<<grid2, WPR * RPC * 32, (size_t)(1 + RPC) * nin * 4, s>>>(
+            C, g.C32, nrows, nin, L64, Lt32, Lmx, lerr, 1.0 / eps, epi);
+      } else {
+        const size_t smem = nin <= kPfStageMax ? (size_t)nin * 4 : 0;
+        if (smem > 48 * 1024) return cudaErrorInvalidValue;
+        rows_lse_f64_pf<WPR, RPC, false><<<grid2, WPR * RPC * 32, smem, s>>>(
+            C, g.C32, nrows, nin, L64, Lt32, Lmx, lerr, 1.0 / eps, epi);
+      }
+      prof_mark_end(PROF_ROWS, s);
+      return cudaGetLastError();
+    }
     prepare_L<double, 1024><<<1, 1024, 0, s>>>(W, logw, nin, eps, Lt, Lmax);
     prof_mark_begin(PROF_ROWS, s);
-    const double* C = (const double*)g.C;
     const double* x = (const double*)g.x;
     const double* y = (const double*)g.y;
     if (g.kind == UOT_GEOM_DENSE || g.d <= 4)

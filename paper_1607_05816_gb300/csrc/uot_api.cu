@@ -138,6 +138,12 @@ __global__ void k_from_f64(const double* __restrict__ src, int64_t n, T* __restr
     dst[i] = (T)src[i];
 }
 
+// *flag = 1 if a and b differ anywhere (bit patterns).
+__global__ void k_differs(const double* __restrict__ a, const double* __restrict__ b, int64_t n, int* flag) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    if (__double_as_longlong(a[i]) != __double_as_longlong(b[i])) *flag = 1;
+}
+
 __global__ void k_fill(double* __restrict__ dst, int64_t n, double v) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -712,6 +718,7 @@ struct Gibbs {
   int prec;
   size_t esz;
   const void* CT = nullptr;     // dense: C^T in the precision's type
+  float* C32[2] = {nullptr, nullptr};  // dense FP64: FP32 copies of C, C^T (row prefilter)
   double* pass[2] = {nullptr, nullptr};  // grid intermediates
   // FP32 grid passes: result of each (direction, pass) from the previous call,
   // reused as the log-sum-exp shift while eps is unchanged (see k_grid.cu)
@@ -733,6 +740,10 @@ struct Gibbs {
     nbatch = batch;
     esz = (prec == UOT_F64) ? 8 : 4;
     if (g.kind == UOT_GEOM_DENSE) sc.reserve<char>((size_t)g.n * g.m * esz);
+    if (g.kind == UOT_GEOM_DENSE && prec == UOT_F64) {
+      for (int k = 0; k < 2; ++k) sc.reserve<float>((size_t)g.n * g.m);
+      sc.reserve<int>(1);
+    }
     if (g.kind == UOT_GEOM_GRID) {
       inter = 1;
       for (int k = 0; k < g.ndim; ++k) inter *= (g.shape_x[k] > g.shape_y[k] ? g.shape_x[k] : g.shape_y[k]);
@@ -745,7 +756,7 @@ struct Gibbs {
       if (prec == UOT_MIXED || prec == UOT_F32) sc.reserve<int>(1);
     } else {
       const int64_t mx = (g.n > g.m ? g.n : g.m);
-      sc.reserve<char>((size_t)mx * 8 + 512);
+      sc.reserve<char>(lscratch_bytes(mx));
       if (points_fast()) {
         sc.reserve<float2>(part_elems());
         if (speculate) {
@@ -756,6 +767,11 @@ struct Gibbs {
     }
   }
   bool points_fast() const { return g.kind == UOT_GEOM_POINTS && prec != UOT_F64 && g.d <= 3; }
+  // shifted input line (+ Lmax) and, for FP64 dense rows, its FP32 copy
+  size_t lscratch_bytes(int64_t mx) const {
+    if (g.kind == UOT_GEOM_DENSE && prec == UOT_F64) return std::max((size_t)mx * 8 + 512, rows_pf_scratch_bytes(mx));
+    return (size_t)mx * 8 + 512;
+  }
   size_t part_elems() const {
     return std::max((size_t)points_nchunks(g.m, g.n) * g.n, (size_t)points_nchunks(g.n, g.m) * g.m);
   }
@@ -770,6 +786,35 @@ struct Gibbs {
       else
         k_transpose<float><<<grid, blk, 0, s>>>((const float*)g.C, g.n, g.m, (float*)ct);
       CT = ct;
+      if (prec == UOT_F64) {
+        const int64_t nm = (int64_t)g.n * g.m;
+        C32[0] = sc.take<float>((size_t)nm);
+        C32[1] = sc.take<float>((size_t)nm);
+        int* dflag = sc.take<int>(1);
+        if (!C32[0] || !C32[1] || !dflag) return cudaErrorInvalidValue;
+        // a symmetric cost (X = Y, e.g. the WF flows) serves both directions from
+        // one copy: half the working set, which then stays in L2
+        bool sym = false;
+        if (g.n == g.m) {
+          cudaError_t e = cudaMemsetAsync(dflag, 0, sizeof(int), s);
+          if (e != cudaSuccess) return e;
+          count_launches(1);
+          k_differs<<<nblocks(nm), kNT, 0, s>>>((const double*)g.C, (const double*)CT, nm, dflag);
+          int h = 1;
+          if ((e = cudaMemcpyAsync(&h, dflag, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+          if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+          sym = (h == 0);
+        }
+        count_launches(1);
+        k_from_f64<float><<<nblocks(nm), kNT, 0, s>>>((const double*)g.C, nm, C32[0]);
+        if (sym) {
+          CT = g.C;
+          C32[1] = C32[0];
+        } else {
+          count_launches(1);
+          k_from_f64<float><<<nblocks(nm), kNT, 0, s>>>((const double*)CT, nm, C32[1]);
+        }
+      }
     }
     if (g.kind == UOT_GEOM_GRID) {
       if (g.ndim > 1) {
@@ -811,7 +856,13 @@ struct Gibbs {
       }
     } else {
       const int64_t mx = (g.n > g.m ? g.n : g.m);
-      Lscratch = sc.take<char>((size_t)mx * 8 + 512);
+      Lscratch = sc.take<char>(lscratch_bytes(mx));
+      if (!Lscratch) return cudaErrorInvalidValue;
+      if (g.kind == UOT_GEOM_DENSE && prec == UOT_F64) {
+        // the prefilter's block counter (first bytes of the scratch)
+        cudaError_t e0 = cudaMemsetAsync(Lscratch, 0, 256, s);
+        if (e0 != cudaSuccess) return e0;
+      }
       if (points_fast()) {
         part = sc.take<float2>(part_elems());
         if (speculate) {
@@ -901,6 +952,7 @@ struct Gibbs {
     rg.kind = g.kind;
     rg.d = g.d;
     rg.C = (dir == 0) ? g.C : CT;
+    rg.C32 = C32[dir];
     rg.x = (dir == 0) ? g.x : g.y;
     rg.y = (dir == 0) ? g.y : g.x;
     const int nrows = (dir == 0) ? g.n : g.m;
@@ -2099,9 +2151,13 @@ __global__ void __launch_bounds__(kNT) k_growth_prox(const double* __restrict__ 
       for (int k = 0; k < a.S; ++k) mx = fmax(mx, Tz[k * a.m + j]);
       double v = a.neg_lam_logc;
       if (mx != -kInf) {
-        double s = 0.0;
-        for (int k = 0; k < a.S; ++k) s += exp(Tz[k * a.m + j] - mx);
-        v = fmin(v, -a.klin * (a.eps * (mx + log(s))));
+        double L = mx;  // one species: the log-sum-exp is the value itself
+        if (a.S > 1) {
+          double s = 0.0;
+          for (int k = 0; k < a.S; ++k) s += exp(Tz[k * a.m + j] - mx);
+          L += log(s);
+        }
+        v = fmin(v, -a.klin * (a.eps * L));
       }
       for (int k = 0; k < a.S; ++k) V[k * a.m + j] = v;
     } else {
@@ -2110,14 +2166,17 @@ __global__ void __launch_bounds__(kNT) k_growth_prox(const double* __restrict__ 
       for (int k = 0; k < a.S; ++k) mx = ff_max(mx, ffl(T2[k * a.m + j]));
       ff v = ffl(a.neg_lam_logc_ff);
       if (mx.hi != -INFINITY) {
-        float s = 0.0f;
-        for (int k = 0; k < a.S; ++k) {
-          const ff t = ffl(T2[k * a.m + j]);
-          if (t.hi == -INFINITY) continue;
-          const ff dlt = ff_sub(t, mx);
-          s += expf(dlt.hi + dlt.lo);
+        ff L = mx;  // one species: the log-sum-exp is the value itself
+        if (a.S > 1) {
+          float s = 0.0f;
+          for (int k = 0; k < a.S; ++k) {
+            const ff t = ffl(T2[k * a.m + j]);
+            if (t.hi == -INFINITY) continue;
+            const ff dlt = ff_sub(t, mx);
+            s += expf(dlt.hi + dlt.lo);
+          }
+          L = ff_add_f(mx, logf(s));
         }
-        const ff L = ff_add_f(mx, logf(s));
         v = ff_min(v, ff_neg(ff_mul(ffl(a.klin_ff), ff_mul(ffl(a.eps_ff), L))));
       }
       float2* V2 = reinterpret_cast<float2*>(V);

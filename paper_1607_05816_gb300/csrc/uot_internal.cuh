@@ -495,6 +495,7 @@ struct RowsGeom {
   const void* x;     // points [nrows*d]
   const void* y;     // points [nin*d]
   int d;
+  const float* C32;  // dense FP64: FP32 copy of C for the row kernel's prefilter (NULL: none)
 };
 // FP32 point clouds with d <= 3 and a `part` buffer use the chunked kernels of
 // k_points.cu (zprev: previous results used as log-sum-exp shifts).
@@ -502,6 +503,9 @@ cudaError_t launch_rows(int prec, const RowsGeom& g, int nrows, int nin, const d
                         const double* logw, double eps, void* scratch_L, const Epilogue& epi,
                         cudaStream_t s, float* zprev = nullptr, int use_prev = 0,
                         void* part = nullptr);
+// Scratch of launch_rows for FP64 dense rows with the FP32 prefilter; its
+// first 4 bytes hold a counter that must be zero before the first launch.
+size_t rows_pf_scratch_bytes(int64_t nin);
 int points_nchunks(int nin, int nout);
 cudaError_t launch_points(const float* x, const float* y, int d, int nout, int nin,
                           const double* W, const double* logw, double eps, float* bmax,
