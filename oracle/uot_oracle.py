@@ -850,3 +850,65 @@ def wf_flow_log(geom: Geometry, dx, P0, tau: float, alpha: float, lam: float, ep
         logP = growth_next_log_density(logr2, c)
         traj.append(np.exp(logP))
     return dict(P=np.stack(traj), U=U, V=V, T=T)
+
+
+# ----------------------------------------------------------------------------
+# colour transfer by barycentric projection (Sec. 5.1, "Color transfer")
+# ----------------------------------------------------------------------------
+
+
+def bin_index(pts, shape) -> np.ndarray:
+    """Row-major bin of each point of [0, 1]^d on a regular grid of `shape`
+    bins: bin k of axis a covers [k/n_a, (k+1)/n_a), points outside the cube
+    (and 1 itself) go to the nearest bin.  The floor is taken on the FP32
+    product x * n_a, the precision the library decides it in."""
+    P = np.asarray(pts, dtype=np.float32).reshape(-1, len(shape))
+    idx = np.zeros(P.shape[0], dtype=np.int64)
+    for a, n in enumerate(shape):
+        with np.errstate(invalid="ignore"):
+            k = np.floor(P[:, a] * np.float32(n))
+        k = np.where(np.isnan(k), 0, k)
+        k = np.clip(k, 0, n - 1).astype(np.int64)
+        idx = idx * n + k
+    return idx
+
+
+def color_histogram(pts, shape) -> np.ndarray:
+    """Colour histogram of an image as the pushforward of the (normalised)
+    pixel measure: the fraction of pixels in each bin, i.e. the density w.r.t.
+    the reference measure giving unit mass to every bin (Sec. 5.1)."""
+    idx = bin_index(pts, shape)
+    counts = np.zeros(int(np.prod(shape)), dtype=np.int64)
+    np.add.at(counts, idx, 1)
+    return counts / max(1, idx.size)
+
+
+def barycentric_projection(geom: Geometry, dx, dy, U, V, eps) -> np.ndarray:
+    """Approximate transport map by barycentric projection (Sec. 5.1):
+    T_i = sum_j R_ij dy_j y_j / sum_j R_ij dy_j with R the plan of (U, V)
+    (Theorem 3.2); rows of zero plan mass keep their own point x_i."""
+    R = np.exp(log_plan(geom, U, V, eps))
+    if geom.kind == "grid":
+        X, Y = grid_points(geom.xs), grid_points(geom.ys)
+    elif geom.kind == "points":
+        X, Y = np.asarray(geom.x, dtype=np.float64), np.asarray(geom.y, dtype=np.float64)
+    else:
+        raise ValueError("the barycentric projection needs point coordinates")
+    X = X.reshape(X.shape[0], -1)
+    Y = Y.reshape(Y.shape[0], -1)
+    w = np.ravel(np.asarray(dy, dtype=np.float64))
+    num = R @ (w[:, None] * Y)
+    den = R @ w
+    with np.errstate(invalid="ignore", divide="ignore"):
+        T = num / den[:, None]
+    return np.where(den[:, None] > 0, T, X)
+
+
+def apply_bin_map(pts, shape, T) -> np.ndarray:
+    """The modified image T o g_X: every pixel takes the value of T at its bin."""
+    return np.asarray(T)[bin_index(pts, shape)]
+
+
+def grid_axes(shape):
+    """Bin centres (k + 1/2)/n of each axis of the colour grid."""
+    return [(np.arange(n, dtype=np.float64) + 0.5) / n for n in shape]

@@ -891,3 +891,78 @@ def test_wf_step_matches_brute_force_minimisation(S, lam):
     assert np.max(np.abs(mub - muo)) < 2e-4
     assert np.max(np.abs(Rb - Ro)) < 2e-3 * np.max(Ro)
     assert np.all(np.sum(muo, axis=0) <= 1.0 + 1e-12)
+
+
+# --------------------------------------------------------------------------
+# colour transfer (Sec. 5.1): histogram, barycentric projection, bin map
+# --------------------------------------------------------------------------
+
+def test_bin_index_edges():
+    """Bin k of an axis covers [k/n, (k+1)/n): hand-computed bins, including
+    the edges, 1 itself and points outside the cube (clamped)."""
+    shape = (4, 2)
+    pts = np.array([[0.0, 0.0], [0.25, 0.5], [0.2499, 0.4999], [1.0, 1.0], [0.99, 0.01],
+                    [-0.3, 2.0], [0.5, 0.75]])
+    want = [0 * 2 + 0, 1 * 2 + 1, 0 * 2 + 0, 3 * 2 + 1, 3 * 2 + 0, 0 * 2 + 1, 2 * 2 + 1]
+    assert O.bin_index(pts, shape).tolist() == want
+
+
+def test_color_histogram_mass_and_counts():
+    g = np.random.default_rng(3)
+    pts = g.uniform(0, 1, size=(1000, 3))
+    shape = (8, 4, 4)
+    p = O.color_histogram(pts, shape)
+    assert abs(p.sum() - 1.0) < 1e-15
+    # brute force: count the points inside each bin's box
+    i0, i1, i2 = 5, 2, 3
+    box = ((pts[:, 0] >= i0 / 8) & (pts[:, 0] < (i0 + 1) / 8) & (pts[:, 1] >= i1 / 4) & (pts[:, 1] < (i1 + 1) / 4)
+           & (pts[:, 2] >= i2 / 4) & (pts[:, 2] < (i2 + 1) / 4))
+    assert p[(i0 * 4 + i1) * 4 + i2] == box.sum() / 1000
+
+
+def test_barycentric_projection_1d_monotone_rearrangement():
+    """Balanced 1-D OT with equal uniform weights is the monotone
+    rearrangement (textbook): as eps -> 0 the barycentric projection sends the
+    k-th smallest x to the k-th smallest y."""
+    g = np.random.default_rng(11)
+    n = 12
+    # spaced points: every swap of two matched targets costs 2 dx dy >> eps
+    x = (np.arange(n) + 0.5) / n + g.uniform(-0.01, 0.01, n)
+    y = ((np.arange(n) + 0.5) / n) ** 2 + g.uniform(-0.002, 0.002, n)
+    g.shuffle(x)
+    geo = O.Geometry("points", x=x[:, None], y=y[:, None])
+    w = np.full(n, 1.0 / n)
+    eps = 2e-4
+    r = O.solve_log(geo, w, w, np.ones(n), np.ones(n), O.EQ(), O.EQ(), eps, max_iter=20000, tol=1e-12)
+    T = O.barycentric_projection(geo, w, w, r["U"], r["V"], eps)[:, 0]
+    ranks = np.argsort(np.argsort(x))
+    assert np.max(np.abs(T - y[ranks])) < 2e-3
+
+
+def test_barycentric_projection_large_eps_is_the_mean():
+    """As eps -> inf the balanced entropic plan tends to the independent
+    coupling p x q, whose barycentric projection is the mean of nu for every x."""
+    geo, dx, dy, p, q = small_problem(7, 9, 4, d=2)
+    q = q / np.sum(q * dy) * np.sum(p * dx)
+    eps = 1e6
+    r = O.solve_log(geo, dx, dy, p, q, O.EQ(), O.EQ(), eps, max_iter=200)
+    T = O.barycentric_projection(geo, dx, dy, r["U"], r["V"], eps)
+    mean = (q * dy) @ geo.y / np.sum(q * dy)
+    assert np.max(np.abs(T - mean[None, :])) < 1e-5
+
+
+def test_barycentric_projection_zero_rows_keep_their_point():
+    geo, dx, dy, p, q = small_problem(6, 5, 8, d=2)
+    U = np.zeros(6)
+    U[2] = -np.inf
+    T = O.barycentric_projection(geo, dx, dy, U, np.zeros(5), 0.1)
+    assert np.array_equal(T[2], geo.x[2])
+    assert np.all((T >= geo.y.min(axis=0) - 1e-12) & (T <= geo.y.max(axis=0) + 1e-12))  # convex combinations
+
+
+def test_apply_bin_map_gathers_by_bin():
+    shape = (2, 2)
+    T = np.array([[0.1, 0.2], [0.3, 0.4], [0.5, 0.6], [0.7, 0.8]])
+    pts = np.array([[0.1, 0.1], [0.9, 0.1], [0.1, 0.9], [0.6, 0.6]])
+    out = O.apply_bin_map(pts, shape, T)
+    assert out.tolist() == [[0.1, 0.2], [0.5, 0.6], [0.3, 0.4], [0.7, 0.8]]
