@@ -372,7 +372,10 @@ def run_single(args, rank, world, local_rank):
     bary: KL barycenter of 32 blob images 128x128, lambda = 1, eps = 1e-2, 500 iterations.
     wf: WF gradient flow with growth (Sec. 5.3) on 3000 samples of [0, 1], FP64, 500
     iterations per flow step, 4 flow steps per bench step: one species tau = 0.006,
-    eps = 1e-8, or two species tau = 0.004, eps = 1e-7 (the paper's runs), alpha = 1."""
+    eps = 1e-8, or two species tau = 0.004, eps = 1e-7 (the paper's runs), alpha = 1.
+    color: colour transfer (Sec. 5.1) between two 1024x1024 synthetic images, 64x32x32 colour
+    bins, F1 = EQ, F2 = 0.03 KL, eps = 0.002, 2000 iterations (the paper's setting); one step is
+    the whole pipeline (two histograms, the 3-D grid solve, the barycentric map, the bin map)."""
     import torch
 
     from paper_1607_05816_gb300 import synth, uot
@@ -428,6 +431,23 @@ def run_single(args, rank, world, local_rank):
                "iters_per_flow_step": 500, "flow_steps_per_bench_step": nflow,
                "cost": "WF, unscaled distance (cut locus at pi/2)"}
         dtype = "f64"
+    elif wl == "color":
+        bins, iters_c = (64, 32, 32), 2000
+        prec = {"f32": uot.F32, "f64": uot.F64, "mixed": uot.F32}[args.precision]
+        ix = f(synth.color_image(1024, 1024, seed=1242 + 2 * rank))
+        iy = f(synth.color_image(1024, 1024, seed=1243 + 2 * rank))
+
+        def step():
+            out_, T_, info = uot.color_transfer(ix, iy, uot.KL(0.03), eps=0.002, iters=iters_c, bins=bins,
+                                                precision=prec, launch_mode=args.launch_mode, check_every=100)
+            return out_, T_, info
+        nb = 64 * 32 * 32
+        # separable passes per direction: axis 0 (1024 lines x 64 x 64), axes 1, 2 (2048 lines x 32 x 32)
+        work_per_iter, unit_work, kernel = 2.0 * (1024 * 64 * 64 + 2 * 2048 * 32 * 32), "Gexp2/s", "grid_pass"
+        cfg = {"workload": "color-transfer-1024x1024-bins64x32x32-eq-kl0.03-eps2e-3-2000it",
+               "image": [1024, 1024], "bins": list(bins), "eps": 0.002, "iters": iters_c,
+               "F1": "EQ", "F2": "0.03 KL", "bins_total": nb}
+        dtype = {uot.F32: "f32", uot.F64: "f64"}[prec]
     else:  # bary
         b = synth.barycenter_images(32, 128, 128, seed=1237 + rank)
         prec = {"f32": uot.F32, "mixed": uot.MIXED, "f64": uot.F64}[args.precision]
@@ -486,7 +506,7 @@ def run_single(args, rank, world, local_rank):
     if unit_work == "Gexp2/s":
         line["roofline"] = alu_roofline(kernel, achieved, FP32_OPS_PER_TERM["points3" if wl == "points" else "grid"],
                                         timing)
-        if wl == "bary":
+        if wl in ("bary", "color"):
             line["grid_tiles"] = uot.autotune_table().strip().splitlines()
     elif unit_work == "Gterm/s":
         # rows_lse_f64_pf: the FP32 prefilter reads the FP32 copy of the cost once
@@ -652,7 +672,8 @@ def main():
     ap.add_argument("--max-iter", type=int, default=0)
     ap.add_argument("--no-eps-scaling", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="grid2d", choices=["grid2d", "batch", "points", "dense1d", "bary", "wf"])
+    ap.add_argument("--workload", default="grid2d",
+                    choices=["grid2d", "batch", "points", "dense1d", "bary", "wf", "color"])
     ap.add_argument("--wf-species", type=int, default=1, choices=[1, 2],
                     help="species of the wf workload (Sec. 5.3: the tumor example or its two-species extension)")
     ap.add_argument("--penalty", default="kl", choices=["kl", "tv"])
@@ -678,7 +699,7 @@ def main():
     try:
         if args.workload == "batch":
             run_batch(args, rank, world, local_rank)
-        elif args.workload in ("points", "dense1d", "bary", "wf"):
+        elif args.workload in ("points", "dense1d", "bary", "wf", "color"):
             run_single(args, rank, world, local_rank)
         else:
             run_ours(args, rank, world, local_rank)

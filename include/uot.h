@@ -490,6 +490,34 @@ uot_status uot_wf_flow(const uot_geom* g, int nspecies, const void* P0, const vo
                        void* V, uot_result* res, void* stream);
 
 /*
+ * Colour transfer (Sec. 5.1): colours are points of [0, 1]^d (the paper uses
+ * CIE-Lab rescaled to [0, 1]^3 and 64 x 32 x 32 bins), an image's colour
+ * histogram is the pushforward of its pixel measure, the plan between two
+ * histograms gives a map by barycentric projection, and the new image is
+ * T o g_X.  Binning: bin k of axis a covers [k/n_a, (k+1)/n_a), decided on the
+ * FP32 product x * n_a; points outside the cube go to the nearest bin (NaN to
+ * bin 0); bins are numbered row-major, like the potentials of a grid.
+ *
+ * uot_histogram: p [prod shape] (precision's type) = fraction of the npts points
+ *   pts [npts*d] (float, row-major) in each bin, i.e. the density w.r.t. the
+ *   reference measure with unit mass per bin (the paper's dx = 1).  1 <= d <= 8,
+ *   shape host [d], 1 <= npts < 2^32.
+ * uot_barycentric_map: T [n*dim] (precision's type, UOT_F64 or UOT_F32) with
+ *   T_i = sum_j R_ij dy_j y_j / sum_j R_ij dy_j, R_ij = exp((U_i + V_j - C_ij)/eps)
+ *   the plan, y_j the points of Y (grid points or the cloud); dim = g->ndim or g->d.
+ *   Rows of zero plan mass keep their own point x_i.  Grid and point geometries
+ *   (UOT_EUNSUPPORTED for dense costs).
+ * uot_apply_bin_map: out [npts*d] (float) = T[bin(pts_k)] for every point,
+ *   T [prod shape * d] in the precision's type.
+ */
+uot_status uot_histogram(const float* pts, long long npts, int d, const int* shape, int precision, void* p,
+                         void* stream);
+uot_status uot_barycentric_map(const uot_geom* g, const void* U, const void* V, double eps, const void* dx,
+                               const void* dy, int precision, void* T, void* stream);
+uot_status uot_apply_bin_map(const float* pts, long long npts, int d, const int* shape, const void* T,
+                             int precision, float* out, void* stream);
+
+/*
  * Learned warm start (not in the paper).  A small dilated convolutional
  * network maps (log p, log q, log eps, log lambda) on a grid to initial
  * potentials (U0, V0) that replace b = 1 of Algorithm 1; the plain iteration

@@ -2395,6 +2395,101 @@ uot_status wf_flow_impl(const uot_geom* g, int S, const void* P0, const void* dx
   return out;
 }
 
+
+// ---------------------------------------------------------------------------
+// Colour transfer (Sec. 5.1): histograms, barycentric projection, bin map
+// ---------------------------------------------------------------------------
+
+constexpr int kMaxBinDim = 8;
+struct BinGrid {
+  int d;
+  int shape[kMaxBinDim];
+};
+
+// Row-major bin of a point of [0, 1]^d: bin k of axis a covers [k/n_a, (k+1)/n_a);
+// the floor is taken on the FP32 product x * n_a, outside points are clamped
+// and NaN goes to bin 0.
+__device__ __forceinline__ int64_t bin_of(const float* __restrict__ x, const BinGrid& b) {
+  int64_t idx = 0;
+  for (int a = 0; a < b.d; ++a) {
+    const float v = floorf(__fmul_rn(x[a], (float)b.shape[a]));
+    const int k = (v != v || v < 0.0f) ? 0 : (v > (float)(b.shape[a] - 1) ? b.shape[a] - 1 : (int)v);
+    idx = idx * b.shape[a] + k;
+  }
+  return idx;
+}
+
+__global__ void k_histogram(const float* __restrict__ pts, int64_t npts, BinGrid b, unsigned* __restrict__ counts) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < npts; q += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(&counts[bin_of(pts + q * b.d, b)], 1u);
+}
+
+template <typename T>
+__global__ void k_hist_norm(const unsigned* __restrict__ counts, int64_t nb, double npts, T* __restrict__ p) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nb; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = (T)((double)counts[i] / npts);
+}
+
+struct PointsOf {
+  int kind, d;  // UOT_GEOM_GRID: axes and shape; UOT_GEOM_POINTS: row-major points
+  int shape[UOT_MAX_DIM];
+  const void* axes[UOT_MAX_DIM];
+  const void* pts;
+};
+
+template <typename T>
+__device__ __forceinline__ T coord_of(const PointsOf& P, int64_t j, int k) {
+  if (P.kind == UOT_GEOM_POINTS) return reinterpret_cast<const T*>(P.pts)[j * P.d + k];
+  int64_t r = j;
+  for (int a = P.d - 1; a > k; --a) r /= P.shape[a];
+  return reinterpret_cast<const T*>(P.axes[k])[r % P.shape[k]];
+}
+
+// F[j][0..d-1] = coordinates of point j, F[j][d] = 1.
+template <typename T>
+__global__ void k_coords1(PointsOf P, int64_t m, T* __restrict__ F) {
+  const int c = P.d + 1;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < m * c; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = q / c;
+    const int k = (int)(q - j * c);
+    F[q] = (k == P.d) ? T(1) : coord_of<T>(P, j, k);
+  }
+}
+
+// T_i = RF[i][0..d-1] / RF[i][d]; rows of zero plan mass keep their own point.
+template <typename T>
+__global__ void k_bary_divide(const T* __restrict__ RF, PointsOf X, int64_t n, T* __restrict__ Tm) {
+  const int d = X.d, c = d + 1;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n * d; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = q / d;
+    const int k = (int)(q - i * d);
+    const T den = RF[i * c + d];
+    Tm[q] = (den > T(0)) ? RF[i * c + k] / den : coord_of<T>(X, i, k);
+  }
+}
+
+template <typename T>
+__global__ void k_apply_bin_map(const float* __restrict__ pts, int64_t npts, BinGrid b, const T* __restrict__ Tm,
+                                float* __restrict__ out) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < npts; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t bin = bin_of(pts + q * b.d, b);
+    for (int c = 0; c < b.d; ++c) out[q * b.d + c] = (float)Tm[bin * b.d + c];
+  }
+}
+
+uot_status bin_grid(int d, const int* shape, BinGrid& b, int64_t& nb) {
+  if (d < 1 || d > kMaxBinDim || !shape) return UOT_EINVAL;
+  b.d = d;
+  nb = 1;
+  for (int a = 0; a < d; ++a) {
+    if (shape[a] < 1) return UOT_EINVAL;
+    b.shape[a] = shape[a];
+    nb *= shape[a];
+    if (nb > ((int64_t)1 << 31)) return UOT_EINVAL;
+  }
+  return UOT_OK;
+}
+
 }  // namespace
 
 void count_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
@@ -2537,6 +2632,104 @@ uot_status uot_wf_flow(const uot_geom* g, int nspecies, const void* P0, const vo
                        void* V, uot_result* res, void* stream) {
   clear_stale_error();
   return wf_flow_impl(g, nspecies, P0, dx, tau, alpha, lambda, o, nsteps, P, U, V, res, (cudaStream_t)stream);
+}
+
+uot_status uot_histogram(const float* pts, long long npts, int d, const int* shape, int precision, void* p,
+                         void* stream) {
+  clear_stale_error();
+  BinGrid b;
+  int64_t nb = 0;
+  uot_status st = bin_grid(d, shape, b, nb);
+  if (st != UOT_OK) return st;
+  if (!pts || !p || npts < 1 || (precision != UOT_F64 && precision != UOT_F32)) return UOT_EINVAL;
+  if (npts > 0xffffffffLL) return UOT_EINVAL;  // 32-bit counters
+  cudaStream_t s = (cudaStream_t)stream;
+  Scratch sc(s);
+  sc.reserve<unsigned>(nb);
+  UOT_CK(sc.allocate());
+  unsigned* counts = sc.take<unsigned>(nb);
+  UOT_SCRATCH_OK(sc);
+  UOT_CK(cudaMemsetAsync(counts, 0, nb * sizeof(unsigned), s));
+  count_launches(2);
+  k_histogram<<<nblocks(npts), kNT, 0, s>>>(pts, npts, b, counts);
+  if (precision == UOT_F64)
+    k_hist_norm<double><<<nblocks(nb), kNT, 0, s>>>(counts, nb, (double)npts, (double*)p);
+  else
+    k_hist_norm<float><<<nblocks(nb), kNT, 0, s>>>(counts, nb, (double)npts, (float*)p);
+  UOT_CK(cudaGetLastError());
+  return UOT_OK;
+}
+
+uot_status uot_barycentric_map(const uot_geom* g, const void* U, const void* V, double eps, const void* dx,
+                               const void* dy, int precision, void* T, void* stream) {
+  clear_stale_error();
+  uot_status st = check_geom(g);
+  if (st != UOT_OK) return st;
+  if (!U || !V || !dx || !dy || !T || !(eps > 0.0) || (precision != UOT_F64 && precision != UOT_F32))
+    return UOT_EINVAL;
+  if (g->kind == UOT_GEOM_DENSE) return UOT_EUNSUPPORTED;
+  const int d = (g->kind == UOT_GEOM_GRID) ? g->ndim : g->d;
+  if (d + 1 > 64) return UOT_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t n = g->n, m = g->m;
+  const size_t esz = precision == UOT_F64 ? 8 : 4;
+  PointsOf X, Y;
+  memset(&X, 0, sizeof(X));
+  memset(&Y, 0, sizeof(Y));
+  X.kind = Y.kind = g->kind;
+  X.d = Y.d = d;
+  if (g->kind == UOT_GEOM_GRID) {
+    for (int k = 0; k < d; ++k) {
+      X.shape[k] = g->shape_x[k];
+      X.axes[k] = g->axes_x[k];
+      Y.shape[k] = g->shape_y[k];
+      Y.axes[k] = g->axes_y[k];
+    }
+  } else {
+    X.pts = g->x;
+    Y.pts = g->y;
+  }
+  Scratch sc(s);
+  sc.reserve<char>((size_t)m * (d + 1) * esz);
+  sc.reserve<char>((size_t)n * (d + 1) * esz);
+  UOT_CK(sc.allocate());
+  char* F = sc.take<char>((size_t)m * (d + 1) * esz);
+  char* RF = sc.take<char>((size_t)n * (d + 1) * esz);
+  UOT_SCRATCH_OK(sc);
+  count_launches(1);
+  if (precision == UOT_F64)
+    k_coords1<double><<<nblocks(m * (d + 1)), kNT, 0, s>>>(Y, m, (double*)F);
+  else
+    k_coords1<float><<<nblocks(m * (d + 1)), kNT, 0, s>>>(Y, m, (float*)F);
+  UOT_CK(cudaGetLastError());
+  // R (dy y) and R dy in one pass of d + 1 columns
+  st = uot_apply_plan(g, U, V, eps, dx, dy, F, d + 1, 0, precision, RF, stream);
+  if (st != UOT_OK) return st;
+  count_launches(1);
+  if (precision == UOT_F64)
+    k_bary_divide<double><<<nblocks(n * d), kNT, 0, s>>>((const double*)RF, X, n, (double*)T);
+  else
+    k_bary_divide<float><<<nblocks(n * d), kNT, 0, s>>>((const float*)RF, X, n, (float*)T);
+  UOT_CK(cudaGetLastError());
+  return UOT_OK;
+}
+
+uot_status uot_apply_bin_map(const float* pts, long long npts, int d, const int* shape, const void* T,
+                             int precision, float* out, void* stream) {
+  clear_stale_error();
+  BinGrid b;
+  int64_t nb = 0;
+  uot_status st = bin_grid(d, shape, b, nb);
+  if (st != UOT_OK) return st;
+  if (!pts || !T || !out || npts < 1 || (precision != UOT_F64 && precision != UOT_F32)) return UOT_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  count_launches(1);
+  if (precision == UOT_F64)
+    k_apply_bin_map<double><<<nblocks(npts), kNT, 0, s>>>(pts, npts, b, (const double*)T, out);
+  else
+    k_apply_bin_map<float><<<nblocks(npts), kNT, 0, s>>>(pts, npts, b, (const float*)T, out);
+  UOT_CK(cudaGetLastError());
+  return UOT_OK;
 }
 
 uot_status uot_solve_many(const uot_geom* g, int batch, const void* p, const void* dx,

@@ -13,7 +13,9 @@ Shapes follow the paper's experiments:
   * 3-D colour-like point clouds in [0, 1]^3 (Sec. 5.1, colour transfer);
   * batches of 2-D point clouds and stacks of blob images for barycenters
     (Sec. 5.2);
-  * initial tumor densities on [0, 1] for the WF gradient flows (Sec. 5.3).
+  * initial tumor densities on [0, 1] for the WF gradient flows (Sec. 5.3);
+  * colour images in [0, 1]^3 (rescaled Lab-like coordinates) for the colour
+    transfer of Sec. 5.1.
 The reference measures are the discretised Lebesgue measure (grid) or the
 uniform empirical measure (points), both probability vectors (Sec. 4.2).
 """
@@ -193,3 +195,22 @@ def tumor_densities(n: int = 3000, species: int = 1, seed: int = 1240):
         f = g.uniform(10.0, 40.0)
         P[k] = np.where(np.abs(x - c0) < w, amp * (1.0 + 0.2 * np.sin(f * x)), 0.0)
     return x, np.full(n, 1.0 / n), P
+
+
+def color_image(H: int = 512, W: int = 512, seed: int = 1241, ncolors: int = 5):
+    """A synthetic colour image [H, W, 3] in [0, 1]^3 (float32), colours as
+    rescaled Lab-like coordinates (luminance first): a Voronoi partition of
+    the image into `ncolors` regions of random palette colours (luminance
+    0.15-0.95, chrominance 0.2-0.8), each with a smooth spatial gradient and
+    pixel noise, clipped to the cube.  The paper's photographs are not
+    available; two such images with different seeds have different palettes."""
+    g = rng(seed)
+    pal = np.stack([g.uniform(0.15, 0.95, ncolors), g.uniform(0.2, 0.8, ncolors), g.uniform(0.2, 0.8, ncolors)], 1)
+    seeds = g.uniform(0, 1, size=(ncolors, 2))
+    yy, xx = np.meshgrid((np.arange(H) + 0.5) / H, (np.arange(W) + 0.5) / W, indexing="ij")
+    d2 = (yy[..., None] - seeds[:, 0]) ** 2 + (xx[..., None] - seeds[:, 1]) ** 2
+    cell = np.argmin(d2, axis=-1)
+    grad = g.uniform(-0.15, 0.15, size=(ncolors, 3, 2))
+    img = pal[cell] + grad[cell, :, 0] * (yy - 0.5)[..., None] + grad[cell, :, 1] * (xx - 0.5)[..., None]
+    img = img + g.normal(0.0, 0.02, size=img.shape)
+    return np.clip(img, 0.0, 1.0).astype(np.float32)

@@ -16,6 +16,7 @@ import math
 import os
 from dataclasses import dataclass
 
+import numpy as np
 import torch
 
 from . import build as _build
@@ -86,6 +87,12 @@ _SIGS = {
     "uot_wf_flow": (C.c_int, [C.POINTER(CGeom), C.c_int, C.c_void_p, C.c_void_p, C.c_double, C.c_double,
                               C.c_double, C.POINTER(COpts), C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                               C.POINTER(CResult), C.c_void_p]),
+    "uot_histogram": (C.c_int, [C.c_void_p, C.c_longlong, C.c_int, C.POINTER(C.c_int), C.c_int, C.c_void_p,
+                                C.c_void_p]),
+    "uot_barycentric_map": (C.c_int, [C.POINTER(CGeom), C.c_void_p, C.c_void_p, C.c_double, C.c_void_p,
+                                      C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "uot_apply_bin_map": (C.c_int, [C.c_void_p, C.c_longlong, C.c_int, C.POINTER(C.c_int), C.c_void_p, C.c_int,
+                                    C.c_void_p, C.c_void_p]),
     "uot_gibbs_log": (C.c_int, [C.POINTER(CGeom), C.c_void_p, C.c_void_p, C.c_double, C.c_int,
                                 C.c_int, C.c_void_p, C.c_void_p]),
     "uot_gibbs_log_noalloc": (C.c_int, [C.POINTER(CGeom), C.c_void_p, C.c_void_p, C.c_double,
@@ -422,6 +429,69 @@ def wf_flow(geom: Geometry, P0, dx, tau, alpha, lam, eps, nsteps, *, precision=F
                          _ptr(V, dt, "V"), C.byref(r), _stream())
     _check(st, "uot_wf_flow")
     return P, U, V, dict(iters=r.iters, total_iters=r.total_iters, ms=r.ms, status=STATUS[st])
+
+
+def histogram(pts, shape, precision=F64, out=None):
+    """uot_histogram: fraction of the points pts [N, d] (float32, in [0, 1]^d)
+    in each bin of the regular grid `shape` (row-major), as a flat tensor."""
+    lib = load()
+    dt = _dtype(precision)
+    d = len(shape)
+    pts = pts.reshape(-1, d)
+    out = torch.empty(int(np.prod(shape)), dtype=dt, device=pts.device) if out is None else out
+    sh = (C.c_int * d)(*[int(v) for v in shape])
+    _check(lib.uot_histogram(_ptr(pts, torch.float32, "pts"), pts.shape[0], d, sh, precision,
+                             _ptr(out, dt, "p"), _stream()), "uot_histogram")
+    return out
+
+
+def barycentric_map(geom: Geometry, U, V, eps, dx, dy, precision=F64, out=None):
+    """uot_barycentric_map: T [n, dim], T_i = sum_j R_ij dy_j y_j / sum_j R_ij dy_j."""
+    lib = load()
+    dt = _dtype(precision)
+    dim = len(geom.axes_x) if geom.kind == GEOM_GRID else geom.x.shape[1]
+    out = torch.empty(geom.n, dim, dtype=dt, device=U.device) if out is None else out
+    g = geom.c(precision)
+    _check(lib.uot_barycentric_map(C.byref(g), _ptr(U, dt, "U"), _ptr(V, dt, "V"), float(eps), _ptr(dx, dt, "dx"),
+                                   _ptr(dy, dt, "dy"), precision, _ptr(out, dt, "T"), _stream()),
+           "uot_barycentric_map")
+    return out
+
+
+def apply_bin_map(pts, shape, T, precision=F64, out=None):
+    """uot_apply_bin_map: every point of pts [N, d] takes the value of T at its bin."""
+    lib = load()
+    dt = _dtype(precision)
+    d = len(shape)
+    pts = pts.reshape(-1, d)
+    out = torch.empty(pts.shape[0], d, dtype=torch.float32, device=pts.device) if out is None else out
+    sh = (C.c_int * d)(*[int(v) for v in shape])
+    _check(lib.uot_apply_bin_map(_ptr(pts, torch.float32, "pts"), pts.shape[0], d, sh, _ptr(T, dt, "T"), precision,
+                                 _ptr(out, torch.float32, "out"), _stream()), "uot_apply_bin_map")
+    return out
+
+
+def color_transfer(img_x, img_y, F2: Div, eps=0.002, iters=2000, bins=(64, 32, 32), precision=F32,
+                   launch_mode=2, check_every=100):
+    """Colour transfer of Sec. 5.1: the colours of img_y imposed on img_x
+    (both [..., 3] float32 in [0, 1]^3): histograms on `bins`, the scaling
+    iteration on the separable grid with F1 = EQ(p) and F2 w.r.t. q (unit
+    reference mass per bin), the barycentric projection T, and T o g_X.
+    Returns (new image shaped like img_x, T, info)."""
+    dt = _dtype(precision)
+    dev = img_x.device
+    px = img_x.reshape(-1, len(bins)).contiguous()
+    py = img_y.reshape(-1, len(bins)).contiguous()
+    p = histogram(px, bins, precision)
+    q = histogram(py, bins, precision)
+    axes = [((torch.arange(n, dtype=torch.float64, device=dev) + 0.5) / n).to(dt) for n in bins]
+    geo = Geometry.grid(axes, axes)
+    ones = torch.ones(p.numel(), dtype=dt, device=dev)
+    U, V, info = solve(geo, p, ones, q, ones, EQ(), F2, eps, precision=precision, max_iter=iters,
+                       check_every=check_every, launch_mode=launch_mode)
+    T = barycentric_map(geo, U, V, eps, ones, ones, precision)
+    out = apply_bin_map(px, bins, T, precision)
+    return out.reshape(img_x.shape), T, info
 
 
 def solve_many(geom: Geometry, P, dx, Q, dy, F1: Div, F2: Div, eps, *, precision=F64,
