@@ -554,10 +554,16 @@ cudaError_t launch_rows(int prec, const RowsGeom& g, int nrows, int nin, const d
 cudaError_t launch_alg1_half(const double* K, int nrows, int nin, const double* b,
                              const double* w, const double* p, DivParams F, double eps,
                              double* a, const double* wout, double* err, cudaStream_t s) {
-  constexpr int WARPS = 8;
   count_launches(1);
-  alg1_half<WARPS><<<(nrows + WARPS - 1) / WARPS, WARPS * 32, 0, s>>>(K, nrows, nin, b, w, p, F,
-                                                                      eps, a, wout, err);
+  // one row per warp; with few rows, one warp per CTA so that every SM's
+  // (narrow) FP64 pipe takes part
+  if (nrows < 8 * 152) {
+    alg1_half<1><<<nrows, 32, 0, s>>>(K, nrows, nin, b, w, p, F, eps, a, wout, err);
+  } else {
+    constexpr int WARPS = 8;
+    alg1_half<WARPS><<<(nrows + WARPS - 1) / WARPS, WARPS * 32, 0, s>>>(K, nrows, nin, b, w, p, F, eps, a, wout,
+                                                                        err);
+  }
   return cudaGetLastError();
 }
 

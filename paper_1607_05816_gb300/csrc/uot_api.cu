@@ -1610,35 +1610,7 @@ uot_status solve_impl(const uot_geom* g, int batch, const void* p, const void* d
 // kernels take part in programmatic dependent launch like the grid passes:
 // they wait for the preceding kernel before reading anything.
 
-constexpr int kMassBlocks = 304;  // 2 x 152 SMs
-
-// (max, sum) merge of two partial log-sum-exps.
-__device__ inline void lse_merge(double& mx, double& s, double m2, double s2) {
-  if (m2 == -kInf) return;
-  if (mx == -kInf) {
-    mx = m2;
-    s = s2;
-  } else if (m2 > mx) {
-    s = s * exp(mx - m2) + s2;
-    mx = m2;
-  } else {
-    s += s2 * exp(m2 - mx);
-  }
-}
-__device__ inline void lse_merge_ff(ff& mx, float& s, ff m2, float s2) {
-  if (m2.hi == -INFINITY) return;
-  if (mx.hi == -INFINITY) {
-    mx = m2;
-    s = s2;
-  } else if (ff_lt(mx, m2)) {
-    const ff d = ff_sub(mx, m2);
-    s = s * expf(d.hi + d.lo) + s2;
-    mx = m2;
-  } else {
-    const ff d = ff_sub(m2, mx);
-    s += s2 * expf(d.hi + d.lo);
-  }
-}
+constexpr int kMassBlocks = kNT;  // partials of the mass reduction: one per block, at most kNT blocks
 
 struct MassArgs {
   int64_t n;
@@ -1661,11 +1633,57 @@ __device__ __forceinline__ void pdl_begin() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// Block-wide maximum and sum (kNT threads), result broadcast to every thread.
+__device__ inline double block_max_d(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  v = sh[0];
+  for (int k = 1; k < kNT / 32; ++k) v = fmax(v, sh[k]);
+  return v;
+}
+__device__ inline double block_sum_d(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  v = sh[0];
+  for (int k = 1; k < kNT / 32; ++k) v += sh[k];
+  return v;
+}
+__device__ inline ff block_max_ff(ff v, float2* sh) {
+  for (int o = 16; o > 0; o >>= 1)
+    v = ff_max(v, ff{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)});
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = ff2(v);
+  __syncthreads();
+  v = ffl(sh[0]);
+  for (int k = 1; k < kNT / 32; ++k) v = ff_max(v, ffl(sh[k]));
+  return v;
+}
+__device__ inline float block_sum_f(float v, float2* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = make_float2(v, 0.0f);
+  __syncthreads();
+  v = sh[0].x;
+  for (int k = 1; k < kNT / 32; ++k) v += sh[k].x;
+  return v;
+}
+
+constexpr int kMassPerThread = 4;  // elements per thread of the mass reduction (grid cap permitting)
+
+// Per block: the maximum of l_i = log dx_i + U_i/eps + z_i over its
+// grid-stride share, then the sum of e^{l_i - max} (a second sweep): two
+// block reductions with one exponential per element.  The last block to
+// finish merges the partials (one per thread, at most kNT blocks) the same
+// way and applies F3's row.
 template <bool FF>
 __global__ void __launch_bounds__(kNT) k_mass_reduce(const double* __restrict__ U, const double* __restrict__ z,
                                                      const double* __restrict__ logdx, MassArgs a) {
-  __shared__ double smx[kNT / 32], ssum[kNT / 32];
-  __shared__ float2 sfx[kNT / 32];
+  __shared__ double shd[kNT / 32];
+  __shared__ float2 shf[kNT / 32];
   __shared__ bool last;
   pdl_begin();
   if (!a.update) {
@@ -1674,25 +1692,23 @@ __global__ void __launch_bounds__(kNT) k_mass_reduce(const double* __restrict__ 
     }
     return;
   }
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t i0 = (int64_t)blockIdx.x * kNT + threadIdx.x, stride = (int64_t)gridDim.x * kNT;
   if constexpr (!FF) {
-    double mx = -kInf, s = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)kNT + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * kNT) {
+    auto lval = [&](int64_t i) {
       const double u = U[i], zi = z[i];
-      if (u == -kInf || zi == -kInf) continue;
-      lse_merge(mx, s, logdx[i] + u / a.eps + zi, 1.0);
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      const double m2 = __shfl_xor_sync(0xffffffffu, mx, o), s2 = __shfl_xor_sync(0xffffffffu, s, o);
-      lse_merge(mx, s, m2, s2);
-    }
-    if (lane == 0) {
-      smx[w] = mx;
-      ssum[w] = s;
-    }
-    __syncthreads();
+      return (u == -kInf || zi == -kInf) ? -kInf : logdx[i] + u / a.eps + zi;
+    };
+    double mx = -kInf;
+    for (int64_t i = i0; i < a.n; i += stride) mx = fmax(mx, lval(i));
+    mx = block_max_d(mx, shd);
+    double s = 0.0;
+    if (mx != -kInf)
+      for (int64_t i = i0; i < a.n; i += stride) {
+        const double l = lval(i);
+        if (l != -kInf) s += exp(l - mx);
+      }
+    s = block_sum_d(s, shd);
     if (threadIdx.x == 0) {
-      for (int k = 1; k < kNT / 32; ++k) lse_merge(mx, s, smx[k], ssum[k]);
       a.part[blockIdx.x] = make_double2(mx, s);
       __threadfence();
       last = atomicAdd(a.count, 1u) == gridDim.x - 1;
@@ -1700,26 +1716,13 @@ __global__ void __launch_bounds__(kNT) k_mass_reduce(const double* __restrict__ 
     __syncthreads();
     if (!last) return;
     __threadfence();
-    mx = -kInf;
-    s = 0.0;
-    for (int k = threadIdx.x; k < (int)gridDim.x; k += kNT) {
-      const double2 v = __ldcg(&a.part[k]);
-      lse_merge(mx, s, v.x, v.y);
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      const double m2 = __shfl_xor_sync(0xffffffffu, mx, o), s2 = __shfl_xor_sync(0xffffffffu, s, o);
-      lse_merge(mx, s, m2, s2);
-    }
-    __syncthreads();
-    if (lane == 0) {
-      smx[w] = mx;
-      ssum[w] = s;
-    }
-    __syncthreads();
+    double2 v = make_double2(-kInf, 0.0);
+    if (threadIdx.x < gridDim.x) v = __ldcg(&a.part[threadIdx.x]);
+    const double M = block_max_d(v.x, shd);
+    const double S = block_sum_d((M == -kInf || v.x == -kInf) ? 0.0 : v.y * exp(v.x - M), shd);
     if (threadIdx.x == 0) {
-      for (int k = 1; k < kNT / 32; ++k) lse_merge(mx, s, smx[k], ssum[k]);
       // eps log M, then Z = prox of F3 at the total mass
-      const double SM = (mx == -kInf || s == 0.0) ? -kInf : a.eps * (mx + log(s));
+      const double SM = (M == -kInf || S == 0.0) ? -kInf : a.eps * (M + log(S));
       const double Zold = a.Z[0];
       const double Znew = prox_update(a.F3, a.logm0, SM, a.eps);
       a.Z[0] = Znew;
@@ -1734,52 +1737,44 @@ __global__ void __launch_bounds__(kNT) k_mass_reduce(const double* __restrict__ 
     const float2* z2 = reinterpret_cast<const float2*>(z);
     const float2* w2 = reinterpret_cast<const float2*>(logdx);
     const ff inv_eps = ffl(a.inv_eps_ff);
-    ff mx = ff_ninf();
-    float s = 0.0f;
-    for (int64_t i = blockIdx.x * (int64_t)kNT + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * kNT) {
+    auto lval = [&](int64_t i) {
       const ff u = ffl(U2[i]), zi = ffl(z2[i]);
-      if (u.hi == -INFINITY || zi.hi == -INFINITY) continue;
-      lse_merge_ff(mx, s, ff_add(ff_add(ffl(w2[i]), ff_mul(u, inv_eps)), zi), 1.0f);
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      const ff m2{__shfl_xor_sync(0xffffffffu, mx.hi, o), __shfl_xor_sync(0xffffffffu, mx.lo, o)};
-      lse_merge_ff(mx, s, m2, __shfl_xor_sync(0xffffffffu, s, o));
-    }
-    if (lane == 0) {
-      sfx[w] = ff2(mx);
-      ssum[w] = s;
-    }
-    __syncthreads();
+      return (u.hi == -INFINITY || zi.hi == -INFINITY) ? ff_ninf()
+                                                       : ff_add(ff_add(ffl(w2[i]), ff_mul(u, inv_eps)), zi);
+    };
+    ff mx = ff_ninf();
+    for (int64_t i = i0; i < a.n; i += stride) mx = ff_max(mx, lval(i));
+    mx = block_max_ff(mx, shf);
+    float s = 0.0f;
+    if (mx.hi != -INFINITY)
+      for (int64_t i = i0; i < a.n; i += stride) {
+        const ff l = lval(i);
+        if (l.hi == -INFINITY) continue;
+        const ff d = ff_sub(l, mx);
+        s += expf(d.hi + d.lo);
+      }
+    s = block_sum_f(s, shf);
     if (threadIdx.x == 0) {
-      for (int k = 1; k < kNT / 32; ++k) lse_merge_ff(mx, s, ffl(sfx[k]), (float)ssum[k]);
-      float4* p4 = reinterpret_cast<float4*>(a.part);
-      p4[blockIdx.x] = make_float4(mx.hi, mx.lo, s, 0.0f);
+      reinterpret_cast<float4*>(a.part)[blockIdx.x] = make_float4(mx.hi, mx.lo, s, 0.0f);
       __threadfence();
       last = atomicAdd(a.count, 1u) == gridDim.x - 1;
     }
     __syncthreads();
     if (!last) return;
     __threadfence();
-    mx = ff_ninf();
-    s = 0.0f;
-    for (int k = threadIdx.x; k < (int)gridDim.x; k += kNT) {
-      const float4 v = __ldcg(&reinterpret_cast<const float4*>(a.part)[k]);
-      lse_merge_ff(mx, s, ff{v.x, v.y}, v.z);
+    float4 v = make_float4(-INFINITY, 0.0f, 0.0f, 0.0f);
+    if (threadIdx.x < gridDim.x) v = __ldcg(&reinterpret_cast<const float4*>(a.part)[threadIdx.x]);
+    const ff vm{v.x, v.y};
+    const ff M = block_max_ff(vm, shf);
+    float t = 0.0f;
+    if (M.hi != -INFINITY && vm.hi != -INFINITY) {
+      const ff d = ff_sub(vm, M);
+      t = v.z * expf(d.hi + d.lo);
     }
-    for (int o = 16; o > 0; o >>= 1) {
-      const ff m2{__shfl_xor_sync(0xffffffffu, mx.hi, o), __shfl_xor_sync(0xffffffffu, mx.lo, o)};
-      lse_merge_ff(mx, s, m2, __shfl_xor_sync(0xffffffffu, s, o));
-    }
-    __syncthreads();
-    if (lane == 0) {
-      sfx[w] = ff2(mx);
-      ssum[w] = s;
-    }
-    __syncthreads();
+    const float S = block_sum_f(t, shf);
     if (threadIdx.x == 0) {
-      for (int k = 1; k < kNT / 32; ++k) lse_merge_ff(mx, s, ffl(sfx[k]), (float)ssum[k]);
       const ff eps = ffl(a.eps_ff);
-      const ff SM = (mx.hi == -INFINITY || s == 0.0f) ? ff_ninf() : ff_mul(eps, ff_add_f(mx, logf(s)));
+      const ff SM = (M.hi == -INFINITY || S == 0.0f) ? ff_ninf() : ff_mul(eps, ff_add_f(M, logf(S)));
       float2* Z2 = reinterpret_cast<float2*>(a.Z);
       const ff Zold = ffl(Z2[0]);
       const ff Znew = prox_update_ff(a.F3ff, ffl(a.logm0_ff), SM, eps);
@@ -1934,7 +1929,9 @@ uot_status solve_mass_impl(const uot_geom* g, const void* p, const void* dx, con
   UOT_CK(cudaMemsetAsync(count, 0, sizeof(unsigned), s));
   UOT_CK(cudaGetLastError());
 
-  const int red_blocks = (int)std::min<int64_t>(kMassBlocks, std::max<int64_t>(1, (n + kNT - 1) / kNT));
+  // one partial per block (at most kNT: the last block merges them with one thread each)
+  const int64_t per_block = (int64_t)kNT * kMassPerThread;
+  const int red_blocks = (int)std::min<int64_t>(kNT, std::max<int64_t>(1, (n + per_block - 1) / per_block));
   bool first = true;
   // programmatic dependent launch (the kernels wait for their predecessor first)
   auto pdl_launch = [&](auto kern, int grid, cudaStream_t st, auto... args) -> cudaError_t {
