@@ -622,6 +622,20 @@ def barycenter_div(geom: Geometry, alpha, P, dx, dy, F1: Div, Fh: Div, eps, *, p
                             ms=r.ms, status=STATUS[st])
 
 
+def geodesic(geom: Geometry, p0, p1, ts, dx, dy, F1: Div, Fh: Div, eps, **kw):
+    """Geodesic between two measures as weighted barycenters of the endpoints
+    (Sec. 5.2, numerical experiments): for each t, uot_barycenter_div with
+    K = 2 and weights (1 - t, t).  With the WF cost (uot_wf_cost) and KL(1) for
+    F1 and Fh this is the WF geodesic; with |x - y|^2 and EQ, the Wasserstein
+    one.  Returns eps log h for every t, [len(ts), m]."""
+    P = torch.stack([p0.reshape(-1), p1.reshape(-1)])
+    out = []
+    for t in ts:
+        logh, _, _, _ = barycenter_div(geom, [1.0 - float(t), float(t)], P, dx, dy, F1, Fh, eps, **kw)
+        out.append(logh)
+    return torch.stack(out)
+
+
 def solve_batch(sizes, divs, d, x, p, dx, y, q, dy, eps, *, max_iter=1000, tol=0.0,
                 check_every=10, eps_start=None, eps_stages=10, iters_per_stage=100, U=None, V=None):
     """uot_solve_batch (FP32): sizes = [(n_k, m_k)], divs = [(F1_k, F2_k)]; x, p, dx

@@ -399,12 +399,15 @@ def test_autotuner_records_choice_and_keeps_parity():
         assert len(times) == 8 and all(t > 0 for t in times[:7])
         times = [t if t > 0 else math.inf for t in times]  # tc3 not admitted on this grid
         chosen = lines[0].split("-> ")[1].split(";")[0]
-        best = int(np.argmin(times))
-        if times[0] <= 1.05 * times[best]:
-            best = 0  # the first tile is kept unless another one is more than 5% faster
         names = ["warps=%d outputs/lane=%d" % sh for sh in [(8, 4), (4, 4), (2, 4), (1, 4), (8, 2), (4, 2), (2, 2)]]
         names.append("tensor-core tc3")
-        assert chosen == names[best]
+        k = names.index(chosen)
+        tb = min(times)
+        tick = 0.011  # the table prints times to 0.01 us: ties at that precision may go either way
+        if k == 0:  # the first tile is kept unless another one is more than 5% faster
+            assert times[0] <= 1.05 * tb + tick
+        else:
+            assert times[k] <= tb + tick and times[0] >= 1.05 * times[k] - tick
     finally:
         U.set_autotune(prev)
 

@@ -143,3 +143,35 @@ def test_wf_flow_invalid_arguments():
         U.wf_flow(geo32, T(P0, U.F32), T(dx, U.F32), 0.1, 1.0, 1.0, 1e-2, 1, precision=U.MIXED)
     with pytest.raises(U.UotError, match="EINVAL"):
         U.wf_cost(xt, xt, 0.0)
+
+
+@pytest.mark.parametrize("prec", [U.F64, U.F32])
+@pytest.mark.parametrize("kind", ["wf", "w2"])
+def test_geodesic_as_weighted_barycenters(kind, prec):
+    """Geodesics as weighted barycenters of the endpoints (Sec. 5.2): K = 2,
+    weights (1 - t, t).  WF: the dense WF cost with the cut locus at 0.2, F1 =
+    KL(1), barycenter KL(1) (Table 2 (ii)); Wasserstein: |x - y|^2, F1 = EQ,
+    barycenter EQ (Table 2 (i)).  200 samples of [0, 1], two bumps."""
+    n = 200
+    x = (np.arange(n) + 0.5) / n
+    dx = np.full(n, 1.0 / n)
+    p0 = np.exp(-((x - 0.25) / 0.06) ** 2) + 1e-3
+    p1 = 1.6 * np.exp(-((x - 0.7) / 0.09) ** 2) + 1e-3
+    if kind == "w2":
+        p1 *= np.sum(p0 * dx) / np.sum(p1 * dx)
+        C = O.sqdist(x, x)
+        OF1, lam, bk, UF1, UFh = O.EQ(), 1.0, "eq", U.EQ(), U.EQ()
+    else:
+        C = O.wf_cost(x, x, 0.2)
+        OF1, lam, bk, UF1, UFh = O.KL(1.0), 1.0, "kl", U.KL(1.0), U.KL(1.0)
+    eps, iters = (1e-3, 60) if prec == U.F64 else (1e-2, 60)
+    rx, rdx, rp0, rp1 = rounded(prec, x, dx, p0, p1)
+    rC = rounded(prec, C)
+    geo = U.Geometry.dense(T(C, prec))
+    ts = [0.25, 0.5, 0.75]
+    got = to_np(U.geodesic(geo, T(p0, prec), T(p1, prec), ts, T(dx, prec), T(dx, prec), UF1, UFh, eps,
+                           precision=prec, max_iter=iters))
+    for k, t in enumerate(ts):
+        _, _, elogh = O.barycenter_log(O.Geometry("dense", C=rC), rdx, rdx, np.stack([rp0, rp1]),
+                                       np.array([1.0 - t, t]), OF1, lam, eps, iters, bary_kind=bk)
+        assert rel_err(got[k], elogh) <= TOL[prec]
