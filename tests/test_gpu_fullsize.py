@@ -148,3 +148,46 @@ def test_points20000_solve_reaches_tolerance():
     _, _, info = U.solve(geo, *ins, U.KL(0.1), U.KL(0.1), 1e-3, precision=U.F32, max_iter=5000, tol=1e-6,
                          check_every=20, eps_start=1e-1, eps_stages=10, iters_per_stage=100)
     assert info["status"] == "UOT_OK" and info["marg_err"] <= 1e-6, info
+
+
+@pytest.mark.parametrize("kind", ["tv", "rg"])
+def test_barycenter_tv_rg_32x128x128_iterations_match_oracle(kind):
+    """The bench's TV (lambda = 1) and RG [0.5, 2] barycenters of the 32 blob
+    images (Table 2 (iii), (iv); alpha_k = 1/32, F1 = EQ, eps = 1e-2): three
+    iterations, FP32 path vs FP64 oracle, eps log h and the V_k."""
+    b = synth.barycenter_images(32, 128, 128, seed=1237)
+    alpha = np.full(32, 1.0 / 32)
+    eps, iters = 1e-2, 3
+    geo = U.Geometry.grid([dev(a) for a in b["xs"]])
+    UF = {"tv": U.TV(1.0), "rg": U.RG(0.5, 2.0)}[kind]
+    P = torch.as_tensor(f32(b["P"]).reshape(32, -1), dtype=torch.float32, device="cuda")
+    lh, Ug, Vg, _ = U.barycenter_div(geo, alpha, P, dev(b["dx"]), dev(b["dy"]), U.EQ(), UF, eps, precision=U.F32,
+                                     max_iter=iters)
+    og = O.Geometry("grid", xs=[f32(a) for a in b["xs"]], ys=[f32(a) for a in b["ys"]])
+    Uo, Vo, lho = O.barycenter_log(og, f32(b["dx"]), f32(b["dy"]), f32(b["P"]), alpha, O.EQ(), 1.0, eps, iters,
+                                   bary_kind=kind, beta=(0.5, 2.0))
+    for got, want in ((lh, lho), (Vg, Vo.reshape(32, -1))):
+        gv = got.double().cpu().numpy().ravel()
+        wv = want.ravel()
+        assert np.max(np.abs(gv - wv)) <= 1e-5 * max(1.0, np.max(np.abs(wv)))
+
+
+def test_mass_grid256_first_iterations_match_oracle():
+    """Algorithm 4 in the bench's configuration (256 x 256 grid, KL 0.5
+    marginals, F3 = EQ with m0 = 1.5) from the cold start at eps = 1e-1:
+    five iterations, FP32 path vs FP64 oracle, U, V and Z."""
+    d, geo, og = grid_setup()
+    ins = [dev(d[k]) for k in ("p", "dx", "q", "dy")]
+    eps, iters = 1e-1, 5
+    Ug, Vg, Zg, info = U.solve_mass(geo, *ins, U.KL(0.5), U.KL(0.5), U.EQ(), 1.5, eps, precision=U.F32,
+                                    max_iter=iters)
+    r = O.solve_mass_log(og, f32(d["dx"]), f32(d["dy"]), f32(d["p"]), f32(d["q"]), O.KL(0.5), O.KL(0.5), O.EQ(),
+                         1.5, eps, max_iter=iters)
+    for got, want in ((Ug, r["U"]), (Vg, r["V"])):
+        gv = got.double().cpu().numpy().ravel()
+        wv = np.asarray(want).ravel()
+        fin = np.isfinite(wv)
+        assert np.array_equal(np.isfinite(gv), fin)
+        assert np.max(np.abs(gv[fin] - wv[fin])) <= 1e-5 * max(1.0, np.max(np.abs(wv[fin])))
+    assert abs(Zg - r["Z"]) <= 1e-5 * max(1.0, abs(r["Z"]))
+    assert r["Z"] != 0.0
