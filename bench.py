@@ -356,6 +356,12 @@ def run_ours(args, rank, world, local_rank):
         line["roofline"]["traffic"] = GRID_PASS_F32_TRAFFIC_BYTES
         line["roofline"]["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
                                               "grid_pass_f32<8, 4> launch (profiles/grid_pass_f32_grid256.md)")
+    # sustained pipe rates measured by the library's own probes (ops/clk/SM), beside
+    # the unit counts the derived peak uses
+    probe = uot.probe_pipes()
+    line["roofline"]["pipe_probe"] = dict(probe, peak_gexp_from_probe=min(
+        probe["mufu_ex2_per_clk_per_sm"], probe["ffma_per_clk_per_sm"] / FP32_OPS_PER_TERM["grid"])
+        * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e9)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_iters, args.mass_div)
     print(json.dumps(line), flush=True)

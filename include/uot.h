@@ -208,6 +208,17 @@ int uot_autotune_table(char* buf, int len);
 uot_status uot_force_batch_warps(int warps);
 
 /*
+ * uot_probe_pipes -- throughput probes (instrumentation): out (host) receives
+ * the sustained rates of the pipes the kernels are bound by, in operations per
+ * clock per SM measured with in-kernel clock64() over dependent-chain loops
+ * with 64 resident warps per SM:
+ *   out[0]: FP32 FMA lane operations, out[1]: MUFU ex2.approx.f32, out[2]: FP64
+ *   FMA lane operations.
+ * A few milliseconds of work; synchronises `stream`.
+ */
+uot_status uot_probe_pipes(double* out, void* stream);
+
+/*
  * uot_selftest_bounded_wait -- failure-detection self-test (instrumentation).
  * Runs the bounded device-side wait that guards every wait of a kernel on
  * other CTAs (the persistent solve's grid barrier) on a flag that nothing

@@ -125,6 +125,7 @@ _SIGS = {
     "uot_grid_tile_count": (C.c_int, []),
     "uot_force_batch_warps": (C.c_int, [C.c_int]),
     "uot_selftest_bounded_wait": (C.c_int, [C.c_double, C.c_void_p]),
+    "uot_probe_pipes": (C.c_int, [C.POINTER(C.c_double), C.c_void_p]),
     "uot_autotune_table": (C.c_int, [C.c_char_p, C.c_int]),
     "uot_barycenter_div": (C.c_int, [C.POINTER(CGeom), C.c_int, C.POINTER(C.c_double), C.c_void_p,
                                      C.c_void_p, C.c_void_p, C.POINTER(CDiv), C.POINTER(CDiv),
@@ -200,6 +201,15 @@ def selftest_bounded_wait(seconds: float) -> str:
     if st < 0 and STATUS.get(st) != "UOT_TIMEOUT":
         _check(st, "uot_selftest_bounded_wait")
     return STATUS[st]
+
+
+def probe_pipes() -> dict:
+    """uot_probe_pipes: sustained FP32 FMA, MUFU ex2 and FP64 FMA rates in
+    operations per clock per SM."""
+    lib = load()
+    out = (C.c_double * 3)()
+    _check(lib.uot_probe_pipes(out, _stream()), "uot_probe_pipes")
+    return {"ffma_per_clk_per_sm": out[0], "mufu_ex2_per_clk_per_sm": out[1], "dfma_per_clk_per_sm": out[2]}
 
 
 def grid_tile_count() -> int:
