@@ -149,13 +149,6 @@ __global__ void __launch_bounds__(WARPS * 32)
   if (epi.err) block_add2<WARPS * 32>(num, den, epi.err);
 }
 
-// FP64 rows of a dense cost with an FP32 prefilter.  GB300's FP64 pipe
-// issues 2 operations per clock per SM against 128 for FP32, and at small eps
-// most terms of a row underflow (e^a = 0 in FP64 for a < -745.2).  The max
-// sweep and a conservative skip test therefore run on FP32 copies of C and of
-// the shifted input line; only the terms that can reach the FP64 range are
-// evaluated in FP64, shifted by the FP32 maximum (converted exactly), so the
-// result is the plain FP64 row sum up to FP64 rounding.
 constexpr int kPfStageMax = 12288;  // inputs staged in shared memory (48 KB)
 constexpr int kPfPrepBlocks = 32;   // blocks of the prefilter's line preparation
 
@@ -222,8 +215,10 @@ __global__ void __launch_bounds__(256) prepare_L_pf(const double* __restrict__ W
 // the shifted input line; the columns that can reach the FP64 range are
 // collected per warp (ballot, shared-memory list) and evaluated in FP64 32 at
 // a time with every lane active, shifted by the FP32 maximum (converted
-// exactly), so the result is the plain FP64 row sum up to FP64 rounding.  WPR
-// warps share a row (RPC rows per CTA) so that enough loads are in flight.
+// exactly), so the result is the plain FP64 row sum up to FP64 rounding.  The
+// warps' leftover lists (< 32 each) are pooled per CTA and evaluated in full
+// batches too, and every sum is taken in a fixed order.  WPR warps share a row
+// (RPC rows per CTA) so that enough loads are in flight.
 template <int WPR, int RPC, bool kRows>
 __global__ void __launch_bounds__(WPR * RPC * 32)
     rows_lse_f64_pf(const double* __restrict__ C, const float* __restrict__ C32, int nrows, int nin,
@@ -237,7 +232,11 @@ __global__ void __launch_bounds__(WPR * RPC * 32)
   extern __shared__ float sL[];
   __shared__ float sm_m[RPC][WPR];
   __shared__ double sm_s[RPC][WPR];
+  __shared__ double rsum[RPC];
   __shared__ int slist[NW][64];
+  __shared__ int pool[NW * 32];     // leftover columns, warp by warp (so row by row)
+  __shared__ double pval[NW * 32];  // their FP64 terms
+  __shared__ int woff[NW + 1];      // exclusive prefix sum of the warps' leftover counts
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int rloc = warp / WPR, part = warp % WPR;
   const int i = blockIdx.x * RPC + rloc;
@@ -277,15 +276,19 @@ __global__ void __launch_bounds__(WPR * RPC * 32)
   m = sm_m[rloc][0];
 #pragma unroll
   for (int w = 1; w < WPR; ++w) m = fmaxf(m, sm_m[rloc][w]);
+  // FP64 term of column j of CTA row r, relative to that row's FP32 maximum
+  auto term = [&](int r, int j) {
+    const int64_t ri = (int64_t)(blockIdx.x * RPC + r);
+    float mr = sm_m[r][0];
+#pragma unroll
+    for (int w = 1; w < WPR; ++w) mr = fmaxf(mr, sm_m[r][w]);
+    const double a64 = fma(-k2, C[ri * nin + j], L64[j] - Lmax) - (double)mr;
+    return a64 > -746.0 ? exp(a64) : 0.0;
+  };
   double s = 0.0;
+  int cnt = 0;  // warp-uniform
+  int* lst = slist[warp];
   if (live && m != -INFINITY) {
-    const double ms = (double)m;
-    int* lst = slist[warp];
-    int cnt = 0;  // warp-uniform
-    auto term = [&](int j) {
-      const double a64 = fma(-k2, C[rowbase + j], L64[j] - Lmax) - ms;
-      return a64 > -746.0 ? exp(a64) : 0.0;
-    };
     // warp-uniform sweep (the ballots need every lane)
     for (int j0 = part * 32; j0 < nin; j0 += WPR * 32) {
       const int j = j0 + lane;
@@ -303,9 +306,9 @@ __global__ void __launch_bounds__(WPR * RPC * 32)
       if (mask) {
         if (keep) lst[cnt + __popc(mask & ((1u << lane) - 1u))] = j;
         cnt += __popc(mask);
-        if (cnt >= 32) {
+        if (cnt >= 32) {  // a full batch: every lane evaluates one term
           __syncwarp();
-          s += term(lst[lane]);
+          s += term(rloc, lst[lane]);
           const int rest = cnt - 32;
           const int carry = (lane < rest) ? lst[32 + lane] : 0;
           __syncwarp();
@@ -315,11 +318,43 @@ __global__ void __launch_bounds__(WPR * RPC * 32)
         }
       }
     }
-    __syncwarp();
-    if (lane < cnt) s += term(lst[lane]);
   }
-  if (__any_sync(0xffffffffu, s != 0.0)) s = wsum(s);  // most warps of a row hold no term
+  if (__any_sync(0xffffffffu, s != 0.0)) s = wsum(s);  // most warps of a row hold no full batch
   if (lane == 0) sm_s[rloc][part] = s;
+  // pool the leftovers (< 32 per warp) of the whole CTA in a fixed order (warp
+  // by warp, hence row by row), evaluate them 32 at a time, and sum each row's
+  // contiguous segment in a fixed order: the result does not depend on timing
+  if (lane == 0) woff[warp] = cnt;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int o = 0;
+    for (int w = 0; w < NW; ++w) {
+      const int c = woff[w];
+      woff[w] = o;
+      o += c;
+    }
+    woff[NW] = o;
+  }
+  __syncthreads();
+  __syncwarp();
+  if (lane < cnt) pool[woff[warp] + lane] = lst[lane];
+  __syncthreads();
+  const int np = woff[NW];
+  for (int b = warp * 32; b < np; b += NT) {
+    const int k = b + lane;
+    if (k < np) {
+      int r = 0;
+      while (r + 1 < RPC && k >= woff[(r + 1) * WPR]) ++r;
+      pval[k] = term(r, pool[k]);
+    }
+  }
+  __syncthreads();
+  if (warp < RPC) {
+    double t = 0.0;
+    for (int k = woff[warp * WPR] + lane; k < woff[(warp + 1) * WPR]; k += 32) t += pval[k];
+    t = wsum(t);
+    if (lane == 0) rsum[warp] = t;
+  }
   __syncthreads();
   // the CTA's row epilogues (FP64 log and Table 1 row) side by side in the
   // lanes of warp 0: one warp instruction stream for RPC rows instead of one
@@ -329,7 +364,7 @@ __global__ void __launch_bounds__(WPR * RPC * 32)
     if (r < nrows) {
       double z = -kInf;
       float mr = sm_m[lane][0];
-      double sr = sm_s[lane][0];
+      double sr = sm_s[lane][0] + rsum[lane];
 #pragma unroll
       for (int w = 1; w < WPR; ++w) {
         mr = fmaxf(mr, sm_m[lane][w]);
@@ -519,13 +554,20 @@ cudaError_t launch_rows(int prec, const RowsGeom& g, int nrows, int nin, const d
       prepare_L_pf<<<pblk, 256, 0, s>>>(W, logw, nin, 1.0 / eps, L64, Lff, Lmx, Lt32, lerr, (double*)(base + 256),
                                         (unsigned*)base);
       prof_mark_begin(PROF_ROWS, s);
-      constexpr int WPR = 4, RPC = 2;
+      constexpr int WPR = 4, RPC = 4;
       const int grid2 = (nrows + RPC - 1) / RPC;
-      // rows and line in shared memory: 16-byte rows (nin % 4 == 0) within 48 KB
-      const bool rows_smem = (nin % 4 == 0) && (size_t)(1 + RPC) * nin * 4 <= 48 * 1024 &&
-                             ((uintptr_t)g.C32 % 16 == 0) && ((uintptr_t)Lt32 % 16 == 0);
+      // rows and line in shared memory: 16-byte rows (nin % 4 == 0) within 96 KB (opt-in
+      // above 48 KB)
+      const size_t rows_bytes = (size_t)(1 + RPC) * nin * 4;
+      const bool rows_smem = (nin % 4 == 0) && rows_bytes <= 96 * 1024 && ((uintptr_t)g.C32 % 16 == 0) &&
+                             ((uintptr_t)Lt32 % 16 == 0);
       if (rows_smem) {
-        rows_lse_f64_pf<WPR, RPC, true><<<grid2, WPR * RPC * 32, (size_t)(1 + RPC) * nin * 4, s>>>(
+        if (rows_bytes > 48 * 1024) {  // opt-in, for the current device
+          cudaError_t e = cudaFuncSetAttribute(rows_lse_f64_pf<WPR, RPC, true>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+          if (e != cudaSuccess) return e;
+        }
+        rows_lse_f64_pf<WPR, RPC, true><<<grid2, WPR * RPC * 32, rows_bytes, s>>>(
             C, g.C32, nrows, nin, L64, Lt32, Lmx, lerr, 1.0 / eps, epi);
       } else {
         const size_t smem = nin <= kPfStageMax ? (size_t)nin * 4 : 0;
