@@ -54,9 +54,9 @@ FP64_PEAK_GFLOPS = 1250.0
 FP64_PER_CLK = 2
 # HBM copy bandwidth measured on this GPU type (MEASURED_PEAKS.json hbm_gbs)
 HBM_PEAK_GBS = 6760.6
-# dram bytes of one rows_lse_f64_pf<4, 2, 1> launch of the wf workload (ncu,
+# dram bytes of one rows_lse_f64_pf<4, 4, 1> launch of the wf workload (ncu,
 # profiles/rows_lse_f64_pf_wf3000.md); None once the kernel changes
-WF_ROWS_TRAFFIC_BYTES = 36816384
+WF_ROWS_TRAFFIC_BYTES = 36827904
 # FP32 pipe: 128 lanes per clock per SM (FADD/FMUL/FFMA; a packed f32x2
 # instruction occupies it for two lane-slots per pair).
 FP32_PER_CLK = 128
@@ -447,7 +447,7 @@ def run_single(args, rank, world, local_rank):
                                            iters=500, launch_mode=args.launch_mode)
             info["marg_err"] = float("nan")
             return U_, V_, info
-        work_per_iter, unit_work, kernel = 2.0 * S * n * n, "Gterm/s", "rows_lse_f64_pf<4, 2, 1>"
+        work_per_iter, unit_work, kernel = 2.0 * S * n * n, "Gterm/s", "rows_lse_f64_pf<4, 4, 1>"
         cfg = {"workload": f"wf-flow-{S}species-3000-eps{eps:g}-tau{tau:g}-alpha1-500it-x4steps",
                "n": n, "species": S, "eps": eps, "tau": tau, "alpha": 1.0, "lambda": 1.0,
                "iters_per_flow_step": 500, "flow_steps_per_bench_step": nflow,
