@@ -56,7 +56,7 @@ FP64_PER_CLK = 2
 HBM_PEAK_GBS = 6760.6
 # dram bytes of one rows_lse_f64_pf<4, 4, 1> launch of the wf workload (ncu,
 # profiles/rows_lse_f64_pf_wf3000.md); None once the kernel changes
-WF_ROWS_TRAFFIC_BYTES = 36827904
+WF_ROWS_TRAFFIC_BYTES = None
 # FP32 pipe: 128 lanes per clock per SM (FADD/FMUL/FFMA; a packed f32x2
 # instruction occupies it for two lane-slots per pair).
 FP32_PER_CLK = 128
@@ -543,8 +543,9 @@ def run_single(args, rank, world, local_rank):
         line["roofline"] = {"bound": "hbm", "kernel": kernel, "achieved": gbs, "peak": HBM_PEAK_GBS,
                             "unit": "GB/s", "frac": gbs / HBM_PEAK_GBS,
                             "traffic": WF_ROWS_TRAFFIC_BYTES,
-                            "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch "
-                                              "(cold cache; profiles/rows_lse_f64_pf_wf3000.md)",
+                            "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch "
+                                               "(cold cache; profiles/rows_lse_f64_pf_wf3000.md)")
+                            if WF_ROWS_TRAFFIC_BYTES is not None else None,
                             "algorithmic_bytes_per_launch": 4.0 * n * n,
                             "terms_per_s": achieved * 1e9,
                             "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy), of measured",

@@ -10,6 +10,8 @@
 //
 // Algorithm 1 (Sec. 4.2): a_i = proxdiv_F(sum_j K_ij b_j w_j, eps) on a stored
 // FP64 kernel K = exp(-C/eps), with the proxdiv column of Table 1 (u = 0).
+#include <string.h>
+
 #include <algorithm>
 
 #include "uot_internal.cuh"
@@ -149,6 +151,28 @@ __global__ void __launch_bounds__(WARPS * 32)
   if (epi.err) block_add2<WARPS * 32>(num, den, epi.err);
 }
 
+__device__ __forceinline__ void pdl_wait_prev() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_release_next() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Launch with programmatic dependent launch: the kernel may start while its
+// predecessor drains and waits for it (griddepcontrol.wait) before reading
+// anything the predecessor writes.
+template <typename Kern, typename... Args>
+cudaError_t launch_pdl(Kern kern, dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg;
+  memset(&cfg, 0, sizeof(cfg));
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 constexpr int kPfStageMax = 12288;  // inputs staged in shared memory (48 KB)
 constexpr int kPfPrepBlocks = 32;   // blocks of the prefilter's line preparation
 
@@ -165,6 +189,8 @@ __global__ void __launch_bounds__(256) prepare_L_pf(const double* __restrict__ W
                                                    double* __restrict__ part, unsigned* __restrict__ count) {
   __shared__ double red[8];
   __shared__ bool last;
+  pdl_wait_prev();  // W is the preceding kernel's output
+  pdl_release_next();
   double mx = -kInf;
   for (int j = blockIdx.x * 256 + threadIdx.x; j < nin; j += gridDim.x * 256) {
     const double w = W[j];
@@ -241,24 +267,35 @@ __global__ void __launch_bounds__(WPR * RPC * 32)
   const int rloc = warp / WPR, part = warp % WPR;
   const int i = blockIdx.x * RPC + rloc;
   double num = 0.0, den = 0.0;
-  const double Lmax = *Lmax_p;
-  const float lerr = *lerr_p;
   const bool staged = kRows || nin <= kPfStageMax;
   if (kRows) {
-    // nin % 4 == 0 and 16-byte aligned C32: 16-byte copies of the line and the rows
+    // nin % 4 == 0 and 16-byte aligned C32: 16-byte copies of the rows (the cost does
+    // not depend on the preceding kernel, so they are issued before waiting for it),
+    // then of the line
     const int q = nin >> 2;
     const int nr = min(RPC, nrows - (int)blockIdx.x * RPC);
-    for (int t = threadIdx.x; t < q * (1 + nr); t += NT) {
+    for (int t = threadIdx.x; t < q * nr; t += NT) {
       const int r = t / q, c4 = t - r * q;
-      const float* src = (r == 0) ? Lt32 + 4 * c4 : C32 + ((int64_t)(blockIdx.x * RPC + r - 1) * nin + 4 * c4);
-      const unsigned dst = (unsigned)__cvta_generic_to_shared(sL + (size_t)r * nin + 4 * c4);
+      const float* src = C32 + ((int64_t)(blockIdx.x * RPC + r) * nin + 4 * c4);
+      const unsigned dst = (unsigned)__cvta_generic_to_shared(sL + (size_t)(r + 1) * nin + 4 * c4);
       asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+    }
+    pdl_wait_prev();
+    pdl_release_next();
+    for (int c4 = threadIdx.x; c4 < q; c4 += NT) {
+      const unsigned dst = (unsigned)__cvta_generic_to_shared(sL + 4 * c4);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(Lt32 + 4 * c4) : "memory");
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
     asm volatile("cp.async.wait_group 0;" ::: "memory");
-  } else if (staged) {
-    for (int j = threadIdx.x; j < nin; j += NT) sL[j] = Lt32[j];
+  } else {
+    pdl_wait_prev();
+    pdl_release_next();
+    if (staged)
+      for (int j = threadIdx.x; j < nin; j += NT) sL[j] = Lt32[j];
   }
+  const double Lmax = *Lmax_p;
+  const float lerr = *lerr_p;
   __syncthreads();
   const float* L = staged ? sL : Lt32;
   const bool live = i < nrows && Lmax != -kInf;  // warp-uniform
@@ -551,8 +588,9 @@ cudaError_t launch_rows(int prec, const RowsGeom& g, int nrows, int nin, const d
       float2* Lff = (float2*)(base + 768 + r8);
       float* Lt32 = (float*)(base + 768 + 2 * r8);
       const int pblk = std::max(1, std::min(kPfPrepBlocks, (nin + 255) / 256));
-      prepare_L_pf<<<pblk, 256, 0, s>>>(W, logw, nin, 1.0 / eps, L64, Lff, Lmx, Lt32, lerr, (double*)(base + 256),
-                                        (unsigned*)base);
+      cudaError_t e0 = launch_pdl(prepare_L_pf, dim3(pblk), dim3(256), 0, s, W, logw, nin, 1.0 / eps, L64, Lff,
+                                  Lmx, Lt32, lerr, (double*)(base + 256), (unsigned*)base);
+      if (e0 != cudaSuccess) return e0;
       prof_mark_begin(PROF_ROWS, s);
       constexpr int WPR = 4, RPC = 4;
       const int grid2 = (nrows + RPC - 1) / RPC;
@@ -567,13 +605,25 @@ cudaError_t launch_rows(int prec, const RowsGeom& g, int nrows, int nin, const d
                                                cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
           if (e != cudaSuccess) return e;
         }
-        rows_lse_f64_pf<WPR, RPC, true><<<grid2, WPR * RPC * 32, rows_bytes, s>>>(
-            C, g.C32, nrows, nin, L64, Lt32, Lmx, lerr, 1.0 / eps, epi);
+        const float* c32 = g.C32;
+        const double* l64 = L64;
+        const float* lt32 = Lt32;
+        const double* lmx = Lmx;
+        const float* le = lerr;
+        cudaError_t e1 = launch_pdl(rows_lse_f64_pf<WPR, RPC, true>, dim3(grid2), dim3(WPR * RPC * 32), rows_bytes, s,
+                                    C, c32, nrows, nin, l64, lt32, lmx, le, 1.0 / eps, epi);
+        if (e1 != cudaSuccess) return e1;
       } else {
         const size_t smem = nin <= kPfStageMax ? (size_t)nin * 4 : 0;
         if (smem > 48 * 1024) return cudaErrorInvalidValue;
-        rows_lse_f64_pf<WPR, RPC, false><<<grid2, WPR * RPC * 32, smem, s>>>(
-            C, g.C32, nrows, nin, L64, Lt32, Lmx, lerr, 1.0 / eps, epi);
+        const float* c32 = g.C32;
+        const double* l64 = L64;
+        const float* lt32 = Lt32;
+        const double* lmx = Lmx;
+        const float* le = lerr;
+        cudaError_t e1 = launch_pdl(rows_lse_f64_pf<WPR, RPC, false>, dim3(grid2), dim3(WPR * RPC * 32), smem, s,
+                                    C, c32, nrows, nin, l64, lt32, lmx, le, 1.0 / eps, epi);
+        if (e1 != cudaSuccess) return e1;
       }
       prof_mark_end(PROF_ROWS, s);
       return cudaGetLastError();

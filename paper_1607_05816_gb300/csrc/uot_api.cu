@@ -2142,6 +2142,7 @@ struct GrowthArgs {
 template <bool FF>
 __global__ void __launch_bounds__(kNT) k_growth_prox(const double* __restrict__ Tz, double* __restrict__ V,
                                                      GrowthArgs a) {
+  pdl_begin();
   for (int64_t j = blockIdx.x * (int64_t)kNT + threadIdx.x; j < a.m; j += (int64_t)gridDim.x * kNT) {
     if constexpr (!FF) {
       double mx = -kInf;
@@ -2319,11 +2320,19 @@ uot_status wf_flow_impl(const uot_geom* g, int S, const void* P0, const void* dx
     r.bstride = n;
     if ((e = G.apply(1, U, logdx, eps, r, st)) != cudaSuccess) return e;
     count_launches(1);
-    if (ffm)
-      k_growth_prox<true><<<nblocks(n), kNT, 0, st>>>(Tz, V, gargs(eps));
-    else
-      k_growth_prox<false><<<nblocks(n), kNT, 0, st>>>(Tz, V, gargs(eps));
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3(nblocks(n));
+    cfg.blockDim = dim3(kNT);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const double* tz = Tz;
+    return ffm ? cudaLaunchKernelEx(&cfg, k_growth_prox<true>, tz, V, gargs(eps))
+               : cudaLaunchKernelEx(&cfg, k_growth_prox<false>, tz, V, gargs(eps));
   };
   const std::vector<Stage> stages = eps_schedule(*o);
   int stage_iters = 0;
