@@ -51,7 +51,6 @@ MUFU_PEAK_GEXP = SM_COUNT * MUFU_PER_CLK * SM_MAX_MHZ * 1e6 / 1e9
 # FP64 pipe (Algorithm 1 matvec): GB300 runs FP64 at 1.25 TFLOP/s nominal,
 # i.e. 2 DFMA per clock per SM.
 FP64_PEAK_GFLOPS = 1250.0
-FP64_PER_CLK = 2
 # HBM copy bandwidth measured on this GPU type (MEASURED_PEAKS.json hbm_gbs)
 HBM_PEAK_GBS = 6760.6
 # dram bytes of one rows_lse_f64_pf<4, 4, 1> launch of the wf workload (ncu,
