@@ -1600,15 +1600,16 @@ uot_status solve_impl(const uot_geom* g, int batch, const void* p, const void* d
 // ---------------------------------------------------------------------------
 // A scalar z = e^{Z/eps} multiplies the plan; both scaling updates see S + Z
 // and T + Z.  z's own update needs the mass of the current plan without z,
-// M = sum_i dx_i e^{(U_i + S_i)/eps}, over all points before any U_i changes,
-// so the a-side of an iteration is three launches:
-//   Gibbs pass with raw output z_i = S_i/eps  ->  k_mass_reduce (per-block
-//   log-sum-exp of log dx_i + U_i/eps + z_i; the last block to finish merges
-//   the partials and applies the Table 1 row of F3 with p = m0, s = M)  ->
-//   k_mass_prox (U_i = prox_F1(log p_i, S_i + Z) and the violation terms).
-// The b-side is the plain prox pass with Z added to T in its epilogue.  Both
-// kernels take part in programmatic dependent launch like the grid passes:
-// they wait for the preceding kernel before reading anything.
+// M = sum_i dx_i e^{(U_i + S_i)/eps} with S from the new b.  By Fubini M also
+// equals sum_j dy_j e^{(V_j + T_j)/eps} with T from the current a, which the
+// b-side of the previous iteration has at hand: when eps does not change,
+// k_mass_vupdate computes V and the next Z in one kernel after the raw T pass,
+// and the next a-side is the plain prox pass with Z added to S in its
+// epilogue (zshift).  At an eps change the z-update takes the direct route:
+// raw S pass -> k_mass_reduce (per-block maximum and sum of e^{l_i - max},
+// l_i = log dx_i + U_i/eps + z_i, merged by the last block, then F3's row) ->
+// k_mass_prox (U = prox_F1(S + Z) and the violation terms).  All kernels wait
+// for their predecessor first (programmatic dependent launch).
 
 constexpr int kMassBlocks = kNT;  // partials of the mass reduction: one per block, at most kNT blocks
 
@@ -1687,9 +1688,7 @@ __global__ void __launch_bounds__(kNT) k_mass_reduce(const double* __restrict__ 
   __shared__ bool last;
   pdl_begin();
   if (!a.update) {
-    if (blockIdx.x == 0 && threadIdx.x == 0 && a.check) {
-      a.acc[0] = a.acc[1] = a.acc[2] = 0.0;
-    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && a.check) a.acc[0] = a.acc[1] = 0.0;
     return;
   }
   const int64_t i0 = (int64_t)blockIdx.x * kNT + threadIdx.x, stride = (int64_t)gridDim.x * kNT;
@@ -1723,13 +1722,8 @@ __global__ void __launch_bounds__(kNT) k_mass_reduce(const double* __restrict__ 
     if (threadIdx.x == 0) {
       // eps log M, then Z = prox of F3 at the total mass
       const double SM = (M == -kInf || S == 0.0) ? -kInf : a.eps * (M + log(S));
-      const double Zold = a.Z[0];
-      const double Znew = prox_update(a.F3, a.logm0, SM, a.eps);
-      a.Z[0] = Znew;
-      if (a.check) {
-        a.acc[0] = a.acc[1] = 0.0;
-        a.acc[2] = (isfinite(Zold) && isfinite(Znew)) ? fabs(expm1((Zold - Znew) / a.eps)) : 0.0;
-      }
+      a.Z[0] = prox_update(a.F3, a.logm0, SM, a.eps);
+      if (a.check) a.acc[0] = a.acc[1] = 0.0;
       *a.count = 0u;
     }
   } else {
@@ -1775,19 +1769,8 @@ __global__ void __launch_bounds__(kNT) k_mass_reduce(const double* __restrict__ 
     if (threadIdx.x == 0) {
       const ff eps = ffl(a.eps_ff);
       const ff SM = (M.hi == -INFINITY || S == 0.0f) ? ff_ninf() : ff_mul(eps, ff_add_f(M, logf(S)));
-      float2* Z2 = reinterpret_cast<float2*>(a.Z);
-      const ff Zold = ffl(Z2[0]);
-      const ff Znew = prox_update_ff(a.F3ff, ffl(a.logm0_ff), SM, eps);
-      Z2[0] = ff2(Znew);
-      if (a.check) {
-        float merr = 0.0f;
-        if (isfinite(Zold.hi) && isfinite(Znew.hi)) {
-          const ff d = ff_mul(ff_sub(Zold, Znew), ffl(a.inv_eps_ff));
-          merr = fabsf(expm1f(d.hi + d.lo));
-        }
-        a.acc[0] = a.acc[1] = 0.0;
-        a.acc[2] = (double)merr;
-      }
+      reinterpret_cast<float2*>(a.Z)[0] = ff2(prox_update_ff(a.F3ff, ffl(a.logm0_ff), SM, eps));
+      if (a.check) a.acc[0] = a.acc[1] = 0.0;
       *a.count = 0u;
     }
   }
@@ -1848,6 +1831,132 @@ __global__ void __launch_bounds__(kNT) k_mass_prox(const double* __restrict__ z,
   }
 }
 
+// The b-side of an iteration in one kernel, when eps does not change from this
+// iteration to the next: V_j = prox_F2(log q_j, T_j + Z), and the mass of the
+// plan without z for the next z-update.  By Fubini the sum
+// sum_i dx_i e^{(U_i + S_i)/eps}, S from the new b, equals
+// sum_j dy_j e^{(V_j + T_j)/eps}, T from the current a, so it is reduced here
+// (per block: maximum, then the sum of e^{l_j - max}; the last block merges).
+// The last block applies F3's row and keeps the history of Z used for the
+// mass violation: zhist[1] <- zhist[0], zhist[0] <- the Z this iteration used.
+struct MassV {
+  int64_t m;
+  double eps;
+  float2 eps_ff, inv_eps_ff;
+  DivParams F2, F3;
+  DivFF F2ff, F3ff;
+  double logm0;
+  float2 logm0_ff;
+  double* Z;      // [1] Z (FP64) or its float-float pair: read, then replaced by the next one
+  double* zhist;  // [2] the Z of this iteration and of the one before
+  double2* part;  // [kMassBlocks]
+  unsigned* count;
+};
+
+template <bool FF>
+__global__ void __launch_bounds__(kNT) k_mass_vupdate(const double* __restrict__ zT, const double* __restrict__ logq,
+                                                      double* __restrict__ V, const double* __restrict__ logdy,
+                                                      MassV a) {
+  __shared__ double shd[kNT / 32];
+  __shared__ float2 shf[kNT / 32];
+  __shared__ bool last;
+  pdl_begin();
+  const int64_t i0 = (int64_t)blockIdx.x * kNT + threadIdx.x, stride = (int64_t)gridDim.x * kNT;
+  if constexpr (!FF) {
+    const double Zv = a.Z[0];
+    double mx = -kInf;
+    for (int64_t j = i0; j < a.m; j += stride) {
+      const double zj = zT[j];
+      const double Sz = (zj == -kInf || Zv == -kInf) ? -kInf : a.eps * zj + Zv;
+      const double v = prox_update(a.F2, logq[j], Sz, a.eps);
+      V[j] = v;
+      if (v != -kInf && zj != -kInf) mx = fmax(mx, logdy[j] + v / a.eps + zj);
+    }
+    mx = block_max_d(mx, shd);
+    double s = 0.0;
+    if (mx != -kInf)
+      for (int64_t j = i0; j < a.m; j += stride) {
+        const double v = V[j], zj = zT[j];
+        if (v != -kInf && zj != -kInf) s += exp(logdy[j] + v / a.eps + zj - mx);
+      }
+    s = block_sum_d(s, shd);
+    if (threadIdx.x == 0) {
+      a.part[blockIdx.x] = make_double2(mx, s);
+      __threadfence();
+      last = atomicAdd(a.count, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double2 pv = make_double2(-kInf, 0.0);
+    if (threadIdx.x < gridDim.x) pv = __ldcg(&a.part[threadIdx.x]);
+    const double M = block_max_d(pv.x, shd);
+    const double Ssum = block_sum_d((M == -kInf || pv.x == -kInf) ? 0.0 : pv.y * exp(pv.x - M), shd);
+    if (threadIdx.x == 0) {
+      const double SM = (M == -kInf || Ssum == 0.0) ? -kInf : a.eps * (M + log(Ssum));
+      reinterpret_cast<unsigned long long*>(a.zhist)[1] = reinterpret_cast<unsigned long long*>(a.zhist)[0];
+      a.zhist[0] = Zv;
+      a.Z[0] = prox_update(a.F3, a.logm0, SM, a.eps);
+      *a.count = 0u;
+    }
+  } else {
+    const float2* z2 = reinterpret_cast<const float2*>(zT);
+    const float2* q2 = reinterpret_cast<const float2*>(logq);
+    const float2* w2 = reinterpret_cast<const float2*>(logdy);
+    float2* V2 = reinterpret_cast<float2*>(V);
+    const ff eps = ffl(a.eps_ff), inv_eps = ffl(a.inv_eps_ff);
+    const float2 Zraw = reinterpret_cast<const float2*>(a.Z)[0];
+    const ff Zv = ffl(Zraw);
+    auto lval = [&](ff v, ff zj, int64_t j) {
+      return (v.hi == -INFINITY || zj.hi == -INFINITY) ? ff_ninf() : ff_add(ff_add(ffl(w2[j]), ff_mul(v, inv_eps)), zj);
+    };
+    ff mx = ff_ninf();
+    for (int64_t j = i0; j < a.m; j += stride) {
+      const ff zj = ffl(z2[j]);
+      const ff Sz = (zj.hi == -INFINITY || Zv.hi == -INFINITY) ? ff_ninf() : ff_add(ff_mul(zj, eps), Zv);
+      const ff v = prox_update_ff(a.F2ff, ffl(q2[j]), Sz, eps);
+      V2[j] = ff2(v);
+      mx = ff_max(mx, lval(v, zj, j));
+    }
+    mx = block_max_ff(mx, shf);
+    float s = 0.0f;
+    if (mx.hi != -INFINITY)
+      for (int64_t j = i0; j < a.m; j += stride) {
+        const ff l = lval(ffl(V2[j]), ffl(z2[j]), j);
+        if (l.hi == -INFINITY) continue;
+        const ff d = ff_sub(l, mx);
+        s += expf(d.hi + d.lo);
+      }
+    s = block_sum_f(s, shf);
+    if (threadIdx.x == 0) {
+      reinterpret_cast<float4*>(a.part)[blockIdx.x] = make_float4(mx.hi, mx.lo, s, 0.0f);
+      __threadfence();
+      last = atomicAdd(a.count, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    float4 pv = make_float4(-INFINITY, 0.0f, 0.0f, 0.0f);
+    if (threadIdx.x < gridDim.x) pv = __ldcg(&reinterpret_cast<const float4*>(a.part)[threadIdx.x]);
+    const ff vm{pv.x, pv.y};
+    const ff M = block_max_ff(vm, shf);
+    float t = 0.0f;
+    if (M.hi != -INFINITY && vm.hi != -INFINITY) {
+      const ff d = ff_sub(vm, M);
+      t = pv.z * expf(d.hi + d.lo);
+    }
+    const float Ssum = block_sum_f(t, shf);
+    if (threadIdx.x == 0) {
+      const ff SM = (M.hi == -INFINITY || Ssum == 0.0f) ? ff_ninf() : ff_mul(eps, ff_add_f(M, logf(Ssum)));
+      unsigned long long* zh = reinterpret_cast<unsigned long long*>(a.zhist);
+      zh[1] = zh[0];
+      reinterpret_cast<float2*>(a.zhist)[0] = Zraw;
+      reinterpret_cast<float2*>(a.Z)[0] = ff2(prox_update_ff(a.F3ff, ffl(a.logm0_ff), SM, eps));
+      *a.count = 0u;
+    }
+  }
+}
+
 uot_status solve_mass_impl(const uot_geom* g, const void* p, const void* dx, const void* q, const void* dy,
                            const uot_div* F1, const uot_div* F2, const uot_div* F3, double m0,
                            const uot_opts* o, void* Uout, void* Vout, double* Zout, uot_result* res,
@@ -1888,9 +1997,9 @@ uot_status solve_mass_impl(const uot_geom* g, const void* p, const void* dx, con
   sc.reserve<double>(m);            // logq
   sc.reserve<double>(m);            // logdy
   sc.reserve<double>(m);            // V
-  sc.reserve<double>(n);            // raw log-sums z = S/eps of the a-side pass
+  sc.reserve<double>(std::max(n, m));  // raw log-sums of the last pass (S/eps or T/eps)
   sc.reserve<double>(4);            // acc[3] + NaN flag
-  sc.reserve<double>(1);            // Z
+  sc.reserve<double>(3);            // Z, and the Z of the last two iterations
   sc.reserve<double2>(kMassBlocks); // mass partials
   sc.reserve<unsigned>(1);          // finished-block counter
   UOT_CK(sc.allocate());
@@ -1901,10 +2010,11 @@ uot_status solve_mass_impl(const uot_geom* g, const void* p, const void* dx, con
   double* logq = sc.take<double>(m);
   double* logdy = sc.take<double>(m);
   double* V = sc.take<double>(m);
-  double* zb = sc.take<double>(n);
+  double* zb = sc.take<double>(std::max(n, m));
   double* acc = sc.take<double>(4);
   int* flag = (int*)(acc + 3);
-  double* Zd = sc.take<double>(1);
+  double* Zd = sc.take<double>(3);
+  double* zhist = Zd + 1;
   double2* part = sc.take<double2>(kMassBlocks);
   unsigned* count = sc.take<unsigned>(1);
   UOT_SCRATCH_OK(sc);
@@ -1924,7 +2034,7 @@ uot_status solve_mass_impl(const uot_geom* g, const void* p, const void* dx, con
     count_launches(1);
     k_fill<<<nblocks(m), kNT, 0, s>>>(V, m, 0.0);
   }
-  UOT_CK(cudaMemsetAsync(Zd, 0, sizeof(double), s));  // z = 1 (both layouts)
+  UOT_CK(cudaMemsetAsync(Zd, 0, 3 * sizeof(double), s));  // z = 1 (both layouts)
   UOT_CK(cudaMemsetAsync(acc, 0, 4 * sizeof(double), s));
   UOT_CK(cudaMemsetAsync(count, 0, sizeof(unsigned), s));
   UOT_CK(cudaGetLastError());
@@ -1965,6 +2075,13 @@ uot_status solve_mass_impl(const uot_geom* g, const void* p, const void* dx, con
     if (ffm) return pdl_launch(k_mass_prox<true>, nblocks(n), st, zc, lp, U, lw, a);
     return pdl_launch(k_mass_prox<false>, nblocks(n), st, zc, lp, U, lw, a);
   };
+  // One iteration.  a-side: with eps unchanged since the previous iteration the
+  // b-side of that iteration has already computed this iteration's Z (Fubini,
+  // k_mass_vupdate), so the prox of S + Z runs in the pass epilogue; otherwise
+  // (the first iteration of a new eps stage) the z-update takes the plain route:
+  // raw pass, k_mass_reduce, k_mass_prox.  The very first iteration keeps z = 1.
+  // b-side: raw pass, then k_mass_vupdate (V and the next Z).
+  double prev_eps = -1.0;
   auto iteration = [&](double eps, bool check, cudaStream_t st) -> cudaError_t {
     cudaError_t e;
     Epilogue r;
@@ -1973,44 +2090,84 @@ uot_status solve_mass_impl(const uot_geom* g, const void* p, const void* dx, con
     set_eps(r, eps);
     r.out = zb;
     r.bstride = n;
-    if ((e = G.apply(0, V, logdy, eps, r, st)) != cudaSuccess) return e;
-    MassArgs a;
-    memset(&a, 0, sizeof(a));
-    a.n = n;
-    a.eps = eps;
-    a.eps_ff = ff2(ff_make(eps));
-    a.inv_eps_ff = ff2(ff_make(1.0 / eps));
-    a.F3 = D3;
-    a.F3ff = make_div_ff(D3, eps);
-    a.logm0 = log(m0);
-    a.logm0_ff = ff2(ff_make(log(m0)));
-    a.update = first ? 0 : 1;
-    a.check = check ? 1 : 0;
-    a.Z = Zd;
-    a.acc = acc;
-    a.part = part;
-    a.count = count;
-    const double* Uc = U;
-    const double* zc = zb;
-    const double* lw = logdx;
-    const int rb = first ? 1 : red_blocks;
-    e = ffm ? pdl_launch(k_mass_reduce<true>, rb, st, Uc, zc, lw, a)
-            : pdl_launch(k_mass_reduce<false>, rb, st, Uc, zc, lw, a);
+    const bool plain = !first && eps != prev_eps;
+    if (plain) {
+      if ((e = G.apply(0, V, logdy, eps, r, st)) != cudaSuccess) return e;
+      MassArgs a;
+      memset(&a, 0, sizeof(a));
+      a.n = n;
+      a.eps = eps;
+      a.eps_ff = ff2(ff_make(eps));
+      a.inv_eps_ff = ff2(ff_make(1.0 / eps));
+      a.F3 = D3;
+      a.F3ff = make_div_ff(D3, eps);
+      a.logm0 = log(m0);
+      a.logm0_ff = ff2(ff_make(log(m0)));
+      a.update = 1;
+      a.check = check ? 1 : 0;
+      a.Z = Zd;
+      a.acc = acc;
+      a.part = part;
+      a.count = count;
+      const double* Uc = U;
+      const double* zc = zb;
+      const double* lw = logdx;
+      e = ffm ? pdl_launch(k_mass_reduce<true>, red_blocks, st, Uc, zc, lw, a)
+              : pdl_launch(k_mass_reduce<false>, red_blocks, st, Uc, zc, lw, a);
+      if (e != cudaSuccess) return e;
+      if ((e = prox_a(eps, check ? acc : nullptr, st)) != cudaSuccess) return e;
+    } else {
+      Epilogue e1 = prox_epilogue(D1, logp, U, logdx, check ? acc : nullptr, eps);
+      e1.bstride = e1.bstride_p = n;
+      e1.zshift = Zd;
+      if ((e = G.apply(0, V, logdy, eps, e1, st, check ? acc : nullptr)) != cudaSuccess) return e;
+    }
     first = false;
-    if (e != cudaSuccess) return e;
-    if ((e = prox_a(eps, check ? acc : nullptr, st)) != cudaSuccess) return e;
-    Epilogue e2 = prox_epilogue(D2, logq, V, logdy, nullptr, eps);
-    e2.bstride = e2.bstride_p = m;
-    e2.zshift = Zd;
-    return G.apply(1, U, logdx, eps, e2, st);
+    prev_eps = eps;
+    r.bstride = m;
+    if ((e = G.apply(1, U, logdx, eps, r, st)) != cudaSuccess) return e;
+    MassV b;
+    memset(&b, 0, sizeof(b));
+    b.m = m;
+    b.eps = eps;
+    b.eps_ff = ff2(ff_make(eps));
+    b.inv_eps_ff = ff2(ff_make(1.0 / eps));
+    b.F2 = D2;
+    b.F3 = D3;
+    b.F2ff = make_div_ff(D2, eps);
+    b.F3ff = make_div_ff(D3, eps);
+    b.logm0 = log(m0);
+    b.logm0_ff = ff2(ff_make(log(m0)));
+    b.Z = Zd;
+    b.zhist = zhist;
+    b.part = part;
+    b.count = count;
+    const double* zc = zb;
+    const double* lq = logq;
+    const double* lw = logdy;
+    const int vb = (int)std::min<int64_t>(kNT, std::max<int64_t>(1, (m + per_block - 1) / per_block));
+    return ffm ? pdl_launch(k_mass_vupdate<true>, vb, st, zc, lq, V, lw, b)
+               : pdl_launch(k_mass_vupdate<false>, vb, st, zc, lq, V, lw, b);
   };
-  double hacc[3];
+  // the checked iteration's violations: the marginal one from acc, and the mass
+  // one |e^{(Z_old - Z)/eps} - 1| of its z-update from the history of Z (after
+  // the iteration, zhist = {its Z, the previous Z})
+  double hacc[2], hz[2];
+  auto zval = [&](double v) {
+    if (!ffm) return v;
+    float2 f;
+    memcpy(&f, &v, sizeof(f));
+    return (double)f.x + (double)f.y;
+  };
   auto read_err = [&](double& out) -> cudaError_t {
     cudaError_t e = cudaMemcpyAsync(hacc, acc, sizeof(hacc), cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(hz, zhist, sizeof(hz), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
     const double v = (hacc[1] > 0.0) ? hacc[0] / hacc[1] : 0.0;
-    out = (v != v || hacc[2] != hacc[2]) ? NAN : std::max(v, hacc[2]);
+    const double zn = zval(hz[0]), zo = zval(hz[1]);
+    const double merr = (std::isfinite(zn) && std::isfinite(zo)) ? std::fabs(std::expm1((zo - zn) / o->eps)) : 0.0;
+    out = (v != v) ? NAN : std::max(v, merr);
     return cudaSuccess;
   };
 
@@ -2076,7 +2233,7 @@ uot_status solve_mass_impl(const uot_geom* g, const void* p, const void* dx, con
   int hflag = 0, htc = 0;
   double hZ = 0.0;
   UOT_CK(cudaMemcpyAsync(&hflag, flag, 4, cudaMemcpyDeviceToHost, s));
-  UOT_CK(cudaMemcpyAsync(&hZ, Zd, 8, cudaMemcpyDeviceToHost, s));
+  UOT_CK(cudaMemcpyAsync(&hZ, zhist, 8, cudaMemcpyDeviceToHost, s));  // the Z of the last iteration
   if (G.tc_err) UOT_CK(cudaMemcpyAsync(&htc, G.tc_err, 4, cudaMemcpyDeviceToHost, s));
   UOT_CK(cudaStreamSynchronize(s));
   if (ffm) {
