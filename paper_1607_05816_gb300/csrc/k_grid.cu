@@ -748,6 +748,145 @@ __global__ void __launch_bounds__(WARPS * 32)
 
 }  // namespace
 
+
+// ---------------------------------------------------------------------------
+// Short lines (nin, nout <= 64, e.g. the 32- and 64-point axes of a 3-D
+// colour grid): one warp per (line, batch entry), OPL = 1 or 2 outputs per
+// lane, the line staged in the warp's shared memory, no combine across warps.
+// Same arithmetic as grid_pass_f32 (speculative shifts with the exact
+// fallback, float-float result, the same epilogue).
+// ---------------------------------------------------------------------------
+constexpr int kShortWarps = 8, kShortMax = 64;
+
+template <int OPL>
+__global__ void __launch_bounds__(kShortWarps * 32) grid_pass_f32_short(PassArgs a, Epilogue epi) {
+  __shared__ float2 sl[kShortWarps][kShortMax];  // {t, y} of the warp's line
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t item = (int64_t)blockIdx.x * kShortWarps + warp;
+  const int nin = a.nin, nout = a.nout, nlines = a.nlines;
+  const bool live = item < (int64_t)nlines * a.nbatch;  // warp-uniform
+  const int l = live ? (int)(item % nlines) : 0;
+  const int64_t bz = live ? item / nlines : 0;
+  float num = 0.0f, den = 0.0f;
+  const float2* in = a.in + bz * (int64_t)nlines * nin;
+  const int64_t base = (int64_t)l * nin;
+  float* zprev = a.zprev ? a.zprev + bz * (int64_t)nout * nlines : nullptr;
+  const bool spec = a.use_prev && zprev;
+  // ---- prologue independent of the preceding kernel ----
+  bool owns[OPL];
+  int64_t my_pt[OPL];
+  float zp[OPL], xq[OPL];
+  EpiPre pre[OPL];
+#pragma unroll
+  for (int q = 0; q < OPL; ++q) {
+    const int i = lane + 32 * q;
+    owns[q] = live && i < nout;
+    my_pt[q] = (int64_t)i * nlines + l;
+    zp[q] = 0.0f;
+    xq[q] = a.xo[i < nout ? i : nout - 1];
+    if (owns[q]) {
+      if (spec) zp[q] = zprev[my_pt[q]];
+      epilogue_prefetch(epi, bz, my_pt[q], pre[q]);
+    }
+  }
+  const float y0 = (lane < nin) ? a.yi[lane] : 0.0f, y1 = (lane + 32 < nin) ? a.yi[lane + 32] : 0.0f;
+  pdl_wait();
+  if (a.zero_acc && live && l == 0 && lane < 2) a.zero_acc[2 * bz + lane] = 0.0;
+  pdl_launch_dependents();
+  if (live) {
+    const ff v0 = (lane < nin) ? load_L_ff(a, in, base + lane) : ff_ninf();
+    const ff v1 = (lane + 32 < nin) ? load_L_ff(a, in, base + lane + 32) : ff_ninf();
+    const float mx = warp_maxf(fmaxf(v0.hi, v1.hi));
+    if (mx == -INFINITY) {
+      // b = 0 on the whole line: every sum is empty
+#pragma unroll
+      for (int q = 0; q < OPL; ++q) {
+        if (!owns[q]) continue;
+        if (zprev) zprev[my_pt[q]] = -INFINITY;
+        float n1, d1;
+        epilogue_apply(epi, bz, my_pt[q], ff_ninf(), pre[q], n1, d1);
+        num += n1;
+        den += d1;
+      }
+    } else {
+      auto stage = [&](ff v) { return (v.hi == -INFINITY) ? -INFINITY : ((v.hi - mx) + v.lo) * kLog2e; };
+      sl[warp][lane] = make_float2(stage(v0), y0);
+      if (lane + 32 < kShortMax) sl[warp][lane + 32] = make_float2(stage(v1), y1);
+      __syncwarp();
+      const float2* L = sl[warp];
+      const float nk2 = -a.k2;
+      float m[OPL], S[OPL];
+      bool exact = !spec;
+      for (int attempt = 0; attempt < 2; ++attempt) {
+#pragma unroll
+        for (int q = 0; q < OPL; ++q) {
+          m[q] = (zp[q] == -INFINITY) ? 0.0f : (zp[q] - mx) * kLog2e;
+          S[q] = 0.0f;
+        }
+        if (exact) {
+#pragma unroll
+          for (int q = 0; q < OPL; ++q) m[q] = -INFINITY;
+          for (int j = 0; j < nin; ++j) {
+            const float2 v = L[j];
+#pragma unroll
+            for (int q = 0; q < OPL; ++q) {
+              const float d = xq[q] - v.y;
+              m[q] = fmaxf(m[q], fmaf(nk2, d * d, v.x));
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < OPL; ++q)
+            if (m[q] == -INFINITY) m[q] = 0.0f;
+        }
+        for (int j = 0; j < nin; ++j) {
+          const float2 v = L[j];
+#pragma unroll
+          for (int q = 0; q < OPL; ++q) {
+            const float d = xq[q] - v.y;
+            S[q] += ex2_approx(fmaf(nk2, d * d, v.x - m[q]));
+          }
+        }
+        bool bad = false;
+#pragma unroll
+        for (int q = 0; q < OPL; ++q)
+          if (owns[q] && !exact) bad = bad || !(S[q] >= 0x1p-90f && S[q] <= 0x1p100f);
+        if (__any_sync(0xffffffffu, bad) && !exact) {
+          exact = true;
+          continue;  // warp-uniform: redo with exact maxima
+        }
+        break;
+      }
+#pragma unroll
+      for (int q = 0; q < OPL; ++q) {
+        if (!owns[q]) continue;
+        ff z = ff_ninf();
+        if (S[q] > 0.0f) {
+          // z = mx + ln2 m + ln2 log2(S), the first product kept exact in float-float
+          const ff ln2 = ff{0.693147182464599609375f, -1.904654323148236017e-09f};
+          z = ff_add_f(ff_add_f(ff_mul_f(ln2, m[q]), mx), kLn2 * lg2_approx(S[q]));
+        }
+        if (zprev) zprev[my_pt[q]] = z.hi;
+        float n1, d1;
+        epilogue_apply(epi, bz, my_pt[q], z, pre[q], n1, d1);
+        num += n1;
+        den += d1;
+      }
+    }
+  }
+  // the warps of a block may belong to different batch entries: one sum per warp
+  if (epi.err && live) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      num += __shfl_xor_sync(0xffffffffu, num, o);
+      den += __shfl_xor_sync(0xffffffffu, den, o);
+    }
+    if (lane == 0) {
+      atomicAdd(epi.err + 2 * bz, (double)num);
+      atomicAdd(epi.err + 2 * bz + 1, (double)den);
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Tile shapes of the FP32 pass and the tuner that picks one per pass shape.
 // ---------------------------------------------------------------------------
@@ -756,10 +895,32 @@ namespace {
 struct TileShape {
   int nw, opl;
 };
-// the last entry stands for the tensor-core pass (k_grid_tc3.cu), used where
-// its block-stabilisation condition holds (else the first tile runs)
-constexpr TileShape kTiles[] = {{8, 4}, {4, 4}, {2, 4}, {1, 4}, {8, 2}, {4, 2}, {2, 2}, {0, 0}};
+// entry 7 stands for the tensor-core pass (k_grid_tc3.cu), used where its
+// block-stabilisation condition holds, entry 8 for the warp-per-line pass of
+// short lines (nin, nout <= 64); where they do not apply the first tile runs
+constexpr TileShape kTiles[] = {{8, 4}, {4, 4}, {2, 4}, {1, 4}, {8, 2}, {4, 2}, {2, 2}, {0, 0}, {0, 0}};
 constexpr int kTc3Tile = 7;
+constexpr int kShortTile = 8;
+
+bool short_ok(const PassArgs& a) { return a.nin <= kShortMax && a.nout <= kShortMax; }
+
+cudaError_t launch_f32_short(const PassArgs& a, const Epilogue& epi, int nbatch, cudaStream_t s) {
+  const int64_t items = (int64_t)a.nlines * nbatch;
+  PassArgs b = a;
+  b.nbatch = nbatch;
+  cudaLaunchConfig_t cfg;
+  memset(&cfg, 0, sizeof(cfg));
+  cfg.gridDim = dim3((unsigned)((items + kShortWarps - 1) / kShortWarps));
+  cfg.blockDim = dim3(kShortWarps * 32);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (a.nout <= 32) return cudaLaunchKernelEx(&cfg, grid_pass_f32_short<1>, b, epi);
+  return cudaLaunchKernelEx(&cfg, grid_pass_f32_short<2>, b, epi);
+}
 constexpr int kNumTiles = (int)(sizeof(kTiles) / sizeof(kTiles[0]));
 
 template <int NW, int OPL>
@@ -790,6 +951,7 @@ cudaError_t launch_f32(int t, const PassArgs& a, const Epilogue& epi, int nbatch
   if (t == kTc3Tile && a.tc3_ok)
     return launch_grid_pass_tc3(a.in, a.logw, a.in_is_pot, a.nlines, a.nin, a.yi, a.nout, a.xo, a.inv_eps, a.k2,
                                 nbatch, epi, s, a.tc_err, a.zero_acc);
+  if (t == kShortTile && short_ok(a)) return launch_f32_short(a, epi, nbatch, s);
   switch (t) {
     case 0: return launch_f32_tile<8, 4>(a, epi, nbatch, s);
     case 1: return launch_f32_tile<4, 4>(a, epi, nbatch, s);
@@ -876,7 +1038,7 @@ TuneEntry tune_tiles(const PassArgs& base, int nbatch, cudaStream_t s) {
     bool wok = step(0, 0) && step(0, 0);
     for (int r = 0; r < kWarm && wok; ++r) wok = step(0, 1);
     for (int t = 0; t < kNumTiles; ++t) {
-      okt[t] = wok && (t != kTc3Tile || base.tc3_ok);
+      okt[t] = wok && (t != kTc3Tile || base.tc3_ok) && (t != kShortTile || short_ok(base));
       tmin[t] = 1e30f;
     }
     for (int round = 0; round < kRounds && wok; ++round) {
@@ -987,6 +1149,9 @@ std::string grid_tile_table() {
     if (e.tile == kTc3Tile)
       snprintf(buf, sizeof(buf), "dev%d lines=%d nin=%d nout=%d batch=%d -> tensor-core tc3;", k.dev, k.nlines, k.nin,
                k.nout, k.nbatch);
+    else if (e.tile == kShortTile)
+      snprintf(buf, sizeof(buf), "dev%d lines=%d nin=%d nout=%d batch=%d -> warp per line;", k.dev, k.nlines, k.nin,
+               k.nout, k.nbatch);
     else
       snprintf(buf, sizeof(buf), "dev%d lines=%d nin=%d nout=%d batch=%d -> warps=%d outputs/lane=%d;", k.dev,
                k.nlines, k.nin, k.nout, k.nbatch, kTiles[e.tile].nw, kTiles[e.tile].opl);
@@ -994,6 +1159,8 @@ std::string grid_tile_table() {
     for (int t = 0; t < kNumTiles; ++t) {
       if (t == kTc3Tile)
         snprintf(buf, sizeof(buf), " tc3:%.2fus", e.us[t]);
+      else if (t == kShortTile)
+        snprintf(buf, sizeof(buf), " line:%.2fus", e.us[t]);
       else
         snprintf(buf, sizeof(buf), " %dx%d:%.2fus", kTiles[t].nw, kTiles[t].opl, e.us[t]);
       s += buf;

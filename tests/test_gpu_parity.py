@@ -348,14 +348,16 @@ def test_persistent_launch_matches_per_pass_launches(shape):
 # FP32 grid-pass tile shapes and the tuner
 # ----------------------------------------------------------------------------
 
-@pytest.mark.parametrize("tile", range(8))
+@pytest.mark.parametrize("tile", range(9))
 @pytest.mark.parametrize("name,make", GIBBS_CASES[:3])
 def test_every_grid_tile_matches_oracle(tile, name, make):
     """Every tile shape the tuner may pick computes the operator and a short
     KL/TV solve to the FP32 tolerance (ragged lines and outputs included).
     Tile 7 is the tensor-core pass, which these coarse grids at eps = 0.01
-    do not admit (the SIMT tile runs instead)."""
-    assert U.grid_tile_count() == 8
+    do not admit (the SIMT tile runs instead); tile 8 is the warp-per-line
+    pass, which runs where lines and outputs are at most 64 long (every pass
+    of the 3-D case, some of the 2-D one)."""
+    assert U.grid_tile_count() == 9
     og, lg, dx, dy, p, q = make()
     g = synth.rng(19)
     eps = 0.01
@@ -380,6 +382,45 @@ def test_every_grid_tile_matches_oracle(tile, name, make):
         U.force_grid_tile(-1)
 
 
+def test_short_line_pass_batched():
+    """The warp-per-line pass (tile 8) on a batch of problems whose lines do
+    not fill a block (a block's warps straddle batch entries): potentials after
+    20 iterations match the oracle problem by problem, and with a tolerance the
+    per-entry violation sums stop where the general tile's do (within one
+    check block: the two tiles round differently)."""
+    g = synth.rng(61)
+    shape = (16, 8, 5)  # 40, 80 and 128 lines: blocks of 8 warps straddle the 7 entries
+    xs = [synth.grid_axis(n) for n in shape]
+    B = 7
+    dx = np.full(shape, 1.0 / np.prod(shape))
+    P = g.uniform(0.2, 2.0, size=(B,) + shape)
+    Q = g.uniform(0.2, 2.0, size=(B,) + shape)
+    P[2].ravel()[::5] = 0.0
+    og = O.Geometry("grid", xs=xs, ys=xs)
+    rd = lambda a: rounded(U.F32, a)
+    geo = U.Geometry.grid([T(a, U.F32) for a in xs], [T(a, U.F32) for a in xs])
+    args = (T(P.reshape(B, -1), U.F32), T(dx, U.F32).ravel(), T(Q.reshape(B, -1), U.F32), T(dx, U.F32).ravel())
+    stops = {}
+    for tile in (8, 0):
+        U.force_grid_tile(tile)
+        try:
+            Ug, Vg, _ = U.solve_many(geo, *args, U.KL(0.5), U.TV(0.3), 0.02, precision=U.F32, max_iter=20)
+            if tile == 8:
+                for k in range(B):
+                    r = O.solve_log(round_geom(og, U.F32), rd(dx), rd(dx), rd(P[k]), rd(Q[k]), O.KL(0.5),
+                                    O.TV(0.3), 0.02, max_iter=20)
+                    assert rel_err(to_np(Ug[k]), r["U"]) <= TOL[U.F32]
+                    assert rel_err(to_np(Vg[k]), r["V"]) <= TOL[U.F32]
+            _, _, info = U.solve_many(geo, *args, U.KL(0.5), U.TV(0.3), 0.02, precision=U.F32, max_iter=4000,
+                                      tol=1e-6, check_every=10)
+        finally:
+            U.force_grid_tile(-1)
+        assert info["status"] == "UOT_OK"
+        stops[tile] = (info["iters"], info["marg_err"])
+    assert abs(stops[8][0] - stops[0][0]) <= 10
+    assert stops[8][1] <= 1e-6 and stops[0][1] <= 1e-6
+
+
 def test_autotuner_records_choice_and_keeps_parity():
     """First use of a new pass shape times every tile and records the fastest;
     the tuned pass still matches the oracle."""
@@ -396,11 +437,11 @@ def test_autotuner_records_choice_and_keeps_parity():
         lines = [ln for ln in table.splitlines() if "nin=79 nout=83" in ln and "lines=61" in ln]
         assert len(lines) == 1, table
         times = [float(t.split(":")[1][:-2]) for t in lines[0].split(";")[1].split()]
-        assert len(times) == 8 and all(t > 0 for t in times[:7])
-        times = [t if t > 0 else math.inf for t in times]  # tc3 not admitted on this grid
+        assert len(times) == 9 and all(t > 0 for t in times[:7])
+        times = [t if t > 0 else math.inf for t in times]  # tc3 and short lines not admitted on this grid
         chosen = lines[0].split("-> ")[1].split(";")[0]
         names = ["warps=%d outputs/lane=%d" % sh for sh in [(8, 4), (4, 4), (2, 4), (1, 4), (8, 2), (4, 2), (2, 2)]]
-        names.append("tensor-core tc3")
+        names += ["tensor-core tc3", "warp per line"]
         k = names.index(chosen)
         tb = min(times)
         tick = 0.011  # the table prints times to 0.01 us: ties at that precision may go either way
