@@ -181,12 +181,15 @@ constexpr int kPfPrepBlocks = 32;   // blocks of the prefilter's line preparatio
 // as a float-float pair (Lff), and per-block maxima.  The last block to
 // finish (an atomic counter, no waiting) merges the maxima into *Lmax and
 // writes the shifted FP32 line Lt32_j = L_j - max L from the pairs with FP32
-// operations only (the FP64 pipe of one SM would take longer).
+// operations only (the FP64 pipe of one SM would take longer).  With merge =
+// 0 only L64 and Lff are written (any number of blocks): the consumer stages
+// the line and finds its maximum itself.
 __global__ void __launch_bounds__(256) prepare_L_pf(const double* __restrict__ W, const double* __restrict__ logw,
                                                    int nin, double inv_eps, double* __restrict__ L64,
                                                    float2* __restrict__ Lff, double* __restrict__ Lmax,
                                                    float* __restrict__ Lt32, float* __restrict__ lerr,
-                                                   double* __restrict__ part, unsigned* __restrict__ count) {
+                                                   double* __restrict__ part, unsigned* __restrict__ count,
+                                                   int merge) {
   __shared__ double red[8];
   __shared__ bool last;
   pdl_wait_prev();  // W is the preceding kernel's output
@@ -200,6 +203,7 @@ __global__ void __launch_bounds__(256) prepare_L_pf(const double* __restrict__ W
     Lff[j] = make_float2(hi, (L == -kInf) ? 0.0f : (float)(L - (double)hi));
     mx = fmax(mx, L);
   }
+  if (!merge) return;
   mx = wmax(mx);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
   __syncthreads();
@@ -249,8 +253,8 @@ template <int WPR, int RPC, bool kRows>
 __global__ void __launch_bounds__(WPR * RPC * 32)
     rows_lse_f64_pf(const double* __restrict__ C, const float* __restrict__ C32, int nrows, int nin,
                     const double* __restrict__ L64, const float* __restrict__ Lt32,
-                    const double* __restrict__ Lmax_p, const float* __restrict__ lerr_p, double k2,
-                    Epilogue epi) {
+                    const double* __restrict__ Lmax_p, const float* __restrict__ lerr_p,
+                    const float2* __restrict__ Lff, double k2, Epilogue epi) {
   constexpr int NT = WPR * RPC * 32, NW = WPR * RPC;
   // shared memory: the shifted FP32 input line (when it fits) and, with kRows,
   // the CTA's RPC rows of C32, copied in with cp.async so that every byte is
@@ -263,15 +267,17 @@ __global__ void __launch_bounds__(WPR * RPC * 32)
   __shared__ int pool[NW * 32];     // leftover columns, warp by warp (so row by row)
   __shared__ double pval[NW * 32];  // their FP64 terms
   __shared__ int woff[NW + 1];      // exclusive prefix sum of the warps' leftover counts
+  __shared__ float sm_lm[NW];       // the warps' maxima of the line (kRows)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int rloc = warp / WPR, part = warp % WPR;
   const int i = blockIdx.x * RPC + rloc;
   double num = 0.0, den = 0.0;
   const bool staged = kRows || nin <= kPfStageMax;
+  double Lmax;
+  float lerr;
   if (kRows) {
     // nin % 4 == 0 and 16-byte aligned C32: 16-byte copies of the rows (the cost does
-    // not depend on the preceding kernel, so they are issued before waiting for it),
-    // then of the line
+    // not depend on the preceding kernel, so they are issued before waiting for it)
     const int q = nin >> 2;
     const int nr = min(RPC, nrows - (int)blockIdx.x * RPC);
     for (int t = threadIdx.x; t < q * nr; t += NT) {
@@ -280,22 +286,36 @@ __global__ void __launch_bounds__(WPR * RPC * 32)
       const unsigned dst = (unsigned)__cvta_generic_to_shared(sL + (size_t)(r + 1) * nin + 4 * c4);
       asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
     }
+    asm volatile("cp.async.commit_group;" ::: "memory");
     pdl_wait_prev();
     pdl_release_next();
-    for (int c4 = threadIdx.x; c4 < q; c4 += NT) {
-      const unsigned dst = (unsigned)__cvta_generic_to_shared(sL + 4 * c4);
-      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(Lt32 + 4 * c4) : "memory");
+    // the line from its float-float pairs: every CTA finds the same maximum
+    // (mhi, the FP32 rounding of max L, so Lmax = mhi exactly) and writes the
+    // shifted line Lt32_j = (hi_j - mhi) + lo_j with FP32 operations only
+    float mloc = -INFINITY;
+    for (int j = threadIdx.x; j < nin; j += NT) mloc = fmaxf(mloc, Lff[j].x);
+    mloc = wmax(mloc);
+    if (lane == 0) sm_lm[warp] = mloc;
+    __syncthreads();
+    float mhi = sm_lm[0];
+#pragma unroll
+    for (int w = 1; w < NW; ++w) mhi = fmaxf(mhi, sm_lm[w]);
+    for (int j = threadIdx.x; j < nin; j += NT) {
+      const float2 l = Lff[j];
+      sL[j] = (mhi == -INFINITY || l.x == -INFINITY) ? -INFINITY : (l.x - mhi) + l.y;
     }
-    asm volatile("cp.async.commit_group;" ::: "memory");
+    Lmax = (mhi == -INFINITY) ? -kInf : (double)mhi;
+    // the pairs carry |L| 2^-47 of representation error besides the FP32 rounding
+    lerr = (mhi == -INFINITY) ? 4.0f : fmaf(fabsf(mhi), 0x1p-44f, 4.0f);
     asm volatile("cp.async.wait_group 0;" ::: "memory");
   } else {
     pdl_wait_prev();
     pdl_release_next();
     if (staged)
       for (int j = threadIdx.x; j < nin; j += NT) sL[j] = Lt32[j];
+    Lmax = *Lmax_p;
+    lerr = *lerr_p;
   }
-  const double Lmax = *Lmax_p;
-  const float lerr = *lerr_p;
   __syncthreads();
   const float* L = staged ? sL : Lt32;
   const bool live = i < nrows && Lmax != -kInf;  // warp-uniform
@@ -587,18 +607,18 @@ cudaError_t launch_rows(int prec, const RowsGeom& g, int nrows, int nin, const d
       double* L64 = (double*)(base + 768);
       float2* Lff = (float2*)(base + 768 + r8);
       float* Lt32 = (float*)(base + 768 + 2 * r8);
-      const int pblk = std::max(1, std::min(kPfPrepBlocks, (nin + 255) / 256));
-      cudaError_t e0 = launch_pdl(prepare_L_pf, dim3(pblk), dim3(256), 0, s, W, logw, nin, 1.0 / eps, L64, Lff,
-                                  Lmx, Lt32, lerr, (double*)(base + 256), (unsigned*)base);
-      if (e0 != cudaSuccess) return e0;
-      prof_mark_begin(PROF_ROWS, s);
       constexpr int WPR = 4, RPC = 4;
       const int grid2 = (nrows + RPC - 1) / RPC;
       // rows and line in shared memory: 16-byte rows (nin % 4 == 0) within 96 KB (opt-in
-      // above 48 KB)
+      // above 48 KB); the rows kernel then finds the line's maximum itself
       const size_t rows_bytes = (size_t)(1 + RPC) * nin * 4;
-      const bool rows_smem = (nin % 4 == 0) && rows_bytes <= 96 * 1024 && ((uintptr_t)g.C32 % 16 == 0) &&
-                             ((uintptr_t)Lt32 % 16 == 0);
+      const bool rows_smem = (nin % 4 == 0) && rows_bytes <= 96 * 1024 && ((uintptr_t)g.C32 % 16 == 0);
+      const int pblk = rows_smem ? (nin + 255) / 256 : std::max(1, std::min(kPfPrepBlocks, (nin + 255) / 256));
+      cudaError_t e0 = launch_pdl(prepare_L_pf, dim3(pblk), dim3(256), 0, s, W, logw, nin, 1.0 / eps, L64, Lff,
+                                  Lmx, Lt32, lerr, (double*)(base + 256), (unsigned*)base, rows_smem ? 0 : 1);
+      if (e0 != cudaSuccess) return e0;
+      prof_mark_begin(PROF_ROWS, s);
+      const float2* lff = Lff;
       if (rows_smem) {
         if (rows_bytes > 48 * 1024) {  // opt-in, for the current device
           cudaError_t e = cudaFuncSetAttribute(rows_lse_f64_pf<WPR, RPC, true>,
@@ -611,7 +631,7 @@ cudaError_t launch_rows(int prec, const RowsGeom& g, int nrows, int nin, const d
         const double* lmx = Lmx;
         const float* le = lerr;
         cudaError_t e1 = launch_pdl(rows_lse_f64_pf<WPR, RPC, true>, dim3(grid2), dim3(WPR * RPC * 32), rows_bytes, s,
-                                    C, c32, nrows, nin, l64, lt32, lmx, le, 1.0 / eps, epi);
+                                    C, c32, nrows, nin, l64, lt32, lmx, le, lff, 1.0 / eps, epi);
         if (e1 != cudaSuccess) return e1;
       } else {
         const size_t smem = nin <= kPfStageMax ? (size_t)nin * 4 : 0;
@@ -622,7 +642,7 @@ cudaError_t launch_rows(int prec, const RowsGeom& g, int nrows, int nin, const d
         const double* lmx = Lmx;
         const float* le = lerr;
         cudaError_t e1 = launch_pdl(rows_lse_f64_pf<WPR, RPC, false>, dim3(grid2), dim3(WPR * RPC * 32), smem, s,
-                                    C, c32, nrows, nin, l64, lt32, lmx, le, 1.0 / eps, epi);
+                                    C, c32, nrows, nin, l64, lt32, lmx, le, lff, 1.0 / eps, epi);
         if (e1 != cudaSuccess) return e1;
       }
       prof_mark_end(PROF_ROWS, s);
