@@ -55,7 +55,7 @@ FP64_PEAK_GFLOPS = 1250.0
 HBM_PEAK_GBS = 6760.6
 # dram bytes of one rows_lse_f64_pf<4, 4, 1> launch of the wf workload (ncu,
 # profiles/rows_lse_f64_pf_wf3000.md); None once the kernel changes
-WF_ROWS_TRAFFIC_BYTES = None
+WF_ROWS_TRAFFIC_BYTES = 36848640
 # FP32 pipe: 128 lanes per clock per SM (FADD/FMUL/FFMA; a packed f32x2
 # instruction occupies it for two lane-slots per pair).
 FP32_PER_CLK = 128
