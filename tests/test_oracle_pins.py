@@ -966,3 +966,113 @@ def test_apply_bin_map_gathers_by_bin():
     pts = np.array([[0.1, 0.1], [0.9, 0.1], [0.1, 0.9], [0.6, 0.6]])
     out = O.apply_bin_map(pts, shape, T)
     assert out.tolist() == [[0.1, 0.2], [0.5, 0.6], [0.3, 0.4], [0.7, 0.8]]
+
+
+# --------------------------------------------------------------------------
+# Direct pins of the helpers the solvers call
+# --------------------------------------------------------------------------
+
+def test_eps_schedule_is_geometric_down_to_eps():
+    """eps-scaling (Sec. 4.4): the stages start at eps_start and divide eps by
+    one fixed factor, and the division after the last stage lands on the final
+    eps; no stages when there is nothing to scale."""
+    st = O.eps_schedule(1e-3, eps_start=0.1, stages=4, iters_per_stage=7)
+    assert len(st) == 4 and all(k == 7 for _, k in st)
+    e = [v for v, _ in st]
+    assert e[0] == 0.1
+    assert np.allclose([e[k] / e[k + 1] for k in range(3)], 100.0 ** 0.25, rtol=1e-14, atol=0)
+    assert math.isclose(e[-1] / 100.0 ** 0.25, 1e-3, rel_tol=1e-13)
+    assert O.eps_schedule(1e-3) == [] and O.eps_schedule(1e-3, eps_start=1e-3) == []
+    assert O.eps_schedule(1e-3, eps_start=1e-4) == [] and O.eps_schedule(1e-3, eps_start=0.1, stages=0) == []
+
+
+def test_grid_axes_and_points_enumerate_the_bins():
+    """Colour grid (Sec. 5.1): bin k of an n-bin axis of [0, 1] is centred at
+    (k + 1/2)/n, and the grid's points are listed row-major (last axis
+    fastest), as a brute-force product of the axes lists them."""
+    import itertools
+    axes = O.grid_axes((2, 3, 4))
+    assert [len(a) for a in axes] == [2, 3, 4]
+    assert axes[0].tolist() == [0.25, 0.75] and axes[1].tolist() == [1 / 6, 0.5, 5 / 6]
+    pts = O.grid_points(axes)
+    assert pts.shape == (24, 3)
+    assert np.array_equal(pts, np.array(list(itertools.product(*[a.tolist() for a in axes]))))
+
+
+def test_growth_c_values():
+    """Sec. 5.3: the growth term -alpha mu(X) over a step tau enters the
+    proxdiv through c = 1 - 2 tau alpha / lam: 0.988 in the paper's one-species
+    run (tau = 0.006, alpha = 1, lam = 1), 1 without growth, and no step once
+    2 tau alpha reaches lam."""
+    assert math.isclose(O.growth_c(0.006, 1.0, 1.0), 0.988, rel_tol=1e-15)
+    assert O.growth_c(0.3, 0.0, 2.0) == 1.0
+    for tau in (0.5, 0.6):
+        with pytest.raises(ValueError):
+            O.growth_c(tau, 1.0, 1.0)
+
+
+@pytest.mark.parametrize("lam", [None, 0.7, 3.0])
+def test_mass_update_log_by_brute_force(lam):
+    """Algorithm 4 (Sec. 4.5): z = proxdiv_F3(M) with M = sum_i dx_i
+    e^{(U_i + S_i)/eps}, the plan's mass without z, summed here term by term.
+    F3 = iota_{=m0}: z M = m0 exactly.  F3 = lam KL(.|m0): z M is the minimiser
+    y of (lam/eps) KL(y|m0) + KL(y|M) (the prox of Table 1), found from its
+    optimality condition (lam/eps) log(y/m0) + log(y/M) = 0 by bisection."""
+    g = synth.rng(5)
+    n, eps, m0 = 9, 0.05, 1.7
+    U = g.normal(size=n) * 0.05
+    S = g.normal(size=n) * 0.05
+    U[2] = -np.inf
+    dx = g.uniform(0.5, 1.5, size=n) / n
+    M = sum(dx[i] * math.exp((U[i] + S[i]) / eps) for i in range(n) if np.isfinite(U[i]))
+    F3 = O.EQ() if lam is None else O.KL(lam)
+    Z = O.mass_update_log(F3, m0, U, S, np.log(dx), eps)
+    zM = math.exp(Z / eps) * M
+    if lam is None:
+        assert math.isclose(zM, m0, rel_tol=1e-12)
+    else:
+        assert abs(M - m0) > 0.05  # a proper bracket
+        y = optimize.brentq(lambda t: (lam / eps) * math.log(t / m0) + math.log(t / M), min(m0, M), max(m0, M),
+                            xtol=1e-15, rtol=4 * np.finfo(float).eps)
+        assert math.isclose(zM, y, rel_tol=1e-11)
+        # the KL row pulls the mass toward m0, more so the larger lam
+        assert min(m0, M) < zM < max(m0, M)
+
+
+def test_points_streamed_operator_by_brute_force():
+    """Sec. 4.3: S_i = eps log sum_j w_j exp((V_j - |x_i - y_j|^2)/eps), term
+    by term with math.exp, for 7 x 5 points in 2-D; the stream is cut into
+    blocks of 3 rows (a ragged last block)."""
+    g = synth.rng(8)
+    x = g.uniform(0, 1, size=(7, 2))
+    y = g.uniform(0, 1, size=(5, 2))
+    V = g.normal(size=5) * 0.1
+    w = g.uniform(0.5, 1.5, size=5)
+    eps = 0.3
+    got = O.apply_K_points_streamed(x, y, V, np.log(w), eps, block=3)
+    for i in range(7):
+        s = sum(w[j] * math.exp((V[j] - ((x[i, 0] - y[j, 0]) ** 2 + (x[i, 1] - y[j, 1]) ** 2)) / eps)
+                for j in range(5))
+        assert math.isclose(got[i], eps * math.log(s), rel_tol=1e-13, abs_tol=1e-14)
+
+
+def test_safe_log_conventions():
+    """Zero masses (Prop. 5.1, 0/0 = 0) need log 0 = -inf, quietly."""
+    got = O.safe_log([0.0, 1.0, math.e, 2.0])
+    assert got[0] == -math.inf and got[1] == 0.0
+    assert math.isclose(got[2], 1.0, rel_tol=1e-15) and got[3] == math.log(2.0)
+
+
+def test_violation_measure_on_a_hand_example():
+    """The stopping measure: sum dx |r1 - rho1| / sum dx rho1, r1 the first
+    marginal of the current plan and rho1 its prox target.  With S = 0,
+    U_old = eps (0, log 2), U_new = eps (log 3, 0), dx = (1/4, 3/4): r1 = (1, 2),
+    rho1 = (3, 1), so (1/4 * 2 + 3/4 * 1) / (1/4 * 3 + 3/4 * 1) = 5/6; a third
+    point with S = -inf (no plan mass) changes nothing."""
+    from oracle.uot_oracle import _violation_from
+    eps = 0.1
+    U_old = np.array([0.0, eps * math.log(2.0), 0.4])
+    U_new = np.array([eps * math.log(3.0), 0.0, -0.2])
+    S = np.array([0.0, 0.0, -np.inf])
+    logdx = np.log([0.25, 0.75, 0.5])
+    assert math.isclose(_violation_from(U_old, U_new, S, logdx, eps), 5.0 / 6.0, rel_tol=1e-14)
