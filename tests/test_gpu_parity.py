@@ -305,6 +305,53 @@ def test_barycenter_parity(kind, prec):
 # argument checking (host side, nothing launched)
 # ----------------------------------------------------------------------------
 
+def test_empty_inputs_rejected():
+    """Empty inputs are argument errors (EINVAL) found on the host before any
+    launch: a cost with no rows or no columns, a point cloud without points, a
+    grid with an axis of length 0 (solve, Gibbs operator, Algorithm 4,
+    barycentric map), a histogram or bin map of no points, a batch without
+    problems or with an empty one."""
+    f64, dev = torch.float64, "cuda"
+    z = lambda *sh: torch.zeros(*sh, dtype=f64, device=dev)
+    o = lambda *sh: torch.ones(*sh, dtype=f64, device=dev)
+    geoms = [
+        U.Geometry.dense(z(0, 16)),
+        U.Geometry.dense(z(16, 0)),
+        U.Geometry.points(z(0, 2), z(16, 2)),
+        U.Geometry.points(z(16, 2), z(0, 2)),
+        U.Geometry.grid([z(0), o(4)], [o(4), o(4)]),
+    ]
+    for geo in geoms:
+        p, q = o(geo.n), o(geo.m)
+        with pytest.raises(U.UotError, match="EINVAL"):
+            U.solve(geo, p, p, q, q, U.KL(1.0), U.KL(1.0), 0.1)
+        with pytest.raises(U.UotError, match="EINVAL"):
+            U.gibbs_log(geo, q, q, 0.1)
+        with pytest.raises(U.UotError, match="EINVAL"):
+            U.solve_mass(geo, p, p, q, q, U.KL(1.0), U.KL(1.0), U.EQ(), 1.0, 0.1)
+        if geo.kind != U.GEOM_DENSE:
+            with pytest.raises(U.UotError, match="EINVAL"):
+                U.barycentric_map(geo, p, q, 0.1, p, q)
+    pts = torch.zeros(0, 3, dtype=torch.float32, device=dev)
+    with pytest.raises(U.UotError, match="EINVAL"):
+        U.histogram(pts, (4, 4, 4))
+    with pytest.raises(U.UotError, match="EINVAL"):
+        U.apply_bin_map(pts, (4, 4, 4), z(64, 3))
+    f32 = lambda n, *r: torch.ones(n, *r, dtype=torch.float32, device=dev)
+    with pytest.raises(U.UotError, match="EINVAL"):
+        U.solve_batch([(3, 0)], [(U.KL(1.0), U.KL(1.0))], 2, f32(3, 2), f32(3), f32(3), f32(1, 2), f32(1), f32(1),
+                      0.1)
+    with pytest.raises((U.UotError, ValueError)):
+        U.solve_batch([], [], 2, f32(1, 2), f32(1), f32(1), f32(1, 2), f32(1), f32(1), 0.1)
+    # past the largest size: the histogram's 32-bit counters take at most 2^32 - 1
+    # points (rejected before the buffer is touched)
+    import ctypes
+    real, hist = torch.zeros(8, 3, dtype=torch.float32, device=dev), z(64)
+    sh = (ctypes.c_int * 3)(4, 4, 4)
+    rc = U.load().uot_histogram(real.data_ptr(), 2**32, 3, sh, U.F64, hist.data_ptr(), None)
+    assert U.STATUS[rc] == "UOT_EINVAL"
+
+
 def test_invalid_arguments_rejected():
     og, lg, dx, dy, p, q = dense_problem(16, 16, 3)
     geo = lg(U.F64)
