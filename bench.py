@@ -427,11 +427,16 @@ def run_single(args, rank, world, local_rank):
         geo = uot.Geometry.dense(f(C, torch.float64))
         ins = [f(d[k], torch.float64).ravel() for k in ("p", "dx", "q", "dy")]
 
+        # launch mode 1: Algorithm 1 as one launch of a thread-block cluster holding K in
+        # shared memory (mode 0: two launches per iteration)
+        lm = 0 if args.launch_mode == 0 else 1
+
         def step():
             return uot.solve(geo, *ins, uot.KL(1.0), uot.KL(1.0), 1e-2, precision=uot.F64, max_iter=2000,
-                             plain_scaling=True)
-        work_per_iter, unit_work, kernel = 2.0 * 256 * 256 * 2, "GFLOP/s", "alg1_half"
-        cfg = {"workload": "dense1d-256-kl1-eps1e-2-alg1-2000it", "n": 256, "m": 256}
+                             plain_scaling=True, launch_mode=lm)
+        work_per_iter, unit_work = 2.0 * 256 * 256 * 2, "GFLOP/s"
+        kernel = "alg1_cluster" if lm == 1 else "alg1_half"
+        cfg = {"workload": "dense1d-256-kl1-eps1e-2-alg1-2000it", "n": 256, "m": 256, "launch_mode": lm}
         dtype = "f64"
     elif wl == "wf":
         S = args.wf_species

@@ -124,7 +124,11 @@ typedef struct {
                           1: FP32 grid problems (batch 1) run as one persistent cooperative
                           launch, eps stages and convergence test on the device, grid barriers
                           between passes (measured slower at 256 x 256: 23.7k vs 39.5k it/s);
-                          other problems ignore it;
+                          with plain_scaling (Algorithm 1), each eps runs as one launch of one
+                          thread-block cluster (16 CTAs, else 8) holding K and K^T in shared
+                          memory, convergence tested on the device: the same iterates as 0,
+                          used where 8 (ceil(n/CL) m + ceil(m/CL) n + 2(n + m)) bytes fit in
+                          200 KB, else as 0; other problems ignore it;
                           2: as 0, but once a block of check_every iterations at the final eps
                           repeats the same launches (shifts from the previous iteration), it
                           is captured once as a CUDA graph and replayed block by block (log

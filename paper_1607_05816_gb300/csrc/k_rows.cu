@@ -12,6 +12,8 @@
 // FP64 kernel K = exp(-C/eps), with the proxdiv column of Table 1 (u = 0).
 #include <string.h>
 
+#include <cooperative_groups.h>
+
 #include <algorithm>
 
 #include "uot_internal.cuh"
@@ -555,6 +557,146 @@ __global__ void __launch_bounds__(WARPS * 32)
   if (err) block_add2<WARPS * 32>(num, den, err);
 }
 
+// Algorithm 1 for one eps with the stored kernel resident in the shared memory
+// of one thread-block cluster (CL CTAs, all iterations in one launch).  CTA r
+// holds rows [r R, r R + R) of K and rows [r Q, r Q + Q) of K^T (R = ceil(n/CL),
+// Q = ceil(m/CL)) and full copies of b (.) dy and a (.) dx.  A half-step is
+// alg1_half's arithmetic (one warp per row, lane-strided FMAs, warp sum), so a
+// and b are bit for bit those of the per-launch path.  After each half-step a
+// cluster barrier, then every CTA copies the other CTAs' new entries out of
+// their shared memory.  The violation sums of a checked iteration are reduced
+// per CTA, and every CTA adds the CTAs' sums in the same order, so all of them
+// take the same stop decision; there is no spin loop, only hardware barriers.
+constexpr int kAlg1Warps = 16;
+
+struct Alg1ClusterArgs {
+  const double* K;
+  const double* KT;
+  int n, m, R, Q;
+  const double *p, *dx, *q, *dy;
+  DivParams F1, F2;
+  double eps;
+  double* a;  // [n] in/out
+  double* b;  // [m] in/out
+  int iters, check_every;  // check_every = 0: no checks
+  double tol;
+  double* res;  // [3]: violation of the last check, iterations run, converged (0/1)
+};
+
+__global__ void __launch_bounds__(kAlg1Warps * 32) alg1_cluster(Alg1ClusterArgs A) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  extern __shared__ double sh[];
+  __shared__ double cpart[2];  // this CTA's violation sums, read by every CTA
+  const int CL = (int)cluster.num_blocks(), rank = (int)cluster.block_rank();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, NT = kAlg1Warps * 32;
+  const int n = A.n, m = A.m, R = A.R, Q = A.Q;
+  const int r0 = rank * R, nr = max(0, min(R, n - r0));
+  const int c0 = rank * Q, nc = max(0, min(Q, m - c0));
+  double* sK = sh;                      // [R][m]
+  double* sKT = sK + (size_t)R * m;     // [Q][n]
+  double* sbw = sKT + (size_t)Q * n;    // [m] b (.) dy
+  double* saw = sbw + m;                // [n] a (.) dx
+  double* sa = saw + n;                 // [R] this CTA's a
+  double* sb = sa + R;                  // [Q] this CTA's b
+  double* ssum = sb + Q;                // [max(R, Q)] row sums of the current half-step
+  for (size_t t = threadIdx.x; t < (size_t)nr * m; t += NT) sK[t] = A.K[(size_t)r0 * m + t];
+  for (size_t t = threadIdx.x; t < (size_t)nc * n; t += NT) sKT[t] = A.KT[(size_t)c0 * n + t];
+  for (int j = threadIdx.x; j < m; j += NT) sbw[j] = A.b[j] * A.dy[j];
+  for (int i = threadIdx.x; i < nr; i += NT) sa[i] = A.a[r0 + i];
+  for (int j = threadIdx.x; j < nc; j += NT) sb[j] = A.b[c0 + j];
+  __syncthreads();
+  double err = INFINITY;
+  int done = 0, conv = 0;
+  for (int k = 0; k < A.iters; ++k) {
+    const bool check = A.check_every > 0 && ((k + 1) % A.check_every == 0 || k == A.iters - 1);
+    // a-update on this CTA's rows: the sums, then Table 1 one row per lane of
+    // warp 0 (one FP64 instruction stream for all rows on the narrow FP64 pipe)
+    for (int r = warp; r < nr; r += kAlg1Warps) {
+      const double* row = sK + (size_t)r * m;
+      double sacc = 0.0;
+      for (int j = lane; j < m; j += 32) sacc = fma(row[j], sbw[j], sacc);
+      sacc = wsum(sacc);
+      if (lane == 0) ssum[r] = sacc;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      double num = 0.0, den = 0.0;
+      for (int r = lane; r < nr; r += 32) {
+        const int i = r0 + r;
+        const double sv = ssum[r], aold = sa[r];
+        const double anew = proxdiv_plain(A.F1, A.p[i], sv, A.eps);
+        sa[r] = anew;
+        saw[i] = anew * A.dx[i];
+        if (check) {
+          num += A.dx[i] * fabs(aold * sv - anew * sv);
+          den += A.dx[i] * anew * sv;
+        }
+      }
+      if (check) {
+        num = wsum(num);
+        den = wsum(den);
+        if (lane == 0) {
+          cpart[0] = num;
+          cpart[1] = den;
+        }
+      }
+    }
+    cluster.sync();
+    // the other CTAs' a (.) dx
+    for (int i = threadIdx.x; i < n; i += NT) {
+      const int owner = i / R;
+      if (owner != rank) saw[i] = *cluster.map_shared_rank(saw + i, owner);
+    }
+    if (check) {
+      double tn = 0.0, td = 0.0;
+      for (int c = 0; c < CL; ++c) {
+        const double* pc = cluster.map_shared_rank(cpart, c);
+        tn += pc[0];
+        td += pc[1];
+      }
+      err = (td > 0.0) ? tn / td : 0.0;
+    }
+    __syncthreads();
+    // b-update on this CTA's columns
+    for (int r = warp; r < nc; r += kAlg1Warps) {
+      const double* row = sKT + (size_t)r * n;
+      double sacc = 0.0;
+      for (int i = lane; i < n; i += 32) sacc = fma(row[i], saw[i], sacc);
+      sacc = wsum(sacc);
+      if (lane == 0) ssum[r] = sacc;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      for (int r = lane; r < nc; r += 32) {
+        const int j = c0 + r;
+        const double bnew = proxdiv_plain(A.F2, A.q[j], ssum[r], A.eps);
+        sb[r] = bnew;
+        sbw[j] = bnew * A.dy[j];
+      }
+    }
+    cluster.sync();
+    for (int j = threadIdx.x; j < m; j += NT) {
+      const int owner = j / Q;
+      if (owner != rank) sbw[j] = *cluster.map_shared_rank(sbw + j, owner);
+    }
+    __syncthreads();
+    done = k + 1;
+    if (check && done > 1 && A.tol > 0.0 && err <= A.tol) {  // the same decision in every CTA
+      conv = 1;
+      break;
+    }
+  }
+  for (int i = threadIdx.x; i < nr; i += NT) A.a[r0 + i] = sa[i];
+  for (int j = threadIdx.x; j < nc; j += NT) A.b[c0 + j] = sb[j];
+  if (rank == 0 && threadIdx.x == 0) {
+    A.res[0] = err;
+    A.res[1] = (double)done;
+    A.res[2] = (double)conv;
+  }
+  cluster.sync();  // no CTA leaves while another may still read its shared memory
+}
+
 }  // namespace
 
 size_t rows_pf_scratch_bytes(int64_t nin) {
@@ -661,6 +803,73 @@ cudaError_t launch_rows(int prec, const RowsGeom& g, int nrows, int nin, const d
   }
   prof_mark_end(PROF_ROWS, s);
   return cudaGetLastError();
+}
+
+size_t alg1_cluster_smem(int n, int m, int CL) {
+  const size_t R = (n + CL - 1) / CL, Q = (m + CL - 1) / CL;
+  return 8 * (R * m + Q * n + m + n + R + Q + std::max(R, Q));
+}
+
+cudaError_t launch_alg1_cluster(const double* K, const double* KT, int n, int m, const double* p,
+                                const double* dx, const double* q, const double* dy, DivParams F1,
+                                DivParams F2, double eps, double* a, double* b, int iters, int check_every,
+                                double tol, double* res, cudaStream_t s, bool* launched) {
+  *launched = false;
+  for (int CL : {16, 8}) {
+    const size_t smem = alg1_cluster_smem(n, m, CL);
+    if (smem > 200 * 1024) continue;
+    if (CL > 8 && cudaFuncSetAttribute(alg1_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+      (void)cudaGetLastError();
+      continue;
+    }
+    if (cudaFuncSetAttribute(alg1_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+      (void)cudaGetLastError();
+      continue;
+    }
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3(CL);
+    cfg.blockDim = dim3(kAlg1Warps * 32);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, alg1_cluster, &cfg) != cudaSuccess || nclusters < 1) {
+      (void)cudaGetLastError();
+      continue;
+    }
+    Alg1ClusterArgs A;
+    A.K = K;
+    A.KT = KT;
+    A.n = n;
+    A.m = m;
+    A.R = (n + CL - 1) / CL;
+    A.Q = (m + CL - 1) / CL;
+    A.p = p;
+    A.dx = dx;
+    A.q = q;
+    A.dy = dy;
+    A.F1 = F1;
+    A.F2 = F2;
+    A.eps = eps;
+    A.a = a;
+    A.b = b;
+    A.iters = iters;
+    A.check_every = check_every;
+    A.tol = tol;
+    A.res = res;
+    count_launches(1);
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, alg1_cluster, A);
+    if (e == cudaSuccess) *launched = true;
+    return e;
+  }
+  return cudaSuccess;  // does not fit: the caller runs the per-launch path
 }
 
 cudaError_t launch_alg1_half(const double* K, int nrows, int nin, const double* b,

@@ -1166,6 +1166,7 @@ uot_status solve_impl(const uot_geom* g, int batch, const void* p, const void* d
     sc.reserve<double>((size_t)n * m);  // K^T
     for (int k = 0; k < 3; ++k) sc.reserve<double>(n);  // a, p, dx
     for (int k = 0; k < 3; ++k) sc.reserve<double>(m);  // b, q, dy
+    sc.reserve<double>(4);                               // cluster solve's result
   }
   UOT_CK(sc.allocate());
   UOT_CK(G.take(sc, s));
@@ -1515,6 +1516,7 @@ uot_status solve_impl(const uot_geom* g, int batch, const void* p, const void* d
     double* qd = sc.take<double>(m);
     double* dxd = sc.take<double>(n);
     double* dyd = sc.take<double>(m);
+    double* cres = sc.take<double>(4);
     UOT_SCRATCH_OK(sc);
     UOT_CK(to_f64(prec, p, n, pd, s));
     UOT_CK(to_f64(prec, q, m, qd, s));
@@ -1536,16 +1538,40 @@ uot_status solve_impl(const uot_geom* g, int batch, const void* p, const void* d
       k_log_scale<<<nblocks(m), kNT, 0, s>>>(b, m, eps, V);
       return cudaGetLastError();
     };
+    // launch_mode 1: each eps runs as one launch of a cluster holding K in
+    // shared memory (where it fits; the same iterates as the per-launch path)
+    const bool cluster_mode = o->launch_mode == 1;
     for (const Stage& sg : stages) {
       UOT_CK(set_eps(sg.eps));
-      for (int k = 0; k < sg.iters; ++k, ++total) {
-        UOT_CK(launch_alg1_half(K, (int)n, (int)m, b, dyd, pd, D1, sg.eps, a, dxd, nullptr, s));
-        UOT_CK(launch_alg1_half(KT, (int)m, (int)n, a, dxd, qd, D2, sg.eps, b, dyd, nullptr, s));
+      bool launched = false;
+      if (cluster_mode)
+        UOT_CK(launch_alg1_cluster(K, KT, (int)n, (int)m, pd, dxd, qd, dyd, D1, D2, sg.eps, a, b, sg.iters, 0, 0.0,
+                                   cres, s, &launched));
+      if (launched) {
+        total += sg.iters;
+      } else {
+        for (int k = 0; k < sg.iters; ++k, ++total) {
+          UOT_CK(launch_alg1_half(K, (int)n, (int)m, b, dyd, pd, D1, sg.eps, a, dxd, nullptr, s));
+          UOT_CK(launch_alg1_half(KT, (int)m, (int)n, a, dxd, qd, D2, sg.eps, b, dyd, nullptr, s));
+        }
       }
       UOT_CK(to_pot(sg.eps));
     }
     UOT_CK(set_eps(o->eps));
-    while (it < o->max_iter) {
+    bool launched = false;
+    if (cluster_mode && o->max_iter > 0)
+      UOT_CK(launch_alg1_cluster(K, KT, (int)n, (int)m, pd, dxd, qd, dyd, D1, D2, o->eps, a, b, o->max_iter,
+                                 check_every, o->tol, cres, s, &launched));
+    if (launched) {
+      double h[3];
+      UOT_CK(cudaMemcpyAsync(h, cres, sizeof(h), cudaMemcpyDeviceToHost, s));
+      UOT_CK(cudaStreamSynchronize(s));
+      err = h[0];
+      it = (int)h[1];
+      total += it;
+      converged = h[2] != 0.0;
+    }
+    while (!launched && it < o->max_iter) {
       const bool check = ((it + 1) % check_every == 0) || (it == o->max_iter - 1);
       if (check) UOT_CK(cudaMemsetAsync(acc, 0, 16, s));
       UOT_CK(launch_alg1_half(K, (int)n, (int)m, b, dyd, pd, D1, o->eps, a, dxd, check ? acc : nullptr, s));

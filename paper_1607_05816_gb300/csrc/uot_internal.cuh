@@ -557,4 +557,16 @@ cudaError_t launch_alg1_half(const double* K, int nrows, int nin, const double* 
                              const double* w, const double* p, DivParams F, double eps,
                              double* a, const double* wout, double* err, cudaStream_t s);
 
+// Algorithm 1 at one eps, `iters` iterations (a then b) in one launch of one
+// thread-block cluster holding K and K^T in shared memory (16 CTAs, else 8).
+// check_every > 0: the violation of every check_every-th and of the last
+// iteration, stopping once it is <= tol (tol > 0) after more than one
+// iteration; res [3] receives the last violation, the iterations run and the
+// converged flag.  *launched = false (and nothing queued) when the kernel
+// does not fit or no such cluster can be scheduled.
+cudaError_t launch_alg1_cluster(const double* K, const double* KT, int n, int m, const double* p,
+                                const double* dx, const double* q, const double* dy, DivParams F1,
+                                DivParams F2, double eps, double* a, double* b, int iters, int check_every,
+                                double tol, double* res, cudaStream_t s, bool* launched);
+
 }  // namespace uot

@@ -209,19 +209,53 @@ def test_solve_dense_parity(prec):
     assert rel_err(Vg, r["V"]) <= TOL[prec]
 
 
-def test_plain_scaling_alg1_parity():
+@pytest.mark.parametrize("launch_mode", [0, 1])
+def test_plain_scaling_alg1_parity(launch_mode):
     """Algorithm 1 (no stabilisation) on the dense 1-D problem: 256 points,
-    KL lambda = 1 both sides, eps = 1e-2, FP64, against the oracle's
-    Algorithm 1 run verbatim."""
+    KL lambda = 1 both sides, eps = 1e-2, FP64, 2000 iterations, against the
+    oracle's Algorithm 1 run verbatim; per-launch (0) and as one launch of a
+    cluster holding K in shared memory (1, the benchmark's configuration)."""
     d = synth.problem_1d(256, 256, seed=1234)
     C = O.sqdist(d["x"], d["y"])
     eps, iters = 1e-2, 2000
     a, b = O.scaling_alg1(np.exp(-C / eps), d["dx"], d["dy"], d["p"], d["q"], O.KL(1.0), O.KL(1.0), eps, iters)
+    n0 = U.launch_count()
     Ug, Vg, info = U.solve(U.Geometry.dense(T(C, U.F64)), T(d["p"], U.F64), T(d["dx"], U.F64),
                            T(d["q"], U.F64), T(d["dy"], U.F64), U.KL(1.0), U.KL(1.0), eps,
-                           precision=U.F64, max_iter=iters, plain_scaling=True)
+                           precision=U.F64, max_iter=iters, plain_scaling=True, launch_mode=launch_mode)
     assert rel_err(to_np(Ug), eps * np.log(a)) <= 1e-10
     assert rel_err(to_np(Vg), eps * np.log(b)) <= 1e-10
+    assert info["iters"] == iters
+    if launch_mode == 1:
+        assert U.launch_count() - n0 < 20  # one solve launch, not 2 per iteration
+
+
+@pytest.mark.parametrize("n,m,F1,F2", [
+    (256, 256, U.KL(1.0), U.KL(0.5)),
+    (100, 37, U.TV(0.05), U.KL(0.3)),     # ragged bands: 7 rows of K, 3 of K^T per CTA
+    (5, 300, U.RG(0.7, 1.4), U.EQ()),      # most CTAs own no row of K
+    (600, 600, U.KL(1.0), U.KL(1.0)),     # does not fit: the per-launch path runs
+])
+def test_alg1_cluster_same_iterates_as_per_launch(n, m, F1, F2):
+    """launch_mode 1 of Algorithm 1 gives the per-launch path's iterates bit
+    for bit (the same sums in the same order), with eps-scaling stages, the
+    tolerance stop (checked every 7 iterations) and the violation it reports."""
+    d = synth.problem_1d(n, m, seed=n + m)
+    C = O.sqdist(d["x"], d["y"])
+    geo = U.Geometry.dense(T(C, U.F64))
+    args = [T(d[k], U.F64) for k in ("p", "dx", "q", "dy")]
+    if F1.kind == U.DIV_EQ or F2.kind == U.DIV_EQ:
+        args[2] = args[2] * (torch.sum(args[0] * args[1]) / torch.sum(args[2] * args[3]))
+    outs = []
+    for mode in (0, 1):
+        outs.append(U.solve(geo, *args, F1, F2, 0.02, precision=U.F64, max_iter=3000, tol=1e-9, check_every=7,
+                            eps_start=0.2, eps_stages=3, iters_per_stage=20, plain_scaling=True,
+                            launch_mode=mode))
+    (U0, V0, i0), (U1, V1, i1) = outs
+    assert torch.equal(U0, U1) and torch.equal(V0, V1)
+    assert i0["iters"] == i1["iters"] and i0["total_iters"] == i1["total_iters"] == i0["iters"] + 60
+    assert i0["status"] == i1["status"]
+    assert abs(i0["marg_err"] - i1["marg_err"]) <= 1e-12 * max(1.0, abs(i0["marg_err"]))
 
 
 def test_tolerance_stop_matches_oracle():
