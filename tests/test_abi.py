@@ -39,3 +39,22 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(uot.CDiv) == 32
     assert ctypes.sizeof(uot.COpts) == 8 + 8 + 8 + 4 + 4 + 4 + 4 + 8 + 4 + 4 + 4 + 4 + 8 + 8
     assert ctypes.sizeof(uot.CResult) == 4 + 4 + 8 + 8 + 4 + 4
+
+
+def test_no_cpu_fallback(monkeypatch):
+    """The binding has no CPU path: host tensors are refused before the
+    library is called, and a library that cannot be loaded raises instead of
+    degrading to another implementation."""
+    import pytest
+    import torch
+    C = torch.zeros(4, 3, dtype=torch.float64)
+    v4, v3 = torch.ones(4, dtype=torch.float64), torch.ones(3, dtype=torch.float64)
+    with pytest.raises(TypeError, match="CUDA tensor"):
+        uot.solve(uot.Geometry.dense(C), v4, v4, v3, v3, uot.KL(1.0), uot.KL(1.0), 0.1)
+    with pytest.raises(TypeError, match="CUDA tensor"):
+        uot.gibbs_log(uot.Geometry.dense(C), v3, v3, 0.1)
+    monkeypatch.setattr(uot, "_LIB", None)
+    monkeypatch.setattr(uot._build, "build", lambda *a, **k: None)
+    with pytest.raises(OSError):
+        uot.load(os.path.join(ROOT, "no-such-dir", "libuot.so"))
+    assert uot._LIB is None
