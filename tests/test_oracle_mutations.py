@@ -1,0 +1,82 @@
+"""The oracle's pins catch plausible mistakes.  Each case plants one mistake
+(a dropped term, a wrong sign, factor, index order or rounding) in a copy of
+the oracle, on the CPU, and runs the pins that cover that function against the
+copy: at least one of them must fail.  The oracle itself is never modified."""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+# (what goes wrong, text in oracle/uot_oracle.py, the planted text, pins that cover it)
+PLANTS = [
+    ("KL row exponent", "U = (F.lam / (F.lam + eps)) * ubar", "U = (F.lam / (F.lam + 2 * eps)) * ubar",
+     "prox_rows_brute_force or one_point_kl"),
+    ("TV clamp", "U = np.clip(ubar, -F.lam, F.lam)", "U = np.clip(ubar, -2 * F.lam, F.lam)",
+     "prox_rows_brute_force or one_point_piecewise"),
+    ("sign of S in the update", "eps * np.where(p_zero, 0.0, logp) - S_f", "eps * np.where(p_zero, 0.0, logp) + S_f",
+     "prox_rows_brute_force"),
+    ("Gibbs weights dropped", "L = V / eps + np.asarray(logw, dtype=np.float64)", "L = V / eps",
+     "gibbs_operator_matches_definition"),
+    ("barycenter weight normalisation", "(lse(Z, axis=0) - math.log(np.sum(alpha)))", "(lse(Z, axis=0))",
+     "barycenter"),
+    ("WF cost: cos not squared", "np.log(np.cos(np.minimum(d, math.pi / 2)) ** 2)",
+     "np.log(np.cos(np.minimum(d, math.pi / 2)))", "wf_cost_closed_forms"),
+    ("growth: per-species T", "Ttot = eps * lse(T / eps, axis=0)", "Ttot = T[0]",
+     "growth_prox_two_species"),
+    ("growth: lam dropped", "-lam * Ttot / (lam + eps))", "-Ttot / (lam + eps))", "growth_prox"),
+    ("bins: round for floor", "k = np.floor(P[:, a] * np.float32(n))", "k = np.round(P[:, a] * np.float32(n))",
+     "bin_index or color_histogram"),
+    ("mass: U - S", "np.asarray(logdx) + (U + S) / eps", "np.asarray(logdx) + (U - S) / eps", "mass_update"),
+    ("mass: dx dropped", "np.asarray(logdx) + (U + S) / eps", "0.0 + (U + S) / eps", "mass_update"),
+    ("eps stages: one too many in the ratio", "rho = (eps_start / eps_final) ** (1.0 / stages)",
+     "rho = (eps_start / eps_final) ** (1.0 / (stages + 1))", "eps_schedule"),
+    ("grid points column-major", 'indexing="ij"', 'indexing="xy"', "grid_axes"),
+    ("bin centres", "(np.arange(n, dtype=np.float64) + 0.5) / n", "(np.arange(n, dtype=np.float64) + 0.5) / (n + 1)",
+     "grid_axes"),
+    ("growth: tau alpha for 2 tau alpha", "c = 1.0 - 2.0 * tau * alpha / lam", "c = 1.0 - tau * alpha / lam",
+     "growth_c"),
+    ("streamed operator: weights dropped",
+     "L = np.asarray(V, dtype=np.float64) / eps + np.asarray(logw, dtype=np.float64)",
+     "L = np.asarray(V, dtype=np.float64) / eps", "streamed"),
+    ("violation relative to the current marginal", "den = np.sum(w * np.exp(lt))", "den = np.sum(w * np.exp(lr))",
+     "violation_measure"),
+]
+
+
+def _copy_tree(dst):
+    """The oracle, its pins and the seeded input generator, nothing else."""
+    shutil.copytree(os.path.join(ROOT, "oracle"), os.path.join(dst, "oracle"),
+                    ignore=shutil.ignore_patterns("__pycache__"))
+    os.makedirs(os.path.join(dst, "tests"))
+    os.makedirs(os.path.join(dst, "paper_1607_05816_gb300"))
+    for rel in ("pytest.ini", os.path.join("tests", "conftest.py"), os.path.join("tests", "test_oracle_pins.py"),
+                os.path.join("paper_1607_05816_gb300", "__init__.py"),
+                os.path.join("paper_1607_05816_gb300", "synth.py")):
+        shutil.copy(os.path.join(ROOT, rel), os.path.join(dst, rel))
+
+
+@pytest.mark.parametrize("what,orig,planted,pins", PLANTS, ids=[p[0] for p in PLANTS])
+def test_planted_mistake_is_caught(tmp_path, what, orig, planted, pins):
+    _copy_tree(str(tmp_path))
+    path = os.path.join(str(tmp_path), "oracle", "uot_oracle.py")
+    src = open(path).read()
+    assert src.count(orig) >= 1, f"the oracle no longer contains the text of plant '{what}'"
+    open(path, "w").write(src.replace(orig, planted, 1))
+    out = subprocess.run([sys.executable, "-m", "pytest", "tests/test_oracle_pins.py", "-q", "-x", "-k", pins],
+                         cwd=str(tmp_path), capture_output=True, text=True, timeout=600)
+    # exit code 1: tests ran and at least one failed (2-5 would be usage, import or collection errors)
+    assert out.returncode == 1, f"plant '{what}' not caught:\n{out.stdout[-1500:]}{out.stderr[-1500:]}"
+
+
+def test_unplanted_copy_passes_the_same_pins(tmp_path):
+    """Control: the copy without a plant passes every pin the cases select,
+    so each failure above is the plant's."""
+    _copy_tree(str(tmp_path))
+    sel = " or ".join(sorted({p[3] for p in PLANTS}))
+    out = subprocess.run([sys.executable, "-m", "pytest", "tests/test_oracle_pins.py", "-q", "-k", sel],
+                         cwd=str(tmp_path), capture_output=True, text=True, timeout=900)
+    assert out.returncode == 0, out.stdout[-2000:] + out.stderr[-2000:]
