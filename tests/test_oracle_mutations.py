@@ -44,6 +44,20 @@ PLANTS = [
      "L = np.asarray(V, dtype=np.float64) / eps", "streamed"),
     ("violation relative to the current marginal", "den = np.sum(w * np.exp(lt))", "den = np.sum(w * np.exp(lr))",
      "violation_measure"),
+    ("Algorithm 4: Z dropped from the a-update", "Sz = np.where(np.isneginf(S), NEG_INF, S + Z)", "Sz = S",
+     "alg4"),
+    ("Algorithm 4: Z dropped from the b-update", "Tz = np.where(np.isneginf(T), NEG_INF, T + Z)", "Tz = T",
+     "alg4"),
+    ("next density per species", "return R2 / np.maximum(c, np.sum(R2, axis=0))", "return R2 / np.maximum(c, R2)",
+     "growth_next_density"),
+    ("next log density per species", "tot = np.sum(np.exp(logR2), axis=0)", "tot = np.exp(logR2)",
+     "growth_next or wf_step"),
+    ("WF step: U for V in r2", "logr2 = np.where(np.isneginf(T), NEG_INF, (V + T) / eps)",
+     "logr2 = np.where(np.isneginf(T), NEG_INF, (U + T) / eps)", "wf_step"),
+    ("colour: dy weights dropped", "w = np.ravel(np.asarray(dy, dtype=np.float64))",
+     "w = np.ones(np.size(dy))", "barycentric_projection"),
+    ("colour: empty rows sent to 0", "return np.where(den[:, None] > 0, T, X)",
+     "return np.where(den[:, None] > 0, T, 0.0)", "barycentric_projection"),
 ]
 
 
