@@ -264,9 +264,10 @@ uot_status uot_solve(const uot_geom* g, const void* p, const void* dx, const voi
                      void* U, void* V, uot_result* res, void* stream);
 
 /*
- * uot_solve_many -- `batch` independent problems that share the geometry, the
- * reference weights dx, dy, eps and the penalties F1, F2 but not the
- * densities: p and U are [batch][n], q and V are [batch][m] (row-major).  For
+ * uot_solve_many -- the iteration of uot_solve (eq. S in the log form of
+ * Sec. 4.3, Table 1 rows) for `batch` independent problems that share the
+ * geometry, the reference weights dx, dy, eps and the penalties F1, F2 but not
+ * the densities: p and U are [batch][n], q and V are [batch][m] (row-major).  For
  * grids every Gibbs-operator pass treats all problems in one launch.  Options
  * as in uot_solve (plain_scaling unsupported); the iteration runs until every
  * problem's marginal violation is <= tol, and res->marg_err is the largest.
@@ -316,9 +317,11 @@ uot_status uot_gibbs_log(const uot_geom* g, const void* W, const void* w, double
                          int transpose, int precision, void* out, void* stream);
 
 /*
- * uot_gibbs_log_noalloc -- uot_gibbs_log without any device allocation.
+ * uot_gibbs_log_noalloc -- uot_gibbs_log (the log-domain Gibbs operator of
+ * Sec. 4.3, passes one axis at a time on grids as in Sec. 4.4) without any
+ * device allocation.
  *
- * The paper has no counterpart: this is a deployment variant for callers that
+ * The allocation-free form has no counterpart in the paper: it is a deployment variant for callers that
  * cannot allocate device memory (inside a CUDA stream capture that must stay
  * free of allocation nodes, under a foreign allocator that owns all device
  * memory, or in latency-critical loops where an allocation may block).
