@@ -23,9 +23,12 @@
  *  - Array arguments are DEVICE pointers owned by the caller unless the
  *    comment says "host".  The library keeps no pointer after it returns.
  *  - Floating-point arrays have the element type selected by `precision`:
- *    UOT_F64 -> double, UOT_F32 -> float.  (UOT_F32 runs the per-entry
- *    kernel arithmetic in FP32; per-point potentials are still accumulated in
- *    FP64 internally and returned as float.)
+ *    UOT_F64 -> double, UOT_F32 and UOT_MIXED -> float.  (UOT_F32 runs the
+ *    per-entry kernel arithmetic in FP32 and keeps every per-point quantity
+ *    -- potentials, log densities, log weights, intermediate log-sums -- as
+ *    a float-float pair (hi + lo, about 48 significant bits) built from
+ *    error-free FP32 transformations, so the FP64 pipe stays idle; outputs
+ *    are rounded to float unless uot_opts.out_f64 asks for double.)
  *  - Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
  *    stream).  Entry points that return host values (uot_solve's result,
  *    uot_objective) synchronise that stream before returning.
@@ -141,6 +144,19 @@ typedef struct {
                           problems run as 2 */
   const void* U0;      /* optional warm start [n] (NULL: U = 0) */
   const void* V0;      /* optional warm start [m] (NULL: V = 0, i.e. b = 1 as in Algorithm 1) */
+  int out_f64;         /* 1: U and V are written as double whatever the precision (UOT_F32 and
+                          UOT_MIXED: the float-float state, about 48 significant bits, rounded
+                          to FP64 instead of FP32); 0: the precision's type */
+  int verify;          /* 1 (log domain, UOT_F32 / UOT_MIXED, tol > 0): a stop signalled by the
+                          FP32 check is confirmed by evaluating the marginal violation of the
+                          current potentials in FP64 (FP64 Gibbs operator on FP64 copies of
+                          the geometry and of the state).  If the FP64 value is above tol
+                          the FP32 iteration continues with a proportionally lower internal
+                          threshold; once the FP32 check stops decreasing (its rounding
+                          floor), the remaining iterations run in FP64 from the current
+                          state, checked every iteration, until the FP64 violation is
+                          <= tol.  marg_err is then the FP64 value.  Launch modes 1 and 3
+                          run as 2.  0: the FP32 check decides. */
 } uot_opts;
 
 typedef struct {
@@ -149,6 +165,9 @@ typedef struct {
   double marg_err;  /* last measured marginal violation (see uot_solve) */
   double ms;        /* device time of the whole solve (CUDA events) */
   int status;       /* uot_status of the solve */
+  int verifications;    /* FP64 confirmations run (opts.verify) */
+  int polish_iters;     /* iterations run in FP64 after the FP32 floor (opts.verify) */
+  double marg_err_fp32; /* last FP32-evaluated violation (NaN if none) */
 } uot_result;
 
 /* Version string of the library build. */
@@ -312,6 +331,8 @@ uot_status uot_solve_mass(const uot_geom* g, const void* p, const void* dx, cons
  *   transpose = 0: out_i = eps log sum_j exp((W_j - C_ij)/eps) w_j   (out [n], W,w [m])
  *   transpose = 1: out_j = eps log sum_i exp((W_i - C_ij)/eps) w_i   (out [m], W,w [n])
  * i.e. eps log K(e^{W/eps} . w).  W may hold -inf (zero scaling).
+ * UOT_MIXED synchronises `stream` and returns UOT_TIMEOUT if a bounded wait of
+ * the tensor-core pass expired.
  */
 uot_status uot_gibbs_log(const uot_geom* g, const void* W, const void* w, double eps,
                          int transpose, int precision, void* out, void* stream);
@@ -321,27 +342,40 @@ uot_status uot_gibbs_log(const uot_geom* g, const void* W, const void* w, double
  * Sec. 4.3, passes one axis at a time on grids as in Sec. 4.4) without any
  * device allocation.
  *
- * The allocation-free form has no counterpart in the paper: it is a deployment variant for callers that
- * cannot allocate device memory (inside a CUDA stream capture that must stay
- * free of allocation nodes, under a foreign allocator that owns all device
- * memory, or in latency-critical loops where an allocation may block).
- * Arguments, layout and result are those of uot_gibbs_log; the caller still
- * provides W, w and out.  Temporary buffers come from one fixed device array
- * of UOT_NOALLOC_SCRATCH_BYTES bytes inside the library, which every GPU that
- * loads the library holds until the process exits.
- *  - Grid and point-cloud geometries only (UOT_EUNSUPPORTED for dense costs).
- *  - A problem whose scratch would exceed UOT_NOALLOC_SCRATCH_BYTES is
- *    rejected with UOT_EINVAL and a message in uot_last_error().  A 2-D grid
- *    needs about 40 bytes per point of its larger side, so grids of up to
- *    about 100,000 points per side (e.g. 256 x 256) fit.
+ * The allocation-free form has no counterpart in the paper.  It serves callers
+ * that cannot call cudaMalloc or cudaMallocAsync: code running under a foreign
+ * allocator that owns all device memory (a framework's pool or a pre-reserved
+ * arena, where a second allocator would fight it for memory), and real-time
+ * or latency-critical loops in which an allocation may block, synchronise or
+ * fail.  Arguments, layout and result are those of uot_gibbs_log; the caller
+ * still provides W, w and out.  Temporary buffers come from one fixed device
+ * array of UOT_NOALLOC_SCRATCH_BYTES bytes inside the library, which every GPU
+ * that loads the library holds until the process exits.
+ *  - Grid and point-cloud geometries, UOT_F64 and UOT_F32 (UOT_EUNSUPPORTED for
+ *    dense costs and for UOT_MIXED, whose set-up reads the grid axes back to
+ *    the host and synchronises the stream).
+ *  - Scratch needed, each buffer rounded up to 256 bytes, with nin, nout the
+ *    input and output sizes:
+ *      grids:  8 (2 nin + nout), plus 16 prod_k max(shape_x[k], shape_y[k]) when
+ *              ndim > 1, plus 256 for UOT_F32;
+ *      points: 8 (2 nin + nout) + 8 max(n, m) + 512, plus for UOT_F32 with d <= 3
+ *              8 x the chunk partials, max(c(m, n) n, c(n, m) m), where c(nin, nout)
+ *              >= ceil(nin / 1024) is the number of input chunks of a pass.
+ *    A square 2-D grid needs about 40 bytes per point: up to 323 x 323 fits
+ *    (256 x 256 does, 512 x 512 does not).  A larger problem is rejected with
+ *    UOT_EINVAL and a message in uot_last_error(), before anything is launched.
  *  - The first call on each device looks up the array's device address
- *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture on the device.
- *  - All calls share the array and it keeps the last call's contents: calls
+ *    (cudaGetSymbolAddress) with that device current, checks the result, and
+ *    keeps it for the life of the process; make that first call before any
+ *    stream capture on the device.  The kept address belongs to the CUDA
+ *    context of that first call: do not use this entry point after
+ *    cudaDeviceReset.
+ *  - All calls share the array and it keeps the last call's contents (every
+ *    buffer is written before it is read, so nothing needs clearing): calls
  *    whose work overlaps on the GPU (different streams, or several host
  *    threads) race and corrupt each other's results.  Serialise them.
- *  - No cudaMalloc, cudaMallocAsync, cudaFree or allocating library routine
- *    is called.
+ *  - No cudaMalloc, cudaMallocAsync, cudaFree or allocating library routine is
+ *    called, and the grid tile tuner (which allocates) is held off.
  */
 #define UOT_NOALLOC_SCRATCH_BYTES (4u << 20)
 uot_status uot_gibbs_log_noalloc(const uot_geom* g, const void* W, const void* w, double eps,

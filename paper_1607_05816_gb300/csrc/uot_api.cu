@@ -1085,14 +1085,161 @@ std::vector<Stage> eps_schedule(const uot_opts& o) {
   return st;
 }
 
-uot_status check_opts(const uot_opts* o) {
+uot_result empty_result() {
+  uot_result r;
+  memset(&r, 0, sizeof(r));
+  r.marg_err_fp32 = NAN;
+  return r;
+}
+
+// only uot_solve and uot_solve_many honour out_f64 and verify
+uot_status check_opts(const uot_opts* o, bool solve_outputs = false) {
   if (!o || !prec_ok(o->precision)) return UOT_EINVAL;
+  if ((o->out_f64 != 0 && o->out_f64 != 1) || (o->verify != 0 && o->verify != 1)) return UOT_EINVAL;
+  if (!solve_outputs && (o->out_f64 || o->verify)) return UOT_EUNSUPPORTED;
   if (!(o->eps > 0.0) || !isfinite(o->eps)) return UOT_EINVAL;
   if (o->max_iter < 0 || o->check_every < 0 || !(o->tol >= 0.0)) return UOT_EINVAL;
   if (o->eps_stages < 0 || o->iters_per_stage < 0) return UOT_EINVAL;
   if (o->eps_start > o->eps && !isfinite(o->eps_start)) return UOT_EINVAL;
   return UOT_OK;
 }
+
+// ---------------------------------------------------------------------------
+// FP64 confirmation of an FP32-path stop (uot_opts.verify), and the FP64
+// iterations that finish a solve once the FP32 check has reached its rounding
+// floor.  FP64 copies of the geometry and of the state, an FP64 Gibbs
+// operator on them; the violation is the stopping criterion of uot_solve
+// evaluated in FP64, i.e. the oracle's definition.
+// ---------------------------------------------------------------------------
+__global__ void k_ff_to_f64(const float2* __restrict__ src, int64_t n, double* __restrict__ dst) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float2 v = src[i];
+    dst[i] = (v.x == -INFINITY) ? -kInf : (double)v.x + (double)v.y;
+  }
+}
+
+struct Check64 {
+  Scratch sc;
+  Gibbs G;
+  int batch = 1;
+  int64_t n = 0, m = 0;
+  double *logp = nullptr, *logq = nullptr, *logdx = nullptr, *logdy = nullptr;
+  double *U = nullptr, *V = nullptr, *acc = nullptr;
+  std::vector<double> acc_h;
+  bool ready = false;
+  explicit Check64(cudaStream_t s) : sc(s) {}
+
+  // p, q, dx, dy, and the geometry's arrays, are the caller's FP32 inputs.
+  cudaError_t setup(const uot_geom& g, int batch_, const void* p, const void* dx, const void* q,
+                    const void* dy, cudaStream_t s) {
+    batch = batch_;
+    n = g.n;
+    m = g.m;
+    G.g = g;
+    G.prec = UOT_F64;
+    G.speculate = false;
+    // FP64 copies of the geometry
+    int64_t glen[2 * UOT_MAX_DIM + 1] = {0};
+    int ng = 0;
+    if (g.kind == UOT_GEOM_GRID) {
+      for (int k = 0; k < g.ndim; ++k) glen[ng++] = g.shape_x[k];
+      for (int k = 0; k < g.ndim; ++k) glen[ng++] = g.shape_y[k];
+    } else if (g.kind == UOT_GEOM_POINTS) {
+      glen[ng++] = (int64_t)g.n * g.d;
+      glen[ng++] = (int64_t)g.m * g.d;
+    } else {
+      glen[ng++] = (int64_t)g.n * g.m;
+    }
+    for (int k = 0; k < ng; ++k) sc.reserve<double>(glen[k]);
+    G.plan(sc, batch);
+    sc.reserve<double>(n * batch);  // logp
+    sc.reserve<double>(m * batch);  // logq
+    sc.reserve<double>(n);          // logdx
+    sc.reserve<double>(m);          // logdy
+    sc.reserve<double>(n * batch);  // U
+    sc.reserve<double>(m * batch);  // V
+    sc.reserve<double>(2 * (size_t)batch);
+    cudaError_t e = sc.allocate();
+    if (e != cudaSuccess) return e;
+    const void* src[2 * UOT_MAX_DIM + 1];
+    ng = 0;
+    if (g.kind == UOT_GEOM_GRID) {
+      for (int k = 0; k < g.ndim; ++k) src[ng++] = g.axes_x[k];
+      for (int k = 0; k < g.ndim; ++k) src[ng++] = g.axes_y[k];
+    } else if (g.kind == UOT_GEOM_POINTS) {
+      src[ng++] = g.x;
+      src[ng++] = g.y;
+    } else {
+      src[ng++] = g.C;
+    }
+    for (int k = 0; k < ng; ++k) {
+      double* dst = sc.take<double>(glen[k]);
+      if (!dst) return cudaErrorInvalidValue;
+      count_launches(1);
+      k_to_f64<float><<<nblocks(glen[k]), kNT, 0, s>>>((const float*)src[k], glen[k], dst);
+      if (g.kind == UOT_GEOM_GRID) {
+        if (k < g.ndim) G.g.axes_x[k] = dst;
+        else G.g.axes_y[k - g.ndim] = dst;
+      } else if (g.kind == UOT_GEOM_POINTS) {
+        if (k == 0) G.g.x = dst;
+        else G.g.y = dst;
+      } else {
+        G.g.C = dst;
+      }
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = G.take(sc, s)) != cudaSuccess) return e;
+    logp = sc.take<double>(n * batch);
+    logq = sc.take<double>(m * batch);
+    logdx = sc.take<double>(n);
+    logdy = sc.take<double>(m);
+    U = sc.take<double>(n * batch);
+    V = sc.take<double>(m * batch);
+    acc = sc.take<double>(2 * (size_t)batch);
+    if (!sc.ok()) return cudaErrorInvalidValue;
+    const void* in[4] = {p, q, dx, dy};
+    double* out[4] = {logp, logq, logdx, logdy};
+    const int64_t len[4] = {n * batch, m * batch, n, m};
+    for (int k = 0; k < 4; ++k) {
+      count_launches(1);
+      k_to_log<float><<<nblocks(len[k]), kNT, 0, s>>>((const float*)in[k], len[k], out[k]);
+    }
+    acc_h.assign(2 * (size_t)batch, 0.0);
+    ready = true;
+    return cudaGetLastError();
+  }
+  // the FP32 path's float-float state -> FP64
+  cudaError_t load_state(const double* Uff, const double* Vff, cudaStream_t s) {
+    count_launches(2);
+    k_ff_to_f64<<<nblocks(n * batch), kNT, 0, s>>>(reinterpret_cast<const float2*>(Uff), n * batch, U);
+    k_ff_to_f64<<<nblocks(m * batch), kNT, 0, s>>>(reinterpret_cast<const float2*>(Vff), m * batch, V);
+    return cudaGetLastError();
+  }
+  // One FP64 iteration of the log-domain scaling; with `check` the violation
+  // of the state it starts from is accumulated (read it with read_err).
+  cudaError_t iterate(const DivParams& D1, const DivParams& D2, double eps, bool check, bool v_update,
+                      cudaStream_t s) {
+    Epilogue e1 = prox_epilogue(D1, logp, U, logdx, check ? acc : nullptr, eps);
+    e1.bstride = e1.bstride_p = n;
+    cudaError_t e = G.apply(0, V, logdy, eps, e1, s, check ? acc : nullptr);
+    if (e != cudaSuccess || !v_update) return e;
+    Epilogue e2 = prox_epilogue(D2, logq, V, logdy, nullptr, eps);
+    e2.bstride = e2.bstride_p = m;
+    return G.apply(1, U, logdx, eps, e2, s);
+  }
+  cudaError_t read_err(double& out, cudaStream_t s) {
+    cudaError_t e = cudaMemcpyAsync(acc_h.data(), acc, 16 * (size_t)batch, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    out = 0.0;
+    for (int b = 0; b < batch; ++b) {
+      const double v = (acc_h[2 * b + 1] > 0.0) ? acc_h[2 * b] / acc_h[2 * b + 1] : 0.0;
+      out = (v > out || v != v) ? v : out;
+    }
+    return cudaSuccess;
+  }
+};
 
 // ---------------------------------------------------------------------------
 // solve
@@ -1106,7 +1253,7 @@ uot_status solve_impl(const uot_geom* g, int batch, const void* p, const void* d
                       void* Uout, void* Vout, uot_result* res, cudaStream_t s) {
   uot_status st = check_geom(g);
   if (st != UOT_OK) return st;
-  if ((st = check_opts(o)) != UOT_OK) return st;
+  if ((st = check_opts(o, true)) != UOT_OK) return st;
   if (batch < 1 || !p || !dx || !q || !dy || !Uout || !Vout || !div_ok(F1) || !div_ok(F2))
     return UOT_EINVAL;
   if (o->plain_scaling && (g->kind != UOT_GEOM_DENSE || o->precision != UOT_F64 || batch != 1))
@@ -1145,11 +1292,12 @@ uot_status solve_impl(const uot_geom* g, int batch, const void* p, const void* d
   // one persistent cooperative launch for FP32 grid problems
   const std::vector<Stage> stages_p = eps_schedule(*o);
   const int nst = (int)stages_p.size();
+  const bool verify = o->verify && prec != UOT_F64 && o->tol > 0.0 && !o->plain_scaling;
   const bool persist = o->launch_mode == 1 && prec == UOT_F32 && g->kind == UOT_GEOM_GRID &&
-                       batch == 1 && !o->plain_scaling;
+                       batch == 1 && !o->plain_scaling && !verify;
   // two kernels per iteration, each fusing two passes on one line (2-D FP32 grids)
   const bool fused2d = o->launch_mode == 3 && prec == UOT_F32 && g->kind == UOT_GEOM_GRID && g->ndim == 2 &&
-                       batch == 1 && !o->plain_scaling &&
+                       batch == 1 && !o->plain_scaling && !verify &&
                        grid_fused2_smem(std::max(g->shape_y[0], g->shape_x[1]), std::max(g->shape_x[0], g->shape_y[1])) <=
                            160 * 1024;
   if (persist) {
@@ -1203,6 +1351,14 @@ uot_status solve_impl(const uot_geom* g, int batch, const void* p, const void* d
   int it = 0, total = 0;
   double err = INFINITY;
   bool converged = false;
+  // opts.verify: FP64 confirmation of the stop, then FP64 iterations past the FP32 floor
+  Check64 c64(s);
+  double err32 = NAN, err64 = NAN, tol_int = o->tol;
+  int nverify = 0, npolish = 0;
+  bool polish = false, polished = false;
+  // FP32 progress: first check at the final eps, best value so far (1% steps)
+  double first_err = NAN, best_err = INFINITY;
+  int first_it = 0, best_it = 0;
 
   auto read_err = [&](double& out) -> cudaError_t {
     cudaError_t e = cudaMemcpyAsync(acc_h.data(), acc, 16 * (size_t)batch, cudaMemcpyDeviceToHost, s);
@@ -1451,6 +1607,52 @@ uot_status solve_impl(const uot_geom* g, int batch, const void* p, const void* d
       }
     }
   } else if (!o->plain_scaling) {
+    // The stop decision after a check (err = the FP32 violation just read).
+    auto decide = [&](bool& stop) -> cudaError_t {
+      stop = false;
+      err32 = err;
+      if (!(o->tol > 0.0)) return cudaSuccess;
+      if (!verify) {
+        if (err <= o->tol) converged = stop = true;
+        return cudaSuccess;
+      }
+      if (err <= tol_int) {
+        cudaError_t e = cudaSuccess;
+        if (!c64.ready && (e = c64.setup(*g, batch, p, dx, q, dy, s)) != cudaSuccess) return e;
+        if ((e = c64.load_state(U, V, s)) != cudaSuccess) return e;
+        if ((e = c64.iterate(D1, D2, o->eps, true, false, s)) != cudaSuccess) return e;
+        if ((e = c64.read_err(err64, s)) != cudaSuccess) return e;
+        ++nverify;
+        if (err64 <= o->tol) {
+          converged = stop = true;
+          return cudaSuccess;
+        }
+        // aim the FP32 check proportionally lower
+        tol_int = err * std::min(0.7, std::max(0.05, o->tol / err64));
+        best_err = err;
+        best_it = it;
+        return cudaSuccess;
+      }
+      // The FP32 check's rounding floor: no 1% improvement on its best value
+      // for W iterations, W = max(50, 5 check_every, 3x the iterations a 1%
+      // step took at the rate observed since the first check).
+      if (std::isnan(first_err)) {
+        first_err = err;
+        first_it = it;
+      }
+      if (err < 0.99 * best_err) {
+        best_err = err;
+        best_it = it;
+        return cudaSuccess;
+      }
+      double W = std::max(50, 5 * check_every);
+      if (best_err < first_err && best_it > first_it) {
+        const double rate = std::log(best_err / first_err) / (best_it - first_it);  // < 0
+        W = std::max(W, std::min(1e8, 3.0 * std::log(0.99) / rate));
+      }
+      if (it - best_it >= W) polish = stop = true;
+      return cudaSuccess;
+    };
     auto iteration = [&](double eps, bool check, cudaStream_t st) -> cudaError_t {
       cudaError_t e;
       Epilogue e1 = prox_epilogue(D1, logp, U, logdx, check ? acc : nullptr, eps);
@@ -1488,10 +1690,9 @@ uot_status solve_impl(const uot_geom* g, int batch, const void* p, const void* d
         it += check_every;
         total += check_every;
         UOT_CK(read_err(err));
-        if (o->tol > 0.0 && err <= o->tol) {
-          converged = true;
-          break;
-        }
+        bool stop = false;
+        UOT_CK(decide(stop));
+        if (stop) break;
         continue;
       }
       const bool check = ((it + 1) % check_every == 0) || (it == o->max_iter - 1);
@@ -1500,12 +1701,32 @@ uot_status solve_impl(const uot_geom* g, int batch, const void* p, const void* d
       ++total;
       if (check) {
         UOT_CK(read_err(err));
-        if (it > 1 && o->tol > 0.0 && err <= o->tol) {
+        if (it > 1) {
+          bool stop = false;
+          UOT_CK(decide(stop));
+          if (stop) break;
+        } else {
+          err32 = err;
+        }
+      }
+    }
+    if (polish) {
+      // the FP32 check has reached its rounding floor: FP64 iterations from the current state
+      UOT_CK(c64.load_state(U, V, s));
+      while (it < o->max_iter) {
+        UOT_CK(c64.iterate(D1, D2, o->eps, true, true, s));
+        ++it;
+        ++total;
+        ++npolish;
+        UOT_CK(c64.read_err(err64, s));
+        if (err64 <= o->tol) {
           converged = true;
           break;
         }
       }
+      polished = true;
     }
+    if (verify && !std::isnan(err64)) err = err64;
   } else {
     // Algorithm 1 on a stored FP64 kernel.
     double* K = sc.take<double>((size_t)n * m);
@@ -1592,15 +1813,32 @@ uot_status solve_impl(const uot_geom* g, int batch, const void* p, const void* d
     UOT_CK(to_pot(o->eps));
   }
 
-  // NaN check and output conversion
+  // NaN check and output conversion (after FP64 iterations the state is FP64)
+  const double* Ufin = polished ? c64.U : U;
+  const double* Vfin = polished ? c64.V : V;
+  const bool fin_ff = prec != UOT_F64 && !polished;
   UOT_CK(cudaMemsetAsync(flag, 0, 4, s));
   count_launches(1);
-  k_nan_flag<<<nblocks(bn), kNT, 0, s>>>(U, bn, prec != UOT_F64, flag);
+  k_nan_flag<<<nblocks(bn), kNT, 0, s>>>(Ufin, bn, fin_ff, flag);
   count_launches(1);
-  k_nan_flag<<<nblocks(bm), kNT, 0, s>>>(V, bm, prec != UOT_F64, flag);
+  k_nan_flag<<<nblocks(bm), kNT, 0, s>>>(Vfin, bm, fin_ff, flag);
   UOT_CK(cudaGetLastError());
-  UOT_CK(from_f64(prec, U, bn, Uout, s));
-  UOT_CK(from_f64(prec, V, bm, Vout, s));
+  if (fin_ff && o->out_f64) {
+    count_launches(2);
+    k_ff_to_f64<<<nblocks(bn), kNT, 0, s>>>(reinterpret_cast<const float2*>(Ufin), bn, (double*)Uout);
+    k_ff_to_f64<<<nblocks(bm), kNT, 0, s>>>(reinterpret_cast<const float2*>(Vfin), bm, (double*)Vout);
+    UOT_CK(cudaGetLastError());
+  } else if (!fin_ff && prec != UOT_F64 && !o->out_f64) {
+    // FP64 state (after FP64 iterations) to float outputs
+    count_launches(2);
+    k_from_f64<float><<<nblocks(bn), kNT, 0, s>>>(Ufin, bn, (float*)Uout);
+    k_from_f64<float><<<nblocks(bm), kNT, 0, s>>>(Vfin, bm, (float*)Vout);
+    UOT_CK(cudaGetLastError());
+  } else {
+    const int out_prec = fin_ff ? prec : UOT_F64;
+    UOT_CK(from_f64(out_prec, Ufin, bn, Uout, s));
+    UOT_CK(from_f64(out_prec, Vfin, bm, Vout, s));
+  }
   UOT_CK(cudaEventRecord(ev1, s));
   int hflag = 0, htc = 0;
   UOT_CK(cudaMemcpyAsync(&hflag, flag, 4, cudaMemcpyDeviceToHost, s));
@@ -1612,11 +1850,15 @@ uot_status solve_impl(const uot_geom* g, int batch, const void* p, const void* d
                        : hflag ? UOT_NUMERICAL
                                : ((o->tol > 0.0 && !converged && o->max_iter > 0) ? UOT_NOT_CONVERGED : UOT_OK);
   if (res) {
+    *res = empty_result();
     res->iters = it;
     res->total_iters = total;
     res->marg_err = err;
     res->ms = ms;
     res->status = out;
+    res->verifications = nverify;
+    res->polish_iters = npolish;
+    res->marg_err_fp32 = err32;
   }
   return out;
 }
@@ -2274,6 +2516,7 @@ uot_status solve_mass_impl(const uot_geom* g, const void* p, const void* dx, con
                        : (hflag || hZ != hZ) ? UOT_NUMERICAL
                                              : ((o->tol > 0.0 && !converged && o->max_iter > 0) ? UOT_NOT_CONVERGED : UOT_OK);
   if (res) {
+    *res = empty_result();
     res->iters = it;
     res->total_iters = total;
     res->marg_err = err;
@@ -2575,6 +2818,7 @@ uot_status wf_flow_impl(const uot_geom* g, int S, const void* P0, const void* dx
   UOT_CK(cudaEventElapsedTime(&ms, ev0, ev1));
   const uot_status out = htc ? UOT_TIMEOUT : hflag ? UOT_NUMERICAL : UOT_OK;
   if (res) {
+    *res = empty_result();
     res->iters = o->max_iter;
     res->total_iters = nsteps * (stage_iters + o->max_iter);
     res->marg_err = NAN;
@@ -2959,6 +3203,16 @@ uot_status uot_gibbs_log(const uot_geom* g, const void* W, const void* w, double
   e.out = od;
   UOT_CK(G.apply(transpose ? 1 : 0, Wd, logw, eps, e, s));
   UOT_CK(from_f64(precision, od, nout, out, s));
+  if (precision == UOT_MIXED && G.tc_err) {
+    // the tensor-core pass's bounded waits report through this flag
+    int htc = 0;
+    UOT_CK(cudaMemcpyAsync(&htc, G.tc_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    UOT_CK(cudaStreamSynchronize(s));
+    if (htc) {
+      g_last_error = "uot_gibbs_log: a bounded wait of the tensor-core pass expired";
+      return UOT_TIMEOUT;
+    }
+  }
   return UOT_OK;
 }
 
@@ -3022,6 +3276,11 @@ uot_status uot_gibbs_log_noalloc(const uot_geom* g, const void* W, const void* w
   if (!W || !w || !out || !(eps > 0.0) || !prec_ok(precision)) return UOT_EINVAL;
   if (g->kind == UOT_GEOM_DENSE) {
     g_last_error = "uot_gibbs_log_noalloc: dense cost matrices are not supported (grid and points only)";
+    return UOT_EUNSUPPORTED;
+  }
+  if (precision == UOT_MIXED) {
+    // its set-up copies the grid axes to the host and synchronises the stream
+    g_last_error = "uot_gibbs_log_noalloc: UOT_MIXED is not supported (UOT_F64 and UOT_F32 only)";
     return UOT_EUNSUPPORTED;
   }
   cudaStream_t s = (cudaStream_t)stream;
@@ -3396,6 +3655,7 @@ uot_status uot_solve_batch(int nprob, const uot_batch_problem* probs, int d, con
   }
   const uot_status out = all_conv ? UOT_OK : UOT_NOT_CONVERGED;
   if (res) {
+    *res = empty_result();
     res->iters = total;
     res->total_iters = total + nprob * nstage * o->iters_per_stage;
     res->marg_err = worst;
@@ -3644,6 +3904,7 @@ static uot_status barycenter_impl(const uot_geom* g, int Kmeas, const double* al
   UOT_CK(cudaEventElapsedTime(&ms, ev0, ev1));
   uot_status out = (o->tol > 0.0 && !converged && o->max_iter > 0) ? UOT_NOT_CONVERGED : UOT_OK;
   if (res) {
+    *res = empty_result();
     res->iters = it;
     res->total_iters = total;
     res->marg_err = err;

@@ -52,7 +52,8 @@ class COpts(C.Structure):
     _fields_ = [("precision", C.c_int), ("eps", C.c_double), ("eps_start", C.c_double),
                 ("eps_stages", C.c_int), ("iters_per_stage", C.c_int), ("max_iter", C.c_int),
                 ("tol", C.c_double), ("check_every", C.c_int), ("plain_scaling", C.c_int),
-                ("launch_mode", C.c_int), ("U0", C.c_void_p), ("V0", C.c_void_p)]
+                ("launch_mode", C.c_int), ("U0", C.c_void_p), ("V0", C.c_void_p),
+                ("out_f64", C.c_int), ("verify", C.c_int)]
 
 
 class CBatchProblem(C.Structure):
@@ -61,7 +62,8 @@ class CBatchProblem(C.Structure):
 
 class CResult(C.Structure):
     _fields_ = [("iters", C.c_int), ("total_iters", C.c_int), ("marg_err", C.c_double),
-                ("ms", C.c_double), ("status", C.c_int)]
+                ("ms", C.c_double), ("status", C.c_int), ("verifications", C.c_int),
+                ("polish_iters", C.c_int), ("marg_err_fp32", C.c_double)]
 
 
 _LIB = None
@@ -351,6 +353,12 @@ class Geometry:
         return g
 
 
+def _info(r: "CResult", st: int) -> dict:
+    return dict(iters=r.iters, total_iters=r.total_iters, marg_err=r.marg_err, ms=r.ms,
+                status=STATUS[st], verifications=r.verifications, polish_iters=r.polish_iters,
+                marg_err_fp32=r.marg_err_fp32)
+
+
 def _check(status, what):
     if status < 0:
         raise UotError(status, what)
@@ -360,24 +368,27 @@ def _check(status, what):
 def solve(geom: Geometry, p, dx, q, dy, F1: Div, F2: Div, eps: float, *, precision=F64,
           max_iter=1000, tol=0.0, check_every=10, eps_start=None, eps_stages=10,
           iters_per_stage=100, plain_scaling=False, U0=None, V0=None, U=None, V=None,
-          launch_mode=0):
+          launch_mode=0, out_f64=False, verify=False):
     """uot_solve: returns (U, V, result dict).  Inputs are CUDA tensors of the
-    precision's dtype; U, V (optional) are preallocated outputs."""
+    precision's dtype; U, V (optional) are preallocated outputs (float64 when
+    out_f64).  verify: the stop is confirmed by an FP64 evaluation of the
+    violation (FP32 / mixed paths)."""
     lib = load()
     dt = _dtype(precision)
-    U = torch.empty(geom.n, dtype=dt, device=p.device) if U is None else U
-    V = torch.empty(geom.m, dtype=dt, device=p.device) if V is None else V
+    odt = torch.float64 if out_f64 else dt
+    U = torch.empty(geom.n, dtype=odt, device=p.device) if U is None else U
+    V = torch.empty(geom.m, dtype=odt, device=p.device) if V is None else V
     o = COpts(precision, float(eps), float(eps_start) if eps_start else 0.0, int(eps_stages),
               int(iters_per_stage), int(max_iter), float(tol), int(check_every),
-              int(bool(plain_scaling)), int(launch_mode), _ptr(U0, dt, "U0"), _ptr(V0, dt, "V0"))
+              int(bool(plain_scaling)), int(launch_mode), _ptr(U0, dt, "U0"), _ptr(V0, dt, "V0"),
+              int(bool(out_f64)), int(bool(verify)))
     r = CResult()
     g = geom.c(precision)
     st = lib.uot_solve(C.byref(g), _ptr(p, dt, "p"), _ptr(dx, dt, "dx"), _ptr(q, dt, "q"),
                        _ptr(dy, dt, "dy"), C.byref(F1.c()), C.byref(F2.c()), C.byref(o),
-                       _ptr(U, dt, "U"), _ptr(V, dt, "V"), C.byref(r), _stream())
+                       _ptr(U, odt, "U"), _ptr(V, odt, "V"), C.byref(r), _stream())
     _check(st, "uot_solve")
-    return U, V, dict(iters=r.iters, total_iters=r.total_iters, marg_err=r.marg_err, ms=r.ms,
-                      status=STATUS[st])
+    return U, V, _info(r, st)
 
 
 def solve_mass(geom: Geometry, p, dx, q, dy, F1: Div, F2: Div, F3: Div, m0: float, eps: float, *,
@@ -506,25 +517,26 @@ def color_transfer(img_x, img_y, F2: Div, eps=0.002, iters=2000, bins=(64, 32, 3
 
 def solve_many(geom: Geometry, P, dx, Q, dy, F1: Div, F2: Div, eps, *, precision=F64,
                max_iter=1000, tol=0.0, check_every=10, eps_start=None, eps_stages=10,
-               iters_per_stage=100, U0=None, V0=None, U=None, V=None):
+               iters_per_stage=100, U0=None, V0=None, U=None, V=None, launch_mode=0,
+               out_f64=False, verify=False):
     """uot_solve_many: P [B, n], Q [B, m] densities of B independent problems
     sharing geometry, weights, eps and penalties.  Returns (U [B,n], V [B,m], info)."""
     lib = load()
     dt = _dtype(precision)
+    odt = torch.float64 if out_f64 else dt
     B = P.shape[0]
-    U = torch.empty(B, geom.n, dtype=dt, device=P.device) if U is None else U
-    V = torch.empty(B, geom.m, dtype=dt, device=P.device) if V is None else V
+    U = torch.empty(B, geom.n, dtype=odt, device=P.device) if U is None else U
+    V = torch.empty(B, geom.m, dtype=odt, device=P.device) if V is None else V
     o = COpts(precision, float(eps), float(eps_start) if eps_start else 0.0, int(eps_stages),
-              int(iters_per_stage), int(max_iter), float(tol), int(check_every), 0, 0,
-              _ptr(U0, dt, "U0"), _ptr(V0, dt, "V0"))
+              int(iters_per_stage), int(max_iter), float(tol), int(check_every), 0, int(launch_mode),
+              _ptr(U0, dt, "U0"), _ptr(V0, dt, "V0"), int(bool(out_f64)), int(bool(verify)))
     r = CResult()
     g = geom.c(precision)
     st = lib.uot_solve_many(C.byref(g), int(B), _ptr(P, dt, "P"), _ptr(dx, dt, "dx"),
                             _ptr(Q, dt, "Q"), _ptr(dy, dt, "dy"), C.byref(F1.c()), C.byref(F2.c()),
-                            C.byref(o), _ptr(U, dt, "U"), _ptr(V, dt, "V"), C.byref(r), _stream())
+                            C.byref(o), _ptr(U, odt, "U"), _ptr(V, odt, "V"), C.byref(r), _stream())
     _check(st, "uot_solve_many")
-    return U, V, dict(iters=r.iters, total_iters=r.total_iters, marg_err=r.marg_err, ms=r.ms,
-                      status=STATUS[st])
+    return U, V, _info(r, st)
 
 
 def gibbs_log(geom: Geometry, W, w, eps, transpose=False, precision=F64, out=None):

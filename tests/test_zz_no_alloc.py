@@ -1,12 +1,15 @@
 """The no-allocation Gibbs operator (uot_gibbs_log_noalloc).
 
-Callers that cannot allocate device memory (inside a stream capture, under a
-foreign allocator, in latency-critical loops) use this entry point; it must
-give the same result as uot_gibbs_log, which allocates its scratch.  Two calls
-in a row check that what the shared scratch array keeps from the previous
-call does not leak into the next one.  This file is collected last on
-purpose, so a failure here does not hide any other test.
+Callers that cannot call cudaMalloc (code under a foreign allocator that owns
+all device memory, real-time loops where an allocation may block or fail) use
+this entry point; it must give the same result as uot_gibbs_log, which
+allocates its scratch, and it must allocate nothing.  Two calls in a row check
+that what the shared scratch array keeps from the previous call does not leak
+into the next one.  This file is collected last on purpose, so a failure here
+does not hide any other test.
 """
+import ctypes
+
 import numpy as np
 import pytest
 import torch
@@ -76,3 +79,45 @@ def test_noalloc_rejects_oversized_problem():
     with pytest.raises(U.UotError, match="EINVAL"):
         U.gibbs_log_noalloc(geo, W, w, 0.01, False, U.F64)
     assert "UOT_NOALLOC_SCRATCH_BYTES" in U._last_error()
+
+
+# cudaMemPoolAttrUsedMemHigh (driver_types.h): the high-water mark of the
+# memory handed out by a pool since it was last reset to zero.  The library's
+# allocating entry points take their scratch from the device's default pool
+# (cudaMallocAsync); torch's caching allocator does not use that pool.
+_USED_MEM_HIGH = 8
+
+
+def _default_pool_used_high(reset=False):
+    rt = ctypes.CDLL("libcudart.so.13")
+    dev = torch.cuda.current_device()
+    pool = ctypes.c_void_p()
+    assert rt.cudaDeviceGetDefaultMemPool(ctypes.byref(pool), dev) == 0
+    v = ctypes.c_uint64(0)
+    if reset:
+        assert rt.cudaMemPoolSetAttribute(pool, _USED_MEM_HIGH, ctypes.byref(v)) == 0
+    assert rt.cudaMemPoolGetAttribute(pool, _USED_MEM_HIGH, ctypes.byref(v)) == 0
+    return v.value
+
+
+@pytest.mark.parametrize("prec", [U.F64, U.F32])
+def test_noalloc_allocates_nothing(prec):
+    geo, W, w = _grid(prec, (256, 256), (256, 256), 5)
+    U.gibbs_log_noalloc(geo, W, w, 0.01, False, prec)  # the first call's set-up
+    torch.cuda.synchronize()
+    # the measure works: the allocating operator moves the high-water mark
+    _default_pool_used_high(reset=True)
+    U.gibbs_log(geo, W, w, 0.01, False, prec)
+    torch.cuda.synchronize()
+    assert _default_pool_used_high() > 0
+    _default_pool_used_high(reset=True)
+    for _ in range(2):
+        U.gibbs_log_noalloc(geo, W, w, 0.01, False, prec)
+    torch.cuda.synchronize()
+    assert _default_pool_used_high() == 0
+
+
+def test_noalloc_rejects_mixed_precision():
+    geo, W, w = _grid(U.F32, (64, 64), (64, 64), 6)
+    with pytest.raises(U.UotError, match="EUNSUPPORTED"):
+        U.gibbs_log_noalloc(geo, W, w, 0.01, False, U.MIXED)
