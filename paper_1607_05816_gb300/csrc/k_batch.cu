@@ -39,47 +39,6 @@
 namespace uot {
 namespace {
 
-typedef unsigned long long f2p;
-__device__ __forceinline__ f2p pk(float a, float b) {
-  f2p r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-  return r;
-}
-__device__ __forceinline__ float2 upk(f2p r) {
-  float2 v;
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
-  return v;
-}
-__device__ __forceinline__ f2p fma2(f2p a, f2p b, f2p c) {
-  f2p d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
-}
-__device__ __forceinline__ f2p add2(f2p a, f2p b) {
-  f2p d;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ f2p sub2(f2p a, f2p b) {
-  f2p d;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ f2p mul2(f2p a, f2p b) {
-  f2p d;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ float ex2_approx(float x) {
-  float y;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-__device__ __forceinline__ float lg2_approx(float x) {
-  float y;
-  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
 
 constexpr int kOB = 128;  // outputs per warp block (4 per lane)
 
@@ -251,7 +210,7 @@ struct Half {
 // violation terms.
 __device__ __forceinline__ void output_epilogue(const Half& h, int i, float Mo, float So, float mx, float& num,
                                                 float& den) {
-  const ff ln2 = ff{0.693147182464599609375f, -1.904654323148236017e-09f};
+  const ff ln2 = ln2_ff();
   ff z = ff_ninf();
   if (Mo != -INFINITY && So > 0.0f) z = ff_add_f(ff_add_f(ff_mul_f(ln2, Mo), mx), kLn2 * lg2_approx(So));
   h.zprev[i] = z.hi;

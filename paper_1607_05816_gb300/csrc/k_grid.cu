@@ -29,11 +29,6 @@
 namespace uot {
 namespace {
 
-__device__ __forceinline__ float ex2_approx(float x) {
-  float y;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
 
 __device__ __forceinline__ double warp_max(double v) {
 #pragma unroll
@@ -50,43 +45,7 @@ __device__ __forceinline__ double load_L(const double* __restrict__ in,
 }
 
 // ---- packed FP32 pairs (f32x2 arithmetic of sm_100+ family GPUs) ----
-typedef unsigned long long f2p;
 
-__device__ __forceinline__ f2p pk(float a, float b) {
-  f2p r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-  return r;
-}
-__device__ __forceinline__ float2 upk(f2p r) {
-  float2 v;
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
-  return v;
-}
-__device__ __forceinline__ f2p fma2(f2p a, f2p b, f2p c) {
-  f2p d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
-}
-__device__ __forceinline__ f2p add2(f2p a, f2p b) {
-  f2p d;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ f2p sub2(f2p a, f2p b) {
-  f2p d;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ f2p mul2(f2p a, f2p b) {
-  f2p d;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ float lg2_approx(float x) {
-  float y;
-  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
 
 // FP32 grid pass.  One CTA = one line x (32 * OPL) consecutive outputs; its NW
 // warps split the contraction index j into NW contiguous ranges and combine
@@ -129,18 +88,9 @@ __device__ __forceinline__ ff load_L_ff(const PassArgs& a, const float2* in, int
   return ff_add(ff_mul(v, ffl(a.inv_eps)), ffl(a.logw[idx]));
 }
 
-__device__ __forceinline__ float warp_maxf(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
 
 // Programmatic dependent launch: wait until the preceding kernel in the stream
 // has completed and its writes are visible / let the next kernel launch early.
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_launch_dependents() {
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
 
 // Operands of the epilogue that do not depend on the preceding kernel, loaded
 // before waiting on it.
@@ -400,7 +350,7 @@ __device__ __forceinline__ void grid_item_f32(const PassArgs& a, const Epilogue&
       ff z = ff_ninf();
       if (So[r] > 0.0f) {
         // z = mx + ln2 Mo + ln2 log2(So), the first product kept exact in float-float
-        const ff ln2 = ff{0.693147182464599609375f, -1.904654323148236017e-09f};
+        const ff ln2 = ln2_ff();
         z = ff_add_f(ff_add_f(ff_mul_f(ln2, Mo[r]), mx), kLn2 * lg2_approx(So[r]));
       }
       if (zprev) zprev[my_pt[r]] = z.hi;
@@ -862,7 +812,7 @@ __global__ void __launch_bounds__(kShortWarps * 32) grid_pass_f32_short(PassArgs
         ff z = ff_ninf();
         if (S[q] > 0.0f) {
           // z = mx + ln2 m + ln2 log2(S), the first product kept exact in float-float
-          const ff ln2 = ff{0.693147182464599609375f, -1.904654323148236017e-09f};
+          const ff ln2 = ln2_ff();
           z = ff_add_f(ff_add_f(ff_mul_f(ln2, m[q]), mx), kLn2 * lg2_approx(S[q]));
         }
         if (zprev) zprev[my_pt[q]] = z.hi;

@@ -34,51 +34,6 @@
 namespace uot {
 namespace {
 
-typedef unsigned long long f2p;
-__device__ __forceinline__ f2p pk(float a, float b) {
-  f2p r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-  return r;
-}
-__device__ __forceinline__ float2 upk(f2p r) {
-  float2 v;
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
-  return v;
-}
-__device__ __forceinline__ f2p fma2(f2p a, f2p b, f2p c) {
-  f2p d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
-}
-__device__ __forceinline__ f2p add2(f2p a, f2p b) {
-  f2p d;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ f2p sub2(f2p a, f2p b) {
-  f2p d;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ f2p mul2(f2p a, f2p b) {
-  f2p d;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ float ex2_approx(float x) {
-  float y;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-__device__ __forceinline__ float lg2_approx(float x) {
-  float y;
-  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_launch_dependents() {
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
 
 constexpr int kGW = 8;                 // warps per group
 constexpr int kG = 2;                  // groups per CTA
@@ -134,7 +89,7 @@ __device__ void line_pass(const FSmem& sm, int nin, int nout, const float* __res
   const int J = (nin + kGW - 1) / kGW;
   const int j0 = min(nin, gw * J), j1 = min(nin, j0 + J);
   const f2p nk2 = pk(-k2, -k2);
-  const ff ln2 = ff{0.693147182464599609375f, -1.904654323148236017e-09f};
+  const ff ln2 = ln2_ff();
   for (int r = 0; r < rounds; ++r) {
     const int item = r * kG + g;
     const bool has = item < nitems;

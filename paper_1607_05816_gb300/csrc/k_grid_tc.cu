@@ -34,35 +34,6 @@ namespace {
 constexpr int kT = 32;     // block size (outputs and inputs)
 constexpr int kLines = 128;
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ float ex2f(float x) {
-  float y;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-__device__ __forceinline__ float lg2f(float x) {
-  float y;
-  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-
-// Shared-memory matrix descriptor, K-major operand without swizzle: core
-// matrices of 8 rows x 16 bytes; lbo = byte step between core matrices along
-// K, sbo = along M/N.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
-  d |= (uint64_t)1 << 46;
-  return d;
-}
-
-// byte offset of element (row, k) in a K-major, no-swizzle tile with K = 32
-// bf16 (4 core matrices along K): lbo = 128, sbo = 512
-__device__ __forceinline__ uint32_t tile_off(int row, int k) {
-  return (uint32_t)((row >> 3) * 512 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
-}
 
 struct TcArgs {
   const float2* in;    // float-float line values (or potentials when in_is_pot), batch-contiguous
@@ -175,8 +146,8 @@ __global__ void __launch_bounds__(kLines, 1)
     }
 #pragma unroll
     for (int q = 0; q < kT; q += 2) {
-      const float e0 = (mJ == -INFINITY) ? 0.0f : ex2f(av[q] - mJ);
-      const float e1 = (mJ == -INFINITY) ? 0.0f : ex2f(av[q + 1] - mJ);
+      const float e0 = (mJ == -INFINITY) ? 0.0f : ex2_approx(av[q] - mJ);
+      const float e1 = (mJ == -INFINITY) ? 0.0f : ex2_approx(av[q + 1] - mJ);
       *reinterpret_cast<__nv_bfloat162*>(sA + tile_off(tid, q)) = __floats2bfloat162_rn(e0, e1);
     }
     // G tile: rows = outputs i of the block, cols = inputs j of the block
@@ -186,7 +157,7 @@ __global__ void __launch_bounds__(kLines, 1)
       float g = 0.0f;
       if (j < nin && i0 + r < nout) {
         const float dd = (sx[r] - cI) - (a.yi[j] - cJ);
-        g = ex2f(-k2 * dd * dd);
+        g = ex2_approx(-k2 * dd * dd);
       }
       *reinterpret_cast<__nv_bfloat16*>(sG + tile_off(r, q)) = __float2bfloat16_rn(g);
     }
@@ -238,9 +209,9 @@ __global__ void __launch_bounds__(kLines, 1)
         const float P = __uint_as_float(r[q]);
         if (P > 0.0f) {
           const float di = sx[q] - cI;
-          const float v = lg2f(P) + mJ - k2 * Dd * (Dd + 2.0f * di);
+          const float v = lg2_approx(P) + mJ - k2 * Dd * (Dd + 2.0f * di);
           const float nm = fmaxf(Mr[q], v);
-          Sr[q] = Sr[q] * ex2f(Mr[q] - nm) + ex2f(v - nm);
+          Sr[q] = Sr[q] * ex2_approx(Mr[q] - nm) + ex2_approx(v - nm);
           Mr[q] = nm;
         }
       }
@@ -257,14 +228,14 @@ __global__ void __launch_bounds__(kLines, 1)
   if ((L0 + tid) < total_lines && !wait_failed) {
     const int64_t L = L0 + tid;
     const int64_t b = L / nlines, l = L % nlines;
-    const ff ln2 = ff{0.693147182464599609375f, -1.904654323148236017e-09f};
+    const ff ln2 = ln2_ff();
 #pragma unroll
     for (int q = 0; q < kT; ++q) {
       const int i = i0 + q;
       if (i >= nout) continue;
       ff z = ff_ninf();
       if (mx_l != -INFINITY && Sr[q] > 0.0f)
-        z = ff_add_f(ff_add_f(ff_mul_f(ln2, Mr[q]), mx_l), kLn2 * lg2f(Sr[q]));
+        z = ff_add_f(ff_add_f(ff_mul_f(ln2, Mr[q]), mx_l), kLn2 * lg2_approx(Sr[q]));
       float na, nb;
       apply_epilogue_ff(epi, b, (int64_t)i * nlines + l, z, na, nb);
       num += na;

@@ -50,35 +50,6 @@ constexpr int kTileA = kLines * kT * 2;      // bytes of one BF16 A tile
 constexpr int kTileG = kT * kT * 2;          // bytes of one BF16 G tile
 constexpr int kSmem = 3 * kTileA + 3 * kTileG + kLines * kT * 4 + kLines * 4;
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ float ex2f(float x) {
-  float y;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-__device__ __forceinline__ float lg2f(float x) {
-  float y;
-  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-
-// Shared-memory matrix descriptor, K-major operand without swizzle: core
-// matrices of 8 rows x 16 bytes; lbo = byte step between core matrices along
-// K, sbo = along M/N.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
-  d |= (uint64_t)1 << 46;
-  return d;
-}
-
-// byte offset of element (row, k) in a K-major, no-swizzle tile with K = 32
-// bf16 (4 core matrices along K): lbo = 128, sbo = 512
-__device__ __forceinline__ uint32_t tile_off(int row, int k) {
-  return (uint32_t)((row >> 3) * 512 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
-}
 
 // x = p0 + p1 + p2, each part the BF16 rounding of what the previous ones leave.
 __device__ __forceinline__ void split3(float x, __nv_bfloat16 (&p)[3]) {
@@ -174,8 +145,8 @@ __global__ void __launch_bounds__(kLines, 4) grid_pass_tc3(Tc3Args a, Epilogue e
   }
 #pragma unroll
   for (int q = 0; q < kT; q += 2) {
-    const float e0 = (M == -INFINITY || hv[q] == -INFINITY) ? 0.0f : ex2f(hv[q] - M);
-    const float e1 = (M == -INFINITY || hv[q + 1] == -INFINITY) ? 0.0f : ex2f(hv[q + 1] - M);
+    const float e0 = (M == -INFINITY || hv[q] == -INFINITY) ? 0.0f : ex2_approx(hv[q] - M);
+    const float e1 = (M == -INFINITY || hv[q + 1] == -INFINITY) ? 0.0f : ex2_approx(hv[q + 1] - M);
     __nv_bfloat16 p0[3], p1[3];
     split3(e0, p0);
     split3(e1, p1);
@@ -193,7 +164,7 @@ __global__ void __launch_bounds__(kLines, 4) grid_pass_tc3(Tc3Args a, Epilogue e
     float g = 0.0f;
     if (i0 + r < nout && j0 + q < nin) {
       const float dd = (sx[r] - cI) - (sy[q] - cJ);
-      g = ex2f(-k2 * dd * dd);
+      g = ex2_approx(-k2 * dd * dd);
     }
     __nv_bfloat16 p[3];
     split3(g, p);
@@ -264,7 +235,7 @@ __global__ void __launch_bounds__(kLines, 4) grid_pass_tc3(Tc3Args a, Epilogue e
   for (int q = 0; q < kT; ++q) {
     const float P = __uint_as_float(r[q]);
     float v = -INFINITY;
-    if (M != -INFINITY && P > 0.0f) v = M + lg2f(P) - k2 * D * (D + 2.0f * (sx[q] - cI));
+    if (M != -INFINITY && P > 0.0f) v = M + lg2_approx(P) - k2 * D * (D + 2.0f * (sx[q] - cI));
     spart[tid * kT + q] = v;
   }
   smx[tid] = mJ;
@@ -299,7 +270,7 @@ __global__ void __launch_bounds__(kLines, 4) grid_pass_tc3(Tc3Args a, Epilogue e
 
   const int64_t bA = (L0 + tl_begin) / nlines;  // batch entry of the share's first line
   float num0 = 0.0f, den0 = 0.0f, num1 = 0.0f, den1 = 0.0f;
-  const ff ln2 = ff{0.693147182464599609375f, -1.904654323148236017e-09f};
+  const ff ln2 = ln2_ff();
   const ff log2e = ff{1.44269502162933349609375f, 1.925963033500011079e-08f};
   for (int e = tid; e < nsh; e += kLines) {
     const int o = o_begin + e;
@@ -328,9 +299,9 @@ __global__ void __launch_bounds__(kLines, 4) grid_pass_tc3(Tc3Args a, Epilogue e
         // 2^((m_c - base) log2 e + r_c - r_b), the difference of the block maxima kept exact
         const ff dm = ff_two_sum(st_mx[c * nl + (tl - tl_begin)], -base);
         const ff dl = ff_mul(dm, log2e);
-        sum += ex2f(dl.hi + (dl.lo + (rc - rb)));
+        sum += ex2_approx(dl.hi + (dl.lo + (rc - rb)));
       }
-      z = ff_add_f(ff_add_f(ff_mul_f(ln2, rb), base), kLn2 * lg2f(sum));
+      z = ff_add_f(ff_add_f(ff_mul_f(ln2, rb), base), kLn2 * lg2_approx(sum));
     }
     const int64_t b = Lo / nlines, l = Lo % nlines;
     float na, nb;

@@ -23,47 +23,6 @@
 namespace uot {
 namespace {
 
-typedef unsigned long long f2p;
-__device__ __forceinline__ f2p pk(float a, float b) {
-  f2p r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-  return r;
-}
-__device__ __forceinline__ float2 upk(f2p r) {
-  float2 v;
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
-  return v;
-}
-__device__ __forceinline__ f2p fma2(f2p a, f2p b, f2p c) {
-  f2p d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
-}
-__device__ __forceinline__ f2p add2(f2p a, f2p b) {
-  f2p d;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ f2p sub2(f2p a, f2p b) {
-  f2p d;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ f2p mul2(f2p a, f2p b) {
-  f2p d;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ float ex2f(float x) {
-  float y;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-__device__ __forceinline__ float lg2f(float x) {
-  float y;
-  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
 
 constexpr int kNW = 8;                 // warps per CTA
 constexpr int kOutBlk = kNW * 128;     // outputs per CTA
@@ -218,8 +177,8 @@ __global__ void __launch_bounds__(kNW * 32)
       }
       const float2 A = upk(fma2(nk2, QA, sub2(T, MA)));
       const float2 B = upk(fma2(nk2, QB, sub2(T, MB)));
-      SA = add2(SA, pk(ex2f(A.x), ex2f(A.y)));
-      SB = add2(SB, pk(ex2f(B.x), ex2f(B.y)));
+      SA = add2(SA, pk(ex2_approx(A.x), ex2_approx(A.y)));
+      SB = add2(SB, pk(ex2_approx(B.x), ex2_approx(B.y)));
     }
     const float2 s01 = upk(SA), s23 = upk(SB);
     sq[0] = s01.x;
@@ -277,7 +236,7 @@ __global__ void __launch_bounds__(256)
     if (M != -INFINITY)
       for (int c = lane; c < a.nchunks; c += 32) {
         const float2 pr = a.part[(int64_t)c * a.nout + i];
-        if (pr.y > 0.0f) S += pr.y * ex2f(pr.x - M);
+        if (pr.y > 0.0f) S += pr.y * ex2_approx(pr.x - M);
       }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) S += __shfl_xor_sync(0xffffffffu, S, o);
@@ -302,7 +261,7 @@ __global__ void __launch_bounds__(256)
       for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
       float s = 0.0f;
       if (m != -INFINITY)
-        for (int j = lane; j < a.nin; j += 32) s += ex2f(arg(j) - m);
+        for (int j = lane; j < a.nin; j += 32) s += ex2_approx(arg(j) - m);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
       M = m;
@@ -311,8 +270,8 @@ __global__ void __launch_bounds__(256)
     if (lane == 0) {
       ff z = ff_ninf();
       if (Lmax != -INFINITY && M != -INFINITY && S > 0.0f) {
-        const ff ln2 = ff{0.693147182464599609375f, -1.904654323148236017e-09f};
-        z = ff_add_f(ff_add_f(ff_mul_f(ln2, M), Lmax), kLn2 * lg2f(S));
+        const ff ln2 = ln2_ff();
+        z = ff_add_f(ff_add_f(ff_mul_f(ln2, M), Lmax), kLn2 * lg2_approx(S));
       }
       if (a.zprev) a.zprev[i] = z.hi;
       apply_epilogue_ff(epi, 0, i, z, num, den);

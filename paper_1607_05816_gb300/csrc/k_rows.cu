@@ -21,11 +21,6 @@
 namespace uot {
 namespace {
 
-__device__ __forceinline__ float ex2_approx(float x) {
-  float y;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
 
 template <typename T>
 __device__ __forceinline__ T wmax(T v) {
@@ -501,7 +496,7 @@ __global__ void __launch_bounds__(WARPS * 32)
       if (lane == 0 && m == -INFINITY) {
         apply_epilogue_ff(epi, 0, i, ff_ninf(), num, den);
       } else if (lane == 0) {
-        const ff ln2 = ff{0.693147182464599609375f, -1.904654323148236017e-09f};
+        const ff ln2 = ln2_ff();
         float lg;
         asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(lg) : "f"(s));
         const ff z = ff_add_f(ff_add_f(ff_mul_f(ln2, m), Lmax), kLn2 * lg);

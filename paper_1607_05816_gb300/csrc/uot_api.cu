@@ -1211,6 +1211,7 @@ struct Check64 {
   }
   // the FP32 path's float-float state -> FP64
   cudaError_t load_state(const double* Uff, const double* Vff, cudaStream_t s) {
+    if (!ready) return cudaErrorInvalidValue;  // setup() first
     count_launches(2);
     k_ff_to_f64<<<nblocks(n * batch), kNT, 0, s>>>(reinterpret_cast<const float2*>(Uff), n * batch, U);
     k_ff_to_f64<<<nblocks(m * batch), kNT, 0, s>>>(reinterpret_cast<const float2*>(Vff), m * batch, V);
@@ -1220,6 +1221,7 @@ struct Check64 {
   // of the state it starts from is accumulated (read it with read_err).
   cudaError_t iterate(const DivParams& D1, const DivParams& D2, double eps, bool check, bool v_update,
                       cudaStream_t s) {
+    if (!ready) return cudaErrorInvalidValue;  // setup() first
     Epilogue e1 = prox_epilogue(D1, logp, U, logdx, check ? acc : nullptr, eps);
     e1.bstride = e1.bstride_p = n;
     cudaError_t e = G.apply(0, V, logdy, eps, e1, s, check ? acc : nullptr);
@@ -1229,6 +1231,7 @@ struct Check64 {
     return G.apply(1, U, logdx, eps, e2, s);
   }
   cudaError_t read_err(double& out, cudaStream_t s) {
+    if (!ready) return cudaErrorInvalidValue;  // setup() first
     cudaError_t e = cudaMemcpyAsync(acc_h.data(), acc, 16 * (size_t)batch, cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) return e;
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
@@ -1712,6 +1715,7 @@ uot_status solve_impl(const uot_geom* g, int batch, const void* p, const void* d
     }
     if (polish) {
       // the FP32 check has reached its rounding floor: FP64 iterations from the current state
+      if (!c64.ready) UOT_CK(c64.setup(*g, batch, p, dx, q, dy, s));
       UOT_CK(c64.load_state(U, V, s));
       while (it < o->max_iter) {
         UOT_CK(c64.iterate(D1, D2, o->eps, true, true, s));

@@ -2,8 +2,9 @@
 //
 // Notation (arXiv:1607.05816): potentials U = eps log a, V = eps log b
 // (Sec. 4.3 with every update absorbed), S = eps log K(b.dy),
-// T = eps log K^T(a.dx).  Per-point state is FP64; the per-entry arithmetic of
-// the Gibbs operator is FP32 or FP64 depending on the requested precision.
+// T = eps log K^T(a.dx).  Per-point state occupies 8-byte slots: a double on
+// the FP64 path, a float-float pair on the FP32 path; the per-entry arithmetic
+// of the Gibbs operator is FP32 or FP64 depending on the requested precision.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -81,6 +82,89 @@ __device__ __forceinline__ bool ff_lt(ff a, ff b) { return a.hi < b.hi || (a.hi 
 __device__ __forceinline__ ff ff_min(ff a, ff b) { return ff_lt(b, a) ? b : a; }
 __device__ __forceinline__ ff ff_max(ff a, ff b) { return ff_lt(a, b) ? b : a; }
 __host__ __device__ constexpr ff ff_ninf() { return ff{-__builtin_huge_valf(), 0.0f}; }
+
+// ln 2 as a float-float pair (hi = the FP32 rounding of ln 2)
+__host__ __device__ constexpr ff ln2_ff() { return ff{0.693147182464599609375f, -1.904654323148236017e-09f}; }
+
+// ---------------------------------------------------------------------------
+// Device helpers shared by the kernel files.
+// ---------------------------------------------------------------------------
+
+// SFU base-2 exponential and logarithm (denormal results flushed to zero).
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float lg2_approx(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Packed FP32 pairs: the f32x2 arithmetic of the sm_100 family.
+typedef unsigned long long f2p;
+__device__ __forceinline__ f2p pk(float a, float b) {
+  f2p r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ float2 upk(f2p r) {
+  float2 v;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
+  return v;
+}
+__device__ __forceinline__ f2p fma2(f2p a, f2p b, f2p c) {
+  f2p d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ f2p add2(f2p a, f2p b) {
+  f2p d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2p sub2(f2p a, f2p b) {
+  f2p d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2p mul2(f2p a, f2p b) {
+  f2p d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+
+__device__ __forceinline__ float warp_maxf(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Programmatic dependent launch: wait until the preceding kernel in the stream
+// has completed and its writes are visible / let the next kernel launch early.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// tcgen05 operands in shared memory.
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+// Shared-memory matrix descriptor, K-major operand without swizzle: core
+// matrices of 8 rows x 16 bytes; lbo = byte step between core matrices along
+// K, sbo = along M/N.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+// byte offset of element (row, k) in a K-major, no-swizzle tile with K = 32
+// bf16 (4 core matrices along K): lbo = 128, sbo = 512
+__device__ __forceinline__ uint32_t tile_off(int row, int k) {
+  return (uint32_t)((row >> 3) * 512 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
+}
 
 // A marginal penalty prepared for the device (Table 1 row + parameters).
 struct DivParams {
