@@ -184,7 +184,9 @@ const char* uot_last_error(void);
  * operator kernel is bracketed by a pair of CUDA events recorded on the stream
  * it is launched on; uot_profile_end synchronises those events and returns the
  * summed kernel time (ms) and the number of launches of one family:
- *   family 0: separable grid passes, family 1: row kernels (dense / points).
+ *   family 0: separable grid passes (log-sum-exp tiles, tensor-core passes),
+ *   family 1: row kernels (dense / points), family 2: separable grid passes run
+ *   by the block-stabilised kernel of uniform axes.
  * Not thread-safe across concurrent solves.
  */
 long long uot_launch_count(void);

@@ -24,7 +24,7 @@
 #include <mutex>
 #include <string>
 
-#include "uot_internal.cuh"
+#include "k_grid_pass.cuh"
 
 namespace uot {
 namespace {
@@ -44,9 +44,6 @@ __device__ __forceinline__ double load_L(const double* __restrict__ in,
   return (v == -kInf) ? -kInf : v * inv_eps + logw[idx];
 }
 
-// ---- packed FP32 pairs (f32x2 arithmetic of sm_100+ family GPUs) ----
-
-
 // FP32 grid pass.  One CTA = one line x (32 * OPL) consecutive outputs; its NW
 // warps split the contraction index j into NW contiguous ranges and combine
 // their partial (max, sum) pairs through shared memory.  Each lane owns OPL
@@ -63,64 +60,6 @@ __device__ __forceinline__ double load_L(const double* __restrict__ in,
 // its outputs with the exact per-range maximum (a max sweep and a sum sweep).
 constexpr int kNW = 8;                    // tile of the persistent solve: warps per CTA
 constexpr int kOutCTA = 128;              // ... and outputs per CTA (4 per lane)
-
-struct PassArgs {
-  const float2* in;    // float-float line values (or potentials when in_is_pot)
-  const float2* logw;  // float-float log weights (in_is_pot only)
-  int in_is_pot;
-  int nlines, nin, nout;
-  const float* yi;
-  const float* xo;
-  float2 inv_eps;      // 1/eps as float-float
-  float k2;            // log2(e)/eps
-  float* zprev;        // [nbatch][nout*nlines] approximate result of the previous call, or NULL
-  int use_prev;
-  double* zero_acc;    // if set, the first block of each batch entry b clears zero_acc[2b..2b+1]
-  int tc3_ok;          // the tensor-core pass (k_grid_tc3.cu) is valid for this pass
-  int* tc_err;         // its bounded-wait flag (may be NULL)
-  int nbatch;
-};
-
-__device__ __forceinline__ ff load_L_ff(const PassArgs& a, const float2* in, int64_t idx) {
-  const ff v = ffl(in[idx]);
-  if (!a.in_is_pot) return v;
-  if (v.hi == -INFINITY) return ff_ninf();
-  return ff_add(ff_mul(v, ffl(a.inv_eps)), ffl(a.logw[idx]));
-}
-
-
-// Programmatic dependent launch: wait until the preceding kernel in the stream
-// has completed and its writes are visible / let the next kernel launch early.
-
-// Operands of the epilogue that do not depend on the preceding kernel, loaded
-// before waiting on it.
-struct EpiPre {
-  float2 uold, lp, lw;
-};
-
-__device__ __forceinline__ void epilogue_prefetch(const Epilogue& e, int64_t b, int64_t pt, EpiPre& o) {
-  if (e.mode == EPI_PROX) {
-    const int64_t q = b * e.bstride + pt;
-    o.uold = reinterpret_cast<const float2*>(e.pot)[q];
-    o.lp = reinterpret_cast<const float2*>(e.logp)[b * e.bstride_p + pt];
-    o.lw = e.err ? reinterpret_cast<const float2*>(e.logw)[pt] : make_float2(0.0f, 0.0f);
-  }
-}
-
-__device__ __forceinline__ void epilogue_apply(const Epilogue& e, int64_t b, int64_t pt, ff z,
-                                               const EpiPre& o, float& num, float& den) {
-  if (e.mode != EPI_PROX) {
-    apply_epilogue_ff(e, b, pt, z, num, den);
-    return;
-  }
-  num = den = 0.0f;
-  const ff eps = ffl(e.eps_ff);
-  ff S = (z.hi == -INFINITY) ? ff_ninf() : ff_mul(z, eps);
-  if (e.zshift) S = ff_zshift(S, e.zshift);
-  const ff Unew = prox_update_ff(e.Fff, ffl(o.lp), S, eps);
-  reinterpret_cast<float2*>(e.pot)[b * e.bstride + pt] = ff2(Unew);
-  if (e.err) violation_terms_ff(ffl(o.uold), Unew, S, ffl(o.lw), ffl(e.inv_eps_ff), num, den);
-}
 
 // Compile-time quantities of a tile shape.
 template <int NW, int OPL>
@@ -847,10 +786,19 @@ struct TileShape {
 };
 // entry 7 stands for the tensor-core pass (k_grid_tc3.cu), used where its
 // block-stabilisation condition holds, entry 8 for the warp-per-line pass of
-// short lines (nin, nout <= 64); where they do not apply the first tile runs
-constexpr TileShape kTiles[] = {{8, 4}, {4, 4}, {2, 4}, {1, 4}, {8, 2}, {4, 2}, {2, 2}, {0, 0}, {0, 0}};
+// short lines (nin, nout <= 64), entries 9-12 for the block-stabilised pass of
+// uniform axes (k_grid_blk.cu); where they do not apply the first tile runs
+constexpr TileShape kTiles[] = {{8, 4}, {4, 4}, {2, 4}, {1, 4}, {8, 2}, {4, 2}, {2, 2},
+                                {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}};
 constexpr int kTc3Tile = 7;
 constexpr int kShortTile = 8;
+constexpr int kBlkTile0 = 9;  // + variant 0..3
+bool is_blk(int t) { return t >= kBlkTile0 && t < kBlkTile0 + 4; }
+int blk_mask(const PassArgs& a) {
+  int m = 0;
+  for (int v = 0; v < grid_blk_variants(); ++v) m |= grid_blk_ok(a, v) ? (1 << v) : 0;
+  return m;
+}
 
 bool short_ok(const PassArgs& a) { return a.nin <= kShortMax && a.nout <= kShortMax; }
 
@@ -902,6 +850,7 @@ cudaError_t launch_f32(int t, const PassArgs& a, const Epilogue& epi, int nbatch
     return launch_grid_pass_tc3(a.in, a.logw, a.in_is_pot, a.nlines, a.nin, a.yi, a.nout, a.xo, a.inv_eps, a.k2,
                                 nbatch, epi, s, a.tc_err, a.zero_acc);
   if (t == kShortTile && short_ok(a)) return launch_f32_short(a, epi, nbatch, s);
+  if (is_blk(t) && grid_blk_ok(a, t - kBlkTile0)) return launch_grid_pass_blk(a, t - kBlkTile0, epi, nbatch, s);
   switch (t) {
     case 0: return launch_f32_tile<8, 4>(a, epi, nbatch, s);
     case 1: return launch_f32_tile<4, 4>(a, epi, nbatch, s);
@@ -915,9 +864,10 @@ cudaError_t launch_f32(int t, const PassArgs& a, const Epilogue& epi, int nbatch
 }
 
 struct TuneKey {
-  int dev, nlines, nin, nout, nbatch, tc3;
+  int dev, nlines, nin, nout, nbatch, tc3, blk;
   bool operator<(const TuneKey& o) const {
     if (tc3 != o.tc3) return tc3 < o.tc3;
+    if (blk != o.blk) return blk < o.blk;
     if (dev != o.dev) return dev < o.dev;
     if (nlines != o.nlines) return nlines < o.nlines;
     if (nin != o.nin) return nin < o.nin;
@@ -988,7 +938,8 @@ TuneEntry tune_tiles(const PassArgs& base, int nbatch, cudaStream_t s) {
     bool wok = step(0, 0) && step(0, 0);
     for (int r = 0; r < kWarm && wok; ++r) wok = step(0, 1);
     for (int t = 0; t < kNumTiles; ++t) {
-      okt[t] = wok && (t != kTc3Tile || base.tc3_ok) && (t != kShortTile || short_ok(base));
+      okt[t] = wok && (t != kTc3Tile || base.tc3_ok) && (t != kShortTile || short_ok(base)) &&
+               (!is_blk(t) || grid_blk_ok(base, t - kBlkTile0));
       tmin[t] = 1e30f;
     }
     for (int round = 0; round < kRounds && wok; ++round) {
@@ -1045,6 +996,7 @@ int pick_tile(const PassArgs& a, int nbatch, cudaStream_t s) {
   key.nout = a.nout;
   key.nbatch = nbatch;
   key.tc3 = a.tc3_ok;
+  key.blk = blk_mask(a);
   auto it = g_tuned.find(key);
   if (it != g_tuned.end()) return it->second.tile;
   if (g_tune_hold) return 0;
@@ -1102,6 +1054,9 @@ std::string grid_tile_table() {
     else if (e.tile == kShortTile)
       snprintf(buf, sizeof(buf), "dev%d lines=%d nin=%d nout=%d batch=%d -> warp per line;", k.dev, k.nlines, k.nin,
                k.nout, k.nbatch);
+    else if (is_blk(e.tile))
+      snprintf(buf, sizeof(buf), "dev%d lines=%d nin=%d nout=%d batch=%d -> block-stabilised %s;", k.dev, k.nlines,
+               k.nin, k.nout, k.nbatch, grid_blk_name(e.tile - kBlkTile0));
     else
       snprintf(buf, sizeof(buf), "dev%d lines=%d nin=%d nout=%d batch=%d -> warps=%d outputs/lane=%d;", k.dev,
                k.nlines, k.nin, k.nout, k.nbatch, kTiles[e.tile].nw, kTiles[e.tile].opl);
@@ -1111,6 +1066,8 @@ std::string grid_tile_table() {
         snprintf(buf, sizeof(buf), " tc3:%.2fus", e.us[t]);
       else if (t == kShortTile)
         snprintf(buf, sizeof(buf), " line:%.2fus", e.us[t]);
+      else if (is_blk(t))
+        snprintf(buf, sizeof(buf), " %s:%.2fus", grid_blk_name(t - kBlkTile0), e.us[t]);
       else
         snprintf(buf, sizeof(buf), " %dx%d:%.2fus", kTiles[t].nw, kTiles[t].opl, e.us[t]);
       s += buf;
@@ -1123,7 +1080,8 @@ std::string grid_tile_table() {
 cudaError_t launch_grid_pass(int prec, const double* in, const double* logw, int in_is_pot,
                              int nlines, int nin, const void* yi, int nout, const void* xo,
                              double eps, int nbatch, const Epilogue& epi, cudaStream_t s,
-                             float* zprev, int use_prev, double* zero_acc, int tc3_ok, int* tc_err) {
+                             float* zprev, int use_prev, double* zero_acc, int tc3_ok, int* tc_err,
+                             const BlkAxis* blk) {
   if (prec == UOT_F32) {
     PassArgs a;
     a.in = reinterpret_cast<const float2*>(in);
@@ -1142,12 +1100,14 @@ cudaError_t launch_grid_pass(int prec, const double* in, const double* logw, int
     a.tc3_ok = (tc3_ok && nin <= grid_pass_tc3_max_nin()) ? 1 : 0;
     a.tc_err = tc_err;
     a.nbatch = nbatch;
+    a.blk = blk ? *blk : BlkAxis{0, 0.0f, 0.0f};
     const int tile = pick_tile(a, nbatch, s);
-    prof_mark_begin(PROF_GRID_PASS, s);
+    const int fam = (is_blk(tile) && grid_blk_ok(a, tile - kBlkTile0)) ? PROF_GRID_BLK : PROF_GRID_PASS;
+    prof_mark_begin(fam, s);
     count_launches(1);
     cudaError_t e = launch_f32(tile, a, epi, nbatch, s);
     if (e != cudaSuccess) return e;
-    prof_mark_end(PROF_GRID_PASS, s);
+    prof_mark_end(fam, s);
     return cudaGetLastError();
   }
   prof_mark_begin(PROF_GRID_PASS, s);

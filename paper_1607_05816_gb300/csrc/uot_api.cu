@@ -40,7 +40,7 @@ struct Prof {
   bool on = false;
   std::vector<cudaEvent_t> pool;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> marks[PROF_NFAM];
-  cudaEvent_t pending[PROF_NFAM] = {nullptr, nullptr};
+  cudaEvent_t pending[PROF_NFAM] = {};
 } g_prof;
 
 bool profiling_on() {
@@ -730,6 +730,10 @@ struct Gibbs {
   double span_x[UOT_MAX_DIM] = {0, 0, 0}, span_y[UOT_MAX_DIM] = {0, 0, 0};
   int* tc_err = nullptr;
   bool spans_known = false;
+  // FP32 grids: uniform-axis data of each (direction, axis) pass for the
+  // block-stabilised kernel; read from the axes at set-up when host_setup
+  BlkAxis blk[2][UOT_MAX_DIM] = {};
+  bool host_setup = true;
   void* Lscratch = nullptr;     // rows: shifted input line
   void* part = nullptr;         // FP32 point clouds: per-chunk partial sums
   float* zrow[2] = {nullptr, nullptr};  // FP32 point clouds: previous results per direction
@@ -829,8 +833,11 @@ struct Gibbs {
         if (!tc_err) return cudaErrorInvalidValue;
         cudaError_t e = cudaMemsetAsync(tc_err, 0, sizeof(int), s);
         if (e != cudaSuccess) return e;
-        // largest coordinate span of the 32-point blocks of every axis (tensor-core passes)
-        if (prec == UOT_MIXED || grid_tc3_wanted()) {
+        // largest coordinate span of the 32-point blocks of every axis
+        // (tensor-core passes), and uniform axes (block-stabilised pass):
+        // both read the axes on the host once
+        const bool want_spans = prec == UOT_MIXED || grid_tc3_wanted();
+        if (want_spans || host_setup) {
           std::vector<float> h[2][UOT_MAX_DIM];
           for (int side = 0; side < 2; ++side)
             for (int k = 0; k < g.ndim; ++k) {
@@ -841,17 +848,43 @@ struct Gibbs {
               if (e != cudaSuccess) return e;
             }
           if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
-          for (int side = 0; side < 2; ++side)
-            for (int k = 0; k < g.ndim; ++k) {
-              const std::vector<float>& v = h[side][k];
-              const int len = (int)v.size();
-              double span = 0.0;
-              for (int i0 = 0; i0 < len; i0 += 32)
-                for (int i = i0; i < std::min(len, i0 + 32); ++i)
-                  span = std::max(span, std::fabs((double)v[i] - (double)v[i0]));
-              (side == 0 ? span_x : span_y)[k] = span;
-            }
-          spans_known = true;
+          if (want_spans) {
+            for (int side = 0; side < 2; ++side)
+              for (int k = 0; k < g.ndim; ++k) {
+                const std::vector<float>& v = h[side][k];
+                const int len = (int)v.size();
+                double span = 0.0;
+                for (int i0 = 0; i0 < len; i0 += 32)
+                  for (int i = i0; i < std::min(len, i0 + 32); ++i)
+                    span = std::max(span, std::fabs((double)v[i] - (double)v[i0]));
+                (side == 0 ? span_x : span_y)[k] = span;
+              }
+            spans_known = true;
+          }
+          if (host_setup) {
+            // axis k of a side is uniform when v[i] = v[0] + i h exactly
+            double step[2][UOT_MAX_DIM];
+            bool uni[2][UOT_MAX_DIM];
+            for (int side = 0; side < 2; ++side)
+              for (int k = 0; k < g.ndim; ++k) {
+                const std::vector<float>& v = h[side][k];
+                uni[side][k] = v.size() >= 2;
+                step[side][k] = uni[side][k] ? (double)v[1] - (double)v[0] : 0.0;
+                for (size_t i = 0; i < v.size() && uni[side][k]; ++i)
+                  uni[side][k] = (double)v[i] == (double)v[0] + (double)i * step[side][k];
+                uni[side][k] = uni[side][k] && step[side][k] > 0.0 &&
+                               (double)(float)step[side][k] == step[side][k];
+              }
+            for (int dir = 0; dir < 2; ++dir)
+              for (int k = 0; k < g.ndim; ++k) {
+                const int in = dir == 0 ? 1 : 0, out = 1 - in;
+                const double d0 = (double)h[out][k][0] - (double)h[in][k][0];
+                BlkAxis& b = blk[dir][k];
+                b.ok = uni[in][k] && uni[out][k] && step[in][k] == step[out][k] && (double)(float)d0 == d0;
+                b.h = (float)step[in][k];
+                b.d0 = (float)d0;
+              }
+          }
         }
       }
     } else {
@@ -935,7 +968,7 @@ struct Gibbs {
           err = launch_grid_pass(prec == UOT_F64 ? UOT_F64 : UOT_F32, cur, logw, cur_is_pot,
                                  (int)nlines, in_shape[ax], in_axes[ax], out_shape[ax],
                                  out_axes[ax], eps, nbatch, e, s, zbuf[dir][k], use_prev, za,
-                                 tc3_ok(dir, ax, eps, in_shape[ax]), tc_err);
+                                 tc3_ok(dir, ax, eps, in_shape[ax]), tc_err, &blk[dir][ax]);
         }
         if (err != cudaSuccess) return err;
         cur = pass[k & 1];
@@ -3295,6 +3328,7 @@ uot_status uot_gibbs_log_noalloc(const uot_geom* g, const void* W, const void* w
   Gibbs G;
   G.g = *g;
   G.prec = precision;
+  G.host_setup = false;  // no read-back of the axes (it would synchronise the stream)
   G.plan(sc, 1);
   sc.reserve<double>(nin);
   sc.reserve<double>(nin);

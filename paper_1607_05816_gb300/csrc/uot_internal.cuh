@@ -445,7 +445,7 @@ __device__ inline void block_add2(double a, double b, double* acc) {
 // operator kernels (on the stream they are launched on)
 // ---------------------------------------------------------------------------
 
-enum ProfFamily { PROF_GRID_PASS = 0, PROF_ROWS = 1, PROF_NFAM = 2 };
+enum ProfFamily { PROF_GRID_PASS = 0, PROF_ROWS = 1, PROF_GRID_BLK = 2, PROF_NFAM = 3 };
 void count_launches(int k);
 void prof_mark_begin(int family, cudaStream_t s);
 void prof_mark_end(int family, cudaStream_t s);
@@ -466,11 +466,20 @@ void prof_mark_end(int family, cudaStream_t s);
 // tc3_ok: the tensor-core pass (k_grid_tc3.cu) may be used (the tuner's last
 // tile) -- its block-stabilisation condition k (span_out + span_in)^2 <= 90
 // holds for 32-point blocks of both axes; tc_err receives its wait flag.
+// Uniform axes of one pass, for the block-stabilised kernel: every output
+// point is xo[0] + i h and every input point yi[0] + j h, exactly, with the
+// same spacing h on both sides.
+struct BlkAxis {
+  int ok;    // both axes uniform with one spacing (and h, d0 exact in FP32)
+  float h;   // the spacing
+  float d0;  // xo[0] - yi[0]
+};
+
 cudaError_t launch_grid_pass(int prec, const double* in, const double* logw, int in_is_pot,
                              int nlines, int nin, const void* yi, int nout, const void* xo,
                              double eps, int nbatch, const Epilogue& epi, cudaStream_t s,
                              float* zprev, int use_prev, double* zero_acc = nullptr, int tc3_ok = 0,
-                             int* tc_err = nullptr);
+                             int* tc_err = nullptr, const BlkAxis* blk = nullptr);
 
 // The tensor-core pass with three-part BF16 operands (k_grid_tc3.cu): same
 // result as the FP32 pass to FP32 accuracy; nin <= grid_pass_tc3_max_nin().

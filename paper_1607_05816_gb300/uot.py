@@ -227,7 +227,7 @@ def autotune_table() -> str:
     return buf.value.decode()
 
 
-PROF_GRID_PASS, PROF_ROWS = 0, 1
+PROF_GRID_PASS, PROF_ROWS, PROF_GRID_BLK = 0, 1, 2
 
 
 def profile_begin():
