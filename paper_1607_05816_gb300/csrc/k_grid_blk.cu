@@ -34,10 +34,14 @@
 // log-sum-exp tiles of k_grid.cu.
 //
 // Layout: a CTA = 4 lines x one output block I; its JS warps split the input
-// blocks and merge their (max, sum) pairs at the end.  A lane owns one output
-// of the block for the CTA's 4 lines; G(lane - jj + const) for the BJ inputs
-// of a block sits in registers (the same values for every block pair), and
-// the A values of a block are broadcast from shared memory, 4 lines per load.
+// blocks and merge their (max, sum) pairs at the end, and the 4 x 32 results
+// are finished (epilogue) by warps 0..3, one line each.  A lane owns one
+// output of the block for the CTA's 4 lines; G(lane - jj + const) for the BJ
+// inputs of a block sits in registers (the same values for every block
+// pair), and the A values of a block are broadcast from shared memory, 4
+// lines per load.  At these sizes a pass is latency-bound (one wave of CTAs,
+// each a chain load -> stage -> products -> merge -> epilogue), so more warps
+// per CTA mean shorter chains.
 #include <string.h>
 
 #include <algorithm>
@@ -62,7 +66,7 @@ __host__ __device__ constexpr int blk_dmax() {
 }
 
 template <int BJ, int JS>
-__global__ void __launch_bounds__(JS * 32) grid_pass_blk(BlkArgs ba, Epilogue epi) {
+__global__ void __launch_bounds__(JS * 32, 16 / JS) grid_pass_blk(BlkArgs ba, Epilogue epi) {
   constexpr int NT = JS * 32;
   constexpr int DOFF = (BJ - kBI) / 2;  // ic - jc = i_loc - j_loc + DOFF
   constexpr int Q = BJ / 32;            // inputs per lane in the A generation
@@ -86,13 +90,13 @@ __global__ void __launch_bounds__(JS * 32) grid_pass_blk(BlkArgs ba, Epilogue ep
   for (int k = tid; k <= blk_dmax<BJ>(); k += NT) sg[k] = ba.g[k];
   const int i = I * kBI + lane;
   const bool iok = i < nout;
-  // this warp finishes lines (kLW / JS) * warp ... of the CTA
-  constexpr int LPW = kLW / JS;
+  // warp w finishes lines w, w + JS, ... of the CTA
+  constexpr int LPW = (kLW + JS - 1) / JS;
   EpiPre pre[LPW];
 #pragma unroll
-  for (int r = 0; r < LPW; ++r) {
-    const int l = l0 + warp * LPW + r;
-    if (iok && l < nlines) epilogue_prefetch(epi, bz, (int64_t)i * nlines + l, pre[r]);
+  for (int rr = 0; rr < LPW; ++rr) {
+    const int r = warp + JS * rr, l = l0 + r;
+    if (r < kLW && iok && l < nlines) epilogue_prefetch(epi, bz, (int64_t)i * nlines + l, pre[rr]);
   }
   __syncthreads();
   float G[BJ];
@@ -109,19 +113,41 @@ __global__ void __launch_bounds__(JS * 32) grid_pass_blk(BlkArgs ba, Epilogue ep
   // ---- the CTA's lines: float-float values, line maxima, t relative to them ----
   const float2* in = a.in + bz * (int64_t)nlines * nin;
   float lmax[kLW];
+  {
+    // all of a thread's loads are issued before any is used (one L2 round trip)
+    constexpr int kB = 4;
+    float mx[kLW];
 #pragma unroll
-  for (int r = 0; r < kLW; ++r) {
-    const int l = l0 + r;
-    float mx = -INFINITY;
-    for (int j = tid; j < ninp; j += NT) {
-      ff v = ff_ninf();
-      if (l < nlines && j < nin) v = load_L_ff(a, in, (int64_t)l * nin + j);
-      st[r * ninp + j] = v.hi;
-      slo[r * ninp + j] = v.lo;
-      mx = fmaxf(mx, v.hi);
+    for (int r = 0; r < kLW; ++r) mx[r] = -INFINITY;
+    for (int j0 = tid; j0 < ninp; j0 += kB * NT) {
+      float2 raw[kLW][kB];
+#pragma unroll
+      for (int r = 0; r < kLW; ++r)
+#pragma unroll
+        for (int b = 0; b < kB; ++b) {
+          const int j = j0 + b * NT, l = l0 + r;
+          raw[r][b] = (l < nlines && j < nin) ? in[(int64_t)l * nin + j] : make_float2(-INFINITY, 0.0f);
+        }
+#pragma unroll
+      for (int r = 0; r < kLW; ++r)
+#pragma unroll
+        for (int b = 0; b < kB; ++b) {
+          const int j = j0 + b * NT, l = l0 + r;
+          if (j >= ninp) continue;
+          ff v = ffl(raw[r][b]);
+          if (a.in_is_pot && l < nlines && j < nin)
+            v = (v.hi == -INFINITY) ? ff_ninf()
+                                    : ff_add(ff_mul(v, ffl(a.inv_eps)), ffl(a.logw[(int64_t)l * nin + j]));
+          st[r * ninp + j] = v.hi;
+          slo[r * ninp + j] = v.lo;
+          mx[r] = fmaxf(mx[r], v.hi);
+        }
     }
-    lmax[r] = warp_maxf(mx);
-    if (lane == 0) sred[r][warp] = lmax[r];
+#pragma unroll
+    for (int r = 0; r < kLW; ++r) {
+      lmax[r] = warp_maxf(mx[r]);
+      if (lane == 0) sred[r][warp] = lmax[r];
+    }
   }
   __syncthreads();
 #pragma unroll
@@ -198,7 +224,7 @@ __global__ void __launch_bounds__(JS * 32) grid_pass_blk(BlkArgs ba, Epilogue ep
     }
   }
 
-  // ---- merge the warps' pairs; warp w finishes lines w*LPW .. w*LPW+LPW-1 ----
+  // ---- merge the warps' pairs; warp w finishes lines w, w + JS, ... ----
   if (JS > 1) {
 #pragma unroll
     for (int r = 0; r < kLW; ++r) sx[warp][r][lane] = make_float2(R[r], S[r]);
@@ -207,7 +233,8 @@ __global__ void __launch_bounds__(JS * 32) grid_pass_blk(BlkArgs ba, Epilogue ep
   float num = 0.0f, den = 0.0f;
 #pragma unroll
   for (int rr = 0; rr < LPW; ++rr) {
-    const int r = warp * LPW + rr;
+    const int r = warp + JS * rr;
+    if (r >= kLW) break;
     const int l = l0 + r;
     float Rm = R[r], Sm = S[r];
     if (JS > 1) {
@@ -269,15 +296,18 @@ cudaError_t launch_blk(const BlkArgs& ba, const Epilogue& epi, int nbatch, cudaS
   return cudaLaunchKernelEx(&cfg, grid_pass_blk<BJ, JS>, ba, epi);
 }
 
-int variant_bj(int v) { return (v & 2) ? 64 : 32; }
+// (input block, warps per CTA) of each variant
+constexpr int kVariants[][2] = {{32, 2}, {32, 4}, {32, 8}, {64, 2}, {64, 4}};
+constexpr int kNumVariants = (int)(sizeof(kVariants) / sizeof(kVariants[0]));
+int variant_bj(int v) { return kVariants[v][0]; }
 
 }  // namespace
 
-int grid_blk_variants() { return 4; }
+int grid_blk_variants() { return kNumVariants; }
 
-// Variant v: input blocks of 32 (v = 0, 1) or 64 (v = 2, 3) points, split
-// over 1 (even v) or 2 (odd v) warps.
+// Variant v: input blocks of kVariants[v][0] points, kVariants[v][1] warps per CTA.
 bool grid_blk_ok(const PassArgs& a, int v) {
+  if (v < 0 || v >= kNumVariants) return false;
   // staging: 2 x 4 lines x nin floats of shared memory (<= 128 KB)
   if (!a.blk.ok || a.nin < 2 || a.nout < 1 || a.nin > 4096) return false;
   const double dmax = (kBI + variant_bj(v)) / 2 - 1;
@@ -286,8 +316,8 @@ bool grid_blk_ok(const PassArgs& a, int v) {
 }
 
 const char* grid_blk_name(int v) {
-  static const char* names[] = {"blk32x1", "blk32x2", "blk64x1", "blk64x2"};
-  return names[v & 3];
+  static const char* names[] = {"blk32x2", "blk32x4", "blk32x8", "blk64x2", "blk64x4"};
+  return (v >= 0 && v < kNumVariants) ? names[v] : "blk?";
 }
 
 cudaError_t launch_grid_pass_blk(const PassArgs& a, int v, const Epilogue& epi, int nbatch, cudaStream_t s) {
@@ -299,11 +329,12 @@ cudaError_t launch_grid_pass_blk(const PassArgs& a, int v, const Epilogue& epi, 
   const double k2 = (double)a.k2, h = (double)a.blk.h;
   const int dmax = (kBI + variant_bj(v)) / 2 - 1;
   for (int d = 0; d <= dmax; ++d) ba.g[d] = (float)exp2(-k2 * h * h * (double)d * (double)d);
-  switch (v & 3) {
-    case 0: return launch_blk<32, 1>(ba, epi, nbatch, s);
-    case 1: return launch_blk<32, 2>(ba, epi, nbatch, s);
-    case 2: return launch_blk<64, 1>(ba, epi, nbatch, s);
-    default: return launch_blk<64, 2>(ba, epi, nbatch, s);
+  switch (v) {
+    case 0: return launch_blk<32, 2>(ba, epi, nbatch, s);
+    case 1: return launch_blk<32, 4>(ba, epi, nbatch, s);
+    case 2: return launch_blk<32, 8>(ba, epi, nbatch, s);
+    case 3: return launch_blk<64, 2>(ba, epi, nbatch, s);
+    default: return launch_blk<64, 4>(ba, epi, nbatch, s);
   }
 }
 

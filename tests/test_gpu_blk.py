@@ -19,7 +19,7 @@ from test_gpu_parity import rel_err, round_geom, rounded, T, to_np
 pytestmark = [pytest.mark.gpu, pytest.mark.filterwarnings("ignore::RuntimeWarning")]
 
 TOL = 1e-5
-BLK_TILES = [9, 10, 11, 12]  # blk32x1, blk32x2, blk64x1, blk64x2
+BLK_TILES = [9, 10, 11, 12, 13]  # blk32x2, blk32x4, blk32x8, blk64x2, blk64x4
 
 
 def uniform_axis(n, h, first):

@@ -429,7 +429,7 @@ def test_persistent_launch_matches_per_pass_launches(shape):
 # FP32 grid-pass tile shapes and the tuner
 # ----------------------------------------------------------------------------
 
-@pytest.mark.parametrize("tile", range(13))
+@pytest.mark.parametrize("tile", range(14))
 @pytest.mark.parametrize("name,make", GIBBS_CASES[:3])
 def test_every_grid_tile_matches_oracle(tile, name, make):
     """Every tile shape the tuner may pick computes the operator and a short
@@ -437,10 +437,10 @@ def test_every_grid_tile_matches_oracle(tile, name, make):
     Tile 7 is the tensor-core pass, which these coarse grids at eps = 0.01
     do not admit (the SIMT tile runs instead); tile 8 is the warp-per-line
     pass, which runs where lines and outputs are at most 64 long (every pass
-    of the 3-D case, some of the 2-D one); tiles 9-12 are the block-stabilised
+    of the 3-D case, some of the 2-D one); tiles 9-13 are the block-stabilised
     pass of uniform axes, which these cell-centre axes (not x0 + i h exactly
     in FP32 for 300 or 45 points) do not admit (tests/test_gpu_blk.py covers it)."""
-    assert U.grid_tile_count() == 13
+    assert U.grid_tile_count() == 14
     og, lg, dx, dy, p, q = make()
     g = synth.rng(19)
     eps = 0.01
@@ -520,11 +520,13 @@ def test_autotuner_records_choice_and_keeps_parity():
         lines = [ln for ln in table.splitlines() if "nin=79 nout=83" in ln and "lines=61" in ln]
         assert len(lines) == 1, table
         times = [float(t.split(":")[1][:-2]) for t in lines[0].split(";")[1].split()]
-        assert len(times) == 9 and all(t > 0 for t in times[:7])
-        times = [t if t > 0 else math.inf for t in times]  # tc3 and short lines not admitted on this grid
+        assert len(times) == 14 and all(t > 0 for t in times[:7])
+        # tc3, short lines and the block pass (cell-centre axes of 83 and 79 points) not admitted
+        times = [t if t > 0 else math.inf for t in times]
         chosen = lines[0].split("-> ")[1].split(";")[0]
         names = ["warps=%d outputs/lane=%d" % sh for sh in [(8, 4), (4, 4), (2, 4), (1, 4), (8, 2), (4, 2), (2, 2)]]
         names += ["tensor-core tc3", "warp per line"]
+        names += ["block-stabilised " + v for v in ("blk32x2", "blk32x4", "blk32x8", "blk64x2", "blk64x4")]
         k = names.index(chosen)
         tb = min(times)
         tick = 0.011  # the table prints times to 0.01 us: ties at that precision may go either way
