@@ -902,7 +902,7 @@ TuneEntry tune_tiles(const PassArgs& base, int nbatch, cudaStream_t s) {
   float2* buf[2] = {nullptr, nullptr};
   float* z[2] = {nullptr, nullptr};
   // the prox epilogue's arrays (potential, log density, log weight) and violation accumulators
-  const size_t npt = (size_t)nbatch * base.nlines * base.nout;
+  const size_t npt = (size_t)nbatch * base.nlines * (size_t)std::max(base.nin, base.nout);
   float2* pro[3] = {nullptr, nullptr, nullptr};
   double* acc = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -949,6 +949,8 @@ TuneEntry tune_tiles(const PassArgs& base, int nbatch, cudaStream_t s) {
     ep.logw = reinterpret_cast<const double*>(pro[2]);
     ep.err = acc;
     ep.bstride = ep.bstride_p = (int64_t)base.nlines * base.nout;
+    // The chain alternates a solve's first pass (potentials in, raw
+    // intermediate out) and last pass (intermediate in, prox epilogue out).
     int cur = 0, parity = 0;
     auto step = [&](int t, int use_prev) -> bool {
       a.in = buf[cur];
@@ -956,10 +958,14 @@ TuneEntry tune_tiles(const PassArgs& base, int nbatch, cudaStream_t s) {
       a.use_prev = use_prev;
       parity ^= 1;
       if (parity) {
+        a.in_is_pot = 1;
+        a.logw = pro[2];
         e.out = reinterpret_cast<double*>(buf[cur ^ 1]);
         cur ^= 1;
         return launch_f32(t, a, e, nbatch, s) == cudaSuccess;
       }
+      a.in_is_pot = 0;
+      a.logw = nullptr;
       return launch_f32(t, a, ep, nbatch, s) == cudaSuccess;
     };
     // Warm-up (brings the SM clock up before anything is timed; both shift
