@@ -391,7 +391,7 @@ def run_ours(args, rank, world, local_rank):
         * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e9)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_iters, args.mass_div)
-    print(json.dumps(line), flush=True)
+    return line
 
 
 # ----------------------------------------------------------------------------
@@ -570,7 +570,7 @@ def run_single(args, rank, world, local_rank):
         line["roofline"] = {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": FP64_PEAK_GFLOPS,
                             "unit": unit_work, "frac": achieved / FP64_PEAK_GFLOPS, "traffic": None,
                             "timing": timing}
-    print(json.dumps(line), flush=True)
+    return line
 
 
 # ----------------------------------------------------------------------------
@@ -652,7 +652,7 @@ def run_batch(args, rank, world, local_rank):
                                  "exponentials of all problems' iterations / CUDA-event time of the launch"),
         "tuned": uot.autotune_table().strip().splitlines(),
     }
-    print(json.dumps(line), flush=True)
+    return line
 
 
 # ----------------------------------------------------------------------------
@@ -708,6 +708,295 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------
+# the oracle on the host cores for every configuration: one core, and all the
+# host's cores (worker processes started with spawn, each computing a block of
+# output rows of the Gibbs operator; one BLAS thread per worker)
+# ----------------------------------------------------------------------------
+
+_WORKER = {}
+
+
+def _oracle_worker_init(data):
+    _WORKER.clear()
+    _WORKER.update(data)
+
+
+def _oracle_rows(task):
+    """eps log K(e^{W/eps} w) on the output rows [r0, r1) of one direction.
+    grid: rows of the first axis of the output grid; points, dense: rows."""
+    import oracle as O
+    side, r0, r1, W, logw, eps = task
+    kind = _WORKER["kind"]
+    if kind == "grid":
+        out_axes = list(_WORKER["ys"] if side else _WORKER["xs"])
+        in_axes = _WORKER["xs"] if side else _WORKER["ys"]
+        out_axes[0] = out_axes[0][r0:r1]
+        g = O.Geometry("grid", xs=out_axes, ys=in_axes)
+        return O.apply_K_log(g, W, logw, eps)
+    if kind == "points":
+        xo = (_WORKER["y"] if side else _WORKER["x"])[r0:r1]
+        xi = _WORKER["x"] if side else _WORKER["y"]
+        return O.apply_K_points_streamed(xo, xi, W, logw, eps)
+    C = _WORKER["C"]
+    Cs = (C.T if side else C)[r0:r1]
+    return O.apply_K_log(O.Geometry("dense", C=Cs), W, logw, eps)
+
+
+def _oracle_problems(task):
+    """n_iter log-domain iterations of each listed batch problem (KL, KL)."""
+    import oracle as O
+    idx, n_iter, eps = task
+    t0 = time.perf_counter()
+    for k in idx:
+        pr = _WORKER["probs"][k]
+        g = O.Geometry("points", x=pr["x"], y=pr["y"])
+        logs = tuple(O.safe_log(pr[key]) for key in ("dx", "dy", "p", "q"))
+        O.iterate_log(g, *logs, O.KL(pr["lam"]), O.KL(pr["lam"]), eps, n_iter)
+    return time.perf_counter() - t0
+
+
+def _oracle_alg1(task):
+    import oracle as O
+    K, dx, dy, p, q, lam, eps, iters = task
+    t0 = time.perf_counter()
+    O.scaling_alg1(K, dx, dy, p, q, O.KL(lam), O.KL(lam), eps, iters)
+    return time.perf_counter() - t0
+
+
+class OraclePool:
+    """`cores` spawned worker processes with one BLAS/OpenMP thread each."""
+
+    def __init__(self, cores, data, blas_threads=1):
+        import multiprocessing as mp
+        env = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+        old = {k: os.environ.get(k) for k in env}
+        for k in env:
+            os.environ[k] = str(blas_threads)
+        try:
+            self.pool = mp.get_context("spawn").Pool(cores, initializer=_oracle_worker_init, initargs=(data,))
+        finally:
+            for k, v in old.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+        self.cores = cores
+        self.pool.map(abs, range(cores))  # workers up before anything is timed
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def _split(n, parts):
+    b = [(n * k) // parts for k in range(parts + 1)]
+    return [(b[k], b[k + 1]) for k in range(parts) if b[k + 1] > b[k]]
+
+
+def _oracle_log_iterations(pool, n_rows, shape_p, shape_q, logs, F1, F2, eps, n_iter):
+    """n_iter oracle iterations (log domain) with both operators split by
+    output rows over the pool; returns seconds."""
+    import oracle as O
+    logdx, logdy, logp, logq = logs
+    U = np.zeros(shape_p)
+    V = np.zeros(shape_q)
+    nx, ny = n_rows
+    t0 = time.perf_counter()
+    for _ in range(n_iter):
+        parts = pool.pool.map(_oracle_rows, [(0, a, b, V, logdy, eps) for a, b in _split(nx, pool.cores)])
+        S = np.concatenate(parts, axis=0).reshape(shape_p)
+        U = O.prox_update_log(F1, logp, S, eps)
+        parts = pool.pool.map(_oracle_rows, [(1, a, b, U, logdx, eps) for a, b in _split(ny, pool.cores)])
+        T = np.concatenate(parts, axis=0).reshape(shape_q)
+        V = O.prox_update_log(F2, logq, T, eps)
+    return time.perf_counter() - t0
+
+
+def oracle_baselines(name, cores_all, one_core=True):
+    """The oracle on one core and on `cores_all` cores for workload `name`, in
+    the workload's metric (iterations per second; problem-iterations per
+    second for the batch).  Each measurement is a bounded sample (stated)."""
+    import oracle as O
+    from paper_1607_05816_gb300 import synth
+    out = {}
+    for cores in ((1, cores_all) if one_core else (cores_all,)):
+        label = "one_core" if cores == 1 else "all_cores"
+        if name in ("grid2d", "grid2d_f64", "warmstart"):
+            if name == "warmstart":
+                inst = synth.warmstart_instances(1, 64, 64, seed=1239 + 7)
+                xs = inst["xs"]
+                p_, q_, dx_ = inst["P"][0], inst["Q"][0], inst["dx"]
+                e, lam = float(inst["eps"][0]), float(inst["lam"][0])
+                n_iter = 40 if cores == 1 else 80
+                sample = f"{n_iter} cold-start iterations of one 64x64 instance (eps {e:.3g}, lambda {lam:.3g})"
+            else:
+                d = inputs(SEED)
+                xs, p_, q_, dx_ = d["xs"], d["p"], d["q"], d["dx"]
+                e, lam = EPS, LAM
+                n_iter = 4 if cores == 1 else 16
+                sample = f"{n_iter} iterations of the 256x256 grid problem at eps = 1e-3"
+            pool = OraclePool(cores, {"kind": "grid", "xs": xs, "ys": xs})
+            try:
+                logs = tuple(O.safe_log(a) for a in (dx_, dx_, p_, q_))
+                sec = _oracle_log_iterations(pool, (len(xs[0]), len(xs[0])), np.shape(p_), np.shape(q_), logs,
+                                             O.KL(lam), O.KL(lam), e, n_iter)
+            finally:
+                pool.close()
+            out[label] = {"value": n_iter / sec, "unit": "iters/s", "cores": cores, "kind": "oracle",
+                          "sample": sample, "seconds": sec}
+        elif name in ("points_kl", "points_tv"):
+            d = synth.problem_points(20000, 20000, 3, seed=1236)
+            F = O.TV(0.1) if name == "points_tv" else O.KL(0.1)
+            pool = OraclePool(cores, {"kind": "points", "x": d["x"], "y": d["y"]})
+            try:
+                logs = tuple(O.safe_log(d[k]) for k in ("dx", "dy", "p", "q"))
+                if cores == 1:
+                    # output rows [0, 1000) of one half-step, scaled to both half-steps
+                    t0 = time.perf_counter()
+                    pool.pool.map(_oracle_rows, [(0, 0, 1000, np.zeros(20000), logs[1], 1e-3)])
+                    sec = (time.perf_counter() - t0) * 2 * 20000 / 1000
+                    sample = "1000 of 20000 output rows of one half-step at eps = 1e-3, scaled x40 to an iteration"
+                else:
+                    sec = _oracle_log_iterations(pool, (20000, 20000), (20000,), (20000,), logs, F, F, 1e-3, 1)
+                    sample = "1 iteration of the 20000 x 20000 problem at eps = 1e-3"
+            finally:
+                pool.close()
+            out[label] = {"value": 1.0 / sec, "unit": "iters/s", "cores": cores, "kind": "oracle",
+                          "sample": sample, "seconds_per_iter": sec}
+        elif name == "dense1d":
+            d = synth.problem_1d(256, 256, seed=1234)
+            K = np.exp(-(d["x"][:, None] - d["y"][None, :]) ** 2 / 1e-2)
+            pool = OraclePool(1, {}, blas_threads=cores)
+            try:
+                n_iter = 2000
+                sec = pool.pool.apply(_oracle_alg1, ((K, d["dx"], d["dy"], d["p"], d["q"], 1.0, 1e-2, n_iter),))
+            finally:
+                pool.close()
+            out[label] = {"value": n_iter / sec, "unit": "iters/s", "cores": cores, "kind": "oracle",
+                          "sample": f"Algorithm 1 verbatim, {n_iter} iterations (numpy matrix-vector products"
+                                    f" with {cores} BLAS thread{'s' if cores > 1 else ''})", "seconds": sec}
+        elif name == "batch":
+            probs = synth.batch_points(nprob=BATCH_NPROB, size=BATCH_SIZE, d=2, seed=1238)
+            nm = np.array([len(pr["x"]) * len(pr["y"]) for pr in probs], dtype=np.float64)
+            order = np.argsort(nm)
+            sample_idx = [int(k) for k in order[::64]]  # 64 problems spread over the sizes
+            pool = OraclePool(cores, {"probs": [probs[k] for k in sample_idx]})
+            try:
+                n_iter = 1
+                t0 = time.perf_counter()
+                pool.pool.map(_oracle_problems, [(list(range(a, b)), n_iter, BATCH_EPS)
+                                                 for a, b in _split(len(sample_idx), cores)])
+                sec = time.perf_counter() - t0
+            finally:
+                pool.close()
+            # scaled by sum n m: problem-iterations per second of the whole batch's mix
+            rate = n_iter * float(nm[sample_idx].sum()) / sec / float(nm.mean())
+            out[label] = {"value": rate, "unit": "problem-iters/s", "cores": cores, "kind": "oracle",
+                          "sample": f"{n_iter} iterations of 64 of the 4096 problems (every 64th by size), "
+                                    f"scaled by sum n m", "seconds": sec}
+        elif name == "bary":
+            b = synth.barycenter_images(32, 128, 128, seed=1237)
+            pool = OraclePool(cores, {"kind": "grid", "xs": b["xs"], "ys": b["ys"]})
+            try:
+                n_iter = 1 if cores == 1 else 2
+                sec = _oracle_bary_iterations(pool, b, n_iter)
+            finally:
+                pool.close()
+            out[label] = {"value": n_iter / sec, "unit": "iters/s", "cores": cores, "kind": "oracle",
+                          "sample": f"{n_iter} KL-barycenter iteration(s) of the 32 x 128 x 128 workload",
+                          "seconds": sec}
+    return out
+
+
+def _oracle_bary_iterations(pool, b, n_iter):
+    """Barycenter iterations (Sec. 5.2, Table 2 KL) with every measure's
+    operator split by output rows over the pool."""
+    import oracle as O
+    P = np.asarray(b["P"], dtype=np.float64)
+    K = P.shape[0]
+    logdx, logdy, logP = O.safe_log(b["dx"]), O.safe_log(b["dy"]), O.safe_log(P)
+    alpha = np.full(K, 1.0 / K)
+    eps, lam = 1e-2, 1.0
+    U = np.zeros_like(P)
+    V = np.zeros_like(P)
+    H = P.shape[1]
+    t0 = time.perf_counter()
+    for _ in range(n_iter):
+        tasks = [(0, a, c, V[k], logdy, eps) for k in range(K) for a, c in _split(H, pool.cores)]
+        parts = pool.pool.map(_oracle_rows, tasks)
+        per = len(parts) // K
+        for k in range(K):
+            U[k] = O.prox_update_log(O.EQ(), logP[k], np.concatenate(parts[k * per:(k + 1) * per], 0), eps)
+        tasks = [(1, a, c, U[k], logdx, eps) for k in range(K) for a, c in _split(H, pool.cores)]
+        parts = pool.pool.map(_oracle_rows, tasks)
+        T = np.stack([np.concatenate(parts[k * per:(k + 1) * per], 0) for k in range(K)])
+        logh = O.bary_h_log(T, alpha, lam, eps, "kl") / eps
+        for k in range(K):
+            V[k] = O.prox_update_log(O.KL(lam), logh, T[k], eps)
+    return time.perf_counter() - t0
+
+
+def _compact(line, cpu):
+    """The figures of a workload line that the sub-record keeps."""
+    r = line.get("roofline") or {}
+    d = {"value": line["value"], "unit": line["unit"], "time_to_tol_ms": line.get("time_to_tol_ms",
+         line.get("ms_per_step")), "ms_per_step": line["ms_per_step"], "iters_per_step": line.get("iters_per_step"),
+         "final_marg_err": line.get("final_marg_err"), "dtype": line["dtype"], "config": line["config"],
+         "clocks": line.get("clocks"), "gpu_launches": line.get("gpu_launches"),
+         "roofline": {k: r.get(k) for k in ("bound", "kernel", "achieved", "peak", "unit", "frac", "traffic")}}
+    for k in ("stop", "warm_start"):
+        if k in line:
+            d[k] = line[k]
+    if cpu:
+        d["cpu_baseline"] = cpu
+    return d
+
+
+def sub_workloads(args, local_rank, cpu=True):
+    """Every configuration besides the headline, each as a bounded run (1
+    warm-up step, 2 timed steps; FP64 grid: 1 timed step) with its oracle
+    baselines on one core and on all host cores."""
+    import copy
+    import torch
+    cores = host_cores()
+    subs = [
+        ("dense1d", dict(workload="dense1d", launch_mode=1)),
+        ("grid2d_f64", dict(workload="grid2d", precision="f64", steps=1)),
+        ("points_kl", dict(workload="points", penalty="kl")),
+        ("points_tv", dict(workload="points", penalty="tv")),
+        ("batch", dict(workload="batch")),
+        ("bary", dict(workload="bary")),
+    ]
+    res = {"host_cores": cores}
+    for name, over in subs:
+        a = copy.copy(args)
+        a.steps, a.warmup, a.no_e2e, a.no_cpu_baseline, a.grid_tile = 2, 1, True, True, -1
+        a.launch_mode = 2
+        for k, v in over.items():
+            setattr(a, k, v)
+        try:
+            if a.workload == "batch":
+                line = run_batch(a, 0, 1, local_rank)
+            elif a.workload == "grid2d":
+                line = run_ours(a, 0, 1, local_rank)
+            else:
+                line = run_single(a, 0, 1, local_rank)
+            torch.cuda.synchronize()
+            base = oracle_baselines(name, cores) if cpu else None
+            res[name] = _compact(line, base)
+        except Exception as e:  # a failed sub-run is reported, not hidden
+            res[name] = {"error": f"{type(e).__name__}: {e}"}
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -735,6 +1024,8 @@ def main():
                     help="barycenter divergence of the bary workload (Table 2 (ii), (iii), (iv))")
     ap.add_argument("--mass-div", default=None, choices=sorted(MASS_DIVS),
                     help="grid2d workload through Algorithm 4 with this divergence on the plan's total mass")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="grid2d: skip the other configurations' sub-record")
     ap.add_argument("--grid-tile", type=int, default=-1,
                     help="force one FP32 grid-pass tile shape (default: the tuner's choice)")
     args = ap.parse_args()
@@ -749,11 +1040,20 @@ def main():
         dist.init_process_group("nccl")
     try:
         if args.workload == "batch":
-            run_batch(args, rank, world, local_rank)
+            line = run_batch(args, rank, world, local_rank)
         elif args.workload in ("points", "dense1d", "bary", "wf", "color"):
-            run_single(args, rank, world, local_rank)
+            line = run_single(args, rank, world, local_rank)
         else:
-            run_ours(args, rank, world, local_rank)
+            line = run_ours(args, rank, world, local_rank)
+            # every other configuration, measured in the same run (one GPU only)
+            if world == 1 and line is not None and not args.no_workloads and not args.mass_div \
+                    and args.precision == "f32" and not args.max_iter and not args.no_eps_scaling:
+                line["workloads"] = sub_workloads(args, local_rank, cpu=not args.no_cpu_baseline)
+                if not args.no_cpu_baseline:
+                    line["cpu_baseline_all_cores"] = oracle_baselines("grid2d", host_cores(),
+                                                                      one_core=False)["all_cores"]
+        if line is not None:
+            print(json.dumps(line), flush=True)
     finally:
         if world > 1:
             import torch.distributed as dist
