@@ -101,11 +101,16 @@ typedef struct {
 
 /*
  * UOT_MIXED: as UOT_F32 (float arrays, float-float per-point state), but on
- * grids each separable pass runs on the tensor cores (tcgen05, BF16 operands,
+ * grids the separable passes run on the tensor cores (tcgen05, BF16 operands,
  * FP32 accumulation) in a block-stabilised form that needs about a tenth of
  * the exponentials; results carry the BF16 operand rounding (relative error of
  * the kernel sums ~2^-8).  Grid axes whose 32-point blocks are too wide for
  * that form at the given eps, and non-grid geometries, use the FP32 kernels.
+ * In uot_solve / uot_solve_many with tol > 0 the tensor-core passes run through
+ * the eps-scaling stages and at the final eps until the marginal violation
+ * falls to uot_opts.mixed_switch (or stops improving: the BF16 floor); the
+ * remaining iterations use the FP32 passes, to tol.  With uot_opts.verify the
+ * stop is then confirmed in FP64: BF16, then FP32, then FP64 for the check.
  */
 typedef enum { UOT_F64 = 0, UOT_F32 = 1, UOT_MIXED = 2 } uot_precision;
 
@@ -157,6 +162,8 @@ typedef struct {
                           state, checked every iteration, until the FP64 violation is
                           <= tol.  marg_err is then the FP64 value.  Launch modes 1 and 3
                           run as 2.  0: the FP32 check decides. */
+  double mixed_switch; /* UOT_MIXED with tol > 0: violation at which the tensor-core (BF16)
+                          passes hand over to the FP32 passes; 0 means 1e-3 */
 } uot_opts;
 
 typedef struct {
@@ -168,6 +175,7 @@ typedef struct {
   int verifications;    /* FP64 confirmations run (opts.verify) */
   int polish_iters;     /* iterations run in FP64 after the FP32 floor (opts.verify) */
   double marg_err_fp32; /* last FP32-evaluated violation (NaN if none) */
+  int mixed_iters;      /* UOT_MIXED: iterations (stages included) run with the tensor-core passes */
 } uot_result;
 
 /* Version string of the library build. */

@@ -734,6 +734,8 @@ struct Gibbs {
   // block-stabilised kernel; read from the axes at set-up when host_setup
   BlkAxis blk[2][UOT_MAX_DIM] = {};
   bool host_setup = true;
+  // UOT_MIXED: once set, the passes run on the FP32 kernels (end of the BF16 phase)
+  bool tc_off = false;
   void* Lscratch = nullptr;     // rows: shifted input line
   void* part = nullptr;         // FP32 point clouds: per-chunk partial sums
   float* zrow[2] = {nullptr, nullptr};  // FP32 point clouds: previous results per direction
@@ -755,7 +757,7 @@ struct Gibbs {
         sc.reserve<double>((size_t)inter * nbatch);
         sc.reserve<double>((size_t)inter * nbatch);
       }
-      if (speculate && prec == UOT_F32)
+      if (speculate && (prec == UOT_F32 || prec == UOT_MIXED))
         for (int k = 0; k < 2 * g.ndim; ++k) sc.reserve<float>((size_t)inter * nbatch);
       if (prec == UOT_MIXED || prec == UOT_F32) sc.reserve<int>(1);
     } else {
@@ -825,7 +827,7 @@ struct Gibbs {
         pass[0] = sc.take<double>((size_t)inter * nbatch);
         pass[1] = sc.take<double>((size_t)inter * nbatch);
       }
-      if (speculate && prec == UOT_F32)
+      if (speculate && (prec == UOT_F32 || prec == UOT_MIXED))
         for (int d = 0; d < 2; ++d)
           for (int k = 0; k < g.ndim; ++k) zbuf[d][k] = sc.take<float>((size_t)inter * nbatch);
       if (prec == UOT_MIXED || prec == UOT_F32) {
@@ -961,7 +963,7 @@ struct Gibbs {
           }
         }
         cudaError_t err;
-        if (prec == UOT_MIXED && tc_ok(dir, ax, eps, in_shape[ax])) {
+        if (prec == UOT_MIXED && !tc_off && tc_ok(dir, ax, eps, in_shape[ax])) {
           err = launch_grid_pass_tc(cur, logw, cur_is_pot, (int)nlines, in_shape[ax], in_axes[ax],
                                     out_shape[ax], out_axes[ax], eps, nbatch, e, s, tc_err, za);
         } else {
@@ -1042,6 +1044,12 @@ struct BlockGraph {
   cudaError_t launch(cudaStream_t s) {
     count_launches((int)kernels);
     return cudaGraphLaunch(exec, s);
+  }
+  // forget the captured block (its launches changed); the next use recaptures
+  void reset() {
+    if (exec) cudaGraphExecDestroy(exec);
+    exec = nullptr;
+    kernels = 0;
   }
   ~BlockGraph() {
     if (exec) cudaGraphExecDestroy(exec);
@@ -1413,6 +1421,11 @@ uot_status solve_impl(const uot_geom* g, int batch, const void* p, const void* d
   // FP32 progress: first check at the final eps, best value so far (1% steps)
   double first_err = NAN, best_err = INFINITY;
   int first_it = 0, best_it = 0;
+  // UOT_MIXED: the BF16 (tensor-core) phase, until the violation reaches mixed_switch
+  bool mixed_phase = prec == UOT_MIXED && g->kind == UOT_GEOM_GRID && o->tol > 0.0;
+  const double mixed_switch = o->mixed_switch > 0.0 ? o->mixed_switch : 1e-3;
+  int mixed_iters = 0;
+  bool mixed_handover = false;  // set by decide(): the graph block must be recaptured
 
   auto read_err = [&](double& out) -> cudaError_t {
     cudaError_t e = cudaMemcpyAsync(acc_h.data(), acc, 16 * (size_t)batch, cudaMemcpyDeviceToHost, s);
@@ -1662,10 +1675,42 @@ uot_status solve_impl(const uot_geom* g, int batch, const void* p, const void* d
     }
   } else if (!o->plain_scaling) {
     // The stop decision after a check (err = the FP32 violation just read).
+    // No 1% improvement on the best check for W iterations, W = max(50,
+    // 5 check_every, 3x the iterations a 1% step took at the rate observed since
+    // the first check): the check has reached the rounding floor of the passes.
+    auto stalled = [&]() -> bool {
+      if (std::isnan(first_err)) {
+        first_err = err;
+        first_it = it;
+      }
+      if (err < 0.99 * best_err) {
+        best_err = err;
+        best_it = it;
+        return false;
+      }
+      double W = std::max(50, 5 * check_every);
+      if (best_err < first_err && best_it > first_it) {
+        const double rate = std::log(best_err / first_err) / (best_it - first_it);  // < 0
+        W = std::max(W, std::min(1e8, 3.0 * std::log(0.99) / rate));
+      }
+      return it - best_it >= W;
+    };
     auto decide = [&](bool& stop) -> cudaError_t {
       stop = false;
       err32 = err;
       if (!(o->tol > 0.0)) return cudaSuccess;
+      if (mixed_phase) {
+        // BF16 phase: hand over to the FP32 passes at mixed_switch or at the BF16 floor
+        if (err <= mixed_switch || stalled()) {
+          mixed_phase = false;
+          mixed_iters = total;
+          G.tc_off = true;
+          mixed_handover = true;
+          first_err = NAN;
+          best_err = INFINITY;
+        }
+        return cudaSuccess;
+      }
       if (!verify) {
         if (err <= o->tol) converged = stop = true;
         return cudaSuccess;
@@ -1687,24 +1732,8 @@ uot_status solve_impl(const uot_geom* g, int batch, const void* p, const void* d
         best_it = it;
         return cudaSuccess;
       }
-      // The FP32 check's rounding floor: no 1% improvement on its best value
-      // for W iterations, W = max(50, 5 check_every, 3x the iterations a 1%
-      // step took at the rate observed since the first check).
-      if (std::isnan(first_err)) {
-        first_err = err;
-        first_it = it;
-      }
-      if (err < 0.99 * best_err) {
-        best_err = err;
-        best_it = it;
-        return cudaSuccess;
-      }
-      double W = std::max(50, 5 * check_every);
-      if (best_err < first_err && best_it > first_it) {
-        const double rate = std::log(best_err / first_err) / (best_it - first_it);  // < 0
-        W = std::max(W, std::min(1e8, 3.0 * std::log(0.99) / rate));
-      }
-      if (it - best_it >= W) polish = stop = true;
+      // the FP32 check's rounding floor: FP64 iterations take over
+      if (stalled()) polish = stop = true;
       return cudaSuccess;
     };
     auto iteration = [&](double eps, bool check, cudaStream_t st) -> cudaError_t {
@@ -1747,6 +1776,10 @@ uot_status solve_impl(const uot_geom* g, int batch, const void* p, const void* d
         bool stop = false;
         UOT_CK(decide(stop));
         if (stop) break;
+        if (mixed_handover) {
+          bg.reset();  // the block now launches the FP32 passes
+          mixed_handover = false;
+        }
         continue;
       }
       const bool check = ((it + 1) % check_every == 0) || (it == o->max_iter - 1);
@@ -1759,6 +1792,10 @@ uot_status solve_impl(const uot_geom* g, int batch, const void* p, const void* d
           bool stop = false;
           UOT_CK(decide(stop));
           if (stop) break;
+          if (mixed_handover) {
+            bg.reset();
+            mixed_handover = false;
+          }
         } else {
           err32 = err;
         }
@@ -1920,6 +1957,7 @@ uot_status solve_impl(const uot_geom* g, int batch, const void* p, const void* d
     res->verifications = nverify;
     res->polish_iters = npolish;
     res->marg_err_fp32 = err32;
+    res->mixed_iters = (prec == UOT_MIXED && mixed_phase) ? total : mixed_iters;
   }
   return out;
 }

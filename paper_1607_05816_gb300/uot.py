@@ -53,7 +53,7 @@ class COpts(C.Structure):
                 ("eps_stages", C.c_int), ("iters_per_stage", C.c_int), ("max_iter", C.c_int),
                 ("tol", C.c_double), ("check_every", C.c_int), ("plain_scaling", C.c_int),
                 ("launch_mode", C.c_int), ("U0", C.c_void_p), ("V0", C.c_void_p),
-                ("out_f64", C.c_int), ("verify", C.c_int)]
+                ("out_f64", C.c_int), ("verify", C.c_int), ("mixed_switch", C.c_double)]
 
 
 class CBatchProblem(C.Structure):
@@ -63,7 +63,7 @@ class CBatchProblem(C.Structure):
 class CResult(C.Structure):
     _fields_ = [("iters", C.c_int), ("total_iters", C.c_int), ("marg_err", C.c_double),
                 ("ms", C.c_double), ("status", C.c_int), ("verifications", C.c_int),
-                ("polish_iters", C.c_int), ("marg_err_fp32", C.c_double)]
+                ("polish_iters", C.c_int), ("marg_err_fp32", C.c_double), ("mixed_iters", C.c_int)]
 
 
 _LIB = None
@@ -356,7 +356,7 @@ class Geometry:
 def _info(r: "CResult", st: int) -> dict:
     return dict(iters=r.iters, total_iters=r.total_iters, marg_err=r.marg_err, ms=r.ms,
                 status=STATUS[st], verifications=r.verifications, polish_iters=r.polish_iters,
-                marg_err_fp32=r.marg_err_fp32)
+                marg_err_fp32=r.marg_err_fp32, mixed_iters=r.mixed_iters)
 
 
 def _check(status, what):
@@ -368,7 +368,7 @@ def _check(status, what):
 def solve(geom: Geometry, p, dx, q, dy, F1: Div, F2: Div, eps: float, *, precision=F64,
           max_iter=1000, tol=0.0, check_every=10, eps_start=None, eps_stages=10,
           iters_per_stage=100, plain_scaling=False, U0=None, V0=None, U=None, V=None,
-          launch_mode=0, out_f64=False, verify=False):
+          launch_mode=0, out_f64=False, verify=False, mixed_switch=0.0):
     """uot_solve: returns (U, V, result dict).  Inputs are CUDA tensors of the
     precision's dtype; U, V (optional) are preallocated outputs (float64 when
     out_f64).  verify: the stop is confirmed by an FP64 evaluation of the
@@ -381,7 +381,7 @@ def solve(geom: Geometry, p, dx, q, dy, F1: Div, F2: Div, eps: float, *, precisi
     o = COpts(precision, float(eps), float(eps_start) if eps_start else 0.0, int(eps_stages),
               int(iters_per_stage), int(max_iter), float(tol), int(check_every),
               int(bool(plain_scaling)), int(launch_mode), _ptr(U0, dt, "U0"), _ptr(V0, dt, "V0"),
-              int(bool(out_f64)), int(bool(verify)))
+              int(bool(out_f64)), int(bool(verify)), float(mixed_switch))
     r = CResult()
     g = geom.c(precision)
     st = lib.uot_solve(C.byref(g), _ptr(p, dt, "p"), _ptr(dx, dt, "dx"), _ptr(q, dt, "q"),
@@ -518,7 +518,7 @@ def color_transfer(img_x, img_y, F2: Div, eps=0.002, iters=2000, bins=(64, 32, 3
 def solve_many(geom: Geometry, P, dx, Q, dy, F1: Div, F2: Div, eps, *, precision=F64,
                max_iter=1000, tol=0.0, check_every=10, eps_start=None, eps_stages=10,
                iters_per_stage=100, U0=None, V0=None, U=None, V=None, launch_mode=0,
-               out_f64=False, verify=False):
+               out_f64=False, verify=False, mixed_switch=0.0):
     """uot_solve_many: P [B, n], Q [B, m] densities of B independent problems
     sharing geometry, weights, eps and penalties.  Returns (U [B,n], V [B,m], info)."""
     lib = load()
@@ -529,7 +529,8 @@ def solve_many(geom: Geometry, P, dx, Q, dy, F1: Div, F2: Div, eps, *, precision
     V = torch.empty(B, geom.m, dtype=odt, device=P.device) if V is None else V
     o = COpts(precision, float(eps), float(eps_start) if eps_start else 0.0, int(eps_stages),
               int(iters_per_stage), int(max_iter), float(tol), int(check_every), 0, int(launch_mode),
-              _ptr(U0, dt, "U0"), _ptr(V0, dt, "V0"), int(bool(out_f64)), int(bool(verify)))
+              _ptr(U0, dt, "U0"), _ptr(V0, dt, "V0"), int(bool(out_f64)), int(bool(verify)),
+              float(mixed_switch))
     r = CResult()
     g = geom.c(precision)
     st = lib.uot_solve_many(C.byref(g), int(B), _ptr(P, dt, "P"), _ptr(dx, dt, "dx"),

@@ -37,8 +37,8 @@ def test_version_string():
 def test_struct_layouts_match_header():
     # sizes follow from the field lists in include/uot.h on LP64
     assert ctypes.sizeof(uot.CDiv) == 32
-    assert ctypes.sizeof(uot.COpts) == 8 + 8 + 8 + 4 + 4 + 4 + 4 + 8 + 4 + 4 + 4 + 4 + 8 + 8 + 4 + 4
-    assert ctypes.sizeof(uot.CResult) == 4 + 4 + 8 + 8 + 4 + 4 + 4 + 4 + 8
+    assert ctypes.sizeof(uot.COpts) == 8 + 8 + 8 + 4 + 4 + 4 + 4 + 8 + 4 + 4 + 4 + 4 + 8 + 8 + 4 + 4 + 8
+    assert ctypes.sizeof(uot.CResult) == 4 + 4 + 8 + 8 + 4 + 4 + 4 + 4 + 8 + 4 + 4
 
 
 def test_no_cpu_fallback(monkeypatch):

@@ -63,15 +63,54 @@ def test_mixed_solve_error_bound():
         assert err <= 0.05 * eps
 
 
-def test_mixed_barycenter_matches_f32_closely():
+def test_mixed_barycenter_error_bound():
+    """KL barycenter of 8 blob images, 20 iterations at eps = 1e-2: the mixed
+    path's eps log h and V against the FP64 oracle's barycenter iteration."""
     b = synth.barycenter_images(8, 64, 64, seed=12)
     alpha = np.full(8, 1.0 / 8)
+    eps, lam, iters = 1e-2, 1.0, 20
     geo = U.Geometry.grid([dev(a) for a in b["xs"]])
     P = torch.as_tensor(f32(b["P"]).reshape(8, -1), dtype=torch.float32, device="cuda")
-    outs = {}
-    for prec in (U.F32, U.MIXED):
-        outs[prec] = U.barycenter(geo, alpha, P, dev(b["dx"]), dev(b["dy"]), U.EQ(), 1.0, 1e-2,
-                                  precision=prec, max_iter=20)
-    d = torch.max(torch.abs(outs[U.F32][0] - outs[U.MIXED][0])).item()
-    print(f"mixed barycenter: max |eps log h (mixed) - eps log h (f32)| = {d:.3e}")
-    assert d <= 0.05 * 1e-2
+    lh, _, Vg, _ = U.barycenter(geo, alpha, P, dev(b["dx"]), dev(b["dy"]), U.EQ(), lam, eps,
+                                precision=U.MIXED, max_iter=iters)
+    og = O.Geometry("grid", xs=[f32(a) for a in b["xs"]], ys=[f32(a) for a in b["ys"]])
+    _, Vo, lho = O.barycenter_log(og, f32(b["dx"]), f32(b["dy"]), f32(b["P"]), alpha, O.EQ(), lam, eps, iters)
+    for got, want, name in ((lh, lho, "eps log h"), (Vg, Vo.reshape(8, -1), "V")):
+        gv = got.double().cpu().numpy().ravel()
+        wv = np.asarray(want).ravel()
+        assert np.array_equal(np.isneginf(gv), np.isneginf(wv))
+        f = np.isfinite(wv)
+        err = np.max(np.abs(gv[f] - wv[f]))
+        print(f"mixed barycenter: max |{name} - oracle| = {err:.3e} = {err / eps:.3e} eps")
+        assert err <= 0.05 * eps
+
+
+@pytest.mark.parametrize("shape,eps", [((128, 128), 1e-2), ((256, 256), 1e-3)])
+def test_mixed_pipeline_reaches_tol_under_the_oracle(shape, eps):
+    """BF16 tensor-core passes (eps-scaling stages, then the final eps until the
+    violation reaches mixed_switch), FP32 passes to tol, the stop confirmed in
+    FP64: the returned FP64 potentials meet tol when the oracle evaluates them."""
+    d = synth.problem_grid2d(*shape, seed=3, masses=(1.0, 1.3))
+    og = O.Geometry("grid", xs=[f32(a) for a in d["xs"]], ys=[f32(a) for a in d["ys"]])
+    geo = U.Geometry.grid([dev(a) for a in d["xs"]], [dev(a) for a in d["ys"]])
+    tol = 1e-6
+    Ug, Vg, info = U.solve(geo, dev(d["p"]), dev(d["dx"]), dev(d["q"]), dev(d["dy"]), U.KL(0.5), U.KL(0.5),
+                           eps, precision=U.MIXED, max_iter=20000, tol=tol, check_every=20, eps_start=0.1,
+                           eps_stages=10, iters_per_stage=100, launch_mode=2, out_f64=True, verify=True,
+                           mixed_switch=1e-3)
+    print(f"mixed pipeline {shape} eps={eps}: {info}")
+    assert info["status"] == "UOT_OK" and info["mixed_iters"] >= 1000, info
+    assert info["mixed_iters"] < info["total_iters"]  # the FP32 passes finished the solve
+    v = O.marginal_violation(og, f32(d["dx"]), f32(d["dy"]), f32(d["p"]), f32(d["q"]), O.KL(0.5), O.KL(0.5), eps,
+                             Ug.cpu().numpy().reshape(shape), Vg.cpu().numpy().reshape(shape))
+    assert v <= tol, (v, info)
+    assert abs(v - info["marg_err"]) <= 1e-6 * v + 1e-15
+
+
+def test_mixed_without_tol_stays_on_tensor_cores():
+    """tol = 0 (a fixed iteration count): every pass on the tensor cores."""
+    d = synth.problem_grid2d(64, 64, seed=4, masses=(1.0, 1.3))
+    geo = U.Geometry.grid([dev(a) for a in d["xs"]], [dev(a) for a in d["ys"]])
+    _, _, info = U.solve(geo, dev(d["p"]), dev(d["dx"]), dev(d["q"]), dev(d["dy"]), U.KL(0.5), U.KL(0.5), 1e-2,
+                         precision=U.MIXED, max_iter=15)
+    assert info["mixed_iters"] == 15
