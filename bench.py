@@ -285,6 +285,8 @@ def run_ours(args, rank, world, local_rank):
     step()
     torch.cuda.synchronize()
     kern_ms, kern_n = uot.profile_end(uot.PROF_GRID_PASS)
+    blk_ms, blk_n = uot.profile_end(uot.PROF_GRID_BLK)  # passes the block-stabilised kernel ran
+    kern_ms, kern_n = kern_ms + blk_ms, kern_n + blk_n
 
     # ---- end-to-end through the C ABI with host buffers ----
     def pinned(a):
@@ -356,6 +358,10 @@ def run_ours(args, rank, world, local_rank):
                   "fp64_confirmations_per_step": sum(i["verifications"] for i in infos) / len(infos),
                   "fp64_iters_per_step": sum(i["polish_iters"] for i in infos) / len(infos),
                   "outputs": "float64"} if verify else {"rule": "FP32 check"}),
+        "mixed": ({"bf16_tensor_core_iters_per_step": sum(i["mixed_iters"] for i in infos) / len(infos),
+                   "fp32_iters_per_step": sum(i["total_iters"] - i["mixed_iters"] - i["polish_iters"]
+                                              for i in infos) / len(infos),
+                   "switch": "violation <= 1e-3 or the BF16 floor"} if prec == uot.MIXED else None),
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
@@ -368,6 +374,7 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clocks,
         "roofline": alu_roofline(
             "grid_fused2" if (args.launch_mode == 3 and prec == uot.F32) else
+            "grid_pass_blk" if (prec == uot.F32 and blk_n > kern_n // 2) else
             {uot.F32: "grid_pass_f32", uot.F64: "grid_pass_f64", uot.MIXED: "grid_pass_tc"}[prec], achieved,
             FP32_OPS_PER_TERM["grid"],
             "achieved = 4 passes x 256^3 terms per iteration x iterations / CUDA-event time of the timed "
@@ -952,7 +959,7 @@ def _compact(line, cpu):
          "final_marg_err": line.get("final_marg_err"), "dtype": line["dtype"], "config": line["config"],
          "clocks": line.get("clocks"), "gpu_launches": line.get("gpu_launches"),
          "roofline": {k: r.get(k) for k in ("bound", "kernel", "achieved", "peak", "unit", "frac", "traffic")}}
-    for k in ("stop", "warm_start"):
+    for k in ("stop", "warm_start", "mixed"):
         if k in line:
             d[k] = line[k]
     if cpu:
@@ -970,6 +977,7 @@ def sub_workloads(args, local_rank, cpu=True):
     subs = [
         ("dense1d", dict(workload="dense1d", launch_mode=1)),
         ("grid2d_f64", dict(workload="grid2d", precision="f64", steps=1)),
+        ("grid2d_mixed", dict(workload="grid2d", precision="mixed", steps=1)),
         ("points_kl", dict(workload="points", penalty="kl")),
         ("points_tv", dict(workload="points", penalty="tv")),
         ("batch", dict(workload="batch")),
