@@ -1957,7 +1957,7 @@ uot_status solve_impl(const uot_geom* g, int batch, const void* p, const void* d
     res->verifications = nverify;
     res->polish_iters = npolish;
     res->marg_err_fp32 = err32;
-    res->mixed_iters = (prec == UOT_MIXED && mixed_phase) ? total : mixed_iters;
+    res->mixed_iters = prec != UOT_MIXED ? 0 : (G.tc_off ? mixed_iters : total);
   }
   return out;
 }
