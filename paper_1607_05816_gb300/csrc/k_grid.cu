@@ -950,22 +950,27 @@ TuneEntry tune_tiles(const PassArgs& base, int nbatch, cudaStream_t s) {
     ep.err = acc;
     ep.bstride = ep.bstride_p = (int64_t)base.nlines * base.nout;
     // The chain alternates a solve's first pass (potentials in, raw
-    // intermediate out) and last pass (intermediate in, prox epilogue out).
-    int cur = 0, parity = 0;
+    // intermediate out) and last pass (that intermediate in, prox epilogue
+    // out).  The potentials read by the first kind stay fixed (zeros), so
+    // every launch sees bounded, finite data: feeding a pass's log-sums back
+    // as potentials would scale them by 1/eps per step until they overflow,
+    // and the timed kernels would then take their empty-line exits.
+    int parity = 0;
     auto step = [&](int t, int use_prev) -> bool {
-      a.in = buf[cur];
-      a.zprev = z[cur ^ 1];
       a.use_prev = use_prev;
       parity ^= 1;
       if (parity) {
+        a.in = pro[1];  // zero potentials (the prox epilogue only reads this array)
         a.in_is_pot = 1;
         a.logw = pro[2];
-        e.out = reinterpret_cast<double*>(buf[cur ^ 1]);
-        cur ^= 1;
+        a.zprev = z[0];
+        e.out = reinterpret_cast<double*>(buf[0]);
         return launch_f32(t, a, e, nbatch, s) == cudaSuccess;
       }
+      a.in = buf[0];
       a.in_is_pot = 0;
       a.logw = nullptr;
+      a.zprev = z[1];
       return launch_f32(t, a, ep, nbatch, s) == cudaSuccess;
     };
     // Warm-up (brings the SM clock up before anything is timed; both shift
