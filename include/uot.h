@@ -616,6 +616,63 @@ uot_status uot_warmstart_features(const float* p, const float* q, const float* l
                                   const float* log_lam, float* out, int N, int H, int W,
                                   void* stream);
 
+/*
+ * Learned warm start on the tensor cores (not in the paper): BF16 3x3 dilated
+ * convolutions with zero padding on images of width 64, as implicit GEMMs on
+ * tcgen05 with FP32 accumulation in tensor memory, every operand tile loaded
+ * by TMA.  BF16 tensors are passed as void pointers.  Activations are NHWC
+ * with a channel stride; weights are K-major rows [rows][9 taps][channels].
+ * All calls are asynchronous on `stream`; UOT_EUNSUPPORTED if the driver's
+ * tensor-map encoder is unavailable; `err` (device int, may be NULL) is set
+ * to 1 if a bounded wait inside a kernel expired (its outputs are then not
+ * written).
+ *
+ * uot_conv_tc_forward: y[p][co] = epi(sum_{tap, c} wk[co][tap][c] x[p + dil s(tap)][c]),
+ *   s(tap) = (tap/3 - 1, tap%3 - 1) in (y, x), x out of the image = 0.
+ *   x [N][H][W][ldx] (ldx multiple of 8, <= cin_pad; channels ldx..cin_pad-1
+ *   read as 0), wk [bn][9][cin_pad] (bn = 16, 64 or 128; rows >= nout are 0),
+ *   W = 64, H even, cin_pad a multiple of 64, 1 <= nout <= bn.
+ *   mode 0: + bias[co]; 1: + bias then leaky ReLU (slope 0.1); 2: multiplied by
+ *   the leaky-ReLU derivative at ref[p][co] (ref [P][ldref], BF16): with the
+ *   weights of uot_conv_weights_bf16's wb this is the data gradient of a
+ *   layer.  Outputs: y [P][ldy] BF16 (ldy multiple of 16; channels nout..ldy-1
+ *   written 0) and/or yf [P][nout] FP32.
+ * uot_conv_tc_wgrad: dw[co][ci][kh][kw] (FP32, the layer's shape) =
+ *   sum_p dy[p][co] x[p + dil s(3 kh + kw)][ci], from dyT [cout_rows][N][H][W]
+ *   (uot_nhwc_transpose of dy) and xT [3][cin_pad][N][H][W]
+ *   (uot_nhwc_shift_transpose of x); Cout <= 128, cin_pad 64 or 128; part is
+ *   FP32 scratch of splits x 9 x 128 x cin_pad partial sums.
+ * uot_nhwc_shift_transpose: xT[d][c][n][y][x] = x[n][y][x + (d-1) dil][c] (0 off the
+ *   image), d = 0, 1, 2; x [N][H][W][C], W <= 64.
+ * uot_nhwc_transpose: yT[c][p] = y[p][c], y [P][C].
+ * uot_bias_grad_bf16: db[c] = sum_p dy[p][c], dy [P][ld].
+ * uot_conv_weights_bf16: from FP32 w [Cout][Cin][3][3]: wf [cout_pad][9][cin_pad] =
+ *   w[co][ci][tap] and (if wb) wb [cin_rows][9][cout_kpad] = w[co][ci][8 - tap]
+ *   (the data-gradient weights), zero padding, BF16.
+ * uot_warmstart_features_nhwc: out [N][H][W][64] BF16 = (max(log p, -30),
+ *   max(log q, -30), log eps, log lambda) / 4, zeros in channels 4..63.
+ * uot_mse_grad_nhwc: for pred [P][2] FP32 (P = N HW) and targets U, V [N][HW]
+ *   scaled by scale[n]: grad [P][16] BF16 = 2 (pred - target) / (2P) in
+ *   channels 0, 1 (0 beyond), *loss_dev += the mean squared difference.
+ * uot_pred_to_potentials: U0[p] = pred[p][0] scale[n], V0[p] = pred[p][1] scale[n].
+ */
+uot_status uot_conv_tc_forward(const void* x, int ldx, const void* wk, int bn, int N, int H, int W, int cin_pad,
+                               int nout, int dil, int mode, const float* bias, const void* ref, int ldref, void* y,
+                               int ldy, float* yf, int* err, void* stream);
+uot_status uot_conv_tc_wgrad(const void* dyT, int cout_rows, const void* xT, int cin_pad, int N, int H, int W,
+                             int dil, int Cout, int Cin, float* part, int splits, float* dw, int* err, void* stream);
+uot_status uot_nhwc_shift_transpose(const void* x, int N, int H, int W, int C, int dil, void* xT, void* stream);
+uot_status uot_nhwc_transpose(const void* y, long long P, int C, void* yT, void* stream);
+uot_status uot_bias_grad_bf16(const void* dy, long long P, int ld, int C, float* db, void* stream);
+uot_status uot_conv_weights_bf16(const float* w, int Cout, int Cin, int cout_pad, int cin_pad, int cin_rows,
+                                 int cout_kpad, void* wf, void* wb, void* stream);
+uot_status uot_warmstart_features_nhwc(const float* p, const float* q, const float* log_eps, const float* log_lam,
+                                       void* out, int N, int H, int W, void* stream);
+uot_status uot_mse_grad_nhwc(const float* pred, const float* U, const float* V, const float* scale, int N, int HW,
+                             void* grad, double* loss_dev, void* stream);
+uot_status uot_pred_to_potentials(const float* pred, const float* scale, int N, int HW, float* U0, float* V0,
+                                  void* stream);
+
 #ifdef __cplusplus
 }
 #endif

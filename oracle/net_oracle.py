@@ -58,3 +58,31 @@ def fd_grad(params, layers, x, target, which, idx, h=1e-5):
     lm = mse(base, layers, x, target)
     arr[idx] = old
     return (lp - lm) / (2 * h)
+
+
+def conv2d_grads(x, w, g, dil):
+    """Gradients of L = sum(g * conv2d(x, w, b, dil, leaky=False)) with respect to
+    x, w and b, each written from the definition of conv2d (zero padding):
+      dx[n, ci, h, v]   = sum_{co, kh, kw} w[co, ci, kh, kw] g[n, co, h - dil (kh-1), v - dil (kw-1)]
+      dw[co, ci, kh, kw] = sum_{n, h, v} g[n, co, h, v] x[n, ci, h + dil (kh-1), v + dil (kw-1)]
+      db[co]            = sum_{n, h, v} g[n, co, h, v]
+    (terms whose shifted index leaves the image are zero)."""
+    x = np.asarray(x, dtype=np.float64)
+    w = np.asarray(w, dtype=np.float64)
+    g = np.asarray(g, dtype=np.float64)
+    N, Cin, H, W = x.shape
+    pad = dil
+    xp = np.zeros((N, Cin, H + 2 * pad, W + 2 * pad))
+    xp[:, :, pad:pad + H, pad:pad + W] = x
+    gp = np.zeros((N, g.shape[1], H + 2 * pad, W + 2 * pad))
+    gp[:, :, pad:pad + H, pad:pad + W] = g
+    dx = np.zeros_like(x)
+    dw = np.zeros_like(w)
+    for kh in range(3):
+        for kw in range(3):
+            # x[h + dil (kh-1)] lives at xp[h + dil kh]; g[h - dil (kh-1)] at gp[h + dil (2 - kh)]
+            xs = xp[:, :, kh * dil:kh * dil + H, kw * dil:kw * dil + W]
+            gs = gp[:, :, (2 - kh) * dil:(2 - kh) * dil + H, (2 - kw) * dil:(2 - kw) * dil + W]
+            dw[:, :, kh, kw] = np.einsum("nohw,nchw->oc", g, xs)
+            dx += np.einsum("oc,nohw->nchw", w[:, :, kh, kw], gs)
+    return dx, dw, g.sum(axis=(0, 2, 3))

@@ -481,6 +481,34 @@ cudaError_t launch_grid_pass(int prec, const double* in, const double* logw, int
                              float* zprev, int use_prev, double* zero_acc = nullptr, int tc3_ok = 0,
                              int* tc_err = nullptr, const BlkAxis* blk = nullptr);
 
+// Tensor-core convolutions of the warm-start network (k_conv_tc.cu); BF16
+// tensors are passed as void pointers.
+struct ConvTcLaunch {
+  int N, H, W;        // images, image size (W = 64)
+  int ldx;            // channel stride of the NHWC input
+  int cin_pad;        // K channels per tap (multiple of 64, >= ldx)
+  int nout;           // output channels
+  int ldy;            // channel stride of the BF16 output (multiple of 16)
+  int dil;            // dilation
+  int mode;           // 0: + bias, 1: + bias then leaky ReLU, 2: x leaky-ReLU derivative of ref
+  const float* bias;
+  const void* ref;    // mode 2: BF16 [P][ldref]
+  int ldref;
+  void* y;            // BF16 [P][ldy] or NULL
+  float* yf;          // FP32 [P][nout] or NULL
+  int* err;           // bounded-wait flag (may be NULL)
+};
+int conv_tc_available();
+cudaError_t launch_conv_tc(const void* x, const void* wk, int bn, const ConvTcLaunch& L, cudaStream_t s);
+cudaError_t launch_wgrad_tc(const void* dyT, int cout_rows, const void* xT, int cin_pad, int N, int H, int W, int dil,
+                            int Cout, int Cin, float* part, int splits, float* dw, int* err, cudaStream_t s);
+cudaError_t launch_nhwc_to_shifted_cnhw(const void* x, int N, int H, int W, int C, int dil, void* xT,
+                                        cudaStream_t s);
+cudaError_t launch_nhwc_to_cnhw(const void* y, int64_t P, int C, void* yT, cudaStream_t s);
+cudaError_t launch_bias_grad(const void* dy, int64_t P, int ld, int C, float* db, cudaStream_t s);
+cudaError_t launch_weights_bf16(const float* w, int Cout, int Cin, int cout_pad, int cin_pad, int cin_rows,
+                                int cout_kpad, void* wf, void* wb, cudaStream_t s);
+
 // The tensor-core pass with three-part BF16 operands (k_grid_tc3.cu): same
 // result as the FP32 pass to FP32 accuracy; nin <= grid_pass_tc3_max_nin().
 int grid_pass_tc3_max_nin();

@@ -122,6 +122,23 @@ _SIGS = {
     "uot_scale_instances": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_longlong, C.c_void_p]),
     "uot_warmstart_features": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                          C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p]),
+    "uot_conv_tc_forward": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int,
+                                      C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_int,
+                                      C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "uot_conv_tc_wgrad": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                    C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "uot_nhwc_shift_transpose": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p,
+                                           C.c_void_p]),
+    "uot_nhwc_transpose": (C.c_int, [C.c_void_p, C.c_longlong, C.c_int, C.c_void_p, C.c_void_p]),
+    "uot_bias_grad_bf16": (C.c_int, [C.c_void_p, C.c_longlong, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
+    "uot_conv_weights_bf16": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                        C.c_void_p, C.c_void_p, C.c_void_p]),
+    "uot_warmstart_features_nhwc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                              C.c_int, C.c_int, C.c_int, C.c_void_p]),
+    "uot_mse_grad_nhwc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int,
+                                    C.c_void_p, C.c_void_p, C.c_void_p]),
+    "uot_pred_to_potentials": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
+                                         C.c_void_p]),
     "uot_set_autotune": (C.c_int, [C.c_int]),
     "uot_force_grid_tile": (C.c_int, [C.c_int]),
     "uot_grid_tile_count": (C.c_int, []),
@@ -750,3 +767,99 @@ def warmstart_features(P, Q, log_eps, log_lam, out=None):
                                          _ptr(log_lam, f, "log_lam"), _ptr(out, f, "out"), N, H, W,
                                          _stream()), "uot_warmstart_features")
     return out
+
+
+# ---- tensor-core convolutions of the warm-start network (BF16, NHWC) ----
+
+BF16 = torch.bfloat16
+CONV_IDENTITY, CONV_LEAKY, CONV_DACT = 0, 1, 2
+
+
+def conv_tc_forward(x, wk, bn, N, H, W, cin_pad, nout, dil, mode, *, bias=None, ref=None, y=None, yf=None,
+                    err=None):
+    """uot_conv_tc_forward; x [N*H*W, ldx] BF16, wk [bn, 9, cin_pad] BF16, y [P, ldy] BF16 and/or
+    yf [P, nout] FP32 (allocated here when neither is given: y with ldy = max(16, nout))."""
+    P = N * H * W
+    if y is None and yf is None:
+        y = torch.empty(P, max(16, (nout + 15) // 16 * 16), dtype=BF16, device=x.device)
+    _check(load().uot_conv_tc_forward(
+        _ptr(x, BF16, "x"), x.shape[-1], _ptr(wk, BF16, "wk"), bn, N, H, W, cin_pad, nout, dil, mode,
+        _ptr(bias, torch.float32, "bias"), _ptr(ref, BF16, "ref"), 0 if ref is None else ref.shape[-1],
+        _ptr(y, BF16, "y"), 0 if y is None else y.shape[-1], _ptr(yf, torch.float32, "yf"),
+        _ptr(err, torch.int32, "err"), _stream()), "uot_conv_tc_forward")
+    return y if y is not None else yf
+
+
+def conv_tc_wgrad(dyT, xT, cin_pad, N, H, W, dil, Cout, Cin, *, splits=64, part=None, dw=None, err=None):
+    """uot_conv_tc_wgrad; dyT [rows, P] BF16, xT [3, cin_pad, P] BF16 -> dw [Cout, Cin, 3, 3] FP32."""
+    dw = torch.empty(Cout, Cin, 3, 3, dtype=torch.float32, device=dyT.device) if dw is None else dw
+    part = torch.empty(splits * 9 * 128 * cin_pad, dtype=torch.float32, device=dyT.device) if part is None else part
+    _check(load().uot_conv_tc_wgrad(_ptr(dyT, BF16, "dyT"), dyT.shape[0], _ptr(xT, BF16, "xT"), cin_pad, N, H, W,
+                                    dil, Cout, Cin, _ptr(part, torch.float32, "part"), splits,
+                                    _ptr(dw, torch.float32, "dw"), _ptr(err, torch.int32, "err"), _stream()),
+           "uot_conv_tc_wgrad")
+    return dw
+
+
+def nhwc_shift_transpose(x, N, H, W, dil, out=None):
+    C = x.shape[-1]
+    out = torch.empty(3, C, N * H * W, dtype=BF16, device=x.device) if out is None else out
+    _check(load().uot_nhwc_shift_transpose(_ptr(x, BF16, "x"), N, H, W, C, dil, _ptr(out, BF16, "xT"), _stream()),
+           "uot_nhwc_shift_transpose")
+    return out
+
+
+def nhwc_transpose(y, out=None):
+    P, C = y.shape
+    out = torch.empty(C, P, dtype=BF16, device=y.device) if out is None else out
+    _check(load().uot_nhwc_transpose(_ptr(y, BF16, "y"), P, C, _ptr(out, BF16, "yT"), _stream()),
+           "uot_nhwc_transpose")
+    return out
+
+
+def bias_grad_bf16(dy, C, out=None):
+    P, ld = dy.shape
+    out = torch.empty(C, dtype=torch.float32, device=dy.device) if out is None else out
+    _check(load().uot_bias_grad_bf16(_ptr(dy, BF16, "dy"), P, ld, C, _ptr(out, torch.float32, "db"), _stream()),
+           "uot_bias_grad_bf16")
+    return out
+
+
+def conv_weights_bf16(w, cout_pad, cin_pad, cin_rows=0, cout_kpad=0, wf=None, wb=None, backward=True):
+    """FP32 w [Cout, Cin, 3, 3] -> (wf [cout_pad, 9, cin_pad], wb [cin_rows, 9, cout_kpad] or None) BF16."""
+    Cout, Cin = w.shape[:2]
+    wf = torch.empty(cout_pad, 9, cin_pad, dtype=BF16, device=w.device) if wf is None else wf
+    if backward and wb is None:
+        wb = torch.empty(cin_rows, 9, cout_kpad, dtype=BF16, device=w.device)
+    _check(load().uot_conv_weights_bf16(_ptr(w, torch.float32, "w"), Cout, Cin, cout_pad, cin_pad, cin_rows,
+                                        cout_kpad, _ptr(wf, BF16, "wf"), _ptr(wb, BF16, "wb") if backward else None,
+                                        _stream()), "uot_conv_weights_bf16")
+    return wf, (wb if backward else None)
+
+
+def warmstart_features_nhwc(P, Q, log_eps, log_lam, out=None):
+    N, H, W = P.shape
+    f = torch.float32
+    out = torch.empty(N * H * W, 64, dtype=BF16, device=P.device) if out is None else out
+    _check(load().uot_warmstart_features_nhwc(_ptr(P, f, "p"), _ptr(Q, f, "q"), _ptr(log_eps, f, "log_eps"),
+                                              _ptr(log_lam, f, "log_lam"), _ptr(out, BF16, "out"), N, H, W,
+                                              _stream()), "uot_warmstart_features_nhwc")
+    return out
+
+
+def mse_grad_nhwc(pred, U, V, scale, grad, loss_dev):
+    N, HW = U.shape
+    f = torch.float32
+    _check(load().uot_mse_grad_nhwc(_ptr(pred, f, "pred"), _ptr(U, f, "U"), _ptr(V, f, "V"), _ptr(scale, f, "scale"),
+                                    N, HW, _ptr(grad, BF16, "grad"), _ptr(loss_dev, torch.float64, "loss"),
+                                    _stream()), "uot_mse_grad_nhwc")
+    return grad
+
+
+def pred_to_potentials(pred, scale, N, HW, U0=None, V0=None):
+    f = torch.float32
+    U0 = torch.empty(N, HW, dtype=f, device=pred.device) if U0 is None else U0
+    V0 = torch.empty(N, HW, dtype=f, device=pred.device) if V0 is None else V0
+    _check(load().uot_pred_to_potentials(_ptr(pred, f, "pred"), _ptr(scale, f, "scale"), N, HW, _ptr(U0, f, "U0"),
+                                         _ptr(V0, f, "V0"), _stream()), "uot_pred_to_potentials")
+    return U0, V0

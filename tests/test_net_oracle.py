@@ -56,3 +56,28 @@ def test_fd_gradient_matches_closed_form_linear_layer():
         co, ci, kh, kw = idx
         want = np.sum(r[:, co] * xp[:, ci, 2 * kh:2 * kh + 6, 2 * kw:2 * kw + 5])
         assert abs(NO.fd_grad([(w, b)], layers, x, t, (0, 0), idx) - want) < 1e-7
+
+
+def test_conv2d_grads_match_finite_differences():
+    """The adjoint formulas of conv2d_grads against central differences of
+    L = sum(g * conv2d(x, w, b)) on a small random case, every entry."""
+    g0 = np.random.default_rng(7)
+    for dil in (1, 2):
+        x = g0.normal(size=(2, 3, 5, 6))
+        w = g0.normal(size=(4, 3, 3, 3))
+        b = g0.normal(size=4)
+        G = g0.normal(size=(2, 4, 5, 6))
+        dx, dw, db = NO.conv2d_grads(x, w, G, dil)
+        L = lambda x_, w_, b_: float(np.sum(G * NO.conv2d(x_, w_, b_, dil, False)))
+        h = 1e-6
+        for arr, grad, which in ((x, dx, 0), (w, dw, 1), (b, db, 2)):
+            fd = np.zeros_like(arr)
+            for idx in np.ndindex(arr.shape):
+                old = arr[idx]
+                arr[idx] = old + h
+                lp = L(x, w, b)
+                arr[idx] = old - h
+                lm = L(x, w, b)
+                arr[idx] = old
+                fd[idx] = (lp - lm) / (2 * h)
+            assert np.max(np.abs(fd - grad)) <= 1e-6 * max(1.0, np.max(np.abs(grad))), which
