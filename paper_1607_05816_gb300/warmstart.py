@@ -154,3 +154,170 @@ def iterations_to_tol(P, Q, eps, lam, H, W, *, U0=None, V0=None, tol=1e-6, max_i
                            U0=None if U0 is None else U0.reshape(-1).contiguous(),
                            V0=None if V0 is None else V0.reshape(-1).contiguous())
     return info["iters"], info["marg_err"], info["ms"]
+
+
+# ---------------------------------------------------------------------------
+# The tensor-core network: BF16 3x3 dilated convolutions on tcgen05 (FP32
+# accumulation), NHWC activations, FP32 master weights updated by Adam.
+# ---------------------------------------------------------------------------
+
+TC_DILATIONS = (1, 2, 4, 8, 16, 32, 1, 2, 4, 8, 16, 1)
+
+
+class WarmStartNetTC:
+    """conv3x3(4 -> C) + leaky, len(dilations) x conv3x3(C -> C, dilation d) + leaky,
+    conv3x3(C -> 2) linear; C = 128 gives ~1.8M parameters.  Images 64 wide.
+    Output channel 0 is U0 / lambda, channel 1 is V0 / lambda."""
+
+    def __init__(self, channels=128, dilations=TC_DILATIONS, device="cuda", seed=0):
+        assert channels in (64, 128)
+        gen = torch.Generator(device="cpu").manual_seed(seed)
+        self.C = channels
+        self.layers = [(4, channels, 1, True)]
+        self.layers += [(channels, channels, d, True) for d in dilations]
+        self.layers += [(channels, 2, 1, False)]
+        self.params, self.m, self.v = [], [], []
+        for cin, cout, _, leaky in self.layers:
+            std = math.sqrt(2.0 / (cin * 9)) * (1.0 if leaky else 0.1)
+            w = (torch.randn(cout, cin, 3, 3, generator=gen) * std).to(device)
+            b = torch.zeros(cout, device=device)
+            self.params.append([w, b])
+            self.m.append([torch.zeros_like(w), torch.zeros_like(b)])
+            self.v.append([torch.zeros_like(w), torch.zeros_like(b)])
+        self.t = 0
+        self.loss_dev = torch.zeros(1, dtype=torch.float64, device=device)
+        self.err = torch.zeros(1, dtype=torch.int32, device=device)
+        self._refresh_bf16()
+        self._ws = {}
+
+    # geometry of each layer's GEMMs
+    def _pads(self, li):
+        cin, cout, _, _ = self.layers[li]
+        cin_pad = 64 if cin <= 64 else 128            # K channels per tap (forward)
+        bn = 16 if cout <= 16 else (64 if cout <= 64 else 128)  # output tile width
+        cout_kpad = 64 if cout <= 64 else 128          # K channels per tap (data gradient)
+        return cin_pad, bn, cout_kpad
+
+    def _refresh_bf16(self):
+        self.wf, self.wb = [], []
+        for li, (w, _) in enumerate(self.params):
+            cin_pad, bn, cout_kpad = self._pads(li)
+            wf, wb = uot.conv_weights_bf16(w, bn, cin_pad, cin_rows=cin_pad, cout_kpad=cout_kpad, backward=li > 0)
+            self.wf.append(wf)
+            self.wb.append(wb)
+
+    def _refresh_bf16_inplace(self):
+        for li, (w, _) in enumerate(self.params):
+            cin_pad, bn, cout_kpad = self._pads(li)
+            uot.conv_weights_bf16(w, bn, cin_pad, cin_rows=cin_pad, cout_kpad=cout_kpad, wf=self.wf[li],
+                                  wb=self.wb[li], backward=li > 0)
+
+    def n_params(self):
+        return sum(t.numel() for pr in self.params for t in pr)
+
+    def _buf(self, key, shape, dtype):
+        t = self._ws.get(key)
+        if t is None or t.shape != torch.Size(shape) or t.dtype != dtype:
+            t = torch.empty(shape, dtype=dtype, device=self.params[0][0].device)
+            self._ws[key] = t
+        return t
+
+    def forward(self, feats, N, H, W, keep=True):
+        """feats [N*H*W, 64] BF16 -> (activations, yf [N*H*W, 2] FP32)."""
+        acts = [feats]
+        h = feats
+        P = N * H * W
+        for li, (cin, cout, dil, leaky) in enumerate(self.layers[:-1]):
+            cin_pad, bn, _ = self._pads(li)
+            y = self._buf(("act", li) if keep else ("act", li % 2), (P, cout), torch.bfloat16)
+            uot.conv_tc_forward(h, self.wf[li], bn, N, H, W, cin_pad, cout, dil, uot.CONV_LEAKY,
+                                bias=self.params[li][1], y=y, err=self.err)
+            acts.append(y)
+            h = y
+        li = len(self.layers) - 1
+        cin_pad, bn, _ = self._pads(li)
+        yf = self._buf("out", (P, 2), torch.float32)
+        uot.conv_tc_forward(h, self.wf[li], bn, N, H, W, cin_pad, 2, 1, uot.CONV_IDENTITY,
+                            bias=self.params[li][1], yf=yf, err=self.err)
+        return acts, yf
+
+    def backward(self, acts, g, N, H, W):
+        """g [P, 16] BF16: gradient at the output; returns [(dw, db)] per layer."""
+        grads = [None] * len(self.layers)
+        P = N * H * W
+        for li in range(len(self.layers) - 1, -1, -1):
+            cin, cout, dil, _ = self.layers[li]
+            cin_pad, bn, cout_kpad = self._pads(li)
+            x = acts[li]
+            xT = uot.nhwc_shift_transpose(x, N, H, W, dil, out=self._buf("xT", (3, x.shape[1], P), torch.bfloat16))
+            gT = uot.nhwc_transpose(g, out=self._buf(("gT", g.shape[1]), (g.shape[1], P), torch.bfloat16))
+            splits = max(1, min(N * H, 64))
+            dw = uot.conv_tc_wgrad(gT, xT, cin_pad, N, H, W, dil, cout, cin, splits=splits,
+                                   part=self._buf(("part", cin_pad), (splits * 9 * 128 * cin_pad,), torch.float32),
+                                   dw=self._buf(("dw", li), (cout, cin, 3, 3), torch.float32), err=self.err)
+            db = uot.bias_grad_bf16(g, cout, out=self._buf(("db", li), (cout,), torch.float32))
+            grads[li] = (dw, db)
+            if li > 0:
+                gin = self._buf(("g", li % 2), (P, cin), torch.bfloat16)
+                uot.conv_tc_forward(g, self.wb[li], cin_pad, N, H, W, cout_kpad, cin, dil, uot.CONV_DACT,
+                                    ref=x, y=gin, err=self.err)
+                g = gin
+        return grads
+
+    def train_step(self, feats, U, V, inv_lam, N, H, W, lr):
+        """One Adam step on a batch: feats [P, 64] BF16, targets U, V [N, HW]
+        (potentials), inv_lam [N] (the network predicts potentials / lambda)."""
+        acts, yf = self.forward(feats, N, H, W)
+        g = self._buf("gout", (N * H * W, 16), torch.bfloat16)
+        uot.mse_grad_nhwc(yf, U, V, inv_lam, g, self.loss_dev)
+        grads = self.backward(acts, g, N, H, W)
+        self.t += 1
+        for li, (dw, db) in enumerate(grads):
+            uot.adam_step(self.params[li][0], dw, self.m[li][0], self.v[li][0], lr, self.t)
+            uot.adam_step(self.params[li][1], db, self.m[li][1], self.v[li][1], lr, self.t)
+        self._refresh_bf16_inplace()
+        return self.loss_dev
+
+    def features(self, P, Q, eps, lam):
+        le = torch.as_tensor(np.log(np.asarray(eps, dtype=np.float64)), dtype=torch.float32, device=P.device)
+        ll = torch.as_tensor(np.log(np.asarray(lam, dtype=np.float64)), dtype=torch.float32, device=P.device)
+        return uot.warmstart_features_nhwc(P, Q, le, ll)
+
+    def predict(self, P, Q, eps, lam):
+        """(U0, V0) [N, H*W] FP32 for the instances P, Q [N, H, W]."""
+        N, H, W = P.shape
+        _, yf = self.forward(self.features(P, Q, eps, lam), N, H, W, keep=False)
+        lamt = torch.as_tensor(np.asarray(lam, dtype=np.float32), device=P.device)
+        return uot.pred_to_potentials(yf, lamt, N, H * W)
+
+
+def train_tc(net, P, Q, U, V, eps, lam, *, epochs=10, batch=32, lr=1e-3, seed=0):
+    """Minimise the mean squared error between the network output and the
+    solver potentials divided by lambda.  P, Q, U, V [n, H, W] FP32 device
+    tensors; features are formed per batch.  Returns the mean loss of each epoch."""
+    n, H, W = P.shape
+    dev = P.device
+    le = torch.as_tensor(np.log(np.asarray(eps, dtype=np.float64)), dtype=torch.float32, device=dev)
+    ll = torch.as_tensor(np.log(np.asarray(lam, dtype=np.float64)), dtype=torch.float32, device=dev)
+    inv_lam = torch.as_tensor(1.0 / np.asarray(lam, dtype=np.float64), dtype=torch.float32, device=dev)
+    Uf = U.reshape(n, H * W)
+    Vf = V.reshape(n, H * W)
+    feats = torch.empty(batch * H * W, 64, dtype=torch.bfloat16, device=dev)
+    rng = np.random.Generator(np.random.Philox(seed))
+    hist = []
+    nb = n // batch
+    steps = epochs * nb
+    step = 0
+    for ep in range(epochs):
+        perm = torch.as_tensor(rng.permutation(n), device=dev)
+        net.loss_dev.zero_()
+        for s in range(nb):
+            idx = perm[s * batch:(s + 1) * batch]
+            uot.warmstart_features_nhwc(P[idx].contiguous(), Q[idx].contiguous(), le[idx].contiguous(),
+                                        ll[idx].contiguous(), out=feats)
+            lr_t = lr * 0.5 * (1 + math.cos(math.pi * step / max(1, steps)))
+            net.train_step(feats, Uf[idx].contiguous(), Vf[idx].contiguous(), inv_lam[idx].contiguous(),
+                           batch, H, W, lr_t)
+            step += 1
+        hist.append(float(net.loss_dev.item()) / max(1, nb))
+    return hist

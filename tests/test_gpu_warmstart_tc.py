@@ -1,0 +1,73 @@
+"""The tensor-core warm-start network (BF16 tcgen05 convolutions, FP32
+master weights): its gradients against the FP64 network oracle's exact
+gradients chained layer by layer, and training on solver-generated instances.
+BF16 activations carry a relative rounding of 2^-9 per layer, so the
+whole-network gradient is compared with a 3% bound on its largest entry."""
+import numpy as np
+import pytest
+import torch
+
+import oracle.net_oracle as NO
+from paper_1607_05816_gb300 import synth
+from paper_1607_05816_gb300 import uot as U
+from paper_1607_05816_gb300 import warmstart as WS
+
+pytestmark = pytest.mark.gpu
+
+
+def bf(t):
+    return t.detach().to(torch.bfloat16).double().cpu().numpy()
+
+
+def test_tc_network_gradients_match_oracle():
+    N, H, W = 2, 4, 64
+    inst = synth.warmstart_instances(N, H, W, seed=5, group=N)
+    net = WS.WarmStartNetTC(channels=64, dilations=(1, 3), seed=2)
+    P = torch.as_tensor(inst["P"], dtype=torch.float32, device="cuda")
+    Q = torch.as_tensor(inst["Q"], dtype=torch.float32, device="cuda")
+    feats = net.features(P, Q, inst["eps"], inst["lam"])
+    g = np.random.default_rng(1)
+    Ut = torch.as_tensor(g.normal(size=(N, H * W)), dtype=torch.float32, device="cuda")
+    Vt = torch.as_tensor(g.normal(size=(N, H * W)), dtype=torch.float32, device="cuda")
+    inv_lam = torch.ones(N, device="cuda")
+    acts, yf = net.forward(feats, N, H, W)
+    gout = torch.empty(N * H * W, 16, dtype=torch.bfloat16, device="cuda")
+    net.loss_dev.zero_()
+    U.mse_grad_nhwc(yf, Ut, Vt, inv_lam, gout, net.loss_dev)
+    grads = net.backward(acts, gout, N, H, W)
+    torch.cuda.synchronize()
+    assert net.err.item() == 0
+    # oracle: FP64 forward and chained exact backward on the BF16-rounded weights and features
+    x = np.transpose(bf(feats).reshape(N, H, W, 64)[..., :4], (0, 3, 1, 2))
+    ws = [(bf(w), b.detach().double().cpu().numpy()) for w, b in net.params]
+    hs, zs = [x], []
+    for (w, b), (_, _, dil, leaky) in zip(ws, net.layers):
+        z = NO.conv2d(hs[-1], w, b, dil, False)
+        zs.append(z)
+        hs.append(np.where(z < 0, NO.LEAK * z, z) if leaky else z)
+    out = hs[-1]
+    tgt = np.stack([Ut.double().cpu().numpy().reshape(N, H, W), Vt.double().cpu().numpy().reshape(N, H, W)], 1)
+    G = 2.0 * (out - tgt) / out.size
+    for li in range(len(ws) - 1, -1, -1):
+        dil = net.layers[li][2]
+        dx, dw, db = NO.conv2d_grads(hs[li], ws[li][0], G, dil)
+        got_w = grads[li][0].double().cpu().numpy()
+        got_b = grads[li][1].double().cpu().numpy()
+        assert np.max(np.abs(got_w - dw)) <= 3e-2 * np.max(np.abs(dw)), (li, np.max(np.abs(got_w - dw)))
+        assert np.max(np.abs(got_b - db)) <= 3e-2 * max(1e-12, np.max(np.abs(db))), li
+        if li > 0:
+            G = dx * np.where(zs[li - 1] < 0, NO.LEAK, 1.0)
+    assert abs(net.loss_dev.item() - float(np.mean((out - tgt) ** 2))) <= 2e-2 * float(np.mean((out - tgt) ** 2))
+
+
+def test_tc_training_reduces_loss():
+    H = W = 64
+    inst = synth.warmstart_instances(128, H, W, seed=31, group=32, eps=(1e-2, 1e-1), lam=(0.3, 10.0))
+    P, Q, Us, Vs = WS.generate_targets(inst, H, W, max_iter=3000, group=32)
+    net = WS.WarmStartNetTC(channels=128, seed=3)
+    assert 1.5e6 < net.n_params() < 2.5e6
+    hist = WS.train_tc(net, P, Q, Us, Vs, inst["eps"], inst["lam"], epochs=6, batch=16, lr=1e-3)
+    torch.cuda.synchronize()
+    assert net.err.item() == 0
+    print("tc training loss per epoch:", hist)
+    assert hist[-1] < 0.5 * hist[0]
