@@ -663,6 +663,105 @@ def run_batch(args, rank, world, local_rank):
 
 
 # ----------------------------------------------------------------------------
+# learned warm start (64 x 64 grids): the network trained on solver-generated
+# instances, then held-out instances solved to 1e-6 three ways
+# ----------------------------------------------------------------------------
+
+WS_TRAIN, WS_EPOCHS, WS_EVAL, WS_GROUP = 8192, 8, 1024, 32
+# measured dense BF16 GEMM rate of this GPU type (MEASURED_PEAKS.json bf16_tflops, burst)
+BF16_PEAK_TFLOPS = 1916.2
+
+
+def run_warmstart(args, rank, world, local_rank):
+    import torch
+
+    from paper_1607_05816_gb300 import synth, uot
+    from paper_1607_05816_gb300 import warmstart as WS
+
+    torch.cuda.set_device(local_rank)
+    uot.load()
+    H = W = 64
+    ntrain = args.ws_train or WS_TRAIN
+    epochs = args.ws_epochs or WS_EPOCHS
+    neval = args.ws_eval or WS_EVAL
+    t0 = time.perf_counter()
+    inst = synth.warmstart_instances(ntrain, H, W, seed=1239 + 1000 * rank, group=256)
+    P, Q, Us, Vs = WS.generate_targets(inst, H, W, max_iter=6000, group=256)
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    net = WS.WarmStartNetTC(channels=128, seed=rank)
+    t0 = time.perf_counter()
+    hist = WS.train_tc(net, P, Q, Us, Vs, inst["eps"], inst["lam"], epochs=epochs, batch=32, lr=1e-3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    del P, Q, Us, Vs
+    ev = synth.warmstart_instances(neval, H, W, seed=777001 + rank, group=WS_GROUP)  # held out: other seed
+    warm_inst = {k: (v[:2 * WS_GROUP] if k in ("P", "Q", "eps", "lam") else v) for k, v in ev.items()}
+    WS.evaluate_tc(net, warm_inst, H, W, group=WS_GROUP, plain_sample=2)  # warm-up (tile tuner, graphs)
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    time.sleep(0.3)
+    launches0 = uot.launch_count()
+    res = WS.evaluate_tc(net, ev, H, W, group=WS_GROUP, plain_sample=16)
+    launches = uot.launch_count() - launches0
+    clocks = sampler.stop()
+    # the convolutions' rate: one forward pass of 64 instances, CUDA events
+    Pb = torch.as_tensor(ev["P"][:64], dtype=torch.float32, device="cuda")
+    Qb = torch.as_tensor(ev["Q"][:64], dtype=torch.float32, device="cuda")
+    feats = net.features(Pb, Qb, ev["eps"][:64], ev["lam"][:64])
+    for _ in range(3):
+        net.forward(feats, 64, H, W, keep=False)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(10):
+        net.forward(feats, 64, H, W, keep=False)
+    e1.record()
+    e1.synchronize()
+    fwd_ms = e0.elapsed_time(e1) / 10
+    pad = lambda c: 64 if c <= 64 else 128
+    out_pad = lambda c: 16 if c <= 16 else (64 if c <= 64 else 128)
+    flops_alg = 2.0 * 9 * sum(ci * co for ci, co, _, _ in net.layers) * 64 * H * W
+    flops_mma = 2.0 * 9 * sum(pad(ci) * out_pad(co) for ci, co, _, _ in net.layers) * 64 * H * W
+    if rank != 0:
+        return None
+    med = lambda a: float(np.median(a)) if len(a) else None
+    warm_total = res["warm_ms"] + res["warm_infer_ms"]
+    line = {
+        "metric": "instances_per_s", "value": neval / (warm_total / 1e3), "unit": "instances/s",
+        "n_gpus": world, "steps": 1, "warmup": 1, "ms_per_step": warm_total, "time_to_tol_ms": warm_total,
+        "iters_per_step": float(np.sum(res["warm_iters"])), "final_marg_err": res["worst_err_warm"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16-mma/f32",
+        "data": "synthetic",
+        "config": {"workload": f"warmstart-64x64-train{ntrain}x{epochs}ep-heldout{neval}-groups{WS_GROUP}-tol1e-6",
+                   "grid": [H, W], "eps": "logU[1e-3, 1e-1]", "lambda": "logU[0.1, 10]", "masses": "U[0.5, 2]",
+                   "parallelism": "replicas", "l2": "inputs resident; solves and inference back to back"},
+        "gpu_launches": launches, "clocks": clocks,
+        "roofline": {"bound": "tensor", "kernel": "conv_tc<128> (network forward, 64 instances)",
+                     "achieved": flops_alg / (fwd_ms / 1e3) / 1e12, "peak": BF16_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": flops_alg / (fwd_ms / 1e3) / 1e12 / BF16_PEAK_TFLOPS, "traffic": None,
+                     "mma_flops_incl_padding_tflops": flops_mma / (fwd_ms / 1e3) / 1e12,
+                     "forward_ms_64_instances": fwd_ms,
+                     "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst), of measured",
+                     "timing": "algorithmic FLOPs of one forward pass (2 x 9 Cin Cout per pixel and layer) / "
+                               "CUDA-event time"},
+        "warm_start": {
+            "params": net.n_params(), "train_instances": ntrain, "epochs": epochs, "batch": 32,
+            "data_generation_s": gen_s, "train_s": train_s, "train_loss_per_epoch": hist,
+            "heldout_instances": neval, "group": WS_GROUP,
+            "plain_per_instance_ms_total": res["plain_ms"], "plain_sampled_instances": len(res["plain_iters"]),
+            "batched_cold_ms_total": res["batched_ms"], "batched_warm_ms_total": warm_total,
+            "warm_inference_ms_total": res["warm_infer_ms"],
+            "speedup_vs_plain": res["plain_ms"] / warm_total, "speedup_vs_batched_cold": res["batched_ms"] / warm_total,
+            "median_iters": {"plain_cold_eps_scaling": med(res["plain_iters"]),
+                             "batched_cold_eps_scaling": med(res["batched_iters"]),
+                             "batched_warm": med(res["warm_iters"])},
+            "worst_marg_err_fp64": {"batched_cold": res["worst_err_batched"], "batched_warm": res["worst_err_warm"]},
+        },
+    }
+    return line
+
+
+# ----------------------------------------------------------------------------
 # the oracle on the host (baseline and --impl reference)
 # ----------------------------------------------------------------------------
 
@@ -982,6 +1081,7 @@ def sub_workloads(args, local_rank, cpu=True):
         ("points_tv", dict(workload="points", penalty="tv")),
         ("batch", dict(workload="batch")),
         ("bary", dict(workload="bary")),
+        ("warmstart", dict(workload="warmstart")),
     ]
     res = {"host_cores": cores}
     for name, over in subs:
@@ -993,6 +1093,8 @@ def sub_workloads(args, local_rank, cpu=True):
         try:
             if a.workload == "batch":
                 line = run_batch(a, 0, 1, local_rank)
+            elif a.workload == "warmstart":
+                line = run_warmstart(a, 0, 1, local_rank)
             elif a.workload == "grid2d":
                 line = run_ours(a, 0, 1, local_rank)
             else:
@@ -1021,7 +1123,10 @@ def main():
     ap.add_argument("--no-verify", action="store_true",
                     help="grid2d FP32/mixed: stop on the FP32 check alone and return float potentials")
     ap.add_argument("--workload", default="grid2d",
-                    choices=["grid2d", "batch", "points", "dense1d", "bary", "wf", "color"])
+                    choices=["grid2d", "batch", "points", "dense1d", "bary", "wf", "color", "warmstart"])
+    ap.add_argument("--ws-train", type=int, default=0, help="warmstart: training instances")
+    ap.add_argument("--ws-epochs", type=int, default=0, help="warmstart: epochs")
+    ap.add_argument("--ws-eval", type=int, default=0, help="warmstart: held-out instances")
     ap.add_argument("--wf-species", type=int, default=1, choices=[1, 2],
                     help="species of the wf workload (Sec. 5.3: the tumor example or its two-species extension)")
     ap.add_argument("--penalty", default="kl", choices=["kl", "tv"])
@@ -1049,6 +1154,8 @@ def main():
     try:
         if args.workload == "batch":
             line = run_batch(args, rank, world, local_rank)
+        elif args.workload == "warmstart":
+            line = run_warmstart(args, rank, world, local_rank)
         elif args.workload in ("points", "dense1d", "bary", "wf", "color"):
             line = run_single(args, rank, world, local_rank)
         else:

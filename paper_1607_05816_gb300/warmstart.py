@@ -321,3 +321,73 @@ def train_tc(net, P, Q, U, V, eps, lam, *, epochs=10, batch=32, lr=1e-3, seed=0)
             step += 1
         hist.append(float(net.loss_dev.item()) / max(1, nb))
     return hist
+
+
+def _ev_ms(fn):
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    out = fn()
+    e1.record()
+    e1.synchronize()
+    return e0.elapsed_time(e1), out
+
+
+def evaluate_tc(net, inst, H, W, *, group, tol=1e-6, plain_sample=16, max_iter=20000, check_every=10,
+                device="cuda"):
+    """Time to a `tol` marginal violation (confirmed in FP64, FP64 potentials
+    returned) on held-out instances whose consecutive blocks of `group` share
+    (eps, lambda), three ways:
+      plain  : uot_solve per instance, cold start with eps-scaling (1e-1 -> eps,
+               10 stages x 40 iterations when eps < 1e-1), on the first
+               `plain_sample` instances, scaled to all of them;
+      batched: uot_solve_many per group, cold start, same eps-scaling;
+      warm   : network inference, then uot_solve_many per group from the
+               predicted potentials at the final eps (no eps-scaling);
+    inference time is included in `warm`.  Returns a dict of totals and the
+    per-group iteration counts (a batch stops when its last problem does)."""
+    xs = [torch.as_tensor((np.arange(n) + 0.5) / n, dtype=torch.float32, device=device) for n in (H, W)]
+    geo = uot.Geometry.grid(xs, xs)
+    dx = torch.full((H * W,), 1.0 / (H * W), dtype=torch.float32, device=device)
+    P = torch.as_tensor(inst["P"], dtype=torch.float32, device=device)
+    Q = torch.as_tensor(inst["Q"], dtype=torch.float32, device=device)
+    n = P.shape[0]
+    res = {"n": n, "group": group, "plain_ms": 0.0, "batched_ms": 0.0, "warm_ms": 0.0, "warm_infer_ms": 0.0,
+           "plain_iters": [], "batched_iters": [], "warm_iters": [], "worst_err_warm": 0.0, "worst_err_batched": 0.0}
+
+    def sched(e):
+        return dict(eps_start=0.1, eps_stages=10, iters_per_stage=40) if e < 0.1 else dict(eps_start=None)
+    for k in range(min(plain_sample, n)):
+        e, lam = float(inst["eps"][k]), float(inst["lam"][k])
+        ms, (_, _, info) = _ev_ms(lambda: uot.solve(
+            geo, P[k].reshape(-1).contiguous(), dx, Q[k].reshape(-1).contiguous(), dx, uot.KL(lam), uot.KL(lam), e,
+            precision=uot.F32, max_iter=max_iter, tol=tol, check_every=check_every, launch_mode=2, out_f64=True,
+            verify=True, **sched(e)))
+        res["plain_ms"] += ms
+        res["plain_iters"].append(info["total_iters"])
+    res["plain_ms"] *= n / max(1, min(plain_sample, n))
+    for s in range(0, n, group):
+        sl = slice(s, min(n, s + group))
+        e, lam = float(inst["eps"][s]), float(inst["lam"][s])
+        Pg = P[sl].reshape(-1, H * W).contiguous()
+        Qg = Q[sl].reshape(-1, H * W).contiguous()
+        ms, (_, _, info) = _ev_ms(lambda: uot.solve_many(
+            geo, Pg, dx, Qg, dx, uot.KL(lam), uot.KL(lam), e, precision=uot.F32, max_iter=max_iter, tol=tol,
+            check_every=check_every, launch_mode=2, out_f64=True, verify=True, **sched(e)))
+        res["batched_ms"] += ms
+        res["batched_iters"].append(info["total_iters"])
+        res["worst_err_batched"] = max(res["worst_err_batched"], info["marg_err"])
+
+        def warm():
+            U0, V0 = net.predict(P[sl].contiguous(), Q[sl].contiguous(), inst["eps"][sl], inst["lam"][sl])
+            return uot.solve_many(geo, Pg, dx, Qg, dx, uot.KL(lam), uot.KL(lam), e, precision=uot.F32,
+                                  max_iter=max_iter, tol=tol, check_every=check_every, launch_mode=2, U0=U0, V0=V0,
+                                  out_f64=True, verify=True)
+        ms_inf, _ = _ev_ms(lambda: net.predict(P[sl].contiguous(), Q[sl].contiguous(), inst["eps"][sl],
+                                               inst["lam"][sl]))
+        ms, (Uw, Vw, info) = _ev_ms(warm)
+        res["warm_ms"] += ms
+        res["warm_infer_ms"] += ms_inf
+        res["warm_iters"].append(info["total_iters"])
+        res["worst_err_warm"] = max(res["worst_err_warm"], info["marg_err"])
+        res.setdefault("_last_warm", (s, Uw, Vw))
+    return res
