@@ -691,7 +691,7 @@ def run_warmstart(args, rank, world, local_rank):
     gen_s = time.perf_counter() - t0
     net = WS.WarmStartNetTC(channels=128, seed=rank)
     t0 = time.perf_counter()
-    hist = WS.train_tc(net, P, Q, Us, Vs, inst["eps"], inst["lam"], epochs=epochs, batch=32, lr=1e-3)
+    hist = WS.train_tc(net, P, Q, Us, Vs, inst["eps"], inst["lam"], epochs=epochs, batch=32, lr=3e-4)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
     del P, Q, Us, Vs

@@ -147,7 +147,8 @@ typedef struct {
                           first, contracting axis 0 first, and the V-update's last pass with the
                           next U-update's first), replayed as CUDA-graph blocks like 2; other
                           problems run as 2 */
-  const void* U0;      /* optional warm start [n] (NULL: U = 0) */
+  const void* U0;      /* optional warm start [n] (NULL: U = 0); -inf allowed (zero scaling),
+                          NaN or +inf rejected with UOT_EINVAL (uot_solve, uot_solve_many) */
   const void* V0;      /* optional warm start [m] (NULL: V = 0, i.e. b = 1 as in Algorithm 1) */
   int out_f64;         /* 1: U and V are written as double whatever the precision (UOT_F32 and
                           UOT_MIXED: the float-float state, about 48 significant bits, rounded

@@ -676,7 +676,7 @@ __global__ void k_mse_nhwc(const float* __restrict__ pred, const float* __restri
     for (int k = 1; k < 8; ++k) h[k] = __floats2bfloat162_rn(0.0f, 0.0f);
     uint4* dst = reinterpret_cast<uint4*>(grad + p * 16);
     dst[0] = reinterpret_cast<const uint4*>(h)[0];
-    dst[1] = reinterpret_cast<const uint4*>(h)[4];
+    dst[1] = reinterpret_cast<const uint4*>(h)[1];
   }
   __shared__ float red[256];
   red[threadIdx.x] = acc;

@@ -218,6 +218,15 @@ __global__ void k_log_scale(const double* __restrict__ a, int64_t n, double eps,
     U[i] = (a[i] > 0.0) ? eps * log(a[i]) : -kInf;
 }
 
+// *flag = 1 where a start potential is NaN or +inf (-inf is a valid zero scaling)
+__global__ void k_bad_start(const double* __restrict__ a, int64_t n, int ffmode, int* flag) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = ffmode ? (double)reinterpret_cast<const float2*>(a)[i].x : a[i];
+    if (v != v || v == kInf) *flag = 1;
+  }
+}
+
 __global__ void k_nan_flag(const double* __restrict__ a, int64_t n, int ffmode, int* flag) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -1407,6 +1416,20 @@ uot_status solve_impl(const uot_geom* g, int batch, const void* p, const void* d
     k_fill<<<nblocks(bm), kNT, 0, s>>>(V, bm, 0.0);
   }
   UOT_CK(cudaGetLastError());
+  if (o->U0 || o->V0) {
+    // a NaN or +inf start would spread through the log-sum-exps (all -inf, an empty plan)
+    UOT_CK(cudaMemsetAsync(flag, 0, 4, s));
+    count_launches(2);
+    k_bad_start<<<nblocks(bn), kNT, 0, s>>>(U, bn, prec != UOT_F64, flag);
+    k_bad_start<<<nblocks(bm), kNT, 0, s>>>(V, bm, prec != UOT_F64, flag);
+    int hbad = 0;
+    UOT_CK(cudaMemcpyAsync(&hbad, flag, 4, cudaMemcpyDeviceToHost, s));
+    UOT_CK(cudaStreamSynchronize(s));
+    if (hbad) {
+      g_last_error = "uot_solve: the warm start U0/V0 holds NaN or +inf";
+      return UOT_EINVAL;
+    }
+  }
 
   const std::vector<Stage> stages = eps_schedule(*o);
   const int check_every = o->check_every > 0 ? o->check_every : 1;

@@ -118,3 +118,31 @@ def test_trained_network_reduces_iterations():
         cold.append(ic)
         warm.append(iw)
     assert np.median(warm) < np.median(cold), (np.median(warm), np.median(cold))
+
+
+@pytest.mark.parametrize("prec", [U.F64, U.F32])
+@pytest.mark.parametrize("bad", [float("nan"), float("inf")])
+def test_bad_warm_start_rejected(prec, bad):
+    """A NaN or +inf start potential is refused with UOT_EINVAL (it would turn
+    every log-sum-exp into NaN or -inf); -inf (a zero scaling) is a valid start."""
+    inst = synth.warmstart_instances(2, 16, 16, seed=4, group=2)
+    dt = U._dtype(prec)
+    xs = [torch.as_tensor(a, dtype=dt, device="cuda") for a in inst["xs"]]
+    geo = U.Geometry.grid(xs, xs)
+    dx = torch.as_tensor(inst["dx"], dtype=dt, device="cuda").ravel()
+    P = torch.as_tensor(inst["P"].reshape(2, -1), dtype=dt, device="cuda")
+    Q = torch.as_tensor(inst["Q"].reshape(2, -1), dtype=dt, device="cuda")
+    e, lam = float(inst["eps"][0]), float(inst["lam"][0])
+    U0 = torch.zeros(256, dtype=dt, device="cuda")
+    U0[17] = -float("inf")
+    _, _, info = U.solve(geo, P[0], dx, Q[0], dx, U.KL(lam), U.KL(lam), e, precision=prec, max_iter=5, U0=U0)
+    assert info["status"] in ("UOT_OK", "UOT_NOT_CONVERGED")
+    U0[40] = bad
+    with pytest.raises(U.UotError) as ex:
+        U.solve(geo, P[0], dx, Q[0], dx, U.KL(lam), U.KL(lam), e, precision=prec, max_iter=5, U0=U0)
+    assert ex.value.status == -1
+    V0 = torch.zeros(2, 256, dtype=dt, device="cuda")
+    V0[1, 3] = bad
+    with pytest.raises(U.UotError) as ex:
+        U.solve_many(geo, P, dx, Q, dx, U.KL(lam), U.KL(lam), e, precision=prec, max_iter=5, V0=V0)
+    assert ex.value.status == -1

@@ -92,3 +92,28 @@ def test_tc_training_reduces_loss():
     assert net.err.item() == 0
     print("tc training loss per epoch:", hist)
     assert hist[-1] < 0.5 * hist[0]
+
+
+def test_mse_gradient_pads_with_zeros():
+    """The loss gradient buffer is 16 channels wide (the last layer's padded
+    output): channels 0, 1 hold 2 (pred - target s) / (2P), channels 2 to 15 are
+    written as exact zeros whatever the buffer held (here NaN), since the data
+    gradient multiplies them by the zero padding weights."""
+    N, HW = 3, 64 * 4
+    g = np.random.default_rng(7)
+    pred = torch.as_tensor(g.normal(size=(N * HW, 2)), dtype=torch.float32, device="cuda")
+    Ut = torch.as_tensor(g.normal(size=(N, HW)), dtype=torch.float32, device="cuda")
+    Vt = torch.as_tensor(g.normal(size=(N, HW)), dtype=torch.float32, device="cuda")
+    s = torch.as_tensor([0.5, 1.0, 2.0], dtype=torch.float32, device="cuda")
+    grad = torch.full((N * HW, 16), float("nan"), dtype=torch.bfloat16, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    U.mse_grad_nhwc(pred, Ut, Vt, s, grad, loss)
+    torch.cuda.synchronize()
+    got = grad.double().cpu().numpy()
+    assert np.all(got[:, 2:] == 0.0)
+    pr = pred.double().cpu().numpy()
+    sc = np.repeat(s.double().cpu().numpy(), HW)
+    tgt = np.stack([Ut.double().cpu().numpy().ravel() * sc, Vt.double().cpu().numpy().ravel() * sc], 1)
+    want = 2.0 * (pr - tgt) / pr.size
+    assert np.max(np.abs(got[:, :2] - want)) <= 2.0 ** -8 * np.max(np.abs(want))
+    assert abs(loss.item() - np.mean((pr - tgt) ** 2)) <= 1e-5 * np.mean((pr - tgt) ** 2)
