@@ -343,14 +343,55 @@ def eps_schedule(eps_final: float, eps_start: float | None = None, stages: int =
     return [(eps_start / rho ** s, iters_per_stage) for s in range(stages)]
 
 
+def kl_translation(logdx, logdy, logp, logq, F1: Div, F2: Div, U, V) -> float:
+    """The shift c for which (U + c, V - c) maximises the dual D_eps (Theorem
+    3.2) along the direction (1, -1), for lam1 KL and lam2 KL penalties.
+
+    NOT part of the paper's algorithms: this is the translation step of the
+    translation-invariant formulation of Sejourne, Vialard, Peyre (2022),
+    restated here from the dual.  U + c and V - c leave U_i + V_j, hence the
+    plan and the entropic term of D_eps, unchanged, so along the line only
+    -F1*(-U - c) - F2*(-V + c) varies; with the KL conjugate (div_conj) its
+    derivative in c is A e^{-c/lam1} - B e^{c/lam2}, A = sum_i dx_i p_i
+    e^{-U_i/lam1}, B = sum_j dy_j q_j e^{-V_j/lam2} (the masses of the marginals
+    that the optimality conditions predict), which vanishes at
+        c = lam1 lam2 / (lam1 + lam2) (log A - log B).
+    Entries with p_i = 0 (U_i = -inf) contribute nothing; c = 0 when either
+    measure is zero."""
+    if F1.kind != "kl" or F2.kind != "kl":
+        raise ValueError("the translation step is defined here for KL penalties on both sides")
+    U = np.ravel(U)
+    V = np.ravel(V)
+    ta = np.ravel(logdx + logp)
+    tb = np.ravel(logdy + logq)
+    fa = np.isfinite(ta) & np.isfinite(U)
+    fb = np.isfinite(tb) & np.isfinite(V)
+    if not fa.any() or not fb.any():
+        return 0.0
+    la = float(lse(ta[fa] - U[fa] / F1.lam))
+    lb = float(lse(tb[fb] - V[fb] / F2.lam))
+    return F1.lam * F2.lam / (F1.lam + F2.lam) * (la - lb)
+
+
+def translate_log(logdx, logdy, logp, logq, F1: Div, F2: Div, U, V):
+    """(U + c, V - c) with c = kl_translation (finite entries only)."""
+    c = kl_translation(np.broadcast_to(logdx, np.shape(logp)), np.broadcast_to(logdy, np.shape(logq)),
+                       logp, logq, F1, F2, U, V)
+    return U + c, V - c
+
+
 def iterate_log(geom: Geometry, logdx, logdy, logp, logq, F1: Div, F2: Div,
-                eps: float, iters: int, U=None, V=None, history: bool = False):
+                eps: float, iters: int, U=None, V=None, history: bool = False,
+                translate_every: int = 0):
     """`iters` scaling iterations in the log domain at fixed eps.
 
     One iteration (eq. S, Sec. 3.3, in the log form of Sec. 4.3):
       S = eps log K(b.dy);  U = prox_update_F1(S)
       T = eps log K^T(a.dx); V = prox_update_F2(T)
     Starts from V = 0 (b = 1, Algorithm 1) unless V is given.
+    translate_every > 0 (KL on both sides; not in the paper): after the
+    V-update of iterations translate_every, 2 translate_every, ... the
+    translation step of translate_log.
     Returns U, V and, if history, the marginal violation of each iterate
     (see marginal_violation) computed before the a-update that follows it.
     """
@@ -359,7 +400,7 @@ def iterate_log(geom: Geometry, logdx, logdy, logp, logq, F1: Div, F2: Div,
     if U is None:
         U = np.zeros(np.shape(logp))
     errs = []
-    for _ in range(iters):
+    for k in range(iters):
         S = apply_K_log(geom, V, logdy, eps)
         Un = prox_update_log(F1, logp, S, eps)
         if history:
@@ -367,12 +408,15 @@ def iterate_log(geom: Geometry, logdx, logdy, logp, logq, F1: Div, F2: Div,
         U = Un
         T = apply_K_log(geom, U, logdx, eps, transpose=True)
         V = prox_update_log(F2, logq, T, eps)
+        if translate_every > 0 and (k + 1) % translate_every == 0:
+            U, V = translate_log(logdx, logdy, logp, logq, F1, F2, U, V)
     return (U, V, errs) if history else (U, V)
 
 
 def solve_log(geom: Geometry, dx, dy, p, q, F1: Div, F2: Div, eps: float,
               max_iter: int, tol: float = 0.0, eps_start=None, stages: int = 10,
-              iters_per_stage: int = 100, check_every: int = 1, U0=None, V0=None):
+              iters_per_stage: int = 100, check_every: int = 1, U0=None, V0=None,
+              translate: bool = False):
     """eps-scaling then iterations at eps until marginal_violation <= tol.
 
     The violation is measured every `check_every` iterations, in iterations
@@ -380,11 +424,15 @@ def solve_log(geom: Geometry, dx, dy, p, q, F1: Div, F2: Div, eps: float,
     iterate l happens inside iteration l+1 (its a-update), so the returned
     state is one iteration past the first one under tol; `iters` counts
     iterations at the final eps only.
+    translate (KL on both sides; not in the paper): the translation step of
+    translate_log after the V-update of every checked iteration, and of
+    iterations check_every, 2 check_every, ... of each eps-scaling stage.
     """
     logdx, logdy, logp, logq = map(safe_log, (dx, dy, p, q))
     U, V = U0, V0
     for e, n in eps_schedule(eps, eps_start, stages, iters_per_stage):
-        U, V = iterate_log(geom, logdx, logdy, logp, logq, F1, F2, e, n, U, V)
+        U, V = iterate_log(geom, logdx, logdy, logp, logq, F1, F2, e, n, U, V,
+                           translate_every=check_every if translate else 0)
     if V is None:
         V = np.zeros(np.shape(q))
     if U is None:
@@ -394,7 +442,8 @@ def solve_log(geom: Geometry, dx, dy, p, q, F1: Div, F2: Div, eps: float,
     while it < max_iter:
         S = apply_K_log(geom, V, logdy, eps)
         Un = prox_update_log(F1, logp, S, eps)
-        if (it + 1) % check_every == 0 or it == max_iter - 1:
+        checked = (it + 1) % check_every == 0 or it == max_iter - 1
+        if checked:
             err = _violation_from(U, Un, S, logdx, eps)
             if it > 0 and tol > 0 and err <= tol:  # tol = 0 runs max_iter
                 stop = True
@@ -405,6 +454,8 @@ def solve_log(geom: Geometry, dx, dy, p, q, F1: Div, F2: Div, eps: float,
         U = Un
         T = apply_K_log(geom, U, logdx, eps, transpose=True)
         V = prox_update_log(F2, logq, T, eps)
+        if translate and checked:
+            U, V = translate_log(logdx, logdy, logp, logq, F1, F2, U, V)
         it += 1
         if stop:
             break

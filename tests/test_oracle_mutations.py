@@ -58,6 +58,11 @@ PLANTS = [
      "w = np.ones(np.size(dy))", "barycentric_projection"),
     ("colour: empty rows sent to 0", "return np.where(den[:, None] > 0, T, X)",
      "return np.where(den[:, None] > 0, T, 0.0)", "barycentric_projection"),
+    ("translation: sign of the shift", "return U + c, V - c", "return U - c, V + c", "translation"),
+    ("translation: one-sided lambda weight", "F1.lam * F2.lam / (F1.lam + F2.lam) * (la - lb)",
+     "0.5 * F1.lam * (la - lb)", "translation"),
+    ("translation: dx weights dropped", "ta = np.ravel(logdx + logp)", "ta = np.ravel(0.0 * logdx + logp)",
+     "translation"),
 ]
 
 

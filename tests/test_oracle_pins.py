@@ -1076,3 +1076,73 @@ def test_violation_measure_on_a_hand_example():
     S = np.array([0.0, 0.0, -np.inf])
     logdx = np.log([0.25, 0.75, 0.5])
     assert math.isclose(_violation_from(U_old, U_new, S, logdx, eps), 5.0 / 6.0, rel_tol=1e-14)
+
+
+# --------------------------------------------------------------------------
+# translation step along (U + c, V - c), KL penalties (not in the paper)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("l1,l2", [(0.5, 0.5), (0.3, 2.0)])
+def test_translation_maximises_the_dual_on_its_line(l1, l2):
+    """kl_translation's c against a brute-force 1-D maximisation of D_eps
+    (Theorem 3.2) over t on the line (U + t, V - t), non-uniform weights, a
+    zero density (U = -inf there), a state pushed off the line's maximum."""
+    geom, dx, dy, p, q = small_problem(7, 6, 31, zeros=True)
+    eps = 0.05
+    F1, F2 = O.KL(l1), O.KL(l2)
+    logs = (np.log(dx), np.log(dy), O.safe_log(p), np.log(q))
+    U, V = O.iterate_log(geom, *logs, F1, F2, eps, 3)
+    U, V = U + 0.4, V - 0.1
+    c = O.kl_translation(*logs, F1, F2, U, V)
+    r = optimize.minimize_scalar(lambda t: -O.dual(geom, dx, dy, p, q, F1, F2, eps, U + t, V - t),
+                                 bracket=(-1.0, 0.0, 1.0), tol=1e-12)
+    assert abs(c - r.x) <= 1e-6, (c, r.x)
+    Ut, Vt = O.translate_log(*logs, F1, F2, U, V)
+    assert np.array_equal(np.isneginf(Ut), np.isneginf(U))
+    assert O.dual(geom, dx, dy, p, q, F1, F2, eps, Ut, Vt) > O.dual(geom, dx, dy, p, q, F1, F2, eps, U, V)
+    # the plan, hence its marginals, is unchanged
+    for a, b in zip(O.marginals(geom, dx, dy, Ut, Vt, eps), O.marginals(geom, dx, dy, U, V, eps)):
+        assert np.allclose(a, b, rtol=1e-12, atol=0)
+
+
+def test_translation_keeps_the_dual_ascent_monotone():
+    """Sinkhorn half-steps and the translation step are exact maximisations of
+    D_eps over blocks of variables: the dual never decreases."""
+    geom, dx, dy, p, q = small_problem(8, 9, 32)
+    eps = 0.03
+    F1, F2 = O.KL(2.0), O.KL(0.7)
+    logs = (np.log(dx), np.log(dy), np.log(p), np.log(q))
+    U, V = O.iterate_log(geom, *logs, F1, F2, eps, 1)
+    prev = O.dual(geom, dx, dy, p, q, F1, F2, eps, U, V)
+    for _ in range(40):
+        U, V = O.iterate_log(geom, *logs, F1, F2, eps, 1, U, V, translate_every=1)
+        d = O.dual(geom, dx, dy, p, q, F1, F2, eps, U, V)
+        assert d >= prev - 1e-13 * abs(prev)
+        prev = d
+
+
+def test_translation_same_fixed_point_fewer_iterations():
+    """With lambda / eps = 300 the plain iteration's translation mode decays
+    by (lam / (lam + eps))^2 per iteration; the translated iteration reaches the
+    same fixed point in a small fraction of the iterations."""
+    xs = [synth.grid_axis(50)]
+    ys = [synth.grid_axis(45)]
+    geom = O.Geometry("grid", xs=xs, ys=ys)
+    g = synth.rng(33)
+    dx, dy = np.full(50, 1 / 50), np.full(45, 1 / 45)
+    p = g.uniform(0.2, 2.0, 50)
+    q = 1.7 * g.uniform(0.2, 2.0, 45)
+    F = O.KL(3.0)
+    eps = 0.01
+    plain = O.solve_log(geom, dx, dy, p, q, F, F, eps, max_iter=100000, tol=1e-11, check_every=5)
+    tr = O.solve_log(geom, dx, dy, p, q, F, F, eps, max_iter=100000, tol=1e-11, check_every=5, translate=True)
+    assert plain["err"] <= 1e-11 and tr["err"] <= 1e-11
+    assert tr["iters"] * 4 < plain["iters"], (tr["iters"], plain["iters"])
+    assert np.max(np.abs(tr["U"] - plain["U"])) <= 1e-7
+    assert np.max(np.abs(tr["V"] - plain["V"])) <= 1e-7
+
+
+def test_translation_requires_kl():
+    geom, dx, dy, p, q = small_problem(4, 4, 34)
+    with pytest.raises(ValueError):
+        O.kl_translation(np.log(dx), np.log(dy), np.log(p), np.log(q), O.KL(1.0), O.TV(1.0), np.zeros(4), np.zeros(4))
