@@ -161,10 +161,25 @@ typedef struct {
                           threshold; once the FP32 check stops decreasing (its rounding
                           floor), the remaining iterations run in FP64 from the current
                           state, checked every iteration, until the FP64 violation is
-                          <= tol.  marg_err is then the FP64 value.  Launch modes 1 and 3
-                          run as 2.  0: the FP32 check decides. */
+                          <= tol.  marg_err is then the FP64 value.  Launch mode 1 runs as
+                          0, launch mode 3 as 2.  0: the FP32 check decides. */
   double mixed_switch; /* UOT_MIXED with tol > 0: violation at which the tensor-core (BF16)
                           passes hand over to the FP32 passes; 0 means 1e-3 */
+  int translate;       /* 1 (uot_solve, uot_solve_many; log domain; UOT_DIV_KL on both sides,
+                          else UOT_EUNSUPPORTED): after the V-update of every checked iteration
+                          (every check_every iterations at the final eps, the FP64 finish of
+                          opts.verify included) and of iterations check_every, 2 check_every,
+                          ... of each eps-scaling stage, U += c and V -= c per problem with
+                          c = lam1 lam2 / (lam1 + lam2) (log A - log B), A = sum_i dx_i p_i
+                          e^{-U_i/lam1}, B = sum_j dy_j q_j e^{-V_j/lam2}: the exact maximum of
+                          the dual (Theorem 3.2) along that direction, which leaves the plan
+                          unchanged.  Not in the paper (the translation step of Sejourne,
+                          Vialard, Peyre 2022): the scaling iteration damps this direction
+                          only by (lam / (lam + eps))^2 per iteration, so for lam >> eps it
+                          removes the slowest mode, and it bounds how far FP32 rounding can
+                          push the state along it.  Same fixed point; different iterates.
+                          Launch mode 1 runs as 0, launch mode 3 as 2.  0: Algorithm 2 as
+                          printed. */
 } uot_opts;
 
 typedef struct {

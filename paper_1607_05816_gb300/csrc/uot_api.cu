@@ -1142,11 +1142,12 @@ uot_result empty_result() {
   return r;
 }
 
-// only uot_solve and uot_solve_many honour out_f64 and verify
+// only uot_solve and uot_solve_many honour out_f64, verify and translate
 uot_status check_opts(const uot_opts* o, bool solve_outputs = false) {
   if (!o || !prec_ok(o->precision)) return UOT_EINVAL;
   if ((o->out_f64 != 0 && o->out_f64 != 1) || (o->verify != 0 && o->verify != 1)) return UOT_EINVAL;
-  if (!solve_outputs && (o->out_f64 || o->verify)) return UOT_EUNSUPPORTED;
+  if (o->translate != 0 && o->translate != 1) return UOT_EINVAL;
+  if (!solve_outputs && (o->out_f64 || o->verify || o->translate)) return UOT_EUNSUPPORTED;
   if (!(o->eps > 0.0) || !isfinite(o->eps)) return UOT_EINVAL;
   if (o->max_iter < 0 || o->check_every < 0 || !(o->tol >= 0.0)) return UOT_EINVAL;
   if (o->eps_stages < 0 || o->iters_per_stage < 0) return UOT_EINVAL;
@@ -1330,6 +1331,9 @@ uot_status solve_impl(const uot_geom* g, int batch, const void* p, const void* d
   if (o->plain_scaling && (g->kind != UOT_GEOM_DENSE || o->precision != UOT_F64 || batch != 1))
     return UOT_EUNSUPPORTED;
   if (g->kind == UOT_GEOM_GRID && batch > 65535) return UOT_EUNSUPPORTED;
+  const bool translate = o->translate != 0;
+  if (translate && (F1->kind != UOT_DIV_KL || F2->kind != UOT_DIV_KL || o->plain_scaling || batch > 65535))
+    return UOT_EUNSUPPORTED;
   const int prec = o->precision;
   const int64_t n = g->n, m = g->m;
   const int64_t bn = n * batch, bm = m * batch;
@@ -1360,15 +1364,16 @@ uot_status solve_impl(const uot_geom* g, int batch, const void* p, const void* d
   sc.reserve<double>(m);   // logdy
   sc.reserve<double>(bm);  // V
   sc.reserve<double>(2 * (size_t)batch + 4);  // err accumulators + flag
+  if (translate) sc.reserve<double2>(kl_translate_part_count(n, m, batch));
   // one persistent cooperative launch for FP32 grid problems
   const std::vector<Stage> stages_p = eps_schedule(*o);
   const int nst = (int)stages_p.size();
   const bool verify = o->verify && prec != UOT_F64 && o->tol > 0.0 && !o->plain_scaling;
   const bool persist = o->launch_mode == 1 && prec == UOT_F32 && g->kind == UOT_GEOM_GRID &&
-                       batch == 1 && !o->plain_scaling && !verify;
+                       batch == 1 && !o->plain_scaling && !verify && !translate;
   // two kernels per iteration, each fusing two passes on one line (2-D FP32 grids)
   const bool fused2d = o->launch_mode == 3 && prec == UOT_F32 && g->kind == UOT_GEOM_GRID && g->ndim == 2 &&
-                       batch == 1 && !o->plain_scaling && !verify &&
+                       batch == 1 && !o->plain_scaling && !verify && !translate &&
                        grid_fused2_smem(std::max(g->shape_y[0], g->shape_x[1]), std::max(g->shape_x[0], g->shape_y[1])) <=
                            160 * 1024;
   if (persist) {
@@ -1397,6 +1402,7 @@ uot_status solve_impl(const uot_geom* g, int batch, const void* p, const void* d
   double* V = sc.take<double>(bm);
   double* acc = sc.take<double>(2 * (size_t)batch + 4);
   int* flag = (int*)(acc + 2 * (size_t)batch);
+  double2* trpart = translate ? sc.take<double2>(kl_translate_part_count(n, m, batch)) : nullptr;
   std::vector<double> acc_h(2 * (size_t)batch);
   UOT_SCRATCH_OK(sc);
   UOT_CK(to_log(prec, p, bn, logp, s));
@@ -1759,17 +1765,21 @@ uot_status solve_impl(const uot_geom* g, int batch, const void* p, const void* d
       if (stalled()) polish = stop = true;
       return cudaSuccess;
     };
-    auto iteration = [&](double eps, bool check, cudaStream_t st) -> cudaError_t {
+    // shift: the translation step after the V-update (opts.translate)
+    auto iteration = [&](double eps, bool check, bool shift, cudaStream_t st) -> cudaError_t {
       cudaError_t e;
       Epilogue e1 = prox_epilogue(D1, logp, U, logdx, check ? acc : nullptr, eps);
       e1.bstride = e1.bstride_p = n;
       if ((e = G.apply(0, V, logdy, eps, e1, st, check ? acc : nullptr)) != cudaSuccess) return e;
       Epilogue e2 = prox_epilogue(D2, logq, V, logdy, nullptr, eps);
       e2.bstride = e2.bstride_p = m;
-      return G.apply(1, U, logdx, eps, e2, st);
+      if ((e = G.apply(1, U, logdx, eps, e2, st)) != cudaSuccess || !shift) return e;
+      return launch_kl_translate(U, V, logp, logq, logdx, logdy, n, m, batch, prec != UOT_F64, D1.lam, D2.lam,
+                                 trpart, st);
     };
     for (const Stage& sg : stages)
-      for (int k = 0; k < sg.iters; ++k, ++total) UOT_CK(iteration(sg.eps, false, s));
+      for (int k = 0; k < sg.iters; ++k, ++total)
+        UOT_CK(iteration(sg.eps, false, translate && (k + 1) % check_every == 0, s));
     // launch_mode 2: once a block of check_every iterations (the last one
     // checked) repeats the same launches -- same eps, shifts from the previous
     // iteration -- it is captured once as a CUDA graph and replayed per block.
@@ -1780,7 +1790,7 @@ uot_status solve_impl(const uot_geom* g, int batch, const void* p, const void* d
         if (!bg.exec) {
           cudaError_t e = bg.capture([&](cudaStream_t cs) -> cudaError_t {
             for (int k = 0; k < check_every; ++k) {
-              cudaError_t e2 = iteration(o->eps, k == check_every - 1, cs);
+              cudaError_t e2 = iteration(o->eps, k == check_every - 1, translate && k == check_every - 1, cs);
               if (e2 != cudaSuccess) return e2;
             }
             return cudaSuccess;
@@ -1806,7 +1816,7 @@ uot_status solve_impl(const uot_geom* g, int batch, const void* p, const void* d
         continue;
       }
       const bool check = ((it + 1) % check_every == 0) || (it == o->max_iter - 1);
-      UOT_CK(iteration(o->eps, check, s));
+      UOT_CK(iteration(o->eps, check, translate && check, s));
       ++it;
       ++total;
       if (check) {
@@ -1841,6 +1851,9 @@ uot_status solve_impl(const uot_geom* g, int batch, const void* p, const void* d
           break;
         }
         UOT_CK(c64.b_update(D2, o->eps, s));
+        if (translate && (it + 1) % check_every == 0)
+          UOT_CK(launch_kl_translate(c64.U, c64.V, c64.logp, c64.logq, c64.logdx, c64.logdy, n, m, batch, 0,
+                                     D1.lam, D2.lam, trpart, s));
         ++it;
         ++total;
         ++npolish;

@@ -672,6 +672,17 @@ int batch_force_warps(int warps);  // 8 or 16 forces a CTA size, 0 returns to th
 std::string batch_tune_table();
 cudaError_t launch_batch(const BatchArgs& a, int variant, int grid, cudaStream_t s);
 
+// Translation step for lam1 KL / lam2 KL penalties (uot_opts.translate; not
+// in the paper): per problem b, c_b = lam1 lam2 / (lam1 + lam2) (log A_b -
+// log B_b), A_b = sum_i dx_i p_bi e^{-U_bi/lam1}, B_b = sum_j dy_j q_bj
+// e^{-V_bj/lam2}; then U_b += c_b, V_b -= c_b (the plan is unchanged).  U, V,
+// log p, log q [batch][n or m], log dx, log dy [n or m], all FP64 or all
+// float-float (ff = 1); part holds kl_translate_part_count double2.
+size_t kl_translate_part_count(int64_t n, int64_t m, int batch);
+cudaError_t launch_kl_translate(double* U, double* V, const double* logp, const double* logq,
+                                const double* logdx, const double* logdy, int64_t n, int64_t m, int batch,
+                                int ff, double lam1, double lam2, double2* part, cudaStream_t s);
+
 // Algorithm 1 (non-log) half-step on a stored FP64 kernel:
 //   a_i = proxdiv_F(sum_j K_ij b_j w_j, eps), also the violation terms.
 cudaError_t launch_alg1_half(const double* K, int nrows, int nin, const double* b,

@@ -53,7 +53,8 @@ class COpts(C.Structure):
                 ("eps_stages", C.c_int), ("iters_per_stage", C.c_int), ("max_iter", C.c_int),
                 ("tol", C.c_double), ("check_every", C.c_int), ("plain_scaling", C.c_int),
                 ("launch_mode", C.c_int), ("U0", C.c_void_p), ("V0", C.c_void_p),
-                ("out_f64", C.c_int), ("verify", C.c_int), ("mixed_switch", C.c_double)]
+                ("out_f64", C.c_int), ("verify", C.c_int), ("mixed_switch", C.c_double),
+                ("translate", C.c_int)]
 
 
 class CBatchProblem(C.Structure):
@@ -385,11 +386,12 @@ def _check(status, what):
 def solve(geom: Geometry, p, dx, q, dy, F1: Div, F2: Div, eps: float, *, precision=F64,
           max_iter=1000, tol=0.0, check_every=10, eps_start=None, eps_stages=10,
           iters_per_stage=100, plain_scaling=False, U0=None, V0=None, U=None, V=None,
-          launch_mode=0, out_f64=False, verify=False, mixed_switch=0.0):
+          launch_mode=0, out_f64=False, verify=False, mixed_switch=0.0, translate=False):
     """uot_solve: returns (U, V, result dict).  Inputs are CUDA tensors of the
     precision's dtype; U, V (optional) are preallocated outputs (float64 when
     out_f64).  verify: the stop is confirmed by an FP64 evaluation of the
-    violation (FP32 / mixed paths)."""
+    violation (FP32 / mixed paths).  translate (KL on both sides): the dual's
+    exact maximum along (U + c, V - c) after every checked iteration."""
     lib = load()
     dt = _dtype(precision)
     odt = torch.float64 if out_f64 else dt
@@ -398,7 +400,7 @@ def solve(geom: Geometry, p, dx, q, dy, F1: Div, F2: Div, eps: float, *, precisi
     o = COpts(precision, float(eps), float(eps_start) if eps_start else 0.0, int(eps_stages),
               int(iters_per_stage), int(max_iter), float(tol), int(check_every),
               int(bool(plain_scaling)), int(launch_mode), _ptr(U0, dt, "U0"), _ptr(V0, dt, "V0"),
-              int(bool(out_f64)), int(bool(verify)), float(mixed_switch))
+              int(bool(out_f64)), int(bool(verify)), float(mixed_switch), int(bool(translate)))
     r = CResult()
     g = geom.c(precision)
     st = lib.uot_solve(C.byref(g), _ptr(p, dt, "p"), _ptr(dx, dt, "dx"), _ptr(q, dt, "q"),
@@ -535,7 +537,7 @@ def color_transfer(img_x, img_y, F2: Div, eps=0.002, iters=2000, bins=(64, 32, 3
 def solve_many(geom: Geometry, P, dx, Q, dy, F1: Div, F2: Div, eps, *, precision=F64,
                max_iter=1000, tol=0.0, check_every=10, eps_start=None, eps_stages=10,
                iters_per_stage=100, U0=None, V0=None, U=None, V=None, launch_mode=0,
-               out_f64=False, verify=False, mixed_switch=0.0):
+               out_f64=False, verify=False, mixed_switch=0.0, translate=False):
     """uot_solve_many: P [B, n], Q [B, m] densities of B independent problems
     sharing geometry, weights, eps and penalties.  Returns (U [B,n], V [B,m], info)."""
     lib = load()
@@ -547,7 +549,7 @@ def solve_many(geom: Geometry, P, dx, Q, dy, F1: Div, F2: Div, eps, *, precision
     o = COpts(precision, float(eps), float(eps_start) if eps_start else 0.0, int(eps_stages),
               int(iters_per_stage), int(max_iter), float(tol), int(check_every), 0, int(launch_mode),
               _ptr(U0, dt, "U0"), _ptr(V0, dt, "V0"), int(bool(out_f64)), int(bool(verify)),
-              float(mixed_switch))
+              float(mixed_switch), int(bool(translate)))
     r = CResult()
     g = geom.c(precision)
     st = lib.uot_solve_many(C.byref(g), int(B), _ptr(P, dt, "P"), _ptr(dx, dt, "dx"),

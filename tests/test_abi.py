@@ -3,6 +3,7 @@ include/uot.h declares (no compute calls: these run without a GPU)."""
 import ctypes
 import os
 import re
+import subprocess
 
 from paper_1607_05816_gb300 import build, uot
 
@@ -34,11 +35,40 @@ def test_version_string():
     assert b"sm_103a" in lib.uot_version()
 
 
-def test_struct_layouts_match_header():
-    # sizes follow from the field lists in include/uot.h on LP64
-    assert ctypes.sizeof(uot.CDiv) == 32
-    assert ctypes.sizeof(uot.COpts) == 8 + 8 + 8 + 4 + 4 + 4 + 4 + 8 + 4 + 4 + 4 + 4 + 8 + 8 + 4 + 4 + 8
-    assert ctypes.sizeof(uot.CResult) == 4 + 4 + 8 + 8 + 4 + 4 + 4 + 4 + 8 + 4 + 4
+# the header's field names, in order, for each struct the binding mirrors
+C_FIELDS = {
+    "uot_div": (uot.CDiv, ["kind", "lambda", "alpha", "beta"]),
+    "uot_geom": (uot.CGeom, ["kind", "n", "m", "C", "ndim", "shape_x", "shape_y", "axes_x", "axes_y", "x", "y",
+                             "d"]),
+    "uot_opts": (uot.COpts, ["precision", "eps", "eps_start", "eps_stages", "iters_per_stage", "max_iter", "tol",
+                             "check_every", "plain_scaling", "launch_mode", "U0", "V0", "out_f64", "verify",
+                             "mixed_switch", "translate"]),
+    "uot_result": (uot.CResult, ["iters", "total_iters", "marg_err", "ms", "status", "verifications",
+                                 "polish_iters", "marg_err_fp32", "mixed_iters"]),
+    "uot_batch_problem": (uot.CBatchProblem, ["n", "m", "F1", "F2"]),
+}
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """sizeof and every field offset of the ctypes mirrors equal what the C
+    compiler lays out from include/uot.h."""
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "uot.h"', "int main(void) {"]
+    for name, (_, fields) in C_FIELDS.items():
+        lines.append(f'  printf("{name} %zu", sizeof({name}));')
+        for f in fields:
+            lines.append(f'  printf(" %zu", offsetof({name}, {f}));')
+        lines.append('  printf("\\n");')
+    lines.append("  return 0;\n}")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {ln.split()[0]: [int(v) for v in ln.split()[1:]] for ln in out if ln.strip()}
+    for name, (cls, fields) in C_FIELDS.items():
+        assert len(cls._fields_) == len(fields), name
+        want = [ctypes.sizeof(cls)] + [getattr(cls, f[0]).offset for f in cls._fields_]
+        assert got[name] == want, (name, got[name], want)
 
 
 def test_no_cpu_fallback(monkeypatch):
