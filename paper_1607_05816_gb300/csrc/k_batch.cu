@@ -370,6 +370,77 @@ __device__ void half_step(const Half& h, float4* st0, typename Stage1<D>::T* st1
   __syncthreads();
 }
 
+// log sum_i e^{lw_i + lp_i - W_i / lam} over one side of the CTA's problem
+// (entries with lp_i = -inf or W_i = -inf take no part); every thread gets
+// the result.  Shifts in FP64, exponentials of shifted differences in FP32.
+template <int NW>
+__device__ double block_side_lse(const float2* W, const float2* lp, const float2* lw, int len, double inv_lam,
+                                 double* red) {
+  constexpr int NT = NW * 32;
+  double mx = -kInf, sm = 0.0;
+  for (int i = threadIdx.x; i < len; i += NT) {
+    const float2 l = lp[i], w = W[i];
+    if (l.x == -INFINITY || w.x == -INFINITY) continue;
+    const float2 g = lw[i];
+    const double t = ((double)g.x + (double)g.y) + ((double)l.x + (double)l.y) - ((double)w.x + (double)w.y) * inv_lam;
+    if (t > mx) {
+      sm = sm * (double)expf((float)(mx - t)) + 1.0;
+      mx = t;
+    } else {
+      sm += (double)expf((float)(t - mx));
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    double m2 = __shfl_down_sync(0xffffffffu, mx, o);
+    double s2 = __shfl_down_sync(0xffffffffu, sm, o);
+    if (m2 > mx) {
+      const double tm = mx, ts = sm;
+      mx = m2;
+      sm = s2;
+      m2 = tm;
+      s2 = ts;
+    }
+    if (m2 != -kInf) sm += s2 * (double)expf((float)(m2 - mx));
+  }
+  __syncthreads();  // red is free
+  if ((threadIdx.x & 31) == 0) {
+    red[threadIdx.x >> 5] = mx;
+    red[NW + (threadIdx.x >> 5)] = sm;
+  }
+  __syncthreads();
+  double M = -kInf, S = 0.0;
+  for (int w = 0; w < NW; ++w) M = fmax(M, red[w]);
+  if (M == -kInf) return -kInf;
+  for (int w = 0; w < NW; ++w)
+    if (red[w] != -kInf) S += red[NW + w] * (double)expf((float)(red[w] - M));
+  return M + log(S);
+}
+
+// Translation step (uot_opts.translate; not in the paper: the translation-
+// invariant formulation of Sejourne, Vialard, Peyre 2022): U += c, V -= c with
+// c = lam1 lam2 / (lam1 + lam2) (log A - log B), the exact maximum of the dual
+// along that direction for KL penalties; A = sum dx p e^{-U/lam1}, B = sum dy
+// q e^{-V/lam2}.  The plan is unchanged.
+template <int NW>
+__device__ void translate_problem(float2* U, float2* V, const float2* lpU, const float2* lwU, const float2* lpV,
+                                  const float2* lwV, int n, int m, double2 lam, double* red) {
+  constexpr int NT = NW * 32;
+  const double la = block_side_lse<NW>(U, lpU, lwU, n, 1.0 / lam.x, red);
+  const double lb = block_side_lse<NW>(V, lpV, lwV, m, 1.0 / lam.y, red);
+  const double c = (la != -kInf && lb != -kInf) ? lam.x * lam.y / (lam.x + lam.y) * (la - lb) : 0.0;
+  const ff cp = ff_make(c), cn = ff_make(-c);
+  for (int i = threadIdx.x; i < n; i += NT) {
+    const float2 u = U[i];
+    if (!isinf(u.x)) U[i] = ff2(ff_add(ffl(u), cp));
+  }
+  for (int j = threadIdx.x; j < m; j += NT) {
+    const float2 v = V[j];
+    if (!isinf(v.x)) V[j] = ff2(ff_add(ffl(v), cn));
+  }
+  __syncthreads();
+}
+
 template <int D, int NW>
 __global__ void __launch_bounds__(NW * 32, NW == 8 ? 3 : 2) batch_solve(BatchArgs a) {
   constexpr int NT = NW * 32;
@@ -378,6 +449,7 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 3 : 2) batch_solve(BatchArg
   __shared__ float red[2 * NW];
   __shared__ int s_prob;
   __shared__ int s_stop;
+  __shared__ double tr_red[2 * NW];
   const int tid = threadIdx.x;
   const int lmax = a.nmax > a.mmax ? a.nmax : a.mmax;
   float4* st0 = smem4;
@@ -440,6 +512,9 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 3 : 2) batch_solve(BatchArg
         half_step<D, NW>(h1, st0, st1, part, red, num, den);
         float dn = 0.0f, dd = 0.0f;
         half_step<D, NW>(h2, st0, st1, part, red, dn, dd);
+        if (a.translate && (final_stage ? check : (it + 1) % a.check_every == 0))
+          translate_problem<NW>(U, V, a.logp + xo, a.logdx + xo, a.logq + yo, a.logdy + yo, n, m, a.lam[k],
+                                tr_red);
         if (final_stage) it_final = it + 1;
         if (check) {
           const float2 tot = block_sum2<NT>(num, den, red);
@@ -572,6 +647,7 @@ BEntry tune_batch(const BatchArgs& full, const int* h_order, cudaStream_t s) {
     a.max_iter = 6;
     a.tol = 0.0f;
     a.check_every = 1 << 30;
+    a.translate = 0;
     float best = 1e30f;
     for (int v = 0; v < 2; ++v) {
       const int per = ctas_any(a.d, v, a.nmax, a.mmax);

@@ -1142,12 +1142,13 @@ uot_result empty_result() {
   return r;
 }
 
-// only uot_solve and uot_solve_many honour out_f64, verify and translate
-uot_status check_opts(const uot_opts* o, bool solve_outputs = false) {
+// only uot_solve and uot_solve_many honour out_f64 and verify; translate also uot_solve_batch
+uot_status check_opts(const uot_opts* o, bool solve_outputs = false, bool allow_translate = false) {
   if (!o || !prec_ok(o->precision)) return UOT_EINVAL;
   if ((o->out_f64 != 0 && o->out_f64 != 1) || (o->verify != 0 && o->verify != 1)) return UOT_EINVAL;
   if (o->translate != 0 && o->translate != 1) return UOT_EINVAL;
-  if (!solve_outputs && (o->out_f64 || o->verify || o->translate)) return UOT_EUNSUPPORTED;
+  if (!solve_outputs && (o->out_f64 || o->verify)) return UOT_EUNSUPPORTED;
+  if (!solve_outputs && !allow_translate && o->translate) return UOT_EUNSUPPORTED;
   if (!(o->eps > 0.0) || !isfinite(o->eps)) return UOT_EINVAL;
   if (o->max_iter < 0 || o->check_every < 0 || !(o->tol >= 0.0)) return UOT_EINVAL;
   if (o->eps_stages < 0 || o->iters_per_stage < 0) return UOT_EINVAL;
@@ -3609,7 +3610,7 @@ uot_status uot_solve_batch(int nprob, const uot_batch_problem* probs, int d, con
                            const void* dy, const uot_opts* o, void* Uout, void* Vout, int* iters,
                            double* errs, uot_result* res, void* stream) {
   clear_stale_error();
-  uot_status st = check_opts(o);
+  uot_status st = check_opts(o, false, true);
   if (st != UOT_OK) return st;
   if (nprob < 1 || !probs || d < 1 || d > 3 || !x || !p || !dx || !y || !q || !dy || !Uout || !Vout)
     return UOT_EINVAL;
@@ -3623,6 +3624,7 @@ uot_status uot_solve_batch(int nprob, const uot_batch_problem* probs, int d, con
     const uot_batch_problem& pr = probs[k];
     if (pr.n < 1 || pr.m < 1 || pr.n > 3072 || pr.m > 3072) return UOT_EINVAL;
     if (!div_ok(&pr.F1) || !div_ok(&pr.F2)) return UOT_EINVAL;
+    if (o->translate && (pr.F1.kind != UOT_DIV_KL || pr.F2.kind != UOT_DIV_KL)) return UOT_EUNSUPPORTED;
     hn[k] = pr.n;
     hm[k] = pr.m;
     hxo[k] = N;
@@ -3691,6 +3693,7 @@ uot_status uot_solve_batch(int nprob, const uot_batch_problem* probs, int d, con
   sc.reserve<float2>(M);     // V state
   sc.reserve<float>(N);      // U-side shifts
   sc.reserve<float>(M);      // V-side shifts
+  if (o->translate) sc.reserve<double2>(nprob);  // (lambda1, lambda2)
   UOT_CK(sc.allocate());
   int* d_order = sc.take<int>(nprob);
   int* d_n = sc.take<int>(nprob);
@@ -3712,7 +3715,13 @@ uot_status uot_solve_batch(int nprob, const uot_batch_problem* probs, int d, con
   float2* d_Vff = sc.take<float2>(M);
   float* d_zU = sc.take<float>(N);
   float* d_zV = sc.take<float>(M);
+  double2* d_lam = o->translate ? sc.take<double2>(nprob) : nullptr;
   UOT_SCRATCH_OK(sc);
+  if (o->translate) {
+    std::vector<double2> hl(nprob);
+    for (int k = 0; k < nprob; ++k) hl[k] = make_double2(probs[k].F1.lambda, probs[k].F2.lambda);
+    UOT_CK(cudaMemcpyAsync(d_lam, hl.data(), nprob * sizeof(double2), cudaMemcpyHostToDevice, s));
+  }
   UOT_CK(cudaMemcpyAsync(d_order, order.data(), nprob * sizeof(int), cudaMemcpyHostToDevice, s));
   UOT_CK(cudaMemcpyAsync(d_n, hn.data(), nprob * sizeof(int), cudaMemcpyHostToDevice, s));
   UOT_CK(cudaMemcpyAsync(d_m, hm.data(), nprob * sizeof(int), cudaMemcpyHostToDevice, s));
@@ -3762,6 +3771,8 @@ uot_status uot_solve_batch(int nprob, const uot_batch_problem* probs, int d, con
   a.Vff = d_Vff;
   a.zU = d_zU;
   a.zV = d_zV;
+  a.translate = o->translate;
+  a.lam = d_lam;
   const int variant = batch_pick_variant(a, order.data(), s);
   const int per_sm = batch_ctas_per_sm(d, variant, nmax, mmax);
   if (per_sm < 1) {

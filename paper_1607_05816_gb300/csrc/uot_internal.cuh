@@ -662,6 +662,8 @@ struct BatchArgs {
   float2* Vff;  // [sum m]
   float* zU;    // [sum n] last log-sums (shifts)
   float* zV;    // [sum m]
+  int translate;        // 1: the translation step (KL / KL problems; uot_opts.translate)
+  const double2* lam;   // [nprob] (lambda1, lambda2) when translate
 };
 // CTA-size variant 0 (8 warps) or 1 (16 warps); the variant for a batch shape
 // (d, nmax, mmax) is timed on a sample of the batch on first use when the

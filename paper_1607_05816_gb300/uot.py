@@ -679,10 +679,13 @@ def geodesic(geom: Geometry, p0, p1, ts, dx, dy, F1: Div, Fh: Div, eps, **kw):
 
 
 def solve_batch(sizes, divs, d, x, p, dx, y, q, dy, eps, *, max_iter=1000, tol=0.0,
-                check_every=10, eps_start=None, eps_stages=10, iters_per_stage=100, U=None, V=None):
+                check_every=10, eps_start=None, eps_stages=10, iters_per_stage=100, U=None, V=None,
+                translate=False):
     """uot_solve_batch (FP32): sizes = [(n_k, m_k)], divs = [(F1_k, F2_k)]; x, p, dx
     packed over the X sides ([sum n, d], [sum n], [sum n]) and y, q, dy over the
-    Y sides.  Returns (U, V, iters [nprob], errs [nprob], result dict)."""
+    Y sides.  translate (KL / KL problems): the translation step of
+    uot_opts.translate, per problem.  Returns (U, V, iters [nprob], errs
+    [nprob], result dict)."""
     lib = load()
     nprob = len(sizes)
     arr = (CBatchProblem * nprob)()
@@ -696,7 +699,8 @@ def solve_batch(sizes, divs, d, x, p, dx, y, q, dy, eps, *, max_iter=1000, tol=0
     iters = (C.c_int * nprob)()
     errs = (C.c_double * nprob)()
     o = COpts(F32, float(eps), float(eps_start) if eps_start else 0.0, int(eps_stages),
-              int(iters_per_stage), int(max_iter), float(tol), int(check_every), 0, 0, None, None)
+              int(iters_per_stage), int(max_iter), float(tol), int(check_every), 0, 0, None, None,
+              0, 0, 0.0, int(bool(translate)))
     r = CResult()
     st = lib.uot_solve_batch(nprob, arr, int(d), _ptr(x, dt, "x"), _ptr(p, dt, "p"),
                              _ptr(dx, dt, "dx"), _ptr(y, dt, "y"), _ptr(q, dt, "q"),

@@ -335,26 +335,35 @@ def _ev_ms(fn):
 
 
 def evaluate_tc(net, inst, H, W, *, group, tol=1e-6, plain_sample=16, max_iter=20000, check_every=10,
-                device="cuda"):
+                cold_plain=True, device="cuda"):
     """Time to a `tol` marginal violation (confirmed in FP64, FP64 potentials
     returned) on held-out instances whose consecutive blocks of `group` share
-    (eps, lambda), three ways:
-      plain  : uot_solve per instance, cold start with eps-scaling (1e-1 -> eps,
-               10 stages x 40 iterations when eps < 1e-1), on the first
-               `plain_sample` instances, scaled to all of them;
-      batched: uot_solve_many per group, cold start, same eps-scaling;
-      warm   : network inference, then uot_solve_many per group from the
-               predicted potentials at the final eps (no eps-scaling);
-    inference time is included in `warm`.  Returns a dict of totals and the
-    per-group iteration counts (a batch stops when its last problem does)."""
+    (eps, lambda):
+      plain    : uot_solve per instance, the iteration as printed (no
+                 translation), cold start with eps-scaling (1e-1 -> eps, 10
+                 stages x 40 iterations when eps < 1e-1), on the first
+                 `plain_sample` instances, scaled to all of them;
+      batched  : uot_solve_many per group, cold start, same eps-scaling, no
+                 translation (skipped when cold_plain is False);
+      batched_tr: the same with the translation step (opts.translate);
+      warm     : network inference, then uot_solve_many per group from the
+                 predicted potentials at the final eps (no eps-scaling), with
+                 the translation step; warm_ms includes the inference, whose
+                 own time (timed once more on its own) is warm_infer_ms.
+    Returns a dict of totals and the per-group iteration counts (a batch
+    stops when its last problem does)."""
     xs = [torch.as_tensor((np.arange(n) + 0.5) / n, dtype=torch.float32, device=device) for n in (H, W)]
     geo = uot.Geometry.grid(xs, xs)
     dx = torch.full((H * W,), 1.0 / (H * W), dtype=torch.float32, device=device)
     P = torch.as_tensor(inst["P"], dtype=torch.float32, device=device)
     Q = torch.as_tensor(inst["Q"], dtype=torch.float32, device=device)
     n = P.shape[0]
-    res = {"n": n, "group": group, "plain_ms": 0.0, "batched_ms": 0.0, "warm_ms": 0.0, "warm_infer_ms": 0.0,
-           "plain_iters": [], "batched_iters": [], "warm_iters": [], "worst_err_warm": 0.0, "worst_err_batched": 0.0}
+    res = {"n": n, "group": group, "plain_ms": 0.0, "batched_ms": 0.0, "batched_tr_ms": 0.0, "warm_ms": 0.0,
+           "warm_infer_ms": 0.0, "plain_iters": [], "batched_iters": [], "batched_tr_iters": [], "warm_iters": [],
+           "worst_err_warm": 0.0, "worst_err_batched": 0.0, "worst_err_batched_tr": 0.0, "worst_err_plain": 0.0,
+           "groups": []}
+    common = dict(precision=uot.F32, max_iter=max_iter, tol=tol, check_every=check_every, launch_mode=2,
+                  out_f64=True, verify=True)
 
     def sched(e):
         return dict(eps_start=0.1, eps_stages=10, iters_per_stage=40) if e < 0.1 else dict(eps_start=None)
@@ -362,28 +371,36 @@ def evaluate_tc(net, inst, H, W, *, group, tol=1e-6, plain_sample=16, max_iter=2
         e, lam = float(inst["eps"][k]), float(inst["lam"][k])
         ms, (_, _, info) = _ev_ms(lambda: uot.solve(
             geo, P[k].reshape(-1).contiguous(), dx, Q[k].reshape(-1).contiguous(), dx, uot.KL(lam), uot.KL(lam), e,
-            precision=uot.F32, max_iter=max_iter, tol=tol, check_every=check_every, launch_mode=2, out_f64=True,
-            verify=True, **sched(e)))
+            **common, **sched(e)))
         res["plain_ms"] += ms
         res["plain_iters"].append(info["total_iters"])
+        res["worst_err_plain"] = max(res["worst_err_plain"], info["marg_err"])
     res["plain_ms"] *= n / max(1, min(plain_sample, n))
     for s in range(0, n, group):
         sl = slice(s, min(n, s + group))
         e, lam = float(inst["eps"][s]), float(inst["lam"][s])
         Pg = P[sl].reshape(-1, H * W).contiguous()
         Qg = Q[sl].reshape(-1, H * W).contiguous()
-        ms, (_, _, info) = _ev_ms(lambda: uot.solve_many(
-            geo, Pg, dx, Qg, dx, uot.KL(lam), uot.KL(lam), e, precision=uot.F32, max_iter=max_iter, tol=tol,
-            check_every=check_every, launch_mode=2, out_f64=True, verify=True, **sched(e)))
-        res["batched_ms"] += ms
-        res["batched_iters"].append(info["total_iters"])
-        res["worst_err_batched"] = max(res["worst_err_batched"], info["marg_err"])
+        grp = {"eps": e, "lam": lam}
+        if cold_plain:
+            ms, (_, _, info) = _ev_ms(lambda: uot.solve_many(geo, Pg, dx, Qg, dx, uot.KL(lam), uot.KL(lam), e,
+                                                             **common, **sched(e)))
+            res["batched_ms"] += ms
+            res["batched_iters"].append(info["total_iters"])
+            res["worst_err_batched"] = max(res["worst_err_batched"], info["marg_err"])
+            grp.update(cold_iters=info["total_iters"], cold_ms=round(ms, 2))
+        ms, (_, _, info) = _ev_ms(lambda: uot.solve_many(geo, Pg, dx, Qg, dx, uot.KL(lam), uot.KL(lam), e,
+                                                         translate=True, **common, **sched(e)))
+        res["batched_tr_ms"] += ms
+        res["batched_tr_iters"].append(info["total_iters"])
+        res["worst_err_batched_tr"] = max(res["worst_err_batched_tr"], info["marg_err"])
+        grp.update(cold_tr_iters=info["total_iters"], cold_tr_ms=round(ms, 2))
 
         def warm():
             U0, V0 = net.predict(P[sl].contiguous(), Q[sl].contiguous(), inst["eps"][sl], inst["lam"][sl])
-            return uot.solve_many(geo, Pg, dx, Qg, dx, uot.KL(lam), uot.KL(lam), e, precision=uot.F32,
-                                  max_iter=max_iter, tol=tol, check_every=check_every, launch_mode=2, U0=U0, V0=V0,
-                                  out_f64=True, verify=True)
+            return uot.solve_many(geo, Pg, dx, Qg, dx, uot.KL(lam), uot.KL(lam), e, U0=U0, V0=V0, translate=True,
+                                  **common)
+        # inference alone, timed separately to report its share (warm() repeats it)
         ms_inf, _ = _ev_ms(lambda: net.predict(P[sl].contiguous(), Q[sl].contiguous(), inst["eps"][sl],
                                                inst["lam"][sl]))
         ms, (Uw, Vw, info) = _ev_ms(warm)
@@ -391,5 +408,7 @@ def evaluate_tc(net, inst, H, W, *, group, tol=1e-6, plain_sample=16, max_iter=2
         res["warm_infer_ms"] += ms_inf
         res["warm_iters"].append(info["total_iters"])
         res["worst_err_warm"] = max(res["worst_err_warm"], info["marg_err"])
+        grp.update(warm_iters=info["total_iters"], warm_ms=round(ms, 2))
+        res["groups"].append(grp)
         res.setdefault("_last_warm", (s, Uw, Vw))
     return res

@@ -102,3 +102,73 @@ def test_batch_converges_to_tolerance(warps):
         assert v <= 20 * tol, (k, v)
         xo += n
         yo += m
+
+
+@pytest.mark.parametrize("d,stages", [(2, 0), (3, 3)])
+def test_batch_translated_parity(d, stages, warps):
+    """opts.translate in the persistent solver: each problem's iterates equal
+    the oracle's translated iteration (the step after every 5th iteration of
+    each stage and of the final eps, and after the last one)."""
+    probs = synth.batch_points(nprob=12, size=(5, 900), d=d, seed=60 + d)
+    sizes = [(len(pr["x"]), len(pr["y"])) for pr in probs]
+    udivs, odivs = make_divs(probs, ["kl"])
+    x, p, dx, y, q, dy = packed(probs)
+    eps, iters = 0.02, 23
+    es = 0.2 if stages else None
+    Ug, Vg, it, errs, info = U.solve_batch(sizes, udivs, d, x, p, dx, y, q, dy, eps, max_iter=iters,
+                                           check_every=5, eps_start=es, eps_stages=stages, iters_per_stage=7,
+                                           translate=True)
+    Ug = Ug.double().cpu().numpy()
+    Vg = Vg.double().cpu().numpy()
+    xo = yo = 0
+    moved = []
+    for k, pr in enumerate(probs):
+        n, m = sizes[k]
+        og = O.Geometry("points", x=rounded(pr["x"]), y=rounded(pr["y"]))
+        args = (og, rounded(pr["dx"]), rounded(pr["dy"]), rounded(pr["p"]), rounded(pr["q"]), *odivs[k], eps)
+        kw = dict(max_iter=iters, eps_start=es, stages=stages, iters_per_stage=7, check_every=5)
+        r = O.solve_log(*args, translate=True, **kw)
+        assert rel_err(Ug[xo:xo + n], r["U"]) <= 1e-5, k
+        assert rel_err(Vg[yo:yo + m], r["V"]) <= 1e-5, k
+        moved.append(rel_err(Ug[xo:xo + n], O.solve_log(*args, **kw)["U"]))
+        xo += n
+        yo += m
+    assert max(moved) > 1e-3  # the step changed the iterates (no silent no-op)
+
+
+def test_batch_translated_needs_fewer_iterations():
+    """KL lambda up to 5 at eps = 0.02: every problem reaches 1e-6 with the
+    step, in at most half the iterations in total, and the oracle, evaluating
+    the returned potentials, agrees with the stop."""
+    probs = synth.batch_points(nprob=40, size=(64, 700), d=2, seed=78)
+    sizes = [(len(pr["x"]), len(pr["y"])) for pr in probs]
+    udivs, odivs = make_divs(probs, ["kl"])
+    x, p, dx, y, q, dy = packed(probs)
+    eps, tol = 0.02, 1e-6
+    out = {}
+    for tr in (False, True):
+        out[tr] = U.solve_batch(sizes, udivs, 2, x, p, dx, y, q, dy, eps, max_iter=40000, tol=tol, check_every=10,
+                                translate=tr)
+        assert out[tr][4]["status"] == "UOT_OK"
+    print("iterations plain", sum(out[False][2]), "translated", sum(out[True][2]))
+    assert 2 * sum(out[True][2]) <= sum(out[False][2])
+    Ug = out[True][0].double().cpu().numpy()
+    Vg = out[True][1].double().cpu().numpy()
+    xo = yo = 0
+    for k, pr in enumerate(probs[:6]):
+        n, m = sizes[k]
+        og = O.Geometry("points", x=rounded(pr["x"]), y=rounded(pr["y"]))
+        v = O.marginal_violation(og, rounded(pr["dx"]), rounded(pr["dy"]), rounded(pr["p"]),
+                                 rounded(pr["q"]), *odivs[k], eps, Ug[xo:xo + n], Vg[yo:yo + m])
+        assert v <= 20 * tol, (k, v)
+        xo += n
+        yo += m
+
+
+def test_batch_translate_needs_kl():
+    probs = synth.batch_points(nprob=3, size=(5, 50), d=2, seed=79)
+    sizes = [(len(pr["x"]), len(pr["y"])) for pr in probs]
+    udivs, _ = make_divs(probs, ["kl", "tv"])
+    with pytest.raises(U.UotError) as ex:
+        U.solve_batch(sizes, udivs, 2, *packed(probs), 0.02, max_iter=5, translate=True)
+    assert ex.value.status == -6
