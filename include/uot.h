@@ -262,7 +262,8 @@ uot_status uot_force_batch_warps(int warps);
  * clock per SM measured with in-kernel clock64() over dependent-chain loops
  * with 64 resident warps per SM:
  *   out[0]: FP32 FMA lane operations, out[1]: MUFU ex2.approx.f32, out[2]: FP64
- *   FMA lane operations.
+ *   FMA lane operations, out[3]: FP64 exponentials exp() (the function the FP64
+ *   Gibbs passes evaluate per kernel term).  out holds 4 doubles.
  * A few milliseconds of work; synchronises `stream`.
  */
 uot_status uot_probe_pipes(double* out, void* stream);

@@ -1,5 +1,6 @@
 // Throughput probes of the pipes the scaling kernels are bound by (FP32 FMA,
-// MUFU ex2, FP64 FMA), reported in operations per clock per SM so that the
+// MUFU ex2, FP64 FMA, and the FP64 exponential exp() of the FP64 Gibbs passes
+// as the library compiles it), reported in operations per clock per SM so that the
 // result does not depend on the clock the GPU runs at.  Each thread runs
 // kChains independent dependency chains (enough to cover the pipe latency);
 // every block records its elapsed SM cycles with clock64(), and the host
@@ -37,8 +38,10 @@ __global__ void __launch_bounds__(kProbeThreads) k_probe(int iters, float seed, 
           float y;
           asm volatile("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(fv[c]));
           fv[c] = y * -0.5f;  // keeps the argument in [-1, 0]: no denormals or overflow
-        } else {
+        } else if (KIND == 2) {
           dv[c] = fma(dv[c], da, db);
+        } else {
+          dv[c] = -0.5 * exp(dv[c]);  // keeps the argument in [-0.5, 0]
         }
       }
     }
@@ -73,12 +76,13 @@ extern "C" uot_status uot_probe_pipes(double* out, void* stream) {
   }
   std::vector<long long> h(blocks);
   uot_status st = UOT_OK;
-  const int iters[3] = {4096, 1024, 64};  // ~10^8 operations or more per SM, a few ms each
-  for (int kind = 0; kind < 3 && st == UOT_OK; ++kind) {
+  const int iters[4] = {4096, 1024, 64, 8};  // a few ms each
+  for (int kind = 0; kind < 4 && st == UOT_OK; ++kind) {
     count_launches(1);
     if (kind == 0) k_probe<0><<<blocks, kProbeThreads, 0, s>>>(iters[kind], 0.5f, dcyc, dsink);
     if (kind == 1) k_probe<1><<<blocks, kProbeThreads, 0, s>>>(iters[kind], -0.5f, dcyc, dsink);
     if (kind == 2) k_probe<2><<<blocks, kProbeThreads, 0, s>>>(iters[kind], 0.5f, dcyc, dsink);
+    if (kind == 3) k_probe<3><<<blocks, kProbeThreads, 0, s>>>(iters[kind], -0.25f, dcyc, dsink);
     if (cudaGetLastError() != cudaSuccess ||
         cudaMemcpyAsync(h.data(), dcyc, sizeof(long long) * blocks, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {

@@ -224,12 +224,13 @@ def selftest_bounded_wait(seconds: float) -> str:
 
 
 def probe_pipes() -> dict:
-    """uot_probe_pipes: sustained FP32 FMA, MUFU ex2 and FP64 FMA rates in
-    operations per clock per SM."""
+    """uot_probe_pipes: sustained FP32 FMA, MUFU ex2, FP64 FMA and FP64 exp()
+    rates in operations per clock per SM."""
     lib = load()
-    out = (C.c_double * 3)()
+    out = (C.c_double * 4)()
     _check(lib.uot_probe_pipes(out, _stream()), "uot_probe_pipes")
-    return {"ffma_per_clk_per_sm": out[0], "mufu_ex2_per_clk_per_sm": out[1], "dfma_per_clk_per_sm": out[2]}
+    return {"ffma_per_clk_per_sm": out[0], "mufu_ex2_per_clk_per_sm": out[1], "dfma_per_clk_per_sm": out[2],
+            "dexp_per_clk_per_sm": out[3]}
 
 
 def grid_tile_count() -> int:

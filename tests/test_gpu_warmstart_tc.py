@@ -7,6 +7,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle as O
 import oracle.net_oracle as NO
 from paper_1607_05816_gb300 import synth
 from paper_1607_05816_gb300 import uot as U
@@ -117,3 +118,45 @@ def test_mse_gradient_pads_with_zeros():
     want = 2.0 * (pr - tgt) / pr.size
     assert np.max(np.abs(got[:, :2] - want)) <= 2.0 ** -8 * np.max(np.abs(want))
     assert abs(loss.item() - np.mean((pr - tgt) ** 2)) <= 1e-5 * np.mean((pr - tgt) ** 2)
+
+
+def test_trained_tc_network_reduces_iterations_to_tol():
+    """What the trained network gains: 2048 solver-generated 64 x 64 instances
+    (eps in [1e-2, 1e-1], lambda in [0.1, 10]), three epochs; on 16 held-out
+    instances the solve to 1e-6 (FP32 passes, stop confirmed in FP64, the
+    translation step in both forms) from the predicted potentials needs fewer
+    iterations than the cold start with eps-scaling, for the median and in
+    total, and the oracle confirms the warm result of one instance."""
+    H = W = 64
+    kw = dict(eps=(1e-2, 1e-1), lam=(0.1, 10.0))
+    inst = synth.warmstart_instances(2048, H, W, seed=31, group=64, **kw)
+    P, Q, Us, Vs = WS.generate_targets(inst, H, W, max_iter=6000, group=64)
+    net = WS.WarmStartNetTC(channels=128, seed=3)
+    hist = WS.train_tc(net, P, Q, Us, Vs, inst["eps"], inst["lam"], epochs=3, batch=32)
+    assert np.isfinite(hist).all() and hist[-1] < 0.5 * hist[0], hist
+    ev = synth.warmstart_instances(16, H, W, seed=32, group=1, **kw)
+    Pe = torch.as_tensor(ev["P"], dtype=torch.float32, device="cuda")
+    Qe = torch.as_tensor(ev["Q"], dtype=torch.float32, device="cuda")
+    U0, V0 = net.predict(Pe, Qe, ev["eps"], ev["lam"])
+    xs = [torch.as_tensor(a, dtype=torch.float32, device="cuda") for a in ev["xs"]]
+    geo = U.Geometry.grid(xs, xs)
+    dx = torch.full((H * W,), 1.0 / (H * W), device="cuda")
+    common = dict(precision=U.F32, max_iter=20000, tol=1e-6, check_every=10, launch_mode=2, out_f64=True,
+                  verify=True, translate=True)
+    cold, warm = [], []
+    for k in range(16):
+        e, lam = float(ev["eps"][k]), float(ev["lam"][k])
+        args = (geo, Pe[k].reshape(-1), dx, Qe[k].reshape(-1), dx, U.KL(lam), U.KL(lam), e)
+        _, _, ic = U.solve(*args, eps_start=0.1 if e < 0.1 else None, eps_stages=10, iters_per_stage=40, **common)
+        Uw, Vw, iw = U.solve(*args, U0=U0[k].contiguous(), V0=V0[k].contiguous(), **common)
+        assert ic["status"] == "UOT_OK" and iw["status"] == "UOT_OK"
+        cold.append(ic["total_iters"])
+        warm.append(iw["total_iters"])
+    print("cold", cold, "\nwarm", warm)
+    assert np.median(warm) < np.median(cold) and sum(warm) < sum(cold)
+    rr = lambda a: np.asarray(a, np.float32).astype(np.float64)
+    ax = [rr(a) for a in ev["xs"]]
+    v = O.marginal_violation(O.Geometry("grid", xs=ax, ys=ax), rr(ev["dx"]), rr(ev["dx"]), rr(ev["P"][15]),
+                             rr(ev["Q"][15]), O.KL(lam), O.KL(lam), e, Uw.double().cpu().numpy().reshape(H, W),
+                             Vw.double().cpu().numpy().reshape(H, W))
+    assert v <= 1e-6, v
