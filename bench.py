@@ -56,6 +56,9 @@ HBM_PEAK_GBS = 6760.6
 # dram bytes of one rows_lse_f64_pf<4, 4, 1> launch of the wf workload (ncu,
 # profiles/rows_lse_f64_pf_wf3000.md); None once the kernel changes
 WF_ROWS_TRAFFIC_BYTES = 36848640
+# dram bytes of one alg1_cluster launch (2000 iterations of the dense 256 x 256
+# problem; profiles/alg1_cluster_dense256.md); None once the kernel changes
+ALG1_CLUSTER_TRAFFIC_BYTES = 1185792
 # FP32 pipe: 128 lanes per clock per SM (FADD/FMUL/FFMA; a packed f32x2
 # instruction occupies it for two lane-slots per pair).
 FP32_PER_CLK = 128
@@ -360,7 +363,8 @@ def run_ours(args, rank, world, local_rank):
                   "marg_err_fp64": max(errs), "marg_err_fp32": max(i["marg_err_fp32"] for i in infos),
                   "fp64_confirmations_per_step": sum(i["verifications"] for i in infos) / len(infos),
                   "fp64_iters_per_step": sum(i["polish_iters"] for i in infos) / len(infos),
-                  "outputs": "float64"} if verify else {"rule": "FP32 check"}),
+                  "outputs": "float64"} if verify else
+                 {"rule": "FP64 check" if prec == uot.F64 else "FP32 check"}),
         "mixed": ({"bf16_tensor_core_iters_per_step": sum(i["mixed_iters"] for i in infos) / len(infos),
                    "fp32_iters_per_step": sum(i["total_iters"] - i["mixed_iters"] - i["polish_iters"]
                                               for i in infos) / len(infos),
@@ -589,9 +593,13 @@ def run_single(args, rank, world, local_rank):
                             "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy), of measured",
                             "timing": timing}
     else:
+        tr = ALG1_CLUSTER_TRAFFIC_BYTES if kernel == "alg1_cluster" else None
         line["roofline"] = {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": FP64_PEAK_GFLOPS,
-                            "unit": unit_work, "frac": achieved / FP64_PEAK_GFLOPS, "traffic": None,
+                            "unit": unit_work, "frac": achieved / FP64_PEAK_GFLOPS, "traffic": tr,
                             "timing": timing}
+        if tr is not None:
+            line["roofline"]["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
+                                                  "2000-iteration launch (profiles/alg1_cluster_dense256.md)")
     return line
 
 
@@ -686,6 +694,10 @@ def run_batch(args, rank, world, local_rank):
 # ----------------------------------------------------------------------------
 
 WS_TRAIN, WS_EPOCHS, WS_EVAL, WS_GROUP = 8192, 8, 1024, 32
+# dram bytes of one conv_tc<128> launch of a 128 -> 128 layer, scaled from the
+# 32-instance capture to the 64 instances of the timed forward pass; None once
+# the kernel changes
+CONV_TC_TRAFFIC_BYTES_128x128_64INST = 2 * (33930240 + 49664)
 # measured dense BF16 GEMM rate of this GPU type (MEASURED_PEAKS.json bf16_tflops, burst)
 BF16_PEAK_TFLOPS = 1916.2
 
@@ -756,7 +768,11 @@ def run_warmstart(args, rank, world, local_rank):
         "gpu_launches": launches, "clocks": clocks,
         "roofline": {"bound": "tensor", "kernel": "conv_tc<128> (network forward, 64 instances)",
                      "achieved": flops_alg / (fwd_ms / 1e3) / 1e12, "peak": BF16_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": flops_alg / (fwd_ms / 1e3) / 1e12 / BF16_PEAK_TFLOPS, "traffic": None,
+                     "frac": flops_alg / (fwd_ms / 1e3) / 1e12 / BF16_PEAK_TFLOPS,
+                     "traffic": CONV_TC_TRAFFIC_BYTES_128x128_64INST,
+                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one conv_tc<128> "
+                                       "launch of a 128 -> 128 layer on 32 instances (33.93 MB + 0.05 MB, "
+                                       "profiles/conv_tc_warmstart64.md), x2 for the 64 instances timed here",
                      "mma_flops_incl_padding_tflops": flops_mma / (fwd_ms / 1e3) / 1e12,
                      "forward_ms_64_instances": fwd_ms,
                      "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst), of measured",

@@ -108,11 +108,38 @@ __global__ void __launch_bounds__(kTrThreads) k_tr_partial(TrArgs a) {
   const double* pot = a.pot[side];
   const double inv_lam = a.inv_lam[side];
   double mx = -kInf, s = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * kTrThreads + threadIdx.x; i < len; i += (int64_t)nb * kTrThreads) {
-    const double lm = load_val<FF>(a.logm[side], (int64_t)b * len + i);
-    const double u = load_val<FF>(pot, (int64_t)b * len + i);
-    if (lm == -kInf || u == -kInf) continue;
-    lse_push<FF>(mx, s, load_val<FF>(a.logw[side], i) + lm - u * inv_lam);
+  if constexpr (FF) {
+    // float-float terms and running maximum, FP32 sum: no FP64 pipe in the loop
+    // (it runs at a small fraction of the FP32 rate); exponentials of the
+    // exactly formed differences t - max, rounded to FP32
+    const float2* lmf = reinterpret_cast<const float2*>(a.logm[side]) + (int64_t)b * len;
+    const float2* uf = reinterpret_cast<const float2*>(pot) + (int64_t)b * len;
+    const float2* lwf = reinterpret_cast<const float2*>(a.logw[side]);
+    const ff nil = ff_make(-inv_lam);
+    ff fmx = ff_ninf();
+    float fs = 0.0f;
+    for (int64_t i = (int64_t)blockIdx.x * kTrThreads + threadIdx.x; i < len; i += (int64_t)nb * kTrThreads) {
+      const float2 lm = lmf[i], u = uf[i];
+      if (lm.x == -INFINITY || u.x == -INFINITY) continue;
+      const ff t = ff_add(ff_add(ffl(lwf[i]), ffl(lm)), ff_mul(ffl(u), nil));
+      if (ff_lt(fmx, t)) {
+        fs = (fmx.hi == -INFINITY) ? 1.0f : fs * expf(ff_sub(fmx, t).hi) + 1.0f;
+        fmx = t;
+      } else {
+        fs += expf(ff_sub(t, fmx).hi);
+      }
+    }
+    if (fmx.hi != -INFINITY) {
+      mx = (double)fmx.hi + (double)fmx.lo;
+      s = (double)fs;
+    }
+  } else {
+    for (int64_t i = (int64_t)blockIdx.x * kTrThreads + threadIdx.x; i < len; i += (int64_t)nb * kTrThreads) {
+      const double lm = load_val<FF>(a.logm[side], (int64_t)b * len + i);
+      const double u = load_val<FF>(pot, (int64_t)b * len + i);
+      if (lm == -kInf || u == -kInf) continue;
+      lse_push<FF>(mx, s, load_val<FF>(a.logw[side], i) + lm - u * inv_lam);
+    }
   }
   lse_warp<FF>(mx, s);
   __shared__ double sm[kTrThreads / 32], ss[kTrThreads / 32];
