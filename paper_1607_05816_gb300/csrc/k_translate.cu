@@ -18,6 +18,8 @@
 // every problem, then a shift kernel in which every block recombines its
 // problem's partials (the same values in the same order, so every block
 // applies the same c) and shifts its share of U and V.
+#include <string.h>
+
 #include <algorithm>
 
 #include "uot_internal.cuh"
@@ -26,9 +28,9 @@ namespace uot {
 namespace {
 
 constexpr int kTrThreads = 256;
-constexpr int kTrPartialPer = 8;  // elements per thread per block, partial kernel (before the cap)
-constexpr int kTrShiftPer = 4;    // the same for the shift kernel
-constexpr int kTrMaxBlocks = 64;  // blocks per problem and side
+constexpr int kTrPartialPer = 2;   // elements per thread per block, partial kernel (before the cap)
+constexpr int kTrShiftPer = 2;     // the same for the shift kernel
+constexpr int kTrMaxBlocks = 256;  // blocks per problem and side: enough loads in flight to hide latency
 
 int blocks_for(int64_t len, int per) {
   const int64_t b = (len + (int64_t)kTrThreads * per - 1) / ((int64_t)kTrThreads * per);
@@ -100,6 +102,10 @@ struct TrArgs {
 // grid (stride, batch, 2): block x of problem y, side z
 template <bool FF>
 __global__ void __launch_bounds__(kTrThreads) k_tr_partial(TrArgs a) {
+  // programmatic dependent launch: wait for the V-update's last pass, then let
+  // the shift kernel launch (it waits for this grid in turn)
+  pdl_wait();
+  pdl_launch_dependents();
   const int side = blockIdx.z;
   const int b = blockIdx.y;
   const int nb = a.nblk[side];
@@ -160,6 +166,9 @@ __global__ void __launch_bounds__(kTrThreads) k_tr_partial(TrArgs a) {
 // grid (blocks, batch): c of problem y from its partials, then U += c, V -= c
 template <bool FF>
 __global__ void __launch_bounds__(kTrThreads) k_tr_shift(TrArgs a) {
+  // waits for the partials; never releases its dependents early: the next pass
+  // reads the old potentials before its own wait, and this grid rewrites them
+  pdl_wait();
   const int b = blockIdx.y;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   __shared__ double slog[2];
@@ -226,14 +235,23 @@ cudaError_t launch_kl_translate(double* U, double* V, const double* logp, const 
   a.part = part;
   const dim3 gp(a.stride, batch, 2);
   const dim3 gs(blocks_for(n + m, kTrShiftPer), batch);
+  cudaLaunchConfig_t cfg;
+  memset(&cfg, 0, sizeof(cfg));
+  cfg.blockDim = dim3(kTrThreads);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
   count_launches(2);
-  if (ff) {
-    k_tr_partial<true><<<gp, kTrThreads, 0, s>>>(a);
-    k_tr_shift<true><<<gs, kTrThreads, 0, s>>>(a);
-  } else {
-    k_tr_partial<false><<<gp, kTrThreads, 0, s>>>(a);
-    k_tr_shift<false><<<gs, kTrThreads, 0, s>>>(a);
-  }
+  cudaError_t e;
+  cfg.gridDim = gp;
+  e = ff ? cudaLaunchKernelEx(&cfg, k_tr_partial<true>, a) : cudaLaunchKernelEx(&cfg, k_tr_partial<false>, a);
+  if (e != cudaSuccess) return e;
+  cfg.gridDim = gs;
+  e = ff ? cudaLaunchKernelEx(&cfg, k_tr_shift<true>, a) : cudaLaunchKernelEx(&cfg, k_tr_shift<false>, a);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

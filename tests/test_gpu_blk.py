@@ -157,3 +157,21 @@ def test_non_uniform_axes_fall_back():
     finally:
         U.force_grid_tile(-1)
     assert n == 0
+
+
+def test_tuner_never_picks_the_block_pass():
+    """On a uniform grid where every block variant is admitted and timed, the
+    automatic choice is a log-sum-exp tile and no block kernel runs."""
+    og, lg, dx, dy, p, q = uniform_problem((96, 80), (96, 80), (1 / 128, 1 / 128), (0, 0), 5)
+    prev = U.set_autotune(1)
+    try:
+        W = rounded(U.F32, np.zeros((96, 80)))
+        _, n = blk_launches(lambda: U.gibbs_log(lg(), T(W, U.F32).ravel(), T(dy, U.F32).ravel(), 0.05, False,
+                                                U.F32))
+        table = U.autotune_table()
+    finally:
+        U.set_autotune(prev)
+    lines = [ln for ln in table.splitlines() if "nin=80 nout=80" in ln]
+    assert lines and all("blk32x4:-1.00us" not in ln for ln in lines), table  # admitted and timed
+    assert all("-> block-stabilised" not in ln for ln in lines), table
+    assert n == 0

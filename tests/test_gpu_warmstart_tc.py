@@ -88,7 +88,7 @@ def test_tc_training_reduces_loss():
     P, Q, Us, Vs = WS.generate_targets(inst, H, W, max_iter=3000, group=32)
     net = WS.WarmStartNetTC(channels=128, seed=3)
     assert 1.5e6 < net.n_params() < 2.5e6
-    hist = WS.train_tc(net, P, Q, Us, Vs, inst["eps"], inst["lam"], epochs=6, batch=16, lr=1e-3)
+    hist = WS.train_tc(net, P, Q, Us, Vs, inst["eps"], inst["lam"], epochs=10, batch=16, lr=3e-4, warmup=10)
     torch.cuda.synchronize()
     assert net.err.item() == 0
     print("tc training loss per epoch:", hist)
