@@ -27,12 +27,16 @@
 //                   stays 0); the y shift is a TMA coordinate.  Split over image
 //                   rows into partial sums, reduced by a second kernel.
 //
-// Roles in a CTA of 128 threads: thread 0 issues the TMA loads into a
-// 4-stage ring, thread 32 issues the MMAs (one per 16 K-elements) and commits
-// each stage back to the producer; all four warps then read the accumulator
-// (warp w: tensor-memory lanes 32w..32w+31) for the epilogue.  Every wait on
-// an mbarrier is bounded by the global timer; on expiry the CTA sets an
-// error flag and skips its stores.
+// The forward / data-gradient kernel is persistent (one CTA per SM walks its
+// share of the 128-pixel tiles) with warp roles: one thread streams the TMA
+// loads into a 6-stage ring, one issues the MMAs (one per 16 K-elements) and
+// commits each stage back to the producer, four epilogue warps read the
+// accumulator (warp w: tensor-memory lanes 32 (w % 4) ..) while the MMAs of
+// the next tile run into the second of two accumulators.  The weight-gradient
+// kernel takes one (tap, row range) per CTA with the same producer / MMA
+// split.  Every wait on an mbarrier is bounded by the global timer; on expiry
+// the CTA sets an error flag, skips its stores, lets the copies and MMAs in
+// flight finish (bounded) and frees its tensor memory.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <string.h>
@@ -163,38 +167,65 @@ struct ConvTcArgs {
   int* err;           // set when a bounded wait expired
 };
 
-// Forward / backward-data convolution: one CTA per 128-pixel tile.
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+// Bounded wait that ignores the abort flag: used only to let copies and MMAs
+// that are already in flight finish before the CTA frees its resources.
+__device__ void mbar_drain(uint64_t* b, uint32_t parity) {
+  const unsigned long long t0 = gtimer();
+  for (uint32_t it = 0;; ++it) {
+    if (mbar_try(b, parity)) return;
+    if ((it & 63) == 63 && gtimer() - t0 > kWaitLimitNs / 10) return;
+  }
+}
+
+constexpr int kConvStages = 6;  // 6 x (16 KB + BN x 128 B): 192 KB at BN = 128
+
+// Forward / backward-data convolution, persistent: CTA c takes the 128-pixel
+// tiles c, c + G, c + 2G, ... (G = grid size, one CTA per SM).  Six warps:
+// warp 0 (one thread) streams the TMA loads of all its tiles through a
+// 6-stage ring; warp 1 owns tensor memory and (one thread) issues the MMAs;
+// warps 2-5 run the epilogue, warp w reading tensor-memory lanes 32 (w % 4)
+// .. 32 (w % 4) + 31.  Two accumulators in tensor memory let the epilogue of
+// tile i overlap the MMAs of tile i + 1: acc_full[b] (committed by the MMAs)
+// hands accumulator b to the epilogue, acc_empty[b] (one arrival per epilogue
+// warp) hands it back.
 template <int BN>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(192, 1)
     conv_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, ConvTcArgs a) {
   constexpr int kTileBytesB = BN * 128;
-  constexpr int kCols = BN < 32 ? 32 : BN;
+  constexpr int kCols = BN < 32 ? 32 : BN;  // columns of one accumulator
+  constexpr int kAllocCols = 2 * kCols;     // a power of two >= 32
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = align1024(smem_raw);
   uint8_t* sA = smem;
-  uint8_t* sB = smem + kStages * kTileBytesA;
-  __shared__ __align__(8) uint64_t full[kStages], empty[kStages], done;
+  uint8_t* sB = smem + kConvStages * kTileBytesA;
+  __shared__ __align__(8) uint64_t full[kConvStages], empty[kConvStages], acc_full[2], acc_empty[2], drain;
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int rows_per_tile = 128 / a.W;
   const int tiles_per_img = a.H / rows_per_tile;
-  const int n = blockIdx.x / tiles_per_img;
-  const int y0 = (blockIdx.x % tiles_per_img) * rows_per_tile;
+  const int ntiles = a.N * tiles_per_img;
   const int chunks = a.cin_pad / 64;
   const int nk = 9 * chunks;
   if (tid == 0) {
-    for (int s = 0; s < kStages; ++s) {
+    for (int s = 0; s < kConvStages; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(&done, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], 4);
+    }
+    mbar_init(&drain, 1);
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
-  if (warp == 0) {
+  if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
-                 "r"(kCols));
+                 "r"(kAllocCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -203,80 +234,123 @@ __global__ void __launch_bounds__(128, 1)
   const uint32_t tmem = tmem_slot;
   volatile int* abort = &abort_flag;
 
-  if (tid == 0) {
-    // producer: the A (activations) and B (weights) tiles of each K step
-    for (int k = 0; k < nk; ++k) {
-      const int s = k % kStages;
-      if (k >= kStages && !mbar_wait(&empty[s], ((k / kStages) - 1) & 1, abort)) break;
-      const int tap = k / chunks, c = k % chunks;
-      const int dy = tap / 3 - 1, dx = tap % 3 - 1;
-      mbar_expect_tx(&full[s], kTileBytesA + kTileBytesB);
-      tma_load_4d(sA + s * kTileBytesA, &tmA, &full[s], c * 64, dx * a.dil, y0 + dy * a.dil, n);
-      tma_load_2d(sB + s * kTileBytesB, &tmB, &full[s], tap * a.cin_pad + c * 64, 0);
+  if (warp == 0) {
+    if (lane == 0) {
+      // producer: the A (activations) and B (weights) tiles of every K step of every tile
+      int k = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        const int n = t / tiles_per_img, y0 = (t % tiles_per_img) * rows_per_tile;
+        for (int kt = 0; kt < nk; ++kt) {
+          const int s = k % kConvStages;
+          if (k >= kConvStages && !mbar_wait(&empty[s], ((k / kConvStages) - 1) & 1, abort)) {
+            ok = false;
+            break;
+          }
+          const int tap = kt / chunks, c = kt % chunks;
+          const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+          mbar_expect_tx(&full[s], kTileBytesA + kTileBytesB);
+          tma_load_4d(sA + s * kTileBytesA, &tmA, &full[s], c * 64, dx * a.dil, y0 + dy * a.dil, n);
+          tma_load_2d(sB + s * kTileBytesB, &tmB, &full[s], tap * a.cin_pad + c * 64, 0);
+          ++k;
+        }
+      }
+      if (!ok) {
+        // let the copies in flight land before the CTA's shared memory goes away
+        for (int j = (k > kConvStages ? k - kConvStages : 0); j < k; ++j)
+          mbar_drain(&full[j % kConvStages], (j / kConvStages) & 1);
+      }
     }
-  } else if (tid == 32) {
-    // MMA issuer: 4 MMAs of K = 16 per stage, each stage returned to the producer
-    constexpr uint32_t idesc = idesc_bf16(128, BN);
-    bool ok = true;
-    for (int k = 0; k < nk && ok; ++k) {
-      const int s = k % kStages;
-      ok = mbar_wait(&full[s], (k / kStages) & 1, abort);
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // MMA issuer: 4 MMAs of K = 16 per stage, each stage returned to the producer
+      constexpr uint32_t idesc = idesc_bf16(128, BN);
+      int k = 0, i = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++i) {
+        const int ab = i & 1;
+        // accumulator ab is free once the epilogue has read tile i - 2 out of it
+        if (i >= 2 && !mbar_wait(&acc_empty[ab], ((i >> 1) - 1) & 1, abort)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t acc = tmem + (uint32_t)(ab * kCols);
+        for (int kt = 0; kt < nk; ++kt, ++k) {
+          const int s = k % kConvStages;
+          if (!mbar_wait(&full[s], (k / kConvStages) & 1, abort)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const uint32_t a0 = smem_u32(sA + s * kTileBytesA), b0 = smem_u32(sB + s * kTileBytesB);
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk)
+            mma_bf16(acc, desc_sw128(a0 + kk * 32), desc_sw128(b0 + kk * 32), idesc, (kt | kk) != 0);
+          mma_commit(&empty[s]);
+        }
+        if (ok) mma_commit(&acc_full[ab]);
+      }
+      // every MMA issued has completed before tensor memory is freed
+      mma_commit(&drain);
+      mbar_drain(&drain, 0);
+    }
+  } else {
+    // epilogue: thread (warp w, lane l) = pixel row 32 (w % 4) + l of each tile
+    const int q = warp & 3;
+    int i = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+      const int ab = i & 1;
+      bool ok = mbar_wait(&acc_full[ab], (i >> 1) & 1, abort);
+      ok = __all_sync(0xffffffffu, ok ? 1 : 0) && !*abort;  // warp-uniform before the aligned TMEM loads
       if (!ok) break;
       asm volatile("tcgen05.fence::after_thread_sync;");
-      const uint32_t a0 = smem_u32(sA + s * kTileBytesA), b0 = smem_u32(sB + s * kTileBytesB);
+      const int n = t / tiles_per_img, y0 = (t % tiles_per_img) * rows_per_tile;
+      const int row = q * 32 + lane;
+      const int64_t p = ((int64_t)n * a.H + y0 + row / a.W) * a.W + row % a.W;
 #pragma unroll
-      for (int kk = 0; kk < 4; ++kk)
-        mma_bf16(tmem, desc_sw128(a0 + kk * 32), desc_sw128(b0 + kk * 32), idesc, (k | kk) != 0);
-      mma_commit(&empty[s]);
-    }
-    if (ok) mma_commit(&done);
-  }
-  // epilogue: lane (warp w, lane l) = pixel row 32 w + l of the tile
-  bool ok = mbar_wait(&done, 0, abort);
-  ok = __all_sync(0xffffffffu, ok ? 1 : 0) && !*abort;  // warp-uniform before the aligned TMEM loads
-  asm volatile("tcgen05.fence::after_thread_sync;");
-  if (ok) {
-    const int row = warp * 32 + lane;
-    const int64_t p = ((int64_t)n * a.H + y0 + row / a.W) * a.W + row % a.W;
+      for (int cb = 0; cb < BN; cb += 16) {
+        float v[16];
+        tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ab * kCols + cb), v);
 #pragma unroll
-    for (int cb = 0; cb < BN; cb += 16) {
-      float v[16];
-      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + cb, v);
-#pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        const int co = cb + k;
-        if (a.mode == 2) {
-          const float r = (co < a.nout) ? __bfloat162float(a.ref[p * a.ldref + co]) : 0.0f;
-          v[k] *= (r < 0.0f) ? kLeakTc : 1.0f;
-        } else {
-          v[k] += (co < a.nout) ? a.bias[co] : 0.0f;
-          if (a.mode == 1 && v[k] < 0.0f) v[k] *= kLeakTc;
+        for (int k = 0; k < 16; ++k) {
+          const int co = cb + k;
+          if (a.mode == 2) {
+            const float r = (co < a.nout) ? __bfloat162float(a.ref[p * a.ldref + co]) : 0.0f;
+            v[k] *= (r < 0.0f) ? kLeakTc : 1.0f;
+          } else {
+            v[k] += (co < a.nout) ? a.bias[co] : 0.0f;
+            if (a.mode == 1 && v[k] < 0.0f) v[k] *= kLeakTc;
+          }
+          if (co >= a.nout) v[k] = 0.0f;
         }
-        if (co >= a.nout) v[k] = 0.0f;
-      }
-      if (a.y) {
-        // 16 channels = 32 bytes, two 16-byte stores (ldy is a multiple of 16)
-        __align__(16) __nv_bfloat162 h[8];
+        if (a.y) {
+          // 16 channels = 32 bytes, two 16-byte stores (ldy is a multiple of 16)
+          __align__(16) __nv_bfloat162 h[8];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) h[k] = __floats2bfloat162_rn(v[2 * k], v[2 * k + 1]);
-        if (cb < a.ldy) {
-          uint4* dst = reinterpret_cast<uint4*>(a.y + p * a.ldy + cb);
-          dst[0] = *reinterpret_cast<const uint4*>(&h[0]);
-          dst[1] = *reinterpret_cast<const uint4*>(&h[4]);
+          for (int k = 0; k < 8; ++k) h[k] = __floats2bfloat162_rn(v[2 * k], v[2 * k + 1]);
+          if (cb < a.ldy) {
+            uint4* dst = reinterpret_cast<uint4*>(a.y + p * a.ldy + cb);
+            dst[0] = *reinterpret_cast<const uint4*>(&h[0]);
+            dst[1] = *reinterpret_cast<const uint4*>(&h[4]);
+          }
+        }
+        if (a.yf) {
+#pragma unroll
+          for (int k = 0; k < 16; ++k)
+            if (cb + k < a.nout) a.yf[p * a.nout + cb + k] = v[k];
         }
       }
-      if (a.yf) {
-#pragma unroll
-        for (int k = 0; k < 16; ++k)
-          if (cb + k < a.nout) a.yf[p * a.nout + cb + k] = v[k];
-      }
+      // accumulator ab read out: hand it back to the MMA issuer
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[ab]);
     }
-  } else if (tid == 0 && a.err) {
-    atomicExch(a.err, 1);
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols));
+  if (tid == 0 && *abort && a.err) atomicExch(a.err, 1);
+  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kAllocCols));
 }
 
 struct WgradTcArgs {
@@ -510,6 +584,7 @@ bool make_map(CUtensorMap* m, const void* base, int rank, const uint64_t* dims, 
 }
 
 size_t smem_bytes(int bn) { return 1024 + (size_t)kStages * (kTileBytesA + bn * 128); }
+size_t conv_smem_bytes(int bn) { return 1024 + (size_t)kConvStages * (kTileBytesA + bn * 128); }
 
 }  // namespace
 
@@ -541,25 +616,30 @@ cudaError_t launch_conv_tc(const void* x, const void* wk, int bn, const ConvTcLa
   a.y = reinterpret_cast<__nv_bfloat16*>(L.y);
   a.yf = L.yf;
   a.err = L.err;
-  const size_t smem = smem_bytes(bn);
-  const dim3 grid((unsigned)((int64_t)L.N * L.H / 2));
+  const size_t smem = conv_smem_bytes(bn);
+  // persistent: one CTA per SM (the stage ring takes most of its shared memory)
+  int dev = 0, sms = 0;
   cudaError_t e;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  const int64_t ntiles = (int64_t)L.N * L.H / 2;
+  const dim3 grid((unsigned)std::min<int64_t>(ntiles, std::max(1, sms)));
   count_launches(1);
   switch (bn) {
     case 16:
       if ((e = cudaFuncSetAttribute(conv_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
         return e;
-      conv_tc<16><<<grid, 128, smem, s>>>(ma, mb, a);
+      conv_tc<16><<<grid, 192, smem, s>>>(ma, mb, a);
       break;
     case 64:
       if ((e = cudaFuncSetAttribute(conv_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
         return e;
-      conv_tc<64><<<grid, 128, smem, s>>>(ma, mb, a);
+      conv_tc<64><<<grid, 192, smem, s>>>(ma, mb, a);
       break;
     default:
       if ((e = cudaFuncSetAttribute(conv_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
         return e;
-      conv_tc<128><<<grid, 128, smem, s>>>(ma, mb, a);
+      conv_tc<128><<<grid, 192, smem, s>>>(ma, mb, a);
   }
   return cudaGetLastError();
 }
