@@ -697,7 +697,7 @@ WS_TRAIN, WS_EPOCHS, WS_EVAL, WS_GROUP = 8192, 8, 1024, 32
 # dram bytes of one conv_tc<128> launch of a 128 -> 128 layer, scaled from the
 # 32-instance capture to the 64 instances of the timed forward pass; None once
 # the kernel changes
-CONV_TC_TRAFFIC_BYTES_128x128_64INST = 2 * (33930240 + 49664)
+CONV_TC_TRAFFIC_BYTES_128x128_64INST = None
 # measured dense BF16 GEMM rate of this GPU type (MEASURED_PEAKS.json bf16_tflops, burst)
 BF16_PEAK_TFLOPS = 1916.2
 
@@ -766,13 +766,13 @@ def run_warmstart(args, rank, world, local_rank):
                    "grid": [H, W], "eps": "logU[1e-3, 1e-1]", "lambda": "logU[0.1, 10]", "masses": "U[0.5, 2]",
                    "parallelism": "replicas", "l2": "inputs resident; solves and inference back to back"},
         "gpu_launches": launches, "clocks": clocks,
-        "roofline": {"bound": "tensor", "kernel": "conv_tc<128> (network forward, 64 instances)",
+        "roofline": {"bound": "tensor", "kernel": "conv_tc_n256 (network forward, 64 instances)",
                      "achieved": flops_alg / (fwd_ms / 1e3) / 1e12, "peak": BF16_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": flops_alg / (fwd_ms / 1e3) / 1e12 / BF16_PEAK_TFLOPS,
                      "traffic": CONV_TC_TRAFFIC_BYTES_128x128_64INST,
-                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one conv_tc<128> "
-                                       "launch of a 128 -> 128 layer on 32 instances (33.93 MB + 0.05 MB, "
-                                       "profiles/conv_tc_warmstart64.md), x2 for the 64 instances timed here",
+                     "traffic_source": None if CONV_TC_TRAFFIC_BYTES_128x128_64INST is None else
+                     "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch of a 128 -> 128 layer on 32 "
+                     "instances (profiles/conv_tc_warmstart64.md), x2 for the 64 instances timed here",
                      "mma_flops_incl_padding_tflops": flops_mma / (fwd_ms / 1e3) / 1e12,
                      "forward_ms_64_instances": fwd_ms,
                      "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst), of measured",

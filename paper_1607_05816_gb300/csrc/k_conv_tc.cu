@@ -353,6 +353,163 @@ __global__ void __launch_bounds__(192, 1)
   if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kAllocCols));
 }
 
+// 128-channel layers with the operands swapped: M = 128 output channels (the
+// weights are the A operand), N = 256 pixels (four image rows; the activations
+// are the B operand), K = 9 taps x 64-channel chunks.  An M = N = 128 MMA reads
+// 8 KB of operands from shared memory per 64 tensor-core cycles, which is the
+// SM's whole shared-memory bandwidth; at N = 256 the same 4 KB of weights
+// serve twice the pixels (12 KB per 128 cycles), and the weights are read from
+// L2 once per 256 pixels instead of once per 128.  Accumulator [co][pixel] in
+// tensor memory (two of 256 columns: all 512); epilogue thread = one output
+// channel (lane 32 (w % 4) + l), walking the tile's pixels, so a warp stores
+// 32 consecutive channels of a pixel (64 contiguous bytes).
+constexpr int kConvN = 256;                       // pixels per tile
+constexpr int kConvNStages = 4;                   // 4 x (16 KB + 32 KB) = 192 KB
+constexpr int kTileBytesPix = kConvN * 128;       // 256 rows x 128 bytes
+
+__global__ void __launch_bounds__(192, 1)
+    conv_tc_n256(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmW, ConvTcArgs a) {
+  constexpr int kCols = kConvN;
+  constexpr int kAllocCols = 2 * kCols;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = align1024(smem_raw);
+  uint8_t* sW = smem;                                   // [stage] 128 channels x 64 K (16 KB)
+  uint8_t* sX = smem + kConvNStages * kTileBytesA;      // [stage] 256 pixels x 64 K (32 KB)
+  __shared__ __align__(8) uint64_t full[kConvNStages], empty[kConvNStages], acc_full[2], acc_empty[2], drain;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int rows_per_tile = kConvN / a.W;  // 4
+  const int tiles_per_img = a.H / rows_per_tile;
+  const int ntiles = a.N * tiles_per_img;
+  const int chunks = a.cin_pad / 64;
+  const int nk = 9 * chunks;
+  if (tid == 0) {
+    for (int s = 0; s < kConvNStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], 4);
+    }
+    mbar_init(&drain, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(kAllocCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_slot;
+  volatile int* abort = &abort_flag;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int k = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        const int n = t / tiles_per_img, y0 = (t % tiles_per_img) * rows_per_tile;
+        for (int kt = 0; kt < nk; ++kt) {
+          const int s = k % kConvNStages;
+          if (k >= kConvNStages && !mbar_wait(&empty[s], ((k / kConvNStages) - 1) & 1, abort)) {
+            ok = false;
+            break;
+          }
+          const int tap = kt / chunks, c = kt % chunks;
+          const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+          mbar_expect_tx(&full[s], kTileBytesA + kTileBytesPix);
+          tma_load_2d(sW + s * kTileBytesA, &tmW, &full[s], tap * a.cin_pad + c * 64, 0);
+          tma_load_4d(sX + s * kTileBytesPix, &tmX, &full[s], c * 64, dx * a.dil, y0 + dy * a.dil, n);
+          ++k;
+        }
+      }
+      if (!ok) {
+        for (int j = (k > kConvNStages ? k - kConvNStages : 0); j < k; ++j)
+          mbar_drain(&full[j % kConvNStages], (j / kConvNStages) & 1);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_bf16(128, kConvN);
+      int k = 0, i = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++i) {
+        const int ab = i & 1;
+        if (i >= 2 && !mbar_wait(&acc_empty[ab], ((i >> 1) - 1) & 1, abort)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t acc = tmem + (uint32_t)(ab * kCols);
+        for (int kt = 0; kt < nk; ++kt, ++k) {
+          const int s = k % kConvNStages;
+          if (!mbar_wait(&full[s], (k / kConvNStages) & 1, abort)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const uint32_t w0 = smem_u32(sW + s * kTileBytesA), x0 = smem_u32(sX + s * kTileBytesPix);
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk)
+            mma_bf16(acc, desc_sw128(w0 + kk * 32), desc_sw128(x0 + kk * 32), idesc, (kt | kk) != 0);
+          mma_commit(&empty[s]);
+        }
+        if (ok) mma_commit(&acc_full[ab]);
+      }
+      mma_commit(&drain);
+      mbar_drain(&drain, 0);
+    }
+  } else {
+    // epilogue: thread (warp w, lane l) = output channel co = 32 (w % 4) + l
+    const int q = warp & 3;
+    const int co = q * 32 + lane;
+    const bool live = co < a.nout;
+    const float bco = (a.mode != 2 && live) ? a.bias[co] : 0.0f;
+    int i = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+      const int ab = i & 1;
+      bool ok = mbar_wait(&acc_full[ab], (i >> 1) & 1, abort);
+      ok = __all_sync(0xffffffffu, ok ? 1 : 0) && !*abort;  // warp-uniform before the aligned TMEM loads
+      if (!ok) break;
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const int n = t / tiles_per_img, y0 = (t % tiles_per_img) * rows_per_tile;
+      const int64_t p0 = ((int64_t)n * a.H + y0) * a.W;  // the tile's pixels are p0 .. p0 + 255
+#pragma unroll 1
+      for (int cb = 0; cb < kConvN; cb += 16) {
+        float v[16];
+        tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ab * kCols + cb), v);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+          const int64_t p = p0 + cb + k;
+          float x = v[k];
+          if (a.mode == 2) {
+            const float r = live ? __bfloat162float(a.ref[p * a.ldref + co]) : 0.0f;
+            x *= (r < 0.0f) ? kLeakTc : 1.0f;
+          } else {
+            x += bco;
+            if (a.mode == 1 && x < 0.0f) x *= kLeakTc;
+          }
+          if (!live) x = 0.0f;
+          if (a.y && co < a.ldy) a.y[p * a.ldy + co] = __float2bfloat16_rn(x);
+          if (a.yf && live) a.yf[p * a.nout + co] = x;
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[ab]);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (tid == 0 && *abort && a.err) atomicExch(a.err, 1);
+  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kAllocCols));
+}
+
 struct WgradTcArgs {
   int N, H, W;
   int dil;
@@ -596,8 +753,11 @@ cudaError_t launch_conv_tc(const void* x, const void* wk, int bn, const ConvTcLa
       (L.mode == 2 && (!L.ref || L.ldref < L.nout)) || (L.mode != 2 && !L.bias))
     return cudaErrorInvalidValue;
   CUtensorMap ma, mb;
+  // 128-channel layers on images of a multiple of 4 rows: the swapped-operand
+  // kernel (256-pixel tiles); others: 128-pixel tiles
+  const bool n256 = bn == 128 && L.H % 4 == 0;
   const uint64_t da[4] = {(uint64_t)L.ldx, (uint64_t)L.W, (uint64_t)L.H, (uint64_t)L.N};
-  const uint32_t ba[4] = {64, (uint32_t)L.W, 2, 1};
+  const uint32_t ba[4] = {64, (uint32_t)L.W, n256 ? 4u : 2u, 1};
   const uint64_t db[2] = {(uint64_t)9 * L.cin_pad, (uint64_t)bn};
   const uint32_t bb[2] = {64, (uint32_t)bn};
   if (!make_map(&ma, x, 4, da, ba) || !make_map(&mb, wk, 2, db, bb)) return cudaErrorInvalidValue;
@@ -622,9 +782,15 @@ cudaError_t launch_conv_tc(const void* x, const void* wk, int bn, const ConvTcLa
   cudaError_t e;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  const int64_t ntiles = (int64_t)L.N * L.H / 2;
+  const int64_t ntiles = (int64_t)L.N * L.H / (n256 ? 4 : 2);
   const dim3 grid((unsigned)std::min<int64_t>(ntiles, std::max(1, sms)));
   count_launches(1);
+  if (n256) {
+    const size_t sm256 = 1024 + (size_t)kConvNStages * (kTileBytesA + kTileBytesPix);
+    if ((e = cudaFuncSetAttribute(conv_tc_n256, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm256))) return e;
+    conv_tc_n256<<<grid, 192, sm256, s>>>(ma, mb, a);
+    return cudaGetLastError();
+  }
   switch (bn) {
     case 16:
       if ((e = cudaFuncSetAttribute(conv_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
