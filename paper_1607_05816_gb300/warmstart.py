@@ -394,7 +394,8 @@ def evaluate_tc(net, inst, H, W, *, group, tol=1e-6, plain_sample=16, max_iter=2
         res["batched_tr_ms"] += ms
         res["batched_tr_iters"].append(info["total_iters"])
         res["worst_err_batched_tr"] = max(res["worst_err_batched_tr"], info["marg_err"])
-        grp.update(cold_tr_iters=info["total_iters"], cold_tr_ms=round(ms, 2))
+        grp.update(cold_tr_iters=info["total_iters"], cold_tr_ms=round(ms, 2), cold_tr_fp64_iters=info["polish_iters"],
+                   cold_tr_fp64_checks=info["verifications"])
 
         def warm():
             U0, V0 = net.predict(P[sl].contiguous(), Q[sl].contiguous(), inst["eps"][sl], inst["lam"][sl])
@@ -408,7 +409,8 @@ def evaluate_tc(net, inst, H, W, *, group, tol=1e-6, plain_sample=16, max_iter=2
         res["warm_infer_ms"] += ms_inf
         res["warm_iters"].append(info["total_iters"])
         res["worst_err_warm"] = max(res["worst_err_warm"], info["marg_err"])
-        grp.update(warm_iters=info["total_iters"], warm_ms=round(ms, 2))
+        grp.update(warm_iters=info["total_iters"], warm_ms=round(ms, 2), warm_fp64_iters=info["polish_iters"],
+                   warm_fp64_checks=info["verifications"])
         res["groups"].append(grp)
         res.setdefault("_last_warm", (s, Uw, Vw))
     return res
