@@ -192,6 +192,8 @@ typedef struct {
   int polish_iters;     /* iterations run in FP64 after the FP32 floor (opts.verify) */
   double marg_err_fp32; /* last FP32-evaluated violation (NaN if none) */
   int mixed_iters;      /* UOT_MIXED: iterations (stages included) run with the tensor-core passes */
+  int precise_iters;    /* opts.verify on grids: FP32 iterations run with the passes that form their
+                           exponents in float-float, after the plain FP32 check stalled */
 } uot_result;
 
 /* Version string of the library build. */
@@ -267,6 +269,22 @@ uot_status uot_force_batch_warps(int warps);
  * A few milliseconds of work; synchronises `stream`.
  */
 uot_status uot_probe_pipes(double* out, void* stream);
+
+/*
+ * uot_force_precise_passes -- on = 1: every FP32 grid pass (uot_solve,
+ * uot_solve_many, uot_gibbs_log, ...) runs the pass that forms its exponents
+ * t_j - k (x_i - y_j)^2 - m_i in float-float (the squared distance by exact
+ * TwoSum, the staged line values, the product with k = log2(e)/eps and the
+ * running maximum), rounding only the final small difference to FP32 for the
+ * exponential.  The usual passes form these exponents in FP32, which costs
+ * ulp(|t_j|) per term when values and costs are large (lambda >> eps): their
+ * rounding floor on the marginal violation can then lie above 1e-6.  Solves
+ * with opts.verify switch to the precise pass by themselves when their FP32
+ * check stalls (uot_result.precise_iters); this switch forces it everywhere
+ * (tests, measurements).  on = 0 restores the default.  Returns the previous
+ * setting.  Process-wide, not tied to a stream.
+ */
+int uot_force_precise_passes(int on);
 
 /*
  * uot_selftest_bounded_wait -- failure-detection self-test (instrumentation).

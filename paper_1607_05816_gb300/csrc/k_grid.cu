@@ -20,6 +20,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <string>
@@ -639,6 +640,129 @@ __global__ void __launch_bounds__(WARPS * 32)
 
 
 // ---------------------------------------------------------------------------
+// FP32 pass with float-float exponents ("precise pass").  The log-sum-exp
+// tiles above stage each line value relative to the line's maximum and form
+// t_j - k (x_i - y_j)^2 - m_i in FP32: a term whose value and cost are both
+// large (tens to hundreds in log2 units, as with lambda >> eps) loses
+// ulp(|t_j|) of its exponent, and the FP32 check stalls above 1e-6.  Here the
+// staged values, the squared distance x_i - y_j (exact TwoSum), its product
+// with k = log2(e)/eps and the running maximum are all float-float; only the
+// final difference a_ij - m_i (small for every term that matters) is rounded
+// to FP32 for the exponential.  One warp per (line, 32 R outputs), an online
+// log-sum-exp per output (rescaled when a new maximum appears), the same
+// float-float epilogue as the other passes.  About 30 FP32 operations per
+// term: the pass the FP32 solves switch to when their check stalls, far
+// cheaper than the FP64 iterations that follow it only if it stalls too.
+// ---------------------------------------------------------------------------
+constexpr ff kLog2eFF{1.44269502162933349609375f, 1.925963033500011e-08f};
+
+template <int R, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32) grid_pass_ffp(PassArgs a, Epilogue epi) {
+  extern __shared__ float4 sm_ffp[];  // [WARPS][nin] {t.hi, t.lo, y, 0}, t in log2 units
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int l = blockIdx.y * WARPS + warp;
+  const int i0 = blockIdx.x * (32 * R);
+  const int64_t bz = blockIdx.z;
+  const int nin = a.nin, nout = a.nout, nlines = a.nlines;
+  const float2* in = a.in + bz * (int64_t)nlines * nin;
+  float* zprev = a.zprev ? a.zprev + bz * (int64_t)nout * nlines : nullptr;
+  float num = 0.0f, den = 0.0f;
+  bool owns[R];
+  int64_t pt[R];
+  float xr[R];
+  EpiPre pre[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int i = i0 + lane + 32 * r;
+    owns[r] = l < nlines && i < nout;
+    pt[r] = (int64_t)i * nlines + l;
+    xr[r] = a.xo[i < nout ? i : nout - 1];
+    if (owns[r]) epilogue_prefetch(epi, bz, pt[r], pre[r]);
+  }
+  if (a.zero_acc && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x < 2) a.zero_acc[2 * bz + threadIdx.x] = 0.0;
+  if (l < nlines) {
+    float4* line = sm_ffp + (size_t)warp * nin;
+    const int64_t base = (int64_t)l * nin;
+    float mx = -INFINITY;
+    for (int j = lane; j < nin; j += 32) mx = fmaxf(mx, load_L_ff(a, in, base + j).hi);
+    mx = warp_maxf(mx);
+    if (mx == -INFINITY) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        if (!owns[r]) continue;
+        if (zprev) zprev[pt[r]] = -INFINITY;
+        float n1, d1;
+        epilogue_apply(epi, bz, pt[r], ff_ninf(), pre[r], n1, d1);
+        num += n1;
+        den += d1;
+      }
+    } else {
+      // staged: (L_j - mx) log2(e) in float-float; mx is any FP32 shift, added back exactly below
+      for (int j = lane; j < nin; j += 32) {
+        const ff v = load_L_ff(a, in, base + j);
+        const ff t = (v.hi == -INFINITY) ? ff_ninf() : ff_mul(ff_add_f(v, -mx), kLog2eFF);
+        line[j] = make_float4(t.hi, t.lo, a.yi[j], 0.0f);
+      }
+      __syncwarp();
+      const ff k2 = ff_mul(ffl(a.inv_eps), kLog2eFF);
+      float mh[R], ml[R], sum[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        mh[r] = -INFINITY;
+        ml[r] = 0.0f;
+        sum[r] = 0.0f;
+      }
+      for (int j = 0; j < nin; ++j) {
+        const float4 tj = line[j];
+        if (tj.x == -INFINITY) continue;  // uniform over the warp
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          // d = x - y exactly, d^2 and c = k2 d^2 as unnormalised float-float pairs
+          const ff d = ff_two_sum(xr[r], -tj.z);
+          const float p = d.hi * d.hi;
+          const float pe = fmaf(d.hi, d.hi, -p) + 2.0f * d.hi * d.lo;
+          const float ch = k2.hi * p;
+          const float ce = fmaf(k2.hi, p, -ch) + fmaf(k2.hi, pe, k2.lo * p);
+          // a = t - c
+          const ff s = ff_two_sum(tj.x, -ch);
+          const float al = s.lo + (tj.y - ce);
+          if (mh[r] == -INFINITY) {
+            mh[r] = s.hi;
+            ml[r] = al;
+            sum[r] = 1.0f;
+            continue;
+          }
+          const ff q = ff_two_sum(s.hi, -mh[r]);
+          const float dm = q.hi + (q.lo + (al - ml[r]));
+          if (dm > 0.0f) {
+            sum[r] = fmaf(sum[r], ex2_approx(-dm), 1.0f);
+            mh[r] = s.hi;
+            ml[r] = al;
+          } else {
+            sum[r] += ex2_approx(dm);
+          }
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        if (!owns[r]) continue;
+        ff z = ff_ninf();
+        if (mh[r] != -INFINITY && sum[r] > 0.0f) {
+          const ff m2 = ff_add_f(ff_fast_two_sum(mh[r], ml[r]), lg2_approx(sum[r]));  // log2 units
+          z = ff_add_f(ff_mul(m2, ln2_ff()), mx);
+        }
+        if (zprev) zprev[pt[r]] = z.hi;
+        float n1, d1;
+        epilogue_apply(epi, bz, pt[r], z, pre[r], n1, d1);
+        num += n1;
+        den += d1;
+      }
+    }
+  }
+  if (epi.err) block_add2f<WARPS * 32>(num, den, epi.err + 2 * bz);
+}
+
+// ---------------------------------------------------------------------------
 // Short lines (nin, nout <= 64, e.g. the 32- and 64-point axes of a 3-D
 // colour grid): one warp per (line, batch entry), OPL = 1 or 2 outputs per
 // lane, the line staged in the warp's shared memory, no combine across warps.
@@ -1130,11 +1254,40 @@ std::string grid_tile_table() {
   return s;
 }
 
+namespace {
+std::atomic<int> g_precise_forced{0};
+
+cudaError_t launch_ffp(const PassArgs& a, const Epilogue& epi, int nbatch, cudaStream_t s) {
+  constexpr int R = 2;
+  const bool four = (size_t)4 * a.nin * sizeof(float4) <= 96 * 1024;
+  const int warps = four ? 4 : 1;
+  const dim3 grid((a.nout + 32 * R - 1) / (32 * R), (a.nlines + warps - 1) / warps, nbatch);
+  if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidConfiguration;
+  const size_t smem = (size_t)warps * a.nin * sizeof(float4);
+  if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  cudaError_t e;
+  if (four) {
+    if (smem > 48 * 1024 &&
+        (e = cudaFuncSetAttribute(grid_pass_ffp<R, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+      return e;
+    grid_pass_ffp<R, 4><<<grid, 4 * 32, smem, s>>>(a, epi);
+  } else {
+    if (smem > 48 * 1024 &&
+        (e = cudaFuncSetAttribute(grid_pass_ffp<R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+      return e;
+    grid_pass_ffp<R, 1><<<grid, 32, smem, s>>>(a, epi);
+  }
+  return cudaGetLastError();
+}
+}  // namespace
+
+int grid_force_precise(int on) { return g_precise_forced.exchange(on ? 1 : 0); }
+
 cudaError_t launch_grid_pass(int prec, const double* in, const double* logw, int in_is_pot,
                              int nlines, int nin, const void* yi, int nout, const void* xo,
                              double eps, int nbatch, const Epilogue& epi, cudaStream_t s,
                              float* zprev, int use_prev, double* zero_acc, int tc3_ok, int* tc_err,
-                             const BlkAxis* blk) {
+                             const BlkAxis* blk, int precise) {
   if (prec == UOT_F32) {
     PassArgs a;
     a.in = reinterpret_cast<const float2*>(in);
@@ -1154,6 +1307,14 @@ cudaError_t launch_grid_pass(int prec, const double* in, const double* logw, int
     a.tc_err = tc_err;
     a.nbatch = nbatch;
     a.blk = blk ? *blk : BlkAxis{0, 0.0f, 0.0f};
+    if (precise || g_precise_forced.load()) {
+      prof_mark_begin(PROF_GRID_PASS, s);
+      count_launches(1);
+      cudaError_t e = launch_ffp(a, epi, nbatch, s);
+      if (e != cudaSuccess) return e;
+      prof_mark_end(PROF_GRID_PASS, s);
+      return cudaGetLastError();
+    }
     const int tile = pick_tile(a, nbatch, s);
     const int fam = (is_blk(tile) && grid_blk_ok(a, tile - kBlkTile0)) ? PROF_GRID_BLK : PROF_GRID_PASS;
     prof_mark_begin(fam, s);

@@ -149,6 +149,8 @@ uot_status uot_force_grid_tile(int idx) { return grid_force_tile(idx) == 0 ? UOT
 
 int uot_grid_tile_count(void) { return grid_tile_count(); }
 
+int uot_force_precise_passes(int on) { return grid_force_precise(on); }
+
 uot_status uot_selftest_bounded_wait(double seconds, void* stream) {
   clear_stale_error();
   if (!(seconds > 0.0) || seconds > 10.0) return UOT_EINVAL;

@@ -752,6 +752,9 @@ struct Gibbs {
   bool host_setup = true;
   // UOT_MIXED: once set, the passes run on the FP32 kernels (end of the BF16 phase)
   bool tc_off = false;
+  // FP32 grids: once set, the passes form their exponents in float-float
+  // (grid_pass_ffp), below the FP32 passes' rounding floor
+  bool precise = false;
   void* Lscratch = nullptr;     // rows: shifted input line
   void* part = nullptr;         // FP32 point clouds: per-chunk partial sums
   float* zrow[2] = {nullptr, nullptr};  // FP32 point clouds: previous results per direction
@@ -971,7 +974,9 @@ struct Gibbs {
         }
         double* za = nullptr;
         if (k == 0 && zero_acc) {
-          if (prec != UOT_F64) {
+          // cleared inside the first pass only when that pass is not also the
+          // last one (whose blocks accumulate into it): 2-D and 3-D grids
+          if (prec != UOT_F64 && d > 1) {
             za = zero_acc;
           } else {
             cudaError_t e0 = cudaMemsetAsync(zero_acc, 0, 16 * (size_t)nbatch, s);
@@ -986,7 +991,7 @@ struct Gibbs {
           err = launch_grid_pass(prec == UOT_F64 ? UOT_F64 : UOT_F32, cur, logw, cur_is_pot,
                                  (int)nlines, in_shape[ax], in_axes[ax], out_shape[ax],
                                  out_axes[ax], eps, nbatch, e, s, zbuf[dir][k], use_prev, za,
-                                 tc3_ok(dir, ax, eps, in_shape[ax]), tc_err, &blk[dir][ax]);
+                                 tc3_ok(dir, ax, eps, in_shape[ax]), tc_err, &blk[dir][ax], precise ? 1 : 0);
         }
         if (err != cudaSuccess) return err;
         cur = pass[k & 1];

@@ -479,7 +479,11 @@ cudaError_t launch_grid_pass(int prec, const double* in, const double* logw, int
                              int nlines, int nin, const void* yi, int nout, const void* xo,
                              double eps, int nbatch, const Epilogue& epi, cudaStream_t s,
                              float* zprev, int use_prev, double* zero_acc = nullptr, int tc3_ok = 0,
-                             int* tc_err = nullptr, const BlkAxis* blk = nullptr);
+                             int* tc_err = nullptr, const BlkAxis* blk = nullptr, int precise = 0);
+// precise = 1 (FP32): the pass with float-float exponents (k_grid.cu,
+// grid_pass_ffp), as every FP32 pass runs while grid_force_precise(1) is set;
+// returns the previous setting
+int grid_force_precise(int on);
 
 // Tensor-core convolutions of the warm-start network (k_conv_tc.cu); BF16
 // tensors are passed as void pointers.

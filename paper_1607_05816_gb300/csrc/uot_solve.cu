@@ -148,6 +148,9 @@ uot_status solve_impl(const uot_geom* g, int batch, const void* p, const void* d
   const double mixed_switch = o->mixed_switch > 0.0 ? o->mixed_switch : 1e-3;
   int mixed_iters = 0;
   bool mixed_handover = false;  // set by decide(): the graph block must be recaptured
+  // verify on grids: iterations run with the float-float-exponent passes after
+  // the FP32 check stalled (-1: not switched)
+  int precise_from = -1;
 
   auto read_err = [&](double& out) -> cudaError_t {
     cudaError_t e = cudaMemcpyAsync(acc_h.data(), acc, 16 * (size_t)batch, cudaMemcpyDeviceToHost, s);
@@ -454,8 +457,20 @@ uot_status solve_impl(const uot_geom* g, int batch, const void* p, const void* d
         best_it = it;
         return cudaSuccess;
       }
-      // the FP32 check's rounding floor: FP64 iterations take over
-      if (stalled()) polish = stop = true;
+      // the FP32 check's rounding floor: on grids the passes with float-float
+      // exponents take over (their floor is far lower), then, if those stall
+      // too, FP64 iterations
+      if (stalled()) {
+        if (g->kind == UOT_GEOM_GRID && !G.precise) {
+          G.precise = true;
+          precise_from = total;
+          mixed_handover = true;  // recapture the graph block with the new passes
+          first_err = NAN;
+          best_err = INFINITY;
+        } else {
+          polish = stop = true;
+        }
+      }
       return cudaSuccess;
     };
     // shift: the translation step after the V-update (opts.translate)
@@ -687,6 +702,7 @@ uot_status solve_impl(const uot_geom* g, int batch, const void* p, const void* d
     res->polish_iters = npolish;
     res->marg_err_fp32 = err32;
     res->mixed_iters = prec != UOT_MIXED ? 0 : (G.tc_off ? mixed_iters : total);
+    res->precise_iters = precise_from < 0 ? 0 : total - precise_from - npolish;
   }
   return out;
 }

@@ -64,7 +64,8 @@ class CBatchProblem(C.Structure):
 class CResult(C.Structure):
     _fields_ = [("iters", C.c_int), ("total_iters", C.c_int), ("marg_err", C.c_double),
                 ("ms", C.c_double), ("status", C.c_int), ("verifications", C.c_int),
-                ("polish_iters", C.c_int), ("marg_err_fp32", C.c_double), ("mixed_iters", C.c_int)]
+                ("polish_iters", C.c_int), ("marg_err_fp32", C.c_double), ("mixed_iters", C.c_int),
+                ("precise_iters", C.c_int)]
 
 
 _LIB = None
@@ -146,6 +147,7 @@ _SIGS = {
     "uot_force_batch_warps": (C.c_int, [C.c_int]),
     "uot_selftest_bounded_wait": (C.c_int, [C.c_double, C.c_void_p]),
     "uot_probe_pipes": (C.c_int, [C.POINTER(C.c_double), C.c_void_p]),
+    "uot_force_precise_passes": (C.c_int, [C.c_int]),
     "uot_autotune_table": (C.c_int, [C.c_char_p, C.c_int]),
     "uot_barycenter_div": (C.c_int, [C.POINTER(CGeom), C.c_int, C.POINTER(C.c_double), C.c_void_p,
                                      C.c_void_p, C.c_void_p, C.POINTER(CDiv), C.POINTER(CDiv),
@@ -202,6 +204,12 @@ def launch_count() -> int:
 def set_autotune(mode: int) -> int:
     """Grid-pass tile tuner on (1) or off (0); returns the previous mode."""
     return int(load().uot_set_autotune(int(mode)))
+
+
+def force_precise_passes(on: bool) -> bool:
+    """uot_force_precise_passes: every FP32 grid pass forms its exponents in
+    float-float (on) or the usual tiles run (off); returns the previous setting."""
+    return bool(load().uot_force_precise_passes(int(bool(on))))
 
 
 def force_grid_tile(idx: int):
@@ -375,7 +383,7 @@ class Geometry:
 def _info(r: "CResult", st: int) -> dict:
     return dict(iters=r.iters, total_iters=r.total_iters, marg_err=r.marg_err, ms=r.ms,
                 status=STATUS[st], verifications=r.verifications, polish_iters=r.polish_iters,
-                marg_err_fp32=r.marg_err_fp32, mixed_iters=r.mixed_iters)
+                marg_err_fp32=r.marg_err_fp32, mixed_iters=r.mixed_iters, precise_iters=r.precise_iters)
 
 
 def _check(status, what):

@@ -44,7 +44,7 @@ C_FIELDS = {
                              "check_every", "plain_scaling", "launch_mode", "U0", "V0", "out_f64", "verify",
                              "mixed_switch", "translate"]),
     "uot_result": (uot.CResult, ["iters", "total_iters", "marg_err", "ms", "status", "verifications",
-                                 "polish_iters", "marg_err_fp32", "mixed_iters"]),
+                                 "polish_iters", "marg_err_fp32", "mixed_iters", "precise_iters"]),
     "uot_batch_problem": (uot.CBatchProblem, ["n", "m", "F1", "F2"]),
 }
 
