@@ -483,13 +483,20 @@ __global__ void __launch_bounds__(192, 1)
       for (int cb = 0; cb < kConvN; cb += 16) {
         float v[16];
         tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ab * kCols + cb), v);
+        // the 16 loads of the previous activation first: y may alias ref as far
+        // as the compiler knows, so a load placed after a store would wait for it
+        float rv[16];
+        if (a.mode == 2) {
+#pragma unroll
+          for (int k = 0; k < 16; ++k)
+            rv[k] = live ? __bfloat162float(a.ref[(p0 + cb + k) * a.ldref + co]) : 0.0f;
+        }
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
           const int64_t p = p0 + cb + k;
           float x = v[k];
           if (a.mode == 2) {
-            const float r = live ? __bfloat162float(a.ref[p * a.ldref + co]) : 0.0f;
-            x *= (r < 0.0f) ? kLeakTc : 1.0f;
+            x *= (rv[k] < 0.0f) ? kLeakTc : 1.0f;
           } else {
             x += bco;
             if (a.mode == 1 && x < 0.0f) x *= kLeakTc;
