@@ -92,9 +92,11 @@ class WarmStartNet:
         return uot.scale_instances(out, lamt)
 
 
-def generate_targets(inst, H, W, *, tol=1e-6, max_iter=3000, group=8, device="cuda"):
-    """Solve every instance (groups share eps, lambda) with uot_solve_many and
-    return (P, Q, U*, V*) as FP32 device tensors [N, H, W]."""
+def generate_targets(inst, H, W, *, tol=1e-6, max_iter=3000, group=8, translate=True, device="cuda"):
+    """Solve every instance (groups share eps, lambda) with uot_solve_many (with
+    the translation step unless told otherwise: the same fixed point, reached
+    in far fewer iterations when lambda >> eps) and return (P, Q, U*, V*) as
+    FP32 device tensors [N, H, W]."""
     xs = [torch.as_tensor(a, dtype=torch.float32, device=device) for a in inst["xs"]]
     geo = uot.Geometry.grid(xs, xs)
     dx = torch.as_tensor(inst["dx"], dtype=torch.float32, device=device).ravel()
@@ -112,7 +114,7 @@ def generate_targets(inst, H, W, *, tol=1e-6, max_iter=3000, group=8, device="cu
         Ug, Vg, _ = uot.solve_many(geo, Pg, dx, Qg, dx, uot.KL(lam), uot.KL(lam), e,
                                    precision=uot.F32, max_iter=max_iter, tol=tol, check_every=20,
                                    eps_start=max(e, 0.1) if e < 0.1 else None, eps_stages=8,
-                                   iters_per_stage=40)
+                                   iters_per_stage=40, translate=translate)
         U[sl] = Ug
         V[sl] = Vg
     return P, Q, U.reshape(n, H, W), V.reshape(n, H, W)
