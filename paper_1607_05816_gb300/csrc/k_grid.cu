@@ -1257,27 +1257,33 @@ std::string grid_tile_table() {
 namespace {
 std::atomic<int> g_precise_forced{0};
 
-cudaError_t launch_ffp(const PassArgs& a, const Epilogue& epi, int nbatch, cudaStream_t s) {
-  constexpr int R = 2;
-  const bool four = (size_t)4 * a.nin * sizeof(float4) <= 96 * 1024;
-  const int warps = four ? 4 : 1;
-  const dim3 grid((a.nout + 32 * R - 1) / (32 * R), (a.nlines + warps - 1) / warps, nbatch);
+template <int R, int WARPS>
+cudaError_t launch_ffp_shape(const PassArgs& a, const Epilogue& epi, int nbatch, cudaStream_t s) {
+  const dim3 grid((a.nout + 32 * R - 1) / (32 * R), (a.nlines + WARPS - 1) / WARPS, nbatch);
   if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidConfiguration;
-  const size_t smem = (size_t)warps * a.nin * sizeof(float4);
+  const size_t smem = (size_t)WARPS * a.nin * sizeof(float4);
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
-  cudaError_t e;
-  if (four) {
-    if (smem > 48 * 1024 &&
-        (e = cudaFuncSetAttribute(grid_pass_ffp<R, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
-      return e;
-    grid_pass_ffp<R, 4><<<grid, 4 * 32, smem, s>>>(a, epi);
-  } else {
-    if (smem > 48 * 1024 &&
-        (e = cudaFuncSetAttribute(grid_pass_ffp<R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
-      return e;
-    grid_pass_ffp<R, 1><<<grid, 32, smem, s>>>(a, epi);
+  if (smem > 48 * 1024) {
+    cudaError_t e =
+        cudaFuncSetAttribute(grid_pass_ffp<R, WARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
   }
+  grid_pass_ffp<R, WARPS><<<grid, WARPS * 32, smem, s>>>(a, epi);
   return cudaGetLastError();
+}
+
+// Launch shape from the work: two outputs per lane and four warps per CTA when
+// there are warps enough to fill the GPU (several per SM), otherwise one
+// output per lane (twice the warps) and one-warp CTAs.
+cudaError_t launch_ffp(const PassArgs& a, const Epilogue& epi, int nbatch, cudaStream_t s) {
+  constexpr int64_t kFill = 152 * 8;  // warps that keep every SM of a GB300 busy
+  const int64_t lines = (int64_t)a.nlines * nbatch;
+  const int64_t warps2 = lines * ((a.nout + 63) / 64);
+  const bool r2 = warps2 >= kFill;
+  const int64_t warps = r2 ? warps2 : lines * ((a.nout + 31) / 32);
+  const bool four = warps >= 4 * kFill && (size_t)4 * a.nin * sizeof(float4) <= 96 * 1024;
+  if (r2) return four ? launch_ffp_shape<2, 4>(a, epi, nbatch, s) : launch_ffp_shape<2, 1>(a, epi, nbatch, s);
+  return four ? launch_ffp_shape<1, 4>(a, epi, nbatch, s) : launch_ffp_shape<1, 1>(a, epi, nbatch, s);
 }
 }  // namespace
 
