@@ -697,7 +697,7 @@ WS_TRAIN, WS_EPOCHS, WS_EVAL, WS_GROUP = 8192, 8, 1024, 32
 # dram bytes of one conv_tc<128> launch of a 128 -> 128 layer, scaled from the
 # 32-instance capture to the 64 instances of the timed forward pass; None once
 # the kernel changes
-CONV_TC_TRAFFIC_BYTES_128x128_64INST = None
+CONV_TC_TRAFFIC_BYTES_128x128_64INST = 2 * (33879040 + 419840)
 # measured dense BF16 GEMM rate of this GPU type (MEASURED_PEAKS.json bf16_tflops, burst)
 BF16_PEAK_TFLOPS = 1916.2
 

@@ -559,12 +559,17 @@ cudaError_t launch_grid_solve_persistent(const PersistLaunch& L, int grid, cudaS
 
 namespace {
 
-// FP64 arithmetic throughout.
+// FP64 arithmetic throughout.  With zprev holding this pass's results from the
+// previous call at the same eps (use_prev), each output takes that value as
+// its log-sum-exp shift and the pass costs one sweep; an output whose sum
+// leaves [1e-290, 1e290] (a shift too far from the new maximum) is redone with
+// its exact maximum (a max sweep and a sum sweep).  The result does not depend
+// on the shift beyond rounding.
 template <int R, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32)
     grid_pass_f64(const double* __restrict__ in, const double* __restrict__ logw, int in_is_pot,
                   int nlines, int nin, const double* __restrict__ yi, int nout,
-                  const double* __restrict__ xo, double eps, Epilogue epi) {
+                  const double* __restrict__ xo, double eps, Epilogue epi, float* zprev, int use_prev) {
   extern __shared__ double2 sm_d2[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int l = blockIdx.y * WARPS + warp;
@@ -596,28 +601,54 @@ __global__ void __launch_bounds__(WARPS * 32)
         }
       }
     } else {
+      float* zp = zprev ? zprev + bz * (int64_t)nout * nlines : nullptr;
       double xr[R], m[R], s[R];
+      bool spec = use_prev && zp;
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const int i = i0 + lane + 32 * r;
         xr[r] = xo[i < nout ? i : nout - 1];
         m[r] = -kInf;
         s[r] = 0.0;
-      }
-      for (int j = 0; j < nin; ++j) {
-        const double2 t = line[j];
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-          const double dd = xr[r] - t.y;
-          m[r] = fmax(m[r], t.x - dd * dd * inv_eps);
+        if (spec) {
+          m[r] = (i < nout) ? (double)zp[(int64_t)i * nlines + l] : 0.0;
+          if (!(m[r] > -kInf)) spec = false;  // no usable shift for this lane
         }
       }
-      for (int j = 0; j < nin; ++j) {
-        const double2 t = line[j];
+      bool exact = !spec;
+      if (spec) {
+        for (int j = 0; j < nin; ++j) {
+          const double2 t = line[j];
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            const double dd = xr[r] - t.y;
+            s[r] += exp((t.x - m[r]) - dd * dd * inv_eps);
+          }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) exact = exact || !(s[r] >= 1e-290 && s[r] <= 1e290);
+      }
+      if (exact) {
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-          const double dd = xr[r] - t.y;
-          s[r] += exp((t.x - m[r]) - dd * dd * inv_eps);
+          m[r] = -kInf;
+          s[r] = 0.0;
+        }
+        for (int j = 0; j < nin; ++j) {
+          const double2 t = line[j];
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            const double dd = xr[r] - t.y;
+            m[r] = fmax(m[r], t.x - dd * dd * inv_eps);
+          }
+        }
+        for (int j = 0; j < nin; ++j) {
+          const double2 t = line[j];
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            const double dd = xr[r] - t.y;
+            s[r] += exp((t.x - m[r]) - dd * dd * inv_eps);
+          }
         }
       }
 #pragma unroll
@@ -625,6 +656,7 @@ __global__ void __launch_bounds__(WARPS * 32)
         const int i = i0 + lane + 32 * r;
         if (i < nout) {
           const double z = m[r] + log(s[r]);
+          if (zp) zp[(int64_t)i * nlines + l] = (float)z;
           double a, b;
           apply_epilogue(epi, bz, (int64_t)i * nlines + l, z, a, b);
           num += a;
@@ -1280,10 +1312,9 @@ cudaError_t launch_ffp(const PassArgs& a, const Epilogue& epi, int nbatch, cudaS
   const int64_t lines = (int64_t)a.nlines * nbatch;
   const int64_t warps2 = lines * ((a.nout + 63) / 64);
   const bool r2 = warps2 >= kFill;
-  const int64_t warps = r2 ? warps2 : lines * ((a.nout + 31) / 32);
-  const bool four = warps >= 4 * kFill && (size_t)4 * a.nin * sizeof(float4) <= 96 * 1024;
-  if (r2) return four ? launch_ffp_shape<2, 4>(a, epi, nbatch, s) : launch_ffp_shape<2, 1>(a, epi, nbatch, s);
-  return four ? launch_ffp_shape<1, 4>(a, epi, nbatch, s) : launch_ffp_shape<1, 1>(a, epi, nbatch, s);
+  if (!r2) return launch_ffp_shape<1, 1>(a, epi, nbatch, s);  // fewer than 2 kFill warps
+  const bool four = warps2 >= 4 * kFill && (size_t)4 * a.nin * sizeof(float4) <= 96 * 1024;
+  return four ? launch_ffp_shape<2, 4>(a, epi, nbatch, s) : launch_ffp_shape<2, 1>(a, epi, nbatch, s);
 }
 }  // namespace
 
@@ -1343,7 +1374,7 @@ cudaError_t launch_grid_pass(int prec, const double* in, const double* logw, int
       if (e != cudaSuccess) return e;
     }
     grid_pass_f64<R, WARPS><<<grid, WARPS * 32, smem, s>>>(
-        in, logw, in_is_pot, nlines, nin, (const double*)yi, nout, (const double*)xo, eps, epi);
+        in, logw, in_is_pot, nlines, nin, (const double*)yi, nout, (const double*)xo, eps, epi, zprev, use_prev);
   }
   prof_mark_end(PROF_GRID_PASS, s);
   return cudaGetLastError();

@@ -776,7 +776,7 @@ struct Gibbs {
         sc.reserve<double>((size_t)inter * nbatch);
         sc.reserve<double>((size_t)inter * nbatch);
       }
-      if (speculate && (prec == UOT_F32 || prec == UOT_MIXED))
+      if (speculate)
         for (int k = 0; k < 2 * g.ndim; ++k) sc.reserve<float>((size_t)inter * nbatch);
       if (prec == UOT_MIXED || prec == UOT_F32) sc.reserve<int>(1);
     } else {
@@ -846,7 +846,7 @@ struct Gibbs {
         pass[0] = sc.take<double>((size_t)inter * nbatch);
         pass[1] = sc.take<double>((size_t)inter * nbatch);
       }
-      if (speculate && (prec == UOT_F32 || prec == UOT_MIXED))
+      if (speculate)
         for (int d = 0; d < 2; ++d)
           for (int k = 0; k < g.ndim; ++k) zbuf[d][k] = sc.take<float>((size_t)inter * nbatch);
       if (prec == UOT_MIXED || prec == UOT_F32) {
