@@ -85,11 +85,13 @@ def test_mixed_barycenter_error_bound():
         assert err <= 0.05 * eps
 
 
-@pytest.mark.parametrize("shape,eps", [((128, 128), 1e-2), ((256, 256), 1e-3)])
-def test_mixed_pipeline_reaches_tol_under_the_oracle(shape, eps):
+@pytest.mark.parametrize("shape,eps,translate", [((128, 128), 1e-2, False), ((256, 256), 1e-3, False),
+                                                 ((128, 128), 1e-2, True)])
+def test_mixed_pipeline_reaches_tol_under_the_oracle(shape, eps, translate):
     """BF16 tensor-core passes (eps-scaling stages, then the final eps until the
     violation reaches mixed_switch), FP32 passes to tol, the stop confirmed in
-    FP64: the returned FP64 potentials meet tol when the oracle evaluates them."""
+    FP64, with and without the translation step: the returned FP64 potentials
+    meet tol when the oracle evaluates them."""
     d = synth.problem_grid2d(*shape, seed=3, masses=(1.0, 1.3))
     og = O.Geometry("grid", xs=[f32(a) for a in d["xs"]], ys=[f32(a) for a in d["ys"]])
     geo = U.Geometry.grid([dev(a) for a in d["xs"]], [dev(a) for a in d["ys"]])
@@ -97,7 +99,7 @@ def test_mixed_pipeline_reaches_tol_under_the_oracle(shape, eps):
     Ug, Vg, info = U.solve(geo, dev(d["p"]), dev(d["dx"]), dev(d["q"]), dev(d["dy"]), U.KL(0.5), U.KL(0.5),
                            eps, precision=U.MIXED, max_iter=20000, tol=tol, check_every=20, eps_start=0.1,
                            eps_stages=10, iters_per_stage=100, launch_mode=2, out_f64=True, verify=True,
-                           mixed_switch=1e-3)
+                           mixed_switch=1e-3, translate=translate)
     print(f"mixed pipeline {shape} eps={eps}: {info}")
     assert info["status"] == "UOT_OK" and info["mixed_iters"] >= 1000, info
     assert info["mixed_iters"] < info["total_iters"]  # the FP32 passes finished the solve
