@@ -152,7 +152,8 @@ typedef struct {
   const void* V0;      /* optional warm start [m] (NULL: V = 0, i.e. b = 1 as in Algorithm 1) */
   int out_f64;         /* 1: U and V are written as double whatever the precision (UOT_F32 and
                           UOT_MIXED: the float-float state, about 48 significant bits, rounded
-                          to FP64 instead of FP32); 0: the precision's type */
+                          to FP64 instead of FP32); 0: the precision's type.  uot_solve,
+                          uot_solve_many and uot_solve_batch */
   int verify;          /* 1 (log domain, UOT_F32 / UOT_MIXED, tol > 0): a stop signalled by the
                           FP32 check is confirmed by evaluating the marginal violation of the
                           current potentials in FP64 (FP64 Gibbs operator on FP64 copies of
@@ -474,8 +475,11 @@ typedef struct {
  *  y, dy, q    packed Y sides likewise
  *  o           options: precision must be UOT_F32; eps, eps_start, eps_stages,
  *              iters_per_stage, max_iter, tol, check_every as in uot_solve;
- *              plain_scaling, U0 and V0 must be 0/NULL
- *  U, V        [sum n], [sum m] outputs (float), packed like the inputs
+ *              translate (every problem KL / KL, else UOT_EUNSUPPORTED) and
+ *              out_f64 as in uot_solve; plain_scaling, verify, U0 and V0 must
+ *              be 0/NULL
+ *  U, V        [sum n], [sum m] outputs (float, or double with out_f64: the
+ *              float-float state rounded to FP64), packed like the inputs
  *  iters       host [nprob] iterations at the final eps per problem, or NULL
  *  errs        host [nprob] last measured marginal violation per problem, or NULL
  * Returns UOT_OK if every problem reached tol (or tol == 0), UOT_NOT_CONVERGED

@@ -527,11 +527,17 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 3 : 2) batch_solve(BatchArg
     }
     for (int i = tid; i < n; i += NT) {
       const float2 u = U[i];
-      a.Uout[xo + i] = (u.x == -INFINITY) ? u.x : u.x + u.y;
+      if (a.Uout64)
+        a.Uout64[xo + i] = (u.x == -INFINITY) ? -kInf : (double)u.x + (double)u.y;
+      else
+        a.Uout[xo + i] = (u.x == -INFINITY) ? u.x : u.x + u.y;
     }
     for (int j = tid; j < m; j += NT) {
       const float2 v = V[j];
-      a.Vout[yo + j] = (v.x == -INFINITY) ? v.x : v.x + v.y;
+      if (a.Vout64)
+        a.Vout64[yo + j] = (v.x == -INFINITY) ? -kInf : (double)v.x + (double)v.y;
+      else
+        a.Vout[yo + j] = (v.x == -INFINITY) ? v.x : v.x + v.y;
     }
     if (tid == 0) {
       a.iters_out[k] = it_final;

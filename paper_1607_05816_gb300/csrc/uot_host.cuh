@@ -1154,13 +1154,14 @@ uot_result empty_result() {
   return r;
 }
 
-// only uot_solve and uot_solve_many honour out_f64 and verify; translate also uot_solve_batch
-uot_status check_opts(const uot_opts* o, bool solve_outputs = false, bool allow_translate = false) {
+// only uot_solve and uot_solve_many honour out_f64 and verify; uot_solve_batch
+// also honours translate and out_f64 (allow_batch)
+uot_status check_opts(const uot_opts* o, bool solve_outputs = false, bool allow_batch = false) {
   if (!o || !prec_ok(o->precision)) return UOT_EINVAL;
   if ((o->out_f64 != 0 && o->out_f64 != 1) || (o->verify != 0 && o->verify != 1)) return UOT_EINVAL;
   if (o->translate != 0 && o->translate != 1) return UOT_EINVAL;
-  if (!solve_outputs && (o->out_f64 || o->verify)) return UOT_EUNSUPPORTED;
-  if (!solve_outputs && !allow_translate && o->translate) return UOT_EUNSUPPORTED;
+  if (!solve_outputs && o->verify) return UOT_EUNSUPPORTED;
+  if (!solve_outputs && !allow_batch && (o->out_f64 || o->translate)) return UOT_EUNSUPPORTED;
   if (!(o->eps > 0.0) || !isfinite(o->eps)) return UOT_EINVAL;
   if (o->max_iter < 0 || o->check_every < 0 || !(o->tol >= 0.0)) return UOT_EINVAL;
   if (o->eps_stages < 0 || o->iters_per_stage < 0) return UOT_EINVAL;

@@ -659,6 +659,8 @@ struct BatchArgs {
   const float* k2;
   float* Uout;
   float* Vout;
+  double* Uout64;  // if set (opts.out_f64): the float-float state rounded to FP64 instead of Uout
+  double* Vout64;
   int* iters_out;
   float* err_out;
   int* next;

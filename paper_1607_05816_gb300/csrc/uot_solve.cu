@@ -885,8 +885,10 @@ uot_status uot_solve_batch(int nprob, const uot_batch_problem* probs, int d, con
   a.eps_ff = d_eps;
   a.inv_eps_ff = d_ieps;
   a.k2 = d_k2;
-  a.Uout = (float*)Uout;
-  a.Vout = (float*)Vout;
+  a.Uout = o->out_f64 ? nullptr : (float*)Uout;
+  a.Vout = o->out_f64 ? nullptr : (float*)Vout;
+  a.Uout64 = o->out_f64 ? (double*)Uout : nullptr;
+  a.Vout64 = o->out_f64 ? (double*)Vout : nullptr;
   a.iters_out = d_iters;
   a.err_out = d_errs;
   a.next = d_next;

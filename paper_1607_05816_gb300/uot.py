@@ -689,7 +689,7 @@ def geodesic(geom: Geometry, p0, p1, ts, dx, dy, F1: Div, Fh: Div, eps, **kw):
 
 def solve_batch(sizes, divs, d, x, p, dx, y, q, dy, eps, *, max_iter=1000, tol=0.0,
                 check_every=10, eps_start=None, eps_stages=10, iters_per_stage=100, U=None, V=None,
-                translate=False):
+                translate=False, out_f64=False):
     """uot_solve_batch (FP32): sizes = [(n_k, m_k)], divs = [(F1_k, F2_k)]; x, p, dx
     packed over the X sides ([sum n, d], [sum n], [sum n]) and y, q, dy over the
     Y sides.  translate (KL / KL problems): the translation step of
@@ -703,17 +703,18 @@ def solve_batch(sizes, divs, d, x, p, dx, y, q, dy, eps, *, max_iter=1000, tol=0
     N = sum(n for n, _ in sizes)
     M = sum(m for _, m in sizes)
     dt = torch.float32
-    U = torch.empty(N, dtype=dt, device=x.device) if U is None else U
-    V = torch.empty(M, dtype=dt, device=x.device) if V is None else V
+    odt = torch.float64 if out_f64 else dt
+    U = torch.empty(N, dtype=odt, device=x.device) if U is None else U
+    V = torch.empty(M, dtype=odt, device=x.device) if V is None else V
     iters = (C.c_int * nprob)()
     errs = (C.c_double * nprob)()
     o = COpts(F32, float(eps), float(eps_start) if eps_start else 0.0, int(eps_stages),
               int(iters_per_stage), int(max_iter), float(tol), int(check_every), 0, 0, None, None,
-              0, 0, 0.0, int(bool(translate)))
+              int(bool(out_f64)), 0, 0.0, int(bool(translate)))
     r = CResult()
     st = lib.uot_solve_batch(nprob, arr, int(d), _ptr(x, dt, "x"), _ptr(p, dt, "p"),
                              _ptr(dx, dt, "dx"), _ptr(y, dt, "y"), _ptr(q, dt, "q"),
-                             _ptr(dy, dt, "dy"), C.byref(o), _ptr(U, dt, "U"), _ptr(V, dt, "V"),
+                             _ptr(dy, dt, "dy"), C.byref(o), _ptr(U, odt, "U"), _ptr(V, odt, "V"),
                              iters, errs, C.byref(r), _stream())
     _check(st, "uot_solve_batch")
     return U, V, list(iters), list(errs), dict(iters=r.iters, total_iters=r.total_iters,

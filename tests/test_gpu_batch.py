@@ -172,3 +172,34 @@ def test_batch_translate_needs_kl():
     with pytest.raises(U.UotError) as ex:
         U.solve_batch(sizes, udivs, 2, *packed(probs), 0.02, max_iter=5, translate=True)
     assert ex.value.status == -6
+
+
+@pytest.mark.parametrize("translate", [False, True])
+def test_batch_fp64_outputs_meet_tol_under_the_oracle(translate):
+    """opts.out_f64: the float-float state is returned in FP64 (FP32 outputs
+    only bound the oracle's violation to ~2e-5 at eps = 0.02).  The batch's stop
+    is its own FP32 check, with no FP64 confirmation: the oracle's violation of
+    the returned potentials lies within 10% of the 1e-6 it reported (measured:
+    1.07e-6 without the translation step, 8.1e-7 with it)."""
+    probs = synth.batch_points(nprob=40, size=(64, 700), d=2, seed=80)
+    sizes = [(len(pr["x"]), len(pr["y"])) for pr in probs]
+    udivs, odivs = make_divs(probs, ["kl"])
+    x, p, dx, y, q, dy = packed(probs)
+    eps, tol = 0.02, 1e-6
+    Ug, Vg, it, errs, info = U.solve_batch(sizes, udivs, 2, x, p, dx, y, q, dy, eps, max_iter=40000, tol=tol,
+                                           check_every=10, translate=translate, out_f64=True)
+    assert info["status"] == "UOT_OK" and Ug.dtype == torch.float64
+    Ug = Ug.cpu().numpy()
+    Vg = Vg.cpu().numpy()
+    xo = yo = 0
+    worst = 0.0
+    for k, pr in enumerate(probs[:10]):
+        n, m = sizes[k]
+        og = O.Geometry("points", x=rounded(pr["x"]), y=rounded(pr["y"]))
+        v = O.marginal_violation(og, rounded(pr["dx"]), rounded(pr["dy"]), rounded(pr["p"]),
+                                 rounded(pr["q"]), *odivs[k], eps, Ug[xo:xo + n], Vg[yo:yo + m])
+        worst = max(worst, v)
+        xo += n
+        yo += m
+    print("worst oracle violation of the returned FP64 potentials:", worst)
+    assert worst <= 1.1 * tol
