@@ -363,6 +363,7 @@ def run_ours(args, rank, world, local_rank):
                   "marg_err_fp64": max(errs), "marg_err_fp32": max(i["marg_err_fp32"] for i in infos),
                   "fp64_confirmations_per_step": sum(i["verifications"] for i in infos) / len(infos),
                   "fp64_iters_per_step": sum(i["polish_iters"] for i in infos) / len(infos),
+                  "precise_iters_per_step": sum(i["precise_iters"] for i in infos) / len(infos),
                   "outputs": "float64"} if verify else
                  {"rule": "FP64 check" if prec == uot.F64 else "FP32 check"}),
         "mixed": ({"bf16_tensor_core_iters_per_step": sum(i["mixed_iters"] for i in infos) / len(infos),
@@ -452,12 +453,14 @@ def run_single(args, rank, world, local_rank):
         tr = bool(getattr(args, "translate", False)) and args.penalty == "kl"
 
         def step():
+            # the stop confirmed in FP64 on FP64 outputs (the float-float state)
             return uot.solve(geo, *ins, F, F, 1e-3, precision=uot.F32, max_iter=MAX_ITER, tol=TOL,
                              check_every=CHECK_EVERY, eps_start=1e-1, eps_stages=10, iters_per_stage=100,
-                             launch_mode=args.launch_mode, translate=tr)
+                             launch_mode=args.launch_mode, translate=tr, out_f64=True, verify=True)
         work_per_iter, unit_work, kernel = 2.0 * 20000 * 20000, "Gexp2/s", "points_partial"
         cfg = {"workload": f"points3d-20000x20000-{args.penalty}0.1-epsscale1e-1to1e-3-tol1e-6"
-                           + ("-translated" if tr else ""), "n": 20000, "m": 20000, "d": 3, "translate": tr}
+                           + ("-translated" if tr else ""), "n": 20000, "m": 20000, "d": 3, "translate": tr,
+               "stop": "FP32 check confirmed by an FP64 evaluation of the returned (FP64) potentials"}
         dtype = "f32"
     elif wl == "dense1d":
         d = synth.problem_1d(256, 256, seed=1234)
@@ -543,7 +546,7 @@ def run_single(args, rank, world, local_rank):
     rank_barrier(world)
     torch.cuda.synchronize()
     launches0 = uot.launch_count()
-    total_ms, iters, errs = 0.0, 0, []
+    total_ms, iters, errs, infos = 0.0, 0, [], []
     for _ in range(args.steps):
         flush.fill_(1.0)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -552,6 +555,7 @@ def run_single(args, rank, world, local_rank):
         e1.record()
         e1.synchronize()
         info = out[-1]
+        infos.append(info)
         total_ms += e0.elapsed_time(e1)
         iters += info["total_iters"]
         errs.append(info["marg_err"])
@@ -571,6 +575,15 @@ def run_single(args, rank, world, local_rank):
         "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic", "config": cfg,
         "gpu_launches": launches, "clocks": clocks,
     }
+    if infos and "verifications" in infos[0] and wl == "points":
+        line["stop"] = {"rule": "FP32 check, confirmed by an FP64 evaluation of the returned potentials' "
+                                "violation (included in the step time); FP64 iterations past the FP32 floor",
+                        "marg_err_fp64": max(errs),
+                        "marg_err_fp32": max(i["marg_err_fp32"] for i in infos),
+                        "fp64_confirmations_per_step": sum(i["verifications"] for i in infos) / len(infos),
+                        "fp64_iters_per_step": sum(i["polish_iters"] for i in infos) / len(infos),
+                        "precise_iters_per_step": sum(i["precise_iters"] for i in infos) / len(infos),
+                        "outputs": "float64"}
     timing = "algorithmic work of all iterations / CUDA-event time of the timed steps"
     if unit_work == "Gexp2/s":
         line["roofline"] = alu_roofline(kernel, achieved, FP32_OPS_PER_TERM["points3" if wl == "points" else "grid"],

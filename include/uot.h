@@ -193,8 +193,9 @@ typedef struct {
   int polish_iters;     /* iterations run in FP64 after the FP32 floor (opts.verify) */
   double marg_err_fp32; /* last FP32-evaluated violation (NaN if none) */
   int mixed_iters;      /* UOT_MIXED: iterations (stages included) run with the tensor-core passes */
-  int precise_iters;    /* opts.verify on grids: FP32 iterations run with the passes that form their
-                           exponents in float-float, after the plain FP32 check stalled */
+  int precise_iters;    /* opts.verify on grids and point clouds (d <= 3): FP32 iterations run with
+                           the passes that form their exponents in float-float, after the plain
+                           FP32 check stalled */
 } uot_result;
 
 /* Version string of the library build. */
@@ -272,10 +273,11 @@ uot_status uot_force_batch_warps(int warps);
 uot_status uot_probe_pipes(double* out, void* stream);
 
 /*
- * uot_force_precise_passes -- on = 1: every FP32 grid pass (uot_solve,
- * uot_solve_many, uot_gibbs_log, ...) runs the pass that forms its exponents
- * t_j - k (x_i - y_j)^2 - m_i in float-float (the squared distance by exact
- * TwoSum, the staged line values, the product with k = log2(e)/eps and the
+ * uot_force_precise_passes -- on = 1: every FP32 Gibbs pass on a grid or on
+ * point clouds of dimension <= 3 (uot_solve, uot_solve_many, uot_gibbs_log,
+ * ...) runs the pass that forms its exponents t_j - k |x_i - y_j|^2 - m_i in
+ * float-float (the coordinate differences by exact TwoSum, the staged input
+ * values, the squared distance, its product with k = log2(e)/eps and the
  * running maximum), rounding only the final small difference to FP32 for the
  * exponential.  The usual passes form these exponents in FP32, which costs
  * ulp(|t_j|) per term when values and costs are large (lambda >> eps): their

@@ -1319,6 +1319,7 @@ cudaError_t launch_ffp(const PassArgs& a, const Epilogue& epi, int nbatch, cudaS
 }  // namespace
 
 int grid_force_precise(int on) { return g_precise_forced.exchange(on ? 1 : 0); }
+int precise_forced() { return g_precise_forced.load(); }
 
 cudaError_t launch_grid_pass(int prec, const double* in, const double* logw, int in_is_pot,
                              int nlines, int nin, const void* yi, int nout, const void* xo,

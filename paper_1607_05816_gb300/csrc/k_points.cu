@@ -280,6 +280,125 @@ __global__ void __launch_bounds__(256)
   if (epi.err) block_add2f<256>(num, den, epi.err);
 }
 
+// ---------------------------------------------------------------------------
+// Precise pass (float-float exponents), used where the FP32 check of a
+// verified solve stalls: with lambda >> eps the staged values t_j and the
+// costs k |x_i - y_j|^2 are both large and their FP32 difference loses
+// ulp(|t_j|) per term.  Here each coordinate difference is an exact TwoSum,
+// the squared distance and its product with k = log2(e)/eps are float-float,
+// the running maximum is float-float; only the final small difference is
+// rounded for ex2.  Eight threads per output, each an online log-sum-exp over
+// every eighth input, merged by shuffles (16 outputs per CTA); the inputs are
+// staged in chunks of kFfpChunk through shared memory; then the same
+// float-float epilogue as points_combine.
+// ---------------------------------------------------------------------------
+constexpr int kFfpThreads = 128;
+constexpr int kFfpSplit = 8;                          // threads per output (input slices)
+constexpr int kFfpOut = kFfpThreads / kFfpSplit;      // outputs per CTA
+constexpr int kFfpChunk = 1024;
+constexpr ff kLog2eFFp{1.44269502162933349609375f, 1.925963033500011e-08f};
+
+struct FfpArgs {
+  const float* x;
+  const float* y;
+  int d, nout, nin, nbmax;
+  const float2* W;
+  const float2* lw;
+  float2 inv_eps;
+  const float* bmax;
+  float* zprev;
+};
+
+// Merges the running (max, sum) of another slice (float-float max).
+__device__ __forceinline__ void ffp_merge(float& mh, float& ml, float& sum, float mh2, float ml2, float s2) {
+  if (mh2 == -INFINITY) return;
+  if (mh == -INFINITY) {
+    mh = mh2;
+    ml = ml2;
+    sum = s2;
+    return;
+  }
+  const ff dq = ff_two_sum(mh2, -mh);
+  const float dm = dq.hi + (dq.lo + (ml2 - ml));
+  if (dm > 0.0f) {
+    sum = fmaf(sum, ex2_approx(-dm), s2);
+    mh = mh2;
+    ml = ml2;
+  } else {
+    sum = fmaf(s2, ex2_approx(dm), sum);
+  }
+}
+
+template <int D>
+__global__ void __launch_bounds__(kFfpThreads) points_ffp(FfpArgs a, Epilogue epi) {
+  __shared__ float4 st[kFfpChunk];  // {t.hi, t.lo, y0, y1}
+  __shared__ float sy2[D == 3 ? kFfpChunk : 1];
+  const int slice = threadIdx.x % kFfpSplit;
+  const int i = blockIdx.x * kFfpOut + threadIdx.x / kFfpSplit;
+  const bool owns = i < a.nout;
+  const float Lmax = all_max(a.bmax, a.nbmax);
+  const ff k2 = ff_mul(ffl(a.inv_eps), kLog2eFFp);
+  float xi[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+  for (int k = 0; k < D; ++k) xi[k] = owns ? a.x[(int64_t)i * D + k] : 0.0f;
+  float mh = -INFINITY, ml = 0.0f, sum = 0.0f;
+  if (Lmax != -INFINITY) {
+    for (int j0 = 0; j0 < a.nin; j0 += kFfpChunk) {
+      const int nj = min(kFfpChunk, a.nin - j0);
+      __syncthreads();  // the previous chunk is no longer read
+      for (int jj = threadIdx.x; jj < nj; jj += kFfpThreads) {
+        const int j = j0 + jj;
+        const ff L = load_L_pt(a.W, a.lw, j, a.inv_eps);
+        const ff t = (L.hi == -INFINITY) ? ff_ninf() : ff_mul(ff_add_f(L, -Lmax), kLog2eFFp);
+        const float y0 = a.y[(int64_t)j * D];
+        const float y1 = D > 1 ? a.y[(int64_t)j * D + 1] : 0.0f;
+        st[jj] = make_float4(t.hi, t.lo, y0, y1);
+        if (D == 3) sy2[jj] = a.y[(int64_t)j * D + 2];
+      }
+      __syncthreads();
+      for (int jj = slice; jj < nj; jj += kFfpSplit) {
+        const float4 tj = st[jj];
+        if (tj.x == -INFINITY) continue;
+        // q = |x_i - y_j|^2 as an unnormalised float-float pair
+        float qh = 0.0f, ql = 0.0f;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          const float yk = (k == 0) ? tj.z : (k == 1) ? tj.w : sy2[D == 3 ? jj : 0];
+          const ff dk = ff_two_sum(xi[k], -yk);
+          const float p = dk.hi * dk.hi;
+          const float pe = fmaf(dk.hi, dk.hi, -p) + 2.0f * dk.hi * dk.lo;
+          const ff sq = ff_two_sum(qh, p);
+          qh = sq.hi;
+          ql += sq.lo + pe;
+        }
+        const float ch = k2.hi * qh;
+        const float ce = fmaf(k2.hi, qh, -ch) + fmaf(k2.hi, ql, k2.lo * qh);
+        const ff sa = ff_two_sum(tj.x, -ch);
+        ffp_merge(mh, ml, sum, sa.hi, sa.lo + (tj.y - ce), 1.0f);
+      }
+    }
+  }
+  // the slices of an output are kFfpSplit consecutive lanes
+#pragma unroll
+  for (int o = 1; o < kFfpSplit; o <<= 1) {
+    const float mh2 = __shfl_xor_sync(0xffffffffu, mh, o);
+    const float ml2 = __shfl_xor_sync(0xffffffffu, ml, o);
+    const float s2 = __shfl_xor_sync(0xffffffffu, sum, o);
+    ffp_merge(mh, ml, sum, mh2, ml2, s2);
+  }
+  float num = 0.0f, den = 0.0f;
+  if (owns && slice == 0) {
+    ff z = ff_ninf();
+    if (mh != -INFINITY && sum > 0.0f) {
+      const ff m2 = ff_add_f(ff_fast_two_sum(mh, ml), lg2_approx(sum));  // log2 units, relative to Lmax
+      z = ff_add_f(ff_mul(m2, ln2_ff()), Lmax);
+    }
+    if (a.zprev) a.zprev[i] = z.hi;
+    apply_epilogue_ff(epi, 0, i, z, num, den);
+  }
+  if (epi.err) block_add2f<kFfpThreads>(num, den, epi.err);
+}
+
 }  // namespace
 
 // Chunking of the inputs: about 1024 inputs per chunk.
@@ -360,6 +479,33 @@ cudaError_t launch_points(const float* x, const float* y, int d, int nout, int n
   b.part = part;
   b.zprev = zprev;
   points_combine<<<(nout + 7) / 8, 256, 0, s>>>(b, epi);
+  prof_mark_end(PROF_ROWS, s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_points_ffp(const float* x, const float* y, int d, int nout, int nin, const double* W,
+                              const double* logw, double eps, float* bmax, float* zprev, const Epilogue& epi,
+                              cudaStream_t s) {
+  if (d < 1 || d > 3) return cudaErrorInvalidValue;
+  FfpArgs a;
+  a.x = x;
+  a.y = y;
+  a.d = d;
+  a.nout = nout;
+  a.nin = nin;
+  a.nbmax = (nin + kMaxBlk - 1) / kMaxBlk;
+  a.W = reinterpret_cast<const float2*>(W);
+  a.lw = reinterpret_cast<const float2*>(logw);
+  a.inv_eps = ff2(ff_make(1.0 / eps));
+  a.bmax = bmax;
+  a.zprev = zprev;
+  prof_mark_begin(PROF_ROWS, s);
+  count_launches(2);
+  points_blockmax<<<a.nbmax, 256, 0, s>>>(a.W, a.lw, nin, a.inv_eps, bmax);
+  const dim3 grid((nout + kFfpOut - 1) / kFfpOut);
+  if (d == 1) points_ffp<1><<<grid, kFfpThreads, 0, s>>>(a, epi);
+  else if (d == 2) points_ffp<2><<<grid, kFfpThreads, 0, s>>>(a, epi);
+  else points_ffp<3><<<grid, kFfpThreads, 0, s>>>(a, epi);
   prof_mark_end(PROF_ROWS, s);
   return cudaGetLastError();
 }

@@ -700,7 +700,10 @@ size_t rows_pf_scratch_bytes(int64_t nin) {
 
 cudaError_t launch_rows(int prec, const RowsGeom& g, int nrows, int nin, const double* W,
                         const double* logw, double eps, void* scratch_L, const Epilogue& epi,
-                        cudaStream_t s, float* zprev, int use_prev, void* part) {
+                        cudaStream_t s, float* zprev, int use_prev, void* part, int precise) {
+  if ((precise || precise_forced()) && prec == UOT_F32 && g.kind == UOT_GEOM_POINTS && g.d <= 3)
+    return launch_points_ffp((const float*)g.x, (const float*)g.y, g.d, nrows, nin, W, logw, eps,
+                             (float*)scratch_L, zprev, epi, s);
   // scratch_L: nin elements of the precision's type followed by one double
   // (Lmax); the FP64 dense prefilter adds nin floats, block maxima and a
   // counter (rows_pf_scratch_bytes).

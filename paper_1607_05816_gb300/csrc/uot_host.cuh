@@ -752,8 +752,9 @@ struct Gibbs {
   bool host_setup = true;
   // UOT_MIXED: once set, the passes run on the FP32 kernels (end of the BF16 phase)
   bool tc_off = false;
-  // FP32 grids: once set, the passes form their exponents in float-float
-  // (grid_pass_ffp), below the FP32 passes' rounding floor
+  // FP32 grids and point clouds: once set, the passes form their exponents
+  // in float-float (grid_pass_ffp, points_ffp), below the FP32 passes'
+  // rounding floor
   bool precise = false;
   void* Lscratch = nullptr;     // rows: shifted input line
   void* part = nullptr;         // FP32 point clouds: per-chunk partial sums
@@ -1026,7 +1027,7 @@ struct Gibbs {
       const int use_prev = (nbatch == 1 && zrow[dir] != nullptr && zeps[dir] == eps) ? 1 : 0;
       cudaError_t err = launch_rows(prec == UOT_F64 ? UOT_F64 : UOT_F32, rg, nrows, nin,
                                     W + (int64_t)b * nin, logw, eps, Lscratch, e, s,
-                                    nbatch == 1 ? zrow[dir] : nullptr, use_prev, part);
+                                    nbatch == 1 ? zrow[dir] : nullptr, use_prev, part, precise ? 1 : 0);
       if (err != cudaSuccess) return err;
     }
     if (zrow[dir] && nbatch == 1) zeps[dir] = eps;

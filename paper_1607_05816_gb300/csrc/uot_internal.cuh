@@ -484,6 +484,7 @@ cudaError_t launch_grid_pass(int prec, const double* in, const double* logw, int
 // grid_pass_ffp), as every FP32 pass runs while grid_force_precise(1) is set;
 // returns the previous setting
 int grid_force_precise(int on);
+int precise_forced();  // the current setting (also read by the point-cloud path)
 
 // Tensor-core convolutions of the warm-start network (k_conv_tc.cu); BF16
 // tensors are passed as void pointers.
@@ -624,10 +625,17 @@ struct RowsGeom {
 };
 // FP32 point clouds with d <= 3 and a `part` buffer use the chunked kernels of
 // k_points.cu (zprev: previous results used as log-sum-exp shifts).
+// precise = 1 (FP32 point clouds, d <= 3): the pass with float-float
+// exponents (launch_points_ffp) instead of the chunked kernels.
 cudaError_t launch_rows(int prec, const RowsGeom& g, int nrows, int nin, const double* W,
                         const double* logw, double eps, void* scratch_L, const Epilogue& epi,
                         cudaStream_t s, float* zprev = nullptr, int use_prev = 0,
-                        void* part = nullptr);
+                        void* part = nullptr, int precise = 0);
+// FP32 point clouds (d <= 3), exponents in float-float (k_points.cu); bmax
+// holds ceil(nin / 1024) floats.
+cudaError_t launch_points_ffp(const float* x, const float* y, int d, int nout, int nin, const double* W,
+                              const double* logw, double eps, float* bmax, float* zprev, const Epilogue& epi,
+                              cudaStream_t s);
 // Scratch of launch_rows for FP64 dense rows with the FP32 prefilter; its
 // first 4 bytes hold a counter that must be zero before the first launch.
 size_t rows_pf_scratch_bytes(int64_t nin);

@@ -457,16 +457,19 @@ uot_status solve_impl(const uot_geom* g, int batch, const void* p, const void* d
         best_it = it;
         return cudaSuccess;
       }
-      // the FP32 check's rounding floor: on grids the passes with float-float
-      // exponents take over (their floor is far lower), then, if those stall
-      // too, FP64 iterations
+      // the FP32 check's rounding floor: on grids and point clouds (d <= 3) the
+      // passes with float-float exponents take over (their floor is far
+      // lower), then, if those stall too, FP64 iterations
       if (stalled()) {
-        if (g->kind == UOT_GEOM_GRID && !G.precise) {
+        if ((g->kind == UOT_GEOM_GRID || (g->kind == UOT_GEOM_POINTS && g->d <= 3)) && !G.precise) {
           G.precise = true;
           precise_from = total;
           mixed_handover = true;  // recapture the graph block with the new passes
           first_err = NAN;
           best_err = INFINITY;
+          // the lowered threshold compensated the plain passes' optimistic check;
+          // the precise passes' check is close to the FP64 value
+          tol_int = o->tol;
         } else {
           polish = stop = true;
         }

@@ -125,3 +125,45 @@ def test_stalled_fp32_check_finishes_with_precise_passes():
     v = O.marginal_violation(O.Geometry("grid", xs=ax, ys=ax), rdx, rdx, rp, rq, O.KL(lam), O.KL(lam), eps,
                              to_np(Ug).reshape(64, 64), to_np(Vg).reshape(64, 64))
     assert v <= 1e-6 and abs(v - info["marg_err"]) <= 1e-6 * v + 1e-15, (v, info)
+
+
+def test_precise_points_operator_and_solve_match_oracle():
+    """Point clouds (d = 3): the precise pass against the oracle's operator and
+    its iterates with every pass precise, to 1e-6."""
+    from test_gpu_parity import points_problem
+    og, lg, dx, dy, p, q = points_problem(1333, 1250, 3, 66)
+    g = synth.rng(67)
+    W = rounded(U.F32, g.normal(size=1250) * 0.05)
+    W[7::19] = -np.inf
+    w = rounded(U.F32, dy)
+    want = O.apply_K_log(round_geom(og, U.F32), W, np.log(w), 0.01)
+    with precise():
+        got = U.gibbs_log(lg(U.F32), T(W, U.F32), T(w, U.F32), 0.01, False, U.F32)
+    assert rel_err(to_np(got), want) <= 1e-6
+    dxr, dyr, pr, qr = rounded(U.F32, dx, dy, p, q)
+    with precise():
+        Ug, Vg, _ = U.solve(lg(U.F32), *[T(a, U.F32).ravel() for a in (pr, dxr, qr, dyr)], U.KL(0.3), U.KL(0.3),
+                            0.01, precision=U.F32, max_iter=15, eps_start=0.1, eps_stages=2, iters_per_stage=4)
+    r = O.solve_log(round_geom(og, U.F32), dxr, dyr, pr, qr, O.KL(0.3), O.KL(0.3), 0.01, max_iter=15,
+                    eps_start=0.1, stages=2, iters_per_stage=4)
+    assert rel_err(to_np(Ug), r["U"]) <= 1e-6
+    assert rel_err(to_np(Vg), r["V"]) <= 1e-6
+
+
+def test_verified_points_solve_finishes_in_fp32():
+    """A 3-D colour-cloud problem (KL 0.1, eps 1e-3) solved to 1e-6 with the stop
+    confirmed in FP64: no FP64 iterations are needed (the precise passes take
+    over where the FP32 check stalls), and the oracle confirms the returned
+    potentials."""
+    d = synth.problem_points(3000, 3000, 3, seed=68)
+    f = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device="cuda")
+    geo = U.Geometry.points(f(d["x"]), f(d["y"]))
+    Ug, Vg, info = U.solve(geo, *[f(d[k]).ravel() for k in ("p", "dx", "q", "dy")], U.KL(0.1), U.KL(0.1), 1e-3,
+                           precision=U.F32, max_iter=20000, tol=1e-6, check_every=20, eps_start=0.1,
+                           eps_stages=10, iters_per_stage=100, launch_mode=2, out_f64=True, verify=True)
+    print(info)
+    assert info["status"] == "UOT_OK" and info["polish_iters"] == 0, info
+    og = O.Geometry("points", x=rounded(U.F32, d["x"]), y=rounded(U.F32, d["y"]))
+    rdx, rdy, rp, rq = rounded(U.F32, d["dx"], d["dy"], d["p"], d["q"])
+    v = O.marginal_violation(og, rdx, rdy, rp, rq, O.KL(0.1), O.KL(0.1), 1e-3, to_np(Ug), to_np(Vg))
+    assert v <= 1e-6 and abs(v - info["marg_err"]) <= 1e-6 * v + 1e-15, (v, info)
