@@ -420,6 +420,18 @@ uot_status solve_impl(const uot_geom* g, int batch, const void* p, const void* d
       }
       return it - best_it >= W;
     };
+    // FP32 passes with float-float exponents exist for grids and point clouds of d <= 3
+    const bool precise_ok = prec != UOT_F64 && (g->kind == UOT_GEOM_GRID || (g->kind == UOT_GEOM_POINTS && g->d <= 3));
+    auto switch_precise = [&]() {
+      G.precise = true;
+      precise_from = total;
+      mixed_handover = true;  // recapture the graph block with the new passes
+      first_err = NAN;
+      best_err = INFINITY;
+      // the lowered threshold compensated the plain passes' optimistic check;
+      // the precise passes' check is close to the FP64 value
+      tol_int = o->tol;
+    };
     auto decide = [&](bool& stop) -> cudaError_t {
       stop = false;
       err32 = err;
@@ -451,6 +463,13 @@ uot_status solve_impl(const uot_geom* g, int batch, const void* p, const void* d
           converged = stop = true;
           return cudaSuccess;
         }
+        // An FP32 check far below the FP64 value measures the plain passes'
+        // own rounding floor, not the state: where the precise passes exist,
+        // switch now instead of chasing a lower threshold.
+        if (precise_ok && !G.precise && err < 0.2 * err64) {
+          switch_precise();
+          return cudaSuccess;
+        }
         // aim the FP32 check proportionally lower
         tol_int = err * std::min(0.7, std::max(0.05, o->tol / err64));
         best_err = err;
@@ -461,18 +480,10 @@ uot_status solve_impl(const uot_geom* g, int batch, const void* p, const void* d
       // passes with float-float exponents take over (their floor is far
       // lower), then, if those stall too, FP64 iterations
       if (stalled()) {
-        if ((g->kind == UOT_GEOM_GRID || (g->kind == UOT_GEOM_POINTS && g->d <= 3)) && !G.precise) {
-          G.precise = true;
-          precise_from = total;
-          mixed_handover = true;  // recapture the graph block with the new passes
-          first_err = NAN;
-          best_err = INFINITY;
-          // the lowered threshold compensated the plain passes' optimistic check;
-          // the precise passes' check is close to the FP64 value
-          tol_int = o->tol;
-        } else {
+        if (precise_ok && !G.precise)
+          switch_precise();
+        else
           polish = stop = true;
-        }
       }
       return cudaSuccess;
     };
