@@ -760,7 +760,8 @@ cudaError_t launch_rows(int prec, const RowsGeom& g, int nrows, int nin, const d
       prof_mark_begin(PROF_ROWS, s);
       const float2* lff = Lff;
       if (rows_smem) {
-        if (rows_bytes > 48 * 1024) {  // opt-in, for the current device
+        {  // opt-in for the current device: rows and line plus the static lists exceed 48 KB from
+           // about 1920 columns on
           cudaError_t e = cudaFuncSetAttribute(rows_lse_f64_pf<WPR, RPC, true>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
           if (e != cudaSuccess) return e;
@@ -776,6 +777,10 @@ cudaError_t launch_rows(int prec, const RowsGeom& g, int nrows, int nin, const d
       } else {
         const size_t smem = nin <= kPfStageMax ? (size_t)nin * 4 : 0;
         if (smem > 48 * 1024) return cudaErrorInvalidValue;
+        // the line (up to 48 KB) and the static lists exceed the default 48 KB per block
+        cudaError_t ea = cudaFuncSetAttribute(rows_lse_f64_pf<WPR, RPC, false>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, kPfStageMax * 4);
+        if (ea != cudaSuccess) return ea;
         const float* c32 = g.C32;
         const double* l64 = L64;
         const float* lt32 = Lt32;
