@@ -34,6 +34,14 @@
  *    uot_objective) synchronise that stream before returning.
  *  - Temporary device memory is taken from the CUDA stream-ordered allocator
  *    (cudaMallocAsync) and released before return.
+ *  - Calls may run at the same time from several host threads on different
+ *    streams (a serving loop solving independent problems side by side): a
+ *    call keeps its state in its own scratch and on its own stream, the last
+ *    error is per thread, CUDA-graph capture uses the thread-local mode, and
+ *    per-kernel launch limits are only ever raised.  The results do not depend
+ *    on what else runs.  Exceptions: uot_gibbs_log_noalloc (one shared
+ *    array), the profiling pair below, and the first use of a grid shape by
+ *    the tile tuner (its timings, not its results, see the other streams).
  *  - Errors are returned as uot_status, never thrown.  Arguments are checked on
  *    the host before any launch; UOT_EINVAL leaves outputs untouched.
  *  - There is no CPU fallback: if no sm_103a device is present every entry

@@ -554,7 +554,7 @@ template <int D, int NW>
 cudaError_t launch_variant(const BatchArgs& a, int grid, cudaStream_t s) {
   const int lmax = std::max(a.nmax, a.mmax);
   const size_t smem = smem_bytes<D, NW>(lmax);
-  cudaError_t e = cudaFuncSetAttribute(batch_solve<D, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = smem_at_least(batch_solve<D, NW>, smem);
   if (e != cudaSuccess) return e;
   batch_solve<D, NW><<<grid, NW * 32, smem, s>>>(a);
   return cudaGetLastError();
@@ -564,7 +564,7 @@ template <int D, int NW>
 int ctas_variant(int nmax, int mmax) {
   const size_t smem = smem_bytes<D, NW>(std::max(nmax, mmax));
   int nb = 0;
-  if (cudaFuncSetAttribute(batch_solve<D, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+  if (smem_at_least(batch_solve<D, NW>, smem) !=
       cudaSuccess) {
     (void)cudaGetLastError();
     return 0;

@@ -794,23 +794,23 @@ cudaError_t launch_conv_tc(const void* x, const void* wk, int bn, const ConvTcLa
   count_launches(1);
   if (n256) {
     const size_t sm256 = 1024 + (size_t)kConvNStages * (kTileBytesA + kTileBytesPix);
-    if ((e = cudaFuncSetAttribute(conv_tc_n256, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm256))) return e;
+    if ((e = smem_at_least(conv_tc_n256, sm256))) return e;
     conv_tc_n256<<<grid, 192, sm256, s>>>(ma, mb, a);
     return cudaGetLastError();
   }
   switch (bn) {
     case 16:
-      if ((e = cudaFuncSetAttribute(conv_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+      if ((e = smem_at_least(conv_tc<16>, smem)))
         return e;
       conv_tc<16><<<grid, 192, smem, s>>>(ma, mb, a);
       break;
     case 64:
-      if ((e = cudaFuncSetAttribute(conv_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+      if ((e = smem_at_least(conv_tc<64>, smem)))
         return e;
       conv_tc<64><<<grid, 192, smem, s>>>(ma, mb, a);
       break;
     default:
-      if ((e = cudaFuncSetAttribute(conv_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+      if ((e = smem_at_least(conv_tc<128>, smem)))
         return e;
       conv_tc<128><<<grid, 192, smem, s>>>(ma, mb, a);
   }
@@ -844,10 +844,10 @@ cudaError_t launch_wgrad_tc(const void* dyT, int cout_rows, const void* xT, int 
   cudaError_t e;
   count_launches(2);
   if (cin_pad == 64) {
-    if ((e = cudaFuncSetAttribute(wgrad_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
+    if ((e = smem_at_least(wgrad_tc<64>, smem))) return e;
     wgrad_tc<64><<<grid, 128, smem, s>>>(ma, mb, a);
   } else {
-    if ((e = cudaFuncSetAttribute(wgrad_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
+    if ((e = smem_at_least(wgrad_tc<128>, smem))) return e;
     wgrad_tc<128><<<grid, 128, smem, s>>>(ma, mb, a);
   }
   if ((e = cudaGetLastError())) return e;

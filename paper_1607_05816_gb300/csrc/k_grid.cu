@@ -504,7 +504,7 @@ int grid_solve_persistent_ctas(int nin_max) {
   int nb = 0, dev = 0, sms = 0;
   const size_t smem = (size_t)nin_max * sizeof(float4);
   if (smem > 48 * 1024 &&
-      cudaFuncSetAttribute(grid_solve_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      smem_at_least(grid_solve_persistent, smem) != cudaSuccess)
     return 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, grid_solve_persistent, kNW * 32, smem) != cudaSuccess) return 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
@@ -548,7 +548,7 @@ cudaError_t launch_grid_solve_persistent(const PersistLaunch& L, int grid, cudaS
   int nin_max = 1;
   for (int k = 0; k < L.ndim; ++k) nin_max = std::max(nin_max, std::max(L.shape_x[k], L.shape_y[k]));
   const size_t smem = (size_t)nin_max * sizeof(float4);
-  cudaError_t e = cudaFuncSetAttribute(grid_solve_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = smem_at_least(grid_solve_persistent, smem);
   if (e != cudaSuccess) return e;
   void* args[] = {&P};
   count_launches(1);
@@ -984,8 +984,7 @@ cudaError_t launch_f32_tile(const PassArgs& a, const Epilogue& epi, int nbatch, 
   if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidConfiguration;
   const size_t smem = (size_t)a.nin * sizeof(float4);
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(grid_pass_f32<NW, OPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = smem_at_least(grid_pass_f32<NW, OPL>, smem);
     if (e != cudaSuccess) return e;
   }
   cudaLaunchConfig_t cfg;
@@ -1297,7 +1296,7 @@ cudaError_t launch_ffp_shape(const PassArgs& a, const Epilogue& epi, int nbatch,
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
   if (smem > 48 * 1024) {
     cudaError_t e =
-        cudaFuncSetAttribute(grid_pass_ffp<R, WARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        smem_at_least(grid_pass_ffp<R, WARPS>, smem);
     if (e != cudaSuccess) return e;
   }
   grid_pass_ffp<R, WARPS><<<grid, WARPS * 32, smem, s>>>(a, epi);
@@ -1370,8 +1369,7 @@ cudaError_t launch_grid_pass(int prec, const double* in, const double* logw, int
     if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidConfiguration;
     const size_t smem = (size_t)WARPS * nin * sizeof(double2);
     if (smem > 48 * 1024) {
-      cudaError_t e = cudaFuncSetAttribute(grid_pass_f64<R, WARPS>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaError_t e = smem_at_least(grid_pass_f64<R, WARPS>, smem);
       if (e != cudaSuccess) return e;
     }
     grid_pass_f64<R, WARPS><<<grid, WARPS * 32, smem, s>>>(

@@ -278,8 +278,7 @@ cudaError_t launch_blk(const BlkArgs& ba, const Epilogue& epi, int nbatch, cudaS
   dim3 grid((a.nout + kBI - 1) / kBI, (a.nlines + kLW - 1) / kLW, nbatch);
   if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidConfiguration;
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(grid_pass_blk<BJ, JS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = smem_at_least(grid_pass_blk<BJ, JS>, smem);
     if (e != cudaSuccess) return e;
   }
   cudaLaunchConfig_t cfg;

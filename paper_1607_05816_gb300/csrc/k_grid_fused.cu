@@ -270,7 +270,7 @@ size_t grid_fused2_smem(int nin1, int nout1) {
 cudaError_t launch_grid_fused2(const FusedArgs& a, cudaStream_t s) {
   const size_t smem = grid_fused2_smem(a.nin1, a.nout1);
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(grid_fused2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = smem_at_least(grid_fused2, smem);
     if (e != cudaSuccess) return e;
   }
   cudaLaunchConfig_t cfg;

@@ -261,7 +261,7 @@ cudaError_t launch_grid_pass_tc(const double* in, const double* logw, int in_is_
                                 double* zero_acc) {
   const size_t smem = grid_pass_tc_smem(nin);
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(grid_pass_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = smem_at_least(grid_pass_tc, smem);
   if (e != cudaSuccess) return e;
   TcArgs a;
   a.in = reinterpret_cast<const float2*>(in);

@@ -456,7 +456,7 @@ cudaError_t launch_points(const float* x, const float* y, int d, int nout, int n
   const size_t smem = (size_t)2 * chunk * sizeof(float4);
   dim3 grid((nout + kOutBlk - 1) / kOutBlk, nchunks);
   auto run = [&](auto kern) -> cudaError_t {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = smem_at_least(kern, smem);
     if (e != cudaSuccess) return e;
     kern<<<grid, kNW * 32, smem, s>>>(a);
     return cudaGetLastError();

@@ -762,8 +762,7 @@ cudaError_t launch_rows(int prec, const RowsGeom& g, int nrows, int nin, const d
       if (rows_smem) {
         {  // opt-in for the current device: rows and line plus the static lists exceed 48 KB from
            // about 1920 columns on
-          cudaError_t e = cudaFuncSetAttribute(rows_lse_f64_pf<WPR, RPC, true>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+          cudaError_t e = smem_at_least(rows_lse_f64_pf<WPR, RPC, true>, 96 * 1024);
           if (e != cudaSuccess) return e;
         }
         const float* c32 = g.C32;
@@ -778,8 +777,7 @@ cudaError_t launch_rows(int prec, const RowsGeom& g, int nrows, int nin, const d
         const size_t smem = nin <= kPfStageMax ? (size_t)nin * 4 : 0;
         if (smem > 48 * 1024) return cudaErrorInvalidValue;
         // the line (up to 48 KB) and the static lists exceed the default 48 KB per block
-        cudaError_t ea = cudaFuncSetAttribute(rows_lse_f64_pf<WPR, RPC, false>,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize, kPfStageMax * 4);
+        cudaError_t ea = smem_at_least(rows_lse_f64_pf<WPR, RPC, false>, kPfStageMax * 4);
         if (ea != cudaSuccess) return ea;
         const float* c32 = g.C32;
         const double* l64 = L64;
@@ -825,7 +823,7 @@ cudaError_t launch_alg1_cluster(const double* K, const double* KT, int n, int m,
       (void)cudaGetLastError();
       continue;
     }
-    if (cudaFuncSetAttribute(alg1_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+    if (smem_at_least(alg1_cluster, smem) != cudaSuccess) {
       (void)cudaGetLastError();
       continue;
     }

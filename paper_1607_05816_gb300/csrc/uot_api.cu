@@ -7,6 +7,10 @@
 // is in uot_host.cuh.
 //
 // Every kernel on the path is this library's own; no CPU fallback exists.
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "uot_host.cuh"
 
 namespace uot {
@@ -114,6 +118,25 @@ uot_status bin_grid(int d, const int* shape, BinGrid& b, int64_t& nb) {
 }  // namespace
 
 void count_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+namespace {
+std::mutex g_smem_mu;
+std::map<std::pair<int, const void*>, size_t> g_smem_limit;  // (device, kernel) -> limit set
+}  // namespace
+
+cudaError_t smem_limit_at_least(const void* kernel, size_t bytes) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(g_smem_mu);
+  size_t& cur = g_smem_limit[{dev, kernel}];
+  if (cur == 0) cur = 48 * 1024;  // the default limit, which needs no attribute
+  if (bytes <= cur) return cudaSuccess;
+  if ((e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)) != cudaSuccess)
+    return e;
+  cur = bytes;
+  return cudaSuccess;
+}
 
 void prof_mark_begin(int family, cudaStream_t s) {
   if (!g_prof.on) return;

@@ -172,8 +172,7 @@ static uot_status barycenter_impl(const uot_geom* g, int Kmeas, const double* al
       const bool pwl = bary_kind == UOT_BARY_TV || bary_kind == UOT_BARY_RG;
       cfg.dynamicSmemBytes = pwl ? (size_t)Kmeas * (kBJ + 1) * sizeof(float) : 0;
       if (cfg.dynamicSmemBytes > 48 * 1024) {
-        e = cudaFuncSetAttribute(k_bary_update_ff, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)cfg.dynamicSmemBytes);
+        e = smem_at_least(k_bary_update_ff, cfg.dynamicSmemBytes);
         if (e != cudaSuccess) return e;
       }
       const double lam_kl = (bary_kind == UOT_BARY_KL) ? lambda : 1.0;

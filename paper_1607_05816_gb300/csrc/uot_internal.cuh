@@ -447,6 +447,18 @@ __device__ inline void block_add2(double a, double b, double* acc) {
 
 enum ProfFamily { PROF_GRID_PASS = 0, PROF_ROWS = 1, PROF_GRID_BLK = 2, PROF_NFAM = 3 };
 void count_launches(int k);
+
+// Raises, never lowers, a kernel's limit on dynamic shared memory (the
+// cudaFuncAttributeMaxDynamicSharedMemorySize attribute) on the current device
+// to at least `bytes`.  The attribute is process-wide per kernel: setting it to
+// each call's own size would let a concurrent call on another stream or host
+// thread lower it between another call's set and launch, which then fails as
+// an invalid launch.  Thread-safe; a no-op once the limit is high enough.
+cudaError_t smem_limit_at_least(const void* kernel, size_t bytes);
+template <typename K>
+cudaError_t smem_at_least(K* kernel, size_t bytes) {
+  return smem_limit_at_least(reinterpret_cast<const void*>(kernel), bytes);
+}
 void prof_mark_begin(int family, cudaStream_t s);
 void prof_mark_end(int family, cudaStream_t s);
 

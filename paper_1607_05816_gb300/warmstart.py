@@ -16,6 +16,8 @@ from __future__ import annotations
 
 import math
 
+import threading
+
 import numpy as np
 import torch
 
@@ -190,7 +192,9 @@ class WarmStartNetTC:
         self.loss_dev = torch.zeros(1, dtype=torch.float64, device=device)
         self.err = torch.zeros(1, dtype=torch.int32, device=device)
         self._refresh_bf16()
-        self._ws = {}
+        # workspace tensors per host thread: forward passes driven from several
+        # threads (each on its own stream) must not share activations
+        self._tls = threading.local()
 
     # geometry of each layer's GEMMs
     def _pads(self, li):
@@ -218,10 +222,13 @@ class WarmStartNetTC:
         return sum(t.numel() for pr in self.params for t in pr)
 
     def _buf(self, key, shape, dtype):
-        t = self._ws.get(key)
+        ws = getattr(self._tls, "ws", None)
+        if ws is None:
+            ws = self._tls.ws = {}
+        t = ws.get(key)
         if t is None or t.shape != torch.Size(shape) or t.dtype != dtype:
             t = torch.empty(shape, dtype=dtype, device=self.params[0][0].device)
-            self._ws[key] = t
+            ws[key] = t
         return t
 
     def forward(self, feats, N, H, W, keep=True):
@@ -336,8 +343,48 @@ def _ev_ms(fn):
     return e0.elapsed_time(e1), out
 
 
+def run_on_streams(jobs, nstreams):
+    """Runs the callables `jobs` (each one complete solve that synchronises
+    with the host at its checks) from `nstreams` host threads, each with its own
+    CUDA stream, job k on thread k % nstreams.  The library keeps no state
+    shared between calls on different streams (stream-ordered scratch,
+    thread-local capture and errors), so latency-bound solves overlap on the
+    GPU.  Returns (milliseconds from the first launch to the last job's end,
+    measured with CUDA events on the caller's stream, the jobs' results)."""
+    out = [None] * len(jobs)
+    err = []
+    main = torch.cuda.current_stream()
+    streams = [torch.cuda.Stream() for _ in range(max(1, nstreams))]
+    e0 = torch.cuda.Event(enable_timing=True)
+    e0.record(main)
+    for st in streams:
+        st.wait_event(e0)
+
+    def worker(w):
+        try:
+            torch.cuda.set_device(main.device)
+            with torch.cuda.stream(streams[w]):
+                for k in range(w, len(jobs), len(streams)):
+                    out[k] = jobs[k]()
+        except Exception as ex:  # re-raised on the caller's thread
+            err.append(ex)
+    threads = [threading.Thread(target=worker, args=(w,)) for w in range(len(streams))]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    if err:
+        raise err[0]
+    for st in streams:
+        main.wait_stream(st)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e1.record(main)
+    e1.synchronize()
+    return e0.elapsed_time(e1), out
+
+
 def evaluate_tc(net, inst, H, W, *, group, tol=1e-6, plain_sample=16, max_iter=20000, check_every=10,
-                cold_plain=True, device="cuda"):
+                cold_plain=True, streams=0, device="cuda"):
     """Time to a `tol` marginal violation (confirmed in FP64, FP64 potentials
     returned) on held-out instances whose consecutive blocks of `group` share
     (eps, lambda):
@@ -352,6 +399,11 @@ def evaluate_tc(net, inst, H, W, *, group, tol=1e-6, plain_sample=16, max_iter=2
                  predicted potentials at the final eps (no eps-scaling), with
                  the translation step; warm_ms includes the inference, whose
                  own time (timed once more on its own) is warm_infer_ms.
+    With streams > 0 the translated cold form and the warm form are run once
+    more with every group in flight at once (run_on_streams): batched_tr_streams_ms,
+    warm_streams_ms, and the number of groups whose iteration count differs from
+    the one-at-a-time run (streams_mismatch; the kernels do not depend on what
+    else runs, so it is 0).
     Returns a dict of totals and the per-group iteration counts (a batch
     stops when its last problem does)."""
     xs = [torch.as_tensor((np.arange(n) + 0.5) / n, dtype=torch.float32, device=device) for n in (H, W)]
@@ -415,4 +467,28 @@ def evaluate_tc(net, inst, H, W, *, group, tol=1e-6, plain_sample=16, max_iter=2
                    warm_fp64_checks=info["verifications"])
         res["groups"].append(grp)
         res.setdefault("_last_warm", (s, Uw, Vw))
+    if streams > 0:
+        starts = list(range(0, n, group))
+
+        def cold_job(s):
+            sl = slice(s, min(n, s + group))
+            e, lam = float(inst["eps"][s]), float(inst["lam"][s])
+            return uot.solve_many(geo, P[sl].reshape(-1, H * W).contiguous(), dx, Q[sl].reshape(-1, H * W).contiguous(),
+                                  dx, uot.KL(lam), uot.KL(lam), e, translate=True, **common, **sched(e))
+
+        def warm_job(s):
+            sl = slice(s, min(n, s + group))
+            e, lam = float(inst["eps"][s]), float(inst["lam"][s])
+            U0, V0 = net.predict(P[sl].contiguous(), Q[sl].contiguous(), inst["eps"][sl], inst["lam"][sl])
+            return uot.solve_many(geo, P[sl].reshape(-1, H * W).contiguous(), dx, Q[sl].reshape(-1, H * W).contiguous(),
+                                  dx, uot.KL(lam), uot.KL(lam), e, U0=U0, V0=V0, translate=True, **common)
+        mism = 0
+        for key, job, iters_key in (("batched_tr_streams", cold_job, "batched_tr_iters"),
+                                    ("warm_streams", warm_job, "warm_iters")):
+            ms, outs = run_on_streams([(lambda s=s: job(s)) for s in starts], streams)
+            res[key + "_ms"] = ms
+            res["worst_err_" + key] = max(o[2]["marg_err"] for o in outs)
+            mism += sum(o[2]["total_iters"] != it for o, it in zip(outs, res[iters_key]))
+        res["streams"] = streams
+        res["streams_mismatch"] = mism
     return res
