@@ -298,6 +298,19 @@ uot_status uot_probe_pipes(double* out, void* stream);
 int uot_force_precise_passes(int on);
 
 /*
+ * uot_fuse_short_passes(on): FP32 separable grids run two consecutive passes
+ * whose four axis sizes are all at most 64 (the 32-point axes of a 64x32x32
+ * colour grid, the axes of 64x64 images) as one launch per plane of the two
+ * axes, the intermediate kept in shared memory (1), or as two launches (0, the
+ * default: on the 64x32x32 colour transfer the fused form takes 61 ms against
+ * 45 ms, since one CTA per plane leaves most SMs idle).  The results are the same bit for bit as two passes on the
+ * short-line kernel; a tile forced by uot_force_grid_tile other than that
+ * kernel turns the fusion off.  The setting is process-wide.  Returns the
+ * previous setting.
+ */
+int uot_fuse_short_passes(int on);
+
+/*
  * uot_selftest_bounded_wait -- failure-detection self-test (instrumentation).
  * Runs the bounded device-side wait that guards every wait of a kernel on
  * other CTAs (the persistent solve's grid barrier) on a flag that nothing

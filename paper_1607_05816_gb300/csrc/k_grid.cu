@@ -803,6 +803,84 @@ __global__ void __launch_bounds__(WARPS * 32) grid_pass_ffp(PassArgs a, Epilogue
 // ---------------------------------------------------------------------------
 constexpr int kShortWarps = 8, kShortMax = 64;
 
+// The log-sum-exp of one short line (nin <= 64) for OPL outputs per lane: v0,
+// v1 the line values at lane and lane + 32 (float-float), y0, y1 their
+// coordinates, xq the lane's output coordinates, zp its speculative shifts
+// (natural units; used when spec).  The line is staged, shifted by its maximum
+// mx, in the warp's sl[64]; the shifts are tried first and an exact max sweep
+// redoes the line when any owned sum leaves [2^-90, 2^100].  Returns z = log
+// sum (float-float) per output, -inf for an empty line.  Warp-collective.
+template <int OPL>
+__device__ __forceinline__ void short_line_lse(ff v0, ff v1, float y0, float y1, int nin, const float* xq,
+                                               const float* zp, bool spec, const bool* owns, float k2,
+                                               float2* sl, ff* z) {
+  const int lane = threadIdx.x & 31;
+  const float mx = warp_maxf(fmaxf(v0.hi, v1.hi));
+#pragma unroll
+  for (int q = 0; q < OPL; ++q) z[q] = ff_ninf();
+  if (mx == -INFINITY) return;  // b = 0 on the whole line: every sum is empty
+  auto stage = [&](ff v) { return (v.hi == -INFINITY) ? -INFINITY : ((v.hi - mx) + v.lo) * kLog2e; };
+  __syncwarp();
+  sl[lane] = make_float2(stage(v0), y0);
+  if (lane + 32 < kShortMax) sl[lane + 32] = make_float2(stage(v1), y1);
+  __syncwarp();
+  const float nk2 = -k2;
+  float m[OPL], S[OPL];
+  bool exact = !spec;
+  for (int attempt = 0; attempt < 2; ++attempt) {
+#pragma unroll
+    for (int q = 0; q < OPL; ++q) {
+      m[q] = (zp[q] == -INFINITY) ? 0.0f : (zp[q] - mx) * kLog2e;
+      S[q] = 0.0f;
+    }
+    if (exact) {
+#pragma unroll
+      for (int q = 0; q < OPL; ++q) m[q] = -INFINITY;
+      for (int j = 0; j < nin; ++j) {
+        const float2 v = sl[j];
+#pragma unroll
+        for (int q = 0; q < OPL; ++q) {
+          const float d = xq[q] - v.y;
+          m[q] = fmaxf(m[q], fmaf(nk2, d * d, v.x));
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < OPL; ++q)
+        if (m[q] == -INFINITY) m[q] = 0.0f;
+    }
+    for (int j = 0; j < nin; ++j) {
+      const float2 v = sl[j];
+#pragma unroll
+      for (int q = 0; q < OPL; ++q) {
+        const float d = xq[q] - v.y;
+        S[q] += ex2_approx(fmaf(nk2, d * d, v.x - m[q]));
+      }
+    }
+    bool bad = false;
+#pragma unroll
+    for (int q = 0; q < OPL; ++q)
+      if (owns[q] && !exact) bad = bad || !(S[q] >= 0x1p-90f && S[q] <= 0x1p100f);
+    if (__any_sync(0xffffffffu, bad) && !exact) {
+      exact = true;
+      continue;  // warp-uniform: redo with exact maxima
+    }
+    break;
+  }
+#pragma unroll
+  for (int q = 0; q < OPL; ++q) {
+    if (S[q] > 0.0f) {
+      // z = mx + ln2 m + ln2 log2(S), the first product kept exact in float-float
+      const ff ln2 = ln2_ff();
+      z[q] = ff_add_f(ff_add_f(ff_mul_f(ln2, m[q]), mx), kLn2 * lg2_approx(S[q]));
+    }
+  }
+}
+
+// Short lines (nin, nout <= 64, e.g. the 32- and 64-point axes of a 3-D
+// colour grid): one warp per (line, batch entry), OPL = 1 or 2 outputs per
+// lane, the line staged in the warp's shared memory, no combine across warps.
+// Same arithmetic as grid_pass_f32 (speculative shifts with the exact
+// fallback, float-float result, the same epilogue).
 template <int OPL>
 __global__ void __launch_bounds__(kShortWarps * 32) grid_pass_f32_short(PassArgs a, Epilogue epi) {
   __shared__ float2 sl[kShortWarps][kShortMax];  // {t, y} of the warp's line
@@ -841,81 +919,16 @@ __global__ void __launch_bounds__(kShortWarps * 32) grid_pass_f32_short(PassArgs
   if (live) {
     const ff v0 = (lane < nin) ? load_L_ff(a, in, base + lane) : ff_ninf();
     const ff v1 = (lane + 32 < nin) ? load_L_ff(a, in, base + lane + 32) : ff_ninf();
-    const float mx = warp_maxf(fmaxf(v0.hi, v1.hi));
-    if (mx == -INFINITY) {
-      // b = 0 on the whole line: every sum is empty
+    ff z[OPL];
+    short_line_lse<OPL>(v0, v1, y0, y1, nin, xq, zp, spec, owns, a.k2, sl[warp], z);
 #pragma unroll
-      for (int q = 0; q < OPL; ++q) {
-        if (!owns[q]) continue;
-        if (zprev) zprev[my_pt[q]] = -INFINITY;
-        float n1, d1;
-        epilogue_apply(epi, bz, my_pt[q], ff_ninf(), pre[q], n1, d1);
-        num += n1;
-        den += d1;
-      }
-    } else {
-      auto stage = [&](ff v) { return (v.hi == -INFINITY) ? -INFINITY : ((v.hi - mx) + v.lo) * kLog2e; };
-      sl[warp][lane] = make_float2(stage(v0), y0);
-      if (lane + 32 < kShortMax) sl[warp][lane + 32] = make_float2(stage(v1), y1);
-      __syncwarp();
-      const float2* L = sl[warp];
-      const float nk2 = -a.k2;
-      float m[OPL], S[OPL];
-      bool exact = !spec;
-      for (int attempt = 0; attempt < 2; ++attempt) {
-#pragma unroll
-        for (int q = 0; q < OPL; ++q) {
-          m[q] = (zp[q] == -INFINITY) ? 0.0f : (zp[q] - mx) * kLog2e;
-          S[q] = 0.0f;
-        }
-        if (exact) {
-#pragma unroll
-          for (int q = 0; q < OPL; ++q) m[q] = -INFINITY;
-          for (int j = 0; j < nin; ++j) {
-            const float2 v = L[j];
-#pragma unroll
-            for (int q = 0; q < OPL; ++q) {
-              const float d = xq[q] - v.y;
-              m[q] = fmaxf(m[q], fmaf(nk2, d * d, v.x));
-            }
-          }
-#pragma unroll
-          for (int q = 0; q < OPL; ++q)
-            if (m[q] == -INFINITY) m[q] = 0.0f;
-        }
-        for (int j = 0; j < nin; ++j) {
-          const float2 v = L[j];
-#pragma unroll
-          for (int q = 0; q < OPL; ++q) {
-            const float d = xq[q] - v.y;
-            S[q] += ex2_approx(fmaf(nk2, d * d, v.x - m[q]));
-          }
-        }
-        bool bad = false;
-#pragma unroll
-        for (int q = 0; q < OPL; ++q)
-          if (owns[q] && !exact) bad = bad || !(S[q] >= 0x1p-90f && S[q] <= 0x1p100f);
-        if (__any_sync(0xffffffffu, bad) && !exact) {
-          exact = true;
-          continue;  // warp-uniform: redo with exact maxima
-        }
-        break;
-      }
-#pragma unroll
-      for (int q = 0; q < OPL; ++q) {
-        if (!owns[q]) continue;
-        ff z = ff_ninf();
-        if (S[q] > 0.0f) {
-          // z = mx + ln2 m + ln2 log2(S), the first product kept exact in float-float
-          const ff ln2 = ln2_ff();
-          z = ff_add_f(ff_add_f(ff_mul_f(ln2, m[q]), mx), kLn2 * lg2_approx(S[q]));
-        }
-        if (zprev) zprev[my_pt[q]] = z.hi;
-        float n1, d1;
-        epilogue_apply(epi, bz, my_pt[q], z, pre[q], n1, d1);
-        num += n1;
-        den += d1;
-      }
+    for (int q = 0; q < OPL; ++q) {
+      if (!owns[q]) continue;
+      if (zprev) zprev[my_pt[q]] = z[q].hi;
+      float n1, d1;
+      epilogue_apply(epi, bz, my_pt[q], z[q], pre[q], n1, d1);
+      num += n1;
+      den += d1;
     }
   }
   // the warps of a block may belong to different batch entries: one sum per warp
@@ -930,6 +943,104 @@ __global__ void __launch_bounds__(kShortWarps * 32) grid_pass_f32_short(PassArgs
       atomicAdd(epi.err + 2 * bz + 1, (double)den);
     }
   }
+}
+
+// Two consecutive short passes fused (axes ax and ax - 1 of the separable
+// operator, each of at most 64 points, FP32).  A pass's line index is
+// s Pn + P, with P over the axes before its own (row-major, Pn of them) and s
+// over the already contracted axes after it.  Pass 1's line (s, P' n2 + j)
+// writes output o at o nl1 + l1, which is element j of pass 2's line
+// ((o S + s) Pc + P'): for a fixed group (P', s) the nin2 lines of pass 1 and
+// the nout1 lines of pass 2 form a closed plane.  One CTA per (group, batch entry)
+// computes pass 1 into shared memory (float-float, the value pass 1 would
+// write), then pass 2 from it with pass 2's epilogue; the results equal the
+// two separate passes bit for bit.  Saves a launch and the intermediate's
+// round trip through global memory.
+constexpr int kPlaneWarps = 32;  // a warp per line of each phase (two for lines of 33-64 points)
+
+template <int OPL1, int OPL2>
+__global__ void __launch_bounds__(kPlaneWarps * 32)
+    grid_pass_f32_plane(PassArgs a1, PassArgs a2, int S, Epilogue epi) {
+  extern __shared__ float2 inter[];  // [o1][nin2]: pass 1's results of the plane
+  __shared__ float2 sl[kPlaneWarps][kShortMax];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = blockIdx.x;
+  const int64_t bz = blockIdx.y;
+  const int Pc = gridDim.x / S;  // prefixes over the axes before the pair
+  const int sfx = g / Pc, Pp = g - sfx * Pc;
+  const int nin1 = a1.nin, nout1 = a1.nout, nin2 = a2.nin, nout2 = a2.nout;
+  const int64_t nl1 = a1.nlines, nl2 = a2.nlines;
+  const float2* in = a1.in + bz * nl1 * nin1;
+  float* zp1 = a1.zprev ? a1.zprev + bz * nl1 * nout1 : nullptr;
+  float* zp2 = a2.zprev ? a2.zprev + bz * nl2 * nout2 : nullptr;
+  const bool spec1 = a1.use_prev && zp1, spec2 = a2.use_prev && zp2;
+  float xq1[OPL1], xq2[OPL2];
+  bool own1[OPL1], own2[OPL2];
+#pragma unroll
+  for (int q = 0; q < OPL1; ++q) {
+    const int i = lane + 32 * q;
+    own1[q] = i < nout1;
+    xq1[q] = a1.xo[i < nout1 ? i : nout1 - 1];
+  }
+#pragma unroll
+  for (int q = 0; q < OPL2; ++q) {
+    const int i = lane + 32 * q;
+    own2[q] = i < nout2;
+    xq2[q] = a2.xo[i < nout2 ? i : nout2 - 1];
+  }
+  const float y10 = (lane < nin1) ? a1.yi[lane] : 0.0f, y11 = (lane + 32 < nin1) ? a1.yi[lane + 32] : 0.0f;
+  const float y20 = (lane < nin2) ? a2.yi[lane] : 0.0f, y21 = (lane + 32 < nin2) ? a2.yi[lane + 32] : 0.0f;
+  pdl_wait();
+  if (a1.zero_acc && g == 0 && threadIdx.x < 2) a1.zero_acc[2 * bz + threadIdx.x] = 0.0;
+  pdl_launch_dependents();
+  // ---- pass 1: the plane's nin2 lines ----
+  for (int j = warp; j < nin2; j += kPlaneWarps) {
+    const int64_t l1 = ((int64_t)sfx * Pc + Pp) * nin2 + j;
+    const int64_t base = l1 * nin1;
+    float zp[OPL1];
+#pragma unroll
+    for (int q = 0; q < OPL1; ++q) zp[q] = (spec1 && own1[q]) ? zp1[(int64_t)(lane + 32 * q) * nl1 + l1] : 0.0f;
+    const ff v0 = (lane < nin1) ? load_L_ff(a1, in, base + lane) : ff_ninf();
+    const ff v1 = (lane + 32 < nin1) ? load_L_ff(a1, in, base + lane + 32) : ff_ninf();
+    ff z[OPL1];
+    short_line_lse<OPL1>(v0, v1, y10, y11, nin1, xq1, zp, spec1, own1, a1.k2, sl[warp], z);
+#pragma unroll
+    for (int q = 0; q < OPL1; ++q) {
+      if (!own1[q]) continue;
+      const int i = lane + 32 * q;
+      if (zp1) zp1[(int64_t)i * nl1 + l1] = z[q].hi;
+      inter[i * nin2 + j] = make_float2(z[q].hi, z[q].lo);
+    }
+  }
+  __syncthreads();
+  // ---- pass 2: the plane's nout1 lines, from shared memory ----
+  float num = 0.0f, den = 0.0f;
+  for (int o = warp; o < nout1; o += kPlaneWarps) {
+    const int64_t l2 = ((int64_t)o * S + sfx) * Pc + Pp;
+    float zp[OPL2];
+    EpiPre pre[OPL2];
+    int64_t pt[OPL2];
+#pragma unroll
+    for (int q = 0; q < OPL2; ++q) {
+      pt[q] = (int64_t)(lane + 32 * q) * nl2 + l2;
+      zp[q] = (spec2 && own2[q]) ? zp2[pt[q]] : 0.0f;
+      if (own2[q]) epilogue_prefetch(epi, bz, pt[q], pre[q]);
+    }
+    const ff v0 = (lane < nin2) ? ffl(inter[o * nin2 + lane]) : ff_ninf();
+    const ff v1 = (lane + 32 < nin2) ? ffl(inter[o * nin2 + lane + 32]) : ff_ninf();
+    ff z[OPL2];
+    short_line_lse<OPL2>(v0, v1, y20, y21, nin2, xq2, zp, spec2, own2, a2.k2, sl[warp], z);
+#pragma unroll
+    for (int q = 0; q < OPL2; ++q) {
+      if (!own2[q]) continue;
+      if (zp2) zp2[pt[q]] = z[q].hi;
+      float n1, d1;
+      epilogue_apply(epi, bz, pt[q], z[q], pre[q], n1, d1);
+      num += n1;
+      den += d1;
+    }
+  }
+  if (epi.err) block_add2f<kPlaneWarps * 32>(num, den, epi.err + 2 * bz);
 }
 
 // ---------------------------------------------------------------------------
@@ -1319,6 +1430,83 @@ cudaError_t launch_ffp(const PassArgs& a, const Epilogue& epi, int nbatch, cudaS
 
 int grid_force_precise(int on) { return g_precise_forced.exchange(on ? 1 : 0); }
 int precise_forced() { return g_precise_forced.load(); }
+
+// 1: fuse short pass pairs where they qualify; 0 (the default): separate passes.  Measured on
+// the 64 x 32 x 32 colour grid: 61 ms fused against 45 ms separate per transfer (a plane per CTA
+// leaves 88 of 152 SMs idle; separate passes overlap through programmatic dependent launch).
+std::atomic<int> g_plane_mode{0};
+
+int grid_fuse_short_pairs(int mode) { return g_plane_mode.exchange(mode); }
+
+bool grid_plane_ok(int n1in, int n1out, int n2in, int n2out) {
+  // a forced tile (uot_force_grid_tile) other than the short-line kernel keeps every pass on it
+  return g_plane_mode.load() != 0 && (g_forced_tile < 0 || g_forced_tile == kShortTile) && n1in <= kShortMax &&
+         n1out <= kShortMax && n2in <= kShortMax && n2out <= kShortMax;
+}
+
+cudaError_t launch_grid_pass_plane(const double* in, const double* logw, int in_is_pot, int64_t ngroups, int S,
+                                   int nin1, const void* yi1, int nout1, const void* xo1, float* zprev1,
+                                   int nin2, const void* yi2, int nout2, const void* xo2, float* zprev2,
+                                   double eps, int nbatch, int use_prev, double* zero_acc, const Epilogue& epi,
+                                   cudaStream_t s) {
+  const int64_t Pc = ngroups / S;  // prefixes over the axes before the pair
+  if (ngroups < 1 || S < 1 || ngroups % S != 0 || nbatch < 1 || nbatch > 65535 || ngroups > INT32_MAX ||
+      Pc * std::max(nin2, nout1) * S > INT32_MAX)
+    return cudaErrorInvalidConfiguration;
+  PassArgs a1, a2;
+  memset(&a1, 0, sizeof(a1));
+  a1.in = reinterpret_cast<const float2*>(in);
+  a1.logw = reinterpret_cast<const float2*>(logw);
+  a1.in_is_pot = in_is_pot;
+  a1.nlines = (int)(Pc * nin2 * S);
+  a1.nin = nin1;
+  a1.nout = nout1;
+  a1.yi = (const float*)yi1;
+  a1.xo = (const float*)xo1;
+  a1.inv_eps = ff2(ff_make(1.0 / eps));
+  a1.k2 = (float)((double)kLog2e / eps);
+  a1.zprev = zprev1;
+  a1.use_prev = use_prev;
+  a1.zero_acc = zero_acc;
+  a1.nbatch = nbatch;
+  a2 = a1;
+  a2.in = nullptr;
+  a2.logw = nullptr;
+  a2.in_is_pot = 0;
+  a2.nlines = (int)(Pc * nout1 * S);
+  a2.nin = nin2;
+  a2.nout = nout2;
+  a2.yi = (const float*)yi2;
+  a2.xo = (const float*)xo2;
+  a2.zprev = zprev2;
+  a2.zero_acc = nullptr;
+  cudaLaunchConfig_t cfg;
+  memset(&cfg, 0, sizeof(cfg));
+  cfg.gridDim = dim3((unsigned)ngroups, (unsigned)nbatch);
+  cfg.blockDim = dim3(kPlaneWarps * 32);
+  cfg.dynamicSmemBytes = (size_t)nout1 * nin2 * sizeof(float2);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  auto kern = nout1 <= 32 ? (nout2 <= 32 ? grid_pass_f32_plane<1, 1> : grid_pass_f32_plane<1, 2>)
+                          : (nout2 <= 32 ? grid_pass_f32_plane<2, 1> : grid_pass_f32_plane<2, 2>);
+  cudaError_t e = smem_at_least(kern, cfg.dynamicSmemBytes);
+  if (e != cudaSuccess) return e;
+  prof_mark_begin(PROF_GRID_PASS, s);
+  count_launches(1);
+  if (nout1 <= 32)
+    e = nout2 <= 32 ? cudaLaunchKernelEx(&cfg, grid_pass_f32_plane<1, 1>, a1, a2, S, epi)
+                    : cudaLaunchKernelEx(&cfg, grid_pass_f32_plane<1, 2>, a1, a2, S, epi);
+  else
+    e = nout2 <= 32 ? cudaLaunchKernelEx(&cfg, grid_pass_f32_plane<2, 1>, a1, a2, S, epi)
+                    : cudaLaunchKernelEx(&cfg, grid_pass_f32_plane<2, 2>, a1, a2, S, epi);
+  if (e != cudaSuccess) return e;
+  prof_mark_end(PROF_GRID_PASS, s);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_grid_pass(int prec, const double* in, const double* logw, int in_is_pot,
                              int nlines, int nin, const void* yi, int nout, const void* xo,

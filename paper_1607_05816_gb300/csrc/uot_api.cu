@@ -129,8 +129,14 @@ cudaError_t smem_limit_at_least(const void* kernel, size_t bytes) {
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   std::lock_guard<std::mutex> lk(g_smem_mu);
-  size_t& cur = g_smem_limit[{dev, kernel}];
-  if (cur == 0) cur = 48 * 1024;  // the default limit, which needs no attribute
+  auto it = g_smem_limit.find({dev, kernel});
+  if (it == g_smem_limit.end()) {
+    // the limit in force (by default 48 KB less the kernel's static shared memory)
+    cudaFuncAttributes fa;
+    if ((e = cudaFuncGetAttributes(&fa, kernel)) != cudaSuccess) return e;
+    it = g_smem_limit.emplace(std::make_pair(dev, kernel), (size_t)fa.maxDynamicSharedSizeBytes).first;
+  }
+  size_t& cur = it->second;
   if (bytes <= cur) return cudaSuccess;
   if ((e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)) != cudaSuccess)
     return e;
@@ -173,6 +179,8 @@ uot_status uot_force_grid_tile(int idx) { return grid_force_tile(idx) == 0 ? UOT
 int uot_grid_tile_count(void) { return grid_tile_count(); }
 
 int uot_force_precise_passes(int on) { return grid_force_precise(on); }
+
+int uot_fuse_short_passes(int on) { return grid_fuse_short_pairs(on ? 1 : 0); }
 
 uot_status uot_selftest_bounded_wait(double seconds, void* stream) {
   clear_stale_error();

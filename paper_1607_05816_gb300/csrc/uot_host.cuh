@@ -962,6 +962,41 @@ struct Gibbs {
       int cur_is_pot = 1;
       for (int k = 0; k < d; ++k) {
         const int ax = d - 1 - k;
+        // two short FP32 passes in a row: one fused launch per plane
+        const bool f32 = prec == UOT_F32 || (prec == UOT_MIXED && tc_off);
+        if (f32 && k + 1 < d && !precise && !precise_forced() &&
+            grid_plane_ok(in_shape[ax], out_shape[ax], in_shape[ax - 1], out_shape[ax - 1])) {
+          int64_t Pc = 1, S = 1;
+          for (int t = 0; t < ax - 1; ++t) Pc *= in_shape[t];
+          for (int t = ax + 1; t < d; ++t) S *= out_shape[t];
+          const int64_t nlines2 = Pc * out_shape[ax] * S;
+          Epilogue e = epi;
+          if (k + 1 < d - 1) {
+            memset(&e, 0, sizeof(e));
+            e.mode = EPI_RAW;
+            e.eps = eps;
+            e.out = pass[(k + 1) & 1];
+            e.bstride = nlines2 * out_shape[ax - 1];
+          }
+          double* za = nullptr;
+          if (k == 0 && zero_acc) {
+            if (k + 1 < d - 1) {
+              za = zero_acc;  // cleared by the fused launch, accumulated by the last pass
+            } else {
+              cudaError_t e0 = cudaMemsetAsync(zero_acc, 0, 16 * (size_t)nbatch, s);
+              if (e0 != cudaSuccess) return e0;
+            }
+          }
+          cudaError_t err = launch_grid_pass_plane(
+              cur, logw, cur_is_pot, Pc * S, (int)S, in_shape[ax], in_axes[ax], out_shape[ax], out_axes[ax],
+              zbuf[dir][k], in_shape[ax - 1], in_axes[ax - 1], out_shape[ax - 1], out_axes[ax - 1], zbuf[dir][k + 1],
+              eps, nbatch, use_prev, za, e, s);
+          if (err != cudaSuccess) return err;
+          cur = pass[(k + 1) & 1];
+          cur_is_pot = 0;
+          ++k;
+          continue;
+        }
         int64_t nlines = 1;
         for (int t = 0; t < ax; ++t) nlines *= in_shape[t];
         for (int t = ax + 1; t < d; ++t) nlines *= out_shape[t];

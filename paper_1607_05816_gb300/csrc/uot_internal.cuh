@@ -487,6 +487,18 @@ struct BlkAxis {
   float d0;  // xo[0] - yi[0]
 };
 
+// Two consecutive FP32 passes over short axes (all four sizes <= 64) fused per
+// plane: ngroups = prefixes over the axes before the pair x S, S = the
+// contracted suffix; pass 1's intermediate stays in shared memory.
+// grid_fuse_short_pairs(mode) sets whether such pairs are fused (1) or run as
+// two passes (0, the default); returns the previous mode.
+int grid_fuse_short_pairs(int mode);
+bool grid_plane_ok(int n1in, int n1out, int n2in, int n2out);
+cudaError_t launch_grid_pass_plane(const double* in, const double* logw, int in_is_pot, int64_t ngroups, int S,
+                                   int nin1, const void* yi1, int nout1, const void* xo1, float* zprev1,
+                                   int nin2, const void* yi2, int nout2, const void* xo2, float* zprev2,
+                                   double eps, int nbatch, int use_prev, double* zero_acc, const Epilogue& epi,
+                                   cudaStream_t s);
 cudaError_t launch_grid_pass(int prec, const double* in, const double* logw, int in_is_pot,
                              int nlines, int nin, const void* yi, int nout, const void* xo,
                              double eps, int nbatch, const Epilogue& epi, cudaStream_t s,

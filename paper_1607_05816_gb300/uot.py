@@ -148,6 +148,7 @@ _SIGS = {
     "uot_selftest_bounded_wait": (C.c_int, [C.c_double, C.c_void_p]),
     "uot_probe_pipes": (C.c_int, [C.POINTER(C.c_double), C.c_void_p]),
     "uot_force_precise_passes": (C.c_int, [C.c_int]),
+    "uot_fuse_short_passes": (C.c_int, [C.c_int]),
     "uot_autotune_table": (C.c_int, [C.c_char_p, C.c_int]),
     "uot_barycenter_div": (C.c_int, [C.POINTER(CGeom), C.c_int, C.POINTER(C.c_double), C.c_void_p,
                                      C.c_void_p, C.c_void_p, C.POINTER(CDiv), C.POINTER(CDiv),
@@ -210,6 +211,13 @@ def force_precise_passes(on: bool) -> bool:
     """uot_force_precise_passes: every FP32 grid pass forms its exponents in
     float-float (on) or the usual tiles run (off); returns the previous setting."""
     return bool(load().uot_force_precise_passes(int(bool(on))))
+
+
+def fuse_short_passes(on: bool) -> bool:
+    """uot_fuse_short_passes: consecutive FP32 grid passes over axes of at most
+    64 points run as one launch per plane (on) or as separate passes (off, the
+    default); returns the previous setting."""
+    return bool(load().uot_fuse_short_passes(int(bool(on))))
 
 
 def force_grid_tile(idx: int):
