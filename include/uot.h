@@ -42,6 +42,8 @@
  *    on what else runs.  Exceptions: uot_gibbs_log_noalloc (one shared
  *    array), the profiling pair below, and the first use of a grid shape by
  *    the tile tuner (its timings, not its results, see the other streams).
+ *    The per-kernel launch settings are kept for the life of the process:
+ *    after a cudaDeviceReset the library must not be called again.
  *  - Errors are returned as uot_status, never thrown.  Arguments are checked on
  *    the host before any launch; UOT_EINVAL leaves outputs untouched.
  *  - There is no CPU fallback: if no sm_103a device is present every entry
