@@ -919,16 +919,81 @@ __global__ void __launch_bounds__(kShortWarps * 32) grid_pass_f32_short(PassArgs
   if (live) {
     const ff v0 = (lane < nin) ? load_L_ff(a, in, base + lane) : ff_ninf();
     const ff v1 = (lane + 32 < nin) ? load_L_ff(a, in, base + lane + 32) : ff_ninf();
-    ff z[OPL];
-    short_line_lse<OPL>(v0, v1, y0, y1, nin, xq, zp, spec, owns, a.k2, sl[warp], z);
+    const float mx = warp_maxf(fmaxf(v0.hi, v1.hi));
+    if (mx == -INFINITY) {
+      // b = 0 on the whole line: every sum is empty
 #pragma unroll
-    for (int q = 0; q < OPL; ++q) {
-      if (!owns[q]) continue;
-      if (zprev) zprev[my_pt[q]] = z[q].hi;
-      float n1, d1;
-      epilogue_apply(epi, bz, my_pt[q], z[q], pre[q], n1, d1);
-      num += n1;
-      den += d1;
+      for (int q = 0; q < OPL; ++q) {
+        if (!owns[q]) continue;
+        if (zprev) zprev[my_pt[q]] = -INFINITY;
+        float n1, d1;
+        epilogue_apply(epi, bz, my_pt[q], ff_ninf(), pre[q], n1, d1);
+        num += n1;
+        den += d1;
+      }
+    } else {
+      auto stage = [&](ff v) { return (v.hi == -INFINITY) ? -INFINITY : ((v.hi - mx) + v.lo) * kLog2e; };
+      sl[warp][lane] = make_float2(stage(v0), y0);
+      if (lane + 32 < kShortMax) sl[warp][lane + 32] = make_float2(stage(v1), y1);
+      __syncwarp();
+      const float2* L = sl[warp];
+      const float nk2 = -a.k2;
+      float m[OPL], S[OPL];
+      bool exact = !spec;
+      for (int attempt = 0; attempt < 2; ++attempt) {
+#pragma unroll
+        for (int q = 0; q < OPL; ++q) {
+          m[q] = (zp[q] == -INFINITY) ? 0.0f : (zp[q] - mx) * kLog2e;
+          S[q] = 0.0f;
+        }
+        if (exact) {
+#pragma unroll
+          for (int q = 0; q < OPL; ++q) m[q] = -INFINITY;
+          for (int j = 0; j < nin; ++j) {
+            const float2 v = L[j];
+#pragma unroll
+            for (int q = 0; q < OPL; ++q) {
+              const float d = xq[q] - v.y;
+              m[q] = fmaxf(m[q], fmaf(nk2, d * d, v.x));
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < OPL; ++q)
+            if (m[q] == -INFINITY) m[q] = 0.0f;
+        }
+        for (int j = 0; j < nin; ++j) {
+          const float2 v = L[j];
+#pragma unroll
+          for (int q = 0; q < OPL; ++q) {
+            const float d = xq[q] - v.y;
+            S[q] += ex2_approx(fmaf(nk2, d * d, v.x - m[q]));
+          }
+        }
+        bool bad = false;
+#pragma unroll
+        for (int q = 0; q < OPL; ++q)
+          if (owns[q] && !exact) bad = bad || !(S[q] >= 0x1p-90f && S[q] <= 0x1p100f);
+        if (__any_sync(0xffffffffu, bad) && !exact) {
+          exact = true;
+          continue;  // warp-uniform: redo with exact maxima
+        }
+        break;
+      }
+#pragma unroll
+      for (int q = 0; q < OPL; ++q) {
+        if (!owns[q]) continue;
+        ff z = ff_ninf();
+        if (S[q] > 0.0f) {
+          // z = mx + ln2 m + ln2 log2(S), the first product kept exact in float-float
+          const ff ln2 = ln2_ff();
+          z = ff_add_f(ff_add_f(ff_mul_f(ln2, m[q]), mx), kLn2 * lg2_approx(S[q]));
+        }
+        if (zprev) zprev[my_pt[q]] = z.hi;
+        float n1, d1;
+        epilogue_apply(epi, bz, my_pt[q], z, pre[q], n1, d1);
+        num += n1;
+        den += d1;
+      }
     }
   }
   // the warps of a block may belong to different batch entries: one sum per warp
