@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(kNW * 32)
     const f2p MA = pk(mq[0] == -INFINITY ? 0.0f : mq[0], mq[1] == -INFINITY ? 0.0f : mq[1]);
     const f2p MB = pk(mq[2] == -INFINITY ? 0.0f : mq[2], mq[3] == -INFINITY ? 0.0f : mq[3]);
     f2p SA = pk(0.0f, 0.0f), SB = SA;
-#pragma unroll 4
+#pragma unroll 8
     for (int j = 0; j < nj; ++j) {
       const float4 s0 = st[2 * j], s1 = st[2 * j + 1];
       const f2p T = pk(s0.x, s0.y), Y0 = pk(s0.z, s0.w), Y1 = pk(s1.x, s1.y), Y2 = pk(s1.z, s1.w);
