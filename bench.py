@@ -92,7 +92,7 @@ WORKLOAD = "grid2d-256x256-kl0.5-epsscale1e-1to1e-3-tol1e-6"
 # dram__bytes_read.sum + dram__bytes_write.sum of one grid_pass_f32<8, 4>
 # launch on this workload (profiles/grid_pass_f32_grid256.md); None once the
 # kernel changes after that capture.
-GRID_PASS_F32_TRAFFIC_BYTES = 903168
+GRID_PASS_F32_TRAFFIC_BYTES = 904192
 # --mass-div: Algorithm 4 (Sec. 4.5) on the same workload, a divergence on the
 # plan's total mass with target MASS_M0 (the plain solve's plan has mass ~1.14)
 MASS_M0 = 1.5
