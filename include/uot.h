@@ -97,7 +97,13 @@ typedef struct {
   /* UOT_GEOM_DENSE */
   const void* C; /* [n*m] row-major; C_ij >= 0 need not hold; +INFINITY means K_ij = 0 (not for
                     uot_objective or plain_scaling, which need finite costs); no NaN or -inf */
-  /* UOT_GEOM_GRID: potentials and densities are row-major arrays of the grid's shape */
+  /* UOT_GEOM_GRID: potentials and densities are row-major arrays of the grid's shape.
+     Size limits (UOT_EUNSUPPORTED, with a message, before any launch): every axis
+     has at most 3000 points, and every separable pass covers at most 65535 lines.
+     Passes run from the last axis to the first, so the pass along axis a covers the
+     input side's axes before a and the output side's axes after a.  1-D and 2-D
+     grids always fit; a 3-D grid fits when each product of two axes is at most
+     65535 (2 x 255 x 257 does, 2 x 256 x 256 does not). */
   int ndim;                        /* 1..UOT_MAX_DIM */
   int shape_x[UOT_MAX_DIM];        /* grid of X: shape_x[0] x ... x shape_x[ndim-1] */
   int shape_y[UOT_MAX_DIM];        /* grid of Y */

@@ -646,6 +646,9 @@ DivParams make_div(const uot_div& F) {
 
 bool prec_ok(int p) { return p == UOT_F64 || p == UOT_F32 || p == UOT_MIXED; }
 
+// Largest second launch-grid dimension: the most lines one grid pass covers.
+constexpr int64_t kMaxGridPassLines = 65535;
+
 uot_status check_geom(const uot_geom* g) {
   if (!g) return UOT_EINVAL;
   if (g->n < 1 || g->m < 1) return UOT_EINVAL;
@@ -661,11 +664,32 @@ uot_status check_geom(const uot_geom* g) {
         if (g->shape_x[k] < 1 || g->shape_y[k] < 1) return UOT_EINVAL;
         if (!g->axes_x[k] || !g->axes_y[k]) return UOT_EINVAL;
         // a staged line must fit in shared memory (4 warps x nin x 16 bytes)
-        if (g->shape_x[k] > 3000 || g->shape_y[k] > 3000) return UOT_EUNSUPPORTED;
+        if (g->shape_x[k] > 3000 || g->shape_y[k] > 3000) {
+          g_last_error = "grid axis longer than 3000 points";
+          return UOT_EUNSUPPORTED;
+        }
         nx *= g->shape_x[k];
         ny *= g->shape_y[k];
       }
-      return (nx == g->n && ny == g->m) ? UOT_OK : UOT_EINVAL;
+      if (nx != g->n || ny != g->m) return UOT_EINVAL;
+      // The pass kernels put the line index in the launch grid's second
+      // dimension.  Passes run from the last axis to the first; the pass along
+      // axis a covers the input side's axes before a and the output side's
+      // axes after a (in both directions).
+      for (int dir = 0; dir < 2; ++dir) {
+        const int* in_shape = dir == 0 ? g->shape_y : g->shape_x;
+        const int* out_shape = dir == 0 ? g->shape_x : g->shape_y;
+        for (int a = 0; a < g->ndim; ++a) {
+          int64_t lines = 1;
+          for (int t = 0; t < a; ++t) lines *= in_shape[t];
+          for (int t = a + 1; t < g->ndim; ++t) lines *= out_shape[t];
+          if (lines > kMaxGridPassLines) {
+            g_last_error = "a grid pass would run over more than 65535 lines (product of the other axes)";
+            return UOT_EUNSUPPORTED;
+          }
+        }
+      }
+      return UOT_OK;
     }
     default:
       return UOT_EINVAL;

@@ -182,6 +182,27 @@ def test_solve_grid_parity(divs, prec):
 
 
 @pytest.mark.parametrize("prec", [U.F64, U.F32])
+def test_degenerate_penalties(prec):
+    """Degenerate rows of Table 1 as F1, with F2 = KL(0.5): RG with
+    alpha = beta = 1 is the equality constraint; TV with lambda far above every
+    |U| never clamps, which is the equality update too; KL with a huge lambda
+    tends to it.  Each matches the oracle after 30 iterations, and the first
+    two reproduce the solve with F1 = EQ."""
+    og, lg, dx, dy, p, q = grid_problem((40, 67), (52, 38), 13, zeros=False)
+    F2 = (O.KL(0.5), U.KL(0.5))
+    _, Ueq, Veq, _ = run_both(og, lg, dx, dy, p, q, (O.EQ(), F2[0], U.EQ(), F2[1]), 0.01, 30, prec)
+    for OF, UF, like_eq in ((O.RG(1.0, 1.0), U.RG(1.0, 1.0), True), (O.TV(1e8), U.TV(1e8), True),
+                            (O.KL(1e8), U.KL(1e8), False)):
+        r, Ug, Vg, info = run_both(og, lg, dx, dy, p, q, (OF, F2[0], UF, F2[1]), 0.01, 30, prec)
+        assert info["iters"] == 30
+        assert rel_err(Ug, r["U"]) <= TOL[prec]
+        assert rel_err(Vg, r["V"]) <= TOL[prec]
+        if like_eq:
+            assert rel_err(Ug, Ueq) <= TOL[prec]
+            assert rel_err(Vg, Veq) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [U.F64, U.F32])
 def test_solve_grid_eps_scaling_parity(prec):
     """eps-scaling stages (Sec. 4.4) then iterations at the final eps."""
     og, lg, dx, dy, p, q = grid_problem((48, 48), (48, 48), 11, zeros=False)
@@ -400,6 +421,41 @@ def test_invalid_arguments_rejected():
         gp = grid_problem((8,), (8,), 1)
         U.solve(gp[1](U.F64), T(gp[4], U.F64), T(gp[2], U.F64), T(gp[5], U.F64), T(gp[3], U.F64),
                 U.KL(1.0), U.KL(1.0), 0.1, plain_scaling=True)
+
+
+@pytest.mark.parametrize("prec,tile", [(U.F64, -1), (U.F32, -1), (U.F32, 0), (U.F32, 8)])
+def test_grid_at_the_pass_line_limit(prec, tile):
+    """Largest grid passes.  On a 2 x 255 x 257 grid the pass along the first
+    axis runs over 255 * 257 = 65535 lines, the most one launch grid holds:
+    the operator matches the oracle in both directions, with the tuner's
+    choice, the first SIMT tile, and the warp-per-line pass (which takes the
+    2-point pass; the long axes fall back to the first tile).  One line past
+    the limit (2 x 256 x 256), or an axis longer than 3000 points, is refused
+    on the host with a message, before any launch."""
+    shape = (2, 255, 257)
+    og, lg, dx, dy, p, q = grid_problem(shape, shape, 41, zeros=False)
+    g = synth.rng(43)
+    eps = 0.01
+    U.force_grid_tile(tile)
+    try:
+        for transpose in (False, True):
+            W = g.normal(size=shape) * 0.05
+            W.ravel()[5:: 13] = -np.inf
+            w = dx if transpose else dy
+            W, w = rounded(prec, W, w)
+            want = O.apply_K_log(round_geom(og, prec), W, np.log(w), eps, transpose=transpose)
+            got = U.gibbs_log(lg(prec), T(W, prec).ravel(), T(w, prec).ravel(), eps, transpose, prec)
+            assert rel_err(to_np(got), want) <= TOL[prec]
+    finally:
+        U.force_grid_tile(-1)
+    for sx, sy, why in (((2, 256, 256), (2, 256, 256), "65535 lines"), ((3001,), (4,), "3000 points")):
+        _, lg2, dx2, dy2, p2, q2 = grid_problem(sx, sy, 5, zeros=False)
+        geo = lg2(prec)
+        with pytest.raises(U.UotError, match="EUNSUPPORTED.*" + why):
+            U.gibbs_log(geo, T(q2, prec).ravel(), T(dy2, prec).ravel(), eps, False, prec)
+        with pytest.raises(U.UotError, match="EUNSUPPORTED.*" + why):
+            U.solve(geo, *[T(a, prec).ravel() for a in (p2, dx2, q2, dy2)], U.KL(1.0), U.KL(1.0), eps,
+                    precision=prec, max_iter=5)
 
 
 @pytest.mark.parametrize("shape", [(48, 64), (9, 13, 6), (300,)])
