@@ -64,7 +64,7 @@ typedef enum {
   UOT_NUMERICAL = -3,    /* NaN appeared in the potentials */
   UOT_TIMEOUT = -4,      /* a bounded device-side wait expired */
   UOT_ECUDA = -5,        /* CUDA runtime error (no device, launch failure, ...) */
-  UOT_EUNSUPPORTED = -6  /* valid request outside what this build implements */
+  UOT_EUNSUPPORTED = -6  /* valid request outside what this library implements */
 } uot_status;
 
 /* Marginal penalties (Sec. 2.1 examples; Table 1 rows). */
@@ -102,8 +102,9 @@ typedef struct {
      has at most 3000 points, and every separable pass covers at most 65535 lines.
      Passes run from the last axis to the first, so the pass along axis a covers the
      input side's axes before a and the output side's axes after a.  1-D and 2-D
-     grids always fit; a 3-D grid fits when each product of two axes is at most
-     65535 (2 x 255 x 257 does, 2 x 256 x 256 does not). */
+     grids always fit; a 3-D grid with the same shape on both sides fits when each
+     product of two axes is at most 65535 (2 x 255 x 257 does, 2 x 256 x 256 does
+     not). */
   int ndim;                        /* 1..UOT_MAX_DIM */
   int shape_x[UOT_MAX_DIM];        /* grid of X: shape_x[0] x ... x shape_x[ndim-1] */
   int shape_y[UOT_MAX_DIM];        /* grid of Y */
@@ -653,7 +654,7 @@ uot_status uot_apply_bin_map(const float* pts, long long npts, int d, const int*
  * Learned warm start (not in the paper).  A small dilated convolutional
  * network maps (log p, log q, log eps, log lambda) on a grid to initial
  * potentials (U0, V0) that replace b = 1 of Algorithm 1; the plain iteration
- * remains the judge of the result.  These are its training and inference
+ * decides the result.  These are its training and inference
  * kernels; all arrays are FP32 device arrays, activations [N][C][H][W],
  * weights [Cout][Cin][3][3], biases [Cout].
  *

@@ -550,7 +550,7 @@ def _violation_from(U_old, U_new, S, logdx, eps):
 
 
 def marginal_violation(geom, dx, dy, p, q, F1, F2, eps, U, V):
-    """Stopping criterion of this build (the paper leaves it open, Alg. 1):
+    """Stopping criterion used here (the paper leaves it open, Alg. 1):
     relative L1(dx) distance between the plan's first marginal and the prox
     target prox^KL_{F1/eps}(K b); it is the Sinkhorn marginal error when F1 is
     the equality constraint."""

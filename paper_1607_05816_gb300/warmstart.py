@@ -3,7 +3,7 @@
 A small dilated convolutional network maps the features
 (log p, log q, log eps, log lambda) of a grid problem to initial potentials
 (U0, V0), which replace the cold start b = 1 of Algorithm 1.  The plain
-iteration stays the judge: it runs from the predicted potentials to the same
+iteration decides the result: it runs from the predicted potentials to the same
 tolerance, so the network can only change how many iterations are needed,
 never the answer.
 
