@@ -218,7 +218,10 @@ typedef struct {
 /* Version string of the library build. */
 const char* uot_version(void);
 
-/* Last CUDA error string seen by the library on this thread ("" if none). */
+/* Message of the last failed call on this thread: a CUDA error string or the
+   reason for a refusal ("" if none).  The solver, Gibbs, plan, objective,
+   barycenter, mass, WF, colour-transfer and self-test entry points reset it
+   when they start, so it describes the latest of those calls. */
 const char* uot_last_error(void);
 
 /*

@@ -71,9 +71,13 @@ uot_status fail_cuda(cudaError_t e, const char* what = nullptr, const char* file
     if (e_ != cudaSuccess) return fail_cuda(e_, #expr, __FILE__, __LINE__); \
   } while (0)
 
-// Errors raised by other code sharing this CUDA runtime (non-sticky ones) must
-// not be attributed to this call: clear them on entry.
-inline void clear_stale_error() { (void)cudaGetLastError(); }
+// At the start of every entry point: drop a non-sticky CUDA error left by
+// other code sharing this runtime, and the previous call's message, so that
+// uot_last_error() describes this call only.
+inline void clear_stale_error() {
+  (void)cudaGetLastError();
+  g_last_error.clear();
+}
 
 // ---------------------------------------------------------------------------
 // pointwise kernels

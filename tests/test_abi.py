@@ -88,3 +88,55 @@ def test_no_cpu_fallback(monkeypatch):
     with pytest.raises(OSError):
         uot.load(os.path.join(ROOT, "no-such-dir", "libuot.so"))
     assert uot._LIB is None
+
+
+def _grid_geom(shape_x, shape_y):
+    """A grid geometry whose axis pointers are placeholders: every call below
+    is refused by the host-side checks before any pointer is used."""
+    g = uot.CGeom()
+    g.kind, g.ndim = uot.GEOM_GRID, len(shape_x)
+    g.n, g.m = 1, 1
+    for k, (a, b) in enumerate(zip(shape_x, shape_y)):
+        g.shape_x[k], g.shape_y[k] = a, b
+        g.axes_x[k] = g.axes_y[k] = _PLACEHOLDER
+        g.n, g.m = g.n * a, g.m * b
+    return g
+
+
+_PLACEHOLDER = 1 << 12  # never dereferenced: the calls return before any use
+
+
+def test_host_checks_refuse_before_any_launch():
+    """Argument checks run on the host before the library touches a pointer,
+    allocates or launches (so this runs without a GPU): grid passes over more
+    than 65535 lines (the launch grid's second dimension) and axes over 3000
+    points are UOT_EUNSUPPORTED with a message; an empty axis and eps <= 0 are
+    UOT_EINVAL.  Every entry point resets the message when it starts, so a
+    refusal without a message does not show the previous call's."""
+    lib = uot.load()
+    P = ctypes.c_void_p(_PLACEHOLDER)
+
+    def gibbs(g, eps=0.1, prec=uot.F64):
+        return uot.STATUS[lib.uot_gibbs_log(ctypes.byref(g), P, P, eps, 0, prec, P, None)]
+
+    def solve(g):
+        o = uot.COpts(precision=uot.F64, eps=0.1, max_iter=10, check_every=1)
+        F = uot.CDiv(uot.DIV_KL, 1.0, 0.0, 0.0)
+        r = uot.CResult()
+        return uot.STATUS[lib.uot_solve(ctypes.byref(g), P, P, P, P, ctypes.byref(F), ctypes.byref(F),
+                                        ctypes.byref(o), P, P, ctypes.byref(r), None)]
+
+    over = _grid_geom((2, 256, 256), (2, 256, 256))  # the pass along axis 0 covers 256 * 256 lines
+    for call in (gibbs, solve):
+        assert call(over) == "UOT_EUNSUPPORTED"
+        assert b"65535 lines" in lib.uot_last_error()
+    long_axis = _grid_geom((3001,), (4,))
+    assert gibbs(long_axis, prec=uot.F32) == "UOT_EUNSUPPORTED"
+    assert b"3000 points" in lib.uot_last_error()
+    assert gibbs(_grid_geom((0, 4), (4, 4))) == "UOT_EINVAL"
+    assert lib.uot_last_error() == b""
+    assert gibbs(_grid_geom((4, 4), (4, 4)), eps=0.0) == "UOT_EINVAL"
+    assert lib.uot_last_error() == b""
+    # the pass into Y along its last axis covers X's first two axes: 300 * 300
+    # lines, although Y's own axes give at most 300
+    assert gibbs(_grid_geom((300, 300, 1), (1, 1, 300))) == "UOT_EUNSUPPORTED"
