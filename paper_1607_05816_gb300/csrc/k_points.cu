@@ -401,17 +401,25 @@ __global__ void __launch_bounds__(kFfpThreads) points_ffp(FfpArgs a, Epilogue ep
 
 }  // namespace
 
-// Chunking of the inputs: about 1024 inputs per chunk.
+// The chunk index is the launch grid's second dimension.
+constexpr int kMaxPointChunks = 65535;
+
+// Inputs of at most 65535 chunks of 1024: larger clouds take the general
+// FP32 row kernel instead of the chunked one.
+bool points_chunks_fit(int nin) { return (nin + 1023) / 1024 <= kMaxPointChunks; }
+
 // Chunking of the inputs: at most 1024 inputs per chunk; among the counts up
-// to 1.5x the least, the one that best balances the grid (output blocks x
-// chunks) over the 152 SMs -- the slowest SM sets the pass time -- with a
-// small charge for each extra chunk (more partial sums to combine).
+// to 1.5x the least (and at most kMaxPointChunks), the one that best balances
+// the grid (output blocks x chunks) over the 152 SMs -- the slowest SM sets
+// the pass time -- with a small charge for each extra chunk (more partial sums
+// to combine).
 int points_nchunks(int nin, int nout) {
   const int least = (nin + 1023) / 1024;
   const int oblocks = (nout + kOutBlk - 1) / kOutBlk;
+  const int most = std::min(least + least / 2, std::max(least, kMaxPointChunks));
   int best = least;
   double best_waste = 2.0;
-  for (int c = least; c <= least + least / 2; ++c) {
+  for (int c = least; c <= most; ++c) {
     if (c > 1 && (nin + c - 1) / c < 256) break;  // chunks of at least 256 inputs
     const long g = (long)oblocks * c;
     const long rounds = (g + 151) / 152;

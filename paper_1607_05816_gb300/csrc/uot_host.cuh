@@ -820,7 +820,10 @@ struct Gibbs {
       }
     }
   }
-  bool points_fast() const { return g.kind == UOT_GEOM_POINTS && prec != UOT_F64 && g.d <= 3; }
+  bool points_fast() const {
+    return g.kind == UOT_GEOM_POINTS && prec != UOT_F64 && g.d <= 3 && points_chunks_fit(g.n) &&
+           points_chunks_fit(g.m);
+  }
   // shifted input line (+ Lmax) and, for FP64 dense rows, its FP32 copy
   size_t lscratch_bytes(int64_t mx) const {
     if (g.kind == UOT_GEOM_DENSE && prec == UOT_F64) return std::max((size_t)mx * 8 + 512, rows_pf_scratch_bytes(mx));

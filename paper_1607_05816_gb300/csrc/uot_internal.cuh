@@ -664,6 +664,7 @@ cudaError_t launch_points_ffp(const float* x, const float* y, int d, int nout, i
 // first 4 bytes hold a counter that must be zero before the first launch.
 size_t rows_pf_scratch_bytes(int64_t nin);
 int points_nchunks(int nin, int nout);
+bool points_chunks_fit(int nin);
 cudaError_t launch_points(const float* x, const float* y, int d, int nout, int nin,
                           const double* W, const double* logw, double eps, float* bmax,
                           float* zprev, int use_prev, float2* part, const Epilogue& epi,
