@@ -1,7 +1,7 @@
 """Plain numpy FP64 reference of the warm-start network (test infrastructure only).
 
 The network is not part of the paper: it is the learned warm start of this
-build.  This module restates its forward pass in the most direct way (a sum
+library.  This module restates its forward pass in the most direct way (a sum
 of shifted image slices per 3x3 tap, zero padding, leaky ReLU with slope 0.1)
 and obtains gradients by central finite differences, so that the CUDA forward
 and backward kernels can be checked against something that shares no code

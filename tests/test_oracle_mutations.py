@@ -66,6 +66,31 @@ PLANTS = [
 ]
 
 
+# The same for the warm-start network's reference (oracle/net_oracle.py) and
+# its pins (tests/test_net_oracle.py): brute-force convolution, closed-form and
+# finite-difference gradients.
+NET_PLANTS = [
+    ("conv: taps flipped", "sl = xp[:, :, kh * dil:kh * dil + H, kw * dil:kw * dil + W]",
+     "sl = xp[:, :, (2 - kh) * dil:(2 - kh) * dil + H, (2 - kw) * dil:(2 - kw) * dil + W]",
+     "brute_force"),
+    ("conv: leak slope", "LEAK = 0.1", "LEAK = 0.2", "brute_force"),
+    ("conv: bias dropped", "y = np.zeros((N, Cout, H, W)) + np.asarray(b, dtype=np.float64)[None, :, None, None]",
+     "y = np.zeros((N, Cout, H, W))", "brute_force or closed_form"),
+    ("conv: padding of one for every dilation", "    pad = dil\n    xp = np.zeros((N, Cin, H + 2 * pad, W + 2 * pad))\n"
+     "    xp[:, :, pad:pad + H, pad:pad + W] = x\n    y = ",
+     "    pad = 1\n    xp = np.zeros((N, Cin, H + 2 * pad, W + 2 * pad))\n"
+     "    xp[:, :, pad:pad + H, pad:pad + W] = x\n    y = ", "brute_force"),
+    ("data gradient: gradient not shifted back",
+     "gs = gp[:, :, (2 - kh) * dil:(2 - kh) * dil + H, (2 - kw) * dil:(2 - kw) * dil + W]",
+     "gs = gp[:, :, kh * dil:kh * dil + H, kw * dil:kw * dil + W]", "conv2d_grads"),
+    ("weight gradient: tap flipped", 'dw[:, :, kh, kw] = np.einsum("nohw,nchw->oc", g, xs)',
+     'dw[:, :, 2 - kh, 2 - kw] = np.einsum("nohw,nchw->oc", g, xs)', "conv2d_grads"),
+    ("bias gradient over the channels", "return dx, dw, g.sum(axis=(0, 2, 3))",
+     "return dx, dw, g.sum(axis=(1, 2, 3))[: g.shape[1]]", "conv2d_grads"),
+    ("finite difference: one-sided step", "return (lp - lm) / (2 * h)", "return (lp - lm) / h", "closed_form"),
+]
+
+
 def _copy_tree(dst):
     """The oracle, its pins and the seeded input generator, nothing else."""
     shutil.copytree(os.path.join(ROOT, "oracle"), os.path.join(dst, "oracle"),
@@ -73,6 +98,7 @@ def _copy_tree(dst):
     os.makedirs(os.path.join(dst, "tests"))
     os.makedirs(os.path.join(dst, "paper_1607_05816_gb300"))
     for rel in ("pytest.ini", os.path.join("tests", "conftest.py"), os.path.join("tests", "test_oracle_pins.py"),
+                os.path.join("tests", "test_net_oracle.py"),
                 os.path.join("paper_1607_05816_gb300", "__init__.py"),
                 os.path.join("paper_1607_05816_gb300", "synth.py")):
         shutil.copy(os.path.join(ROOT, rel), os.path.join(dst, rel))
@@ -98,4 +124,24 @@ def test_unplanted_copy_passes_the_same_pins(tmp_path):
     sel = " or ".join(sorted({p[3] for p in PLANTS}))
     out = subprocess.run([sys.executable, "-m", "pytest", "tests/test_oracle_pins.py", "-q", "-k", sel],
                          cwd=str(tmp_path), capture_output=True, text=True, timeout=900)
+    assert out.returncode == 0, out.stdout[-2000:] + out.stderr[-2000:]
+
+
+@pytest.mark.parametrize("what,orig,planted,pins", NET_PLANTS, ids=[p[0] for p in NET_PLANTS])
+def test_planted_network_mistake_is_caught(tmp_path, what, orig, planted, pins):
+    _copy_tree(str(tmp_path))
+    path = os.path.join(str(tmp_path), "oracle", "net_oracle.py")
+    src = open(path).read()
+    assert src.count(orig) >= 1, f"the network oracle no longer contains the text of plant '{what}'"
+    open(path, "w").write(src.replace(orig, planted, 1))
+    out = subprocess.run([sys.executable, "-m", "pytest", "tests/test_net_oracle.py", "-q", "-x", "-k", pins],
+                         cwd=str(tmp_path), capture_output=True, text=True, timeout=600)
+    assert out.returncode == 1, f"plant '{what}' not caught:\n{out.stdout[-1500:]}{out.stderr[-1500:]}"
+
+
+def test_unplanted_network_copy_passes_the_same_pins(tmp_path):
+    _copy_tree(str(tmp_path))
+    sel = " or ".join(sorted({p[3] for p in NET_PLANTS}))
+    out = subprocess.run([sys.executable, "-m", "pytest", "tests/test_net_oracle.py", "-q", "-k", sel],
+                         cwd=str(tmp_path), capture_output=True, text=True, timeout=600)
     assert out.returncode == 0, out.stdout[-2000:] + out.stderr[-2000:]
